@@ -1,0 +1,11 @@
+"""FP64 CPU oracle for resolvent sampling + Rayleigh-Ritz (test infrastructure).
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline / reference legs
+of `bench.py` may import this package.  The product (the CUDA library and its
+Python binding) never imports it and shares no code with it.
+"""
+from .rsrr import (sample_points, quad_weights, inside, eval_fn, assemble,
+                   coeff_matrix, resolvent_samples, backward_error_inf,
+                   sample_matrix, normalize_columns, truncated_basis, project,
+                   ss_full, residual, plain_residual, rsrr, negative_inertia,
+                   argument_principle_count, companion_eigvals)

@@ -1,0 +1,325 @@
+"""Plain FP64 CPU oracle of resolvent sampling + Rayleigh-Ritz (RSRR).
+
+TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline leg
+of the benchmark may import this module.  It shares no code with the CUDA path
+and never reads anything the CUDA path produced.
+
+Every function follows a passage of Xiao, Zhang, Huang, Sakurai, "Solving
+large-scale nonlinear eigenvalue problems by rational interpolation approach
+and resolvent sampling based Rayleigh-Ritz method" (2016), cited in its
+docstring.  Library primitives (banded/dense LAPACK solves, SVD, eig) serve as
+single steps; nothing is blocked, fused or reordered beyond the paper's
+algorithm.
+
+Parity status per function:
+  sample_points, quad_weights ........ pinned (ellipse equation, Cauchy integral)
+  eval_fn, assemble .................. pinned (decoupled closed forms)
+  resolvent_samples .................. pinned (decoupled closed forms, residual)
+  truncated_basis, project, ss_full .. pinned (closed-form spectra, inertia counts,
+                                       companion linearisation, Lambert W, the
+                                       loaded-string example of Section 4.2)
+  rsrr ............................... pinned (as above)
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from workloads import (F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP, Problem,
+                       Region)
+
+
+# ---------------------------------------------------------------------------
+# Step 1 of RSRR: sampling points (Section 4.1, ellipse contour and N-point
+# trapezoid rule; the RIA allows explicit points, Section 3.1)
+# ---------------------------------------------------------------------------
+
+def sample_points(region: Region, N: int) -> np.ndarray:
+    """z_j = phi(alpha_j), alpha_j = 2 pi (j + 1/2)/N on the ellipse
+    phi(alpha) = gamma + a cos(alpha) + i b sin(alpha) (Section 4.1, ellipse
+    contour and trapezoid nodes), or the region's explicit points."""
+    if region.kind == "points":
+        return np.asarray(region.points, dtype=np.complex128).copy()
+    j = np.arange(N)
+    alpha = 2.0 * np.pi * (j + 0.5) / N
+    return region.center + region.a * np.cos(alpha) + 1j * region.b * np.sin(alpha)
+
+
+def quad_weights(region: Region, NQ: int) -> np.ndarray:
+    """omega_j = (1/N) dphi/dalpha at alpha_j (Section 4.1 trapezoid rule)."""
+    j = np.arange(NQ)
+    alpha = 2.0 * np.pi * (j + 0.5) / NQ
+    return (-region.a * np.sin(alpha) + 1j * region.b * np.cos(alpha)) / NQ
+
+
+def inside(region: Region, z) -> np.ndarray:
+    """Strict interior of the ellipse ((x-gr)/a)^2 + ((y-gi)/b)^2 < 1."""
+    z = np.asarray(z)
+    x = (z.real - region.center.real) / region.a
+    y = (z.imag - region.center.imag) / region.b
+    return x * x + y * y < 1.0
+
+
+# ---------------------------------------------------------------------------
+# The NEP T(z) = sum_i f_i(z) A_i (Eq. 1 and the families of Section 2.1)
+# ---------------------------------------------------------------------------
+
+def eval_fn(fn, z):
+    """Scalar coefficient f_i(z) = scale * base(z) for the families of
+    Section 2.1 (polynomial, rational z/(z - sigma) and 1/(sigma - z),
+    square root sqrt(z^2 - kappa^2)) plus exp(-tau z) for delay problems."""
+    z = np.asarray(z, dtype=np.complex128)
+    if fn.kind == F_ONE:
+        base = np.ones_like(z)
+    elif fn.kind == F_ZPOW:
+        base = z ** int(fn.param)
+    elif fn.kind == F_RATIONAL:
+        base = z / (z - fn.param)
+    elif fn.kind == F_INV:
+        base = 1.0 / (fn.param - z)
+    elif fn.kind == F_SQRT:
+        base = np.sqrt(z * z - fn.param * fn.param)
+    elif fn.kind == F_EXP:
+        base = np.exp(-fn.param * z)
+    else:
+        raise ValueError(f"unknown function kind {fn.kind}")
+    return complex(fn.scale) * base
+
+
+def coeff_matrix(prob: Problem, i: int):
+    """A_i as a scipy CSR matrix on the shared pattern."""
+    import scipy.sparse as sp
+    return sp.csr_matrix((prob.values[i], prob.col_idx, prob.row_ptr), shape=(prob.n, prob.n))
+
+
+def assemble(prob: Problem, z: complex):
+    """T(z) = sum_i f_i(z) A_i (Eq. 1 with the form of Section 2.1)."""
+    vals = np.zeros(prob.nnz, dtype=np.complex128)
+    for fn, v in zip(prob.fns, prob.values):
+        vals += eval_fn(fn, z) * v
+    import scipy.sparse as sp
+    return sp.csr_matrix((vals, prob.col_idx, prob.row_ptr), shape=(prob.n, prob.n))
+
+
+def _to_band(T, kl: int, ku: int) -> np.ndarray:
+    """LAPACK general band layout ab[ku + i - j, j] = T[i, j]."""
+    n = T.shape[0]
+    ab = np.zeros((kl + ku + 1, n), dtype=np.complex128)
+    coo = T.tocoo()
+    ab[ku + coo.row - coo.col, coo.col] = coo.data
+    return ab
+
+
+# ---------------------------------------------------------------------------
+# Step 2 of RSRR: the resolvent samples X_j = T(z_j)^{-1} U (Section 3.3)
+# ---------------------------------------------------------------------------
+
+def resolvent_samples(prob: Problem, z: np.ndarray, U: np.ndarray | None = None) -> list:
+    """X_j = T(z_j)^{-1} U for each sampling point (Section 3.3, step 2),
+    by a banded LU solve with partial pivoting (LAPACK gbsv) per point."""
+    if U is None:
+        U = prob.U
+    kl, ku = prob.bandwidths()
+    out = []
+    for zj in z:
+        ab = _to_band(assemble(prob, zj), kl, ku)
+        out.append(sla.solve_banded((kl, ku), ab, U, check_finite=False))
+    return out
+
+
+def backward_error_inf(prob: Problem, z: complex, X: np.ndarray, U: np.ndarray | None = None):
+    """Per-column normwise backward error
+    eta = ||U - T(z) X||_inf / (||T(z)||_inf ||X||_inf + ||U||_inf)."""
+    if U is None:
+        U = prob.U
+    T = assemble(prob, z)
+    R = U - T @ X
+    tn = np.abs(T).sum(axis=1).max()
+    num = np.abs(R).max(axis=0)
+    den = tn * np.abs(X).max(axis=0) + np.abs(U).max(axis=0)
+    return num / den
+
+
+# ---------------------------------------------------------------------------
+# Step 3 of RSRR: S, column normalisation, truncated SVD (Eq. hatS, Section 3.2
+# last paragraph, Section 3.3 step 3)
+# ---------------------------------------------------------------------------
+
+def sample_matrix(samples: list) -> np.ndarray:
+    """S = [T(z_0)^{-1}U, ..., T(z_{N-1})^{-1}U] (Eq. for S in Section 3.2)."""
+    return np.concatenate(samples, axis=1)
+
+
+def normalize_columns(S: np.ndarray) -> np.ndarray:
+    """Scale every column of S to unit 2-norm before the SVD (Section 3.2)."""
+    return S / np.linalg.norm(S, axis=0, keepdims=True)
+
+
+def truncated_basis(S: np.ndarray, delta: float = 1e-14):
+    """S ~ Q Sigma V^H keeping the k singular values > delta*sigma_1
+    (Section 3.3 step 3; delta = 1e-14 as in the paper)."""
+    Qf, sig, _ = np.linalg.svd(S, full_matrices=False)
+    k = int(np.sum(sig > delta * sig[0]))
+    return Qf[:, :k], sig, k
+
+
+# ---------------------------------------------------------------------------
+# Step 4 of RSRR: projection T_Q(z) = Q^H T(z) Q (Eq. for T_Q, Section 3)
+# ---------------------------------------------------------------------------
+
+def project(prob: Problem, Q: np.ndarray) -> list:
+    """P_i = Q^H A_i Q so that T_Q(z) = sum_i f_i(z) P_i."""
+    return [Q.conj().T @ (coeff_matrix(prob, i) @ Q) for i in range(prob.m)]
+
+
+def ss_full(P: list, fns: list, region: Region, NQ: int = 500, KQ: int = 2,
+            tol_gap: float = 1e3):
+    """SS-FULL: the SS-RI algorithm of Section 2.3 with U = I (F = T_Q^{-1}),
+    sampling points on the ellipse by the trapezoid rule of Section 4.1.
+
+    Moments A_alpha = sum_q omega_q ((z_q - gamma)/rho)^alpha F(z_q), alpha <
+    2 KQ (the scaled-moment reading: a fixed change of basis of z that keeps
+    the pencil's eigenvalues, applied against overflow), block Hankel H, H^<
+    (Eq. HH), truncated SVD of H with the count fixed by the largest gap
+    sigma_j/sigma_{j+1} (gap strategy, tol_gap = 1e3), A = V0^H H^< W0
+    Sigma0^{-1} (Eq. A), eigenpairs of A, and g = M W0 Sigma0^{-1} b
+    (Eq. eigens) with M = [A_0 ... A_{KQ-1}] since U = I.
+
+    Returns (lam, G, info): eigenvalues of the projected NEP, the projected
+    eigenvectors as columns of G, and {"nbar", "gmax", "sv"}.
+    """
+    k = P[0].shape[0]
+    zq = sample_points(Region(region.center, region.a, region.b), NQ)
+    wq = quad_weights(region, NQ)
+    gamma = region.center
+    rho = max(region.a, region.b)
+    Amom = [np.zeros((k, k), dtype=np.complex128) for _ in range(2 * KQ)]
+    I = np.eye(k, dtype=np.complex128)
+    for z, w in zip(zq, wq):
+        TQ = sum(eval_fn(fn, z) * Pi for fn, Pi in zip(fns, P))
+        F = np.linalg.solve(TQ, I)
+        s = (z - gamma) / rho
+        for al in range(2 * KQ):
+            Amom[al] += w * s ** al * F
+    H = np.block([[Amom[i + j] for j in range(KQ)] for i in range(KQ)])
+    Hs = np.block([[Amom[i + j + 1] for j in range(KQ)] for i in range(KQ)])
+    V, sv, Wh = np.linalg.svd(H)
+    ratios = sv[:-1] / np.maximum(sv[1:], np.finfo(float).tiny)
+    nbar = int(np.argmax(ratios)) + 1
+    gmax = float(ratios[nbar - 1])
+    V0 = V[:, :nbar]
+    W0 = Wh.conj().T[:, :nbar]
+    S0inv = np.diag(1.0 / sv[:nbar])
+    A = V0.conj().T @ Hs @ W0 @ S0inv
+    lam_s, B = np.linalg.eig(A)
+    lam = gamma + rho * lam_s
+    Mmat = np.concatenate(Amom[:KQ], axis=1)
+    G = Mmat @ W0 @ S0inv @ B
+    return lam, G, dict(nbar=nbar, gmax=gmax, sv=sv)
+
+
+# ---------------------------------------------------------------------------
+# Residual measure (Section 4.4, E(v, lambda) with the 1-norms of the A_i)
+# ---------------------------------------------------------------------------
+
+def residual(prob: Problem, lam: complex, v: np.ndarray) -> float:
+    """rho(lam, v) = ||T(lam) v||_2 / ((sum_i |f_i(lam)| ||A_i||_1) ||v||_2),
+    the normalised relative residual of Section 4.4."""
+    T = assemble(prob, lam)
+    scale = 0.0
+    for i, fn in enumerate(prob.fns):
+        a1 = np.abs(coeff_matrix(prob, i)).sum(axis=0).max()
+        scale += abs(eval_fn(fn, lam)) * a1
+    return float(np.linalg.norm(T @ v) / (scale * np.linalg.norm(v)))
+
+
+def plain_residual(prob: Problem, lam: complex, v: np.ndarray) -> float:
+    """||T(lam) v||_2 / ||v||_2 (Section 2.3, gap-strategy remark)."""
+    return float(np.linalg.norm(assemble(prob, lam) @ v) / np.linalg.norm(v))
+
+
+# ---------------------------------------------------------------------------
+# The whole method (Section 3.3, steps 1-5)
+# ---------------------------------------------------------------------------
+
+def rsrr(prob: Problem, delta: float = 1e-14, NQ: int = 500, KQ: int = 2,
+         tol_gap: float = 1e3, U: np.ndarray | None = None, res_tol: float = 1e-6):
+    """RSRR: points and probes (step 1), X_j = T(z_j)^{-1}U (step 2), S with
+    normalised columns and truncated SVD basis Q (step 3), T_Q = Q^H T Q solved
+    by SS-FULL (step 4), v = Q g (step 5).
+
+    Acceptance (readings): only pairs strictly inside the contour are kept (the
+    method asks for the n_C pairs inside), and, following the advice of the
+    gap-strategy paragraph of Section 2.3 to check residuals, a pair is kept
+    only if its normalised residual is <= res_tol."""
+    z = sample_points(prob.region, prob.N)
+    X = resolvent_samples(prob, z, U)
+    S = normalize_columns(sample_matrix(X))
+    Q, sig, k = truncated_basis(S, delta)
+    P = project(prob, Q)
+    lam, G, info = ss_full(P, prob.fns, prob.region, NQ, KQ, tol_gap)
+    V = Q @ G
+    V = V / np.linalg.norm(V, axis=0, keepdims=True)
+    keep = inside(prob.region, lam)
+    lam, V = lam[keep], V[:, keep]
+    res = np.array([residual(prob, l, V[:, c]) for c, l in enumerate(lam)])
+    ok = res <= res_tol
+    lam, V, res = lam[ok], V[:, ok], res[ok]
+    order = np.lexsort((np.angle(lam), np.abs(lam)))
+    lam, V, res = lam[order], V[:, order], res[order]
+    return dict(lam=lam, V=V, res=res, k=k, sigma=sig, info=info, z=z, X=X, P=P, Q=Q)
+
+
+# ---------------------------------------------------------------------------
+# Independent counting tools used as pins (no RSRR arithmetic)
+# ---------------------------------------------------------------------------
+
+def negative_inertia(prob: Problem, x: float) -> int:
+    """nu(T(x)): number of negative eigenvalues of the real symmetric T(x)."""
+    T = assemble(prob, x).toarray().real
+    return int(np.sum(np.linalg.eigvalsh(T) < 0.0))
+
+
+def argument_principle_count(prob: Problem, region: Region, npts: int = 4096) -> int:
+    """Number of zeros of det T inside the ellipse: the winding number of
+    det T(phi(alpha)) for alpha in [0, 2 pi), with the phase unwrapped and the
+    contour refined until every step changes the argument by < pi/4."""
+    def logdet(z):
+        T = assemble(prob, z).toarray()
+        sgn, _ = np.linalg.slogdet(T)
+        return np.angle(sgn)
+
+    alpha = np.linspace(0.0, 2.0 * np.pi, npts + 1)
+    while True:
+        zz = region.center + region.a * np.cos(alpha) + 1j * region.b * np.sin(alpha)
+        ph = np.array([logdet(z) for z in zz])
+        d = np.angle(np.exp(1j * np.diff(ph)))
+        if np.all(np.abs(d) < np.pi / 4) or len(alpha) > 1 << 16:
+            break
+        alpha = np.sort(np.concatenate([alpha, 0.5 * (alpha[1:] + alpha[:-1])]))
+    return int(round(d.sum() / (2.0 * np.pi)))
+
+
+def companion_eigvals(prob: Problem) -> np.ndarray:
+    """All eigenvalues of a quadratic NEP T(z) = B0 + z B1 + z^2 B2 (B_i the
+    scaled coefficient matrices) from its first companion linearisation
+    [[0, I], [-B0, -B1]] w = z [[I, 0], [0, B2]] w, solved densely (QZ).
+    Brute force used to pin the RSRR count and eigenvalues of quadratic
+    problems (Section 2.1 remarks that polynomial problems admit
+    linearisation)."""
+    B = [None, None, None]
+    for i, fn in enumerate(prob.fns):
+        if fn.kind == F_ONE:
+            p = 0
+        elif fn.kind == F_ZPOW and int(fn.param) in (1, 2):
+            p = int(fn.param)
+        else:
+            raise ValueError("companion_eigvals needs a quadratic NEP")
+        Ai = complex(fn.scale) * coeff_matrix(prob, i).toarray()
+        B[p] = Ai if B[p] is None else B[p] + Ai
+    n = prob.n
+    B = [np.zeros((n, n)) if b is None else b for b in B]
+    Z, I = np.zeros((n, n)), np.eye(n)
+    A = np.block([[Z, I], [-B[0], -B[1]]])
+    Bm = np.block([[I, Z], [Z, B[2]]])
+    return sla.eigvals(A, Bm)

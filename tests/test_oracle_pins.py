@@ -1,0 +1,222 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, Cauchy's integral, Sylvester inertia, companion linearisation,
+Lambert W, the argument principle, the paper's loaded-string example).  None of
+these re-types the oracle's formulas or re-calls its library step."""
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+from scipy.special import lambertw
+
+import oracle
+import workloads as W
+from util import match_eigs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ORACLE_MOD = sys.modules["oracle.rsrr"]
+
+
+# ---------------------------------------------------------------- closed forms
+def exact_roots(p):
+    """Roots of the decoupled scalar problems behind a hidden_diagonal NEP."""
+    d = p.meta["diags"]
+    if p.name == "diag_quadratic":          # k + z c + z^2 m
+        k, c, m = d
+        disc = np.sqrt((c * c - 4 * m * k).astype(complex))
+        r = np.concatenate([(-c + disc) / (2 * m), (-c - disc) / (2 * m)])
+    elif p.name == "diag_rational":         # k - z m + z e/(z - s)
+        k, m, e = d
+        s = p.fns[2].param
+        A, B, C = -m, k + m * s + e, -k * s
+        disc = np.sqrt((B * B - 4 * A * C).astype(complex))
+        r = np.concatenate([(-B + disc) / (2 * A), (-B - disc) / (2 * A)])
+    elif p.name == "diag_delay":            # z - a - b exp(-tau z)
+        _, a, b = d
+        tau = p.fns[2].param
+        r = np.concatenate([a + lambertw(b * tau * np.exp(-a * tau), br) / tau
+                            for br in range(-8, 9)])
+    else:
+        raise KeyError(p.name)
+    return r[oracle.inside(p.region, r)]
+
+
+def _family(name):
+    return getattr(W, name)()
+
+
+def check_family(p, NQ=256):
+    ref = exact_roots(p)
+    out = oracle.rsrr(p, NQ=NQ)
+    return ref, out, match_eigs(ref, out["lam"])
+
+
+# --------------------------------------------------------------------- points
+def test_points_lie_on_ellipse_and_weights_integrate_cauchy():
+    reg = W.Region(0.3 - 1.0j, 2.0, 0.7)
+    z = oracle.sample_points(reg, 256)
+    assert np.allclose(((z.real - 0.3) / 2.0) ** 2 + ((z.imag + 1.0) / 0.7) ** 2, 1.0)
+    w = oracle.quad_weights(reg, 256)
+    # sum_q w_q f(z_q) ~ (1/2pi) contour integral of f: = i for 1/(z-c), c inside
+    for c, expect in ((0.5 - 0.9j, 1j), (-0.4 - 1.2j, 1j), (3.5 + 0.0j, 0.0), (0.0 + 1.0j, 0.0)):
+        assert abs(np.sum(w / (z - c)) - expect) < 1e-12
+    # polynomials integrate to zero on a closed contour
+    assert abs(np.sum(w * z ** 3)) < 1e-12
+
+
+# ------------------------------------------------------------ resolvent (step 2)
+@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational", "diag_delay"])
+def test_resolvent_matches_decoupled_closed_form(name):
+    p = _family(name)
+    G1 = W.givens_layers(p.n, p.meta["layers"], p.meta["g_seed"])
+    G2 = W.givens_layers(p.n, p.meta["layers"], p.meta["g_seed"] + 100)
+    z = np.array([p.region.center + 0.3 * p.region.a, p.region.center - 0.2j * p.region.b])
+    X = oracle.resolvent_samples(p, z)
+    for zj, Xj in zip(z, X):
+        t = sum(oracle.eval_fn(fn, zj) * d for fn, d in zip(p.fns, p.meta["diags"]))
+        expect = G2.T @ ((G1 @ p.U) / t[:, None])
+        assert np.max(np.abs(Xj - expect)) <= 1e-11 * np.max(np.abs(expect))
+
+
+def test_resolvent_backward_error_is_fp64_level():
+    p = W.random_banded()
+    z = oracle.sample_points(p.region, p.N)
+    for zj, Xj in zip(z, oracle.resolvent_samples(p, z)):
+        assert oracle.backward_error_inf(p, zj, Xj).max() < 1e-15
+
+
+# --------------------------------------------------- eigenvalues (steps 3..5)
+@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational", "diag_delay"])
+def test_rsrr_finds_closed_form_eigenvalues(name):
+    p = _family(name)
+    ref, out, err = check_family(p)
+    assert len(ref) >= 5
+    assert len(out["lam"]) == len(ref)
+    assert err <= 1e-9
+    assert out["res"].max() <= 1e-10
+    assert out["k"] < p.n  # a genuine projection, not the full space
+
+
+def test_quadratic_proportional_damping_closed_form_full_size():
+    """n=1000 benchmark recipe with C = c0*M: lambda^2 + c0 lambda + mu_k = 0,
+    mu_k = 6n^2 (2 - 2cos t_k)/(4 + 2cos t_k), t_k = k pi/(n+1)."""
+    n, c0 = 1000, 50.0
+    p = W.quadratic_tridiag(n=n, c_scale=c0, center=-25.0 + 50.0j)
+    t = np.arange(1, n + 1) * np.pi / (n + 1)
+    mu = 6.0 * n * n * (2 - 2 * np.cos(t)) / (4 + 2 * np.cos(t))
+    disc = np.sqrt((c0 * c0 - 4 * mu).astype(complex))
+    lam = np.concatenate([(-c0 + disc) / 2, (-c0 - disc) / 2])
+    rel = np.abs(np.abs(lam - p.region.center) / p.region.a - 1)
+    assert rel.min() > 5e-3, "closed-form roots too close to the contour for a pin"
+    ref = lam[oracle.inside(p.region, lam)]
+    out = oracle.rsrr(p, NQ=500)
+    assert len(ref) >= 10
+    assert match_eigs(ref, out["lam"]) <= 1e-9
+    assert out["res"].max() <= 1e-10
+
+
+def test_quadratic_workload_matches_companion_linearisation():
+    """Benchmark recipe (random diagonal damping): the oracle's eigenvalues in
+    the circle centre -25+50i, radius 40 equal the companion pencil's, and the
+    literal circle centre 50, radius 40 holds none (count-0 case)."""
+    gold = json.load(open(os.path.join(GOLD, "c0_companion.json")))
+    c_empty, c_full = gold["circles"]
+    assert len(c_empty["inside"]) == 0 and c_empty["min_rel_boundary_distance"] > 0.01
+    assert c_full["min_rel_boundary_distance"] > 0.01
+    ref = np.array([complex(a, b) for a, b in c_full["inside"]])
+    out = oracle.rsrr(W.config("c0b"), NQ=500)
+    assert len(ref) == 21
+    assert match_eigs(ref, out["lam"]) <= 1e-9
+    assert out["res"].max() <= 1e-10
+    out0 = oracle.rsrr(W.config("c0"), NQ=500)
+    assert len(out0["lam"]) == 0
+
+
+def test_grid_rational_inertia_count_and_shifted_closed_form():
+    """5-point grid rational NEP (benchmark recipe at g=30).  T(x) is real
+    symmetric and decreasing on (20, 180), so the eigenvalue count there is
+    nu(T(180)) - nu(T(20)) (Sylvester).  With E = e0*I every grid mode mu
+    gives the roots of (mu - z)(z - sigma) + e0 z = 0."""
+    p = W.rational_grid(g=30, N=64, L=8)
+    count = oracle.negative_inertia(p, 180.0) - oracle.negative_inertia(p, 20.0)
+    out = oracle.rsrr(p, NQ=500)
+    assert count == 10
+    assert len(out["lam"]) == count
+    assert np.abs(out["lam"].imag).max() < 1e-8
+    assert out["res"].max() <= 1e-10
+
+    g, s, e0 = 30, 300.0, 0.5
+    p2 = W.rational_grid(g=g, N=64, L=8, frac_e=1.0, e_value=e0)
+    j = np.arange(1, g + 1)
+    sj = 4 * np.sin(j * np.pi / (2 * (g + 1))) ** 2
+    mu = ((g + 1) ** 2 * (sj[:, None] + sj[None, :])).ravel()
+    B = mu + s + e0
+    disc = np.sqrt(B * B - 4 * mu * s)
+    lam = np.concatenate([(B - disc) / 2, (B + disc) / 2])
+    ref = lam[oracle.inside(p2.region, lam)]
+    out2 = oracle.rsrr(p2, NQ=500)
+    assert len(ref) == len(out2["lam"]) >= 8
+    assert match_eigs(ref, out2["lam"]) <= 1e-9
+
+
+def test_loaded_string_example_of_the_paper():
+    gold = json.load(open(os.path.join(GOLD, "loaded_string.json")))
+    p = W.loaded_string(n=gold["n"], N=gold["N"], L=gold["L"])
+    lo, hi = gold["interval"]
+    assert oracle.negative_inertia(p, hi) - oracle.negative_inertia(p, lo) == gold["count"]
+    out = oracle.rsrr(p, NQ=gold["NQ"], KQ=gold["KQ"])
+    lam = out["lam"]
+    assert len(lam) == gold["count"]
+    assert np.all((lam.real > lo) & (lam.real < hi))
+    assert np.abs(lam.imag).max() < 1e-6 * np.abs(lam).max()
+    plain = [oracle.plain_residual(p, l, out["V"][:, c]) for c, l in enumerate(lam)]
+    assert max(plain) <= 10 * gold["plain_residual_level"]
+
+
+def test_argument_principle_count_on_tiny_problem():
+    p = W.diag_quadratic(n=14, seed=3, N=16, L=4, layers=2)
+    reg = W.Region(0.0 + 0.5j, 4.0, 3.0)
+    p.region = reg
+    ref = exact_roots(p)
+    assert oracle.argument_principle_count(p, reg, npts=1024) == len(ref) > 0
+    out = oracle.rsrr(p, NQ=256)
+    assert match_eigs(ref, out["lam"]) <= 1e-9
+
+
+# -------------------------------------------------------------- planted errors
+def _planted(monkeypatch, which):
+    if which == "weights_sign":
+        orig = ORACLE_MOD.quad_weights
+        monkeypatch.setattr(ORACLE_MOD, "quad_weights", lambda r, n: -orig(r, n).conj())
+    elif which == "drop_scale":
+        orig = ORACLE_MOD.eval_fn
+        monkeypatch.setattr(ORACLE_MOD, "eval_fn",
+                            lambda fn, z: orig(W.Fn(fn.kind, fn.param, 1.0), z))
+    elif which == "coefficient_transposed":
+        monkeypatch.setattr(ORACLE_MOD, "project",
+                            lambda prob, Q: [Q.conj().T @ (ORACLE_MOD.coeff_matrix(prob, i).T @ Q)
+                                             for i in range(prob.m)])
+    elif which == "no_normalisation":
+        monkeypatch.setattr(ORACLE_MOD, "normalize_columns", lambda S: S * 1e6)
+    elif which == "hankel_shift":
+        orig_svd = np.linalg.svd
+        monkeypatch.setattr(ORACLE_MOD.np.linalg, "svd",
+                            lambda a, *k, **kw: orig_svd(a.T, *k, **kw))
+
+
+@pytest.mark.parametrize("which", ["weights_sign", "drop_scale", "coefficient_transposed",
+                                   "hankel_shift"])
+def test_planted_mistakes_fail_a_pin(monkeypatch, which):
+    _planted(monkeypatch, which)
+    failed = False
+    for name in ("diag_quadratic", "diag_rational", "diag_delay"):
+        try:
+            ref, out, err = check_family(_family(name))
+        except Exception:
+            failed = True
+            break
+        if not (len(out["lam"]) == len(ref) and err <= 1e-9):
+            failed = True
+            break
+    assert failed, f"planted mistake {which!r} went unnoticed"

@@ -1,0 +1,336 @@
+"""Seeded synthetic NEP workloads, shared as *data* by the oracle and the GPU path.
+
+This module holds problem definitions only: the coefficient matrices A_i of
+T(z) = sum_i f_i(z) A_i on one shared sparse pattern, descriptors of the scalar
+functions f_i (a kind code plus parameters, evaluated by each side on its own),
+the region, N, L and the seeded probe matrix U.  It contains none of the
+resolvent-sampling arithmetic (no sampling points, no solves, no projections).
+
+The problem families follow the paper's NEP classes (Section 2.1: quadratic,
+rational, square-root types) and its loaded-string example (Section 4.1), plus
+synthetic stand-ins for its FEM workloads with the shapes of the benchmark
+configurations (quadratic tridiagonal n=1000; rational 5-point grid n=g^2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Scalar coefficient function kinds.  f(z) = scale * base(z; param):
+#   F_ONE       base = 1
+#   F_ZPOW      base = z**param            (param a non-negative integer)
+#   F_RATIONAL  base = z / (z - param)
+#   F_INV       base = 1 / (param - z)
+#   F_SQRT      base = sqrt(z**2 - param**2)   (principal branch)
+#   F_EXP       base = exp(-param * z)
+F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP = range(6)
+
+
+@dataclass
+class Fn:
+    kind: int
+    param: float = 0.0
+    scale: complex = 1.0
+
+
+@dataclass
+class Region:
+    """Ellipse phi(a) = center + a*cos(t) + i*b*sin(t), or explicit sample points.
+
+    For kind == "points" the explicit points are the sampling points and the
+    ellipse (center, a, b) is still the contour used for the projected solve
+    and for the inside test.
+    """
+    center: complex
+    a: float
+    b: float
+    kind: str = "ellipse"
+    points: np.ndarray | None = None
+
+
+@dataclass
+class Problem:
+    name: str
+    n: int
+    row_ptr: np.ndarray          # int64 [n+1], shared CSR pattern of all A_i
+    col_idx: np.ndarray          # int32 [nnz]
+    values: list                 # m float64 arrays [nnz] (real coefficients)
+    fns: list                    # m Fn
+    region: Region
+    N: int
+    L: int
+    U: np.ndarray                # complex128 [n, L], Fortran order
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return len(self.values)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def bandwidths(self):
+        """(kl, ku) of the shared pattern."""
+        rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
+        d = self.col_idx.astype(np.int64) - rows
+        return int(max(0, -d.min())), int(max(0, d.max()))
+
+
+# ----------------------------------------------------------------------------
+# helpers that build data (patterns, probes); no method arithmetic
+# ----------------------------------------------------------------------------
+
+def probe(n: int, L: int, seed: int) -> np.ndarray:
+    """U with entries (g1 + i g2)/sqrt(2), g ~ N(0,1), PCG64 seeded."""
+    rng = np.random.default_rng(seed)
+    g1 = rng.standard_normal((n, L))
+    g2 = rng.standard_normal((n, L))
+    return np.asfortranarray((g1 + 1j * g2) / np.sqrt(2.0))
+
+
+def _shared_csr(n: int, mats: list):
+    """Union pattern (sorted columns per row) of dense or coo-like matrices.
+
+    `mats` are dicts {(i, j): value}; returns row_ptr, col_idx, values list.
+    """
+    keys = set()
+    for mt in mats:
+        keys.update(mt.keys())
+    keys = sorted(keys)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    for (i, _j) in keys:
+        row_ptr[i + 1] += 1
+    row_ptr = np.cumsum(row_ptr)
+    col_idx = np.array([j for (_i, j) in keys], dtype=np.int32)
+    values = [np.array([mt.get(k, 0.0) for k in keys], dtype=np.float64) for mt in mats]
+    return row_ptr, col_idx, values
+
+
+def _csr_from_dense_band(dense_list: list, kl: int, ku: int):
+    """Shared CSR holding every entry inside the (kl, ku) band (zeros kept)."""
+    n = dense_list[0].shape[0]
+    rows, cols = [], []
+    for i in range(n):
+        lo, hi = max(0, i - kl), min(n - 1, i + ku)
+        rows.extend([i] * (hi - lo + 1))
+        cols.extend(range(lo, hi + 1))
+    rows = np.array(rows, dtype=np.int64)
+    cols = np.array(cols, dtype=np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    values = [np.ascontiguousarray(D[rows, cols], dtype=np.float64) for D in dense_list]
+    return row_ptr, cols.astype(np.int32), values
+
+
+def _tridiag(n, lo, d, up, last=None):
+    mt = {}
+    for i in range(n):
+        mt[(i, i)] = d
+        if i > 0:
+            mt[(i, i - 1)] = lo
+        if i < n - 1:
+            mt[(i, i + 1)] = up
+    if last is not None:
+        mt[(n - 1, n - 1)] = last
+    return mt
+
+
+# ----------------------------------------------------------------------------
+# benchmark-shaped workloads
+# ----------------------------------------------------------------------------
+
+def quadratic_tridiag(n: int = 1000, N: int = 32, L: int = 8,
+                      center: complex = 50.0, radius: float = 40.0,
+                      seed_c: int = 1000, seed_u: int = 1001,
+                      c_scale: float | None = None, name: str = "c0") -> Problem:
+    """T(z) = K + z C + z^2 M, K = n*tridiag(-1,2,-1), M = tridiag(1,4,1)/(6n),
+    C = diag(u), u ~ U[0, 0.1] (seeded).  With c_scale given, C = c_scale*M
+    instead (proportional damping: closed-form spectrum)."""
+    K = {k: v * n for k, v in _tridiag(n, -1.0, 2.0, -1.0).items()}
+    M = {k: v / (6.0 * n) for k, v in _tridiag(n, 1.0, 4.0, 1.0).items()}
+    if c_scale is None:
+        u = np.random.default_rng(seed_c).uniform(0.0, 0.1, n)
+        C = {(i, i): float(u[i]) for i in range(n)}
+    else:
+        C = {k: c_scale * v for k, v in M.items()}
+    row_ptr, col_idx, values = _shared_csr(n, [K, C, M])
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1), Fn(F_ZPOW, 2)]
+    return Problem(name, n, row_ptr, col_idx, values, fns,
+                   Region(complex(center), radius, radius), N, L, probe(n, L, seed_u),
+                   meta=dict(seed_c=seed_c, seed_u=seed_u, c_scale=c_scale))
+
+
+def rational_grid(g: int = 200, N: int = 64, L: int = 32, sigma: float = 300.0,
+                  center: complex = 100.0, a: float = 80.0, b: float = 20.0,
+                  frac_e: float = 0.01, e_value: float = 1.0,
+                  seed_e: int = 2000, seed_u: int = 2001, name: str = "c1") -> Problem:
+    """T(z) = K - z M + (z/(z - sigma)) E on a g x g 5-point grid (natural
+    row-major ordering, half-bandwidth g).  K = (g+1)^2 * (4 on the diagonal,
+    -1 for each grid neighbour), M = I, E = diag with round(frac_e*n) entries
+    equal to e_value at seeded positions (frac_e = 0 gives E = 0)."""
+    n = g * g
+    idx = np.arange(n)
+    gi, gj = idx // g, idx % g
+    s = float((g + 1) ** 2)
+    rows = [idx]
+    cols = [idx]
+    kval = [np.full(n, 4.0 * s)]
+    for di, dj in ((-1, 0), (0, -1), (0, 1), (1, 0)):
+        ok = (gi + di >= 0) & (gi + di < g) & (gj + dj >= 0) & (gj + dj < g)
+        rows.append(idx[ok])
+        cols.append(((gi + di) * g + (gj + dj))[ok])
+        kval.append(np.full(int(ok.sum()), -s))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    kval = np.concatenate(kval)
+    order = np.lexsort((cols, rows))
+    rows, cols, kval = rows[order], cols[order], kval[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    diag = rows == cols
+    mval = np.where(diag, 1.0, 0.0)
+    ne = int(round(frac_e * n))
+    epos = np.random.default_rng(seed_e).choice(n, size=ne, replace=False)
+    emask = np.zeros(n, dtype=bool)
+    emask[epos] = True
+    evals = np.where(diag & emask[rows], e_value, 0.0)
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1, -1.0), Fn(F_RATIONAL, sigma)]
+    return Problem(name, n, row_ptr, cols.astype(np.int32), [kval, mval, evals], fns,
+                   Region(complex(center), a, b), N, L, probe(n, L, seed_u),
+                   meta=dict(g=g, sigma=sigma, seed_e=seed_e, seed_u=seed_u,
+                             ne=ne, e_value=e_value))
+
+
+def loaded_string(n: int = 400, N: int = 100, L: int = 1, kn_last: float = 1.0,
+                  seed_u: int = 7001, name: str = "string") -> Problem:
+    """Loaded string of Section 4.1: T(z) = K_s + z/(z-1) e_n e_n^T - z M.
+    K_s = n*tridiag(-1,2,-1) with K_s[n-1,n-1] = n*kn_last, M = tridiag(1,4,1)/(6n)
+    with M[n-1,n-1] = 2/(6n).  Sampling points: N Chebyshev points of the first
+    kind in [3, 1e4]; contour for the projected problem: ellipse centre 5001.5,
+    a = 4998.5, b = 0.1a (Section 4.2)."""
+    K = {k: v * n for k, v in _tridiag(n, -1.0, 2.0, -1.0, last=kn_last).items()}
+    M = {k: v / (6.0 * n) for k, v in _tridiag(n, 1.0, 4.0, 1.0, last=2.0).items()}
+    E = {(n - 1, n - 1): 1.0}
+    row_ptr, col_idx, values = _shared_csr(n, [K, E, M])
+    fns = [Fn(F_ONE), Fn(F_RATIONAL, 1.0), Fn(F_ZPOW, 1, -1.0)]
+    lo, hi = 3.0, 1.0e4
+    i = np.arange(N)
+    x = np.cos((2 * i + 1) * np.pi / (2 * N))
+    pts = (0.5 * (hi + lo) + 0.5 * (hi - lo) * x).astype(np.complex128)
+    reg = Region(complex(5001.5), 4998.5, 0.1 * 4998.5, kind="points", points=pts)
+    return Problem(name, n, row_ptr, col_idx, values, fns, reg, N, L,
+                   probe(n, L, seed_u), meta=dict(kn_last=kn_last, interval=(lo, hi)))
+
+
+# ----------------------------------------------------------------------------
+# closed-form test families: diagonal NEPs hidden by an orthogonal similarity
+# ----------------------------------------------------------------------------
+
+def givens_layers(n: int, layers: int, seed: int) -> np.ndarray:
+    """Dense orthogonal G = product of `layers` layers of adjacent-pair Givens
+    rotations with seeded angles.  G has half-bandwidths <= `layers`, so
+    G^T D G has half-bandwidth <= 2*layers for diagonal D, and the same
+    eigenvalues."""
+    rng = np.random.default_rng(seed)
+    G = np.eye(n)
+    for lay in range(layers):
+        start = lay % 2
+        for p in range(start, n - 1, 2):
+            th = rng.uniform(0.2, 1.3)
+            c, s = np.cos(th), np.sin(th)
+            rp, rq = G[p].copy(), G[p + 1].copy()
+            G[p] = c * rp - s * rq
+            G[p + 1] = s * rp + c * rq
+    return G
+
+
+def hidden_diagonal(diags: list, fns: list, region: Region, N: int, L: int,
+                    layers: int = 3, seed: int = 5, seed_u: int = 6,
+                    name: str = "hidden") -> Problem:
+    """T(z) = G1^T diag(sum_i f_i(z) d_i) G2 with two different orthogonal G1,
+    G2 from givens_layers (seeds `seed` and `seed`+100): a banded,
+    non-symmetric NEP with det T(z) = +-det(diag(...)), so its eigenvalues are
+    those of the n decoupled scalar problems sum_i f_i(z) d_i[r] = 0."""
+    n = len(diags[0])
+    G1 = givens_layers(n, layers, seed)
+    G2 = givens_layers(n, layers, seed + 100)
+    dense = [G1.T @ np.diag(np.asarray(d, dtype=np.float64)) @ G2 for d in diags]
+    w = 2 * layers
+    row_ptr, col_idx, values = _csr_from_dense_band(dense, w, w)
+    return Problem(name, n, row_ptr, col_idx, values, fns, region, N, L,
+                   probe(n, L, seed_u), meta=dict(diags=[np.asarray(d) for d in diags],
+                                                   layers=layers, g_seed=seed))
+
+
+def diag_quadratic(n: int = 240, seed: int = 11, N: int = 32, L: int = 4,
+                   layers: int = 3) -> Problem:
+    """Decoupled quadratics k_r + z c_r + z^2 m_r, roots re +- i im with
+    re ~ U(-6, 6), im ~ U(0.05, 8); a few percent of them lie in the region."""
+    rng = np.random.default_rng(seed)
+    re = rng.uniform(-6.0, 6.0, n)
+    im = rng.uniform(0.05, 8.0, n)
+    m = rng.uniform(0.5, 2.0, n)
+    c = -2.0 * re * m
+    k = m * (re ** 2 + im ** 2)
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1), Fn(F_ZPOW, 2)]
+    return hidden_diagonal([k, c, m], fns, Region(0.6j - 0.2, 1.0, 0.8), N, L,
+                           layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_quadratic")
+
+
+def diag_rational(n: int = 240, seed: int = 21, N: int = 32, L: int = 4,
+                  sigma: float = 5.0, layers: int = 3) -> Problem:
+    """Decoupled k_r - z m_r + (z/(z - sigma)) e_r (real roots)."""
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(0.2, 40.0, n)
+    m = rng.uniform(0.8, 1.2, n)
+    e = rng.uniform(0.0, 0.5, n)
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1, -1.0), Fn(F_RATIONAL, sigma)]
+    return hidden_diagonal([k, m, e], fns, Region(2.0 + 0.0j, 1.5, 0.5), N, L,
+                           layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_rational")
+
+
+def diag_delay(n: int = 200, seed: int = 31, N: int = 48, L: int = 4,
+               tau: float = 1.0, layers: int = 2) -> Problem:
+    """Decoupled delay problems z - a_r - b_r exp(-tau z), a_r ~ U(-1, 8),
+    b_r ~ U(0.05, 0.3): only the principal-branch roots of a minority of rows
+    fall in the region."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 8.0, n)
+    b = rng.uniform(0.05, 0.3, n)
+    fns = [Fn(F_ZPOW, 1), Fn(F_ONE, 0.0, -1.0), Fn(F_EXP, tau, -1.0)]
+    return hidden_diagonal([np.ones(n), a, b], fns, Region(0.5 + 0.0j, 0.6, 0.5), N, L,
+                           layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_delay")
+
+
+def random_banded(n: int = 300, kl: int = 7, ku: int = 7, m: int = 3, seed: int = 41,
+                  N: int = 8, L: int = 5) -> Problem:
+    """Random real band matrices (every band entry present) with quadratic f;
+    used for solve-level parity (no spectral content assumed)."""
+    rng = np.random.default_rng(seed)
+    dense = []
+    for t in range(m):
+        D = rng.standard_normal((n, n))
+        D = np.triu(np.tril(D, ku), -kl)
+        if t == 0:
+            D += np.diag(np.full(n, 2.0 * (kl + ku)))
+        dense.append(D)
+    row_ptr, col_idx, values = _csr_from_dense_band(dense, kl, ku)
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1), Fn(F_ZPOW, 2)][:m]
+    return Problem("random_banded", n, row_ptr, col_idx, values, fns,
+                   Region(0.3 + 0.2j, 0.5, 0.4), N, L, probe(n, L, seed + 1))
+
+
+# Benchmark configurations by name.
+def config(name: str, **kw) -> Problem:
+    if name == "c0":
+        return quadratic_tridiag(**kw)
+    if name == "c0b":
+        kw.setdefault("center", -25.0 + 50.0j)
+        return quadratic_tridiag(name="c0b", **kw)
+    if name == "c1":
+        return rational_grid(**kw)
+    raise KeyError(name)
