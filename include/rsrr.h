@@ -1,0 +1,246 @@
+/*
+ * rsrr.h -- C ABI of the GB300 resolvent-sampling library.
+ *
+ * The library computes the data-parallel part of the resolvent sampling based
+ * Rayleigh-Ritz method (RSRR) of Xiao, Zhang, Huang and Sakurai (2016) for a
+ * nonlinear eigenvalue problem T(lambda) v = 0 with
+ *
+ *     T(z) = sum_{i<m} f_i(z) A_i                         (Eq. 1, Section 2.1)
+ *
+ * where the A_i are real n x n matrices sharing one sparse (banded) pattern
+ * and the f_i are scalar functions.  The steps are those of the RSRR
+ * algorithm in Section 3.3:
+ *
+ *   rsrr_create   step 1: sampling points z_j, coefficient table f_i(z_j),
+ *                 device copies of the pattern and values.
+ *   rsrr_sample   step 2: X_j = T(z_j)^{-1} U for every point (assembly,
+ *                 banded LU with partial pivoting, triangular solves and FP64
+ *                 iterative refinement), all on the GPU.
+ *   rsrr_project  steps 3-4 (GPU part): S = [X_0 ... X_{N-1}] with unit-norm
+ *                 columns (Section 3.2, last paragraph), orthonormal basis Q of
+ *                 its dominant singular subspace (Section 3.3 step 3), and the
+ *                 projected coefficients P_i = Q^H A_i Q (Section 3, T_Q).
+ *   rsrr_solve    steps 4-5 (host part): the projected NEP by SS-FULL
+ *                 (Section 2.3 with U = I), eigenvectors v = Q g and their
+ *                 residuals.
+ *
+ * Conventions.
+ *   - Complex numbers are rsrr_c128 {re, im}, layout compatible with C99
+ *     double _Complex, std::complex<double> and torch.complex128.
+ *   - Matrices are column major.
+ *   - Host pointers are plain CPU memory; device pointers are CUDA device
+ *     memory of the current device.  Which one an argument is, is stated.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL is the
+ *     legacy default stream).
+ *   - Every call returns an rsrr_status.  Negative values are errors, 0 is
+ *     success, positive values are warnings.  No C++ exception crosses the ABI.
+ *     rsrr_last_error() gives a one-line description of the last failure.
+ *   - A handle is used by one host thread at a time; distinct handles are
+ *     independent.  The handle owns all device memory it allocates; inputs
+ *     are copied at rsrr_create and may be freed by the caller on return.
+ */
+#ifndef RSRR_H
+#define RSRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double re, im;
+} rsrr_c128;
+
+typedef enum {
+    RSRR_OK = 0,
+    RSRR_EINVAL = -1,    /* invalid argument or descriptor */
+    RSRR_ENOMEM = -2,    /* device or host allocation failed */
+    RSRR_ESINGULAR = -3, /* an exactly zero pivot: a sampling point on an eigenvalue */
+    RSRR_ENOCONV = -4,   /* refinement did not reach eta_tol for every column */
+    RSRR_ETIMEOUT = -5,  /* a bounded device-side wait ran out */
+    RSRR_ECUDA = -6,     /* a CUDA runtime error */
+    RSRR_ESTATE = -7,    /* call out of order (e.g. rsrr_project before rsrr_sample) */
+    RSRR_WGAP = 1        /* warning: the gap test g_max >= tol_gap failed (Section 2.3) */
+} rsrr_status;
+
+/* Scalar coefficient functions f(z) = scale * base(z; param) (families of
+ * Section 2.1; EXP covers delay problems):
+ *   RSRR_F_ONE       base = 1
+ *   RSRR_F_ZPOW      base = z^param, param a non-negative integer
+ *   RSRR_F_RATIONAL  base = z / (z - param)
+ *   RSRR_F_INV       base = 1 / (param - z)
+ *   RSRR_F_SQRT      base = sqrt(z^2 - param^2), principal branch
+ *   RSRR_F_EXP       base = exp(-param z)                                   */
+enum {
+    RSRR_F_ONE = 0,
+    RSRR_F_ZPOW = 1,
+    RSRR_F_RATIONAL = 2,
+    RSRR_F_INV = 3,
+    RSRR_F_SQRT = 4,
+    RSRR_F_EXP = 5
+};
+
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double param;
+    rsrr_c128 scale;
+} rsrr_fn;
+
+#define RSRR_MAX_TERMS 8
+
+/* T(z) = sum_{i<m} fn[i](z) A_i.  All A_i share one CSR pattern (row_ptr,
+ * col_idx; columns need not be sorted; duplicates are not allowed); their
+ * real values are stored term-major: A_i's value for pattern entry e is
+ * values[i * nnz + e], nnz = row_ptr[n].  All three arrays are host memory
+ * and are copied by rsrr_create.  The half-bandwidths kl, ku are detected
+ * from the pattern. */
+typedef struct {
+    int64_t n;
+    int32_t m; /* 1 <= m <= RSRR_MAX_TERMS */
+    int32_t reserved;
+    const int64_t *row_ptr; /* host, n + 1 */
+    const int32_t *col_idx; /* host, nnz */
+    const double *values;   /* host, m * nnz */
+    rsrr_fn fn[RSRR_MAX_TERMS];
+} rsrr_nep;
+
+/* Region.  The ellipse phi(t) = center + a cos t + i b sin t is the contour
+ * of the projected solve and defines "inside".  Sampling points are the
+ * N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Section 4.1) for
+ * RSRR_REGION_ELLIPSE, or the N given host points for RSRR_REGION_POINTS
+ * (the rational interpolation approach lets them lie anywhere, Section 2.2). */
+enum { RSRR_REGION_ELLIPSE = 0, RSRR_REGION_POINTS = 1 };
+
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    rsrr_c128 center;
+    double a, b;              /* semi-axes along the real and imaginary axis, > 0 */
+    const rsrr_c128 *points;  /* host, N, only for RSRR_REGION_POINTS */
+} rsrr_region;
+
+/* Precision of the factorisation.
+ *   RSRR_PREC_FP64   complex128 LU and solve, one residual pass for the
+ *                    statistics, no refinement ("plain FP64 path").
+ *   RSRR_PREC_MIXED  complex64 LU and solves on the GPU, refined to FP64
+ *                    accuracy: r = U - T(z_j) X in FP64, d = LU \ r in
+ *                    complex64, X += d, until every column's backward error
+ *                    eta = ||r||_inf / (||T||_inf ||x||_inf + ||u||_inf) is
+ *                    <= eta_tol or max_refine sweeps have run.            */
+enum { RSRR_PREC_FP64 = 0, RSRR_PREC_MIXED = 1 };
+
+typedef struct {
+    int32_t precision;   /* RSRR_PREC_MIXED by default */
+    int32_t max_refine;  /* refinement sweeps, default 8 */
+    double eta_tol;      /* default 1e-10 */
+    double delta;        /* SVD truncation of S relative to sigma_1, paper's 1e-14 */
+    double delta_floor;  /* truncation floor of the Gram-based SVD, default 1e-7 */
+    double tol_gap;      /* gap test of SS-FULL, default 1e3 (Section 2.3) */
+    double res_tol;      /* acceptance of an eigenpair by residual, default 1e-6 */
+    int32_t NQ;          /* SS-FULL quadrature points, default 500 */
+    int32_t KQ;          /* SS-FULL moments, default 2 */
+    int32_t host_threads;/* threads of rsrr_solve, 0 = all cores */
+    int32_t reserved;
+} rsrr_opts;
+
+typedef struct rsrr_handle rsrr_t;
+
+typedef struct {
+    int64_t n;
+    int32_t N, L, m, kl, ku;
+    int32_t refine_sweeps; /* sweeps run by the last rsrr_sample */
+    int32_t converged;     /* 1 if every column reached eta_tol */
+    int32_t singular_point;/* first point with an exactly zero pivot, or -1 */
+    int32_t k;             /* rank kept by the last rsrr_project */
+    int32_t kc;            /* columns kept by its pivoted Cholesky stage */
+    double max_eta;        /* largest per-column backward error after rsrr_sample */
+    double sigma1, sigmak; /* largest and smallest kept singular value of S */
+    size_t device_bytes;   /* device memory held by the handle */
+} rsrr_stats;
+
+/* Result of rsrr_solve.  Arrays are host memory owned by the handle, valid
+ * until the next rsrr_solve or rsrr_destroy. */
+typedef struct {
+    int32_t count;          /* eigenpairs kept: inside the ellipse, residual <= res_tol */
+    int32_t nbar;           /* rank chosen by the gap test */
+    double gmax;            /* largest singular-value gap of the Hankel matrix */
+    const rsrr_c128 *lam;   /* count eigenvalues, sorted by |lambda| then arg */
+    const double *res;      /* count residuals ||T v||_2 / (sum_i |f_i| ||A_i||_1 ||v||_2) */
+    const rsrr_c128 *V;     /* n x count eigenvectors, unit 2-norm columns */
+} rsrr_result;
+
+/* Fills `o` with the defaults listed above. */
+void rsrr_opts_default(rsrr_opts *o);
+
+/* Builds a handle: validates the descriptors, computes the sampling points and
+ * the table f_i(z_j) on the host in FP64, copies the pattern and values to
+ * the device, and allocates every device buffer of the handle (factors for
+ * all N points, S, refinement work space).  The probe U is drawn from a
+ * fixed seed; set it with rsrr_set_probe.  N >= 1, L >= 1.
+ * Errors: EINVAL (bad descriptor), ENOMEM, ECUDA.  *out is NULL on error. */
+rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t N,
+                        int32_t L, const rsrr_opts *opts, rsrr_t **out);
+
+/* Sets the probe matrix U (n x L, column major, Section 3.3 step 1).  U is
+ * host memory if on_device == 0, else device memory; it is copied (async on
+ * `stream` for device input, synchronous for host input). */
+rsrr_status rsrr_set_probe(rsrr_t *h, const rsrr_c128 *U, int32_t on_device, void *stream);
+
+/* Step 2: X_j = T(z_j)^{-1} U for all points, asynchronously on `stream`.
+ * The outcome (ESINGULAR, ENOCONV) is known after the stream is synchronised
+ * and is returned by rsrr_get_stats / rsrr_check. */
+rsrr_status rsrr_sample(rsrr_t *h, void *stream);
+
+/* Waits for `stream` and reports the outcome of the last rsrr_sample:
+ * OK, ESINGULAR (a zero pivot; stats.singular_point names the point) or
+ * ENOCONV (some column above eta_tol after max_refine sweeps). */
+rsrr_status rsrr_check(rsrr_t *h, void *stream);
+
+/* Steps 3-4, GPU part, asynchronously on `stream`: column normalisation of
+ * S, orthonormal basis Q (n x k) of its dominant singular subspace, and
+ * P_i = Q^H A_i Q.  Requires a previous rsrr_sample. */
+rsrr_status rsrr_project(rsrr_t *h, void *stream);
+
+/* Steps 4-5, host part (synchronises the handle's work first): SS-FULL on
+ * T_Q(z) = sum_i f_i(z) P_i in FP64, v = Q g and residuals on the GPU.
+ * Returns OK or WGAP (gap test failed; results still filled). */
+rsrr_status rsrr_solve(rsrr_t *h, rsrr_result *out);
+
+/* Copies S = [X_0 ... X_{N-1}] (n x N*L, column major, before normalisation)
+ * into dst (device memory if dst_on_device, else host; async on stream for
+ * device destinations, synchronous for host ones). */
+rsrr_status rsrr_get_samples(rsrr_t *h, rsrr_c128 *dst, int32_t dst_on_device, void *stream);
+
+/* Copies the per-column backward errors eta (N*L doubles, host) of the last
+ * rsrr_sample.  Synchronises the handle's work. */
+rsrr_status rsrr_get_eta(rsrr_t *h, double *dst);
+
+/* Copies Q (n x k, column major) after rsrr_project; same memory rules as
+ * rsrr_get_samples.  k is in rsrr_stats. */
+rsrr_status rsrr_get_Q(rsrr_t *h, rsrr_c128 *dst, int32_t dst_on_device, void *stream);
+
+/* Copies P_0 ... P_{m-1} (m consecutive k x k column-major blocks) after
+ * rsrr_project; same memory rules as rsrr_get_samples. */
+rsrr_status rsrr_get_projected(rsrr_t *h, rsrr_c128 *dst, int32_t dst_on_device, void *stream);
+
+/* Copies the N sampling points (host). */
+rsrr_status rsrr_get_points(rsrr_t *h, rsrr_c128 *dst);
+
+/* Fills the statistics of the handle (synchronises the handle's work). */
+rsrr_status rsrr_get_stats(rsrr_t *h, rsrr_stats *out);
+
+/* One-line description of the last error on this handle ("" if none).  With
+ * h == NULL: the last error of a failed rsrr_create on this thread. */
+const char *rsrr_last_error(const rsrr_t *h);
+
+/* Frees the handle and all its device memory.  NULL is allowed. */
+void rsrr_destroy(rsrr_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSRR_H */

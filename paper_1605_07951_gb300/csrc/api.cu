@@ -1,0 +1,452 @@
+// Host side of the C ABI declared in include/rsrr.h: descriptor validation,
+// sampling points and coefficient table (RSRR step 1, Section 3.3), device
+// buffers, and the orchestration of the sampling kernels (step 2).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rsrr.h"
+#include "rsrr_handle.h"
+
+using cplx = std::complex<double>;
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+namespace rsrr {
+
+cplx eval_fn_host(const rsrr_fn &f, cplx z) {
+    cplx base;
+    switch (f.kind) {
+        case RSRR_F_ONE: base = 1.0; break;
+        case RSRR_F_ZPOW: {
+            base = 1.0;
+            const int p = (int)f.param;
+            for (int q = 0; q < p; ++q) base *= z;
+            break;
+        }
+        case RSRR_F_RATIONAL: base = z / (z - f.param); break;
+        case RSRR_F_INV: base = 1.0 / (f.param - z); break;
+        case RSRR_F_SQRT: base = std::sqrt(z * z - f.param * f.param); break;
+        case RSRR_F_EXP: base = std::exp(-f.param * z); break;
+        default: base = 0.0;
+    }
+    return cplx(f.scale.re, f.scale.im) * base;
+}
+
+rsrr_status Handle::fail(rsrr_status st, const char *what, cudaError_t e) {
+    char buf[512];
+    if (e != cudaSuccess)
+        snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    else
+        snprintf(buf, sizeof buf, "%s", what);
+    err = buf;
+    return st;
+}
+
+template <typename T> cudaError_t Handle::alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e == cudaSuccess) {
+        allocations.push_back((void *)*p);
+        device_bytes += sizeof(T) * count;
+    }
+    return e;
+}
+
+Handle::~Handle() {
+    for (void *p : allocations) cudaFree(p);
+}
+
+}  // namespace rsrr
+
+using rsrr::Handle;
+
+#define CK(expr, what)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (expr);                                         \
+        if (_e != cudaSuccess) return h->fail(RSRR_ECUDA, what, _e);     \
+    } while (0)
+
+extern "C" {
+
+void rsrr_opts_default(rsrr_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = RSRR_PREC_MIXED;
+    o->max_refine = 8;
+    o->eta_tol = 1e-10;
+    o->delta = 1e-14;
+    o->delta_floor = 1e-7;
+    o->tol_gap = 1e3;
+    o->res_tol = 1e-6;
+    o->NQ = 500;
+    o->KQ = 2;
+    o->host_threads = 0;
+}
+
+static rsrr_status create_fail(const char *msg) {
+    g_create_error = msg;
+    return RSRR_EINVAL;
+}
+
+rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                        const rsrr_opts *opts, rsrr_t **out) {
+    if (!out) return create_fail("rsrr_create: out is NULL");
+    *out = nullptr;
+    g_create_error.clear();
+    if (!nep || !region) return create_fail("rsrr_create: nep or region is NULL");
+    if (nep->n < 1 || nep->n > (int64_t)1 << 30) return create_fail("rsrr_create: n out of range");
+    if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
+    if (!nep->row_ptr || !nep->col_idx || !nep->values)
+        return create_fail("rsrr_create: pattern or values NULL");
+    if (N < 1 || L < 1) return create_fail("rsrr_create: N and L must be >= 1");
+    if (!(region->a > 0.0) || !(region->b > 0.0))
+        return create_fail("rsrr_create: ellipse semi-axes must be > 0");
+    if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS)
+        return create_fail("rsrr_create: unknown region kind");
+    if (region->kind == RSRR_REGION_POINTS && !region->points)
+        return create_fail("rsrr_create: points region without points");
+    for (int i = 0; i < nep->m; ++i) {
+        const rsrr_fn &f = nep->fn[i];
+        if (f.kind < RSRR_F_ONE || f.kind > RSRR_F_EXP) return create_fail("rsrr_create: bad fn kind");
+        if (f.kind == RSRR_F_ZPOW && (f.param < 0 || f.param != std::floor(f.param) || f.param > 64))
+            return create_fail("rsrr_create: ZPOW needs a small non-negative integer");
+    }
+    const int64_t n = nep->n;
+    const int64_t nnz = nep->row_ptr[n];
+    if (nep->row_ptr[0] != 0 || nnz < 1 || nnz > INT32_MAX)
+        return create_fail("rsrr_create: bad row_ptr");
+    // pattern checks and bandwidths
+    int64_t kl = 0, ku = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (nep->row_ptr[i + 1] < nep->row_ptr[i]) return create_fail("rsrr_create: row_ptr decreasing");
+        for (int64_t e = nep->row_ptr[i]; e < nep->row_ptr[i + 1]; ++e) {
+            const int64_t c = nep->col_idx[e];
+            if (c < 0 || c >= n) return create_fail("rsrr_create: column index out of range");
+            kl = std::max(kl, i - c);
+            ku = std::max(ku, c - i);
+        }
+    }
+    if (kl > rsrr::KL_MAX) return create_fail("rsrr_create: lower bandwidth above 480");
+    const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
+    if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
+        return create_fail("rsrr_create: unknown precision");
+
+    Handle *h = new (std::nothrow) Handle();
+    if (!h) { g_create_error = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
+    if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);
+    h->n = n; h->nnz = nnz; h->N = N; h->L = L; h->m = nep->m;
+    h->kl = (int)kl; h->ku = (int)ku;
+    h->region = *region;
+    h->region.points = nullptr;
+    for (int i = 0; i < nep->m; ++i) h->fn[i] = nep->fn[i];
+    h->geom.kl = (int)kl;
+    h->geom.ku = (int)ku;
+    h->geom.nb = prec == RSRR_PREC_MIXED ? rsrr::NB_C64 : rsrr::NB_C128;
+    h->geom.ldab = 2 * (int)kl + (int)ku + h->geom.nb;
+
+    // host copies of the pattern (int32 row pointers; nnz < 2^31 checked)
+    h->h_row_ptr.resize(n + 1);
+    for (int64_t i = 0; i <= n; ++i) h->h_row_ptr[i] = (int32_t)nep->row_ptr[i];
+    h->h_col_idx.assign(nep->col_idx, nep->col_idx + nnz);
+    h->h_vals.assign(nep->values, nep->values + (size_t)nep->m * nnz);
+    // duplicates inside a row are rejected (a CSC lookup needs unique entries)
+    {
+        std::vector<int32_t> cnt(n + 1, 0);
+        for (int64_t e = 0; e < nnz; ++e) cnt[h->h_col_idx[e] + 1]++;
+        std::vector<int32_t> cptr(n + 1, 0);
+        for (int64_t c = 0; c < n; ++c) cptr[c + 1] = cptr[c] + cnt[c + 1];
+        std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+        std::vector<int32_t> crow(nnz), cperm(nnz);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = h->h_row_ptr[i]; e < h->h_row_ptr[i + 1]; ++e) {
+                const int c = h->h_col_idx[e];
+                crow[fill[c]] = (int32_t)i;
+                cperm[fill[c]] = (int32_t)e;
+                fill[c]++;
+            }
+        // rows within a column are increasing because rows are visited in order
+        for (int64_t c = 0; c < n; ++c)
+            for (int32_t q = cptr[c] + 1; q < cptr[c + 1]; ++q)
+                if (crow[q] == crow[q - 1]) {
+                    delete h;
+                    return create_fail("rsrr_create: duplicate entry in the pattern");
+                }
+        h->h_csc_ptr = std::move(cptr);
+        h->h_csc_row = std::move(crow);
+        h->h_csc_perm = std::move(cperm);
+    }
+    // step 1: sampling points (trapezoid nodes on the ellipse, Section 4.1, or
+    // the explicit points) and the coefficient table f_i(z_j)
+    h->z.resize(N);
+    for (int j = 0; j < N; ++j) {
+        if (region->kind == RSRR_REGION_POINTS) {
+            h->z[j] = cplx(region->points[j].re, region->points[j].im);
+        } else {
+            const double al = 2.0 * M_PI * (j + 0.5) / N;
+            h->z[j] = cplx(region->center.re + region->a * std::cos(al),
+                           region->center.im + region->b * std::sin(al));
+        }
+    }
+    std::vector<double2> coef((size_t)N * nep->m);
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i < nep->m; ++i) {
+            const cplx v = rsrr::eval_fn_host(nep->fn[i], h->z[j]);
+            if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) {
+                delete h;
+                return create_fail("rsrr_create: f_i is not finite at a sampling point");
+            }
+            coef[(size_t)j * nep->m + i] = make_double2(v.real(), v.imag());
+        }
+
+    rsrr_status st = h->allocate_and_upload(coef);
+    if (st != RSRR_OK) {
+        g_create_error = h->err;
+        delete h;
+        return st;
+    }
+    *out = reinterpret_cast<rsrr_t *>(h);
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_set_probe(rsrr_t *hh, const rsrr_c128 *U, int32_t on_device, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !U) return RSRR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double2) * (size_t)h->n * h->L;
+    if (on_device) {
+        CK(cudaMemcpyAsync(h->d_U, U, bytes, cudaMemcpyDeviceToDevice, s), "set_probe copy");
+    } else {
+        CK(cudaMemcpy(h->d_U, U, bytes, cudaMemcpyHostToDevice), "set_probe copy");
+    }
+    CK(rsrr::launch_colmax(h->d_umax, h->d_U, (int)h->n, h->L, s), "set_probe colmax");
+    h->sampled = false;
+    h->projected = false;
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_sample(rsrr_t *hh, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return RSRR_EINVAL;
+    rsrr_status st = h->sample((cudaStream_t)stream);
+    if (st == RSRR_OK) { h->sampled = true; h->projected = false; }
+    return st;
+}
+
+rsrr_status rsrr_check(rsrr_t *hh, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return RSRR_EINVAL;
+    if (!h->sampled) return h->fail(RSRR_ESTATE, "rsrr_check: no rsrr_sample yet");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "rsrr_check sync");
+    return h->read_outcome();
+}
+
+rsrr_status rsrr_get_samples(rsrr_t *hh, rsrr_c128 *dst, int32_t dst_on_device, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !dst) return RSRR_EINVAL;
+    if (!h->sampled) return h->fail(RSRR_ESTATE, "rsrr_get_samples: no rsrr_sample yet");
+    const size_t bytes = sizeof(double2) * (size_t)h->n * h->N * h->L;
+    if (dst_on_device) {
+        CK(cudaMemcpyAsync(dst, h->d_X, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+           "get_samples copy");
+    } else {
+        CK(cudaStreamSynchronize((cudaStream_t)stream), "get_samples sync");
+        CK(cudaMemcpy(dst, h->d_X, bytes, cudaMemcpyDeviceToHost), "get_samples copy");
+    }
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_get_eta(rsrr_t *hh, double *dst) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !dst) return RSRR_EINVAL;
+    if (!h->sampled) return h->fail(RSRR_ESTATE, "rsrr_get_eta: no rsrr_sample yet");
+    CK(cudaDeviceSynchronize(), "get_eta sync");
+    CK(cudaMemcpy(dst, h->d_eta, sizeof(double) * h->N * h->L, cudaMemcpyDeviceToHost), "get_eta");
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_get_points(rsrr_t *hh, rsrr_c128 *dst) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !dst) return RSRR_EINVAL;
+    for (int j = 0; j < h->N; ++j) dst[j] = {h->z[j].real(), h->z[j].imag()};
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !out) return RSRR_EINVAL;
+    CK(cudaDeviceSynchronize(), "get_stats sync");
+    if (h->sampled) h->read_outcome();
+    memset(out, 0, sizeof *out);
+    out->n = h->n; out->N = h->N; out->L = h->L; out->m = h->m;
+    out->kl = h->kl; out->ku = h->ku;
+    out->refine_sweeps = h->stat_sweeps;
+    out->converged = h->stat_converged;
+    out->singular_point = h->stat_singular;
+    out->max_eta = h->stat_max_eta;
+    out->k = h->k;
+    out->kc = h->kc;
+    out->sigma1 = h->sigma1;
+    out->sigmak = h->sigmak;
+    out->device_bytes = h->device_bytes;
+    return RSRR_OK;
+}
+
+const char *rsrr_last_error(const rsrr_t *hh) {
+    const Handle *h = reinterpret_cast<const Handle *>(hh);
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void rsrr_destroy(rsrr_t *hh) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return;
+    cudaDeviceSynchronize();
+    delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+namespace rsrr {
+
+rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
+    Handle *h = this;
+    const size_t nL = (size_t)n * L, NL = (size_t)N * L;
+    CK(alloc(&d_row_ptr, n + 1), "alloc");
+    CK(alloc(&d_col_idx, nnz), "alloc");
+    CK(alloc(&d_vals, (size_t)m * nnz), "alloc");
+    CK(alloc(&d_csc_ptr, n + 1), "alloc");
+    CK(alloc(&d_csc_row, nnz), "alloc");
+    CK(alloc(&d_csc_perm, nnz), "alloc");
+    CK(alloc(&d_coef, (size_t)N * m), "alloc");
+    CK(alloc(&d_U, nL), "alloc");
+    CK(alloc(&d_umax, L), "alloc");
+    CK(alloc(&d_X, nL * N), "alloc S");
+    CK(alloc(&d_piv, (size_t)n * N), "alloc pivots");
+    CK(alloc(&d_info, N), "alloc");
+    CK(alloc(&d_tnorm, N), "alloc");
+    CK(alloc(&d_eta, NL), "alloc");
+    CK(alloc(&d_rmax, NL), "alloc");
+    CK(alloc(&d_xmax, NL), "alloc");
+    CK(alloc(&d_done, N), "alloc");
+    CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
+    const size_t band = (size_t)geom.ldab * n * N;
+    if (opts.precision == RSRR_PREC_MIXED) {
+        CK(alloc(&d_ab32, band), "alloc band factors (complex64)");
+        CK(alloc(&d_R, nL * N), "alloc residual");
+        CK(alloc(&d_D, nL * N), "alloc correction");
+    } else {
+        CK(alloc(&d_ab64, band), "alloc band factors (complex128)");
+    }
+    CK(cudaMemcpy(d_row_ptr, h_row_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_col_idx, h_col_idx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_vals, h_vals.data(), sizeof(double) * m * nnz, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_csc_ptr, h_csc_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_csc_row, h_csc_row.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_csc_perm, h_csc_perm.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_coef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice), "upload");
+    // default probe: complex normal entries from a fixed-seed generator
+    // (splitmix64 + Box-Muller); rsrr_set_probe replaces it
+    {
+        std::vector<double2> U(nL);
+        uint64_t st = 0x9E3779B97F4A7C15ull;
+        auto next = [&st]() {
+            uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        };
+        for (size_t q = 0; q < nL; ++q) {
+            const double r = std::sqrt(-2.0 * std::log(next())), t = 2.0 * M_PI * next();
+            U[q] = make_double2(r * std::cos(t) / std::sqrt(2.0), r * std::sin(t) / std::sqrt(2.0));
+        }
+        CK(cudaMemcpy(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice), "upload");
+    }
+    CK(launch_colmax(d_umax, d_U, (int)n, L, 0), "colmax");
+    CK(cudaDeviceSynchronize(), "create sync");
+    dp.n = n; dp.nnz = nnz; dp.N = N; dp.L = L; dp.m = m;
+    dp.row_ptr = d_row_ptr; dp.col_idx = d_col_idx; dp.vals = d_vals;
+    dp.csc_ptr = d_csc_ptr; dp.csc_row = d_csc_row; dp.csc_perm = d_csc_perm;
+    dp.coef = d_coef; dp.U = d_U;
+    return RSRR_OK;
+}
+
+// Step 2 of RSRR on the GPU, asynchronously on stream s.
+rsrr_status Handle::sample(cudaStream_t s) {
+    Handle *h = this;
+    const int nn = (int)n;
+    const int64_t per_pt = (int64_t)n * L;
+    CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
+    CK(launch_tnorm(d_tnorm, dp, s), "tnorm");
+    if (opts.precision == RSRR_PREC_MIXED) {
+        CK(launch_assemble<float2>(d_ab32, geom, dp, s), "assemble");
+        CK(launch_band_lu_c64(d_ab32, d_piv, d_info, geom, N, nn, s), "band LU");
+        CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
+        CK(launch_band_solve_c64(d_ab32, d_piv, d_D, geom, N, nn, L, nullptr, s), "band solve");
+        CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
+        CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
+        for (int it = 0; it < opts.max_refine; ++it) {
+            CK(launch_residual(d_R, d_X, dp, d_rmax, d_xmax, d_done, s), "residual");
+            CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
+                          d_sweep_flags + it, d_done, s), "eta");
+            CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
+            CK(launch_band_solve_c64(d_ab32, d_piv, d_D, geom, N, nn, L, d_done, s), "band solve");
+            CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
+        }
+    } else {
+        CK(launch_assemble<double2>(d_ab64, geom, dp, s), "assemble");
+        CK(launch_band_lu_c128(d_ab64, d_piv, d_info, geom, N, nn, s), "band LU");
+        CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
+        CK(launch_band_solve_c128(d_ab64, d_piv, d_X, geom, N, nn, L, nullptr, s), "band solve");
+    }
+    // final backward errors of every column (statistics and convergence)
+    CK(launch_residual(nullptr, d_X, dp, d_rmax, d_xmax, nullptr, s), "residual");
+    CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
+                  d_sweep_flags + opts.max_refine + 1, nullptr, s), "eta");
+    return RSRR_OK;
+}
+
+rsrr_status Handle::read_outcome() {
+    Handle *h = this;
+    std::vector<int32_t> info(N), flags(opts.max_refine + 2);
+    std::vector<double> eta((size_t)N * L);
+    CK(cudaMemcpy(info.data(), d_info, sizeof(int32_t) * N, cudaMemcpyDeviceToHost), "outcome");
+    CK(cudaMemcpy(flags.data(), d_sweep_flags, sizeof(int32_t) * flags.size(), cudaMemcpyDeviceToHost), "outcome");
+    CK(cudaMemcpy(eta.data(), d_eta, sizeof(double) * eta.size(), cudaMemcpyDeviceToHost), "outcome");
+    stat_singular = -1;
+    for (int j = 0; j < N; ++j)
+        if (info[j] != 0) { stat_singular = j; break; }
+    stat_sweeps = 0;
+    if (opts.precision == RSRR_PREC_MIXED)
+        for (int it = 0; it < opts.max_refine; ++it) stat_sweeps += flags[it] ? 1 : 0;
+    stat_max_eta = 0.0;
+    bool finite = true;
+    for (double e : eta) {
+        if (!std::isfinite(e)) finite = false;
+        stat_max_eta = std::max(stat_max_eta, e);
+    }
+    stat_converged = (finite && stat_max_eta <= opts.eta_tol) ? 1 : 0;
+    if (stat_singular >= 0) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "zero pivot at sampling point %d (column %d)", stat_singular,
+                 info[stat_singular] - 1);
+        return fail(RSRR_ESINGULAR, buf);
+    }
+    if (!stat_converged && opts.precision == RSRR_PREC_MIXED) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "refinement stopped at max eta %.3e > %.1e", stat_max_eta, opts.eta_tol);
+        return fail(RSRR_ENOCONV, buf);
+    }
+    return RSRR_OK;
+}
+
+}  // namespace rsrr

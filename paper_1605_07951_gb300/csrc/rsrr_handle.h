@@ -1,0 +1,72 @@
+// The handle behind rsrr_t: host descriptors, device buffers and results.
+#pragma once
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "rsrr.h"
+#include "rsrr_internal.h"
+
+namespace rsrr {
+
+std::complex<double> eval_fn_host(const rsrr_fn &f, std::complex<double> z);
+
+struct Handle {
+    // problem
+    int64_t n = 0, nnz = 0;
+    int N = 0, L = 0, m = 0, kl = 0, ku = 0;
+    rsrr_fn fn[RSRR_MAX_TERMS] = {};
+    rsrr_region region = {};
+    rsrr_opts opts = {};
+    BandGeom geom = {};
+    DevProblem dp = {};
+    std::vector<std::complex<double>> z;
+    std::vector<int32_t> h_row_ptr, h_col_idx, h_csc_ptr, h_csc_row, h_csc_perm;
+    std::vector<double> h_vals;
+
+    // device buffers (owned)
+    std::vector<void *> allocations;
+    size_t device_bytes = 0;
+    int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr;
+    int32_t *d_csc_ptr = nullptr, *d_csc_row = nullptr, *d_csc_perm = nullptr;
+    double *d_vals = nullptr;
+    double2 *d_coef = nullptr, *d_U = nullptr;
+    double *d_umax = nullptr;
+    double2 *d_X = nullptr;           // S = [X_0 ... X_{N-1}], n x NL
+    double2 *d_R = nullptr;           // FP64 residuals (mixed path)
+    float2 *d_D = nullptr;            // complex64 corrections (mixed path)
+    float2 *d_ab32 = nullptr;         // complex64 band factors
+    double2 *d_ab64 = nullptr;        // complex128 band factors
+    int32_t *d_piv = nullptr, *d_info = nullptr, *d_done = nullptr, *d_sweep_flags = nullptr;
+    double *d_tnorm = nullptr, *d_eta = nullptr, *d_rmax = nullptr, *d_xmax = nullptr;
+
+    // projection stage (proj.cu)
+    int k = 0, kc = 0;
+    double sigma1 = 0.0, sigmak = 0.0;
+    double2 *d_Q = nullptr;           // n x k basis
+    double2 *d_P = nullptr;           // m blocks of k x k
+    void *proj_ws = nullptr;          // projection work space (allocated on first use)
+    size_t proj_ws_bytes = 0;
+
+    // results of rsrr_solve
+    std::vector<rsrr_c128> res_lam, res_V;
+    std::vector<double> res_res;
+
+    // state
+    bool sampled = false, projected = false;
+    int stat_sweeps = 0, stat_converged = 0, stat_singular = -1;
+    double stat_max_eta = 0.0;
+    std::string err;
+
+    ~Handle();
+    rsrr_status fail(rsrr_status st, const char *what, cudaError_t e = cudaSuccess);
+    template <typename T> cudaError_t alloc(T **p, size_t count);
+    rsrr_status allocate_and_upload(const std::vector<double2> &coef);
+    rsrr_status sample(cudaStream_t s);
+    rsrr_status read_outcome();
+    rsrr_status project(cudaStream_t s);
+    rsrr_status solve(rsrr_result *out);
+};
+
+}  // namespace rsrr

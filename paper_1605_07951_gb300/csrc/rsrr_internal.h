@@ -1,0 +1,65 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#define RSRR_MAX_TERMS_DEV 8
+
+namespace rsrr {
+
+// Column block of the band LU and of its solve (they must agree).
+constexpr int NB_C64 = 32;
+constexpr int NB_C128 = 16;
+// Largest lower half-bandwidth the band kernels accept (panel rows <= 512).
+constexpr int KL_MAX = 480;
+
+struct BandGeom {
+    int kl, ku, nb, ldab;  // ldab = kl + ku + kl + nb
+};
+
+// Device copies of one problem (all pointers are device memory).
+struct DevProblem {
+    int64_t n, nnz;
+    int N, L, m;
+    const int32_t *row_ptr;  // n + 1 (CSR)
+    const int32_t *col_idx;  // nnz
+    const double *vals;      // m * nnz, term-major
+    const int32_t *csc_ptr;  // n + 1 (column-major copy of the pattern)
+    const int32_t *csc_row;  // nnz
+    const int32_t *csc_perm; // nnz, CSC slot -> CSR entry
+    const double2 *coef;     // N * m, f_i(z_j) at [j * m + i]
+    const double2 *U;        // n * L probe, column major
+};
+
+// ---- band path (band.cu)
+template <typename C>
+cudaError_t launch_assemble(C *ab, const BandGeom &g, const DevProblem &p, cudaStream_t s);
+cudaError_t launch_tnorm(double *tnorm, const DevProblem &p, cudaStream_t s);
+cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, const BandGeom &g, int N,
+                               int n, cudaStream_t s);
+cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, const BandGeom &g,
+                                int N, int n, cudaStream_t s);
+cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, float2 *B, const BandGeom &g,
+                                  int N, int n, int L, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, double2 *B,
+                                   const BandGeom &g, int N, int n, int L, const int32_t *skip,
+                                   cudaStream_t s);
+cudaError_t launch_residual(double2 *R, const double2 *X, const DevProblem &p, double *rmax,
+                            double *xmax, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_eta(double *eta, int32_t *done, const double *rmax, const double *xmax,
+                       const double *umax, const double *tnorm, int N, int L, double tol,
+                       int32_t *sweep_flag, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_colmax(double *out, const double2 *U, int n, int L, cudaStream_t s);
+cudaError_t launch_broadcast_probe_c64(float2 *D, const double2 *U, int64_t nL, int N,
+                                       cudaStream_t s);
+cudaError_t launch_broadcast_probe_c128(double2 *D, const double2 *U, int64_t nL, int N,
+                                        cudaStream_t s);
+cudaError_t launch_widen(double2 *X, const float2 *D, int64_t total, cudaStream_t s);
+cudaError_t launch_narrow(float2 *D, const double2 *R, int64_t per_pt, int N, const int32_t *skip,
+                          cudaStream_t s);
+cudaError_t launch_update(double2 *X, const float2 *D, int64_t per_pt, int N, const int32_t *skip,
+                          cudaStream_t s);
+
+}  // namespace rsrr

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of include/rsrr.h (same names, argument marshalling only).
+
+Every computation runs in librsrr.so (CUDA, sm_103a).  There is no CPU
+fallback: importing this module fails loudly if the library is missing.
+Device buffers may be given as torch CUDA tensors (their data_ptr() is
+passed) and streams as torch.cuda.Stream objects or raw handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsrr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`"
+        " (the resolvent-sampling library has no CPU fallback)")
+
+_lib = C.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- constants
+RSRR_OK, RSRR_EINVAL, RSRR_ENOMEM, RSRR_ESINGULAR = 0, -1, -2, -3
+RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7, 1
+RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = range(6)
+RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
+RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
+RSRR_MAX_TERMS = 8
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",
+                -5: "ETIMEOUT", -6: "ECUDA", -7: "ESTATE", 1: "WGAP"}
+
+
+# ---------------------------------------------------------------- structs
+class rsrr_c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class rsrr_fn(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("param", C.c_double),
+                ("scale", rsrr_c128)]
+
+
+class rsrr_nep(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("reserved", C.c_int32),
+                ("row_ptr", C.POINTER(C.c_int64)), ("col_idx", C.POINTER(C.c_int32)),
+                ("values", C.POINTER(C.c_double)), ("fn", rsrr_fn * RSRR_MAX_TERMS)]
+
+
+class rsrr_region(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("center", rsrr_c128),
+                ("a", C.c_double), ("b", C.c_double), ("points", C.POINTER(rsrr_c128))]
+
+
+class rsrr_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_refine", C.c_int32), ("eta_tol", C.c_double),
+                ("delta", C.c_double), ("delta_floor", C.c_double), ("tol_gap", C.c_double),
+                ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
+                ("host_threads", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rsrr_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("N", C.c_int32), ("L", C.c_int32), ("m", C.c_int32),
+                ("kl", C.c_int32), ("ku", C.c_int32), ("refine_sweeps", C.c_int32),
+                ("converged", C.c_int32), ("singular_point", C.c_int32), ("k", C.c_int32),
+                ("kc", C.c_int32), ("max_eta", C.c_double), ("sigma1", C.c_double),
+                ("sigmak", C.c_double), ("device_bytes", C.c_size_t)]
+
+
+class rsrr_result(C.Structure):
+    _fields_ = [("count", C.c_int32), ("nbar", C.c_int32), ("gmax", C.c_double),
+                ("lam", C.POINTER(rsrr_c128)), ("res", C.POINTER(C.c_double)),
+                ("V", C.POINTER(rsrr_c128))]
+
+
+_h = C.c_void_p
+_p = C.c_void_p
+
+
+def _sig(name, restype, argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = argtypes
+    return f
+
+
+rsrr_opts_default = _sig("rsrr_opts_default", None, [C.POINTER(rsrr_opts)])
+rsrr_create = _sig("rsrr_create", C.c_int, [C.POINTER(rsrr_nep), C.POINTER(rsrr_region),
+                                            C.c_int32, C.c_int32, C.POINTER(rsrr_opts),
+                                            C.POINTER(_h)])
+rsrr_set_probe = _sig("rsrr_set_probe", C.c_int, [_h, _p, C.c_int32, _p])
+rsrr_sample = _sig("rsrr_sample", C.c_int, [_h, _p])
+rsrr_check = _sig("rsrr_check", C.c_int, [_h, _p])
+rsrr_project = _sig("rsrr_project", C.c_int, [_h, _p])
+rsrr_solve = _sig("rsrr_solve", C.c_int, [_h, C.POINTER(rsrr_result)])
+rsrr_get_samples = _sig("rsrr_get_samples", C.c_int, [_h, _p, C.c_int32, _p])
+rsrr_get_eta = _sig("rsrr_get_eta", C.c_int, [_h, _p])
+rsrr_get_Q = _sig("rsrr_get_Q", C.c_int, [_h, _p, C.c_int32, _p])
+rsrr_get_projected = _sig("rsrr_get_projected", C.c_int, [_h, _p, C.c_int32, _p])
+rsrr_get_points = _sig("rsrr_get_points", C.c_int, [_h, _p])
+rsrr_get_stats = _sig("rsrr_get_stats", C.c_int, [_h, C.POINTER(rsrr_stats)])
+rsrr_last_error = _sig("rsrr_last_error", C.c_char_p, [_h])
+rsrr_destroy = _sig("rsrr_destroy", None, [_h])
+
+
+class RSRRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(buf):
+    """Device pointer of a torch tensor, or address of a numpy array."""
+    if hasattr(buf, "data_ptr"):
+        return C.c_void_p(buf.data_ptr())
+    return buf.ctypes.data_as(C.c_void_p)
+
+
+def default_opts(**kw) -> rsrr_opts:
+    o = rsrr_opts()
+    rsrr_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """Owns one rsrr_t handle built from a problem description with fields
+    n, row_ptr, col_idx, values (list of m arrays), fns (kind, param, scale),
+    region (center, a, b, kind, points), N, L."""
+
+    def __init__(self, prob, opts: rsrr_opts | None = None, N: int | None = None,
+                 L: int | None = None):
+        self.prob = prob
+        self.N = int(N if N is not None else prob.N)
+        self.L = int(L if L is not None else prob.L)
+        self.n = int(prob.n)
+        self._row_ptr = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
+        self._col_idx = np.ascontiguousarray(prob.col_idx, dtype=np.int32)
+        self._values = np.ascontiguousarray(np.concatenate(
+            [np.asarray(v, dtype=np.float64) for v in prob.values]))
+        nep = rsrr_nep()
+        nep.n = self.n
+        nep.m = len(prob.values)
+        nep.row_ptr = self._row_ptr.ctypes.data_as(C.POINTER(C.c_int64))
+        nep.col_idx = self._col_idx.ctypes.data_as(C.POINTER(C.c_int32))
+        nep.values = self._values.ctypes.data_as(C.POINTER(C.c_double))
+        for i, fn in enumerate(prob.fns):
+            sc = complex(fn.scale)
+            nep.fn[i] = rsrr_fn(int(fn.kind), 0, float(fn.param), rsrr_c128(sc.real, sc.imag))
+        reg = rsrr_region()
+        r = prob.region
+        reg.center = rsrr_c128(complex(r.center).real, complex(r.center).imag)
+        reg.a, reg.b = float(r.a), float(r.b)
+        self._pts = None
+        if getattr(r, "kind", "ellipse") == "points":
+            reg.kind = RSRR_REGION_POINTS
+            self._pts = np.ascontiguousarray(np.asarray(r.points, dtype=np.complex128))
+            reg.points = self._pts.ctypes.data_as(C.POINTER(rsrr_c128))
+        else:
+            reg.kind = RSRR_REGION_ELLIPSE
+        self.opts = opts if opts is not None else default_opts()
+        h = _h()
+        st = rsrr_create(C.byref(nep), C.byref(reg), self.N, self.L, C.byref(self.opts),
+                         C.byref(h))
+        if st != RSRR_OK:
+            raise RSRRError(st, rsrr_last_error(None).decode())
+        self.h = h
+        if getattr(prob, "U", None) is not None:
+            self.set_probe(prob.U)
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st, ok=(RSRR_OK,)):
+        if st not in ok:
+            raise RSRRError(st, rsrr_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            rsrr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- calls
+    def set_probe(self, U, stream=None):
+        if hasattr(U, "data_ptr"):
+            return self._check(rsrr_set_probe(self.h, _ptr(U), 1, _stream_handle(stream)))
+        Uf = np.asfortranarray(np.asarray(U, dtype=np.complex128))
+        assert Uf.shape == (self.n, self.L)
+        return self._check(rsrr_set_probe(self.h, Uf.ctypes.data_as(C.c_void_p), 0, None))
+
+    def sample(self, stream=None):
+        return self._check(rsrr_sample(self.h, _stream_handle(stream)))
+
+    def check(self, stream=None):
+        return self._check(rsrr_check(self.h, _stream_handle(stream)))
+
+    def check_status(self, stream=None):
+        return rsrr_check(self.h, _stream_handle(stream))
+
+    def project(self, stream=None):
+        return self._check(rsrr_project(self.h, _stream_handle(stream)))
+
+    def samples(self, out=None, stream=None):
+        """S (n x N*L) as a numpy array, or into a device tensor `out`."""
+        if out is not None:
+            self._check(rsrr_get_samples(self.h, _ptr(out), 1, _stream_handle(stream)))
+            return out
+        S = np.empty((self.N * self.L, self.n), dtype=np.complex128)
+        self._check(rsrr_get_samples(self.h, S.ctypes.data_as(C.c_void_p), 0,
+                                     _stream_handle(stream)))
+        return S.T
+
+    def eta(self):
+        e = np.empty(self.N * self.L, dtype=np.float64)
+        self._check(rsrr_get_eta(self.h, e.ctypes.data_as(C.c_void_p)))
+        return e
+
+    def points(self):
+        z = np.empty(self.N, dtype=np.complex128)
+        self._check(rsrr_get_points(self.h, z.ctypes.data_as(C.c_void_p)))
+        return z
+
+    def stats(self) -> dict:
+        s = rsrr_stats()
+        self._check(rsrr_get_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in rsrr_stats._fields_}
+
+    def Q(self, out=None, stream=None):
+        k = self.stats()["k"]
+        if out is not None:
+            self._check(rsrr_get_Q(self.h, _ptr(out), 1, _stream_handle(stream)))
+            return out
+        Q = np.empty((k, self.n), dtype=np.complex128)
+        self._check(rsrr_get_Q(self.h, Q.ctypes.data_as(C.c_void_p), 0, _stream_handle(stream)))
+        return Q.T
+
+    def projected(self, out=None, stream=None):
+        k = self.stats()["k"]
+        m = len(self.prob.values)
+        if out is not None:
+            self._check(rsrr_get_projected(self.h, _ptr(out), 1, _stream_handle(stream)))
+            return out
+        P = np.empty((m, k, k), dtype=np.complex128)
+        self._check(rsrr_get_projected(self.h, P.ctypes.data_as(C.c_void_p), 0,
+                                       _stream_handle(stream)))
+        return [P[i].T.copy() for i in range(m)]
+
+    def solve(self) -> dict:
+        r = rsrr_result()
+        st = self._check(rsrr_solve(self.h, C.byref(r)), ok=(RSRR_OK, RSRR_WGAP))
+        cnt = r.count
+        lam = np.ctypeslib.as_array(C.cast(r.lam, C.POINTER(C.c_double)), shape=(cnt * 2,)).copy() \
+            if cnt else np.zeros(0)
+        lam = lam.view(np.complex128) if cnt else np.zeros(0, dtype=np.complex128)
+        res = np.ctypeslib.as_array(r.res, shape=(cnt,)).copy() if cnt else np.zeros(0)
+        if cnt:
+            V = np.ctypeslib.as_array(C.cast(r.V, C.POINTER(C.c_double)),
+                                      shape=(cnt * self.n * 2,)).copy().view(np.complex128)
+            V = V.reshape(cnt, self.n).T
+        else:
+            V = np.zeros((self.n, 0), dtype=np.complex128)
+        return dict(status=st, lam=lam, res=res, V=V, nbar=r.nbar, gmax=r.gmax)

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every function include/rsrr.h
+declares (no compute call: no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rsrr.h")
+LIB = os.path.join(ROOT, "paper_1605_07951_gb300", "librsrr.so")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(rsrr_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        from paper_1605_07951_gb300 import build
+        build.build()
+    return ctypes.CDLL(LIB)
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for required in ("rsrr_create", "rsrr_sample", "rsrr_project", "rsrr_solve",
+                     "rsrr_set_probe", "rsrr_get_samples", "rsrr_get_Q", "rsrr_get_projected",
+                     "rsrr_get_stats", "rsrr_destroy", "rsrr_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rsrr_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_uses_the_same_names(lib):
+    from paper_1605_07951_gb300 import rsrr
+    for name in declared_functions():
+        assert callable(getattr(rsrr, name)), name
+
+
+def test_struct_layouts_match_the_header(lib):
+    from paper_1605_07951_gb300 import rsrr
+    assert ctypes.sizeof(rsrr.rsrr_c128) == 16
+    assert ctypes.sizeof(rsrr.rsrr_fn) == 32
+    assert ctypes.sizeof(rsrr.rsrr_region) == 48
+    # defaults come from the library itself
+    o = rsrr.default_opts()
+    assert o.precision == rsrr.RSRR_PREC_MIXED and o.eta_tol == 1e-10 and o.delta == 1e-14
+    assert o.NQ == 500 and o.KQ == 2 and o.tol_gap == 1e3
+
+
+def test_create_rejects_bad_descriptors_without_touching_the_gpu(lib):
+    import numpy as np
+    from paper_1605_07951_gb300 import rsrr
+    import workloads as W
+    p = W.random_banded(n=40, kl=2, ku=2, N=2, L=2)
+    p.col_idx = p.col_idx.copy()
+    p.col_idx[3] = 10_000  # column out of range
+    with pytest.raises(rsrr.RSRRError) as e:
+        rsrr.Solver(p)
+    assert e.value.status == rsrr.RSRR_EINVAL
+    p = W.random_banded(n=40, kl=2, ku=2, N=2, L=2)
+    p.region.a = -1.0
+    with pytest.raises(rsrr.RSRRError) as e:
+        rsrr.Solver(p)
+    assert e.value.status == rsrr.RSRR_EINVAL
