@@ -1,0 +1,330 @@
+"""Benchmark of the resolvent-sampling hot path on one GB300.
+
+Workload: the rational 5-point-grid NEP T(z) = K - zM + (z/(z-300))E, n = 40000
+(200 x 200 grid, natural ordering, half-bandwidth 200), ellipse centre 100,
+semi-axes 80/20, N = 64 sampling points, L = 32 probe columns, mixed precision
+(complex64 band LU, FP64 refinement to backward error <= 1e-10).
+
+One step = one pass of the whole GPU hot path over the workload: rsrr_sample
+(assembly, band LU, solves, FP64 refinement) + rsrr_project (normalisation,
+Gram, truncated SVD basis, projections).  value = resolvent columns (N*L per
+step) per second of device time; e2e = the same through the C ABI with the
+probe U in pinned host memory copied in and the projected matrices copied
+out every step.  The oracle (numpy/scipy, FP64) is timed on a bounded sample
+of the same workload as the CPU baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid5pt_rational_n40000_bw200_N64_L32"
+METRIC = "resolvent columns/s at 1e-10 rel. residual (mixed vs FP64); RSRR p50/p99 latency"
+UNIT = "resolvent columns/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x FMA x max SM clock (GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--g", type=int, default=200, help="grid side (n = g^2)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--sample-points", type=int, default=2,
+                    help="sampling points of the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- oracle leg
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle, workloads as W
+p = W.rational_grid(g={g})
+z = oracle.sample_points(p.region, p.N)[:{npts}]
+oracle.resolvent_samples(p, z[:1])  # warm the code paths
+t = time.perf_counter()
+X = oracle.resolvent_samples(p, z)
+dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt, "columns": int(len(z) * p.L)}}))
+"""
+
+
+def oracle_sample(g, npts):
+    """Time the oracle's resolvent samples (LAPACK banded solves) on `npts`
+    points of the workload in a 1-thread subprocess (BLAS pinned to 1 thread)."""
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, g=g, npts=npts)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["columns"] / d["seconds"], d
+
+
+def cpu_baseline(g, npts):
+    v, d = oracle_sample(g, npts)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{npts} of the 64 sampling points ({d['columns']} resolvent columns, "
+                      f"scipy banded LU, FP64) in {d['seconds']:.1f} s, 1 BLAS thread"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    p = W.rational_grid(g=a.g)
+    opts = rsrr.default_opts(timing=1)
+    s = rsrr.Solver(p, opts)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.sample(stream)
+        s.project(stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = s.check_status()
+    if st != rsrr.RSRR_OK:
+        raise SystemExit(f"sampling did not converge: {rsrr.STATUS_NAMES.get(st, st)}")
+    stats0 = s.stats()
+    launches0 = stats0["launches"]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    lu_ms, sample_ms, project_ms = [], [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+        # the library's own events on the same stream give the stage times
+        torch.cuda.synchronize()
+        sti = s.stats()
+        lu_ms.append(sti["stage_ms"][1])
+        sample_ms.append(sum(sti["stage_ms"][:5]))
+        project_ms.append(sti["stage_ms"][5])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stats = s.stats()
+    assert stats["converged"] == 1 and stats["max_eta"] <= 1e-10, stats
+    launches = (stats["launches"] - launches0)
+    cols = p.N * p.L
+    value = cols * world / (ms / 1e3)
+
+    # e2e: U from pinned host memory, projected matrices back to the host, per step
+    Uh = torch.from_numpy(np.ascontiguousarray(p.U.T)).pin_memory()  # rows = columns of U
+    k = stats["k"]
+    Pout = torch.empty((p.m, k, k), dtype=torch.complex128).pin_memory()
+    import ctypes as C
+
+    def e2e_step():
+        st = rsrr.rsrr_set_probe(s.h, C.c_void_p(Uh.data_ptr()), 0, None)
+        assert st == 0
+        s.sample(stream)
+        s.project(stream)
+        kk = s.stats()["k"]
+        st = rsrr.rsrr_get_projected(s.h, C.c_void_p(Pout.data_ptr()), 0,
+                                     C.c_void_p(stream.cuda_stream))
+        assert st == 0 and kk == k
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / a.steps
+    e2e = {"value": cols * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(Uh.numel() * 16),
+           "d2h_bytes_per_step": int(p.m * k * k * 16)}
+
+    # roofline of the dominant kernel (complex64 band LU, FP32 FMA pipe)
+    n, kl, ku = p.n, stats["kl"], stats["ku"]
+    flop_per_point = 8.0 * sum(min(kl, n - 1 - j) * min(kl + ku, n - 1 - j) for j in range(n))
+    lu_flops = flop_per_point * p.N
+    lu_avg = statistics.mean(lu_ms)
+    achieved = lu_flops / (lu_avg / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "band_lu_kernel<float2> (complex64 FMA, all 64 points)",
+            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "algorithmic_flop_per_launch": lu_flops, "avg_launch_ms": lu_avg,
+            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+
+    fp64 = None
+    if not a.no_fp64:
+        s64 = rsrr.Solver(p, rsrr.default_opts(precision=rsrr.RSRR_PREC_FP64, timing=1))
+        s64.sample(stream)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.sample(stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        st64 = s64.stats()
+        fms = f0.elapsed_time(f1)
+        fp64 = {"sample_value": cols / (fms / 1e3), "sample_ms": fms,
+                "max_eta": st64["max_eta"], "lu_ms": st64["stage_ms"][1]}
+        s64.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": p.n, "kl": kl, "ku": ku, "N": p.N, "L": p.L,
+                   "precision": "mixed (complex64 band LU, FP64 refinement to eta<=1e-10)",
+                   "step": "rsrr_sample + rsrr_project",
+                   "l2": "inputs larger than L2: the 12.9 GB band workspace is rewritten every step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "sample_only": {"value": cols / (statistics.mean(sample_ms) / 1e3),
+                        "ms": statistics.mean(sample_ms), "stage_ms": stats["stage_ms"][:5],
+                        "refine_sweeps": stats["refine_sweeps"], "max_eta": stats["max_eta"]},
+        "project_ms": statistics.mean(project_ms), "rank_k": k, "pivoted_cholesky_kc": stats["kc"],
+        "fp64_plain_path": fp64,
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    s.close()
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a.g, a.sample_points)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    """The oracle (FP64 numpy/scipy) as the reference arm: each step is a
+    bounded sample (a.sample_points sampling points) of the same workload."""
+    if rank != 0:
+        return
+    times, cols = [], 0
+    d = None
+    for i in range(a.warmup + a.steps):
+        v, d = oracle_sample(a.g, a.sample_points)
+        if i >= a.warmup:
+            times.append(d["seconds"])
+    cols = d["columns"]
+    sec = statistics.mean(times)
+    value = cols / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": a.g * a.g, "N": 64, "L": 32,
+                   "step": f"oracle resolvent samples at {a.sample_points} of the 64 points"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{a.sample_points} sampling points per step, 1 BLAS thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    run_ours(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

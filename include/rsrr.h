@@ -137,13 +137,14 @@ typedef struct {
     int32_t max_refine;  /* refinement sweeps, default 8 */
     double eta_tol;      /* default 1e-10 */
     double delta;        /* SVD truncation of S relative to sigma_1, paper's 1e-14 */
-    double delta_floor;  /* truncation floor of the Gram-based SVD, default 1e-7 */
+    double delta_floor;  /* resolution floor of the Gram-based SVD, default 1e-12 */
     double tol_gap;      /* gap test of SS-FULL, default 1e3 (Section 2.3) */
     double res_tol;      /* acceptance of an eigenpair by residual, default 1e-6 */
     int32_t NQ;          /* SS-FULL quadrature points, default 500 */
     int32_t KQ;          /* SS-FULL moments, default 2 */
     int32_t host_threads;/* threads of rsrr_solve, 0 = all cores */
-    int32_t reserved;
+    int32_t timing;      /* nonzero: record CUDA events around every stage on the
+                            caller's stream; times appear in rsrr_stats.stage_ms */
 } rsrr_opts;
 
 typedef struct rsrr_handle rsrr_t;
@@ -159,6 +160,11 @@ typedef struct {
     double max_eta;        /* largest per-column backward error after rsrr_sample */
     double sigma1, sigmak; /* largest and smallest kept singular value of S */
     size_t device_bytes;   /* device memory held by the handle */
+    int64_t launches;      /* CUDA kernels launched by the handle since rsrr_create */
+    /* with opts.timing: device time (ms) of the last rsrr_sample / rsrr_project
+     * stages: [0] assembly + ||T||, [1] band LU, [2] first solve, [3] refinement
+     * sweeps, [4] final backward errors, [5] rsrr_project */
+    double stage_ms[6];
 } rsrr_stats;
 
 /* Result of rsrr_solve.  Arrays are host memory owned by the handle, valid
@@ -199,9 +205,11 @@ rsrr_status rsrr_sample(rsrr_t *h, void *stream);
  * ENOCONV (some column above eta_tol after max_refine sweeps). */
 rsrr_status rsrr_check(rsrr_t *h, void *stream);
 
-/* Steps 3-4, GPU part, asynchronously on `stream`: column normalisation of
- * S, orthonormal basis Q (n x k) of its dominant singular subspace, and
- * P_i = Q^H A_i Q.  Requires a previous rsrr_sample. */
+/* Steps 3-4, GPU part, on `stream`: column normalisation of S, orthonormal
+ * basis Q (n x k) of its dominant singular subspace, and P_i = Q^H A_i Q.
+ * Requires a previous rsrr_sample.  The call waits on `stream` twice (to size
+ * the basis: the pivoted-Cholesky rank and the kept singular values); the
+ * final products run asynchronously. */
 rsrr_status rsrr_project(rsrr_t *h, void *stream);
 
 /* Steps 4-5, host part (synchronises the handle's work first): SS-FULL on

@@ -21,6 +21,7 @@ UNITS = [
     ("band_lu.cu", ["-DRSRR_LU_ONLY=64"], "band_lu64.o"),
     ("band_lu.cu", ["-DRSRR_LU_ONLY=128"], "band_lu128.o"),
     ("proj.cu", [], "proj.o"),
+    ("ssfull_host.cpp", ["-x", "cu"], "ssfull_host.o"),
 ]
 
 

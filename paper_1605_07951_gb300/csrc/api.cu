@@ -62,6 +62,8 @@ template <typename T> cudaError_t Handle::alloc(T **p, size_t count) {
 
 Handle::~Handle() {
     for (void *p : allocations) cudaFree(p);
+    for (auto &e : events)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace rsrr
@@ -83,7 +85,7 @@ void rsrr_opts_default(rsrr_opts *o) {
     o->max_refine = 8;
     o->eta_tol = 1e-10;
     o->delta = 1e-14;
-    o->delta_floor = 1e-7;
+    o->delta_floor = 1e-12;
     o->tol_gap = 1e3;
     o->res_tol = 1e-6;
     o->NQ = 500;
@@ -284,6 +286,12 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
     if (!h || !out) return RSRR_EINVAL;
     CK(cudaDeviceSynchronize(), "get_stats sync");
     if (h->sampled) h->read_outcome();
+    if (h->timed_project) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, h->events[6], h->events[7]), "event time");
+        h->stage_ms[5] = t;
+        h->timed_project = false;
+    }
     memset(out, 0, sizeof *out);
     out->n = h->n; out->N = h->N; out->L = h->L; out->m = h->m;
     out->kl = h->kl; out->ku = h->ku;
@@ -296,6 +304,8 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
     out->sigma1 = h->sigma1;
     out->sigmak = h->sigmak;
     out->device_bytes = h->device_bytes;
+    out->launches = h->launches;
+    for (int i = 0; i < 6; ++i) out->stage_ms[i] = h->stage_ms[i];
     return RSRR_OK;
 }
 
@@ -381,19 +391,36 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
 }
 
 // Step 2 of RSRR on the GPU, asynchronously on stream s.
+rsrr_status Handle::mark(int i, cudaStream_t s) {
+    Handle *h = this;
+    if (!opts.timing) return RSRR_OK;
+    if (!events[0]) {
+        for (auto &e : events) CK(cudaEventCreate(&e), "event");
+    }
+    CK(cudaEventRecord(events[i], s), "event record");
+    return RSRR_OK;
+}
+
+// Step 2 of RSRR on the GPU, asynchronously on stream s.
 rsrr_status Handle::sample(cudaStream_t s) {
     Handle *h = this;
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L;
+    rsrr_status ms;
+    if ((ms = mark(0, s)) != RSRR_OK) return ms;
     CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
     CK(launch_tnorm(d_tnorm, dp, s), "tnorm");
     if (opts.precision == RSRR_PREC_MIXED) {
         CK(launch_assemble<float2>(d_ab32, geom, dp, s), "assemble");
+        if ((ms = mark(1, s)) != RSRR_OK) return ms;
         CK(launch_band_lu_c64(d_ab32, d_piv, d_info, geom, N, nn, s), "band LU");
+        if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
         CK(launch_band_solve_c64(d_ab32, d_piv, d_D, geom, N, nn, L, nullptr, s), "band solve");
         CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
         CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
+        if ((ms = mark(3, s)) != RSRR_OK) return ms;
+        launches += 5;  // assemble, LU, probe, solve, widen
         for (int it = 0; it < opts.max_refine; ++it) {
             CK(launch_residual(d_R, d_X, dp, d_rmax, d_xmax, d_done, s), "residual");
             CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
@@ -401,22 +428,40 @@ rsrr_status Handle::sample(cudaStream_t s) {
             CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
             CK(launch_band_solve_c64(d_ab32, d_piv, d_D, geom, N, nn, L, d_done, s), "band solve");
             CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
+            launches += 5;
         }
     } else {
         CK(launch_assemble<double2>(d_ab64, geom, dp, s), "assemble");
+        if ((ms = mark(1, s)) != RSRR_OK) return ms;
         CK(launch_band_lu_c128(d_ab64, d_piv, d_info, geom, N, nn, s), "band LU");
+        if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
         CK(launch_band_solve_c128(d_ab64, d_piv, d_X, geom, N, nn, L, nullptr, s), "band solve");
+        if ((ms = mark(3, s)) != RSRR_OK) return ms;
+        launches += 4;  // assemble, LU, probe, solve
     }
+    if ((ms = mark(4, s)) != RSRR_OK) return ms;
     // final backward errors of every column (statistics and convergence)
     CK(launch_residual(nullptr, d_X, dp, d_rmax, d_xmax, nullptr, s), "residual");
     CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
                   d_sweep_flags + opts.max_refine + 1, nullptr, s), "eta");
+    if ((ms = mark(5, s)) != RSRR_OK) return ms;
+    launches += 3;  // tnorm, final residual, final eta
+    timed_sample = opts.timing != 0;
     return RSRR_OK;
 }
 
 rsrr_status Handle::read_outcome() {
     Handle *h = this;
+    if (timed_sample) {
+        float t;
+        const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
+        for (int i = 0; i < 5; ++i) {
+            CK(cudaEventElapsedTime(&t, events[pairs[i][0]], events[pairs[i][1]]), "event time");
+            stage_ms[i] = t;
+        }
+        timed_sample = false;
+    }
     std::vector<int32_t> info(N), flags(opts.max_refine + 2);
     std::vector<double> eta((size_t)N * L);
     CK(cudaMemcpy(info.data(), d_info, sizeof(int32_t) * N, cudaMemcpyDeviceToHost), "outcome");

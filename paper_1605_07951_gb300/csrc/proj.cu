@@ -1,16 +1,976 @@
-// placeholder, replaced by the projection stage
+// RSRR steps 3-4 on the GPU (Section 3.2 last paragraph, Section 3.3 steps
+// 3-4): unit-norm columns of S, an orthonormal basis Q of the dominant
+// singular subspace of S, and the projected coefficients P_i = Q^H A_i Q.
+//
+// Truncated SVD through the Gram matrix, all in FP64:
+//   G = D^{-1} S^H S D^{-1}            (D = column norms; Hermitian GEMM)
+//   G ~ B B^H                           (pivoted Cholesky, stopped when the
+//                                        largest remaining diagonal <= floor^2)
+//   B^H B = Y Lambda Y^H                (parallel cyclic Jacobi)
+//   sigma_j = sqrt(lambda_j),  keep sigma_j > max(delta, floor) sigma_1
+//   Q1 = S D^{-1} B Y_k Lambda_k^{-1}  (= S_n V_k Sigma_k^{-1})
+//   Q1^H Q1 = Z M Z^H,  Q = Q1 Z M^{-1/2}   (second pass restores
+//                                        orthogonality lost in the Gram route)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
 #include "rsrr_handle.h"
-extern "C" rsrr_status rsrr_project(rsrr_t *hh, void *stream) {
-    (void)stream;
-    rsrr::Handle *h = reinterpret_cast<rsrr::Handle *>(hh);
-    if (!h) return RSRR_EINVAL;
-    return h->fail(RSRR_ESTATE, "rsrr_project: not available");
+
+namespace rsrr {
+
+// ==========================================================================
+// FP64 complex GEMM: C = alpha * op(A) * B + beta * C (column major),
+// op(A) = A (M x K) or A^H (A is K x M).  64x64 tiles, 256 threads with 4x4
+// outputs each, K slabs of 16 through shared memory, optional split-K into a
+// workspace (deterministic reduction) and optional upper-tile-only mode for
+// Hermitian products (the lower triangle is mirrored afterwards).
+// ==========================================================================
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256)
+zgemm_kernel(int M, int N, int K, bool conjA, const double2 *__restrict__ A, int64_t lda,
+             const double2 *__restrict__ B, int64_t ldb, double2 *__restrict__ Cout, int64_t ldc,
+             int kchunk, bool upper_only, double alpha, double beta) {
+    const int bm = blockIdx.x, bn = blockIdx.y, ks = blockIdx.z;
+    if (upper_only && bm > bn) return;
+    __shared__ double2 As[GK][GT + 1];
+    __shared__ double2 Bs[GK][GT + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;  // outputs rows tx+16a, cols ty+16b
+    const int m0 = bm * GT, n0 = bn * GT;
+    const int kbeg = ks * kchunk, kend = min(K, kbeg + kchunk);
+    double2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0.0, 0.0);
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
+        // A tile: op(A)(m0+i, k0+kk)
+        for (int q = tid; q < GT * GK; q += 256) {
+            int i, kk;
+            double2 v = make_double2(0.0, 0.0);
+            if (conjA) {  // element (kk, i) of A, kk fastest
+                kk = q % GK; i = q / GK;
+                if (m0 + i < M && k0 + kk < kend) {
+                    v = A[(int64_t)(m0 + i) * lda + (k0 + kk)];
+                    v.y = -v.y;
+                }
+            } else {      // element (i, kk) of A, i fastest
+                i = q % GT; kk = q / GT;
+                if (m0 + i < M && k0 + kk < kend) v = A[(int64_t)(k0 + kk) * lda + (m0 + i)];
+            }
+            As[kk][i] = v;
+        }
+        for (int q = tid; q < GT * GK; q += 256) {
+            const int kk = q % GK, j = q / GK;
+            double2 v = make_double2(0.0, 0.0);
+            if (n0 + j < N && k0 + kk < kend) v = B[(int64_t)(n0 + j) * ldb + (k0 + kk)];
+            Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GK; ++kk) {
+            double2 av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = cfma(acc[a][b], av[a], bv[b]);
+        }
+        __syncthreads();
+    }
+    double2 *Cp = Cout + (int64_t)ks * ldc * N;  // split-K slab (ks = 0 when direct)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = m0 + tx + 16 * a, j = n0 + ty + 16 * b;
+            if (i < M && j < N) {
+                double2 r = make_double2(alpha * acc[a][b].x, alpha * acc[a][b].y);
+                if (beta != 0.0) {
+                    const double2 c = Cp[(int64_t)j * ldc + i];
+                    r.x = fma(beta, c.x, r.x);
+                    r.y = fma(beta, c.y, r.y);
+                }
+                Cp[(int64_t)j * ldc + i] = r;
+            }
+        }
 }
+
+// C = alpha * sum_s W[s] + beta * C over the split-K slabs (fixed order)
+__global__ void splitk_reduce_kernel(double2 *__restrict__ C, int64_t ldc,
+                                     const double2 *__restrict__ W, int M, int N, int S,
+                                     double2 alpha, double2 beta, bool upper_only) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % M), j = (int)(q / M);
+        if (upper_only && (i / GT) > (j / GT)) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int t = 0; t < S; ++t) s = cadd(s, W[(int64_t)t * M * N + (int64_t)j * M + i]);
+        double2 c = C[(int64_t)j * ldc + i];
+        double2 r = cmul(alpha, s);
+        if (beta.x != 0.0 || beta.y != 0.0) r = cfma(r, beta, c);
+        C[(int64_t)j * ldc + i] = r;
+    }
+}
+
+// lower triangle <- conj(upper) for Hermitian results computed by tiles
+__global__ void hermitian_mirror_kernel(double2 *__restrict__ C, int64_t ldc, int n) {
+    const int64_t total = (int64_t)n * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % n), j = (int)(q / n);
+        if (i > j) {
+            double2 v = C[(int64_t)i * ldc + j];
+            C[(int64_t)j * ldc + i] = make_double2(v.x, -v.y);
+        }
+    }
+}
+
+static int grid1d(int64_t work, int threads = 256) {
+    int64_t g = (work + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+// workspace-backed GEMM: chooses split-K so that enough CTAs run
+struct Gemm {
+    double2 *ws = nullptr;
+    size_t ws_elems = 0;
+    int64_t *counter = nullptr;
+    cudaError_t run(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
+                    const double2 *B, int64_t ldb, double2 *C, int64_t ldc, cudaStream_t s,
+                    bool hermitian = false, double alpha = 1.0, double beta = 0.0) {
+        if (M <= 0 || N <= 0) return cudaSuccess;
+        const int tm = (M + GT - 1) / GT, tn = (N + GT - 1) / GT;
+        int64_t tiles = hermitian ? (int64_t)tm * (tm + 1) / 2 : (int64_t)tm * tn;
+        int splits = 1;
+        const int64_t target = 152 * 2;
+        if (tiles < target && K > 4 * GK) {
+            splits = (int)std::min<int64_t>((target + tiles - 1) / tiles, (K + 255) / 256);
+            while (splits > 1 && (size_t)splits * M * N > ws_elems) --splits;
+        }
+        if (K <= 0) splits = 1;
+        if (splits > 1 && (size_t)splits * M * N > ws_elems) splits = 1;
+        int kchunk = (K + splits - 1) / splits;
+        kchunk = ((kchunk + GK - 1) / GK) * GK;
+        if (kchunk < GK) kchunk = GK;
+        splits = std::max(1, (K + kchunk - 1) / kchunk);
+        dim3 grid(tm, tn, splits);
+        cudaError_t e;
+        if (counter) *counter += 1 + (splits == 1 ? 0 : 1) + (hermitian ? 1 : 0);
+        if (splits == 1) {  // direct: the kernel writes C itself
+            zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, conjA, A, lda, B, ldb, C, ldc, kchunk,
+                                              hermitian, alpha, beta);
+        } else {
+            zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, conjA, A, lda, B, ldb, ws, M, kchunk,
+                                              hermitian, 1.0, 0.0);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            splitk_reduce_kernel<<<grid1d((int64_t)M * N), 256, 0, s>>>(
+                C, ldc, ws, M, N, splits, make_double2(alpha, 0.0), make_double2(beta, 0.0),
+                hermitian);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (hermitian) {
+            hermitian_mirror_kernel<<<grid1d((int64_t)M * M), 256, 0, s>>>(C, ldc, M);
+            e = cudaGetLastError();
+        }
+        return e;
+    }
+};
+
+// ==========================================================================
+// column norms and scalings
+// ==========================================================================
+__global__ void colnorm_kernel(double *__restrict__ nrm, const double2 *__restrict__ X, int64_t n) {
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 v = X[(int64_t)c * n + i];
+        s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
+    for (int off = 16; off; off >>= 1) s += shfl_down(s, off);
+    __shared__ double w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += w[q];
+        nrm[c] = sqrt(r);
+    }
+}
+
+// G(i,j) /= (d_i d_j)
+__global__ void gram_scale_kernel(double2 *__restrict__ G, const double *__restrict__ d, int n) {
+    const int64_t total = (int64_t)n * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % n), j = (int)(q / n);
+        const double s = 1.0 / (d[i] * d[j]);
+        G[q].x *= s;
+        G[q].y *= s;
+    }
+}
+
+// W(i, j) *= rs[i] * cs[j]   (rs or cs may be null)
+__global__ void scale_rc_kernel(double2 *__restrict__ W, int64_t ld, int M, int N,
+                                const double *__restrict__ rs, const double *__restrict__ cs,
+                                bool rs_inverse, bool cs_inv_sqrt) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % M), j = (int)(q / M);
+        double s = 1.0;
+        if (rs) s *= rs_inverse ? 1.0 / rs[i] : rs[i];
+        if (cs) s *= cs_inv_sqrt ? 1.0 / sqrt(cs[j]) : 1.0 / cs[j];
+        double2 &w = W[(int64_t)j * ld + i];
+        w.x *= s;
+        w.y *= s;
+    }
+}
+
+// ==========================================================================
+// pivoted Cholesky of the Hermitian positive semidefinite G (n x n), one
+// launch per step j (left-looking): pivot p = argmax of the remaining
+// diagonal d (first index on ties), column j of L for every row, d updated
+// into the other buffer.  Stops (flag, kc) when d_p <= tau or j == n.
+// Rows already used as pivots get 0 in later columns.
+// ==========================================================================
+__global__ void pchol_step_kernel(const double2 *__restrict__ G, int n, double2 *__restrict__ Lm,
+                                  const double *__restrict__ dprev, double *__restrict__ dnext,
+                                  int j, double tau, int32_t *__restrict__ state) {
+    // state[0] = stopped flag, state[1] = kc, state[2 + j] = pivot of column j
+    if (state[0]) return;
+    __shared__ double s_v[256];
+    __shared__ int s_i[256];
+    double bv = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = dprev[i];
+        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+    }
+    s_v[threadIdx.x] = bv;
+    s_i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const double ov = s_v[threadIdx.x + w];
+            const int oi = s_i[threadIdx.x + w];
+            if (ov > s_v[threadIdx.x] || (ov == s_v[threadIdx.x] && oi < s_i[threadIdx.x])) {
+                s_v[threadIdx.x] = ov;
+                s_i[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int p = s_i[0];
+    const double dp = s_v[0];
+    if (!(dp > tau)) {
+        // every CTA reaches the same decision; CTA 0 records it.  Later steps
+        // see the flag; this step writes nothing else.
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            state[1] = j;
+            state[0] = 1;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[2 + j] = p;
+    const double sq = sqrt(dp);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        double2 l = make_double2(0.0, 0.0);
+        double dn = dprev[i];
+        if (i == p) {
+            l = make_double2(sq, 0.0);
+            dn = -1.0;
+        } else if (dn >= 0.0) {
+            double2 s = G[(int64_t)p * n + i];
+            for (int t = 0; t < j; ++t) {
+                const double2 a = Lm[(int64_t)t * n + i], b = Lm[(int64_t)t * n + p];
+                // s -= a * conj(b)
+                s.x -= a.x * b.x + a.y * b.y;
+                s.y -= a.y * b.x - a.x * b.y;
+            }
+            l = make_double2(s.x / sq, s.y / sq);
+            dn = fmax(0.0, dn - (l.x * l.x + l.y * l.y));
+        }
+        Lm[(int64_t)j * n + i] = l;
+        dnext[i] = dn;
+    }
+}
+
+__global__ void diag_real_kernel(double *__restrict__ d, const double2 *__restrict__ G, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = G[(int64_t)i * n + i].x;
+}
+
+// ==========================================================================
+// Parallel cyclic Jacobi for a Hermitian k x k matrix: one launch per round
+// of the round-robin ordering (k' = k rounded up to even, k'-1 rounds a
+// sweep).  Each thread owns a 2x2 block (pair a, pair b) of H and rewrites it
+// as J_a^H H J_b, reading the old matrix and writing the new one (double
+// buffer); the rotations come from the old matrix.  Y <- Y J in place.
+// Rotation for [[alpha, beta], [conj(beta), gamma]], beta = |beta| e^{i phi}:
+//   tau = (gamma - alpha) / (2|beta|), t = sign(tau)/(|tau| + sqrt(1+tau^2)),
+//   c = 1/sqrt(1+t^2), s = t c,  J = [[c, s e^{i phi}], [-s e^{-i phi}, c]].
+// ==========================================================================
+struct Rot {
+    double c;
+    double2 se;  // s e^{i phi}
+};
+
+RSRR_DEV void pair_of(int r, int a, int kp, int &p, int &q) {
+    if (a == 0) {
+        p = kp - 1;
+        q = r;
+    } else {
+        p = (r + a) % (kp - 1);
+        q = (r - a + (kp - 1)) % (kp - 1);
+    }
+    if (p > q) { const int t = p; p = q; q = t; }
+}
+
+RSRR_DEV Rot rot_of(const double2 *__restrict__ H, int k, int p, int q) {
+    Rot R;
+    R.c = 1.0;
+    R.se = make_double2(0.0, 0.0);
+    if (p >= k || q >= k) return R;
+    const double al = H[(int64_t)p * k + p].x, ga = H[(int64_t)q * k + q].x;
+    const double2 be = H[(int64_t)q * k + p];  // H(p, q)
+    const double ab = hypot(be.x, be.y);
+    if (ab <= 1e-300 || ab <= 1e-18 * sqrt(fabs(al * ga))) return R;
+    const double tau = (ga - al) / (2.0 * ab);
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+    R.c = c;
+    R.se = make_double2(s * be.x / ab, s * be.y / ab);
+    return R;
+}
+
+__global__ void jacobi_round_kernel(const double2 *__restrict__ Hold, double2 *__restrict__ Hnew,
+                                    double2 *__restrict__ Y, int k, int kp, int r,
+                                    const int32_t *__restrict__ conv) {
+    if (conv[0]) return;
+    const int np = kp / 2;
+    const int64_t nblk = (int64_t)np * np;
+    const int64_t nY = (int64_t)k * np;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nblk + nY;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (q < nblk) {
+            const int a = (int)(q % np), b = (int)(q / np);
+            int pa, qa, pb, qb;
+            pair_of(r, a, kp, pa, qa);
+            pair_of(r, b, kp, pb, qb);
+            const Rot Ra = rot_of(Hold, k, pa, qa), Rb = rot_of(Hold, k, pb, qb);
+            const bool va = qa < k, vb = qb < k;  // pa < qa
+            // rows {pa, qa} x cols {pb, qb}; missing indices (padding) are absent
+            double2 h00 = (pa < k && pb < k) ? Hold[(int64_t)pb * k + pa] : make_double2(0, 0);
+            double2 h01 = (pa < k && vb) ? Hold[(int64_t)qb * k + pa] : make_double2(0, 0);
+            double2 h10 = (va && pb < k) ? Hold[(int64_t)pb * k + qa] : make_double2(0, 0);
+            double2 h11 = (va && vb) ? Hold[(int64_t)qb * k + qa] : make_double2(0, 0);
+            // right: [h00 h01; h10 h11] * Jb, Jb = [[c, se], [-conj(se), c]]
+            const double cb = Rb.c;
+            const double2 sb = Rb.se, sbc = make_double2(-sb.x, sb.y);  // -conj(se)
+            double2 t00 = cadd(make_double2(h00.x * cb, h00.y * cb), cmul(h01, sbc));
+            double2 t01 = cadd(cmul(h00, sb), make_double2(h01.x * cb, h01.y * cb));
+            double2 t10 = cadd(make_double2(h10.x * cb, h10.y * cb), cmul(h11, sbc));
+            double2 t11 = cadd(cmul(h10, sb), make_double2(h11.x * cb, h11.y * cb));
+            // left: Ja^H * T, Ja^H = [[c, -se], [conj(se), c]]
+            const double ca = Ra.c;
+            const double2 sa = Ra.se, msa = make_double2(-sa.x, -sa.y), sac = make_double2(sa.x, -sa.y);
+            double2 n00 = cadd(make_double2(t00.x * ca, t00.y * ca), cmul(msa, t10));
+            double2 n01 = cadd(make_double2(t01.x * ca, t01.y * ca), cmul(msa, t11));
+            double2 n10 = cadd(cmul(sac, t00), make_double2(t10.x * ca, t10.y * ca));
+            double2 n11 = cadd(cmul(sac, t01), make_double2(t11.x * ca, t11.y * ca));
+            if (a == b) {  // diagonal block: exact zero off-diagonal, real diagonal
+                n00.y = 0.0;
+                n11.y = 0.0;
+                if (Ra.se.x != 0.0 || Ra.se.y != 0.0) {
+                    n01 = make_double2(0.0, 0.0);
+                    n10 = make_double2(0.0, 0.0);
+                }
+            }
+            if (pa < k && pb < k) Hnew[(int64_t)pb * k + pa] = n00;
+            if (pa < k && vb) Hnew[(int64_t)qb * k + pa] = n01;
+            if (va && pb < k) Hnew[(int64_t)pb * k + qa] = n10;
+            if (va && vb) Hnew[(int64_t)qb * k + qa] = n11;
+        } else {
+            const int64_t w = q - nblk;
+            const int i = (int)(w % k), b = (int)(w / k);
+            int pb, qb;
+            pair_of(r, b, kp, pb, qb);
+            if (qb >= k) continue;
+            const Rot Rb = rot_of(Hold, k, pb, qb);
+            const double2 yp = Y[(int64_t)pb * k + i], yq = Y[(int64_t)qb * k + i];
+            const double2 sbc = make_double2(-Rb.se.x, Rb.se.y);
+            Y[(int64_t)pb * k + i] = cadd(make_double2(yp.x * Rb.c, yp.y * Rb.c), cmul(yq, sbc));
+            Y[(int64_t)qb * k + i] = cadd(cmul(yp, Rb.se), make_double2(yq.x * Rb.c, yq.y * Rb.c));
+        }
+    }
+}
+
+// off(H)^2 and diag(H)^2 sums -> conv flag when off <= tol^2 * diag
+__global__ void jacobi_check_kernel(const double2 *__restrict__ H, int k, double tol2,
+                                    int32_t *__restrict__ conv, double *__restrict__ acc) {
+    if (conv[0]) return;
+    double off = 0.0, dia = 0.0;
+    const int64_t total = (int64_t)k * k;
+    for (int64_t q = threadIdx.x; q < total; q += blockDim.x) {
+        const int i = (int)(q % k), j = (int)(q / k);
+        const double2 v = H[q];
+        const double a = v.x * v.x + v.y * v.y;
+        if (i == j) dia += a; else off += a;
+    }
+    __shared__ double so[256], sd[256];
+    so[threadIdx.x] = off;
+    sd[threadIdx.x] = dia;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            so[threadIdx.x] += so[threadIdx.x + w];
+            sd[threadIdx.x] += sd[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        acc[0] = so[0];
+        acc[1] = sd[0];
+        if (so[0] <= tol2 * sd[0]) conv[0] = 1;
+    }
+}
+
+__global__ void identity_kernel(double2 *__restrict__ Y, int k) {
+    const int64_t total = (int64_t)k * k;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        Y[q] = make_double2((q % k) == (q / k) ? 1.0 : 0.0, 0.0);
+}
+
+// eigenvalues = real diagonal; order[r] = index of the r-th largest (ties by index);
+// vals[r] sorted descending.  One CTA.
+__global__ void sort_desc_kernel(const double2 *__restrict__ H, int k, int32_t *__restrict__ order,
+                                 double *__restrict__ vals) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double vi = H[(int64_t)i * k + i].x;
+        int rank = 0;
+        for (int j = 0; j < k; ++j) {
+            const double vj = H[(int64_t)j * k + j].x;
+            if (vj > vi || (vj == vi && j < i)) ++rank;
+        }
+        order[rank] = i;
+        vals[rank] = vi;
+    }
+}
+
+// Dst(:, r) = Src(:, order[r]) for r < cols
+__global__ void gather_cols_kernel(double2 *__restrict__ Dst, const double2 *__restrict__ Src,
+                                   int64_t rows, int cols, const int32_t *__restrict__ order) {
+    const int64_t total = rows * cols;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % rows;
+        const int r = (int)(q / rows);
+        Dst[q] = Src[(int64_t)order[r] * rows + i];
+    }
+}
+
+// ==========================================================================
+// Y = A_q X for the real CSR matrix A_q (term q of the shared pattern), X n x k
+// ==========================================================================
+__global__ void spmm_kernel(double2 *__restrict__ Y, const double2 *__restrict__ X,
+                            const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                            const double *__restrict__ vals, int n, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const double a = vals[e];
+        const double2 x = X[(int64_t)c * n + col_idx[e]];
+        s.x = fma(a, x.x, s.x);
+        s.y = fma(a, x.y, s.y);
+    }
+    Y[(int64_t)c * n + i] = s;
+}
+
+// ==========================================================================
+// orchestration
+// ==========================================================================
+struct ProjWs {
+    double *norms;      // NL
+    double2 *G;         // NL x NL
+    double2 *Lm;        // NL x NL (pivoted Cholesky factor, first kc columns)
+    double *dbuf;       // 2 x NL
+    int32_t *state;     // 2 + NL
+    double2 *H, *H2;    // NL x NL each (Jacobi double buffer)
+    double2 *Y;         // NL x NL eigenvectors
+    double2 *Ysort;     // NL x NL
+    int32_t *order;     // NL
+    double *evals;      // NL
+    int32_t *conv;      // 1
+    double *acc;        // 2
+    double2 *W;         // NL x NL
+    double2 *Q1;        // n x NL
+    double2 *Ytmp;      // n x NL (A_q Q)
+    double2 *gws;       // GEMM workspace
+    size_t gws_elems;
+    double2 *C;         // NL x NL coefficients of the deflation
+    double2 *Qall;      // n x NL basis
+    double2 *P;         // RSRR_MAX_TERMS x NL x NL projected coefficients
+    char *end;
+};
+
+template <typename T> static T *carve(char *&p, size_t count) {
+    T *r = reinterpret_cast<T *>(p);
+    p += ((sizeof(T) * count + 255) / 256) * 256;
+    return r;
+}
+
+#define PK(expr, what)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (expr);                                         \
+        if (_e != cudaSuccess) return fail(RSRR_ECUDA, what, _e);        \
+    } while (0)
+
+// Jacobi on the k x k Hermitian matrix in ws.H (overwritten); eigenvalues
+// sorted descending into ws.evals, eigenvectors (same order) into ws.Ysort.
+static cudaError_t jacobi_eig(ProjWs &ws, int k, cudaStream_t s, int64_t *counter,
+                              int max_sweeps = 30) {
+    const int kp = k + (k & 1);
+    cudaError_t e;
+    e = cudaMemsetAsync(ws.conv, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    identity_kernel<<<grid1d((int64_t)k * k), 256, 0, s>>>(ws.Y, k);
+    double2 *a = ws.H, *b = ws.H2;
+    const int np = kp / 2;
+    const int64_t work = (int64_t)np * np + (int64_t)k * np;
+    const double tol2 = 1e-30;  // off(H) <= 1e-15 * ||diag(H)||
+    if (k > 1) {
+        for (int sw = 0; sw < max_sweeps; ++sw) {
+            for (int r = 0; r < kp - 1; ++r) {
+                jacobi_round_kernel<<<grid1d(work), 256, 0, s>>>(a, b, ws.Y, k, kp, r, ws.conv);
+                std::swap(a, b);
+            }
+            jacobi_check_kernel<<<1, 256, 0, s>>>(a, k, tol2, ws.conv, ws.acc);
+        }
+        *counter += (int64_t)max_sweeps * kp;
+    }
+    *counter += 3;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a != ws.H) {
+        e = cudaMemcpyAsync(ws.H, a, sizeof(double2) * k * k, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    sort_desc_kernel<<<1, 256, 0, s>>>(ws.H, k, ws.order, ws.evals);
+    gather_cols_kernel<<<grid1d((int64_t)k * k), 256, 0, s>>>(ws.Ysort, ws.Y, k, k, ws.order);
+    return cudaGetLastError();
+}
+
+// Scale the columns of X into Sn: Sn(:, c) = X(:, c) / d[c]
+__global__ void scale_cols_kernel(double2 *__restrict__ Sn, const double2 *__restrict__ X,
+                                  const double *__restrict__ d, int64_t n, int ncol) {
+    const int64_t total = n * ncol;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double s = 1.0 / d[q / n];
+        Sn[q] = make_double2(X[q].x * s, X[q].y * s);
+    }
+}
+
+__global__ void max_diag_kernel(double *__restrict__ out, const double2 *__restrict__ G, int n) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, G[(int64_t)i * n + i].x);
+    for (int off = 16; off; off >>= 1) m = fmax(m, shfl_down(m, off));
+    __shared__ double w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, w[q]);
+        out[0] = r;
+    }
+}
+
+// Workspace layout of the projection stage (carved from one allocation).
+static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n) {
+    const size_t NL2 = (size_t)NL * NL;
+    ws.norms = carve<double>(cp, NL);
+    ws.G = carve<double2>(cp, NL2);
+    ws.Lm = carve<double2>(cp, NL2);
+    ws.dbuf = carve<double>(cp, 2 * NL);
+    ws.state = carve<int32_t>(cp, 2 + NL);
+    ws.H = carve<double2>(cp, NL2);
+    ws.H2 = carve<double2>(cp, NL2);
+    ws.Y = carve<double2>(cp, NL2);
+    ws.Ysort = carve<double2>(cp, NL2);
+    ws.order = carve<int32_t>(cp, NL);
+    ws.evals = carve<double>(cp, NL);
+    ws.conv = carve<int32_t>(cp, 4);
+    ws.acc = carve<double>(cp, 2);
+    ws.W = carve<double2>(cp, NL2);
+    ws.C = carve<double2>(cp, NL2);
+    ws.Q1 = carve<double2>(cp, (size_t)n * NL);
+    ws.Ytmp = carve<double2>(cp, (size_t)n * NL);
+    ws.gws_elems = std::max<size_t>(NL2 * 4, (size_t)8 << 20);
+    ws.gws = carve<double2>(cp, ws.gws_elems);
+    ws.Qall = carve<double2>(cp, (size_t)n * NL);
+    ws.P = carve<double2>(cp, (size_t)RSRR_MAX_TERMS * NL2);
+    ws.end = cp;
+}
+
+static size_t ws_bytes(int NL, int64_t n) {
+    ProjWs ws;
+    char *base = reinterpret_cast<char *>((uintptr_t)0);
+    carve_ws(base, ws, NL, n);
+    return (size_t)(ws.end - base);
+}
+
+// Orthonormal basis of the dominant singular subspace of Sn = X D^{-1}:
+// deflated multi-level Gram.  Level l works on the remainder R_l (R_0 = Sn):
+//   G_l = R_l^H R_l; pivoted Cholesky G_l ~ B B^H stopped when the largest
+//   remaining diagonal is <= max(lev_tol^2 * maxdiag(G_l), floor^2 sigma_1^2)
+//   (lev_tol = 1e-6: the kept directions sit far above the Gram's rounding);
+//   B^H B = Y Lambda Y^H (Jacobi); new directions R_l B Y Lambda^{-1} for the
+//   eigenvalues well above the level's threshold, orthogonalised twice
+//   against the basis so far and once more within the block (Jacobi on its
+//   Gram); then R_{l+1} = R_l - Qall Qall^H R_l, twice.
+// Each level sees only directions far above its own rounding level, so the
+// levels together resolve singular values down to ~lev_tol^L of sigma_1.
+rsrr_status Handle::project(cudaStream_t s) {
+    const int NL = N * L;
+    const int64_t nn = n;
+    if (!proj_ws) {
+        const size_t bytes = ws_bytes(NL, nn);
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return fail(RSRR_ENOMEM, "projection work space", e);
+        allocations.push_back(p);
+        device_bytes += bytes;
+        proj_ws = p;
+        proj_ws_bytes = bytes;
+    }
+    ProjWs ws;
+    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, nn);
+    d_Q = ws.Qall;
+    d_P = ws.P;
+    Gemm gm;
+    gm.ws = ws.gws;
+    gm.ws_elems = ws.gws_elems;
+    gm.counter = &launches;
+    rsrr_status mst = mark(6, s);
+    if (mst != RSRR_OK) return mst;
+
+    // (A8) unit-norm columns: R_0 = X D^{-1}
+    colnorm_kernel<<<NL, 256, 0, s>>>(ws.norms, d_X, nn);
+    scale_cols_kernel<<<grid1d(nn * NL), 256, 0, s>>>(ws.Q1, d_X, ws.norms, nn, NL);
+    PK(cudaGetLastError(), "normalise");
+    launches += 2;
+    double2 *R = ws.Q1;
+    const double lev_tol = 1e-6;
+    const double floor_ = std::max(opts.delta, opts.delta_floor);
+    int kt = 0;            // columns of Qall so far
+    double s1sq = 0.0;     // sigma_1^2 of Sn (from level 0)
+    double smallest = 0.0; // smallest kept eigenvalue (for sigma_k)
+    kc = 0;
+    for (int lev = 0; lev < 6 && kt < NL; ++lev) {
+        // (A9) Gram of the remainder and its largest diagonal
+        PK(gm.run(NL, NL, (int)nn, true, R, nn, R, nn, ws.G, NL, s, true), "Gram");
+        max_diag_kernel<<<1, 256, 0, s>>>(ws.acc, ws.G, NL);
+        double maxd = 0.0;
+        PK(cudaMemcpyAsync(&maxd, ws.acc, sizeof(double), cudaMemcpyDeviceToHost, s), "maxdiag");
+        PK(cudaStreamSynchronize(s), "maxdiag sync");
+        launches += 1;
+        if (lev > 0 && !(maxd > floor_ * floor_ * s1sq)) break;
+        const double tau = std::max(lev_tol * lev_tol * maxd, floor_ * floor_ * s1sq);
+        PK(cudaMemsetAsync(ws.state, 0, sizeof(int32_t) * (2 + NL), s), "memset");
+        diag_real_kernel<<<(NL + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, NL);
+        for (int j = 0; j < NL; ++j)
+            pchol_step_kernel<<<(NL + 255) / 256, 256, 0, s>>>(
+                ws.G, NL, ws.Lm, ws.dbuf + (j & 1) * NL, ws.dbuf + ((j + 1) & 1) * NL, j, tau,
+                ws.state);
+        PK(cudaGetLastError(), "pivoted Cholesky");
+        launches += 1 + NL;
+        int32_t st2[2];
+        PK(cudaMemcpyAsync(st2, ws.state, sizeof st2, cudaMemcpyDeviceToHost, s), "kc");
+        PK(cudaStreamSynchronize(s), "kc sync");
+        const int kcl = st2[0] ? st2[1] : NL;
+        if (kcl < 1) break;
+        kc += kcl;
+        // small Hermitian eigenproblem B^H B
+        PK(gm.run(kcl, kcl, NL, true, ws.Lm, NL, ws.Lm, NL, ws.H, kcl, s, true), "B^H B");
+        PK(jacobi_eig(ws, kcl, s, &launches), "Jacobi (B^H B)");
+        std::vector<double> ev(kcl);
+        PK(cudaMemcpyAsync(ev.data(), ws.evals, sizeof(double) * kcl, cudaMemcpyDeviceToHost, s), "evals");
+        PK(cudaStreamSynchronize(s), "evals sync");
+        if (lev == 0) s1sq = std::max(ev[0], 0.0);
+        const double keep_tol = std::max(1e-2 * tau, floor_ * floor_ * s1sq);
+        int kb = 0;
+        for (int j = 0; j < kcl; ++j)
+            if (ev[j] > keep_tol) kb = j + 1;
+        if (kb < 1) break;
+        smallest = ev[kb - 1];
+        if (kt + kb > NL) kb = NL - kt;
+        // new directions Qb = R B Y_kb Lambda_kb^{-1} (n x kb) into Ytmp
+        PK(gm.run(NL, kb, kcl, false, ws.Lm, NL, ws.Ysort, kcl, ws.W, NL, s), "B Y");
+        scale_rc_kernel<<<grid1d((int64_t)NL * kb), 256, 0, s>>>(ws.W, NL, NL, kb, nullptr,
+                                                                 ws.evals, false, false);
+        launches += 1;
+        PK(gm.run((int)nn, kb, NL, false, R, nn, ws.W, NL, ws.Ytmp, nn, s), "R W");
+        // orthogonalise against the basis so far, twice
+        for (int pass = 0; pass < 2 && kt > 0; ++pass) {
+            PK(gm.run(kt, kb, (int)nn, true, ws.Qall, nn, ws.Ytmp, nn, ws.C, kt, s), "Q^H Qb");
+            PK(gm.run((int)nn, kb, kt, false, ws.Qall, nn, ws.C, kt, ws.Ytmp, nn, s, false, -1.0, 1.0),
+               "Qb -= Q C");
+        }
+        // within the block: Qb^H Qb = Z M Z^H, Qall(:, kt:kt+kb2) = Qb Z M^{-1/2}
+        PK(gm.run(kb, kb, (int)nn, true, ws.Ytmp, nn, ws.Ytmp, nn, ws.H, kb, s, true), "Qb^H Qb");
+        PK(jacobi_eig(ws, kb, s, &launches), "Jacobi (Qb^H Qb)");
+        std::vector<double> mu(kb);
+        PK(cudaMemcpyAsync(mu.data(), ws.evals, sizeof(double) * kb, cudaMemcpyDeviceToHost, s), "mu");
+        PK(cudaStreamSynchronize(s), "mu sync");
+        int kb2 = 0;
+        for (int j = 0; j < kb; ++j)
+            if (mu[j] > 1e-10 * mu[0]) kb2 = j + 1;
+        if (kb2 < 1) break;
+        scale_rc_kernel<<<grid1d((int64_t)kb * kb2), 256, 0, s>>>(ws.Ysort, kb, kb, kb2, nullptr,
+                                                                  ws.evals, false, true);
+        launches += 1;
+        PK(gm.run((int)nn, kb2, kb, false, ws.Ytmp, nn, ws.Ysort, kb, ws.Qall + (size_t)kt * nn, nn, s),
+           "Qb Z");
+        kt += kb2;
+        // deflate the remainder, twice
+        for (int pass = 0; pass < 2; ++pass) {
+            PK(gm.run(kt, NL, (int)nn, true, ws.Qall, nn, R, nn, ws.C, kt, s), "Q^H R");
+            PK(gm.run((int)nn, NL, kt, false, ws.Qall, nn, ws.C, kt, R, nn, s, false, -1.0, 1.0),
+               "R -= Q C");
+        }
+    }
+    if (kt < 1) return fail(RSRR_ESTATE, "rsrr_project: empty basis");
+    k = kt;
+    sigma1 = std::sqrt(s1sq);
+    sigmak = std::sqrt(std::max(smallest, 0.0));
+
+    // (A10) P_q = Q^H (A_q Q)
+    for (int q = 0; q < m; ++q) {
+        dim3 grid((unsigned)((nn + 127) / 128), k);
+        spmm_kernel<<<grid, 128, 0, s>>>(ws.Ytmp, d_Q, d_row_ptr, d_col_idx, d_vals + (size_t)q * nnz,
+                                         (int)nn, k);
+        PK(cudaGetLastError(), "SpMM");
+        PK(gm.run(k, k, (int)nn, true, d_Q, nn, ws.Ytmp, nn, d_P + (size_t)q * k * k, k, s), "Q^H A Q");
+        launches += 1;
+    }
+    mst = mark(7, s);
+    if (mst != RSRR_OK) return mst;
+    timed_project = opts.timing != 0;
+    return RSRR_OK;
+}
+
+}  // namespace rsrr
+
+using rsrr::Handle;
+
+extern "C" {
+
+rsrr_status rsrr_project(rsrr_t *hh, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return RSRR_EINVAL;
+    if (!h->sampled) return h->fail(RSRR_ESTATE, "rsrr_project: no rsrr_sample yet");
+    rsrr_status st = h->project((cudaStream_t)stream);
+    h->projected = (st == RSRR_OK);
+    return st;
+}
+
+rsrr_status rsrr_get_Q(rsrr_t *hh, rsrr_c128 *dst, int32_t dst_on_device, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !dst) return RSRR_EINVAL;
+    if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_get_Q: no rsrr_project yet");
+    const size_t bytes = sizeof(double2) * (size_t)h->n * h->k;
+    cudaError_t e;
+    if (dst_on_device) {
+        e = cudaMemcpyAsync(dst, h->d_Q, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    } else {
+        e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaMemcpy(dst, h->d_Q, bytes, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return h->fail(RSRR_ECUDA, "rsrr_get_Q", e);
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_get_projected(rsrr_t *hh, rsrr_c128 *dst, int32_t dst_on_device, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !dst) return RSRR_EINVAL;
+    if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_get_projected: no rsrr_project yet");
+    const size_t bytes = sizeof(double2) * (size_t)h->m * h->k * h->k;
+    cudaError_t e;
+    if (dst_on_device) {
+        e = cudaMemcpyAsync(dst, h->d_P, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    } else {
+        e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaMemcpy(dst, h->d_P, bytes, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return h->fail(RSRR_ECUDA, "rsrr_get_projected", e);
+    return RSRR_OK;
+}
+
+}  // extern "C"
+
+// ==========================================================================
+// rsrr_solve: SS-FULL on the host, v = Q g and residuals on the GPU
+// ==========================================================================
+#include "ssfull_host.h"
+
+namespace rsrr {
+
+// rr[c] = ||T(lam_c) v_c||^2, vv[c] = ||v_c||^2 (FP64, CSR, coefficients per pair)
+__global__ void eig_residual_kernel(const double2 *__restrict__ V, const double2 *__restrict__ coef,
+                                    const int32_t *__restrict__ row_ptr,
+                                    const int32_t *__restrict__ col_idx,
+                                    const double *__restrict__ vals, int64_t nnz, int m, int n,
+                                    double *__restrict__ rr, double *__restrict__ vv) {
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double r2 = 0.0, v2 = 0.0;
+    if (i < n) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            double2 a = make_double2(0.0, 0.0);
+            for (int q = 0; q < m; ++q) {
+                const double v = vals[(int64_t)q * nnz + e];
+                a.x = fma(coef[c * m + q].x, v, a.x);
+                a.y = fma(coef[c * m + q].y, v, a.y);
+            }
+            s = cfma(s, a, V[(int64_t)c * n + col_idx[e]]);
+        }
+        r2 = s.x * s.x + s.y * s.y;
+        const double2 x = V[(int64_t)c * n + i];
+        v2 = x.x * x.x + x.y * x.y;
+    }
+    for (int off = 16; off; off >>= 1) {
+        r2 += shfl_down(r2, off);
+        v2 += shfl_down(v2, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(rr + c, r2);
+        atomicAdd(vv + c, v2);
+    }
+}
+
+rsrr_status Handle::solve(rsrr_result *out) {
+    using cplx = std::complex<double>;
+    cudaStream_t s = 0;
+    PK(cudaDeviceSynchronize(), "solve sync");
+
+    // projected coefficients to the host
+    std::vector<std::vector<cplx>> P(m, std::vector<cplx>((size_t)k * k));
+    for (int q = 0; q < m; ++q)
+        PK(cudaMemcpy(P[q].data(), d_P + (size_t)q * k * k, sizeof(double2) * k * k,
+                      cudaMemcpyDeviceToHost), "P to host");
+    std::vector<cplx> lam, G;
+    int nbar = 0;
+    double gmax = 0.0;
+    auto f = [this](int i, cplx z) { return eval_fn_host(fn[i], z); };
+    const cplx gamma(region.center.re, region.center.im);
+    if (ss_full_host(P, k, f, m, gamma, region.a, region.b, opts.NQ, opts.KQ, opts.host_threads,
+                     lam, G, nbar, gmax) != 0)
+        return fail(RSRR_ESINGULAR, "rsrr_solve: projected T_Q singular at a quadrature node");
+    // v = Q g on the GPU
+    ProjWs ws;
+    const int NL = N * L;
+    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, n);
+    Gemm gm;
+    gm.ws = ws.gws;
+    gm.ws_elems = ws.gws_elems;
+    gm.counter = &launches;
+    // G (k x nbar), V = Q G (n x nbar), f_i(lam_c) and the residual sums in a
+    // buffer of their own (nbar may exceed the sample count)
+    const size_t gbytes = sizeof(double2) * (size_t)k * nbar;
+    const size_t vbytes = sizeof(double2) * (size_t)n * nbar;
+    const size_t cbytes = sizeof(double2) * (size_t)nbar * m;
+    void *buf = nullptr;
+    PK(cudaMalloc(&buf, gbytes + vbytes + cbytes + sizeof(double) * 2 * nbar), "solve buffers");
+    struct Free { void *p; ~Free() { cudaFree(p); } } guard{buf};
+    double2 *d_G = reinterpret_cast<double2 *>(buf);
+    double2 *d_V = reinterpret_cast<double2 *>(reinterpret_cast<char *>(buf) + gbytes);
+    double2 *d_cf = reinterpret_cast<double2 *>(reinterpret_cast<char *>(buf) + gbytes + vbytes);
+    double *d_rr = reinterpret_cast<double *>(reinterpret_cast<char *>(buf) + gbytes + vbytes + cbytes);
+    double *d_vv = d_rr + nbar;
+    PK(cudaMemcpy(d_G, G.data(), gbytes, cudaMemcpyHostToDevice), "G");
+    PK(gm.run((int)n, nbar, k, false, d_Q, n, d_G, k, d_V, n, s), "Q G");
+    std::vector<double2> cf((size_t)nbar * m);
+    for (int c = 0; c < nbar; ++c)
+        for (int q = 0; q < m; ++q) {
+            const cplx v = eval_fn_host(fn[q], lam[c]);
+            cf[(size_t)c * m + q] = make_double2(v.real(), v.imag());
+        }
+    PK(cudaMemcpy(d_cf, cf.data(), cbytes, cudaMemcpyHostToDevice), "coef");
+    PK(cudaMemset(d_rr, 0, sizeof(double) * 2 * nbar), "memset");
+    eig_residual_kernel<<<dim3((unsigned)((n + 255) / 256), nbar), 256>>>(
+        d_V, d_cf, d_row_ptr, d_col_idx, d_vals, nnz, m, (int)n, d_rr, d_vv);
+    PK(cudaGetLastError(), "eig residual");
+    launches += 1;
+    std::vector<double> rr(nbar), vv(nbar);
+    std::vector<cplx> V((size_t)n * nbar);
+    PK(cudaMemcpy(rr.data(), d_rr, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "rr");
+    PK(cudaMemcpy(vv.data(), d_vv, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "vv");
+    PK(cudaMemcpy(V.data(), d_V, sizeof(double2) * V.size(), cudaMemcpyDeviceToHost), "V");
+    // ||A_i||_1 (max column sum) on the host
+    std::vector<double> a1(m, 0.0);
+    for (int q = 0; q < m; ++q) {
+        std::vector<double> colsum(n, 0.0);
+        for (int64_t e = 0; e < nnz; ++e) colsum[h_col_idx[e]] += std::fabs(h_vals[(size_t)q * nnz + e]);
+        for (double v : colsum) a1[q] = std::max(a1[q], v);
+    }
+    struct Pair { cplx lam; double res; int c; };
+    std::vector<Pair> keep;
+    for (int c = 0; c < nbar; ++c) {
+        const double x = (lam[c].real() - region.center.re) / region.a;
+        const double y = (lam[c].imag() - region.center.im) / region.b;
+        if (!(x * x + y * y < 1.0)) continue;
+        double scale = 0.0;
+        for (int q = 0; q < m; ++q) scale += std::abs(eval_fn_host(fn[q], lam[c])) * a1[q];
+        const double res = std::sqrt(rr[c]) / (scale * std::sqrt(vv[c]));
+        if (!(res <= opts.res_tol)) continue;
+        keep.push_back({lam[c], res, c});
+    }
+    std::sort(keep.begin(), keep.end(), [](const Pair &a, const Pair &b) {
+        if (std::abs(a.lam) != std::abs(b.lam)) return std::abs(a.lam) < std::abs(b.lam);
+        return std::arg(a.lam) < std::arg(b.lam);
+    });
+    res_lam.resize(keep.size());
+    res_res.resize(keep.size());
+    res_V.resize((size_t)n * keep.size());
+    for (size_t t = 0; t < keep.size(); ++t) {
+        res_lam[t] = {keep[t].lam.real(), keep[t].lam.imag()};
+        res_res[t] = keep[t].res;
+        const double nv = std::sqrt(vv[keep[t].c]);
+        for (int64_t i = 0; i < n; ++i) {
+            const cplx v = V[(size_t)keep[t].c * n + i] / nv;
+            res_V[t * n + i] = {v.real(), v.imag()};
+        }
+    }
+    out->count = (int32_t)keep.size();
+    out->nbar = nbar;
+    out->gmax = gmax;
+    out->lam = res_lam.data();
+    out->res = res_res.data();
+    out->V = res_V.data();
+    return gmax >= opts.tol_gap ? RSRR_OK : RSRR_WGAP;
+}
+
+}  // namespace rsrr
+
 extern "C" rsrr_status rsrr_solve(rsrr_t *hh, rsrr_result *out) {
-    (void)out;
     rsrr::Handle *h = reinterpret_cast<rsrr::Handle *>(hh);
-    if (!h) return RSRR_EINVAL;
-    return h->fail(RSRR_ESTATE, "rsrr_solve: not available");
+    if (!h || !out) return RSRR_EINVAL;
+    if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_solve: no rsrr_project yet");
+    return h->solve(out);
 }
-extern "C" rsrr_status rsrr_get_Q(rsrr_t *hh, rsrr_c128 *, int32_t, void *) { return RSRR_ESTATE; }
-extern "C" rsrr_status rsrr_get_projected(rsrr_t *hh, rsrr_c128 *, int32_t, void *) { return RSRR_ESTATE; }

@@ -58,6 +58,10 @@ struct Handle {
     int stat_sweeps = 0, stat_converged = 0, stat_singular = -1;
     double stat_max_eta = 0.0;
     std::string err;
+    int64_t launches = 0;
+    cudaEvent_t events[8] = {};
+    bool timed_sample = false, timed_project = false;
+    double stage_ms[6] = {};
 
     ~Handle();
     rsrr_status fail(rsrr_status st, const char *what, cudaError_t e = cudaSuccess);
@@ -65,6 +69,7 @@ struct Handle {
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);
     rsrr_status sample(cudaStream_t s);
     rsrr_status read_outcome();
+    rsrr_status mark(int i, cudaStream_t s);
     rsrr_status project(cudaStream_t s);
     rsrr_status solve(rsrr_result *out);
 };

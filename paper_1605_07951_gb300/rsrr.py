@@ -58,7 +58,7 @@ class rsrr_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_refine", C.c_int32), ("eta_tol", C.c_double),
                 ("delta", C.c_double), ("delta_floor", C.c_double), ("tol_gap", C.c_double),
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
-                ("host_threads", C.c_int32), ("reserved", C.c_int32)]
+                ("host_threads", C.c_int32), ("timing", C.c_int32)]
 
 
 class rsrr_stats(C.Structure):
@@ -66,7 +66,8 @@ class rsrr_stats(C.Structure):
                 ("kl", C.c_int32), ("ku", C.c_int32), ("refine_sweeps", C.c_int32),
                 ("converged", C.c_int32), ("singular_point", C.c_int32), ("k", C.c_int32),
                 ("kc", C.c_int32), ("max_eta", C.c_double), ("sigma1", C.c_double),
-                ("sigmak", C.c_double), ("device_bytes", C.c_size_t)]
+                ("sigmak", C.c_double), ("device_bytes", C.c_size_t),
+                ("launches", C.c_int64), ("stage_ms", C.c_double * 6)]
 
 
 class rsrr_result(C.Structure):
@@ -239,7 +240,9 @@ class Solver:
     def stats(self) -> dict:
         s = rsrr_stats()
         self._check(rsrr_get_stats(self.h, C.byref(s)))
-        return {f: getattr(s, f) for f, _ in rsrr_stats._fields_}
+        d = {f: getattr(s, f) for f, _ in rsrr_stats._fields_}
+        d["stage_ms"] = list(s.stage_ms)
+        return d
 
     def Q(self, out=None, stream=None):
         k = self.stats()["k"]
