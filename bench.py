@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "grid5pt_rational_n40000_bw200_N64_L32"
 METRIC = "resolvent columns/s at 1e-10 rel. residual (mixed vs FP64); RSRR p50/p99 latency"
 UNIT = "resolvent columns/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x FMA x max SM clock (GHz)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x FMA x max SM clock (THz)
 
 
 def parse():
