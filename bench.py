@@ -31,6 +31,10 @@ WORKLOAD = "grid5pt_rational_n40000_bw200_N64_L32"
 METRIC = "resolvent columns/s at 1e-10 rel. residual (mixed vs FP64); RSRR p50/p99 latency"
 UNIT = "resolvent columns/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x FMA x max SM clock (THz)
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (an FMA-chain probe measured 1.20 at 2.0 GHz)
+# band LU DRAM traffic per point and per stored band entry, from one ncu capture
+# at n = 4096, bandwidth 64 (961.8 MB for 64 points, 224 x 4096 entries each)
+LU_TRAFFIC_PER_ENTRY = 961.79e6 / (64 * 224 * 4096)
 
 
 def parse():
@@ -42,6 +46,7 @@ def parse():
     ap.add_argument("--g", type=int, default=200, help="grid side (n = g^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--sample-points", type=int, default=2,
                     help="sampling points of the oracle's bounded sample")
     return ap.parse_args()
@@ -145,6 +150,41 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def run_e2e(a, s, p, stats, stream, world):
+    """Same metric through the C ABI with host buffers: U copied from pinned
+    host memory and the projected matrices copied back, every step."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    from paper_1605_07951_gb300 import rsrr
+    cols = p.N * p.L
+    Uh = torch.from_numpy(np.ascontiguousarray(p.U.T)).pin_memory()  # column-major n x L
+    k = stats["k"]
+    Pout = torch.empty((p.m, k, k), dtype=torch.complex128).pin_memory()
+
+    def e2e_step():
+        st = rsrr.rsrr_set_probe(s.h, C.c_void_p(Uh.data_ptr()), 0, None)
+        assert st == 0
+        s.sample(stream)
+        s.project(stream)
+        kk = s.stats()["k"]
+        st = rsrr.rsrr_get_projected(s.h, C.c_void_p(Pout.data_ptr()), 0,
+                                     C.c_void_p(stream.cuda_stream))
+        assert st == 0 and kk == k
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / a.steps
+    e2e = {"value": cols * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(Uh.numel() * 16),
+           "d2h_bytes_per_step": int(p.m * k * k * 16)}
+
+    return e2e
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(a, rank, world, local):
     import numpy as np
@@ -177,7 +217,7 @@ def run_ours(a, rank, world, local):
 
     clocks = ClockSampler(local)
     clocks.start()
-    lu_ms, sample_ms, project_ms = [], [], []
+    lu_ms, sample_ms, project_ms, gemm_ms, gemm_flops = [], [], [], [], []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -192,6 +232,8 @@ def run_ours(a, rank, world, local):
         lu_ms.append(sti["stage_ms"][1])
         sample_ms.append(sum(sti["stage_ms"][:5]))
         project_ms.append(sti["stage_ms"][5])
+        gemm_ms.append(sti["gemm_ms"])
+        gemm_flops.append(sti["gemm_flops"])
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -209,44 +251,36 @@ def run_ours(a, rank, world, local):
     value = cols * world / (ms / 1e3)
 
     # e2e: U from pinned host memory, projected matrices back to the host, per step
-    Uh = torch.from_numpy(np.ascontiguousarray(p.U.T)).pin_memory()  # rows = columns of U
-    k = stats["k"]
-    Pout = torch.empty((p.m, k, k), dtype=torch.complex128).pin_memory()
-    import ctypes as C
-
-    def e2e_step():
-        st = rsrr.rsrr_set_probe(s.h, C.c_void_p(Uh.data_ptr()), 0, None)
-        assert st == 0
-        s.sample(stream)
-        s.project(stream)
-        kk = s.stats()["k"]
-        st = rsrr.rsrr_get_projected(s.h, C.c_void_p(Pout.data_ptr()), 0,
-                                     C.c_void_p(stream.cuda_stream))
-        assert st == 0 and kk == k
-    e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / a.steps
-    e2e = {"value": cols * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(Uh.numel() * 16),
-           "d2h_bytes_per_step": int(p.m * k * k * 16)}
-
-    # roofline of the dominant kernel (complex64 band LU, FP32 FMA pipe)
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(a, s, p, stats, stream, world)
+    fp64 = None
+    # roofline of the dominant kernel: the FP64 GEMMs of rsrr_project (about
+    # three quarters of a step in the ncu launch list); their algorithmic
+    # flops and event-timed device time come from the library per step
+    g_ach = statistics.mean(gemm_flops) / (statistics.mean(gemm_ms) / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "zgemm_kernel (FP64 complex GEMMs of rsrr_project)",
+            "achieved": g_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": g_ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "algorithmic_flop_per_step": statistics.mean(gemm_flops),
+            "gemm_ms_per_step": statistics.mean(gemm_ms),
+            "peak_note": "GB300 nominal FP64 (recipe); FMA-chain probe measured 1.20 TFLOP/s; "
+                         "traffic null: the GEMMs of a step have many shapes"}
+    # secondary: the band LU of rsrr_sample (FP32 FMA pipe)
     n, kl, ku = p.n, stats["kl"], stats["ku"]
     flop_per_point = 8.0 * sum(min(kl, n - 1 - j) * min(kl + ku, n - 1 - j) for j in range(n))
     lu_flops = flop_per_point * p.N
     lu_avg = statistics.mean(lu_ms)
     achieved = lu_flops / (lu_avg / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": "band_lu_kernel<float2> (complex64 FMA, all 64 points)",
-            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "algorithmic_flop_per_launch": lu_flops, "avg_launch_ms": lu_avg,
-            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    ldab = 2 * kl + ku + 32
+    roof_lu = {"bound": "alu", "kernel": "band_lu_kernel<float2> (complex64, one CTA per point)",
+               "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": achieved / FP32_PEAK_TFLOPS,
+               "traffic": LU_TRAFFIC_PER_ENTRY * ldab * n * p.N,
+               "algorithmic_flop_per_launch": lu_flops, "avg_launch_ms": lu_avg,
+               "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; traffic "
+                            "scaled from an ncu capture at n=4096 by stored band entries"}
 
-    fp64 = None
     if not a.no_fp64:
         s64 = rsrr.Solver(p, rsrr.default_opts(precision=rsrr.RSRR_PREC_FP64, timing=1))
         s64.sample(stream)
@@ -275,9 +309,11 @@ def run_ours(a, rank, world, local):
         "sample_only": {"value": cols / (statistics.mean(sample_ms) / 1e3),
                         "ms": statistics.mean(sample_ms), "stage_ms": stats["stage_ms"][:5],
                         "refine_sweeps": stats["refine_sweeps"], "max_eta": stats["max_eta"]},
-        "project_ms": statistics.mean(project_ms), "rank_k": k, "pivoted_cholesky_kc": stats["kc"],
+        "project_ms": statistics.mean(project_ms), "rank_k": stats["k"],
+        "pivoted_cholesky_kc": stats["kc"],
         "fp64_plain_path": fp64,
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roof, "roofline_band_lu": roof_lu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk,
     }
     s.close()
     if rank == 0 and not a.no_cpu_baseline:

@@ -165,6 +165,10 @@ typedef struct {
      * stages: [0] assembly + ||T||, [1] band LU, [2] first solve, [3] refinement
      * sweeps, [4] final backward errors, [5] rsrr_project */
     double stage_ms[6];
+    /* with opts.timing, for the last rsrr_project: algorithmic flops of its
+     * FP64 GEMMs (8 per complex multiply-add, unique entries only for the
+     * Hermitian products) and their summed device time */
+    double gemm_flops, gemm_ms;
 } rsrr_stats;
 
 /* Result of rsrr_solve.  Arrays are host memory owned by the handle, valid

@@ -64,6 +64,20 @@ Handle::~Handle() {
     for (void *p : allocations) cudaFree(p);
     for (auto &e : events)
         if (e) cudaEventDestroy(e);
+    for (auto &e : gemm_events)
+        if (e) cudaEventDestroy(e);
+}
+
+// next event of the GEMM timing pool (grown on demand)
+cudaError_t Handle::gemm_event(cudaEvent_t *out) {
+    if (gemm_events_used == (int)gemm_events.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        gemm_events.push_back(e);
+    }
+    *out = gemm_events[gemm_events_used++];
+    return cudaSuccess;
 }
 
 }  // namespace rsrr
@@ -292,6 +306,16 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
         h->stage_ms[5] = t;
         h->timed_project = false;
     }
+    if (h->gemm_timed) {
+        double tot = 0.0;
+        for (int i = 0; i + 1 < h->gemm_events_used; i += 2) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, h->gemm_events[i], h->gemm_events[i + 1]), "event time");
+            tot += t;
+        }
+        h->gemm_ms = tot;
+        h->gemm_timed = false;
+    }
     memset(out, 0, sizeof *out);
     out->n = h->n; out->N = h->N; out->L = h->L; out->m = h->m;
     out->kl = h->kl; out->ku = h->ku;
@@ -306,6 +330,8 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
     out->device_bytes = h->device_bytes;
     out->launches = h->launches;
     for (int i = 0; i < 6; ++i) out->stage_ms[i] = h->stage_ms[i];
+    out->gemm_flops = h->gemm_flops;
+    out->gemm_ms = h->gemm_ms;
     return RSRR_OK;
 }
 
@@ -351,10 +377,14 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     const size_t band = (size_t)geom.ldab * n * N;
     if (opts.precision == RSRR_PREC_MIXED) {
         CK(alloc(&d_ab32, band), "alloc band factors (complex64)");
+        CK(alloc(&d_dinv32, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
+           "alloc block inverses");
         CK(alloc(&d_R, nL * N), "alloc residual");
         CK(alloc(&d_D, nL * N), "alloc correction");
     } else {
         CK(alloc(&d_ab64, band), "alloc band factors (complex128)");
+        CK(alloc(&d_dinv64, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
+           "alloc block inverses");
     }
     CK(cudaMemcpy(d_row_ptr, h_row_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "upload");
     CK(cudaMemcpy(d_col_idx, h_col_idx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
@@ -413,10 +443,10 @@ rsrr_status Handle::sample(cudaStream_t s) {
     if (opts.precision == RSRR_PREC_MIXED) {
         CK(launch_assemble<float2>(d_ab32, geom, dp, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c64(d_ab32, d_piv, d_info, geom, N, nn, s), "band LU");
+        CK(launch_band_lu_c64(d_ab32, d_piv, d_info, d_dinv32, geom, N, nn, s), "band LU");
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
-        CK(launch_band_solve_c64(d_ab32, d_piv, d_D, geom, N, nn, L, nullptr, s), "band solve");
+        CK(launch_band_solve_c64(d_ab32, d_piv, d_dinv32, d_D, geom, N, nn, L, nullptr, s), "band solve");
         CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
         CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
@@ -426,17 +456,17 @@ rsrr_status Handle::sample(cudaStream_t s) {
             CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
                           d_sweep_flags + it, d_done, s), "eta");
             CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
-            CK(launch_band_solve_c64(d_ab32, d_piv, d_D, geom, N, nn, L, d_done, s), "band solve");
+            CK(launch_band_solve_c64(d_ab32, d_piv, d_dinv32, d_D, geom, N, nn, L, d_done, s), "band solve");
             CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
             launches += 5;
         }
     } else {
         CK(launch_assemble<double2>(d_ab64, geom, dp, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c128(d_ab64, d_piv, d_info, geom, N, nn, s), "band LU");
+        CK(launch_band_lu_c128(d_ab64, d_piv, d_info, d_dinv64, geom, N, nn, s), "band LU");
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
-        CK(launch_band_solve_c128(d_ab64, d_piv, d_X, geom, N, nn, L, nullptr, s), "band solve");
+        CK(launch_band_solve_c128(d_ab64, d_piv, d_dinv64, d_X, geom, N, nn, L, nullptr, s), "band solve");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         launches += 4;  // assemble, LU, probe, solve
     }

@@ -13,6 +13,8 @@
 // multipliers that later row interchanges inside the same NB-column block
 // move down (pivoting is applied dense-style within a block).  The solve
 // walks the same blocks, so the factor and the solve agree on NB.
+#include <algorithm>
+
 #include "common.cuh"
 #include "rsrr_internal.h"
 
@@ -94,115 +96,186 @@ __global__ void tnorm_kernel(double *__restrict__ tnorm, const double2 *__restri
 
 // --------------------------------------------------------------------------
 // Blocked solve with the factors of band_lu_kernel, one CTA per (point,
-// chunk of LC right-hand sides), B overwritten with the solution.
-// Forward: per NB block, the block's interchanges then unit-lower
-// elimination over the block rows (rows j0..j0+pr-1 live in a shared-memory
-// window).  Backward: column-oriented back substitution with the upper band
-// (bandwidth kl+ku), rows [c-KV, c] in a shared-memory window.
-// Points with skip[pt] != 0 are left untouched.
+// chunk of LC right-hand sides); B is overwritten with the solution.
+// Rows live in a circular shared-memory window W[slot][LC] (row major, so
+// a thread reads the LC values of one row as broadcast vector loads).
+// Forward, per NB block (rows j0..j0+pr-1): gather the block's row
+// permutation into G, y = L11^{-1} G_top, then G_below - L21 y with L21
+// staged through shared memory (lane = row, each warp a row group and half
+// of the columns, register accumulators).
+// Backward, per block from the end: t = y_block - U12 x_next with U12 staged
+// in column chunks; the K dimension (columns of U12) is split across warps,
+// each warp accumulates a full NB x LC tile in registers (lane = row), and the
+// partial tiles are summed through shared memory; then x = U11^{-1} t.
+// The diagonal-block inverses come from the factorisation.  Points with
+// skip[pt] != 0 are left untouched.
 // --------------------------------------------------------------------------
 constexpr int SV_THREADS = 512;
+constexpr int SV_WARPS = SV_THREADS / 32;
+constexpr int SV_FCH = 256;  // forward: rows of L21 per staged chunk
+constexpr int SV_BCH = 128;  // backward: columns of U12 per staged chunk
 
 template <typename C, int NB, int LC>
 __global__ void __launch_bounds__(SV_THREADS, 1)
 band_solve_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ piv_all,
-                  C *__restrict__ B_all, int n, int kl, int ku, int ldab, int L,
-                  const int32_t *__restrict__ skip) {
+                  const C *__restrict__ dinv_all, C *__restrict__ B_all, int n, int kl, int ku,
+                  int ldab, int L, const int32_t *__restrict__ skip) {
+    static_assert(NB <= 32, "one lane per block row");
+    constexpr int HC = LC / 2;  // columns per warp in the forward update
     const int pt = blockIdx.y;
     if (skip && skip[pt]) return;
     const int col0 = blockIdx.x * LC;
     const int ncol = min(LC, L - col0);
+    const int nblk = (n + NB - 1) / NB;
     const C *ab = ab_all + (size_t)pt * ldab * n;
     const int32_t *piv = piv_all + (size_t)pt * n;
+    const C *dinv = dinv_all + (size_t)pt * nblk * 2 * NB * NB;
     C *B = B_all + (size_t)pt * L * n + (size_t)col0 * n;
     const int KV = kl + ku;
-    const int tid = threadIdx.x;
+    const int WR = KV + NB;  // >= kl + NB
+    const int PRM = NB + kl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *W = reinterpret_cast<C *>(smem_raw);  // [WR][LC] circular window, row-major by slot
-    const int WF = kl + NB;                  // forward window rows
-    const int WB = KV + NB;                  // backward window rows
-    const int WR = WF > WB ? WF : WB;
+    C *W = reinterpret_cast<C *>(smem_raw);  // [WR][LC]
+    C *G = W + (size_t)WR * LC;              // forward [PRM][LC]; backward partials [SV_WARPS][NB][LC]
+    const int GSZ = max(PRM * LC, SV_WARPS * NB * LC);
+    C *St = G + GSZ;                         // [NB][SV_FCH] fwd or [SV_BCH][NB] bwd
+    C *D = St + NB * SV_FCH;                 // [NB][NB]
+    C *Yb = D + NB * NB;                     // [NB][LC]
+    int *perm = reinterpret_cast<int *>(Yb + NB * LC);  // [PRM]
 
-    // ---------------- forward
-    int loaded = 0;  // rows [.., loaded) are in the window
+    // ---------------- forward: y = L^{-1} P b, block by block
+    int loaded = 0;
     for (int j0 = 0; j0 < n; j0 += NB) {
         const int jb = min(NB, n - j0);
         const int pr = min(n - j0, jb + kl);
         const int need = j0 + pr;
-        for (int o = tid; o < (need - loaded) * LC; o += SV_THREADS) {
-            const int i = loaded + o / LC, col = o % LC;
+        const int nl = need - loaded;
+        for (int o = tid; o < nl * LC; o += SV_THREADS) {
+            const int r = o % nl, col = o / nl;
+            const int i = loaded + r;
             W[(i % WR) * LC + col] = col < ncol ? B[(size_t)col * n + i] : czero<C>();
         }
         loaded = max(loaded, need);
+        for (int r = tid; r < pr; r += SV_THREADS) perm[r] = r;
+        for (int q = tid; q < NB * NB; q += SV_THREADS) D[q] = dinv[(size_t)(j0 / NB) * 2 * NB * NB + q];
         __syncthreads();
-        if (tid < ncol) {
+        if (tid == 0) {
             for (int cc = 0; cc < jb; ++cc) {
-                const int p = piv[j0 + cc];
-                if (p != j0 + cc) {
-                    C *a = W + ((j0 + cc) % WR) * LC + tid;
-                    C *b = W + (p % WR) * LC + tid;
-                    const C t = *a; *a = *b; *b = t;
-                }
+                const int p = piv[j0 + cc] - j0;
+                const int t = perm[cc]; perm[cc] = perm[p]; perm[p] = t;
             }
         }
         __syncthreads();
-        for (int cc = 0; cc < jb; ++cc) {
-            const int c = j0 + cc;
-            const int nrow = pr - cc - 1;  // rows c+1 .. j0+pr-1
-            for (int o = tid; o < nrow * LC; o += SV_THREADS) {
-                const int r = o % nrow, col = o / nrow;
-                const int i = c + 1 + r;
-                if (col < ncol) {
-                    const C l = ab[(size_t)c * ldab + KV + (i - c)];
-                    const C y = W[(c % WR) * LC + col];
-                    C *w = W + (i % WR) * LC + col;
-                    *w = cfms(*w, l, y);
+        for (int o = tid; o < pr * LC; o += SV_THREADS) {
+            const int r = o / LC, col = o % LC;
+            G[r * LC + col] = W[((j0 + perm[r]) % WR) * LC + col];
+        }
+        __syncthreads();
+        // y = L11^{-1} G_top  (thread = (row, column))
+        for (int o = tid; o < NB * LC; o += SV_THREADS) {
+            const int r = o / LC, col = o % LC;
+            C y = czero<C>();
+            if (r < jb) {
+                for (int t = 0; t < jb; ++t) y = cfma(y, D[t * NB + r], G[t * LC + col]);
+                W[((j0 + r) % WR) * LC + col] = y;
+            }
+            Yb[r * LC + col] = y;
+        }
+        __syncthreads();
+        // rows below: G_below - L21 y
+        for (int r0 = jb; r0 < pr; r0 += SV_FCH) {
+            const int ch = min(SV_FCH, pr - r0);
+            for (int o = tid; o < ch * NB; o += SV_THREADS) {
+                const int rr = o % ch, t = o / ch;
+                C v = czero<C>();
+                if (t < jb) v = ab[(size_t)(j0 + t) * ldab + KV + (r0 + rr - t)];
+                St[t * SV_FCH + rr] = v;
+            }
+            __syncthreads();
+            // warp w: rows (w % (SV_WARPS/2))*32 + lane (+ multiples), columns half (w / 8)
+            const int hw = warp / (SV_WARPS / 2), rg = warp % (SV_WARPS / 2);
+            for (int rr = rg * 32 + lane; rr < ch; rr += (SV_WARPS / 2) * 32) {
+                C acc[HC];
+#pragma unroll
+                for (int c = 0; c < HC; ++c) acc[c] = G[(r0 + rr) * LC + hw * HC + c];
+#pragma unroll 4
+                for (int t = 0; t < NB; ++t) {
+                    const C l = St[t * SV_FCH + rr];
+#pragma unroll
+                    for (int c = 0; c < HC; ++c) acc[c] = cfms(acc[c], l, Yb[t * LC + hw * HC + c]);
                 }
+#pragma unroll
+                for (int c = 0; c < HC; ++c) W[((j0 + r0 + rr) % WR) * LC + hw * HC + c] = acc[c];
             }
             __syncthreads();
         }
         for (int o = tid; o < jb * LC; o += SV_THREADS) {
-            const int i = j0 + o / LC, col = o % LC;
-            if (col < ncol) B[(size_t)col * n + i] = W[(i % WR) * LC + col];
+            const int r = o % jb, col = o / jb;
+            if (col < ncol) B[(size_t)col * n + j0 + r] = W[((j0 + r) % WR) * LC + col];
         }
         __syncthreads();
     }
-    // ---------------- backward
-    int low = n;  // rows [low, ..) are in the window
-    for (int j1 = n; j1 > 0; j1 -= NB) {
-        const int j0 = max(0, j1 - NB);
-        const int need = max(0, j0 - KV);
-        for (int o = tid; o < (low - need) * LC; o += SV_THREADS) {
-            const int i = need + o / LC, col = o % LC;
-            W[(i % WR) * LC + col] = col < ncol ? B[(size_t)col * n + i] : czero<C>();
+    // ---------------- backward: x = U^{-1} y, blocks from the end
+    const int nlast = (nblk - 1) * NB;
+    for (int j0 = nlast; j0 >= 0; j0 -= NB) {
+        const int jb = min(NB, n - j0);
+        const int j1 = j0 + jb;
+        for (int o = tid; o < jb * LC; o += SV_THREADS) {
+            const int r = o % jb, col = o / jb;
+            W[((j0 + r) % WR) * LC + col] = col < ncol ? B[(size_t)col * n + j0 + r] : czero<C>();
         }
-        low = min(low, need);
-        __syncthreads();
-        for (int c = j1 - 1; c >= j0; --c) {
-            const C inv = crecip(ab[(size_t)c * ldab + KV]);
-            const int i0 = max(0, c - KV);
-            const int nrow = c - i0;
-            // x_c = w_c / u_cc is formed by every thread from the window
-            for (int o = tid; o < nrow * LC; o += SV_THREADS) {
-                const int r = o % nrow, col = o / nrow;
-                const int i = i0 + r;
-                if (col < ncol) {
-                    const C x = cmul(W[(c % WR) * LC + col], inv);
-                    const C u = ab[(size_t)c * ldab + KV + (i - c)];
-                    C *w = W + (i % WR) * LC + col;
-                    *w = cfms(*w, u, x);
+        for (int q = tid; q < NB * NB; q += SV_THREADS)
+            D[q] = dinv[(size_t)(j0 / NB) * 2 * NB * NB + NB * NB + q];
+        C acc[LC];
+#pragma unroll
+        for (int c = 0; c < LC; ++c) acc[c] = czero<C>();
+        const int cend = min(n, j1 + KV);
+        for (int c0 = j1; c0 < cend; c0 += SV_BCH) {
+            const int ch = min(SV_BCH, cend - c0);
+            __syncthreads();
+            for (int o = tid; o < ch * NB; o += SV_THREADS) {
+                const int r = o % NB, cc = o / NB;
+                C v = czero<C>();
+                const int d = j0 + r - (c0 + cc);
+                if (r < jb && d >= -KV) v = ab[(size_t)(c0 + cc) * ldab + KV + d];
+                St[cc * NB + r] = v;
+            }
+            __syncthreads();
+            if (lane < NB) {
+                for (int cc = warp; cc < ch; cc += SV_WARPS) {
+                    const C u = St[cc * NB + lane];
+                    const C *xr = W + ((c0 + cc) % WR) * LC;
+#pragma unroll
+                    for (int c = 0; c < LC; ++c) acc[c] = cfms(acc[c], u, xr[c]);
                 }
             }
-            __syncthreads();
-            if (tid < ncol) {
-                C *w = W + (c % WR) * LC + tid;
-                *w = cmul(*w, inv);
-            }
-            __syncthreads();
         }
-        for (int o = tid; o < (j1 - j0) * LC; o += SV_THREADS) {
-            const int i = j0 + o / LC, col = o % LC;
-            if (col < ncol) B[(size_t)col * n + i] = W[(i % WR) * LC + col];
+        __syncthreads();
+        if (lane < NB) {
+#pragma unroll
+            for (int c = 0; c < LC; ++c) G[(warp * NB + lane) * LC + c] = acc[c];
+        }
+        __syncthreads();
+        for (int o = tid; o < NB * LC; o += SV_THREADS) {
+            const int r = o / LC, col = o % LC;
+            C t = czero<C>();
+            if (r < jb) {
+                t = W[((j0 + r) % WR) * LC + col];
+                for (int w = 0; w < SV_WARPS; ++w) t = cadd(t, G[(w * NB + r) * LC + col]);
+            }
+            Yb[r * LC + col] = t;
+        }
+        __syncthreads();
+        for (int o = tid; o < NB * LC; o += SV_THREADS) {
+            const int r = o / LC, col = o % LC;
+            if (r < jb) {
+                C x = czero<C>();
+#pragma unroll 8
+                for (int q = 0; q < NB; ++q) x = cfma(x, D[q * NB + r], Yb[q * LC + col]);
+                W[((j0 + r) % WR) * LC + col] = x;
+                if (col < ncol) B[(size_t)col * n + j0 + r] = x;
+            }
         }
         __syncthreads();
     }
@@ -381,27 +454,41 @@ cudaError_t launch_tnorm(double *tnorm, const DevProblem &p, cudaStream_t s) {
 }
 
 template <typename C, int NB, int LC>
-static cudaError_t solve_dispatch(const C *ab, const int32_t *piv, C *B, const BandGeom &g, int N,
-                                  int n, int L, const int32_t *skip, cudaStream_t s) {
-    const int WR = max(g.kl + NB, g.kl + g.ku + NB);
-    const size_t smem = sizeof(C) * (size_t)WR * LC;
+static size_t solve_smem(const BandGeom &g) {
+    const int WR = g.kl + g.ku + NB, PRM = NB + g.kl;
+    const size_t gsz = std::max<size_t>((size_t)PRM * LC, (size_t)SV_WARPS * NB * LC);
+    return sizeof(C) * ((size_t)WR * LC + gsz + (size_t)NB * SV_FCH + NB * NB + NB * LC) +
+           sizeof(int) * PRM;
+}
+
+template <typename C, int NB, int LC>
+static cudaError_t solve_dispatch(const C *ab, const int32_t *piv, const C *dinv, C *B,
+                                  const BandGeom &g, int N, int n, int L, const int32_t *skip,
+                                  cudaStream_t s) {
+    const size_t smem = solve_smem<C, NB, LC>(g);
     cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<C, NB, LC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((L + LC - 1) / LC, N);
-    band_solve_kernel<C, NB, LC><<<grid, SV_THREADS, smem, s>>>(ab, piv, B, n, g.kl, g.ku, g.ldab,
-                                                                 L, skip);
+    band_solve_kernel<C, NB, LC><<<grid, SV_THREADS, smem, s>>>(ab, piv, dinv, B, n, g.kl, g.ku,
+                                                                 g.ldab, L, skip);
     return cudaGetLastError();
 }
 
-cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, float2 *B, const BandGeom &g,
-                                  int N, int n, int L, const int32_t *skip, cudaStream_t s) {
-    return solve_dispatch<float2, NB_C64, 16>(ab, piv, B, g, N, n, L, skip, s);
+// the right-hand-side chunk shrinks for wide bands so that the window fits
+cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const float2 *dinv,
+                                  float2 *B, const BandGeom &g, int N, int n, int L,
+                                  const int32_t *skip, cudaStream_t s) {
+    if (solve_smem<float2, NB_C64, 16>(g) <= 200 * 1024)
+        return solve_dispatch<float2, NB_C64, 16>(ab, piv, dinv, B, g, N, n, L, skip, s);
+    return solve_dispatch<float2, NB_C64, 8>(ab, piv, dinv, B, g, N, n, L, skip, s);
 }
-cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, double2 *B,
-                                   const BandGeom &g, int N, int n, int L, const int32_t *skip,
-                                   cudaStream_t s) {
-    return solve_dispatch<double2, NB_C128, 8>(ab, piv, B, g, N, n, L, skip, s);
+cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, const double2 *dinv,
+                                   double2 *B, const BandGeom &g, int N, int n, int L,
+                                   const int32_t *skip, cudaStream_t s) {
+    if (solve_smem<double2, NB_C128, 8>(g) <= 200 * 1024)
+        return solve_dispatch<double2, NB_C128, 8>(ab, piv, dinv, B, g, N, n, L, skip, s);
+    return solve_dispatch<double2, NB_C128, 4>(ab, piv, dinv, B, g, N, n, L, skip, s);
 }
 
 cudaError_t launch_residual(double2 *R, const double2 *X, const DevProblem &p, double *rmax,

@@ -28,20 +28,25 @@ constexpr int LU_WARPS = LU_THREADS / 32;
 template <typename C, int NB, int RA, int CB>
 __global__ void __launch_bounds__(LU_THREADS, 1)
 band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
-               int32_t *__restrict__ info_all, int n, int kl, int ku, int ldab) {
+               int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl, int ku,
+               int ldab) {
     using R = typename real_of<C>::type;
     constexpr int CW = LU_WARPS * CB;
     constexpr int PRA = NB + 32 * RA;  // allocated panel rows (>= NB + kl)
     const int pt = blockIdx.x;
     C *ab = ab_all + (size_t)pt * ldab * n;
     int32_t *piv = piv_all + (size_t)pt * n;
+    const int nblk = (n + NB - 1) / NB;
+    // per block: L11^{-1} then U11^{-1}, both NB x NB column major
+    C *dinv = dinv_all + (size_t)pt * nblk * 2 * NB * NB;
     const int KV = kl + ku;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *P = reinterpret_cast<C *>(smem_raw);  // [NB][PRA], column major
     C *Linv = P + NB * PRA;                  // [NB][NB+1], column major, padded
-    C *Ut = Linv + NB * (NB + 1);                 // [NB][CW]  (row t, col) at t*CW+col
+    C *Uinv = Linv + NB * (NB + 1);          // [NB][NB+1], column major, padded
+    C *Ut = Uinv + NB * (NB + 1);            // [NB][CW]  (row t, col) at t*CW+col
     C *U2 = Ut + NB * CW;                    // [NB][CW]
     C *prow = U2 + NB * CW;                  // [2][NB]
     C *drow = prow + 2 * NB;                 // [2][NB]
@@ -153,8 +158,30 @@ band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
                     Linv[j * (NB + 1) + i] = (i < j || i >= jb || j >= jb) ? czero<C>() : s;
                 }
             }
+        } else if (warp == 2) {
+            // column j = lane of U11^{-1}: x_j = 1/u_jj,
+            // x_i = -(sum_{i<t<=j} u_it x_t) / u_ii for i = j-1 .. 0
+            const int j = lane;
+            if (j < NB) {
+                for (int i = 0; i < NB; ++i) Uinv[j * (NB + 1) + i] = czero<C>();
+                if (j < jb) {
+                    Uinv[j * (NB + 1) + j] = crecip(P[j * PRA + j]);
+                    for (int i = j - 1; i >= 0; --i) {
+                        C s = czero<C>();
+                        for (int t = i + 1; t <= j; ++t) s = cfma(s, P[t * PRA + i], Uinv[j * (NB + 1) + t]);
+                        Uinv[j * (NB + 1) + i] = cmul(csub(czero<C>(), s), crecip(P[i * PRA + i]));
+                    }
+                }
+            }
         }
         __syncthreads();
+        {
+            C *dst = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
+            for (int q = tid; q < 2 * NB * NB; q += LU_THREADS) {
+                const int w = q / (NB * NB), e = q % (NB * NB), j = e / NB, i = e % NB;
+                dst[q] = (w == 0 ? Linv : Uinv)[j * (NB + 1) + i];
+            }
+        }
 
         // ---------------- trailing update
         const int c_beg = j0 + jb;
@@ -237,42 +264,43 @@ template <typename C, int NB, int RA, int CB>
 static size_t lu_smem_bytes() {
     constexpr int CW = LU_WARPS * CB;
     constexpr int PRA = NB + 32 * RA;
-    size_t b = sizeof(C) * ((size_t)NB * PRA + NB * (NB + 1) + 2 * NB * CW + 4 * NB);
+    size_t b = sizeof(C) * ((size_t)NB * PRA + 2 * NB * (NB + 1) + 2 * NB * CW + 4 * NB);
     b += sizeof(typename real_of<C>::type) * 2 * LU_WARPS + sizeof(int) * (2 * LU_WARPS + PRA + NB);
     return b;
 }
 
 template <typename C, int NB, int RA, int CB>
-static cudaError_t lu_dispatch(C *ab, int32_t *piv, int32_t *info, const BandGeom &g, int N,
-                               int n, cudaStream_t s) {
+static cudaError_t lu_dispatch(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g,
+                               int N, int n, cudaStream_t s) {
     const size_t smem = lu_smem_bytes<C, NB, RA, CB>();
     cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<C, NB, RA, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    band_lu_kernel<C, NB, RA, CB><<<N, LU_THREADS, smem, s>>>(ab, piv, info, n, g.kl, g.ku, g.ldab);
+    band_lu_kernel<C, NB, RA, CB><<<N, LU_THREADS, smem, s>>>(ab, piv, info, dinv, n, g.kl, g.ku,
+                                                               g.ldab);
     return cudaGetLastError();
 }
 
 template <typename C, int NB, int CB>
-static cudaError_t lu_by_kl(C *ab, int32_t *piv, int32_t *info, const BandGeom &g, int N, int n,
-                            cudaStream_t s) {
+static cudaError_t lu_by_kl(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g, int N,
+                            int n, cudaStream_t s) {
     const int kl = g.kl;
-    if (kl <= 32) return lu_dispatch<C, NB, 1, CB>(ab, piv, info, g, N, n, s);
-    if (kl <= 128) return lu_dispatch<C, NB, 4, CB>(ab, piv, info, g, N, n, s);
-    if (kl <= 224) return lu_dispatch<C, NB, 7, CB>(ab, piv, info, g, N, n, s);
-    return lu_dispatch<C, NB, 15, CB>(ab, piv, info, g, N, n, s);
+    if (kl <= 32) return lu_dispatch<C, NB, 1, CB>(ab, piv, info, dinv, g, N, n, s);
+    if (kl <= 128) return lu_dispatch<C, NB, 4, CB>(ab, piv, info, dinv, g, N, n, s);
+    if (kl <= 224) return lu_dispatch<C, NB, 7, CB>(ab, piv, info, dinv, g, N, n, s);
+    return lu_dispatch<C, NB, 15, CB>(ab, piv, info, dinv, g, N, n, s);
 }
 
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 64
-cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, const BandGeom &g, int N,
-                               int n, cudaStream_t s) {
-    return lu_by_kl<float2, NB_C64, 4>(ab, piv, info, g, N, n, s);
+cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *dinv,
+                               const BandGeom &g, int N, int n, cudaStream_t s) {
+    return lu_by_kl<float2, NB_C64, 4>(ab, piv, info, dinv, g, N, n, s);
 }
 #endif
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 128
-cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, const BandGeom &g,
-                                int N, int n, cudaStream_t s) {
-    return lu_by_kl<double2, NB_C128, 1>(ab, piv, info, g, N, n, s);
+cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, double2 *dinv,
+                                const BandGeom &g, int N, int n, cudaStream_t s) {
+    return lu_by_kl<double2, NB_C128, 1>(ab, piv, info, dinv, g, N, n, s);
 }
 #endif
 

@@ -144,6 +144,7 @@ struct Gemm {
     double2 *ws = nullptr;
     size_t ws_elems = 0;
     int64_t *counter = nullptr;
+    Handle *timer = nullptr;  // records events around every call when set
     cudaError_t run(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                     const double2 *B, int64_t ldb, double2 *C, int64_t ldc, cudaStream_t s,
                     bool hermitian = false, double alpha = 1.0, double beta = 0.0) {
@@ -164,6 +165,14 @@ struct Gemm {
         splits = std::max(1, (K + kchunk - 1) / kchunk);
         dim3 grid(tm, tn, splits);
         cudaError_t e;
+        cudaEvent_t ev1 = nullptr;
+        if (timer) {
+            cudaEvent_t ev0;
+            if ((e = timer->gemm_event(&ev0)) != cudaSuccess) return e;
+            if ((e = timer->gemm_event(&ev1)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+            timer->gemm_flops += hermitian ? 8.0 * (double)M * (M + 1) / 2 * K : 8.0 * M * N * (double)K;
+        }
         if (counter) *counter += 1 + (splits == 1 ? 0 : 1) + (hermitian ? 1 : 0);
         if (splits == 1) {  // direct: the kernel writes C itself
             zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, conjA, A, lda, B, ldb, C, ldc, kchunk,
@@ -183,6 +192,7 @@ struct Gemm {
             hermitian_mirror_kernel<<<grid1d((int64_t)M * M), 256, 0, s>>>(C, ldc, M);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess && timer) e = cudaEventRecord(ev1, s);
         return e;
     }
 };
@@ -237,28 +247,58 @@ __global__ void scale_rc_kernel(double2 *__restrict__ W, int64_t ld, int M, int 
     }
 }
 
+__global__ void diag_real_kernel(double *__restrict__ d, const double2 *__restrict__ G, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = G[(int64_t)i * n + i].x;
+}
+
 // ==========================================================================
-// pivoted Cholesky of the Hermitian positive semidefinite G (n x n), one
-// launch per step j (left-looking): pivot p = argmax of the remaining
-// diagonal d (first index on ties), column j of L for every row, d updated
-// into the other buffer.  Stops (flag, kc) when d_p <= tau or j == n.
-// Rows already used as pivots get 0 in later columns.
+// Bounded grid-wide barrier for cooperative launches (all CTAs co-resident).
+// bar[0] arrivals, bar[1] generation, bar[2] error flag.  A CTA that waits
+// more than 2^24 polls (~2 s) sets the error flag; every CTA then stops.
+// Returns false once the flag is set.
 // ==========================================================================
-__global__ void pchol_step_kernel(const double2 *__restrict__ G, int n, double2 *__restrict__ Lm,
-                                  const double *__restrict__ dprev, double *__restrict__ dnext,
-                                  int j, double tau, int32_t *__restrict__ state) {
-    // state[0] = stopped flag, state[1] = kc, state[2 + j] = pivot of column j
-    if (state[0]) return;
+constexpr long long GRID_WAIT_LIMIT = 1LL << 24;
+
+RSRR_DEV bool grid_sync(unsigned int *bar, unsigned int nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vb = bar;
+        const unsigned int gen = vb[1];
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (vb[1] == gen) {
+                if (vb[2]) { ok = 0; break; }
+                if (++it > GRID_WAIT_LIMIT) { atomicExch(bar + 2, 1u); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !vb[2];
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// block-wide argmax of d (first index on ties); every CTA computes it
+RSRR_DEV void block_argmax(const double *__restrict__ d, int n, double &bv, int &bi) {
     __shared__ double s_v[256];
     __shared__ int s_i[256];
-    double bv = -1.0;
-    int bi = 0x7fffffff;
+    double v = -1.0;
+    int ix = 0x7fffffff;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double v = dprev[i];
-        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        const double x = d[i];
+        if (x > v || (x == v && i < ix)) { v = x; ix = i; }
     }
-    s_v[threadIdx.x] = bv;
-    s_i[threadIdx.x] = bi;
+    s_v[threadIdx.x] = v;
+    s_i[threadIdx.x] = ix;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
@@ -271,45 +311,50 @@ __global__ void pchol_step_kernel(const double2 *__restrict__ G, int n, double2 
         }
         __syncthreads();
     }
-    const int p = s_i[0];
-    const double dp = s_v[0];
-    if (!(dp > tau)) {
-        // every CTA reaches the same decision; CTA 0 records it.  Later steps
-        // see the flag; this step writes nothing else.
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            state[1] = j;
-            state[0] = 1;
-        }
-        return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) state[2 + j] = p;
-    const double sq = sqrt(dp);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        double2 l = make_double2(0.0, 0.0);
-        double dn = dprev[i];
-        if (i == p) {
-            l = make_double2(sq, 0.0);
-            dn = -1.0;
-        } else if (dn >= 0.0) {
-            double2 s = G[(int64_t)p * n + i];
-            for (int t = 0; t < j; ++t) {
-                const double2 a = Lm[(int64_t)t * n + i], b = Lm[(int64_t)t * n + p];
-                // s -= a * conj(b)
-                s.x -= a.x * b.x + a.y * b.y;
-                s.y -= a.y * b.x - a.x * b.y;
-            }
-            l = make_double2(s.x / sq, s.y / sq);
-            dn = fmax(0.0, dn - (l.x * l.x + l.y * l.y));
-        }
-        Lm[(int64_t)j * n + i] = l;
-        dnext[i] = dn;
-    }
+    bv = s_v[0];
+    bi = s_i[0];
+    __syncthreads();
 }
 
-__global__ void diag_real_kernel(double *__restrict__ d, const double2 *__restrict__ G, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) d[i] = G[(int64_t)i * n + i].x;
+// Pivoted Cholesky G ~ L L^H in one cooperative launch (left-looking; one
+// grid barrier per column).  state[0] = stopped, state[1] = kc.
+__global__ void __launch_bounds__(256)
+pchol_persistent_kernel(const double2 *__restrict__ G, int n, double2 *__restrict__ Lm,
+                        double *__restrict__ dbuf, double tau, int32_t *__restrict__ state,
+                        unsigned int *__restrict__ bar) {
+    for (int j = 0; j < n; ++j) {
+        const double *dprev = dbuf + (j & 1) * n;
+        double *dnext = dbuf + ((j + 1) & 1) * n;
+        double dp;
+        int p;
+        block_argmax(dprev, n, dp, p);
+        if (!(dp > tau)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) { state[1] = j; state[0] = 1; }
+            return;
+        }
+        const double sq = sqrt(dp);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            double2 l = make_double2(0.0, 0.0);
+            double dn = dprev[i];
+            if (i == p) {
+                l = make_double2(sq, 0.0);
+                dn = -1.0;
+            } else if (dn >= 0.0) {
+                double2 s = G[(int64_t)p * n + i];
+                for (int t = 0; t < j; ++t) {
+                    const double2 a = Lm[(int64_t)t * n + i], b = Lm[(int64_t)t * n + p];
+                    s.x -= a.x * b.x + a.y * b.y;
+                    s.y -= a.y * b.x - a.x * b.y;
+                }
+                l = make_double2(s.x / sq, s.y / sq);
+                dn = fmax(0.0, dn - (l.x * l.x + l.y * l.y));
+            }
+            Lm[(int64_t)j * n + i] = l;
+            dnext[i] = dn;
+        }
+        if (!grid_sync(bar, gridDim.x)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { state[1] = n; state[0] = 1; }
 }
 
 // ==========================================================================
@@ -355,10 +400,10 @@ RSRR_DEV Rot rot_of(const double2 *__restrict__ H, int k, int p, int q) {
     return R;
 }
 
-__global__ void jacobi_round_kernel(const double2 *__restrict__ Hold, double2 *__restrict__ Hnew,
-                                    double2 *__restrict__ Y, int k, int kp, int r,
-                                    const int32_t *__restrict__ conv) {
-    if (conv[0]) return;
+// One round of the round-robin ordering, grid-stride over the 2x2 blocks and
+// the rows of Y (same arithmetic as jacobi_round_kernel).
+RSRR_DEV void jacobi_round(const double2 *__restrict__ Hold, double2 *__restrict__ Hnew,
+                           double2 *__restrict__ Y, int k, int kp, int r) {
     const int np = kp / 2;
     const int64_t nblk = (int64_t)np * np;
     const int64_t nY = (int64_t)k * np;
@@ -370,27 +415,24 @@ __global__ void jacobi_round_kernel(const double2 *__restrict__ Hold, double2 *_
             pair_of(r, a, kp, pa, qa);
             pair_of(r, b, kp, pb, qb);
             const Rot Ra = rot_of(Hold, k, pa, qa), Rb = rot_of(Hold, k, pb, qb);
-            const bool va = qa < k, vb = qb < k;  // pa < qa
-            // rows {pa, qa} x cols {pb, qb}; missing indices (padding) are absent
+            const bool va = qa < k, vb = qb < k;
             double2 h00 = (pa < k && pb < k) ? Hold[(int64_t)pb * k + pa] : make_double2(0, 0);
             double2 h01 = (pa < k && vb) ? Hold[(int64_t)qb * k + pa] : make_double2(0, 0);
             double2 h10 = (va && pb < k) ? Hold[(int64_t)pb * k + qa] : make_double2(0, 0);
             double2 h11 = (va && vb) ? Hold[(int64_t)qb * k + qa] : make_double2(0, 0);
-            // right: [h00 h01; h10 h11] * Jb, Jb = [[c, se], [-conj(se), c]]
             const double cb = Rb.c;
-            const double2 sb = Rb.se, sbc = make_double2(-sb.x, sb.y);  // -conj(se)
+            const double2 sb = Rb.se, sbc = make_double2(-sb.x, sb.y);
             double2 t00 = cadd(make_double2(h00.x * cb, h00.y * cb), cmul(h01, sbc));
             double2 t01 = cadd(cmul(h00, sb), make_double2(h01.x * cb, h01.y * cb));
             double2 t10 = cadd(make_double2(h10.x * cb, h10.y * cb), cmul(h11, sbc));
             double2 t11 = cadd(cmul(h10, sb), make_double2(h11.x * cb, h11.y * cb));
-            // left: Ja^H * T, Ja^H = [[c, -se], [conj(se), c]]
             const double ca = Ra.c;
             const double2 sa = Ra.se, msa = make_double2(-sa.x, -sa.y), sac = make_double2(sa.x, -sa.y);
             double2 n00 = cadd(make_double2(t00.x * ca, t00.y * ca), cmul(msa, t10));
             double2 n01 = cadd(make_double2(t01.x * ca, t01.y * ca), cmul(msa, t11));
             double2 n10 = cadd(cmul(sac, t00), make_double2(t10.x * ca, t10.y * ca));
             double2 n11 = cadd(cmul(sac, t01), make_double2(t11.x * ca, t11.y * ca));
-            if (a == b) {  // diagonal block: exact zero off-diagonal, real diagonal
+            if (a == b) {
                 n00.y = 0.0;
                 n11.y = 0.0;
                 if (Ra.se.x != 0.0 || Ra.se.y != 0.0) {
@@ -417,41 +459,58 @@ __global__ void jacobi_round_kernel(const double2 *__restrict__ Hold, double2 *_
     }
 }
 
-// off(H)^2 and diag(H)^2 sums -> conv flag when off <= tol^2 * diag
-__global__ void jacobi_check_kernel(const double2 *__restrict__ H, int k, double tol2,
-                                    int32_t *__restrict__ conv, double *__restrict__ acc) {
-    if (conv[0]) return;
-    double off = 0.0, dia = 0.0;
-    const int64_t total = (int64_t)k * k;
-    for (int64_t q = threadIdx.x; q < total; q += blockDim.x) {
-        const int i = (int)(q % k), j = (int)(q / k);
-        const double2 v = H[q];
-        const double a = v.x * v.x + v.y * v.y;
-        if (i == j) dia += a; else off += a;
-    }
-    __shared__ double so[256], sd[256];
-    so[threadIdx.x] = off;
-    sd[threadIdx.x] = dia;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            so[threadIdx.x] += so[threadIdx.x + w];
-            sd[threadIdx.x] += sd[threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        acc[0] = so[0];
-        acc[1] = sd[0];
-        if (so[0] <= tol2 * sd[0]) conv[0] = 1;
-    }
-}
-
-__global__ void identity_kernel(double2 *__restrict__ Y, int k) {
-    const int64_t total = (int64_t)k * k;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+// Whole cyclic Jacobi in one cooperative launch: Y = I, then sweeps of
+// kp-1 rounds (grid barrier after each), convergence test after each sweep
+// (off(H)^2 <= tol2 * diag(H)^2 from per-sweep atomic sums in acc, zeroed by
+// the host).  The final matrix is copied back into H0.  state[0] = sweeps run.
+__global__ void __launch_bounds__(256)
+jacobi_persistent_kernel(double2 *__restrict__ H0, double2 *__restrict__ H1,
+                         double2 *__restrict__ Y, int k, int max_sweeps, double tol2,
+                         double *__restrict__ acc, int32_t *__restrict__ state,
+                         unsigned int *__restrict__ bar) {
+    const int kp = k + (k & 1);
+    const int64_t kk = (int64_t)k * k;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < kk;
          q += (int64_t)gridDim.x * blockDim.x)
         Y[q] = make_double2((q % k) == (q / k) ? 1.0 : 0.0, 0.0);
+    if (!grid_sync(bar, gridDim.x)) return;
+    double2 *a = H0, *b = H1;
+    int sweeps = 0;
+    if (k > 1) {
+        for (int sw = 0; sw < max_sweeps; ++sw) {
+            for (int r = 0; r < kp - 1; ++r) {
+                jacobi_round(a, b, Y, k, kp, r);
+                if (!grid_sync(bar, gridDim.x)) return;
+                double2 *t = a; a = b; b = t;
+            }
+            ++sweeps;
+            double off = 0.0, dia = 0.0;
+            for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < kk;
+                 q += (int64_t)gridDim.x * blockDim.x) {
+                const double2 v = a[q];
+                const double m2 = v.x * v.x + v.y * v.y;
+                if ((q % k) == (q / k)) dia += m2; else off += m2;
+            }
+            for (int o = 16; o; o >>= 1) {
+                off += shfl_down(off, o);
+                dia += shfl_down(dia, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(acc + 2 * sw, off);
+                atomicAdd(acc + 2 * sw + 1, dia);
+            }
+            if (!grid_sync(bar, gridDim.x)) return;
+            const double o2 = *((volatile double *)(acc + 2 * sw));
+            const double d2 = *((volatile double *)(acc + 2 * sw + 1));
+            if (o2 <= tol2 * d2) break;
+        }
+    }
+    if (a != H0) {
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < kk;
+             q += (int64_t)gridDim.x * blockDim.x)
+            H0[q] = a[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[0] = sweeps;
 }
 
 // eigenvalues = real diagonal; order[r] = index of the r-th largest (ties by index);
@@ -523,6 +582,8 @@ struct ProjWs {
     double2 *gws;       // GEMM workspace
     size_t gws_elems;
     double2 *C;         // NL x NL coefficients of the deflation
+    unsigned int *bar;  // grid barrier of the cooperative kernels
+    double *jacc;       // per-sweep convergence sums of the Jacobi kernel
     double2 *Qall;      // n x NL basis
     double2 *P;         // RSRR_MAX_TERMS x NL x NL projected coefficients
     char *end;
@@ -540,38 +601,36 @@ template <typename T> static T *carve(char *&p, size_t count) {
         if (_e != cudaSuccess) return fail(RSRR_ECUDA, what, _e);        \
     } while (0)
 
-// Jacobi on the k x k Hermitian matrix in ws.H (overwritten); eigenvalues
-// sorted descending into ws.evals, eigenvectors (same order) into ws.Ysort.
+// Cooperative launch helper: as many CTAs as can be co-resident (<= cap).
+template <typename K, typename... Args>
+static cudaError_t launch_coop(K kern, int cap, cudaStream_t s, Args... args) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    int grid = std::max(1, std::min(cap, nsm * std::max(per, 1)));
+    void *argv[] = {(void *)&args...};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), argv, 0, s);
+}
+
+// Jacobi on the k x k Hermitian matrix in ws.H (overwritten with its
+// eigenvalues on the diagonal); eigenvalues sorted descending into
+// ws.evals, eigenvectors (same order) into ws.Ysort.  One cooperative
+// launch plus the sort; a barrier timeout is reported through ws.bar[2].
 static cudaError_t jacobi_eig(ProjWs &ws, int k, cudaStream_t s, int64_t *counter,
                               int max_sweeps = 30) {
-    const int kp = k + (k & 1);
-    cudaError_t e;
-    e = cudaMemsetAsync(ws.conv, 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.jacc, 0, sizeof(double) * 2 * max_sweeps, s);
     if (e != cudaSuccess) return e;
-    identity_kernel<<<grid1d((int64_t)k * k), 256, 0, s>>>(ws.Y, k);
-    double2 *a = ws.H, *b = ws.H2;
-    const int np = kp / 2;
-    const int64_t work = (int64_t)np * np + (int64_t)k * np;
-    const double tol2 = 1e-30;  // off(H) <= 1e-15 * ||diag(H)||
-    if (k > 1) {
-        for (int sw = 0; sw < max_sweeps; ++sw) {
-            for (int r = 0; r < kp - 1; ++r) {
-                jacobi_round_kernel<<<grid1d(work), 256, 0, s>>>(a, b, ws.Y, k, kp, r, ws.conv);
-                std::swap(a, b);
-            }
-            jacobi_check_kernel<<<1, 256, 0, s>>>(a, k, tol2, ws.conv, ws.acc);
-        }
-        *counter += (int64_t)max_sweeps * kp;
-    }
-    *counter += 3;
-    e = cudaGetLastError();
+    const double tol2 = 1e-30;  // off(H) <= 1e-15 ||diag(H)||
+    const int64_t work = (int64_t)(k + 1) / 2 * ((k + 1) / 2) + (int64_t)k * ((k + 1) / 2);
+    e = launch_coop(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, 1 << 20), s,
+                    ws.H, ws.H2, ws.Y, k, max_sweeps, tol2, ws.jacc, ws.state + 1, ws.bar);
     if (e != cudaSuccess) return e;
-    if (a != ws.H) {
-        e = cudaMemcpyAsync(ws.H, a, sizeof(double2) * k * k, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return e;
-    }
     sort_desc_kernel<<<1, 256, 0, s>>>(ws.H, k, ws.order, ws.evals);
     gather_cols_kernel<<<grid1d((int64_t)k * k), 256, 0, s>>>(ws.Ysort, ws.Y, k, k, ws.order);
+    *counter += 3;
     return cudaGetLastError();
 }
 
@@ -589,6 +648,34 @@ __global__ void scale_cols_kernel(double2 *__restrict__ Sn, const double2 *__res
 __global__ void max_diag_kernel(double *__restrict__ out, const double2 *__restrict__ G, int n) {
     double m = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, G[(int64_t)i * n + i].x);
+    for (int off = 16; off; off >>= 1) m = fmax(m, shfl_down(m, off));
+    __shared__ double w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, w[q]);
+        out[0] = r;
+    }
+}
+
+// d[c] = G(c,c) - sum_j |C(j,c)|^2 (clamped at 0): squared column norms of
+// R - Q C for C = Q^H R with orthonormal Q, without forming it
+__global__ void remainder_norm_kernel(double *__restrict__ d, const double2 *__restrict__ G,
+                                      const double2 *__restrict__ Cm, int kb, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double s = G[(int64_t)c * n + c].x;
+    for (int j = 0; j < kb; ++j) {
+        const double2 v = Cm[(int64_t)c * kb + j];
+        s -= v.x * v.x + v.y * v.y;
+    }
+    d[c] = fmax(s, 0.0);
+}
+
+__global__ void max_vec_kernel(double *__restrict__ out, const double *__restrict__ v, int n) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
     for (int off = 16; off; off >>= 1) m = fmax(m, shfl_down(m, off));
     __shared__ double w[32];
     if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
@@ -618,6 +705,8 @@ static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n) {
     ws.acc = carve<double>(cp, 2);
     ws.W = carve<double2>(cp, NL2);
     ws.C = carve<double2>(cp, NL2);
+    ws.bar = carve<unsigned int>(cp, 4);
+    ws.jacc = carve<double>(cp, 64);
     ws.Q1 = carve<double2>(cp, (size_t)n * NL);
     ws.Ytmp = carve<double2>(cp, (size_t)n * NL);
     ws.gws_elems = std::max<size_t>(NL2 * 4, (size_t)8 << 20);
@@ -666,6 +755,12 @@ rsrr_status Handle::project(cudaStream_t s) {
     gm.ws = ws.gws;
     gm.ws_elems = ws.gws_elems;
     gm.counter = &launches;
+    if (opts.timing) {
+        gm.timer = this;
+        gemm_events_used = 0;
+        gemm_flops = 0.0;
+        gemm_timed = true;
+    }
     rsrr_status mst = mark(6, s);
     if (mst != RSRR_OK) return mst;
 
@@ -683,25 +778,25 @@ rsrr_status Handle::project(cudaStream_t s) {
     kc = 0;
     for (int lev = 0; lev < 6 && kt < NL; ++lev) {
         // (A9) Gram of the remainder and its largest diagonal
+        double maxd = 1.0;
         PK(gm.run(NL, NL, (int)nn, true, R, nn, R, nn, ws.G, NL, s, true), "Gram");
         max_diag_kernel<<<1, 256, 0, s>>>(ws.acc, ws.G, NL);
-        double maxd = 0.0;
         PK(cudaMemcpyAsync(&maxd, ws.acc, sizeof(double), cudaMemcpyDeviceToHost, s), "maxdiag");
         PK(cudaStreamSynchronize(s), "maxdiag sync");
         launches += 1;
-        if (lev > 0 && !(maxd > floor_ * floor_ * s1sq)) break;
         const double tau = std::max(lev_tol * lev_tol * maxd, floor_ * floor_ * s1sq);
-        PK(cudaMemsetAsync(ws.state, 0, sizeof(int32_t) * (2 + NL), s), "memset");
+        PK(cudaMemsetAsync(ws.state, 0, sizeof(int32_t) * 4, s), "memset");
+        PK(cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int) * 4, s), "memset");
         diag_real_kernel<<<(NL + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, NL);
-        for (int j = 0; j < NL; ++j)
-            pchol_step_kernel<<<(NL + 255) / 256, 256, 0, s>>>(
-                ws.G, NL, ws.Lm, ws.dbuf + (j & 1) * NL, ws.dbuf + ((j + 1) & 1) * NL, j, tau,
-                ws.state);
-        PK(cudaGetLastError(), "pivoted Cholesky");
-        launches += 1 + NL;
+        PK(launch_coop(pchol_persistent_kernel, (NL + 255) / 256, s, (const double2 *)ws.G, NL,
+                       ws.Lm, ws.dbuf, tau, ws.state, ws.bar), "pivoted Cholesky");
+        launches += 2;
         int32_t st2[2];
+        unsigned int bar_err = 0;
         PK(cudaMemcpyAsync(st2, ws.state, sizeof st2, cudaMemcpyDeviceToHost, s), "kc");
+        PK(cudaMemcpyAsync(&bar_err, ws.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s), "kc");
         PK(cudaStreamSynchronize(s), "kc sync");
+        if (bar_err) return fail(RSRR_ETIMEOUT, "rsrr_project: grid barrier timeout (pivoted Cholesky)");
         const int kcl = st2[0] ? st2[1] : NL;
         if (kcl < 1) break;
         kc += kcl;
@@ -710,7 +805,9 @@ rsrr_status Handle::project(cudaStream_t s) {
         PK(jacobi_eig(ws, kcl, s, &launches), "Jacobi (B^H B)");
         std::vector<double> ev(kcl);
         PK(cudaMemcpyAsync(ev.data(), ws.evals, sizeof(double) * kcl, cudaMemcpyDeviceToHost, s), "evals");
+        PK(cudaMemcpyAsync(&bar_err, ws.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s), "evals");
         PK(cudaStreamSynchronize(s), "evals sync");
+        if (bar_err) return fail(RSRR_ETIMEOUT, "rsrr_project: grid barrier timeout (Jacobi)");
         if (lev == 0) s1sq = std::max(ev[0], 0.0);
         const double keep_tol = std::max(1e-2 * tau, floor_ * floor_ * s1sq);
         int kb = 0;
@@ -736,7 +833,9 @@ rsrr_status Handle::project(cudaStream_t s) {
         PK(jacobi_eig(ws, kb, s, &launches), "Jacobi (Qb^H Qb)");
         std::vector<double> mu(kb);
         PK(cudaMemcpyAsync(mu.data(), ws.evals, sizeof(double) * kb, cudaMemcpyDeviceToHost, s), "mu");
+        PK(cudaMemcpyAsync(&bar_err, ws.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s), "mu");
         PK(cudaStreamSynchronize(s), "mu sync");
+        if (bar_err) return fail(RSRR_ETIMEOUT, "rsrr_project: grid barrier timeout (Jacobi)");
         int kb2 = 0;
         for (int j = 0; j < kb; ++j)
             if (mu[j] > 1e-10 * mu[0]) kb2 = j + 1;
@@ -744,15 +843,29 @@ rsrr_status Handle::project(cudaStream_t s) {
         scale_rc_kernel<<<grid1d((int64_t)kb * kb2), 256, 0, s>>>(ws.Ysort, kb, kb, kb2, nullptr,
                                                                   ws.evals, false, true);
         launches += 1;
-        PK(gm.run((int)nn, kb2, kb, false, ws.Ytmp, nn, ws.Ysort, kb, ws.Qall + (size_t)kt * nn, nn, s),
-           "Qb Z");
+        double2 *Qnew = ws.Qall + (size_t)kt * nn;
+        PK(gm.run((int)nn, kb2, kb, false, ws.Ytmp, nn, ws.Ysort, kb, Qnew, nn, s), "Qb Z");
+        const int kprev = kt;
         kt += kb2;
-        // deflate the remainder, twice
-        for (int pass = 0; pass < 2; ++pass) {
-            PK(gm.run(kt, NL, (int)nn, true, ws.Qall, nn, R, nn, ws.C, kt, s), "Q^H R");
-            PK(gm.run((int)nn, NL, kt, false, ws.Qall, nn, ws.C, kt, R, nn, s, false, -1.0, 1.0),
-               "R -= Q C");
-        }
+        // deflate the remainder: pass 1 against the new block (R is already
+        // orthogonal to the earlier blocks), pass 2 against the whole basis.
+        // Before pass 1's update, the column norms the deflation would leave,
+        // diag(G) - |Qnew^H R|^2, tell whether another level is needed; if
+        // not, R is not needed any more and the updates are skipped.
+        PK(gm.run(kb2, NL, (int)nn, true, Qnew, nn, R, nn, ws.C, kb2, s), "Qnew^H R");
+        remainder_norm_kernel<<<(NL + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, ws.C, kb2, NL);
+        max_vec_kernel<<<1, 256, 0, s>>>(ws.acc, ws.dbuf, NL);
+        launches += 2;
+        double rem = 0.0;
+        PK(cudaMemcpyAsync(&rem, ws.acc, sizeof(double), cudaMemcpyDeviceToHost, s), "remainder");
+        PK(cudaStreamSynchronize(s), "remainder sync");
+        if (!(rem > floor_ * floor_ * s1sq) || kt >= NL) break;
+        PK(gm.run((int)nn, NL, kb2, false, Qnew, nn, ws.C, kb2, R, nn, s, false, -1.0, 1.0),
+           "R -= Qnew C");
+        PK(gm.run(kt, NL, (int)nn, true, ws.Qall, nn, R, nn, ws.C, kt, s), "Q^H R");
+        PK(gm.run((int)nn, NL, kt, false, ws.Qall, nn, ws.C, kt, R, nn, s, false, -1.0, 1.0),
+           "R -= Q C");
+        (void)kprev;
     }
     if (kt < 1) return fail(RSRR_ESTATE, "rsrr_project: empty basis");
     k = kt;

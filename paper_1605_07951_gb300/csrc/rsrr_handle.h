@@ -38,6 +38,8 @@ struct Handle {
     float2 *d_D = nullptr;            // complex64 corrections (mixed path)
     float2 *d_ab32 = nullptr;         // complex64 band factors
     double2 *d_ab64 = nullptr;        // complex128 band factors
+    float2 *d_dinv32 = nullptr;       // per block L11^{-1}, U11^{-1} (complex64)
+    double2 *d_dinv64 = nullptr;      // per block L11^{-1}, U11^{-1} (complex128)
     int32_t *d_piv = nullptr, *d_info = nullptr, *d_done = nullptr, *d_sweep_flags = nullptr;
     double *d_tnorm = nullptr, *d_eta = nullptr, *d_rmax = nullptr, *d_xmax = nullptr;
 
@@ -62,8 +64,14 @@ struct Handle {
     cudaEvent_t events[8] = {};
     bool timed_sample = false, timed_project = false;
     double stage_ms[6] = {};
+    // GEMM timing of the last rsrr_project (opts.timing)
+    std::vector<cudaEvent_t> gemm_events;  // pairs
+    int gemm_events_used = 0;
+    double gemm_flops = 0.0, gemm_ms = 0.0;
+    bool gemm_timed = false;
 
     ~Handle();
+    cudaError_t gemm_event(cudaEvent_t *out);
     rsrr_status fail(rsrr_status st, const char *what, cudaError_t e = cudaSuccess);
     template <typename T> cudaError_t alloc(T **p, size_t count);
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);

@@ -37,15 +37,17 @@ struct DevProblem {
 template <typename C>
 cudaError_t launch_assemble(C *ab, const BandGeom &g, const DevProblem &p, cudaStream_t s);
 cudaError_t launch_tnorm(double *tnorm, const DevProblem &p, cudaStream_t s);
-cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, const BandGeom &g, int N,
-                               int n, cudaStream_t s);
-cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, const BandGeom &g,
-                                int N, int n, cudaStream_t s);
-cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, float2 *B, const BandGeom &g,
-                                  int N, int n, int L, const int32_t *skip, cudaStream_t s);
-cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, double2 *B,
-                                   const BandGeom &g, int N, int n, int L, const int32_t *skip,
-                                   cudaStream_t s);
+// dinv: per point and NB block, L11^{-1} then U11^{-1} (NB x NB each)
+cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *dinv,
+                               const BandGeom &g, int N, int n, cudaStream_t s);
+cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, double2 *dinv,
+                                const BandGeom &g, int N, int n, cudaStream_t s);
+cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const float2 *dinv,
+                                  float2 *B, const BandGeom &g, int N, int n, int L,
+                                  const int32_t *skip, cudaStream_t s);
+cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, const double2 *dinv,
+                                   double2 *B, const BandGeom &g, int N, int n, int L,
+                                   const int32_t *skip, cudaStream_t s);
 cudaError_t launch_residual(double2 *R, const double2 *X, const DevProblem &p, double *rmax,
                             double *xmax, const int32_t *skip, cudaStream_t s);
 cudaError_t launch_eta(double *eta, int32_t *done, const double *rmax, const double *xmax,

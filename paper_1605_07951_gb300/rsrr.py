@@ -67,7 +67,8 @@ class rsrr_stats(C.Structure):
                 ("converged", C.c_int32), ("singular_point", C.c_int32), ("k", C.c_int32),
                 ("kc", C.c_int32), ("max_eta", C.c_double), ("sigma1", C.c_double),
                 ("sigmak", C.c_double), ("device_bytes", C.c_size_t),
-                ("launches", C.c_int64), ("stage_ms", C.c_double * 6)]
+                ("launches", C.c_int64), ("stage_ms", C.c_double * 6),
+                ("gemm_flops", C.c_double), ("gemm_ms", C.c_double)]
 
 
 class rsrr_result(C.Structure):
