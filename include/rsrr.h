@@ -245,11 +245,40 @@ rsrr_status rsrr_get_points(rsrr_t *h, rsrr_c128 *dst);
 rsrr_status rsrr_get_stats(rsrr_t *h, rsrr_stats *out);
 
 /* One-line description of the last error on this handle ("" if none).  With
- * h == NULL: the last error of a failed rsrr_create on this thread. */
+ * h == NULL: the last error of a failed rsrr_create or
+ * rsrr_solve_band_noalloc on this thread. */
 const char *rsrr_last_error(const rsrr_t *h);
 
 /* Frees the handle and all its device memory.  NULL is allowed. */
 void rsrr_destroy(rsrr_t *h);
+
+/* Allocation-free solve of one banded system T X = U in complex128: the
+ * factorisation (partial pivoting) and the triangular solves of rsrr_sample's
+ * FP64 path, for a T the caller has already assembled.  The paper has no
+ * counterpart; it exists for callers that cannot call cudaMalloc: plug-ins
+ * whose host application's caching allocator or memory pool has reserved the
+ * device memory up front, and latency-bound loops that must never enter the
+ * allocator.  Nothing is allocated: the work space comes from a fixed 32 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   n, kl, ku  order and half-bandwidths of T (kl <= 480)
+ *   band       device, (kl+ku+1) x n, LAPACK general band layout:
+ *              T(i,j) at band[(ku + i - j) + j*(kl+ku+1)]
+ *   L, U       device, n x L right-hand sides (column major); not modified
+ *   X          device, n x L solution (column major); may not alias U
+ *   stream     work is queued on it; the call waits for it before returning
+ * Limit: 16*n*(2kl+ku+16) + 32*n*16 + 4*n bytes (each rounded up to 256) must
+ * fit in 32 MiB, else RSRR_EINVAL with the needed size in the message.
+ * Returns OK, EINVAL, ESINGULAR (an exactly zero pivot) or ECUDA; the message
+ * is in rsrr_last_error(NULL).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and overwrites
+ * all of it that it uses (no state carries over), so calls that overlap on
+ * the GPU -- from several host threads or on several streams -- race: issue
+ * them one after another. */
+rsrr_status rsrr_solve_band_noalloc(int64_t n, int32_t kl, int32_t ku, const rsrr_c128 *band,
+                                    int32_t L, const rsrr_c128 *U, rsrr_c128 *X, void *stream);
 
 #ifdef __cplusplus
 }

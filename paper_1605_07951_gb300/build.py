@@ -22,6 +22,7 @@ UNITS = [
     ("band_lu.cu", ["-DRSRR_LU_ONLY=128"], "band_lu128.o"),
     ("proj.cu", [], "proj.o"),
     ("ssfull_host.cpp", ["-x", "cu"], "ssfull_host.o"),
+    ("noalloc.cu", [], "noalloc.o"),
 ]
 
 

@@ -14,11 +14,13 @@
 
 using cplx = std::complex<double>;
 
-namespace {
-thread_local std::string g_create_error;
-}
-
 namespace rsrr {
+
+// last error of a call without a handle (rsrr_create, rsrr_solve_band_noalloc)
+std::string &thread_error() {
+    thread_local std::string s;
+    return s;
+}
 
 cplx eval_fn_host(const rsrr_fn &f, cplx z) {
     cplx base;
@@ -108,7 +110,7 @@ void rsrr_opts_default(rsrr_opts *o) {
 }
 
 static rsrr_status create_fail(const char *msg) {
-    g_create_error = msg;
+    rsrr::thread_error() = msg;
     return RSRR_EINVAL;
 }
 
@@ -116,7 +118,7 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
                         const rsrr_opts *opts, rsrr_t **out) {
     if (!out) return create_fail("rsrr_create: out is NULL");
     *out = nullptr;
-    g_create_error.clear();
+    rsrr::thread_error().clear();
     if (!nep || !region) return create_fail("rsrr_create: nep or region is NULL");
     if (nep->n < 1 || nep->n > (int64_t)1 << 30) return create_fail("rsrr_create: n out of range");
     if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
@@ -156,7 +158,7 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
         return create_fail("rsrr_create: unknown precision");
 
     Handle *h = new (std::nothrow) Handle();
-    if (!h) { g_create_error = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
+    if (!h) { rsrr::thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
     if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);
     h->n = n; h->nnz = nnz; h->N = N; h->L = L; h->m = nep->m;
     h->kl = (int)kl; h->ku = (int)ku;
@@ -224,7 +226,7 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
 
     rsrr_status st = h->allocate_and_upload(coef);
     if (st != RSRR_OK) {
-        g_create_error = h->err;
+        rsrr::thread_error() = h->err;
         delete h;
         return st;
     }
@@ -337,7 +339,7 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
 
 const char *rsrr_last_error(const rsrr_t *hh) {
     const Handle *h = reinterpret_cast<const Handle *>(hh);
-    if (!h) return g_create_error.c_str();
+    if (!h) return rsrr::thread_error().c_str();
     return h->err.c_str();
 }
 

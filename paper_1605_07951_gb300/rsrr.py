@@ -105,6 +105,8 @@ rsrr_get_points = _sig("rsrr_get_points", C.c_int, [_h, _p])
 rsrr_get_stats = _sig("rsrr_get_stats", C.c_int, [_h, C.POINTER(rsrr_stats)])
 rsrr_last_error = _sig("rsrr_last_error", C.c_char_p, [_h])
 rsrr_destroy = _sig("rsrr_destroy", None, [_h])
+rsrr_solve_band_noalloc = _sig("rsrr_solve_band_noalloc", C.c_int,
+                               [C.c_int64, C.c_int32, C.c_int32, _p, C.c_int32, _p, _p, _p])
 
 
 class RSRRError(RuntimeError):
