@@ -323,3 +323,150 @@ def companion_eigvals(prob: Problem) -> np.ndarray:
     A = np.block([[Z, I], [-B[0], -B[1]]])
     Bm = np.block([[I, Z], [Z, B[2]]])
     return sla.eigvals(A, Bm)
+
+
+# ---------------------------------------------------------------------------
+# Dense BEM-like problems (Section 2.1, Nystrom single-layer kernel)
+# ---------------------------------------------------------------------------
+
+def distances(prob) -> np.ndarray:
+    P = prob.points
+    return np.linalg.norm(P[:, None, :] - P[None, :, :], axis=2)
+
+
+def assemble_dense(prob, z: complex, R: np.ndarray | None = None) -> np.ndarray:
+    """T(z)_ij = exp(i z r_ij)/(4 pi r_ij) for i != j, T_ii = diag."""
+    if R is None:
+        R = distances(prob)
+    n = prob.n
+    off = ~np.eye(n, dtype=bool)
+    T = np.empty((n, n), dtype=np.complex128)
+    T[off] = np.exp(1j * z * R[off]) / (4.0 * np.pi * R[off])
+    T[~off] = prob.diag
+    return T
+
+
+def resolvent_samples_dense(prob, z: np.ndarray, U: np.ndarray | None = None) -> list:
+    """X_j = T(z_j)^{-1} U by dense LU with partial pivoting (LAPACK gesv)."""
+    if U is None:
+        U = prob.U
+    R = distances(prob)
+    return [np.linalg.solve(assemble_dense(prob, zj, R), U) for zj in z]
+
+
+def taylor_terms(prob, R: np.ndarray | None = None) -> int:
+    """Smallest P with (r_max rho)^P / P! < 1e-17, rho = max(a, b): the
+    remainder bound of the Taylor series of exp(i z r) about the centre."""
+    if R is None:
+        R = distances(prob)
+    x = R.max() * max(prob.region.a, prob.region.b)
+    P, term = 0, 1.0
+    while term >= 1e-17:
+        P += 1
+        term *= x / P
+    return P
+
+
+def taylor_coefficients(prob, R: np.ndarray | None = None, P: int | None = None) -> list:
+    """A_p with T(z) = sum_{p<P} (z - c)^p A_p: A_p(i,j) = e^{i c r}(i r)^p /
+    (p! 4 pi r) off the diagonal, A_0 diagonal = diag, A_p diagonal = 0 (p > 0).
+    The Taylor series of exp(i z r) about the region centre c: the
+    interpolation of T that makes T_Q = Q^H T Q computable (Section 5.2 uses
+    a Chebyshev interpolant for the same purpose)."""
+    if R is None:
+        R = distances(prob)
+    if P is None:
+        P = taylor_terms(prob, R)
+    c = prob.region.center
+    n = prob.n
+    off = ~np.eye(n, dtype=bool)
+    base = np.zeros((n, n), dtype=np.complex128)
+    base[off] = np.exp(1j * c * R[off]) / (4.0 * np.pi * R[off])
+    out = []
+    term = base.copy()
+    for p in range(P):
+        A = term.copy()
+        if p == 0:
+            A[~off] = prob.diag
+        out.append(A)
+        term = term * (1j * R) / (p + 1)
+    return out
+
+
+def residual_dense(prob, lam: complex, v: np.ndarray, R: np.ndarray | None = None) -> float:
+    """||T(lam) v||_2 / (||T(lam)||_1 ||v||_2), the 1-norm computed directly."""
+    T = assemble_dense(prob, lam, R)
+    return float(np.linalg.norm(T @ v) / (np.abs(T).sum(axis=0).max() * np.linalg.norm(v)))
+
+
+def backward_error_inf_dense(prob, z: complex, X: np.ndarray, U: np.ndarray | None = None):
+    """Per-column eta = ||U - T X||_inf / (||T||_inf ||X||_inf + ||U||_inf)."""
+    if U is None:
+        U = prob.U
+    T = assemble_dense(prob, z)
+    Rr = U - T @ X
+    tn = np.abs(T).sum(axis=1).max()
+    return np.abs(Rr).max(axis=0) / (tn * np.abs(X).max(axis=0) + np.abs(U).max(axis=0))
+
+
+def rsrr_dense(prob, delta: float = 1e-14, NQ: int = 500, KQ: int = 2, tol_gap: float = 1e3,
+               U: np.ndarray | None = None, res_tol: float = 1e-6):
+    """RSRR (Section 3.3) for the dense kernel problem: samples by dense
+    solves, the truncated SVD basis of the normalised S, projection of the
+    Taylor coefficients P_p = Q^H A_p Q, SS-FULL on T_Q(z) = sum_p (z-c)^p P_p,
+    v = Q g, acceptance as in rsrr()."""
+    from workloads import Fn
+    R = distances(prob)
+    z = sample_points(prob.region, prob.N)
+    X = resolvent_samples_dense(prob, z, U)
+    S = normalize_columns(sample_matrix(X))
+    Q, sig, k = truncated_basis(S, delta)
+    A = taylor_coefficients(prob, R)
+    P = [Q.conj().T @ (Ap @ Q) for Ap in A]
+    c = prob.region.center
+    fns = [ShiftPow(p, c) for p in range(len(A))]
+    lam, G, info = ss_full(P, fns, prob.region, NQ, KQ, tol_gap)
+    V = Q @ G
+    V = V / np.linalg.norm(V, axis=0, keepdims=True)
+    keep = inside(prob.region, lam)
+    lam, V = lam[keep], V[:, keep]
+    res = np.array([residual_dense(prob, l, V[:, j], R) for j, l in enumerate(lam)])
+    ok = res <= res_tol
+    lam, V, res = lam[ok], V[:, ok], res[ok]
+    order = np.lexsort((np.angle(lam), np.abs(lam)))
+    return dict(lam=lam[order], V=V[:, order], res=res[order], k=k, sigma=sig, info=info,
+                z=z, X=X, P=P, Q=Q, terms=len(A))
+
+
+class ShiftPow:
+    """f(z) = (z - c)^p, the scalar functions of the Taylor-expanded T."""
+    def __init__(self, p: int, c: complex):
+        self.p, self.c = p, c
+
+
+_eval_fn_base = eval_fn
+
+
+def eval_fn(fn, z):  # noqa: F811  (extends the families with the Taylor powers)
+    if isinstance(fn, ShiftPow):
+        return (np.asarray(z, dtype=np.complex128) - fn.c) ** fn.p
+    return _eval_fn_base(fn, z)
+
+
+def argument_principle_count_dense(prob, npts: int = 2048) -> int:
+    """Zeros of det T inside the region by the winding number of det T(z)."""
+    R = distances(prob)
+    reg = prob.region
+
+    def phase(z):
+        s, _ = np.linalg.slogdet(assemble_dense(prob, z, R))
+        return np.angle(s)
+    alpha = np.linspace(0.0, 2.0 * np.pi, npts + 1)
+    while True:
+        zz = reg.center + reg.a * np.cos(alpha) + 1j * reg.b * np.sin(alpha)
+        ph = np.array([phase(z) for z in zz])
+        d = np.angle(np.exp(1j * np.diff(ph)))
+        if np.all(np.abs(d) < np.pi / 4) or len(alpha) > 1 << 15:
+            break
+        alpha = np.sort(np.concatenate([alpha, 0.5 * (alpha[1:] + alpha[:-1])]))
+    return int(round(d.sum() / (2.0 * np.pi)))

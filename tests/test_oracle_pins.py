@@ -220,3 +220,40 @@ def test_planted_mistakes_fail_a_pin(monkeypatch, which):
             failed = True
             break
     assert failed, f"planted mistake {which!r} went unnoticed"
+
+
+# ------------------------------------------------------------ dense BEM kernel
+def test_taylor_expansion_reproduces_the_kernel_matrix():
+    """T(z) = sum_{p<P} (z - c)^p A_p inside the circle: the series of
+    exp(i z r) about the centre, truncated where (r_max rho)^P/P! < 1e-17."""
+    p = W.helmholtz_sphere(n=96, N=8, L=4)
+    R = oracle.distances(p)
+    A = oracle.taylor_coefficients(p, R)
+    assert len(A) == oracle.taylor_terms(p, R) >= 20
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        z = p.region.center + 0.95 * p.region.a * np.exp(2j * np.pi * rng.random()) * rng.random()
+        T = oracle.assemble_dense(p, z, R)
+        Ts = sum((z - p.region.center) ** q * Aq for q, Aq in enumerate(A))
+        assert np.abs(T - Ts).max() <= 1e-13 * np.abs(T).max()
+
+
+@pytest.mark.parametrize("n,count", [(64, 4), (128, 1)])
+def test_dense_rsrr_count_equals_argument_principle(n, count):
+    p = W.helmholtz_sphere(n=n, N=32, L=16)
+    assert oracle.argument_principle_count_dense(p, 512) == count
+    out = oracle.rsrr_dense(p, NQ=256)
+    assert len(out["lam"]) == count
+    assert out["res"].max() <= 1e-10
+
+
+def test_dense_eigenvalue_drifts_towards_pi():
+    """Trend only: the continuum single-layer operator on the unit sphere is
+    singular at the zeros of j_0(k) = sin(k)/k, k = pi; the discrete NEP's
+    eigenvalue in |z - 3| < 1 approaches pi as n grows."""
+    d = []
+    for n in (128, 256):
+        lam = oracle.rsrr_dense(W.helmholtz_sphere(n=n, N=32, L=16), NQ=256)["lam"]
+        assert len(lam) == 1
+        d.append(abs(lam[0] - np.pi))
+    assert d[1] < d[0]

@@ -334,3 +334,58 @@ def config(name: str, **kw) -> Problem:
     if name == "c1":
         return rational_grid(**kw)
     raise KeyError(name)
+
+
+# ----------------------------------------------------------------------------
+# dense BEM-like workload: single-layer Helmholtz kernel on a sphere
+# ----------------------------------------------------------------------------
+
+@dataclass
+class DenseProblem:
+    """T(z)_ij = exp(i z r_ij) / (4 pi r_ij) for i != j, T_ii = diag, with
+    r_ij the distances between `points` (the BEM kernel of Section 2.1,
+    Nystrom form with uniform weights)."""
+    name: str
+    n: int
+    points: np.ndarray   # float64 [n, 3]
+    diag: float
+    region: Region
+    N: int
+    L: int
+    U: np.ndarray        # complex128 [n, L], Fortran order
+    meta: dict = field(default_factory=dict)
+
+
+def fibonacci_sphere(n: int, seed: int) -> np.ndarray:
+    """Quasi-uniform points on the unit sphere: Fibonacci lattice turned by a
+    seeded random rotation (QR of a Gaussian matrix, sign-fixed)."""
+    i = np.arange(n) + 0.5
+    phi = np.arccos(1.0 - 2.0 * i / n)
+    theta = np.pi * (1.0 + 5.0 ** 0.5) * i
+    P = np.stack([np.cos(theta) * np.sin(phi), np.sin(theta) * np.sin(phi), np.cos(phi)], axis=1)
+    Qr, R = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    Qr = Qr * np.sign(np.diag(R))
+    return np.ascontiguousarray(P @ Qr.T)
+
+
+def mean_nn_distance(P: np.ndarray) -> float:
+    """Mean nearest-neighbour distance of a point cloud (blockwise, O(n^2))."""
+    n = len(P)
+    best = np.full(n, np.inf)
+    for s in range(0, n, 1024):
+        d = np.linalg.norm(P[s:s + 1024, None, :] - P[None, :, :], axis=2)
+        d[np.arange(d.shape[0]), np.arange(s, s + d.shape[0])] = np.inf
+        best[s:s + 1024] = d.min(axis=1)
+    return float(best.mean())
+
+
+def helmholtz_sphere(n: int = 4096, N: int = 32, L: int = 64, center: complex = 3.0,
+                     radius: float = 1.0, seed: int = 3000, seed_u: int = 3001,
+                     name: str = "c2") -> DenseProblem:
+    """Dense BEM-like NEP on the unit sphere: n points (Fibonacci lattice,
+    seeded rotation), diagonal 1/(2h) with h the mean nearest-neighbour
+    distance, circle region (centre 3, radius 1 for the benchmark shape)."""
+    P = fibonacci_sphere(n, seed)
+    h = mean_nn_distance(P)
+    return DenseProblem(name, n, P, 1.0 / (2.0 * h), Region(complex(center), radius, radius), N, L,
+                        probe(n, L, seed_u), meta=dict(h=h, seed=seed, seed_u=seed_u))
