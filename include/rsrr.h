@@ -91,20 +91,34 @@ typedef struct {
 
 #define RSRR_MAX_TERMS 8
 
-/* T(z) = sum_{i<m} fn[i](z) A_i.  All A_i share one CSR pattern (row_ptr,
- * col_idx; columns need not be sorted; duplicates are not allowed); their
- * real values are stored term-major: A_i's value for pattern entry e is
- * values[i * nnz + e], nnz = row_ptr[n].  All three arrays are host memory
- * and are copied by rsrr_create.  The half-bandwidths kl, ku are detected
- * from the pattern. */
+/* The NEP.  Two kinds:
+ *
+ * RSRR_NEP_SPARSE: T(z) = sum_{i<m} fn[i](z) A_i.  All A_i share one CSR
+ * pattern (row_ptr, col_idx; columns need not be sorted; duplicates are not
+ * allowed); their real values are stored term-major: A_i's value for pattern
+ * entry e is values[i * nnz + e], nnz = row_ptr[n].  The half-bandwidths kl,
+ * ku are detected from the pattern (kl <= 480) and the band path is used.
+ *
+ * RSRR_NEP_HELMHOLTZ: the dense Nystrom single-layer kernel of Section 2.1,
+ * T(z)_ij = exp(i z r_ij) / (4 pi r_ij) for i != j and T_ii = diag, with
+ * r_ij the distances between the n points (points[3i..3i+2], row major);
+ * m, fn and the CSR fields are ignored.  The dense path is used, and the
+ * projection expands T in a Taylor series about the region centre
+ * (Section 5.2 interpolates T for the same purpose).
+ *
+ * All arrays are host memory and are copied by rsrr_create. */
+enum { RSRR_NEP_SPARSE = 0, RSRR_NEP_HELMHOLTZ = 1 };
+
 typedef struct {
     int64_t n;
-    int32_t m; /* 1 <= m <= RSRR_MAX_TERMS */
-    int32_t reserved;
+    int32_t m;    /* 1 <= m <= RSRR_MAX_TERMS (sparse kind) */
+    int32_t kind; /* RSRR_NEP_SPARSE or RSRR_NEP_HELMHOLTZ */
     const int64_t *row_ptr; /* host, n + 1 */
     const int32_t *col_idx; /* host, nnz */
     const double *values;   /* host, m * nnz */
     rsrr_fn fn[RSRR_MAX_TERMS];
+    const double *points;   /* host, 3n (Helmholtz kind) */
+    double diag;            /* T_ii (Helmholtz kind) */
 } rsrr_nep;
 
 /* Region.  The ellipse phi(t) = center + a cos t + i b sin t is the contour
@@ -235,7 +249,9 @@ rsrr_status rsrr_get_eta(rsrr_t *h, double *dst);
 rsrr_status rsrr_get_Q(rsrr_t *h, rsrr_c128 *dst, int32_t dst_on_device, void *stream);
 
 /* Copies P_0 ... P_{m-1} (m consecutive k x k column-major blocks) after
- * rsrr_project; same memory rules as rsrr_get_samples. */
+ * rsrr_project; same memory rules as rsrr_get_samples.  For the Helmholtz
+ * kind m is the number of Taylor terms (rsrr_stats.m): T_Q(z) =
+ * sum_p (z - center)^p P_p. */
 rsrr_status rsrr_get_projected(rsrr_t *h, rsrr_c128 *dst, int32_t dst_on_device, void *stream);
 
 /* Copies the N sampling points (host). */

@@ -23,6 +23,7 @@ UNITS = [
     ("proj.cu", [], "proj.o"),
     ("ssfull_host.cpp", ["-x", "cu"], "ssfull_host.o"),
     ("noalloc.cu", [], "noalloc.o"),
+    ("dense.cu", [], "dense.o"),
 ]
 
 

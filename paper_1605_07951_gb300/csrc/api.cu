@@ -41,6 +41,23 @@ cplx eval_fn_host(const rsrr_fn &f, cplx z) {
     return cplx(f.scale.re, f.scale.im) * base;
 }
 
+// complex normal entries (g1 + i g2)/sqrt(2) from splitmix64 + Box-Muller
+void default_probe(std::vector<double2> &U, size_t count) {
+    U.resize(count);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto next = [&st]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t q = 0; q < count; ++q) {
+        const double r = std::sqrt(-2.0 * std::log(next())), t = 2.0 * M_PI * next();
+        U[q] = make_double2(r * std::cos(t) / std::sqrt(2.0), r * std::sin(t) / std::sqrt(2.0));
+    }
+}
+
 rsrr_status Handle::fail(rsrr_status st, const char *what, cudaError_t e) {
     char buf[512];
     if (e != cudaSuccess)
@@ -114,6 +131,11 @@ static rsrr_status create_fail(const char *msg) {
     return RSRR_EINVAL;
 }
 
+namespace rsrr {
+rsrr_status create_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                         const rsrr_opts *opts, rsrr_t **out);
+}
+
 rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
                         const rsrr_opts *opts, rsrr_t **out) {
     if (!out) return create_fail("rsrr_create: out is NULL");
@@ -121,10 +143,13 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
     rsrr::thread_error().clear();
     if (!nep || !region) return create_fail("rsrr_create: nep or region is NULL");
     if (nep->n < 1 || nep->n > (int64_t)1 << 30) return create_fail("rsrr_create: n out of range");
+    if (N < 1 || L < 1) return create_fail("rsrr_create: N and L must be >= 1");
+    if (nep->kind != RSRR_NEP_SPARSE && nep->kind != RSRR_NEP_HELMHOLTZ)
+        return create_fail("rsrr_create: unknown NEP kind");
+    if (nep->kind == RSRR_NEP_HELMHOLTZ) return rsrr::create_dense(nep, region, N, L, opts, out);
     if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
     if (!nep->row_ptr || !nep->col_idx || !nep->values)
         return create_fail("rsrr_create: pattern or values NULL");
-    if (N < 1 || L < 1) return create_fail("rsrr_create: N and L must be >= 1");
     if (!(region->a > 0.0) || !(region->b > 0.0))
         return create_fail("rsrr_create: ellipse semi-axes must be > 0");
     if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS)
@@ -253,7 +278,7 @@ rsrr_status rsrr_set_probe(rsrr_t *hh, const rsrr_c128 *U, int32_t on_device, vo
 rsrr_status rsrr_sample(rsrr_t *hh, void *stream) {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h) return RSRR_EINVAL;
-    rsrr_status st = h->sample((cudaStream_t)stream);
+    rsrr_status st = h->dense ? h->sample_dense((cudaStream_t)stream) : h->sample((cudaStream_t)stream);
     if (st == RSRR_OK) { h->sampled = true; h->projected = false; }
     return st;
 }
@@ -395,22 +420,11 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     CK(cudaMemcpy(d_csc_row, h_csc_row.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
     CK(cudaMemcpy(d_csc_perm, h_csc_perm.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
     CK(cudaMemcpy(d_coef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice), "upload");
-    // default probe: complex normal entries from a fixed-seed generator
-    // (splitmix64 + Box-Muller); rsrr_set_probe replaces it
+    // default probe: complex normal entries from a fixed-seed generator;
+    // rsrr_set_probe replaces it
     {
-        std::vector<double2> U(nL);
-        uint64_t st = 0x9E3779B97F4A7C15ull;
-        auto next = [&st]() {
-            uint64_t z = (st += 0x9E3779B97F4A7C15ull);
-            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-            z ^= z >> 31;
-            return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-        };
-        for (size_t q = 0; q < nL; ++q) {
-            const double r = std::sqrt(-2.0 * std::log(next())), t = 2.0 * M_PI * next();
-            U[q] = make_double2(r * std::cos(t) / std::sqrt(2.0), r * std::sin(t) / std::sqrt(2.0));
-        }
+        std::vector<double2> U;
+        default_probe(U, nL);
         CK(cudaMemcpy(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice), "upload");
     }
     CK(launch_colmax(d_umax, d_U, (int)n, L, 0), "colmax");
@@ -523,6 +537,195 @@ rsrr_status Handle::read_outcome() {
         snprintf(buf, sizeof buf, "refinement stopped at max eta %.3e > %.1e", stat_max_eta, opts.eta_tol);
         return fail(RSRR_ENOCONV, buf);
     }
+    return RSRR_OK;
+}
+
+}  // namespace rsrr
+
+// ---------------------------------------------------------------------------
+// dense (Helmholtz kernel) problems
+// ---------------------------------------------------------------------------
+namespace rsrr {
+
+rsrr_status create_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                         const rsrr_opts *opts, rsrr_t **out) {
+    if (!nep->points) return create_fail("rsrr_create: Helmholtz kind without points");
+    if (!(std::isfinite(nep->diag))) return create_fail("rsrr_create: diag is not finite");
+    const int64_t n = nep->n;
+    if (n > 65536) return create_fail("rsrr_create: dense order above 65536");
+    const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
+    if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
+        return create_fail("rsrr_create: unknown precision");
+    Handle *h = new (std::nothrow) Handle();
+    if (!h) { thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
+    if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);
+    h->dense = true;
+    h->n = n; h->nnz = 0; h->N = N; h->L = L;
+    h->diag = nep->diag;
+    h->region = *region;
+    h->region.points = nullptr;
+    h->h_points.assign(nep->points, nep->points + 3 * n);
+    double rmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(h->h_points[3 * i]) || !std::isfinite(h->h_points[3 * i + 1]) ||
+            !std::isfinite(h->h_points[3 * i + 2])) {
+            delete h;
+            return create_fail("rsrr_create: point coordinates must be finite");
+        }
+        for (int64_t j = 0; j < i; ++j) {
+            const double dx = h->h_points[3 * i] - h->h_points[3 * j];
+            const double dy = h->h_points[3 * i + 1] - h->h_points[3 * j + 1];
+            const double dz = h->h_points[3 * i + 2] - h->h_points[3 * j + 2];
+            const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+            if (!(r > 0.0)) {
+                delete h;
+                return create_fail("rsrr_create: two points coincide");
+            }
+            rmax = std::max(rmax, r);
+        }
+    }
+    // Taylor terms: smallest P with (r_max rho)^P / P! < 1e-17
+    const double x = rmax * std::max(region->a, region->b);
+    int P = 0;
+    double term = 1.0;
+    while (term >= 1e-17 && P < 200) { ++P; term *= x / P; }
+    h->m = P;
+    h->z.resize(N);
+    for (int j = 0; j < N; ++j) {
+        if (region->kind == RSRR_REGION_POINTS) {
+            h->z[j] = cplx(region->points[j].re, region->points[j].im);
+        } else {
+            const double al = 2.0 * M_PI * (j + 0.5) / N;
+            h->z[j] = cplx(region->center.re + region->a * std::cos(al),
+                           region->center.im + region->b * std::sin(al));
+        }
+    }
+    rsrr_status st = h->allocate_dense();
+    if (st != RSRR_OK) {
+        thread_error() = h->err;
+        delete h;
+        return st;
+    }
+    *out = reinterpret_cast<rsrr_t *>(h);
+    return RSRR_OK;
+}
+
+rsrr_status Handle::allocate_dense() {
+    Handle *h = this;
+    const size_t nL = (size_t)n * L, NL = (size_t)N * L, nn2 = (size_t)n * n;
+    const bool mixed = opts.precision == RSRR_PREC_MIXED;
+    const int nb = mixed ? NB_C64 : NB_C128;
+    const size_t nblk = ((size_t)n + nb - 1) / nb;
+    CK(alloc(&d_points, 3 * n), "alloc");
+    CK(alloc(&d_z, N), "alloc");
+    CK(alloc(&d_U, nL), "alloc");
+    CK(alloc(&d_umax, L), "alloc");
+    CK(alloc(&d_X, nL * N), "alloc S");
+    CK(alloc(&d_R, nL * N), "alloc residual");
+    CK(alloc(&d_piv, (size_t)n * N), "alloc pivots");
+    CK(alloc(&d_info, N), "alloc");
+    CK(alloc(&d_tnorm, N), "alloc");
+    CK(alloc(&d_eta, NL), "alloc");
+    CK(alloc(&d_rmax, NL), "alloc");
+    CK(alloc(&d_xmax, NL), "alloc");
+    CK(alloc(&d_done, N), "alloc");
+    CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
+    CK(alloc(&d_T64, nn2 * N), "alloc dense matrices (complex128)");
+    if (mixed) {
+        CK(alloc(&d_A32, nn2 * N), "alloc dense factors (complex64)");
+        CK(alloc(&d_D, nL * N), "alloc correction");
+        CK(alloc(&d_dinv32, (size_t)N * nblk * 2 * nb * nb), "alloc block inverses");
+    } else {
+        CK(alloc(&d_ab64, nn2 * N), "alloc dense factors (complex128)");
+        CK(alloc(&d_dinv64, (size_t)N * nblk * 2 * nb * nb), "alloc block inverses");
+    }
+    std::vector<double2> zs(N);
+    for (int j = 0; j < N; ++j) zs[j] = make_double2(z[j].real(), z[j].imag());
+    CK(cudaMemcpy(d_points, h_points.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(d_z, zs.data(), sizeof(double2) * N, cudaMemcpyHostToDevice), "upload");
+    {
+        std::vector<double2> U;
+        default_probe(U, nL);
+        CK(cudaMemcpy(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice), "upload");
+    }
+    CK(launch_colmax(d_umax, d_U, (int)n, L, 0), "colmax");
+    CK(cudaDeviceSynchronize(), "create sync");
+    dp.n = n; dp.N = N; dp.L = L; dp.m = m; dp.U = d_U;
+    return RSRR_OK;
+}
+
+// R = U - T X in FP64 (stored complex128 T) and the column maxima of |R|, |X|,
+// for every point, or (skip_done) only for points whose done flag is 0 (the
+// flags are read on the host first).
+rsrr_status Handle::dense_residual(bool skip_done, cudaStream_t s) {
+    Handle *h = this;
+    std::vector<int32_t> done(N, 0);
+    if (skip_done) {
+        CK(cudaMemcpyAsync(done.data(), d_done, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s), "done");
+        CK(cudaStreamSynchronize(s), "done sync");
+    }
+    const size_t per = (size_t)n * L, nn2 = (size_t)n * n;
+    for (int pt = 0; pt < N; ++pt) {
+        if (done[pt]) continue;
+        CK(cudaMemcpyAsync(d_R + pt * per, d_U, sizeof(double2) * per, cudaMemcpyDeviceToDevice, s), "R = U");
+        CK(fp64_gemm((int)n, L, (int)n, false, d_T64 + pt * nn2, n, d_X + pt * per, n, d_R + pt * per, n,
+                     -1.0, 1.0, s), "R -= T X");
+        CK(launch_dense_colmax(d_R + pt * per, d_X + pt * per, (int)n, L, d_rmax + pt * L, d_xmax + pt * L, s),
+           "colmax");
+        launches += 2;
+    }
+    return RSRR_OK;
+}
+
+// Step 2 of RSRR for the dense kernel problem.
+rsrr_status Handle::sample_dense(cudaStream_t s) {
+    Handle *h = this;
+    const int nn = (int)n;
+    const int64_t per_pt = (int64_t)n * L, total = (int64_t)n * n * N;
+    rsrr_status ms;
+    if ((ms = mark(0, s)) != RSRR_OK) return ms;
+    CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
+    CK(launch_assemble_dense_c128(d_T64, d_points, d_z, diag, nn, N, s), "assemble");
+    CK(launch_dense_tnorm(d_tnorm, d_T64, nn, N, s), "tnorm");
+    launches += 2;
+    if (opts.precision == RSRR_PREC_MIXED) {
+        CK(launch_narrow_all(d_A32, d_T64, total, s), "narrow");
+        launches += 1;
+        if ((ms = mark(1, s)) != RSRR_OK) return ms;
+        CK(launch_dense_lu_c64(d_A32, d_piv, d_info, d_dinv32, nn, N, s, &launches), "dense LU");
+        if ((ms = mark(2, s)) != RSRR_OK) return ms;
+        CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
+        CK(launch_dense_solve_c64(d_A32, d_piv, d_dinv32, d_D, nn, N, L, nullptr, s), "dense solve");
+        CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
+        CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
+        launches += 3;
+        if ((ms = mark(3, s)) != RSRR_OK) return ms;
+        for (int it = 0; it < opts.max_refine; ++it) {
+            if ((ms = dense_residual(true, s)) != RSRR_OK) return ms;
+            CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
+                          d_sweep_flags + it, d_done, s), "eta");
+            CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
+            CK(launch_dense_solve_c64(d_A32, d_piv, d_dinv32, d_D, nn, N, L, d_done, s), "dense solve");
+            CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
+            launches += 4;
+        }
+    } else {
+        CK(cudaMemcpyAsync(d_ab64, d_T64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s), "copy");
+        if ((ms = mark(1, s)) != RSRR_OK) return ms;
+        CK(launch_dense_lu_c128(d_ab64, d_piv, d_info, d_dinv64, nn, N, s, &launches), "dense LU");
+        if ((ms = mark(2, s)) != RSRR_OK) return ms;
+        CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
+        CK(launch_dense_solve_c128(d_ab64, d_piv, d_dinv64, d_X, nn, N, L, nullptr, s), "dense solve");
+        launches += 2;
+        if ((ms = mark(3, s)) != RSRR_OK) return ms;
+    }
+    if ((ms = mark(4, s)) != RSRR_OK) return ms;
+    if ((ms = dense_residual(false, s)) != RSRR_OK) return ms;
+    CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
+                  d_sweep_flags + opts.max_refine + 1, nullptr, s), "eta");
+    launches += 1;
+    if ((ms = mark(5, s)) != RSRR_OK) return ms;
+    timed_sample = opts.timing != 0;
     return RSRR_OK;
 }
 

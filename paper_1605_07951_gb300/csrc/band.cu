@@ -394,6 +394,13 @@ __global__ void broadcast_probe_kernel(C *__restrict__ D, const double2 *__restr
         store_c(D + q, U[q % nL]);
 }
 
+// D = (c64) S for a whole array
+__global__ void narrow_all_kernel(float2 *__restrict__ D, const double2 *__restrict__ S, int64_t total) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        D[q] = to_c64(S[q]);
+}
+
 // X = (c128) D for all points
 __global__ void widen_kernel(double2 *__restrict__ X, const float2 *__restrict__ D, int64_t total) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -526,6 +533,10 @@ cudaError_t launch_broadcast_probe_c128(double2 *D, const double2 *U, int64_t nL
 }
 cudaError_t launch_widen(double2 *X, const float2 *D, int64_t total, cudaStream_t s) {
     widen_kernel<<<grid_for(total, 256), 256, 0, s>>>(X, D, total);
+    return cudaGetLastError();
+}
+cudaError_t launch_narrow_all(float2 *D, const double2 *S, int64_t total, cudaStream_t s) {
+    narrow_all_kernel<<<grid_for(total, 256), 256, 0, s>>>(D, S, total);
     return cudaGetLastError();
 }
 cudaError_t launch_narrow(float2 *D, const double2 *R, int64_t per_pt, int N, const int32_t *skip,

@@ -197,6 +197,12 @@ struct Gemm {
     }
 };
 
+cudaError_t fp64_gemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda, const double2 *B,
+                      int64_t ldb, double2 *C, int64_t ldc, double alpha, double beta, cudaStream_t s) {
+    Gemm g;  // no work space: always the direct path
+    return g.run(M, N, K, conjA, A, lda, B, ldb, C, ldc, s, false, alpha, beta);
+}
+
 // ==========================================================================
 // column norms and scalings
 // ==========================================================================
@@ -461,8 +467,9 @@ RSRR_DEV void jacobi_round(const double2 *__restrict__ Hold, double2 *__restrict
 
 // Whole cyclic Jacobi in one cooperative launch: Y = I, then sweeps of
 // kp-1 rounds (grid barrier after each), convergence test after each sweep
-// (off(H)^2 <= tol2 * diag(H)^2 from per-sweep atomic sums in acc, zeroed by
-// the host).  The final matrix is copied back into H0.  state[0] = sweeps run.
+// (off(H)^2 <= tol2 * diag(H)^2 from per-CTA partial sums in acc, one slot
+// pair per CTA, added in CTA order).  The final matrix is copied back into
+// H0.  state[0] = sweeps run.
 __global__ void __launch_bounds__(256)
 jacobi_persistent_kernel(double2 *__restrict__ H0, double2 *__restrict__ H1,
                          double2 *__restrict__ Y, int k, int max_sweeps, double tol2,
@@ -491,18 +498,30 @@ jacobi_persistent_kernel(double2 *__restrict__ H0, double2 *__restrict__ H1,
                 const double m2 = v.x * v.x + v.y * v.y;
                 if ((q % k) == (q / k)) dia += m2; else off += m2;
             }
+            // deterministic reduction: per-CTA partials in fixed slots, summed
+            // in CTA order by every CTA after the barrier
+            __shared__ double s_off[8], s_dia[8];
             for (int o = 16; o; o >>= 1) {
                 off += shfl_down(off, o);
                 dia += shfl_down(dia, o);
             }
-            if ((threadIdx.x & 31) == 0) {
-                atomicAdd(acc + 2 * sw, off);
-                atomicAdd(acc + 2 * sw + 1, dia);
+            if ((threadIdx.x & 31) == 0) { s_off[threadIdx.x >> 5] = off; s_dia[threadIdx.x >> 5] = dia; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double a = 0.0, b2 = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_off[w]; b2 += s_dia[w]; }
+                acc[2 * blockIdx.x] = a;
+                acc[2 * blockIdx.x + 1] = b2;
             }
             if (!grid_sync(bar, gridDim.x)) return;
-            const double o2 = *((volatile double *)(acc + 2 * sw));
-            const double d2 = *((volatile double *)(acc + 2 * sw + 1));
-            if (o2 <= tol2 * d2) break;
+            double o2 = 0.0, d2 = 0.0;
+            for (int c = 0; c < (int)gridDim.x; ++c) {
+                o2 += *((volatile double *)(acc + 2 * c));
+                d2 += *((volatile double *)(acc + 2 * c + 1));
+            }
+            const bool done = o2 <= tol2 * d2;
+            if (!grid_sync(bar, gridDim.x)) return;  // acc is rewritten next sweep
+            if (done) break;
         }
     }
     if (a != H0) {
@@ -621,11 +640,11 @@ static cudaError_t launch_coop(K kern, int cap, cudaStream_t s, Args... args) {
 static cudaError_t jacobi_eig(ProjWs &ws, int k, cudaStream_t s, int64_t *counter,
                               int max_sweeps = 30) {
     cudaError_t e = cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws.jacc, 0, sizeof(double) * 2 * max_sweeps, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.jacc, 0, sizeof(double) * 2 * 4096, s);
     if (e != cudaSuccess) return e;
     const double tol2 = 1e-30;  // off(H) <= 1e-15 ||diag(H)||
     const int64_t work = (int64_t)(k + 1) / 2 * ((k + 1) / 2) + (int64_t)k * ((k + 1) / 2);
-    e = launch_coop(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, 1 << 20), s,
+    e = launch_coop(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, 4096), s,
                     ws.H, ws.H2, ws.Y, k, max_sweeps, tol2, ws.jacc, ws.state + 1, ws.bar);
     if (e != cudaSuccess) return e;
     sort_desc_kernel<<<1, 256, 0, s>>>(ws.H, k, ws.order, ws.evals);
@@ -688,7 +707,7 @@ __global__ void max_vec_kernel(double *__restrict__ out, const double *__restric
 }
 
 // Workspace layout of the projection stage (carved from one allocation).
-static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n) {
+static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n, int terms) {
     const size_t NL2 = (size_t)NL * NL;
     ws.norms = carve<double>(cp, NL);
     ws.G = carve<double2>(cp, NL2);
@@ -706,20 +725,20 @@ static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n) {
     ws.W = carve<double2>(cp, NL2);
     ws.C = carve<double2>(cp, NL2);
     ws.bar = carve<unsigned int>(cp, 4);
-    ws.jacc = carve<double>(cp, 64);
+    ws.jacc = carve<double>(cp, 2 * 4096);
     ws.Q1 = carve<double2>(cp, (size_t)n * NL);
     ws.Ytmp = carve<double2>(cp, (size_t)n * NL);
     ws.gws_elems = std::max<size_t>(NL2 * 4, (size_t)8 << 20);
     ws.gws = carve<double2>(cp, ws.gws_elems);
     ws.Qall = carve<double2>(cp, (size_t)n * NL);
-    ws.P = carve<double2>(cp, (size_t)RSRR_MAX_TERMS * NL2);
+    ws.P = carve<double2>(cp, (size_t)std::max(terms, RSRR_MAX_TERMS) * NL2);
     ws.end = cp;
 }
 
-static size_t ws_bytes(int NL, int64_t n) {
+static size_t ws_bytes(int NL, int64_t n, int terms) {
     ProjWs ws;
     char *base = reinterpret_cast<char *>((uintptr_t)0);
-    carve_ws(base, ws, NL, n);
+    carve_ws(base, ws, NL, n, terms);
     return (size_t)(ws.end - base);
 }
 
@@ -738,7 +757,7 @@ rsrr_status Handle::project(cudaStream_t s) {
     const int NL = N * L;
     const int64_t nn = n;
     if (!proj_ws) {
-        const size_t bytes = ws_bytes(NL, nn);
+        const size_t bytes = ws_bytes(NL, nn, m);
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) return fail(RSRR_ENOMEM, "projection work space", e);
@@ -748,7 +767,7 @@ rsrr_status Handle::project(cudaStream_t s) {
         proj_ws_bytes = bytes;
     }
     ProjWs ws;
-    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, nn);
+    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, nn, m);
     d_Q = ws.Qall;
     d_P = ws.P;
     Gemm gm;
@@ -872,8 +891,19 @@ rsrr_status Handle::project(cudaStream_t s) {
     sigma1 = std::sqrt(s1sq);
     sigmak = std::sqrt(std::max(smallest, 0.0));
 
-    // (A10) P_q = Q^H (A_q Q)
-    for (int q = 0; q < m; ++q) {
+    // (A10) P_q = Q^H (A_q Q); for the dense kernel the A_p are the Taylor
+    // coefficients about the region centre, generated in place one after the
+    // other in the (now free) complex128 matrix storage of the first point
+    if (dense) {
+        const double2 c = make_double2(region.center.re, region.center.im);
+        for (int q = 0; q < m; ++q) {
+            PK(launch_taylor_step(d_T64, d_points, c, diag, (int)nn, q, s), "Taylor coefficient");
+            PK(gm.run((int)nn, k, (int)nn, false, d_T64, nn, d_Q, nn, ws.Ytmp, nn, s), "A_p Q");
+            PK(gm.run(k, k, (int)nn, true, d_Q, nn, ws.Ytmp, nn, d_P + (size_t)q * k * k, k, s), "Q^H A_p Q");
+            launches += 1;
+        }
+    }
+    for (int q = 0; q < m && !dense; ++q) {
         dim3 grid((unsigned)((nn + 127) / 128), k);
         spmm_kernel<<<grid, 128, 0, s>>>(ws.Ytmp, d_Q, d_row_ptr, d_col_idx, d_vals + (size_t)q * nnz,
                                          (int)nn, k);
@@ -990,7 +1020,15 @@ rsrr_status Handle::solve(rsrr_result *out) {
     std::vector<cplx> lam, G;
     int nbar = 0;
     double gmax = 0.0;
-    auto f = [this](int i, cplx z) { return eval_fn_host(fn[i], z); };
+    const cplx cen(region.center.re, region.center.im);
+    auto f = [this, cen](int i, cplx z) {
+        if (dense) {  // Taylor powers (z - c)^i
+            cplx r = 1.0;
+            for (int q = 0; q < i; ++q) r *= (z - cen);
+            return r;
+        }
+        return eval_fn_host(fn[i], z);
+    };
     const cplx gamma(region.center.re, region.center.im);
     if (ss_full_host(P, k, f, m, gamma, region.a, region.b, opts.NQ, opts.KQ, opts.host_threads,
                      lam, G, nbar, gmax) != 0)
@@ -998,7 +1036,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
     // v = Q g on the GPU
     ProjWs ws;
     const int NL = N * L;
-    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, n);
+    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, n, m);
     Gemm gm;
     gm.ws = ws.gws;
     gm.ws_elems = ws.gws_elems;
@@ -1007,7 +1045,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
     // buffer of their own (nbar may exceed the sample count)
     const size_t gbytes = sizeof(double2) * (size_t)k * nbar;
     const size_t vbytes = sizeof(double2) * (size_t)n * nbar;
-    const size_t cbytes = sizeof(double2) * (size_t)nbar * m;
+    const size_t cbytes = sizeof(double2) * (size_t)nbar * std::max(m, 2);
     void *buf = nullptr;
     PK(cudaMalloc(&buf, gbytes + vbytes + cbytes + sizeof(double) * 2 * nbar), "solve buffers");
     struct Free { void *p; ~Free() { cudaFree(p); } } guard{buf};
@@ -1018,18 +1056,32 @@ rsrr_status Handle::solve(rsrr_result *out) {
     double *d_vv = d_rr + nbar;
     PK(cudaMemcpy(d_G, G.data(), gbytes, cudaMemcpyHostToDevice), "G");
     PK(gm.run((int)n, nbar, k, false, d_Q, n, d_G, k, d_V, n, s), "Q G");
-    std::vector<double2> cf((size_t)nbar * m);
-    for (int c = 0; c < nbar; ++c)
-        for (int q = 0; q < m; ++q) {
-            const cplx v = eval_fn_host(fn[q], lam[c]);
-            cf[(size_t)c * m + q] = make_double2(v.real(), v.imag());
-        }
-    PK(cudaMemcpy(d_cf, cf.data(), cbytes, cudaMemcpyHostToDevice), "coef");
-    PK(cudaMemset(d_rr, 0, sizeof(double) * 2 * nbar), "memset");
-    eig_residual_kernel<<<dim3((unsigned)((n + 255) / 256), nbar), 256>>>(
-        d_V, d_cf, d_row_ptr, d_col_idx, d_vals, nnz, m, (int)n, d_rr, d_vv);
-    PK(cudaGetLastError(), "eig residual");
-    launches += 1;
+    std::vector<double> t1(nbar, 0.0);
+    if (dense) {
+        std::vector<double2> lz(nbar);
+        for (int c = 0; c < nbar; ++c) lz[c] = make_double2(lam[c].real(), lam[c].imag());
+        PK(cudaMemcpy(d_cf, lz.data(), sizeof(double2) * nbar, cudaMemcpyHostToDevice), "lam");
+        PK(cudaMemset(d_rr, 0, sizeof(double) * 2 * nbar), "memset");
+        double *d_t1 = reinterpret_cast<double *>(d_cf + nbar);
+        PK(cudaMemset(d_t1, 0, sizeof(double) * nbar), "memset");
+        PK(launch_dense_eig_residual(d_V, d_cf, d_points, diag, (int)n, nbar, d_rr, d_vv, d_t1, s),
+           "dense eig residual");
+        PK(cudaMemcpy(t1.data(), d_t1, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "t1");
+        launches += 1;
+    } else {
+        std::vector<double2> cf((size_t)nbar * m);
+        for (int c = 0; c < nbar; ++c)
+            for (int q = 0; q < m; ++q) {
+                const cplx v = eval_fn_host(fn[q], lam[c]);
+                cf[(size_t)c * m + q] = make_double2(v.real(), v.imag());
+            }
+        PK(cudaMemcpy(d_cf, cf.data(), sizeof(double2) * cf.size(), cudaMemcpyHostToDevice), "coef");
+        PK(cudaMemset(d_rr, 0, sizeof(double) * 2 * nbar), "memset");
+        eig_residual_kernel<<<dim3((unsigned)((n + 255) / 256), nbar), 256>>>(
+            d_V, d_cf, d_row_ptr, d_col_idx, d_vals, nnz, m, (int)n, d_rr, d_vv);
+        PK(cudaGetLastError(), "eig residual");
+        launches += 1;
+    }
     std::vector<double> rr(nbar), vv(nbar);
     std::vector<cplx> V((size_t)n * nbar);
     PK(cudaMemcpy(rr.data(), d_rr, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "rr");
@@ -1037,7 +1089,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
     PK(cudaMemcpy(V.data(), d_V, sizeof(double2) * V.size(), cudaMemcpyDeviceToHost), "V");
     // ||A_i||_1 (max column sum) on the host
     std::vector<double> a1(m, 0.0);
-    for (int q = 0; q < m; ++q) {
+    for (int q = 0; q < m && !dense; ++q) {
         std::vector<double> colsum(n, 0.0);
         for (int64_t e = 0; e < nnz; ++e) colsum[h_col_idx[e]] += std::fabs(h_vals[(size_t)q * nnz + e]);
         for (double v : colsum) a1[q] = std::max(a1[q], v);
@@ -1049,7 +1101,9 @@ rsrr_status Handle::solve(rsrr_result *out) {
         const double y = (lam[c].imag() - region.center.im) / region.b;
         if (!(x * x + y * y < 1.0)) continue;
         double scale = 0.0;
-        for (int q = 0; q < m; ++q) scale += std::abs(eval_fn_host(fn[q], lam[c])) * a1[q];
+        if (dense) scale = t1[c];  // ||T(lam)||_1 computed directly
+        else
+            for (int q = 0; q < m; ++q) scale += std::abs(eval_fn_host(fn[q], lam[c])) * a1[q];
         const double res = std::sqrt(rr[c]) / (scale * std::sqrt(vv[c]));
         if (!(res <= opts.res_tol)) continue;
         keep.push_back({lam[c], res, c});

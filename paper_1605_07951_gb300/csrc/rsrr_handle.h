@@ -24,7 +24,14 @@ struct Handle {
     std::vector<std::complex<double>> z;
     std::vector<int32_t> h_row_ptr, h_col_idx, h_csc_ptr, h_csc_row, h_csc_perm;
     std::vector<double> h_vals;
-
+    // dense (Helmholtz kernel) problems
+    bool dense = false;
+    double diag = 0.0;
+    std::vector<double> h_points;
+    double *d_points = nullptr;       // 3n
+    double2 *d_z = nullptr;           // N sampling points
+    double2 *d_T64 = nullptr;         // N dense complex128 matrices (residuals)
+    float2 *d_A32 = nullptr;          // N dense complex64 factors
     // device buffers (owned)
     std::vector<void *> allocations;
     size_t device_bytes = 0;
@@ -76,6 +83,9 @@ struct Handle {
     template <typename T> cudaError_t alloc(T **p, size_t count);
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);
     rsrr_status sample(cudaStream_t s);
+    rsrr_status sample_dense(cudaStream_t s);
+    rsrr_status dense_residual(bool skip_done, cudaStream_t s);
+    rsrr_status allocate_dense();
     rsrr_status read_outcome();
     rsrr_status mark(int i, cudaStream_t s);
     rsrr_status project(cudaStream_t s);

@@ -64,4 +64,32 @@ cudaError_t launch_narrow(float2 *D, const double2 *R, int64_t per_pt, int N, co
 cudaError_t launch_update(double2 *X, const float2 *D, int64_t per_pt, int N, const int32_t *skip,
                           cudaStream_t s);
 
+// ---- dense kernel path (dense.cu)
+cudaError_t launch_assemble_dense_c64(float2 *A, const double *pts, const double2 *zs, double diag,
+                                      int n, int N, cudaStream_t s);
+cudaError_t launch_assemble_dense_c128(double2 *A, const double *pts, const double2 *zs, double diag,
+                                       int n, int N, cudaStream_t s);
+cudaError_t launch_dense_tnorm(double *tnorm, const double2 *A, int n, int N, cudaStream_t s);
+cudaError_t launch_dense_lu_c64(float2 *A, int32_t *piv, int32_t *info, float2 *dinv, int n, int N,
+                                cudaStream_t s, int64_t *launches);
+cudaError_t launch_dense_lu_c128(double2 *A, int32_t *piv, int32_t *info, double2 *dinv, int n, int N,
+                                 cudaStream_t s, int64_t *launches);
+cudaError_t launch_dense_solve_c64(const float2 *A, const int32_t *piv, const float2 *dinv, float2 *B,
+                                   int n, int N, int L, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_dense_solve_c128(const double2 *A, const int32_t *piv, const double2 *dinv,
+                                    double2 *B, int n, int N, int L, const int32_t *skip,
+                                    cudaStream_t s);
+cudaError_t launch_dense_colmax(const double2 *R, const double2 *X, int n, int L, double *rmax,
+                                double *xmax, cudaStream_t s);
+cudaError_t launch_taylor_step(double2 *A, const double *pts, double2 c, double diag, int n, int p,
+                               cudaStream_t s);
+cudaError_t launch_dense_eig_residual(const double2 *V, const double2 *lam, const double *pts,
+                                      double diag, int n, int cnt, double *rr, double *vv, double *t1,
+                                      cudaStream_t s);
+cudaError_t launch_narrow_all(float2 *D, const double2 *S, int64_t total, cudaStream_t s);
+
+// ---- FP64 GEMM of proj.cu without split-K: C = alpha op(A) B + beta C
+cudaError_t fp64_gemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda, const double2 *B,
+                      int64_t ldb, double2 *C, int64_t ldc, double alpha, double beta, cudaStream_t s);
+
 }  // namespace rsrr

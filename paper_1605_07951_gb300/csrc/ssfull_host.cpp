@@ -31,17 +31,17 @@ struct Mat {
 };
 
 void parallel_for(int count, int threads, const std::function<void(int, int)> &fn) {
-    // fn(index, worker)
+    // fn(index, worker); worker w takes indices w, w + threads, ... so that
+    // per-worker partial sums (and their rounding) do not depend on timing
     threads = std::max(1, std::min(threads, count));
     if (threads == 1) {
         for (int i = 0; i < count; ++i) fn(i, 0);
         return;
     }
-    std::atomic<int> next(0);
     std::vector<std::thread> pool;
     for (int w = 0; w < threads; ++w)
         pool.emplace_back([&, w]() {
-            for (int i = next++; i < count; i = next++) fn(i, w);
+            for (int i = w; i < count; i += threads) fn(i, w);
         });
     for (auto &t : pool) t.join();
 }

@@ -28,6 +28,7 @@ RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7
 RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = range(6)
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
+RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ = 0, 1
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",
                 -5: "ETIMEOUT", -6: "ECUDA", -7: "ESTATE", 1: "WGAP"}
@@ -44,9 +45,10 @@ class rsrr_fn(C.Structure):
 
 
 class rsrr_nep(C.Structure):
-    _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("kind", C.c_int32),
                 ("row_ptr", C.POINTER(C.c_int64)), ("col_idx", C.POINTER(C.c_int32)),
-                ("values", C.POINTER(C.c_double)), ("fn", rsrr_fn * RSRR_MAX_TERMS)]
+                ("values", C.POINTER(C.c_double)), ("fn", rsrr_fn * RSRR_MAX_TERMS),
+                ("points", C.POINTER(C.c_double)), ("diag", C.c_double)]
 
 
 class rsrr_region(C.Structure):
@@ -139,9 +141,10 @@ def default_opts(**kw) -> rsrr_opts:
 
 
 class Solver:
-    """Owns one rsrr_t handle built from a problem description with fields
-    n, row_ptr, col_idx, values (list of m arrays), fns (kind, param, scale),
-    region (center, a, b, kind, points), N, L."""
+    """Owns one rsrr_t handle built from a problem description: either
+    n, row_ptr, col_idx, values (list of m arrays), fns (kind, param, scale)
+    for T(z) = sum_i f_i(z) A_i, or n, points (n x 3), diag for the dense
+    Helmholtz kernel; plus region (center, a, b, kind, points), N, L."""
 
     def __init__(self, prob, opts: rsrr_opts | None = None, N: int | None = None,
                  L: int | None = None):
@@ -149,19 +152,27 @@ class Solver:
         self.N = int(N if N is not None else prob.N)
         self.L = int(L if L is not None else prob.L)
         self.n = int(prob.n)
-        self._row_ptr = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
-        self._col_idx = np.ascontiguousarray(prob.col_idx, dtype=np.int32)
-        self._values = np.ascontiguousarray(np.concatenate(
-            [np.asarray(v, dtype=np.float64) for v in prob.values]))
         nep = rsrr_nep()
         nep.n = self.n
-        nep.m = len(prob.values)
-        nep.row_ptr = self._row_ptr.ctypes.data_as(C.POINTER(C.c_int64))
-        nep.col_idx = self._col_idx.ctypes.data_as(C.POINTER(C.c_int32))
-        nep.values = self._values.ctypes.data_as(C.POINTER(C.c_double))
-        for i, fn in enumerate(prob.fns):
-            sc = complex(fn.scale)
-            nep.fn[i] = rsrr_fn(int(fn.kind), 0, float(fn.param), rsrr_c128(sc.real, sc.imag))
+        self.dense = getattr(prob, "points", None) is not None and not hasattr(prob, "row_ptr")
+        if self.dense:
+            self._points = np.ascontiguousarray(np.asarray(prob.points, dtype=np.float64))
+            nep.kind = RSRR_NEP_HELMHOLTZ
+            nep.points = self._points.ctypes.data_as(C.POINTER(C.c_double))
+            nep.diag = float(prob.diag)
+        else:
+            self._row_ptr = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
+            self._col_idx = np.ascontiguousarray(prob.col_idx, dtype=np.int32)
+            self._values = np.ascontiguousarray(np.concatenate(
+                [np.asarray(v, dtype=np.float64) for v in prob.values]))
+            nep.kind = RSRR_NEP_SPARSE
+            nep.m = len(prob.values)
+            nep.row_ptr = self._row_ptr.ctypes.data_as(C.POINTER(C.c_int64))
+            nep.col_idx = self._col_idx.ctypes.data_as(C.POINTER(C.c_int32))
+            nep.values = self._values.ctypes.data_as(C.POINTER(C.c_double))
+            for i, fn in enumerate(prob.fns):
+                sc = complex(fn.scale)
+                nep.fn[i] = rsrr_fn(int(fn.kind), 0, float(fn.param), rsrr_c128(sc.real, sc.imag))
         reg = rsrr_region()
         r = prob.region
         reg.center = rsrr_c128(complex(r.center).real, complex(r.center).imag)
@@ -257,8 +268,8 @@ class Solver:
         return Q.T
 
     def projected(self, out=None, stream=None):
-        k = self.stats()["k"]
-        m = len(self.prob.values)
+        st = self.stats()
+        k, m = st["k"], st["m"]
         if out is not None:
             self._check(rsrr_get_projected(self.h, _ptr(out), 1, _stream_handle(stream)))
             return out

@@ -1,0 +1,68 @@
+"""GPU parity of the dense kernel path (T(z)_ij = exp(i z r_ij)/(4 pi r_ij)):
+samples X_j = T(z_j)^{-1} U, the Taylor projection P_p = Q^H A_p Q and the
+eigenpairs, through the C ABI, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from util import match_eigs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1605_07951_gb300 import rsrr
+    return rsrr
+
+
+@pytest.mark.parametrize("n,N,L,prec", [(256, 6, 8, "mixed"), (300, 4, 5, "mixed"),
+                                        (70, 3, 3, "mixed"), (256, 4, 8, "fp64")])
+def test_dense_samples_match_oracle(rs, n, N, L, prec):
+    p = W.helmholtz_sphere(n=n, N=N, L=L)
+    o = rs.default_opts(precision=rs.RSRR_PREC_MIXED if prec == "mixed" else rs.RSRR_PREC_FP64)
+    s = rs.Solver(p, o)
+    s.sample()
+    assert s.check_status() == rs.RSRR_OK
+    S, eta, z = s.samples(), s.eta(), s.points()
+    s.close()
+    zo = oracle.sample_points(p.region, p.N)
+    assert np.abs(z - zo).max() <= 1e-13 * np.abs(zo).max()
+    ref = oracle.resolvent_samples_dense(p, zo)
+    tol_eta = 1e-10 if prec == "mixed" else 1e-14
+    for j, Xr in enumerate(ref):
+        Xg = S[:, j * L:(j + 1) * L]
+        e = oracle.backward_error_inf_dense(p, zo[j], Xg)
+        assert e.max() <= tol_eta
+        assert np.allclose(eta[j * L:(j + 1) * L], e, rtol=1e-3, atol=max(1e-3 * tol_eta, 1e-14))
+        assert np.abs(Xg - Xr).max() <= (1e-6 if prec == "mixed" else 1e-9) * np.abs(Xr).max()
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_dense_eigenpairs_match_oracle(rs, n):
+    p = W.helmholtz_sphere(n=n, N=32, L=16)
+    ref = oracle.rsrr_dense(p, NQ=256)
+    s = rs.Solver(p, rs.default_opts(NQ=256))
+    s.sample()
+    s.check()
+    s.project()
+    out = s.solve()
+    Q = s.Q()
+    P = s.projected()
+    st = s.stats()
+    s.close()
+    assert len(out["lam"]) == len(ref["lam"]) > 0
+    assert match_eigs(ref["lam"], out["lam"]) <= 1e-9
+    assert out["res"].max() <= 1e-10
+    for lam, v in zip(out["lam"], out["V"].T):
+        assert oracle.residual_dense(p, lam, v) <= 1e-10
+    # projected Taylor coefficients equal Q^H A_p Q for the GPU's own Q
+    A = oracle.taylor_coefficients(p)
+    assert st["m"] == len(A)
+    for q in (0, 1, 5, len(A) - 1):
+        Pr = Q.conj().T @ A[q] @ Q
+        assert np.abs(P[q] - Pr).max() <= 1e-12 * max(np.abs(A[q]).sum(axis=0).max(), 1e-300)
