@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2"],
+                    help="c1: banded grid (the benchmark line); c2: dense kernel, sampling only")
     ap.add_argument("--sample-points", type=int, default=2,
                     help="sampling points of the oracle's bounded sample")
     return ap.parse_args()
@@ -353,9 +355,45 @@ def run_reference(a, rank, world):
     print(json.dumps(line))
 
 
+def run_dense(a):
+    """Dense kernel workload (n = 4096 points on the unit sphere, N = 32,
+    L = 64): rsrr_sample timed alone (the projection of this workload is
+    dominated by FP64 Taylor products and is not part of the benchmark line)."""
+    import torch
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    torch.cuda.set_device(0)
+    p = W.helmholtz_sphere(n=4096, N=32, L=64)
+    s = rsrr.Solver(p, rsrr.default_opts(timing=1))
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        s.sample(stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        s.sample(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    st = s.stats()
+    s.close()
+    n = p.n
+    lu_flops = 8.0 / 3.0 * n ** 3 * p.N
+    print(json.dumps({"workload": "helmholtz_sphere_n4096_N32_L64", "metric": UNIT,
+                      "sample_value": p.N * p.L / (ms / 1e3), "ms_per_sample": ms,
+                      "stage_ms": st["stage_ms"][:5], "refine_sweeps": st["refine_sweeps"],
+                      "max_eta": st["max_eta"],
+                      "dense_lu_tflops": lu_flops / (st["stage_ms"][1] / 1e3) / 1e12}))
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
+    if a.workload == "c2":
+        run_dense(a)
+        return
     if a.impl == "reference":
         run_reference(a, rank, world)
         return
