@@ -146,6 +146,18 @@ typedef struct {
  *                    <= eta_tol or max_refine sweeps have run.            */
 enum { RSRR_PREC_FP64 = 0, RSRR_PREC_MIXED = 1 };
 
+/* Arithmetic of the projection's dense complex products (Gram matrices of S,
+ * Q^H R, R W, Q^H A_i Q; Section 3.3's orthonormalisation and projection).
+ *   RSRR_GEMM_FP64   native FP64 fused multiply-adds.
+ *   RSRR_GEMM_OZAKI  FP64-accurate products on the bf16 tensor cores: both
+ *                    operands are scaled per row / column by powers of two,
+ *                    rounded to 55-bit fixed point and split into 7 signed
+ *                    8-bit slices; slice products are summed exactly in FP32
+ *                    groups and combined in 64-bit integers (Ozaki scheme).
+ *                    Error per entry below 2^-52 max|a_i.| max|b_.j| K.
+ *   RSRR_GEMM_AUTO   OZAKI for products of at least 2^30 flops, else FP64. */
+enum { RSRR_GEMM_AUTO = 0, RSRR_GEMM_FP64 = 1, RSRR_GEMM_OZAKI = 2 };
+
 typedef struct {
     int32_t precision;   /* RSRR_PREC_MIXED by default */
     int32_t max_refine;  /* refinement sweeps, default 8 */
@@ -159,6 +171,8 @@ typedef struct {
     int32_t host_threads;/* threads of rsrr_solve, 0 = all cores */
     int32_t timing;      /* nonzero: record CUDA events around every stage on the
                             caller's stream; times appear in rsrr_stats.stage_ms */
+    int32_t gemm;        /* RSRR_GEMM_AUTO by default */
+    int32_t reserved;
 } rsrr_opts;
 
 typedef struct rsrr_handle rsrr_t;
@@ -183,6 +197,10 @@ typedef struct {
      * FP64 GEMMs (8 per complex multiply-add, unique entries only for the
      * Hermitian products) and their summed device time */
     double gemm_flops, gemm_ms;
+    /* with opts.timing, for the last rsrr_project: bf16 tensor-core flops
+     * issued by the sliced (RSRR_GEMM_OZAKI) products' main kernel and the
+     * summed device time of that kernel alone */
+    double tc_flops, tc_ms;
 } rsrr_stats;
 
 /* Result of rsrr_solve.  Arrays are host memory owned by the handle, valid
@@ -295,6 +313,28 @@ void rsrr_destroy(rsrr_t *h);
  * them one after another. */
 rsrr_status rsrr_solve_band_noalloc(int64_t n, int32_t kl, int32_t ku, const rsrr_c128 *band,
                                     int32_t L, const rsrr_c128 *U, rsrr_c128 *X, void *stream);
+
+/* One dense complex product C = alpha op(A) B + beta C on the device, by the
+ * method the projection uses (Section 3.3's Gram matrices and Q^H A_i Q are
+ * such products); exposed so that callers and tests can use or check it alone.
+ *   M, N, K    op(A) is M x K, B is K x N, C is M x N
+ *   conjA      0: op(A) = A (M x K),  1: op(A) = A^H (A is K x M)
+ *   A, B, C    device, column major with leading dimensions lda, ldb, ldc;
+ *              C may not alias A or B
+ *   alpha, beta  real scalars; beta = 0 ignores the contents of C
+ *   method     RSRR_GEMM_FP64, RSRR_GEMM_OZAKI or RSRR_GEMM_AUTO
+ *   hermitian  nonzero with conjA, A == B, lda == ldb, M == N: the result is
+ *              Hermitian; only its upper block triangle is computed and the
+ *              rest mirrored (beta must be 0)
+ *   max_ws_bytes  0: work space for the whole product; else its upper bound
+ *              (the product then runs in chunks of K)
+ *   stream     work is queued on it; the call waits for it before returning
+ * Work space is allocated and freed inside the call.  Returns OK, EINVAL,
+ * ENOMEM (work space) or ECUDA; the message is in rsrr_last_error(NULL). */
+rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsrr_c128 *A,
+                       int64_t lda, const rsrr_c128 *B, int64_t ldb, rsrr_c128 *C, int64_t ldc,
+                       double alpha, double beta, int32_t method, int32_t hermitian,
+                       size_t max_ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,7 @@ UNITS = [
     ("ssfull_host.cpp", ["-x", "cu"], "ssfull_host.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("dense.cu", [], "dense.o"),
+    ("ozaki.cu", [], "ozaki.o"),
 ]
 
 

@@ -83,21 +83,38 @@ Handle::~Handle() {
     for (void *p : allocations) cudaFree(p);
     for (auto &e : events)
         if (e) cudaEventDestroy(e);
-    for (auto &e : gemm_events)
-        if (e) cudaEventDestroy(e);
 }
 
-// next event of the GEMM timing pool (grown on demand)
-cudaError_t Handle::gemm_event(cudaEvent_t *out) {
-    if (gemm_events_used == (int)gemm_events.size()) {
+cudaError_t EventPool::next(cudaEvent_t *out) {
+    if (used == (int)ev.size()) {
         cudaEvent_t e;
         cudaError_t r = cudaEventCreate(&e);
         if (r != cudaSuccess) return r;
-        gemm_events.push_back(e);
+        ev.push_back(e);
     }
-    *out = gemm_events[gemm_events_used++];
+    *out = ev[used++];
     return cudaSuccess;
 }
+
+cudaError_t EventPool::sum_pairs_ms(double *ms) const {
+    double tot = 0.0;
+    for (int i = 0; i + 1 < used; i += 2) {
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        if (e != cudaSuccess) return e;
+        tot += t;
+    }
+    *ms = tot;
+    return cudaSuccess;
+}
+
+EventPool::~EventPool() {
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// next event of the GEMM timing pool
+cudaError_t Handle::gemm_event(cudaEvent_t *out) { return gemm_pool.next(out); }
 
 }  // namespace rsrr
 
@@ -124,6 +141,7 @@ void rsrr_opts_default(rsrr_opts *o) {
     o->NQ = 500;
     o->KQ = 2;
     o->host_threads = 0;
+    o->gemm = RSRR_GEMM_AUTO;
 }
 
 static rsrr_status create_fail(const char *msg) {
@@ -181,6 +199,8 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
     const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
     if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
         return create_fail("rsrr_create: unknown precision");
+    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI))
+        return create_fail("rsrr_create: unknown gemm method");
 
     Handle *h = new (std::nothrow) Handle();
     if (!h) { rsrr::thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
@@ -334,13 +354,8 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
         h->timed_project = false;
     }
     if (h->gemm_timed) {
-        double tot = 0.0;
-        for (int i = 0; i + 1 < h->gemm_events_used; i += 2) {
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, h->gemm_events[i], h->gemm_events[i + 1]), "event time");
-            tot += t;
-        }
-        h->gemm_ms = tot;
+        CK(h->gemm_pool.sum_pairs_ms(&h->gemm_ms), "event time");
+        CK(h->tc_pool.sum_pairs_ms(&h->tc_ms), "event time");
         h->gemm_timed = false;
     }
     memset(out, 0, sizeof *out);
@@ -359,6 +374,8 @@ rsrr_status rsrr_get_stats(rsrr_t *hh, rsrr_stats *out) {
     for (int i = 0; i < 6; ++i) out->stage_ms[i] = h->stage_ms[i];
     out->gemm_flops = h->gemm_flops;
     out->gemm_ms = h->gemm_ms;
+    out->tc_flops = h->tc_flops;
+    out->tc_ms = h->tc_ms;
     return RSRR_OK;
 }
 
@@ -556,6 +573,8 @@ rsrr_status create_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t
     const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
     if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
         return create_fail("rsrr_create: unknown precision");
+    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI))
+        return create_fail("rsrr_create: unknown gemm method");
     Handle *h = new (std::nothrow) Handle();
     if (!h) { thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
     if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);

@@ -1,0 +1,630 @@
+// FP64-accurate complex GEMM on the bf16 tensor cores by error-free slicing
+// (the Ozaki scheme): C = alpha op(A) B + beta C with op(A) = A or A^H and
+// real alpha, beta.  Used for the large products of the projection (Gram
+// matrices of the sample block, Q^H R, R W, Q^H A_i Q) where native FP64
+// runs at the GPU's reduced double-precision rate.
+//
+// 1. The complex product is one real product C~ = A~ B~ of depth K' = 2K
+//    with Re/Im interleaved along K:
+//      A~(i, 2k) = Re op(A)_ik,  A~(i, 2k+1) = Im op(A)_ik
+//      B~(2k, j) = Re B_kj,  B~(2k+1, j) = -Im B_kj      (j < N:  Re C)
+//      B~(2k, N+j) = Im B_kj,  B~(2k+1, N+j) = Re B_kj   (N + j: Im C)
+// 2. Row i of A~ is scaled by 2^-e_i and column j of B~ by 2^-f_j with
+//    2^(e-1) <= max |entry| < 2^e, then rounded to 55-bit fixed point
+//    (exact for the largest entries, below 2^-55 absolute for the rest) and
+//    split into 7 signed base-256 digits a_s in [-128, 128]:
+//      x = sum_s a_s 2^(-7-8s).
+//    Slice s is stored as the bf16 value a_s 2^(-8s) (exact).
+// 3. Slice products of one group t = p + q are multiples of 2^(-8t) with an
+//    integer part below 2^14 each; tensor-core FP32 sums of them stay exact
+//    while the integer part is below 2^24.  Groups t = 0..4 get their own
+//    accumulators and are folded into one int64 per output every 128 of K'
+//    ((t+1) 128 2^14 <= 5 2^21 < 2^24): acc += 2^32 g_t.  Groups 5 and 6
+//    (relative weight <= 2^-40) share one FP32 accumulator folded into an
+//    FP32 sum; the tensor cores round such mixed-magnitude sums (measured:
+//    a shared group-4..6 accumulator lost ~0.3 units of 2^-46), which at
+//    this weight stays below 2^-54.  Pairs with t >= 7 (below 2^-56
+//    relative) are dropped.  At most 512 folds per product keep |acc| below
+//    2^62 (K is chunked beyond 32768).
+// 4. C~_ij = 2^(e_i + f_j) 2^-46 (acc + 2^32 low), rounded once to FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <string>
+
+#include "rsrr.h"
+
+#include "common.cuh"
+#include "rsrr_internal.h"
+
+namespace rsrr {
+
+constexpr int OZ_S = 7;           // slices
+constexpr int OZ_BM = 64;         // CTA tile rows (M)
+constexpr int OZ_BN = 64;         // CTA tile columns (of the 2N real columns)
+constexpr int OZ_KC = 32;         // K' per pipeline stage
+constexpr int OZ_LD = OZ_KC + 8;  // shared-memory row length (bf16): 80 bytes, conflict-free ldmatrix
+constexpr int OZ_NS = 3;          // pipeline stages
+constexpr int OZ_FOLD = 4;        // stages per exact fold (K' = 128)
+constexpr int OZ_BCACHE = 4;      // B slices held in registers per 16-deep step
+constexpr int64_t OZ_KMAX = 32768;  // complex K per chunk: <= 512 folds
+constexpr int OZ_THREADS = 256;   // 8 warps: 2 (M) x 4 (N), 32 x 16 outputs each
+constexpr int OZ_ROWS = OZ_S * (OZ_BM + OZ_BN);         // shared-memory rows per stage
+constexpr int OZ_STAGE = OZ_ROWS * OZ_LD;                // bf16 elements per stage
+constexpr size_t OZ_SMEM = sizeof(__nv_bfloat16) * OZ_STAGE * OZ_NS;  // 215040 bytes
+
+// ----------------------------------------------------------- fixed point
+// biased exponent field of |v|, subnormals and zero counted as 1
+RSRR_DEV int exb_of(double v) {
+    const int b = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    return b ? b : 1;
+}
+
+// round(v 2^(55 - e)) with e = E - 1022, E = largest biased exponent of the
+// row; |result| <= 2^55.  Integer arithmetic only.
+RSRR_DEV long long fixed55(double v, int E) {
+    const long long bits = __double_as_longlong(v);
+    int b = (int)((bits >> 52) & 0x7FF);
+    long long mant = bits & 0xFFFFFFFFFFFFFll;
+    if (b) mant |= 1ll << 52;
+    else b = 1;
+    const int sh = b - E + 2;  // <= 2
+    long long m;
+    if (sh >= 0) m = mant << sh;
+    else if (sh > -62) m = (mant + (1ll << (-sh - 1))) >> (-sh);
+    else m = 0;
+    return bits < 0 ? -m : m;
+}
+
+// the 7 slices of a 55-bit fixed-point value as floats a_s 2^(-8s)
+RSRR_DEV void digits7(long long m, float out[OZ_S]) {
+#pragma unroll
+    for (int s = 0; s < OZ_S - 1; ++s) {
+        const int sh = 48 - 8 * s;
+        const long long a = (m + (1ll << (sh - 1))) >> sh;  // round half up, |a| <= 128
+        m -= a << sh;
+        out[s] = (float)(int)a * ldexpf(1.f, -8 * s);
+    }
+    out[OZ_S - 1] = (float)(int)m * 0x1p-48f;  // remainder in [-128, 128)
+}
+
+// ----------------------------------------------------------- exponents
+// E[c] = largest biased exponent in column c (contiguous, K entries); also
+// written to E[c + dup] when dup > 0 (the Im-output columns of B~)
+__global__ void oz_colexp_kernel(int *__restrict__ E, const double2 *__restrict__ X, int64_t ld,
+                                 int K, int cols, int dup) {
+    __shared__ int w[32];
+    for (int c = blockIdx.x; c < cols; c += gridDim.x) {
+        int m = 1;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const double2 v = X[(int64_t)c * ld + k];
+            m = max(m, max(exb_of(v.x), exb_of(v.y)));
+        }
+        for (int off = 16; off; off >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, off));
+        if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int r = 1;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = max(r, w[q]);
+            E[c] = r;
+            if (dup > 0) E[c + dup] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// E[i] = max(E[i], largest biased exponent in row i of the column-major
+// rows x K matrix X); E starts at 0.  Tiles of 32 rows x 256 columns.
+__global__ void oz_rowexp_kernel(int *__restrict__ E, const double2 *__restrict__ X, int64_t ld,
+                                 int rows, int K) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int i = blockIdx.x * 32 + tx;
+    const int k0 = blockIdx.y * 256;
+    int m = 1;
+    if (i < rows)
+        for (int k = k0 + ty; k < min(K, k0 + 256); k += 8) {
+            const double2 v = X[(int64_t)k * ld + i];
+            m = max(m, max(exb_of(v.x), exb_of(v.y)));
+        }
+    __shared__ int w[8][32];
+    w[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0 && i < rows) {
+        for (int q = 1; q < 8; ++q) m = max(m, w[q][tx]);
+        atomicMax(&E[i], m);
+    }
+}
+
+// ----------------------------------------------------------- slicing
+// Plane layout: P[s][r][k'], row length Kp (a multiple of 32), Rp rows.
+RSRR_DEV void store_slices(__nv_bfloat16 *P, size_t stride, size_t off, double re, double im, int E) {
+    float dr[OZ_S], di[OZ_S];
+    digits7(fixed55(re, E), dr);
+    digits7(fixed55(im, E), di);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s)
+        *reinterpret_cast<__nv_bfloat162 *>(P + s * stride + off) = __floats2bfloat162_rn(dr[s], di[s]);
+}
+
+RSRR_DEV void store_zero(__nv_bfloat16 *P, size_t stride, size_t off) {
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) *reinterpret_cast<__nv_bfloat162 *>(P + s * stride + off) = z;
+}
+
+// Rows built from contiguous columns of X.
+//   mode 0 (A^H):  row r = conj(column r),                  r < R
+//   mode 1 (B):    row r < Nc: (Re, -Im) of column r;  Nc <= r < 2Nc: (Im, Re) of column r - Nc
+// Rows >= R and k >= K are written as zeros.
+__global__ void oz_slice_cols_kernel(__nv_bfloat16 *__restrict__ P, const int *__restrict__ E,
+                                     const double2 *__restrict__ X, int64_t ld, int mode, int R,
+                                     int Nc, int K, int Rp, int Kp) {
+    const size_t stride = (size_t)Rp * Kp;
+    const int Kh = Kp / 2;
+    for (int r = blockIdx.y; r < Rp; r += gridDim.y) {
+        const int c = (mode == 1 && r >= Nc) ? r - Nc : r;
+        const int Ec = (r < R) ? E[c] : 1;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Kh; k += gridDim.x * blockDim.x) {
+            const size_t off = (size_t)r * Kp + 2 * (size_t)k;
+            if (r >= R || k >= K) {
+                store_zero(P, stride, off);
+                continue;
+            }
+            const double2 v = X[(int64_t)c * ld + k];
+            double re = v.x, im = -v.y;
+            if (mode == 1 && r >= Nc) { re = v.y; im = v.x; }
+            store_slices(P, stride, off, re, im, Ec);
+        }
+    }
+}
+
+// Rows of A itself (column-major M x K, row i strided): 32 x 32 tiles
+// transposed through shared memory.  Rows >= M and k >= K are zeros.
+__global__ void oz_slice_rows_kernel(__nv_bfloat16 *__restrict__ P, const int *__restrict__ E,
+                                     const double2 *__restrict__ A, int64_t lda, int M, int K, int Mp,
+                                     int Kp) {
+    __shared__ double2 t[32][33];
+    const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + tx, k = k0 + r;
+        t[r][tx] = (i < M && k < K) ? A[(int64_t)k * lda + i] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const size_t stride = (size_t)Mp * Kp;
+    const int Kh = Kp / 2;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, k = k0 + tx;
+        if (i >= Mp || k >= Kh) continue;
+        const size_t off = (size_t)i * Kp + 2 * (size_t)k;
+        if (i >= M || k >= K) {
+            store_zero(P, stride, off);
+            continue;
+        }
+        const double2 v = t[tx][r];
+        store_slices(P, stride, off, v.x, v.y, E[i]);
+    }
+}
+
+// ----------------------------------------------------------- the GEMM
+RSRR_DEV void cp_async16(unsigned saddr, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem));
+}
+RSRR_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+RSRR_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+RSRR_DEV void ldmatrix_x4(unsigned r[4], unsigned saddr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr));
+}
+
+RSRR_DEV void mma_bf16(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One CTA: a 64 x 64 tile of C~ over K' range [sp kchunk, (sp+1) kchunk).
+// W != null: FP64 partial tile into W[sp][i][j'] (Mp x Np, row major).
+// W == null: C = alpha C~ + beta C written directly (one split).
+// upper_only: tiles strictly below the block diagonal of each half skip.
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs,
+               const int *__restrict__ Ea, const int *__restrict__ Eb, double *__restrict__ W,
+               double2 *__restrict__ C, int64_t ldc, int M, int N, int Mp, int Np, int Kp, int kchunk,
+               int halfN_tiles, int upper_only, double alpha, double beta) {
+    const int bm = blockIdx.x, bn = blockIdx.y, sp = blockIdx.z;
+    if (upper_only && bm > (bn % halfN_tiles)) return;
+    extern __shared__ __align__(128) unsigned char oz_smem[];
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(oz_smem);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int g = lane >> 2, tq = lane & 3;
+    const int m0 = bm * OZ_BM, n0 = bn * OZ_BN;
+    const int kbeg = sp * kchunk;
+    const int kend = min(Kp, kbeg + kchunk);
+    const int nk = kend > kbeg ? (kend - kbeg) / OZ_KC : 0;
+    const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
+
+    float gs[6][2][2][4];
+    long long acc[2][2][4];
+    float low[2][2][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[a][b][q] = 0;
+                low[a][b][q] = 0.f;
+#pragma unroll
+                for (int t = 0; t < 6; ++t) gs[t][a][b][q] = 0.f;
+            }
+
+    // stage rows: slice s, rows 0..63 from A~, 64..127 from B~
+    auto load_stage = [&](int slot, int k0) {
+        const unsigned dst = sbase + (unsigned)(slot * OZ_STAGE * 2);
+        for (int q = tid; q < OZ_ROWS * 4; q += OZ_THREADS) {
+            const int row = q >> 2, c = q & 3;
+            const int s = row >> 7, rr = row & 127;
+            const __nv_bfloat16 *src =
+                (rr < OZ_BM) ? As + s * sA + (size_t)(m0 + rr) * Kp + k0 + c * 8
+                             : Bs + s * sB + (size_t)(n0 + rr - OZ_BM) * Kp + k0 + c * 8;
+            cp_async16(dst + (unsigned)((row * OZ_LD + c * 8) * 2), src);
+        }
+    };
+
+#pragma unroll
+    for (int st = 0; st < OZ_NS - 1; ++st) {
+        if (st < nk) load_stage(st, kbeg + st * OZ_KC);
+        cp_async_commit();
+    }
+    // per-lane ldmatrix row offsets (bf16 elements within one slice)
+    const int li = lane & 7, mi = lane >> 3;
+    const int a_off = (wm * 32 + (mi & 1) * 8 + li) * OZ_LD + (mi >> 1) * 8;
+    const int b_off = (OZ_BM + wn * 16 + (mi >> 1) * 8 + li) * OZ_LD + (mi & 1) * 8;
+
+    for (int it = 0; it < nk; ++it) {
+        cp_async_wait<OZ_NS - 2>();
+        __syncthreads();
+        {
+            const int nx = it + OZ_NS - 1;
+            if (nx < nk) load_stage(nx % OZ_NS, kbeg + nx * OZ_KC);
+            cp_async_commit();
+        }
+        const unsigned st = sbase + (unsigned)((it % OZ_NS) * OZ_STAGE * 2);
+#pragma unroll
+        for (int kk = 0; kk < OZ_KC; kk += 16) {
+            // B slices 0..3 stay in registers for the whole step; 4..6 (used
+            // by p <= 2 only) are loaded where needed
+            unsigned bfr[OZ_BCACHE][4];
+#pragma unroll
+            for (int q = 0; q < OZ_BCACHE; ++q)
+                ldmatrix_x4(bfr[q], st + (unsigned)((q * (OZ_BM + OZ_BN) * OZ_LD + b_off + kk) * 2));
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p) {
+                unsigned afr[2][4];
+                const unsigned pa = st + (unsigned)((p * (OZ_BM + OZ_BN) * OZ_LD + a_off + kk) * 2);
+                ldmatrix_x4(afr[0], pa);
+                ldmatrix_x4(afr[1], pa + 16 * OZ_LD * 2);
+#pragma unroll
+                for (int q = 0; q < OZ_S - p; ++q) {
+                    const int t = p + q < 5 ? p + q : 5;
+                    unsigned bx[4];
+                    if (q < OZ_BCACHE) {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) bx[r] = bfr[q < OZ_BCACHE ? q : 0][r];
+                    } else {
+                        ldmatrix_x4(bx, st + (unsigned)((q * (OZ_BM + OZ_BN) * OZ_LD + b_off + kk) * 2));
+                    }
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) mma_bf16(gs[t][a][b], afr[a], bx[2 * b], bx[2 * b + 1]);
+                }
+            }
+        }
+        if ((it + 1) % OZ_FOLD == 0 || it == nk - 1) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                        for (int t = 0; t < 5; ++t) {
+                            acc[a][b][q] += __float2ll_rn(gs[t][a][b][q] * 0x1p32f);
+                            gs[t][a][b][q] = 0.f;
+                        }
+                        low[a][b][q] += gs[5][a][b][q];
+                        gs[5][a][b][q] = 0.f;
+                    }
+        }
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = m0 + wm * 32 + a * 16 + g + (q >= 2 ? 8 : 0);
+                const int jj = n0 + wn * 16 + b * 8 + 2 * tq + (q & 1);
+                const double v = ldexp((double)acc[a][b][q] + (double)low[a][b][q] * 0x1p32,
+                                       Ea[i] + Eb[jj] - 2090);
+                if (W) {
+                    W[(size_t)sp * Mp * Np + (size_t)i * Np + jj] = v;
+                } else if (i < M && jj < 2 * N) {
+                    const int part = jj >= N, j = jj - part * N;
+                    double *c = reinterpret_cast<double *>(C + (int64_t)j * ldc + i) + part;
+                    double r = alpha * v;
+                    if (beta != 0.0) r = fma(beta, *c, r);
+                    *c = r;
+                }
+            }
+}
+
+// C = alpha sum_s W[s] + beta C (fixed order over the splits)
+__global__ void oz_combine_kernel(double2 *__restrict__ C, int64_t ldc, const double *__restrict__ W,
+                                  int M, int N, int Mp, int Np, int splits, double alpha, double beta,
+                                  int upper_only) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % M), j = (int)(q / M);
+        if (upper_only && (i / OZ_BM) > (j / OZ_BN)) continue;
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < splits; ++s) {
+            const double *Wp = W + (size_t)s * Mp * Np + (size_t)i * Np;
+            re += Wp[j];
+            im += Wp[N + j];
+        }
+        double2 r = make_double2(alpha * re, alpha * im);
+        if (beta != 0.0) {
+            const double2 c = C[(int64_t)j * ldc + i];
+            r.x = fma(beta, c.x, r.x);
+            r.y = fma(beta, c.y, r.y);
+        }
+        C[(int64_t)j * ldc + i] = r;
+    }
+}
+
+__global__ void oz_mirror_kernel(double2 *__restrict__ C, int64_t ldc, int n) {
+    const int64_t total = (int64_t)n * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % n), j = (int)(q / n);
+        if (i > j) {
+            const double2 v = C[(int64_t)i * ldc + j];
+            C[(int64_t)j * ldc + i] = make_double2(v.x, -v.y);
+        } else if (i == j) {
+            C[(int64_t)j * ldc + i].y = 0.0;  // the rounded low groups leave ~2^-56 here
+        }
+    }
+}
+
+// C = beta C (K = 0 or alpha = 0)
+__global__ void oz_scale_kernel(double2 *__restrict__ C, int64_t ldc, int M, int N, double beta) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % M), j = (int)(q / M);
+        double2 &c = C[(int64_t)j * ldc + i];
+        c = beta == 0.0 ? make_double2(0.0, 0.0) : make_double2(beta * c.x, beta * c.y);
+    }
+}
+
+// ----------------------------------------------------------- host side
+static int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+static int grid_for(int64_t work) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 8));
+}
+
+namespace {
+struct OzPlan {
+    int64_t Mp, Np, Kc, Kp;  // Kc: complex K per chunk
+    int splits;
+    int64_t kchunk;          // K' per split
+    size_t bytes;
+};
+
+size_t plan_bytes(int64_t Mp, int64_t Np, int64_t Kp, int splits) {
+    size_t b = rup((int64_t)sizeof(__nv_bfloat16) * OZ_S * Mp * Kp, 256);
+    b += rup((int64_t)sizeof(__nv_bfloat16) * OZ_S * Np * Kp, 256);
+    b += rup((int64_t)sizeof(int) * (Mp + Np), 256);
+    if (splits > 1) b += rup((int64_t)sizeof(double) * splits * Mp * Np, 256);
+    return b;
+}
+
+// splits of K that balance the waves over the 152 SMs (one CTA per SM)
+int choose_splits(int64_t tiles, int64_t Kp) {
+    int best = 1;
+    double best_cost = 1e300;
+    for (int s = 1; s <= 32; ++s) {
+        if (s > 1 && Kp / s < (int64_t)OZ_FOLD * OZ_KC * 2) break;
+        const double waves = (double)((tiles * s + 151) / 152);
+        const double cost = waves / s * (1.0 + 0.01 * s);
+        if (cost < best_cost - 1e-12) {
+            best_cost = cost;
+            best = s;
+        }
+    }
+    return best;
+}
+
+OzPlan make_plan(int M, int N, int K, bool hermitian, size_t ws_bytes) {
+    OzPlan p{};
+    p.Mp = rup(M, OZ_BM);
+    p.Np = rup(2 * (int64_t)N, OZ_BN);
+    const int64_t tiles = (p.Mp / OZ_BM) * (p.Np / OZ_BN) / (hermitian ? 2 : 1);
+    const int64_t Kall = std::max(K, 1);
+    auto fit = [&](int64_t kc) {
+        p.Kc = kc;
+        p.Kp = rup(2 * p.Kc, OZ_KC);
+        p.splits = choose_splits(std::max<int64_t>(tiles, 1), p.Kp);
+        while (p.splits > 1 && plan_bytes(p.Mp, p.Np, p.Kp, p.splits) > ws_bytes) --p.splits;
+        p.bytes = plan_bytes(p.Mp, p.Np, p.Kp, p.splits);
+        return p.bytes <= ws_bytes;
+    };
+    int64_t kc = std::min<int64_t>(Kall, OZ_KMAX);
+    while (!fit(kc) && kc > 16) kc = std::max<int64_t>(16, rup(kc / 2, 16));  // chunk K to fit
+    // chunks of equal depth
+    const int64_t nch = (Kall + kc - 1) / kc;
+    if (nch > 1) fit(std::min(kc, rup((Kall + nch - 1) / nch, 16)));
+    p.kchunk = rup((p.Kp + p.splits - 1) / p.splits, OZ_KC);
+    p.splits = (int)((p.Kp + p.kchunk - 1) / p.kchunk);
+    return p;
+}
+}  // namespace
+
+size_t ozaki_workspace_bytes(int M, int N, int K, bool hermitian) {
+    return make_plan(M, N, K, hermitian, SIZE_MAX).bytes;
+}
+
+double ozaki_tc_flops(int M, int N, int K, bool hermitian) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0.0;
+    const OzPlan p = make_plan(M, N, K, hermitian, SIZE_MAX);
+    const double pairs = OZ_S * (OZ_S + 1) / 2;
+    const double tm = (double)(p.Mp / OZ_BM), tn = (double)(p.Np / OZ_BN);
+    const double tiles = hermitian && M == N && (N % OZ_BN) == 0 ? tm * (tm + 1) : tm * tn;
+    return 2.0 * pairs * tiles * OZ_BM * OZ_BN * (double)p.Kp;
+}
+
+cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
+                        const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
+                        double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
+                        int64_t *launches, EventPool *timer, double *tc_flops) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (K <= 0 || alpha == 0.0) {
+        oz_scale_kernel<<<grid_for((int64_t)M * N), 256, 0, s>>>(C, ldc, M, N, beta);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
+    if (hermitian && (M != N || !conjA || A != B || lda != ldb)) hermitian = false;
+    const OzPlan p = make_plan(M, N, K, hermitian, ws_bytes);
+    if (p.bytes > ws_bytes) return cudaErrorMemoryAllocation;
+    e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    if (e != cudaSuccess) return e;
+    char *w = static_cast<char *>(ws);
+    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(w);
+    w += rup((int64_t)sizeof(__nv_bfloat16) * OZ_S * p.Mp * p.Kp, 256);
+    __nv_bfloat16 *Bs = reinterpret_cast<__nv_bfloat16 *>(w);
+    w += rup((int64_t)sizeof(__nv_bfloat16) * OZ_S * p.Np * p.Kp, 256);
+    int *Ea = reinterpret_cast<int *>(w);
+    int *Eb = Ea + p.Mp;
+    w += rup((int64_t)sizeof(int) * (p.Mp + p.Np), 256);
+    double *Wp = p.splits > 1 ? reinterpret_cast<double *>(w) : nullptr;
+    const bool upper = hermitian && (N % OZ_BN) == 0;
+    const int halfN_tiles = upper ? N / OZ_BN : (int)(p.Np / OZ_BN);
+
+    for (int64_t kc0 = 0; kc0 < K; kc0 += p.Kc) {
+        const int Kc = (int)std::min<int64_t>(p.Kc, K - kc0);
+        const double b = kc0 == 0 ? beta : 1.0;
+        const double2 *Ak = conjA ? A + kc0 : A + kc0 * lda;
+        const double2 *Bk = B + kc0;
+        if ((e = cudaMemsetAsync(Ea, 0, sizeof(int) * (p.Mp + p.Np), s)) != cudaSuccess) return e;
+        if (conjA)
+            oz_colexp_kernel<<<std::min(M, 65535), 256, 0, s>>>(Ea, Ak, lda, Kc, M, 0);
+        else
+            oz_rowexp_kernel<<<dim3((unsigned)((M + 31) / 32), (unsigned)((Kc + 255) / 256)), 256, 0, s>>>(
+                Ea, Ak, lda, M, Kc);
+        oz_colexp_kernel<<<std::min(N, 65535), 256, 0, s>>>(Eb, Bk, ldb, Kc, N, N);
+        const int kx = (int)std::min<int64_t>((p.Kp / 2 + 255) / 256, 64);
+        if (conjA)
+            oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Mp, 65535)), 256, 0, s>>>(
+                As, Ea, Ak, lda, 0, M, M, Kc, (int)p.Mp, (int)p.Kp);
+        else
+            oz_slice_rows_kernel<<<dim3((unsigned)(p.Mp / 32), (unsigned)((p.Kp / 2 + 31) / 32)), 256, 0, s>>>(
+                As, Ea, Ak, lda, M, Kc, (int)p.Mp, (int)p.Kp);
+        oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Np, 65535)), 256, 0, s>>>(
+            Bs, Eb, Bk, ldb, 1, 2 * N, N, Kc, (int)p.Np, (int)p.Kp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const dim3 grid((unsigned)(p.Mp / OZ_BM), (unsigned)(p.Np / OZ_BN), (unsigned)p.splits);
+        cudaEvent_t ev1 = nullptr;
+        if (timer) {
+            cudaEvent_t ev0;
+            if ((e = timer->next(&ev0)) != cudaSuccess) return e;
+            if ((e = timer->next(&ev1)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+        }
+        oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N, (int)p.Mp,
+                                                        (int)p.Np, (int)p.Kp, (int)p.kchunk,
+                                                        halfN_tiles, upper ? 1 : 0, alpha, b);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (timer && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
+        if (tc_flops) *tc_flops += ozaki_tc_flops(M, N, Kc, upper);
+        if (Wp) {
+            oz_combine_kernel<<<grid_for((int64_t)M * N), 256, 0, s>>>(C, ldc, Wp, M, N, (int)p.Mp,
+                                                                       (int)p.Np, p.splits, alpha, b,
+                                                                       upper ? 1 : 0);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (launches) *launches += 5 + (Wp ? 1 : 0);
+    }
+    if (hermitian) {  // exactly Hermitian result, whether or not tiles were skipped
+        oz_mirror_kernel<<<grid_for((int64_t)M * M), 256, 0, s>>>(C, ldc, M);
+        if (launches) *launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rsrr
+
+// ----------------------------------------------------------- C ABI
+namespace rsrr {
+std::string &thread_error();  // api.cu: last error of a handle-less call
+}
+
+extern "C" rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsrr_c128 *A,
+                                  int64_t lda, const rsrr_c128 *B, int64_t ldb, rsrr_c128 *C,
+                                  int64_t ldc, double alpha, double beta, int32_t method,
+                                  int32_t hermitian, size_t max_ws_bytes, void *stream) {
+    using namespace rsrr;
+    auto fail = [](rsrr_status st, const char *what, cudaError_t e = cudaSuccess) {
+        std::string m = std::string("rsrr_zgemm: ") + what;
+        if (e != cudaSuccess) m += std::string(": ") + cudaGetErrorString(e);
+        thread_error() = m;
+        return st;
+    };
+    if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B)))
+        return fail(RSRR_EINVAL, "bad argument");
+    const int64_t rowsA = conjA ? K : M;
+    if (ldc < std::max(1, M) || ldb < std::max(1, K) || lda < std::max<int64_t>(1, rowsA))
+        return fail(RSRR_EINVAL, "leading dimension too small");
+    if (method < RSRR_GEMM_AUTO || method > RSRR_GEMM_OZAKI) return fail(RSRR_EINVAL, "unknown method");
+    if (hermitian && (!conjA || A != B || lda != ldb || M != N || beta != 0.0))
+        return fail(RSRR_EINVAL, "hermitian needs conjA, A == B, lda == ldb, M == N, beta == 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double2 *a = reinterpret_cast<const double2 *>(A);
+    const double2 *b = reinterpret_cast<const double2 *>(B);
+    double2 *c = reinterpret_cast<double2 *>(C);
+    const double flops = 8.0 * M * (double)N * K;
+    const bool sliced = method == RSRR_GEMM_OZAKI || (method == RSRR_GEMM_AUTO && flops >= 1073741824.0);
+    cudaError_t e;
+    if (!sliced) {
+        if ((e = fp64_gemm(M, N, K, conjA != 0, a, lda, b, ldb, c, ldc, alpha, beta, s)) != cudaSuccess)
+            return fail(RSRR_ECUDA, "fp64 gemm", e);
+    } else {
+        size_t need = ozaki_workspace_bytes(M, N, K, hermitian != 0);
+        if (max_ws_bytes > 0) need = std::min(need, max_ws_bytes);
+        void *ws = nullptr;
+        if ((e = cudaMalloc(&ws, need)) != cudaSuccess) return fail(RSRR_ENOMEM, "work space", e);
+        e = ozaki_zgemm(M, N, K, conjA != 0, a, lda, b, ldb, c, ldc, alpha, beta, hermitian != 0, ws,
+                        need, s, nullptr);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(ws);
+        if (e == cudaErrorMemoryAllocation) return fail(RSRR_ENOMEM, "work space below one chunk");
+        if (e != cudaSuccess) return fail(RSRR_ECUDA, "sliced gemm", e);
+        if (e2 != cudaSuccess) return fail(RSRR_ECUDA, "sync", e2);
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(RSRR_ECUDA, "sync", e);
+    thread_error().clear();
+    return RSRR_OK;
+}

@@ -145,10 +145,32 @@ struct Gemm {
     size_t ws_elems = 0;
     int64_t *counter = nullptr;
     Handle *timer = nullptr;  // records events around every call when set
+    int method = RSRR_GEMM_FP64;
+    void *ows = nullptr;      // work space of the sliced tensor-core products
+    size_t ows_bytes = 0;
     cudaError_t run(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                     const double2 *B, int64_t ldb, double2 *C, int64_t ldc, cudaStream_t s,
                     bool hermitian = false, double alpha = 1.0, double beta = 0.0) {
         if (M <= 0 || N <= 0) return cudaSuccess;
+        const double flops = hermitian ? 8.0 * (double)M * (M + 1) / 2 * K : 8.0 * M * N * (double)K;
+        const bool sliced = ows && K > 0 &&
+                            (method == RSRR_GEMM_OZAKI || (method == RSRR_GEMM_AUTO && flops >= 1073741824.0));
+        if (sliced) {
+            cudaError_t e;
+            cudaEvent_t ev1 = nullptr;
+            if (timer) {
+                cudaEvent_t ev0;
+                if ((e = timer->gemm_event(&ev0)) != cudaSuccess) return e;
+                if ((e = timer->gemm_event(&ev1)) != cudaSuccess) return e;
+                if ((e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+                timer->gemm_flops += flops;
+            }
+            e = ozaki_zgemm(M, N, K, conjA, A, lda, B, ldb, C, ldc, alpha, beta, hermitian, ows,
+                            ows_bytes, s, counter, timer ? &timer->tc_pool : nullptr,
+                            timer ? &timer->tc_flops : nullptr);
+            if (e == cudaSuccess && timer) e = cudaEventRecord(ev1, s);
+            return e;
+        }
         const int tm = (M + GT - 1) / GT, tn = (N + GT - 1) / GT;
         int64_t tiles = hermitian ? (int64_t)tm * (tm + 1) / 2 : (int64_t)tm * tn;
         int splits = 1;
@@ -171,7 +193,7 @@ struct Gemm {
             if ((e = timer->gemm_event(&ev0)) != cudaSuccess) return e;
             if ((e = timer->gemm_event(&ev1)) != cudaSuccess) return e;
             if ((e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
-            timer->gemm_flops += hermitian ? 8.0 * (double)M * (M + 1) / 2 * K : 8.0 * M * N * (double)K;
+            timer->gemm_flops += flops;
         }
         if (counter) *counter += 1 + (splits == 1 ? 0 : 1) + (hermitian ? 1 : 0);
         if (splits == 1) {  // direct: the kernel writes C itself
@@ -603,6 +625,8 @@ struct ProjWs {
     double2 *C;         // NL x NL coefficients of the deflation
     unsigned int *bar;  // grid barrier of the cooperative kernels
     double *jacc;       // per-sweep convergence sums of the Jacobi kernel
+    void *ows;          // sliced tensor-core GEMM work space
+    size_t ows_bytes;
     double2 *Qall;      // n x NL basis
     double2 *P;         // RSRR_MAX_TERMS x NL x NL projected coefficients
     char *end;
@@ -706,6 +730,14 @@ __global__ void max_vec_kernel(double *__restrict__ out, const double *__restric
     }
 }
 
+// Work space of the sliced products: the Gram matrix of the n x NL block in
+// one piece (the other products of the sparse kind need less), capped at
+// 8 GiB; a product that needs more runs in chunks of K.
+static size_t ozaki_ws_bytes(int NL, int64_t n) {
+    const int nc = (int)std::min<int64_t>(n, INT32_MAX / 2);
+    return std::min(ozaki_workspace_bytes(NL, NL, nc, true), (size_t)8 << 30);
+}
+
 // Workspace layout of the projection stage (carved from one allocation).
 static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n, int terms) {
     const size_t NL2 = (size_t)NL * NL;
@@ -730,6 +762,8 @@ static void carve_ws(char *cp, ProjWs &ws, int NL, int64_t n, int terms) {
     ws.Ytmp = carve<double2>(cp, (size_t)n * NL);
     ws.gws_elems = std::max<size_t>(NL2 * 4, (size_t)8 << 20);
     ws.gws = carve<double2>(cp, ws.gws_elems);
+    ws.ows_bytes = ozaki_ws_bytes(NL, n);
+    ws.ows = carve<char>(cp, ws.ows_bytes);
     ws.Qall = carve<double2>(cp, (size_t)n * NL);
     ws.P = carve<double2>(cp, (size_t)std::max(terms, RSRR_MAX_TERMS) * NL2);
     ws.end = cp;
@@ -774,10 +808,15 @@ rsrr_status Handle::project(cudaStream_t s) {
     gm.ws = ws.gws;
     gm.ws_elems = ws.gws_elems;
     gm.counter = &launches;
+    gm.method = opts.gemm;
+    gm.ows = ws.ows;
+    gm.ows_bytes = ws.ows_bytes;
     if (opts.timing) {
         gm.timer = this;
-        gemm_events_used = 0;
+        gemm_pool.used = 0;
+        tc_pool.used = 0;
         gemm_flops = 0.0;
+        tc_flops = 0.0;
         gemm_timed = true;
     }
     rsrr_status mst = mark(6, s);

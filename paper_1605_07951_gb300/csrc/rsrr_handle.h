@@ -72,9 +72,10 @@ struct Handle {
     bool timed_sample = false, timed_project = false;
     double stage_ms[6] = {};
     // GEMM timing of the last rsrr_project (opts.timing)
-    std::vector<cudaEvent_t> gemm_events;  // pairs
-    int gemm_events_used = 0;
+    EventPool gemm_pool;                // pairs around every product
+    EventPool tc_pool;                  // pairs around the sliced products' main kernel
     double gemm_flops = 0.0, gemm_ms = 0.0;
+    double tc_flops = 0.0, tc_ms = 0.0;
     bool gemm_timed = false;
 
     ~Handle();

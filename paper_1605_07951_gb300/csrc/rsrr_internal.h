@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <vector>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -88,8 +89,34 @@ cudaError_t launch_dense_eig_residual(const double2 *V, const double2 *lam, cons
                                       cudaStream_t s);
 cudaError_t launch_narrow_all(float2 *D, const double2 *S, int64_t total, cudaStream_t s);
 
+// ---- CUDA events recorded in pairs around launches (grown on demand; api.cu)
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    int used = 0;
+    cudaError_t next(cudaEvent_t *out);
+    cudaError_t sum_pairs_ms(double *ms) const;  // sum of the recorded pairs' durations
+    ~EventPool();
+};
+
 // ---- FP64 GEMM of proj.cu without split-K: C = alpha op(A) B + beta C
 cudaError_t fp64_gemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda, const double2 *B,
                       int64_t ldb, double2 *C, int64_t ldc, double alpha, double beta, cudaStream_t s);
+
+// ---- FP64-accurate complex GEMM on the bf16 tensor cores (ozaki.cu):
+// C = alpha op(A) B + beta C, op(A) = A^H when conjA; hermitian (A == B,
+// conjA, M == N) computes the upper block triangle and mirrors it.  ws holds
+// the slices; the product is done in K chunks when ws is smaller than
+// ozaki_workspace_bytes.  cudaErrorMemoryAllocation if ws cannot hold one
+// chunk of 16.
+// With timer set, a pair of events brackets every launch of the main kernel
+// and *tc_flops grows by the tensor-core flops it issues.
+struct EventPool;
+cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
+                        const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
+                        double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
+                        int64_t *launches, EventPool *timer = nullptr, double *tc_flops = nullptr);
+size_t ozaki_workspace_bytes(int M, int N, int K, bool hermitian);
+// bf16 tensor-core flops the product issues (2 per multiply-add of slices)
+double ozaki_tc_flops(int M, int N, int K, bool hermitian);
 
 }  // namespace rsrr

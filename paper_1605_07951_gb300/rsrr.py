@@ -28,6 +28,7 @@ RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7
 RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = range(6)
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
+RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI = 0, 1, 2
 RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ = 0, 1
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",
@@ -60,7 +61,8 @@ class rsrr_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_refine", C.c_int32), ("eta_tol", C.c_double),
                 ("delta", C.c_double), ("delta_floor", C.c_double), ("tol_gap", C.c_double),
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
-                ("host_threads", C.c_int32), ("timing", C.c_int32)]
+                ("host_threads", C.c_int32), ("timing", C.c_int32), ("gemm", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class rsrr_stats(C.Structure):
@@ -70,7 +72,8 @@ class rsrr_stats(C.Structure):
                 ("kc", C.c_int32), ("max_eta", C.c_double), ("sigma1", C.c_double),
                 ("sigmak", C.c_double), ("device_bytes", C.c_size_t),
                 ("launches", C.c_int64), ("stage_ms", C.c_double * 6),
-                ("gemm_flops", C.c_double), ("gemm_ms", C.c_double)]
+                ("gemm_flops", C.c_double), ("gemm_ms", C.c_double),
+                ("tc_flops", C.c_double), ("tc_ms", C.c_double)]
 
 
 class rsrr_result(C.Structure):
@@ -109,6 +112,9 @@ rsrr_last_error = _sig("rsrr_last_error", C.c_char_p, [_h])
 rsrr_destroy = _sig("rsrr_destroy", None, [_h])
 rsrr_solve_band_noalloc = _sig("rsrr_solve_band_noalloc", C.c_int,
                                [C.c_int64, C.c_int32, C.c_int32, _p, C.c_int32, _p, _p, _p])
+rsrr_zgemm = _sig("rsrr_zgemm", C.c_int,
+                  [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, C.c_int64, _p, C.c_int64, _p,
+                   C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_size_t, _p])
 
 
 class RSRRError(RuntimeError):

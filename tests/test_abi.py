@@ -75,3 +75,32 @@ def test_create_rejects_bad_descriptors_without_touching_the_gpu(lib):
     with pytest.raises(rsrr.RSRRError) as e:
         rsrr.Solver(p)
     assert e.value.status == rsrr.RSRR_EINVAL
+
+
+def test_ctypes_structs_match_the_c_compiler(tmp_path):
+    """sizeof and every field offset of the public structs, as gcc sees the
+    header, against the binding's ctypes mirrors."""
+    from paper_1605_07951_gb300 import rsrr
+    structs = [rsrr.rsrr_opts, rsrr.rsrr_stats, rsrr.rsrr_nep, rsrr.rsrr_region,
+               rsrr.rsrr_result, rsrr.rsrr_fn]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rsrr.h"', 'int main(void) {']
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append('return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        name, field, val = line.split()
+        st = getattr(rsrr, name)
+        want = ctypes.sizeof(st) if field == "size" else getattr(st, field).offset
+        assert int(val) == want, (name, field, int(val), want)
+        seen += 1
+    assert seen == sum(len(s._fields_) + 1 for s in structs)

@@ -50,11 +50,18 @@ FAMILIES = [
 ]
 
 
+# the projection's dense products: native FP64, or FP64-accurate slices on
+# the bf16 tensor cores (forced here even where the sizes would pick FP64)
+GEMMS = [1, 2]
+GEMM_IDS = ["fp64gemm", "ozaki"]
+
+
+@pytest.mark.parametrize("gemm", GEMMS, ids=GEMM_IDS)
 @pytest.mark.parametrize("name,make,NQ,KQ", FAMILIES, ids=[f[0] for f in FAMILIES])
-def test_eigenpairs_match_oracle(rs, name, make, NQ, KQ):
+def test_eigenpairs_match_oracle(rs, name, make, NQ, KQ, gemm):
     p = make()
     ref = oracle.rsrr(p, NQ=NQ, KQ=KQ)
-    out = gpu_rsrr(rs, p, NQ=NQ, KQ=KQ)
+    out = gpu_rsrr(rs, p, NQ=NQ, KQ=KQ, gemm=gemm)
     assert len(ref["lam"]) > 0
     assert len(out["lam"]) == len(ref["lam"]), (len(out["lam"]), len(ref["lam"]))
     assert match_eigs(ref["lam"], out["lam"]) <= 1e-9
@@ -64,10 +71,11 @@ def test_eigenpairs_match_oracle(rs, name, make, NQ, KQ):
         assert oracle.residual(p, lam, v) <= 1e-10
 
 
+@pytest.mark.parametrize("gemm", GEMMS, ids=GEMM_IDS)
 @pytest.mark.parametrize("name,make,NQ,KQ", FAMILIES[:4], ids=[f[0] for f in FAMILIES[:4]])
-def test_basis_is_orthonormal_and_contains_the_eigenvectors(rs, name, make, NQ, KQ):
+def test_basis_is_orthonormal_and_contains_the_eigenvectors(rs, name, make, NQ, KQ, gemm):
     p = make()
-    out = gpu_rsrr(rs, p, NQ=NQ, KQ=KQ)
+    out = gpu_rsrr(rs, p, NQ=NQ, KQ=KQ, gemm=gemm)
     Q = out["Q"]
     k = Q.shape[1]
     assert np.abs(Q.conj().T @ Q - np.eye(k)).max() <= 1e-12
@@ -79,10 +87,11 @@ def test_basis_is_orthonormal_and_contains_the_eigenvectors(rs, name, make, NQ, 
     assert abs(out["stats"]["sigma1"] - ref["sigma"][0]) <= 1e-8 * ref["sigma"][0]
 
 
+@pytest.mark.parametrize("gemm", GEMMS, ids=GEMM_IDS)
 @pytest.mark.parametrize("name,make,NQ,KQ", FAMILIES[:4], ids=[f[0] for f in FAMILIES[:4]])
-def test_projected_coefficients_equal_QH_A_Q(rs, name, make, NQ, KQ):
+def test_projected_coefficients_equal_QH_A_Q(rs, name, make, NQ, KQ, gemm):
     p = make()
-    out = gpu_rsrr(rs, p, NQ=NQ, KQ=KQ)
+    out = gpu_rsrr(rs, p, NQ=NQ, KQ=KQ, gemm=gemm)
     P_ref = oracle.project(p, out["Q"])
     for i, (Pg, Pr) in enumerate(zip(out["P"], P_ref)):
         a1 = np.abs(oracle.coeff_matrix(p, i)).sum(axis=0).max()
@@ -94,8 +103,9 @@ def test_count_zero_region_reports_no_eigenpairs(rs):
     assert len(out["lam"]) == 0
 
 
+@pytest.mark.parametrize("gemm", GEMMS, ids=GEMM_IDS)
 @pytest.mark.parametrize("mode", ["fp64", "mixed_tight"])
-def test_loaded_string_example_of_the_paper(rs, mode):
+def test_loaded_string_example_of_the_paper(rs, mode, gemm):
     """The paper's residual level (~1e-11 in ||T v||/||v||) comes from FP64
     solves: the FP64 path reaches it, and so does the mixed path once its
     refinement target is tightened from 1e-10 to 1e-14."""
@@ -104,10 +114,10 @@ def test_loaded_string_example_of_the_paper(rs, mode):
     # the paper's truncation delta = 1e-14 (Section 3.3) as the resolution floor
     if mode == "fp64":
         out = gpu_rsrr(rs, p, NQ=gold["NQ"], KQ=gold["KQ"], precision=rs.RSRR_PREC_FP64,
-                       delta_floor=1e-14)
+                       delta_floor=1e-14, gemm=gemm)
     else:
         out = gpu_rsrr(rs, p, NQ=gold["NQ"], KQ=gold["KQ"], eta_tol=1e-14, max_refine=12,
-                       delta_floor=1e-14)
+                       delta_floor=1e-14, gemm=gemm)
     lo, hi = gold["interval"]
     lam = out["lam"]
     assert len(lam) == gold["count"]
