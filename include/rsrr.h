@@ -158,6 +158,12 @@ enum { RSRR_PREC_FP64 = 0, RSRR_PREC_MIXED = 1 };
  *   RSRR_GEMM_AUTO   OZAKI for products of at least 2^30 flops, else FP64. */
 enum { RSRR_GEMM_AUTO = 0, RSRR_GEMM_FP64 = 1, RSRR_GEMM_OZAKI = 2 };
 
+/* RSRR_FLAG_PLAIN_SOLVE: banded solves of rsrr_sample by the one-kernel
+ * solve (factor panels read straight from global memory) instead of the
+ * streaming solve; same arithmetic, kept for comparison and as the fallback
+ * for bands too wide for the streaming solve's shared-memory window. */
+enum { RSRR_FLAG_PLAIN_SOLVE = 1 };
+
 typedef struct {
     int32_t precision;   /* RSRR_PREC_MIXED by default */
     int32_t max_refine;  /* refinement sweeps, default 8 */
@@ -172,7 +178,7 @@ typedef struct {
     int32_t timing;      /* nonzero: record CUDA events around every stage on the
                             caller's stream; times appear in rsrr_stats.stage_ms */
     int32_t gemm;        /* RSRR_GEMM_AUTO by default */
-    int32_t reserved;
+    int32_t flags;       /* RSRR_FLAG_* bits, 0 by default */
 } rsrr_opts;
 
 typedef struct rsrr_handle rsrr_t;

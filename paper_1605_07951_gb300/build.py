@@ -25,6 +25,7 @@ UNITS = [
     ("noalloc.cu", [], "noalloc.o"),
     ("dense.cu", [], "dense.o"),
     ("ozaki.cu", [], "ozaki.o"),
+    ("band_solve2.cu", [], "band_solve2.o"),
 ]
 
 

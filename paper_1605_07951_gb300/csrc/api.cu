@@ -419,6 +419,15 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     CK(alloc(&d_done, N), "alloc");
     CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
     const size_t band = (size_t)geom.ldab * n * N;
+    {
+        const size_t smem2 = opts.precision == RSRR_PREC_MIXED ? band_solve2_smem_c64(geom)
+                                                               : band_solve2_smem_c128(geom);
+        solve2 = !(opts.flags & RSRR_FLAG_PLAIN_SOLVE) && smem2 <= 227 * 1024 &&
+                 geom.kl + geom.nb <= KL_MAX + 32;
+        if (solve2)
+            CK(alloc(&d_bperm, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb),
+               "alloc block permutations");
+    }
     if (opts.precision == RSRR_PREC_MIXED) {
         CK(alloc(&d_ab32, band), "alloc band factors (complex64)");
         CK(alloc(&d_dinv32, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
@@ -464,6 +473,21 @@ rsrr_status Handle::mark(int i, cudaStream_t s) {
     return RSRR_OK;
 }
 
+// X = (P L U)^{-1} X in place for every point not skipped (factors of the
+// last LU): the streaming solve when it fits, else the one-kernel solve.
+cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, cudaStream_t s) {
+    const int nn = (int)n;
+    if (mixed)
+        return solve2 ? launch_band_solve2_c64(d_ab32, d_bperm, d_dinv32, static_cast<float2 *>(B), geom,
+                                               N, nn, L, skip, s)
+                      : launch_band_solve_c64(d_ab32, d_piv, d_dinv32, static_cast<float2 *>(B), geom, N,
+                                              nn, L, skip, s);
+    return solve2 ? launch_band_solve2_c128(d_ab64, d_bperm, d_dinv64, static_cast<double2 *>(B), geom, N,
+                                            nn, L, skip, s)
+                  : launch_band_solve_c128(d_ab64, d_piv, d_dinv64, static_cast<double2 *>(B), geom, N,
+                                           nn, L, skip, s);
+}
+
 // Step 2 of RSRR on the GPU, asynchronously on stream s.
 rsrr_status Handle::sample(cudaStream_t s) {
     Handle *h = this;
@@ -477,9 +501,13 @@ rsrr_status Handle::sample(cudaStream_t s) {
         CK(launch_assemble<float2>(d_ab32, geom, dp, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
         CK(launch_band_lu_c64(d_ab32, d_piv, d_info, d_dinv32, geom, N, nn, s), "band LU");
+        if (solve2) {
+            CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "block permutations");
+            launches += 1;
+        }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
-        CK(launch_band_solve_c64(d_ab32, d_piv, d_dinv32, d_D, geom, N, nn, L, nullptr, s), "band solve");
+        CK(band_solve(true, d_D, nullptr, s), "band solve");
         CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
         CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
@@ -489,7 +517,7 @@ rsrr_status Handle::sample(cudaStream_t s) {
             CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
                           d_sweep_flags + it, d_done, s), "eta");
             CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
-            CK(launch_band_solve_c64(d_ab32, d_piv, d_dinv32, d_D, geom, N, nn, L, d_done, s), "band solve");
+            CK(band_solve(true, d_D, d_done, s), "band solve");
             CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
             launches += 5;
         }
@@ -497,9 +525,13 @@ rsrr_status Handle::sample(cudaStream_t s) {
         CK(launch_assemble<double2>(d_ab64, geom, dp, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
         CK(launch_band_lu_c128(d_ab64, d_piv, d_info, d_dinv64, geom, N, nn, s), "band LU");
+        if (solve2) {
+            CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "block permutations");
+            launches += 1;
+        }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
-        CK(launch_band_solve_c128(d_ab64, d_piv, d_dinv64, d_X, geom, N, nn, L, nullptr, s), "band solve");
+        CK(band_solve(false, d_X, nullptr, s), "band solve");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         launches += 4;  // assemble, LU, probe, solve
     }

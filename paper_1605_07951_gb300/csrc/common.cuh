@@ -8,6 +8,9 @@
 #ifndef RSRR_DEV
 #define RSRR_DEV __device__ __forceinline__
 #endif
+#ifndef RSRR_HD
+#define RSRR_HD __host__ __device__ inline
+#endif
 
 template <typename C> struct real_of;
 template <> struct real_of<float2> { using type = float; };

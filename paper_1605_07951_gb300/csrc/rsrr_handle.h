@@ -48,6 +48,8 @@ struct Handle {
     float2 *d_dinv32 = nullptr;       // per block L11^{-1}, U11^{-1} (complex64)
     double2 *d_dinv64 = nullptr;      // per block L11^{-1}, U11^{-1} (complex128)
     int32_t *d_piv = nullptr, *d_info = nullptr, *d_done = nullptr, *d_sweep_flags = nullptr;
+    int32_t *d_bperm = nullptr;       // composed row permutation of every block (streaming solve)
+    bool solve2 = false;              // streaming band solve in use
     double *d_tnorm = nullptr, *d_eta = nullptr, *d_rmax = nullptr, *d_xmax = nullptr;
 
     // projection stage (proj.cu)
@@ -84,6 +86,7 @@ struct Handle {
     template <typename T> cudaError_t alloc(T **p, size_t count);
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);
     rsrr_status sample(cudaStream_t s);
+    cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, cudaStream_t s);
     rsrr_status sample_dense(cudaStream_t s);
     rsrr_status dense_residual(bool skip_done, cudaStream_t s);
     rsrr_status allocate_dense();

@@ -89,6 +89,21 @@ cudaError_t launch_dense_eig_residual(const double2 *V, const double2 *lam, cons
                                       cudaStream_t s);
 cudaError_t launch_narrow_all(float2 *D, const double2 *S, int64_t total, cudaStream_t s);
 
+// ---- streaming band solve (band_solve2.cu): composed block permutations
+// (2 nb ints per block) after each LU, then the pipelined solve.  The solve
+// returns cudaErrorInvalidConfiguration when its shared memory (see
+// band_solve2_smem_*) exceeds 227 KB; the caller then uses launch_band_solve_*.
+cudaError_t launch_block_perm(int32_t *bperm, const int32_t *piv, int n, int kl, int nb, int N,
+                              cudaStream_t s);
+size_t band_solve2_smem_c64(const BandGeom &g);
+size_t band_solve2_smem_c128(const BandGeom &g);
+cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const float2 *dinv,
+                                   float2 *B, const BandGeom &g, int N, int n, int L,
+                                   const int32_t *skip, cudaStream_t s);
+cudaError_t launch_band_solve2_c128(const double2 *ab, const int32_t *bperm, const double2 *dinv,
+                                    double2 *B, const BandGeom &g, int N, int n, int L,
+                                    const int32_t *skip, cudaStream_t s);
+
 // ---- CUDA events recorded in pairs around launches (grown on demand; api.cu)
 struct EventPool {
     std::vector<cudaEvent_t> ev;

@@ -29,6 +29,7 @@ RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = 
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI = 0, 1, 2
+RSRR_FLAG_PLAIN_SOLVE = 1
 RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ = 0, 1
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",
@@ -62,7 +63,7 @@ class rsrr_opts(C.Structure):
                 ("delta", C.c_double), ("delta_floor", C.c_double), ("tol_gap", C.c_double),
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
                 ("host_threads", C.c_int32), ("timing", C.c_int32), ("gemm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
 
 class rsrr_stats(C.Structure):

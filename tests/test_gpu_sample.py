@@ -146,3 +146,26 @@ def test_full_size_grid_rational_sampled_parity(rs):
         Xg = S[:, j * p.L:(j + 1) * p.L]
         assert oracle.backward_error_inf(p, zo[j], Xg).max() <= ETA_TOL
         assert np.abs(Xg - Xr).max() / np.abs(Xr).max() <= 1e-6
+
+
+# the streaming solve (factor panels through a cp.async ring) against the
+# one-kernel solve on the same factors: one solve, no refinement
+SOLVE_CASES = [CASES[0], CASES[1], CASES[2], CASES[3], CASES[4],
+               ("wide_band_many_blocks", lambda: W.random_banded(n=2000, kl=150, ku=140, N=3, L=19, seed=11)),
+               ("band_wider_than_rows", lambda: W.random_banded(n=70, kl=66, ku=60, N=2, L=16, seed=12))]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,make", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_streaming_solve_matches_the_one_kernel_solve(rs, name, make, precision):
+    p = make()
+    a = run(rs, p, precision, max_refine=0)
+    b = run(rs, p, precision, max_refine=0, flags=rs.RSRR_FLAG_PLAIN_SOLVE)
+    scale = np.abs(b["S"]).max()
+    # same factors, same operations in another order: complex64 or complex128 rounding
+    tol = 1e-4 if precision == 1 else 1e-11
+    assert np.abs(a["S"] - b["S"]).max() <= tol * scale
+    # and both are solutions: the refined streaming path reaches the oracle
+    if precision == 1:
+        out = run(rs, p, precision)
+        compare(p, out, rel_tol=1e-6, eta_tol=ETA_TOL)
