@@ -31,7 +31,6 @@ WORKLOAD = "grid5pt_rational_n40000_bw200_N64_L32"
 METRIC = "resolvent columns/s at 1e-10 rel. residual (mixed vs FP64); RSRR p50/p99 latency"
 UNIT = "resolvent columns/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x FMA x max SM clock (THz)
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (an FMA-chain probe measured 1.20 at 2.0 GHz)
 # band LU DRAM traffic per point and per stored band entry, from one ncu capture
 # at n = 4096, bandwidth 64 (961.8 MB for 64 points, 224 x 4096 entries each)
 LU_TRAFFIC_PER_ENTRY = 961.79e6 / (64 * 224 * 4096)
@@ -51,6 +50,9 @@ def parse():
                     help="c1: banded grid (the benchmark line); c2: dense kernel, sampling only")
     ap.add_argument("--sample-points", type=int, default=2,
                     help="sampling points of the oracle's bounded sample")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving latency leg")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -97,6 +99,19 @@ def cpu_baseline(g, npts):
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{npts} of the 64 sampling points ({d['columns']} resolvent columns, "
                       f"scipy banded LU, FP64) in {d['seconds']:.1f} s, 1 BLAS thread"}
+
+
+def measured_peaks():
+    """Roofline denominators: the measured copy bandwidth and bf16 GEMM rates
+    of this GPU model (MEASURED_PEAKS.json), else the fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_burst": d["bf16_tflops"],
+                "bf16_sustained": d["bf16_tflops_sustained"], "source": "of measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_burst": 1900.0, "bf16_sustained": 1700.0,
+                "source": "of fallback"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -187,6 +202,57 @@ def run_e2e(a, s, p, stats, stream, world):
     return e2e
 
 
+# ---------------------------------------------------------------- serving leg
+def serve_stream(rsrr, reqs, rate, precision, slots, seed):
+    """Submit `reqs` to a request server with Poisson arrivals at `rate`
+    requests/s (rate None: all at t = 0) and wait for every reply.  Latency is
+    measured from the scheduled arrival to the result on the host."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    sched = np.cumsum(gaps) - gaps[0]
+    sv = rsrr.Server(slots=slots)
+    ids, lag = [], []
+    t0 = time.perf_counter()
+    for (fam, p), ts in zip(reqs, sched):
+        while time.perf_counter() - t0 < ts:
+            time.sleep(min(1e-3, max(0.0, ts - (time.perf_counter() - t0))))
+        lag.append(time.perf_counter() - t0 - ts)
+        ids.append(sv.submit(p, rsrr.default_opts(precision=precision)))
+    reps = [sv.wait(i, timeout=1800.0) for i in ids]
+    t_end = time.perf_counter() - t0
+    st = sv.stats()
+    for i in ids:
+        sv.release(i)
+    sv.close()
+    lat = np.array([(r["t_done"] - r["t_submit"]) + lg for r, lg in zip(reps, lag)])
+    cols = sum(p.N * p.L for _, p in reqs)
+    ok = sum(1 for r in reps if r["status"] >= 0)
+    return {"requests": len(reqs), "ok": ok, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "makespan_s": t_end, "req_per_s": len(reqs) / t_end, "columns_per_s": cols / t_end,
+            "peak_active": st["peak_active"], "peak_bytes": int(st["peak_bytes"])}
+
+
+def run_serving(a):
+    """Serving of RSRR requests (rsrr_server_*): capacity from a closed burst,
+    then Poisson arrivals at 0.7 x that capacity, mixed precision and the plain
+    FP64 path, p50/p99 latency from arrival to eigenpairs on the host."""
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    reqs = W.serving_stream(a.serve_requests, seed=5000)
+    mixed = rsrr.RSRR_PREC_MIXED
+    serve_stream(rsrr, reqs[:4], None, mixed, a.serve_slots, 1)  # warm-up
+    burst = serve_stream(rsrr, reqs, None, mixed, a.serve_slots, 5001)
+    rate = 0.7 * burst["req_per_s"]
+    poisson = serve_stream(rsrr, reqs, rate, mixed, a.serve_slots, 5002)
+    poisson64 = serve_stream(rsrr, reqs, rate, rsrr.RSRR_PREC_FP64, a.serve_slots, 5002)
+    return {"workload": f"{len(reqs)} requests, families c0/c1/c2 shapes (quadratic n=1000; "
+                        "grid g=40..100; dense n=128..512), random regions, seed 5000",
+            "slots": a.serve_slots, "budget_gb": 150, "burst": burst,
+            "poisson_rate_req_per_s": rate, "poisson_mixed": poisson, "poisson_fp64_plain": poisson64}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(a, rank, world, local):
     import numpy as np
@@ -219,7 +285,7 @@ def run_ours(a, rank, world, local):
 
     clocks = ClockSampler(local)
     clocks.start()
-    lu_ms, sample_ms, project_ms, gemm_ms, gemm_flops = [], [], [], [], []
+    lu_ms, sample_ms, project_ms, gemm_ms, gemm_flops, tc_ms, tc_flops = [], [], [], [], [], [], []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -236,6 +302,8 @@ def run_ours(a, rank, world, local):
         project_ms.append(sti["stage_ms"][5])
         gemm_ms.append(sti["gemm_ms"])
         gemm_flops.append(sti["gemm_flops"])
+        tc_ms.append(sti["tc_ms"])
+        tc_flops.append(sti["tc_flops"])
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -257,18 +325,25 @@ def run_ours(a, rank, world, local):
     if not a.no_e2e:
         e2e = run_e2e(a, s, p, stats, stream, world)
     fp64 = None
-    # roofline of the dominant kernel: the FP64 GEMMs of rsrr_project (about
-    # three quarters of a step in the ncu launch list); their algorithmic
-    # flops and event-timed device time come from the library per step
-    g_ach = statistics.mean(gemm_flops) / (statistics.mean(gemm_ms) / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": "zgemm_kernel (FP64 complex GEMMs of rsrr_project)",
-            "achieved": g_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": g_ach / FP64_PEAK_TFLOPS, "traffic": None,
-            "algorithmic_flop_per_step": statistics.mean(gemm_flops),
-            "gemm_ms_per_step": statistics.mean(gemm_ms),
-            "peak_note": "GB300 nominal FP64 (recipe); FMA-chain probe measured 1.20 TFLOP/s; "
-                         "traffic null: the GEMMs of a step have many shapes"}
-    # secondary: the band LU of rsrr_sample (FP32 FMA pipe)
+    # rooflines of the two kernels that dominate a step, from the library's
+    # own CUDA events on the launching stream (opts.timing): the bf16 slice
+    # products of the FP64-accurate GEMMs of rsrr_project (tensor pipe) and
+    # the complex64 band LU of rsrr_sample (FP32 FMA pipe); "roofline" is the
+    # one with more device time per step
+    peaks = measured_peaks()
+    tc_avg = statistics.mean(tc_ms)
+    tc_ach = statistics.mean(tc_flops) / (tc_avg / 1e3) / 1e12 if tc_avg > 0 else 0.0
+    roof_tc = {"bound": "tensor", "kernel": "oz_gemm_kernel (bf16 slice products, Ozaki GEMMs)",
+               "achieved": tc_ach, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
+               "frac": tc_ach / peaks["bf16_sustained"], "traffic": None,
+               "tensor_flop_per_step": statistics.mean(tc_flops), "ms_per_step": tc_avg,
+               "peak_note": f"bf16 dense, sustained, {peaks['source']}; flops = the 28 slice-pair "
+                            "products per tile the scheme needs (mma.sync m16n8k16); traffic null: "
+                            "many GEMM shapes per step",
+               "fp64_equivalent": {"flop_per_step": statistics.mean(gemm_flops),
+                                   "gemm_ms_per_step": statistics.mean(gemm_ms),
+                                   "tflops": statistics.mean(gemm_flops)
+                                   / (statistics.mean(gemm_ms) / 1e3) / 1e12}}
     n, kl, ku = p.n, stats["kl"], stats["ku"]
     flop_per_point = 8.0 * sum(min(kl, n - 1 - j) * min(kl + ku, n - 1 - j) for j in range(n))
     lu_flops = flop_per_point * p.N
@@ -282,6 +357,7 @@ def run_ours(a, rank, world, local):
                "algorithmic_flop_per_launch": lu_flops, "avg_launch_ms": lu_avg,
                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; traffic "
                             "scaled from an ncu capture at n=4096 by stored band entries"}
+    roof, roof_other = (roof_lu, roof_tc) if lu_avg >= tc_avg else (roof_tc, roof_lu)
 
     if not a.no_fp64:
         s64 = rsrr.Solver(p, rsrr.default_opts(precision=rsrr.RSRR_PREC_FP64, timing=1))
@@ -314,10 +390,12 @@ def run_ours(a, rank, world, local):
         "project_ms": statistics.mean(project_ms), "rank_k": stats["k"],
         "pivoted_cholesky_kc": stats["kc"],
         "fp64_plain_path": fp64,
-        "roofline": roof, "roofline_band_lu": roof_lu, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roof, "roofline_second": roof_other, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
     }
     s.close()
+    if not a.no_serving and rank == 0:
+        line["serving"] = run_serving(a)
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a.g, a.sample_points)
     if rank == 0:

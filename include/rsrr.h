@@ -254,8 +254,10 @@ rsrr_status rsrr_check(rsrr_t *h, void *stream);
  * final products run asynchronously. */
 rsrr_status rsrr_project(rsrr_t *h, void *stream);
 
-/* Steps 4-5, host part (synchronises the handle's work first): SS-FULL on
- * T_Q(z) = sum_i f_i(z) P_i in FP64, v = Q g and residuals on the GPU.
+/* Steps 4-5 (synchronises the handle's work first): SS-FULL on
+ * T_Q(z) = sum_i f_i(z) P_i in FP64 -- the moments of T_Q^{-1} over the N_Q
+ * quadrature nodes on the GPU (batched complex128 LU), the Hankel SVD and
+ * the small eigenproblem on the host -- then v = Q g and residuals on the GPU.
  * Returns OK or WGAP (gap test failed; results still filled). */
 rsrr_status rsrr_solve(rsrr_t *h, rsrr_result *out);
 
@@ -341,6 +343,109 @@ rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsr
                        int64_t lda, const rsrr_c128 *B, int64_t ldb, rsrr_c128 *C, int64_t ldc,
                        double alpha, double beta, int32_t method, int32_t hermitian,
                        size_t max_ws_bytes, void *stream);
+
+/* Device bytes a handle for this problem holds at its peak (its buffers, the
+ * projection work space and rsrr_solve's temporaries), without allocating
+ * anything or touching the GPU.  Same arguments and validation as
+ * rsrr_create; the request server admits requests by this number. */
+rsrr_status rsrr_estimate_bytes(const rsrr_nep *nep, const rsrr_region *region, int32_t N,
+                                int32_t L, const rsrr_opts *opts, size_t *bytes);
+
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of whole RSRR solves on one GPU.
+ *
+ * Requests (a NEP, a region, N, L, options and optionally a probe U) are
+ * queued by rsrr_server_submit and run by `slots` worker threads, each with
+ * its own non-blocking CUDA stream: a request is admitted, in arrival order,
+ * as soon as a slot is free and its rsrr_estimate_bytes fit in what the
+ * memory budget has left (a later request may pass a waiting one that does
+ * not fit yet, at most 8 times).  Admitted requests allocate from the
+ * server's stream-ordered memory pool and run rsrr_sample, rsrr_project and
+ * rsrr_solve; their kernels overlap on the device with those of the other
+ * admitted requests, and each request's host work overlaps with the others'
+ * GPU work.  Results (eigenvalues, residuals, eigenvectors) are copied to
+ * host memory owned by the server.  Each request runs the same kernels on
+ * the same inputs as a lone handle would: its results do not depend on what
+ * else runs.
+ * ------------------------------------------------------------------------ */
+typedef struct rsrr_server rsrr_server_t;
+
+typedef struct {
+    int32_t slots;            /* requests on the device at once, 1..64, default 4 */
+    int32_t keep;             /* nonzero: a finished request keeps its handle (factors,
+                                 S, Q, P_i) resident, and its bytes counted against
+                                 the budget, until rsrr_server_release; default 0 */
+    int64_t mem_budget_bytes; /* device bytes the admitted requests may hold together,
+                                 default 150e9 */
+    int32_t device;           /* CUDA device; -1 (default): the current device */
+    int32_t reserved;
+} rsrr_server_opts;
+
+typedef struct {
+    int64_t id;
+    int32_t status;        /* the request's outcome: OK, WGAP (results filled) or an error */
+    int32_t count, nbar, k, refine_sweeps;
+    double gmax, max_eta;
+    double t_submit;       /* seconds since rsrr_server_create: submission (arrival), */
+    double t_admit;        /* admission (slot and memory granted) and */
+    double t_done;         /* results on the host */
+    size_t device_bytes;   /* bytes admitted against the budget */
+    int64_t n;
+    const rsrr_c128 *lam;  /* count eigenvalues, as rsrr_result */
+    const double *res;     /* count residuals, as rsrr_result */
+    const rsrr_c128 *V;    /* n x count eigenvectors, as rsrr_result */
+    const char *error;     /* one line if status < 0, else "" */
+} rsrr_reply;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int32_t queued, active, peak_active, reserved;
+    size_t used_bytes, peak_bytes, budget_bytes;
+    double now;            /* seconds since rsrr_server_create */
+} rsrr_server_stats;
+
+/* Fills `o` with the defaults listed above. */
+void rsrr_server_opts_default(rsrr_server_opts *o);
+
+/* Starts a server on the device (memory pool, worker threads and streams).
+ * Errors: EINVAL (slots or budget out of range), ECUDA, ENOMEM; message in
+ * rsrr_last_error(NULL). */
+rsrr_status rsrr_server_create(const rsrr_server_opts *opts, rsrr_server_t **out);
+
+/* Queues one request and returns its id (> 0).  The descriptors are
+ * validated and copied as by rsrr_create, and U (host, n x L, column major,
+ * NULL for the default probe) is copied; the caller may free all of them on
+ * return.  opts.host_threads == 0 gives the request's host work
+ * cores / slots threads.  Errors: EINVAL (descriptor), ENOMEM (the request
+ * alone exceeds the budget), ESTATE (server shutting down). */
+rsrr_status rsrr_server_submit(rsrr_server_t *server, const rsrr_nep *nep,
+                               const rsrr_region *region, int32_t N, int32_t L,
+                               const rsrr_opts *opts, const rsrr_c128 *U, int64_t *id);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for request `id` and fills
+ * *out; the arrays it points to stay valid until rsrr_server_release(id).
+ * Returns OK (the request's own outcome is out->status), ETIMEOUT (not
+ * finished in time; *out untouched) or EINVAL (unknown id). */
+rsrr_status rsrr_server_wait(rsrr_server_t *server, int64_t id, double timeout_s,
+                             rsrr_reply *out);
+
+/* With opts.keep: the finished request's handle, for rsrr_get_Q,
+ * rsrr_get_projected, rsrr_get_samples, rsrr_get_stats ...; owned by the
+ * server (do not destroy it).  NULL if the request is unknown, unfinished,
+ * failed, or the server does not keep handles. */
+rsrr_t *rsrr_server_handle(rsrr_server_t *server, int64_t id);
+
+/* Forgets a finished request: frees its host results and, with keep, its
+ * handle, whose bytes go back to the budget.  EINVAL (unknown id), ESTATE
+ * (not finished). */
+rsrr_status rsrr_server_release(rsrr_server_t *server, int64_t id);
+
+/* Counters and memory use of the server. */
+rsrr_status rsrr_server_get_stats(rsrr_server_t *server, rsrr_server_stats *out);
+
+/* Lets the admitted requests finish, drops the queued ones, frees every
+ * request, the pool and the workers.  NULL is allowed. */
+void rsrr_server_destroy(rsrr_server_t *server);
 
 #ifdef __cplusplus
 }

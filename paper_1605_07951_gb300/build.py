@@ -21,11 +21,13 @@ UNITS = [
     ("band_lu.cu", ["-DRSRR_LU_ONLY=64"], "band_lu64.o"),
     ("band_lu.cu", ["-DRSRR_LU_ONLY=128"], "band_lu128.o"),
     ("proj.cu", [], "proj.o"),
-    ("ssfull_host.cpp", ["-x", "cu"], "ssfull_host.o"),
+    ("ssfull_host.cpp", ["-x", "cu", "-Xcompiler", "-fcx-fortran-rules"], "ssfull_host.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("dense.cu", [], "dense.o"),
     ("ozaki.cu", [], "ozaki.o"),
     ("band_solve2.cu", [], "band_solve2.o"),
+    ("server.cu", [], "server.o"),
+    ("ssfull_dev.cu", [], "ssfull_dev.o"),
 ]
 
 

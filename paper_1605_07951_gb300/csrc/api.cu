@@ -71,16 +71,36 @@ rsrr_status Handle::fail(rsrr_status st, const char *what, cudaError_t e) {
 template <typename T> cudaError_t Handle::alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    return raw_alloc((void **)p, sizeof(T) * count);
+}
+
+// device memory owned by the handle: cudaMalloc, or the server's
+// stream-ordered pool on hs; in dry mode only the bytes are counted
+cudaError_t Handle::raw_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (dry) {
+        device_bytes += bytes;
+        return cudaSuccess;
+    }
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, hs) : cudaMalloc(p, bytes);
     if (e == cudaSuccess) {
-        allocations.push_back((void *)*p);
-        device_bytes += sizeof(T) * count;
+        allocations.push_back(*p);
+        device_bytes += bytes;
     }
     return e;
 }
 
+// frees a buffer obtained outside alloc() (temporary buffers of rsrr_solve)
+cudaError_t Handle::raw_free(void *p) { return pool ? cudaFreeAsync(p, hs) : cudaFree(p); }
+
+// waits for the handle's work: its own stream, or the whole device
+cudaError_t Handle::wait() { return hs ? cudaStreamSynchronize(hs) : cudaDeviceSynchronize(); }
+
 Handle::~Handle() {
-    for (void *p : allocations) cudaFree(p);
+    for (void *p : allocations) {
+        if (pool) cudaFreeAsync(p, hs);
+        else cudaFree(p);
+    }
     for (auto &e : events)
         if (e) cudaEventDestroy(e);
 }
@@ -150,13 +170,45 @@ static rsrr_status create_fail(const char *msg) {
 }
 
 namespace rsrr {
-rsrr_status create_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
-                         const rsrr_opts *opts, rsrr_t **out);
+rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                          const rsrr_opts *opts, Handle **out);
 }
 
 rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
                         const rsrr_opts *opts, rsrr_t **out) {
     if (!out) return create_fail("rsrr_create: out is NULL");
+    *out = nullptr;
+    Handle *h = nullptr;
+    rsrr_status st = rsrr::prepare(nep, region, N, L, opts, &h);
+    if (st != RSRR_OK) return st;
+    st = h->allocate();
+    if (st != RSRR_OK) {
+        rsrr::thread_error() = h->err;
+        delete h;
+        return st;
+    }
+    *out = reinterpret_cast<rsrr_t *>(h);
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_estimate_bytes(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                                const rsrr_opts *opts, size_t *bytes) {
+    if (!bytes) return create_fail("rsrr_estimate_bytes: bytes is NULL");
+    *bytes = 0;
+    Handle *h = nullptr;
+    rsrr_status st = rsrr::prepare(nep, region, N, L, opts, &h);
+    if (st != RSRR_OK) return st;
+    *bytes = h->estimate_bytes();
+    delete h;
+    return RSRR_OK;
+}
+
+}  // extern "C"
+
+namespace rsrr {
+
+rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                    const rsrr_opts *opts, Handle **out) {
     *out = nullptr;
     rsrr::thread_error().clear();
     if (!nep || !region) return create_fail("rsrr_create: nep or region is NULL");
@@ -164,7 +216,7 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
     if (N < 1 || L < 1) return create_fail("rsrr_create: N and L must be >= 1");
     if (nep->kind != RSRR_NEP_SPARSE && nep->kind != RSRR_NEP_HELMHOLTZ)
         return create_fail("rsrr_create: unknown NEP kind");
-    if (nep->kind == RSRR_NEP_HELMHOLTZ) return rsrr::create_dense(nep, region, N, L, opts, out);
+    if (nep->kind == RSRR_NEP_HELMHOLTZ) return rsrr::prepare_dense(nep, region, N, L, opts, out);
     if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
     if (!nep->row_ptr || !nep->col_idx || !nep->values)
         return create_fail("rsrr_create: pattern or values NULL");
@@ -258,7 +310,8 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
                            region->center.im + region->b * std::sin(al));
         }
     }
-    std::vector<double2> coef((size_t)N * nep->m);
+    std::vector<double2> &coef = h->h_coef;
+    coef.resize((size_t)N * nep->m);
     for (int j = 0; j < N; ++j)
         for (int i = 0; i < nep->m; ++i) {
             const cplx v = rsrr::eval_fn_host(nep->fn[i], h->z[j]);
@@ -268,16 +321,33 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
             }
             coef[(size_t)j * nep->m + i] = make_double2(v.real(), v.imag());
         }
-
-    rsrr_status st = h->allocate_and_upload(coef);
-    if (st != RSRR_OK) {
-        rsrr::thread_error() = h->err;
-        delete h;
-        return st;
-    }
-    *out = reinterpret_cast<rsrr_t *>(h);
+    *out = h;
     return RSRR_OK;
 }
+
+// device part of rsrr_create
+rsrr_status Handle::allocate() { return dense ? allocate_dense() : allocate_and_upload(h_coef); }
+
+// device bytes the handle will hold after rsrr_project and during rsrr_solve:
+// its buffers (counted by a dry run of allocate()), the projection's work
+// space, and rsrr_solve's temporaries (SS-FULL moment stage, eigenvector
+// block of up to 256 columns)
+size_t Handle::estimate_bytes() {
+    dry = true;
+    device_bytes = 0;
+    allocate();
+    dry = false;
+    size_t b = device_bytes;
+    device_bytes = 0;
+    b += projection_ws_bytes(N * L, n, m);
+    b += ssfull_dev_bytes(std::min<int64_t>((int64_t)N * L, n), m, opts.NQ, opts.KQ);
+    b += sizeof(double2) * ((size_t)n + (size_t)N * L + 8) * 256 + (1u << 20);
+    return b;
+}
+
+}  // namespace rsrr
+
+extern "C" {
 
 rsrr_status rsrr_set_probe(rsrr_t *hh, const rsrr_c128 *U, int32_t on_device, void *stream) {
     Handle *h = reinterpret_cast<Handle *>(hh);
@@ -439,22 +509,25 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
         CK(alloc(&d_dinv64, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
            "alloc block inverses");
     }
-    CK(cudaMemcpy(d_row_ptr, h_row_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_col_idx, h_col_idx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_vals, h_vals.data(), sizeof(double) * m * nnz, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_csc_ptr, h_csc_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_csc_row, h_csc_row.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_csc_perm, h_csc_perm.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_coef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice), "upload");
+    if (dry) return RSRR_OK;
+    // (pageable sources: each copy returns once its source has been staged)
+    const auto H2D = cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(d_row_ptr, h_row_ptr.data(), sizeof(int32_t) * (n + 1), H2D, hs), "upload");
+    CK(cudaMemcpyAsync(d_col_idx, h_col_idx.data(), sizeof(int32_t) * nnz, H2D, hs), "upload");
+    CK(cudaMemcpyAsync(d_vals, h_vals.data(), sizeof(double) * m * nnz, H2D, hs), "upload");
+    CK(cudaMemcpyAsync(d_csc_ptr, h_csc_ptr.data(), sizeof(int32_t) * (n + 1), H2D, hs), "upload");
+    CK(cudaMemcpyAsync(d_csc_row, h_csc_row.data(), sizeof(int32_t) * nnz, H2D, hs), "upload");
+    CK(cudaMemcpyAsync(d_csc_perm, h_csc_perm.data(), sizeof(int32_t) * nnz, H2D, hs), "upload");
+    CK(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double2) * coef.size(), H2D, hs), "upload");
     // default probe: complex normal entries from a fixed-seed generator;
     // rsrr_set_probe replaces it
     {
         std::vector<double2> U;
         default_probe(U, nL);
-        CK(cudaMemcpy(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice), "upload");
+        CK(cudaMemcpyAsync(d_U, U.data(), sizeof(double2) * nL, H2D, hs), "upload");
     }
-    CK(launch_colmax(d_umax, d_U, (int)n, L, 0), "colmax");
-    CK(cudaDeviceSynchronize(), "create sync");
+    CK(launch_colmax(d_umax, d_U, (int)n, L, hs), "colmax");
+    CK(wait(), "create sync");
     dp.n = n; dp.nnz = nnz; dp.N = N; dp.L = L; dp.m = m;
     dp.row_ptr = d_row_ptr; dp.col_idx = d_col_idx; dp.vals = d_vals;
     dp.csc_ptr = d_csc_ptr; dp.csc_row = d_csc_row; dp.csc_perm = d_csc_perm;
@@ -559,9 +632,11 @@ rsrr_status Handle::read_outcome() {
     }
     std::vector<int32_t> info(N), flags(opts.max_refine + 2);
     std::vector<double> eta((size_t)N * L);
-    CK(cudaMemcpy(info.data(), d_info, sizeof(int32_t) * N, cudaMemcpyDeviceToHost), "outcome");
-    CK(cudaMemcpy(flags.data(), d_sweep_flags, sizeof(int32_t) * flags.size(), cudaMemcpyDeviceToHost), "outcome");
-    CK(cudaMemcpy(eta.data(), d_eta, sizeof(double) * eta.size(), cudaMemcpyDeviceToHost), "outcome");
+    const auto D2H = cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int32_t) * N, D2H, hs), "outcome");
+    CK(cudaMemcpyAsync(flags.data(), d_sweep_flags, sizeof(int32_t) * flags.size(), D2H, hs), "outcome");
+    CK(cudaMemcpyAsync(eta.data(), d_eta, sizeof(double) * eta.size(), D2H, hs), "outcome");
+    CK(cudaStreamSynchronize(hs), "outcome");
     stat_singular = -1;
     for (int j = 0; j < N; ++j)
         if (info[j] != 0) { stat_singular = j; break; }
@@ -596,8 +671,8 @@ rsrr_status Handle::read_outcome() {
 // ---------------------------------------------------------------------------
 namespace rsrr {
 
-rsrr_status create_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
-                         const rsrr_opts *opts, rsrr_t **out) {
+rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                          const rsrr_opts *opts, Handle **out) {
     if (!nep->points) return create_fail("rsrr_create: Helmholtz kind without points");
     if (!(std::isfinite(nep->diag))) return create_fail("rsrr_create: diag is not finite");
     const int64_t n = nep->n;
@@ -651,13 +726,7 @@ rsrr_status create_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t
                            region->center.im + region->b * std::sin(al));
         }
     }
-    rsrr_status st = h->allocate_dense();
-    if (st != RSRR_OK) {
-        thread_error() = h->err;
-        delete h;
-        return st;
-    }
-    *out = reinterpret_cast<rsrr_t *>(h);
+    *out = h;
     return RSRR_OK;
 }
 
@@ -690,17 +759,18 @@ rsrr_status Handle::allocate_dense() {
         CK(alloc(&d_ab64, nn2 * N), "alloc dense factors (complex128)");
         CK(alloc(&d_dinv64, (size_t)N * nblk * 2 * nb * nb), "alloc block inverses");
     }
+    if (dry) return RSRR_OK;
     std::vector<double2> zs(N);
     for (int j = 0; j < N; ++j) zs[j] = make_double2(z[j].real(), z[j].imag());
-    CK(cudaMemcpy(d_points, h_points.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(d_z, zs.data(), sizeof(double2) * N, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpyAsync(d_points, h_points.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, hs), "upload");
+    CK(cudaMemcpyAsync(d_z, zs.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, hs), "upload");
     {
         std::vector<double2> U;
         default_probe(U, nL);
-        CK(cudaMemcpy(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice), "upload");
+        CK(cudaMemcpyAsync(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice, hs), "upload");
     }
-    CK(launch_colmax(d_umax, d_U, (int)n, L, 0), "colmax");
-    CK(cudaDeviceSynchronize(), "create sync");
+    CK(launch_colmax(d_umax, d_U, (int)n, L, hs), "colmax");
+    CK(wait(), "create sync");
     dp.n = n; dp.N = N; dp.L = L; dp.m = m; dp.U = d_U;
     return RSRR_OK;
 }

@@ -776,6 +776,8 @@ static size_t ws_bytes(int NL, int64_t n, int terms) {
     return (size_t)(ws.end - base);
 }
 
+size_t projection_ws_bytes(int NL, int64_t n, int terms) { return ws_bytes(NL, n, terms); }
+
 // Orthonormal basis of the dominant singular subspace of Sn = X D^{-1}:
 // deflated multi-level Gram.  Level l works on the remainder R_l (R_0 = Sn):
 //   G_l = R_l^H R_l; pivoted Cholesky G_l ~ B B^H stopped when the largest
@@ -793,10 +795,8 @@ rsrr_status Handle::project(cudaStream_t s) {
     if (!proj_ws) {
         const size_t bytes = ws_bytes(NL, nn, m);
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = raw_alloc(&p, bytes);
         if (e != cudaSuccess) return fail(RSRR_ENOMEM, "projection work space", e);
-        allocations.push_back(p);
-        device_bytes += bytes;
         proj_ws = p;
         proj_ws_bytes = bytes;
     }
@@ -1048,14 +1048,10 @@ __global__ void eig_residual_kernel(const double2 *__restrict__ V, const double2
 
 rsrr_status Handle::solve(rsrr_result *out) {
     using cplx = std::complex<double>;
-    cudaStream_t s = 0;
-    PK(cudaDeviceSynchronize(), "solve sync");
-
-    // projected coefficients to the host
-    std::vector<std::vector<cplx>> P(m, std::vector<cplx>((size_t)k * k));
-    for (int q = 0; q < m; ++q)
-        PK(cudaMemcpy(P[q].data(), d_P + (size_t)q * k * k, sizeof(double2) * k * k,
-                      cudaMemcpyDeviceToHost), "P to host");
+    cudaStream_t s = hs;
+    PK(wait(), "solve sync");
+    const auto D2H = cudaMemcpyDeviceToHost;
+    const auto H2D = cudaMemcpyHostToDevice;
     std::vector<cplx> lam, G;
     int nbar = 0;
     double gmax = 0.0;
@@ -1069,9 +1065,19 @@ rsrr_status Handle::solve(rsrr_result *out) {
         return eval_fn_host(fn[i], z);
     };
     const cplx gamma(region.center.re, region.center.im);
-    if (ss_full_host(P, k, f, m, gamma, region.a, region.b, opts.NQ, opts.KQ, opts.host_threads,
-                     lam, G, nbar, gmax) != 0)
-        return fail(RSRR_ESINGULAR, "rsrr_solve: projected T_Q singular at a quadrature node");
+    // moments of T_Q^{-1} on the GPU, the rest of SS-FULL on the host
+    std::vector<cplx> fq((size_t)opts.NQ * m);
+    for (int q = 0; q < opts.NQ; ++q) {
+        const double t = 2.0 * M_PI * (q + 0.5) / opts.NQ;
+        const cplx z = gamma + cplx(region.a * std::cos(t), region.b * std::sin(t));
+        for (int i = 0; i < m; ++i) fq[(size_t)q * m + i] = f(i, z);
+    }
+    std::vector<std::vector<cplx>> Am;
+    const rsrr_status mst = ssfull_moments(fq, opts.NQ, opts.KQ, Am);
+    if (mst != RSRR_OK) return mst;
+    if (ss_full_finish(Am, k, opts.KQ, gamma, std::max(region.a, region.b), opts.host_threads, lam, G,
+                       nbar, gmax) != 0)
+        return fail(RSRR_ESINGULAR, "rsrr_solve: the SS-FULL moments vanish");
     // v = Q g on the GPU
     ProjWs ws;
     const int NL = N * L;
@@ -1086,26 +1092,31 @@ rsrr_status Handle::solve(rsrr_result *out) {
     const size_t vbytes = sizeof(double2) * (size_t)n * nbar;
     const size_t cbytes = sizeof(double2) * (size_t)nbar * std::max(m, 2);
     void *buf = nullptr;
-    PK(cudaMalloc(&buf, gbytes + vbytes + cbytes + sizeof(double) * 2 * nbar), "solve buffers");
-    struct Free { void *p; ~Free() { cudaFree(p); } } guard{buf};
+    const size_t tbytes = gbytes + vbytes + cbytes + sizeof(double) * 2 * nbar;
+    PK(pool ? cudaMallocFromPoolAsync(&buf, tbytes, pool, s) : cudaMalloc(&buf, tbytes), "solve buffers");
+    struct Free {
+        Handle *h;
+        void *p;
+        ~Free() { h->raw_free(p); }
+    } guard{this, buf};
     double2 *d_G = reinterpret_cast<double2 *>(buf);
     double2 *d_V = reinterpret_cast<double2 *>(reinterpret_cast<char *>(buf) + gbytes);
     double2 *d_cf = reinterpret_cast<double2 *>(reinterpret_cast<char *>(buf) + gbytes + vbytes);
     double *d_rr = reinterpret_cast<double *>(reinterpret_cast<char *>(buf) + gbytes + vbytes + cbytes);
     double *d_vv = d_rr + nbar;
-    PK(cudaMemcpy(d_G, G.data(), gbytes, cudaMemcpyHostToDevice), "G");
+    PK(cudaMemcpyAsync(d_G, G.data(), gbytes, H2D, s), "G");
     PK(gm.run((int)n, nbar, k, false, d_Q, n, d_G, k, d_V, n, s), "Q G");
     std::vector<double> t1(nbar, 0.0);
     if (dense) {
         std::vector<double2> lz(nbar);
         for (int c = 0; c < nbar; ++c) lz[c] = make_double2(lam[c].real(), lam[c].imag());
-        PK(cudaMemcpy(d_cf, lz.data(), sizeof(double2) * nbar, cudaMemcpyHostToDevice), "lam");
-        PK(cudaMemset(d_rr, 0, sizeof(double) * 2 * nbar), "memset");
+        PK(cudaMemcpyAsync(d_cf, lz.data(), sizeof(double2) * nbar, H2D, s), "lam");
+        PK(cudaMemsetAsync(d_rr, 0, sizeof(double) * 2 * nbar, s), "memset");
         double *d_t1 = reinterpret_cast<double *>(d_cf + nbar);
-        PK(cudaMemset(d_t1, 0, sizeof(double) * nbar), "memset");
+        PK(cudaMemsetAsync(d_t1, 0, sizeof(double) * nbar, s), "memset");
         PK(launch_dense_eig_residual(d_V, d_cf, d_points, diag, (int)n, nbar, d_rr, d_vv, d_t1, s),
            "dense eig residual");
-        PK(cudaMemcpy(t1.data(), d_t1, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "t1");
+        PK(cudaMemcpyAsync(t1.data(), d_t1, sizeof(double) * nbar, D2H, s), "t1");
         launches += 1;
     } else {
         std::vector<double2> cf((size_t)nbar * m);
@@ -1114,18 +1125,19 @@ rsrr_status Handle::solve(rsrr_result *out) {
                 const cplx v = eval_fn_host(fn[q], lam[c]);
                 cf[(size_t)c * m + q] = make_double2(v.real(), v.imag());
             }
-        PK(cudaMemcpy(d_cf, cf.data(), sizeof(double2) * cf.size(), cudaMemcpyHostToDevice), "coef");
-        PK(cudaMemset(d_rr, 0, sizeof(double) * 2 * nbar), "memset");
-        eig_residual_kernel<<<dim3((unsigned)((n + 255) / 256), nbar), 256>>>(
+        PK(cudaMemcpyAsync(d_cf, cf.data(), sizeof(double2) * cf.size(), H2D, s), "coef");
+        PK(cudaMemsetAsync(d_rr, 0, sizeof(double) * 2 * nbar, s), "memset");
+        eig_residual_kernel<<<dim3((unsigned)((n + 255) / 256), nbar), 256, 0, s>>>(
             d_V, d_cf, d_row_ptr, d_col_idx, d_vals, nnz, m, (int)n, d_rr, d_vv);
         PK(cudaGetLastError(), "eig residual");
         launches += 1;
     }
     std::vector<double> rr(nbar), vv(nbar);
     std::vector<cplx> V((size_t)n * nbar);
-    PK(cudaMemcpy(rr.data(), d_rr, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "rr");
-    PK(cudaMemcpy(vv.data(), d_vv, sizeof(double) * nbar, cudaMemcpyDeviceToHost), "vv");
-    PK(cudaMemcpy(V.data(), d_V, sizeof(double2) * V.size(), cudaMemcpyDeviceToHost), "V");
+    PK(cudaMemcpyAsync(rr.data(), d_rr, sizeof(double) * nbar, D2H, s), "rr");
+    PK(cudaMemcpyAsync(vv.data(), d_vv, sizeof(double) * nbar, D2H, s), "vv");
+    PK(cudaMemcpyAsync(V.data(), d_V, sizeof(double2) * V.size(), D2H, s), "V");
+    PK(cudaStreamSynchronize(s), "solve results");
     // ||A_i||_1 (max column sum) on the host
     std::vector<double> a1(m, 0.0);
     for (int q = 0; q < m && !dense; ++q) {

@@ -11,6 +11,18 @@
 namespace rsrr {
 
 std::complex<double> eval_fn_host(const rsrr_fn &f, std::complex<double> z);
+struct Handle;
+// host part of rsrr_create: validation, pattern, sampling points, f_i(z_j);
+// the handle holds no device memory until allocate()
+rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                    const rsrr_opts *opts, Handle **out);
+// bytes of the projection stage's work space (proj.cu)
+size_t projection_ws_bytes(int NL, int64_t n, int terms);
+// SS-FULL moments on the GPU (ssfull_dev.cu): node chunks hold T_Q and its
+// inverse for at most this many bytes; device bytes of the stage for basis k
+constexpr size_t kSsfullChunkBytes = (size_t)1 << 30;
+size_t ssfull_dev_bytes(int64_t k, int m, int NQ, int KQ);
+std::string &thread_error();
 
 struct Handle {
     // problem
@@ -35,6 +47,14 @@ struct Handle {
     // device buffers (owned)
     std::vector<void *> allocations;
     size_t device_bytes = 0;
+    // A handle run by the request server draws its memory from a stream-ordered
+    // pool on its own stream `hs`, and every internal copy and wait goes to
+    // `hs`, so that requests on other streams keep running.  With hs == NULL
+    // (rsrr_create) memory comes from cudaMalloc and waits are device-wide.
+    cudaStream_t hs = nullptr;
+    cudaMemPool_t pool = nullptr;
+    bool dry = false;                 // alloc() only counts bytes (estimates)
+    std::vector<double2> h_coef;      // f_i(z_j), N x m, kept until allocate()
     int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr;
     int32_t *d_csc_ptr = nullptr, *d_csc_row = nullptr, *d_csc_perm = nullptr;
     double *d_vals = nullptr;
@@ -84,6 +104,11 @@ struct Handle {
     cudaError_t gemm_event(cudaEvent_t *out);
     rsrr_status fail(rsrr_status st, const char *what, cudaError_t e = cudaSuccess);
     template <typename T> cudaError_t alloc(T **p, size_t count);
+    cudaError_t raw_alloc(void **p, size_t bytes);
+    cudaError_t raw_free(void *p);
+    cudaError_t wait();
+    rsrr_status allocate();
+    size_t estimate_bytes();
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);
     rsrr_status sample(cudaStream_t s);
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, cudaStream_t s);
@@ -94,6 +119,8 @@ struct Handle {
     rsrr_status mark(int i, cudaStream_t s);
     rsrr_status project(cudaStream_t s);
     rsrr_status solve(rsrr_result *out);
+    rsrr_status ssfull_moments(const std::vector<std::complex<double>> &fq, int NQ, int KQ,
+                               std::vector<std::vector<std::complex<double>>> &Am);
 };
 
 }  // namespace rsrr

@@ -1,10 +1,10 @@
 // SS-FULL on the projected NEP T_Q(z) = sum_i f_i(z) P_i (k x k), in FP64 on
-// the host: the SS-RI algorithm of Section 2.3 with U = I (F = T_Q^{-1}),
-// quadrature nodes and weights of the trapezoid rule on the ellipse
-// (Section 4.1), moments scaled by ((z - gamma)/rho)^alpha, block Hankel
-// matrices H and H^<, truncated SVD of H with the count given by the largest
-// singular-value gap (tol_gap test), A = V0^H H^< W0 Sigma0^{-1}, and the
-// eigenpairs of A lifted by g = M W0 Sigma0^{-1} b with M = [A_0 .. A_{K-1}].
+// the host, from the moments A_alpha = sum_q w_q ((z_q - gamma)/rho)^alpha
+// T_Q(z_q)^{-1} (computed on the GPU, ssfull_dev.cu): the SS-RI algorithm of
+// Section 2.3 with U = I, block Hankel matrices H and H^<, truncated SVD of H
+// with the count given by the largest singular-value gap (tol_gap test),
+// A = V0^H H^< W0 Sigma0^{-1}, and the eigenpairs of A lifted by
+// g = M W0 Sigma0^{-1} b with M = [A_0 .. A_{K-1}].
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -46,77 +46,102 @@ void parallel_for(int count, int threads, const std::function<void(int, int)> &f
     for (auto &t : pool) t.join();
 }
 
-// In-place LU with partial pivoting (max modulus, first index on ties) and
-// F = T^{-1} by solving T F = I.  Returns false for an exactly zero pivot.
-bool invert(Mat &T, Mat &F, std::vector<int> &piv) {
-    const int k = T.r;
-    piv.resize(k);
-    for (int j = 0; j < k; ++j) {
-        int p = j;
-        double best = std::abs(T(j, j));
-        for (int i = j + 1; i < k; ++i) {
-            const double v = std::abs(T(i, j));
-            if (v > best) { best = v; p = i; }
-        }
-        piv[j] = p;
-        if (best == 0.0) return false;
-        if (p != j)
-            for (int c = 0; c < k; ++c) std::swap(T(j, c), T(p, c));
-        const cplx inv = 1.0 / T(j, j);
-        for (int i = j + 1; i < k; ++i) T(i, j) *= inv;
-        for (int c = j + 1; c < k; ++c) {
-            const cplx u = T(j, c);
-            if (u == cplx(0.0)) continue;
-            cplx *col = &T(0, c);
-            const cplx *l = &T(0, j);
-            for (int i = j + 1; i < k; ++i) col[i] -= l[i] * u;
-        }
-    }
-    F = Mat(k, k);
-    for (int j = 0; j < k; ++j) F(j, j) = 1.0;
-    for (int j = 0; j < k; ++j)
-        if (piv[j] != j)
-            for (int c = 0; c < k; ++c) std::swap(F(j, c), F(piv[j], c));
-    for (int c = 0; c < k; ++c) {
-        cplx *x = &F(0, c);
-        for (int j = 0; j < k; ++j) {  // L y = b
-            const cplx y = x[j];
-            if (y == cplx(0.0)) continue;
-            const cplx *l = &T(0, j);
-            for (int i = j + 1; i < k; ++i) x[i] -= l[i] * y;
-        }
-        for (int j = k - 1; j >= 0; --j) {  // U x = y
-            x[j] /= T(j, j);
-            const cplx y = x[j];
-            const cplx *u = &T(0, j);
-            for (int i = 0; i < j; ++i) x[i] -= u[i] * y;
-        }
-    }
-    return true;
-}
-
-// One-sided Jacobi SVD (Hestenes): A (r x c, r >= c not required) = U S W^H.
-// Columns are orthogonalised pairwise in a round-robin order (pairs of one
-// round are independent and run in parallel).  Singular values descending.
-void svd_jacobi(const Mat &A0, Mat &U, std::vector<double> &S, Mat &W, int threads) {
+// Truncated SVD A = U S W^H of A (r x c) through a column-pivoted Householder
+// QR: A P = Q R, stopped once every remaining column norm is <= rel_tol times
+// the largest column norm of A (those directions lie at the rounding level of
+// the moments); then one-sided Jacobi on the t columns of R^H (the rows of a
+// pivoted R are graded and nearly orthogonal, so few sweeps are needed):
+// R^H J = X S, hence A = (Q J) S (P X)^H.  U is r x t, W is c x t, S has t
+// values (descending); `tail` is the largest remaining column norm, an upper
+// bound of the next singular value up to a factor sqrt(c).
+void svd_qr_jacobi(const Mat &A0, Mat &U, std::vector<double> &S, double &tail, Mat &W,
+                   int threads, double rel_tol) {
     Mat A = A0;
     const int r = A.r, c = A.c;
-    W = Mat(c, c);
-    for (int j = 0; j < c; ++j) W(j, j) = 1.0;
-    const int cp = c + (c & 1);
+    std::vector<int> perm(c);
+    std::vector<double> nrm2(c);
+    for (int j = 0; j < c; ++j) {
+        perm[j] = j;
+        double s = 0.0;
+        for (int i = 0; i < r; ++i) s += std::norm(A(i, j));
+        nrm2[j] = s;
+    }
+    std::vector<std::vector<cplx>> refl;  // Householder vectors v (rows s..r-1), |v| = sqrt(2)
+    std::vector<cplx> diag;
+    double first = -1.0;
+    tail = 0.0;
+    int t = 0;
+    for (int s = 0; s < std::min(r, c); ++s) {
+        int p = s;
+        for (int j = s + 1; j < c; ++j)
+            if (nrm2[j] > nrm2[p]) p = j;
+        const double np = std::sqrt(std::max(nrm2[p], 0.0));
+        if (first < 0.0) first = np;
+        if (np <= rel_tol * first || np == 0.0) { tail = np; break; }
+        if (p != s) {
+            for (int i = 0; i < r; ++i) std::swap(A(i, s), A(i, p));
+            std::swap(nrm2[s], nrm2[p]);
+            std::swap(perm[s], perm[p]);
+        }
+        // reflector mapping A(s:, s) to alpha e_1, alpha = -e^{i arg x0} |x|
+        double xn = 0.0;
+        for (int i = s; i < r; ++i) xn += std::norm(A(i, s));
+        xn = std::sqrt(xn);
+        const cplx x0 = A(s, s);
+        const cplx ph = std::abs(x0) > 0.0 ? x0 / std::abs(x0) : cplx(1.0);
+        const cplx alpha = -ph * xn;
+        std::vector<cplx> v(r - s);
+        v[0] = x0 - alpha;
+        for (int i = s + 1; i < r; ++i) v[i - s] = A(i, s);
+        double vn = 0.0;
+        for (const cplx &e : v) vn += std::norm(e);
+        vn = std::sqrt(vn);
+        if (vn > 0.0)
+            for (cplx &e : v) e *= std::sqrt(2.0) / vn;  // H = I - v v^H
+        // trailing columns: A(s:, j) -= v (v^H A(s:, j)), column norms recomputed
+        parallel_for(c - s - 1, threads, [&](int jj, int) {
+            const int j = s + 1 + jj;
+            cplx w = 0.0;
+            for (int i = s; i < r; ++i) w += std::conj(v[i - s]) * A(i, j);
+            double nn = 0.0;
+            for (int i = s; i < r; ++i) {
+                A(i, j) -= v[i - s] * w;
+                if (i > s) nn += std::norm(A(i, j));
+            }
+            nrm2[j] = nn;
+        });
+        refl.push_back(std::move(v));
+        diag.push_back(alpha);
+        t = s + 1;
+    }
+    if (t == 0) {
+        U = Mat(r, 0);
+        W = Mat(c, 0);
+        S.clear();
+        return;
+    }
+    // B = R^H (c x t): B(j, i) = conj(R(i, j)), R upper trapezoidal
+    Mat B(c, t);
+    for (int i = 0; i < t; ++i) {
+        B(i, i) = std::conj(diag[i]);
+        for (int j = i + 1; j < c; ++j) B(j, i) = std::conj(A(i, j));
+    }
+    Mat J(t, t);
+    for (int j = 0; j < t; ++j) J(j, j) = 1.0;
+    const int tp = t + (t & 1);
     for (int sweep = 0; sweep < 60; ++sweep) {
         std::atomic<int> rotated(0);
-        for (int round = 0; round < cp - 1; ++round) {
-            parallel_for(cp / 2, threads, [&](int a, int) {
+        for (int round = 0; round < tp - 1; ++round) {
+            auto pair = [&](int a, int) {
                 int p, q;
-                if (a == 0) { p = cp - 1; q = round; }
-                else { p = (round + a) % (cp - 1); q = (round - a + (cp - 1)) % (cp - 1); }
+                if (a == 0) { p = tp - 1; q = round; }
+                else { p = (round + a) % (tp - 1); q = (round - a + (tp - 1)) % (tp - 1); }
                 if (p > q) std::swap(p, q);
-                if (q >= c) return;
+                if (q >= t) return;
                 double al = 0.0, be = 0.0;
                 cplx ga = 0.0;
-                const cplx *x = &A(0, p), *y = &A(0, q);
-                for (int i = 0; i < r; ++i) {
+                const cplx *x = &B(0, p), *y = &B(0, q);
+                for (int i = 0; i < c; ++i) {
                     al += std::norm(x[i]);
                     be += std::norm(y[i]);
                     ga += std::conj(x[i]) * y[i];
@@ -125,45 +150,60 @@ void svd_jacobi(const Mat &A0, Mat &U, std::vector<double> &S, Mat &W, int threa
                 if (ag <= 1e-15 * std::sqrt(al * be) || ag == 0.0) return;
                 rotated++;
                 const double tau = (be - al) / (2.0 * ag);
-                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
-                const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
-                const cplx e = ga / ag;  // e^{i phi}
+                const double tt = (tau >= 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
+                const double cs = 1.0 / std::sqrt(1.0 + tt * tt), sn = tt * cs;
+                const cplx e = ga / ag;
                 const cplx se = sn * e, sec = sn * std::conj(e);
-                cplx *xm = &A(0, p), *ym = &A(0, q);
-                for (int i = 0; i < r; ++i) {
+                cplx *xm = &B(0, p), *ym = &B(0, q);
+                for (int i = 0; i < c; ++i) {
                     const cplx xi = xm[i], yi = ym[i];
                     xm[i] = cs * xi - sec * yi;
                     ym[i] = se * xi + cs * yi;
                 }
-                cplx *wp = &W(0, p), *wq = &W(0, q);
-                for (int i = 0; i < c; ++i) {
-                    const cplx xi = wp[i], yi = wq[i];
-                    wp[i] = cs * xi - sec * yi;
-                    wq[i] = se * xi + cs * yi;
+                cplx *jp = &J(0, p), *jq = &J(0, q);
+                for (int i = 0; i < t; ++i) {
+                    const cplx xi = jp[i], yi = jq[i];
+                    jp[i] = cs * xi - sec * yi;
+                    jq[i] = se * xi + cs * yi;
                 }
-            });
+            };
+            // small rounds run inline: a thread start costs more than the work
+            if ((int64_t)c * t < 200000) {
+                for (int a = 0; a < tp / 2; ++a) pair(a, 0);
+            } else {
+                parallel_for(tp / 2, threads, pair);
+            }
         }
         if (rotated.load() == 0) break;
     }
-    std::vector<double> nrm(c);
-    for (int j = 0; j < c; ++j) {
+    std::vector<double> sv(t);
+    for (int j = 0; j < t; ++j) {
         double s = 0.0;
-        for (int i = 0; i < r; ++i) s += std::norm(A(i, j));
-        nrm[j] = std::sqrt(s);
+        for (int i = 0; i < c; ++i) s += std::norm(B(i, j));
+        sv[j] = std::sqrt(s);
     }
-    std::vector<int> ord(c);
-    for (int j = 0; j < c; ++j) ord[j] = j;
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return nrm[a] > nrm[b]; });
-    U = Mat(r, c);
-    Mat Ws(c, c);
-    S.resize(c);
-    for (int jj = 0; jj < c; ++jj) {
+    std::vector<int> ord(t);
+    for (int j = 0; j < t; ++j) ord[j] = j;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sv[a] > sv[b]; });
+    S.resize(t);
+    // W = P X with X = B J / S;  U = Q [J; 0]
+    W = Mat(c, t);
+    U = Mat(r, t);
+    for (int jj = 0; jj < t; ++jj) {
         const int j = ord[jj];
-        S[jj] = nrm[j];
-        for (int i = 0; i < r; ++i) U(i, jj) = nrm[j] > 0 ? A(i, j) / nrm[j] : cplx(0.0);
-        for (int i = 0; i < c; ++i) Ws(i, jj) = W(i, j);
+        S[jj] = sv[j];
+        for (int i = 0; i < c; ++i) W(perm[i], jj) = sv[j] > 0 ? B(i, j) / sv[j] : cplx(0.0);
+        for (int i = 0; i < t; ++i) U(i, jj) = J(i, j);
     }
-    W = Ws;
+    parallel_for(t, threads, [&](int jj, int) {
+        cplx *u = &U(0, jj);
+        for (int s = t - 1; s >= 0; --s) {
+            const std::vector<cplx> &v = refl[s];
+            cplx w = 0.0;
+            for (int i = s; i < r; ++i) w += std::conj(v[i - s]) * u[i];
+            for (int i = s; i < r; ++i) u[i] -= v[i - s] * w;
+        }
+    });
 }
 
 // Eigenvalues and eigenvectors of a general complex matrix: Householder
@@ -307,41 +347,11 @@ void eig_general(const Mat &A0, std::vector<cplx> &lam, Mat &V) {
 
 }  // namespace
 
-int ss_full_host(const std::vector<std::vector<cplx>> &P, int k,
-                 const std::function<cplx(int, cplx)> &f, int m, cplx gamma, double a, double b,
-                 int NQ, int KQ, int threads, std::vector<cplx> &lam, std::vector<cplx> &G,
-                 int &nbar, double &gmax) {
+int ss_full_finish(const std::vector<std::vector<cplx>> &Amom, int k, int KQ, cplx gamma, double rho,
+                   int threads, std::vector<cplx> &lam, std::vector<cplx> &G, int &nbar, double &gmax) {
     if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
-    const double rho = std::max(a, b);
-    const int nmom = 2 * KQ;
-    std::vector<std::vector<Mat>> part(threads, std::vector<Mat>(nmom, Mat(k, k)));
-    std::atomic<int> singular(0);
-    parallel_for(NQ, threads, [&](int q, int w) {
-        const double al = 2.0 * M_PI * (q + 0.5) / NQ;
-        const cplx z = gamma + cplx(a * std::cos(al), b * std::sin(al));
-        const cplx wq = cplx(-a * std::sin(al), b * std::cos(al)) / (double)NQ;
-        Mat T(k, k);
-        for (int i = 0; i < m; ++i) {
-            const cplx fi = f(i, z);
-            const std::vector<cplx> &Pi = P[i];
-            for (size_t e = 0; e < T.a.size(); ++e) T.a[e] += fi * Pi[e];
-        }
-        Mat F;
-        std::vector<int> piv;
-        if (!invert(T, F, piv)) { singular++; return; }
-        const cplx s = (z - gamma) / rho;
-        cplx c = wq;
-        for (int al2 = 0; al2 < nmom; ++al2) {
-            std::vector<cplx> &acc = part[w][al2].a;
-            for (size_t e = 0; e < acc.size(); ++e) acc[e] += c * F.a[e];
-            c *= s;
-        }
-    });
-    if (singular.load() > 0) return -1;
-    std::vector<Mat> Am(nmom, Mat(k, k));
-    for (int al2 = 0; al2 < nmom; ++al2)
-        for (int w = 0; w < threads; ++w)
-            for (size_t e = 0; e < Am[al2].a.size(); ++e) Am[al2].a[e] += part[w][al2].a[e];
+    std::vector<Mat> Am(2 * KQ, Mat(k, k));
+    for (int al2 = 0; al2 < 2 * KQ; ++al2) Am[al2].a = Amom[al2];
     const int dim = KQ * k;
     Mat H(dim, dim), Hs(dim, dim);
     for (int bi = 0; bi < KQ; ++bi)
@@ -353,11 +363,17 @@ int ss_full_host(const std::vector<std::vector<cplx>> &P, int k,
                 }
     Mat Us, Ws;
     std::vector<double> sv;
-    svd_jacobi(H, Us, sv, Ws, threads);
+    double tail = 0.0;
+    svd_qr_jacobi(H, Us, sv, tail, Ws, threads, 1e-15);
+    const int t = (int)sv.size();
+    if (t == 0) return -1;
+    // gap test over the resolved singular values and the bound of the rest
+    std::vector<double> gs(sv);
+    if (t < dim) gs.push_back(tail);
     nbar = 1;
     gmax = 0.0;
-    for (int j = 0; j + 1 < dim; ++j) {
-        const double r = sv[j] / std::max(sv[j + 1], 1e-300);
+    for (int j = 0; j + 1 < (int)gs.size(); ++j) {
+        const double r = gs[j] / std::max(gs[j + 1], 1e-300);
         if (r > gmax) { gmax = r; nbar = j + 1; }
     }
     if (dim == 1) { nbar = 1; gmax = 0.0; }

@@ -6,14 +6,14 @@
 
 namespace rsrr {
 
-// P: m matrices k x k (column major).  f(i, z) = f_i(z).  Ellipse gamma, a, b.
-// Outputs: lam (nbar eigenvalues of the projected NEP), G (k x nbar, column
-// major; projected eigenvectors), nbar and the gap gmax.  Returns 0, or -1
-// if T_Q is exactly singular at a quadrature node.
-int ss_full_host(const std::vector<std::vector<std::complex<double>>> &P, int k,
-                 const std::function<std::complex<double>(int, std::complex<double>)> &f, int m,
-                 std::complex<double> gamma, double a, double b, int NQ, int KQ, int threads,
-                 std::vector<std::complex<double>> &lam, std::vector<std::complex<double>> &G,
-                 int &nbar, double &gmax);
+// Amom: the 2 KQ moments A_alpha (k x k, column major) of T_Q^{-1} on the
+// ellipse (centre gamma, rho = max(a, b) scaling).  Outputs: lam (nbar
+// eigenvalues of the projected NEP), G (k x nbar, column major; projected
+// eigenvectors), nbar and the gap gmax.  Returns 0, or -1 if the moments
+// vanish.
+int ss_full_finish(const std::vector<std::vector<std::complex<double>>> &Amom, int k, int KQ,
+                   std::complex<double> gamma, double rho, int threads,
+                   std::vector<std::complex<double>> &lam, std::vector<std::complex<double>> &G,
+                   int &nbar, double &gmax);
 
 }  // namespace rsrr

@@ -83,6 +83,27 @@ class rsrr_result(C.Structure):
                 ("V", C.POINTER(rsrr_c128))]
 
 
+class rsrr_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("keep", C.c_int32), ("mem_budget_bytes", C.c_int64),
+                ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rsrr_reply(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("count", C.c_int32),
+                ("nbar", C.c_int32), ("k", C.c_int32), ("refine_sweeps", C.c_int32),
+                ("gmax", C.c_double), ("max_eta", C.c_double), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("device_bytes", C.c_size_t),
+                ("n", C.c_int64), ("lam", C.POINTER(rsrr_c128)), ("res", C.POINTER(C.c_double)),
+                ("V", C.POINTER(rsrr_c128)), ("error", C.c_char_p)]
+
+
+class rsrr_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("queued", C.c_int32), ("active", C.c_int32), ("peak_active", C.c_int32),
+                ("reserved", C.c_int32), ("used_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("budget_bytes", C.c_size_t), ("now", C.c_double)]
+
+
 _h = C.c_void_p
 _p = C.c_void_p
 
@@ -113,6 +134,19 @@ rsrr_last_error = _sig("rsrr_last_error", C.c_char_p, [_h])
 rsrr_destroy = _sig("rsrr_destroy", None, [_h])
 rsrr_solve_band_noalloc = _sig("rsrr_solve_band_noalloc", C.c_int,
                                [C.c_int64, C.c_int32, C.c_int32, _p, C.c_int32, _p, _p, _p])
+rsrr_estimate_bytes = _sig("rsrr_estimate_bytes", C.c_int,
+                           [C.POINTER(rsrr_nep), C.POINTER(rsrr_region), C.c_int32, C.c_int32,
+                            C.POINTER(rsrr_opts), C.POINTER(C.c_size_t)])
+rsrr_server_opts_default = _sig("rsrr_server_opts_default", None, [C.POINTER(rsrr_server_opts)])
+rsrr_server_create = _sig("rsrr_server_create", C.c_int, [C.POINTER(rsrr_server_opts), C.POINTER(_h)])
+rsrr_server_submit = _sig("rsrr_server_submit", C.c_int,
+                          [_h, C.POINTER(rsrr_nep), C.POINTER(rsrr_region), C.c_int32, C.c_int32,
+                           C.POINTER(rsrr_opts), _p, C.POINTER(C.c_int64)])
+rsrr_server_wait = _sig("rsrr_server_wait", C.c_int, [_h, C.c_int64, C.c_double, C.POINTER(rsrr_reply)])
+rsrr_server_handle = _sig("rsrr_server_handle", _h, [_h, C.c_int64])
+rsrr_server_release = _sig("rsrr_server_release", C.c_int, [_h, C.c_int64])
+rsrr_server_get_stats = _sig("rsrr_server_get_stats", C.c_int, [_h, C.POINTER(rsrr_server_stats)])
+rsrr_server_destroy = _sig("rsrr_server_destroy", None, [_h])
 rsrr_zgemm = _sig("rsrr_zgemm", C.c_int,
                   [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, C.c_int64, _p, C.c_int64, _p,
                    C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_size_t, _p])
@@ -147,6 +181,149 @@ def default_opts(**kw) -> rsrr_opts:
     return o
 
 
+def describe(prob):
+    """rsrr_nep and rsrr_region structures for a problem description (see
+    Solver), plus the arrays they point into (keep them alive while the
+    structures are in use)."""
+    keep = []
+    nep = rsrr_nep()
+    nep.n = int(prob.n)
+    dense = getattr(prob, "points", None) is not None and not hasattr(prob, "row_ptr")
+    if dense:
+        pts = np.ascontiguousarray(np.asarray(prob.points, dtype=np.float64))
+        keep.append(pts)
+        nep.kind = RSRR_NEP_HELMHOLTZ
+        nep.points = pts.ctypes.data_as(C.POINTER(C.c_double))
+        nep.diag = float(prob.diag)
+    else:
+        row_ptr = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(prob.col_idx, dtype=np.int32)
+        values = np.ascontiguousarray(np.concatenate(
+            [np.asarray(v, dtype=np.float64) for v in prob.values]))
+        keep += [row_ptr, col_idx, values]
+        nep.kind = RSRR_NEP_SPARSE
+        nep.m = len(prob.values)
+        nep.row_ptr = row_ptr.ctypes.data_as(C.POINTER(C.c_int64))
+        nep.col_idx = col_idx.ctypes.data_as(C.POINTER(C.c_int32))
+        nep.values = values.ctypes.data_as(C.POINTER(C.c_double))
+        for i, fn in enumerate(prob.fns):
+            sc = complex(fn.scale)
+            nep.fn[i] = rsrr_fn(int(fn.kind), 0, float(fn.param), rsrr_c128(sc.real, sc.imag))
+    reg = rsrr_region()
+    r = prob.region
+    reg.center = rsrr_c128(complex(r.center).real, complex(r.center).imag)
+    reg.a, reg.b = float(r.a), float(r.b)
+    if getattr(r, "kind", "ellipse") == "points":
+        reg.kind = RSRR_REGION_POINTS
+        pz = np.ascontiguousarray(np.asarray(r.points, dtype=np.complex128))
+        keep.append(pz)
+        reg.points = pz.ctypes.data_as(C.POINTER(rsrr_c128))
+    else:
+        reg.kind = RSRR_REGION_ELLIPSE
+    return nep, reg, keep
+
+
+def estimate_bytes(prob, opts: rsrr_opts | None = None, N=None, L=None) -> int:
+    """Device bytes a handle for `prob` would hold (no GPU needed)."""
+    nep, reg, keep = describe(prob)
+    o = opts if opts is not None else default_opts()
+    b = C.c_size_t(0)
+    st = rsrr_estimate_bytes(C.byref(nep), C.byref(reg), int(N if N is not None else prob.N),
+                             int(L if L is not None else prob.L), C.byref(o), C.byref(b))
+    if st != RSRR_OK:
+        raise RSRRError(st, rsrr_last_error(None).decode())
+    return int(b.value)
+
+
+def _complex_array(ptr, count):
+    if count == 0:
+        return np.zeros(0, dtype=np.complex128)
+    return np.ctypeslib.as_array(C.cast(ptr, C.POINTER(C.c_double)), shape=(count * 2,)).copy() \
+        .view(np.complex128)
+
+
+class Server:
+    """Request server (rsrr_server_*): submit whole RSRR solves, wait for
+    their replies.  Problems are described as for Solver."""
+
+    def __init__(self, slots=4, mem_budget_bytes=None, keep=False, device=-1):
+        o = rsrr_server_opts()
+        rsrr_server_opts_default(C.byref(o))
+        o.slots = int(slots)
+        o.keep = 1 if keep else 0
+        o.device = int(device)
+        if mem_budget_bytes is not None:
+            o.mem_budget_bytes = int(mem_budget_bytes)
+        h = _h()
+        st = rsrr_server_create(C.byref(o), C.byref(h))
+        if st != RSRR_OK:
+            raise RSRRError(st, rsrr_last_error(None).decode())
+        self.h = h
+
+    def submit(self, prob, opts: rsrr_opts | None = None, U=None, N=None, L=None) -> int:
+        nep, reg, keep = describe(prob)
+        o = opts if opts is not None else default_opts()
+        N = int(N if N is not None else prob.N)
+        L = int(L if L is not None else prob.L)
+        if U is None:
+            U = getattr(prob, "U", None)
+        up = None
+        if U is not None:
+            Uf = np.asfortranarray(np.asarray(U, dtype=np.complex128))
+            assert Uf.shape == (int(prob.n), L)
+            keep.append(Uf)
+            up = Uf.ctypes.data_as(C.c_void_p)
+        rid = C.c_int64(0)
+        st = rsrr_server_submit(self.h, C.byref(nep), C.byref(reg), N, L, C.byref(o), up, C.byref(rid))
+        if st != RSRR_OK:
+            raise RSRRError(st, rsrr_last_error(None).decode())
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout: float = -1.0) -> dict | None:
+        """The reply of request `rid` as a dict, or None on timeout."""
+        r = rsrr_reply()
+        st = rsrr_server_wait(self.h, int(rid), float(timeout), C.byref(r))
+        if st == RSRR_ETIMEOUT:
+            return None
+        if st != RSRR_OK:
+            raise RSRRError(st, rsrr_last_error(None).decode())
+        cnt, n = r.count, r.n
+        lam = _complex_array(r.lam, cnt)
+        res = np.ctypeslib.as_array(r.res, shape=(cnt,)).copy() if cnt else np.zeros(0)
+        V = _complex_array(r.V, cnt * n).reshape(cnt, n).T if cnt else np.zeros((n, 0), np.complex128)
+        return dict(id=r.id, status=r.status, count=cnt, nbar=r.nbar, k=r.k,
+                    refine_sweeps=r.refine_sweeps, gmax=r.gmax, max_eta=r.max_eta,
+                    t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done,
+                    device_bytes=r.device_bytes, lam=lam, res=res, V=V,
+                    error=(r.error or b"").decode())
+
+    def handle(self, rid: int):
+        return rsrr_server_handle(self.h, int(rid))
+
+    def release(self, rid: int):
+        st = rsrr_server_release(self.h, int(rid))
+        if st != RSRR_OK:
+            raise RSRRError(st, rsrr_last_error(None).decode())
+
+    def stats(self) -> dict:
+        s = rsrr_server_stats()
+        st = rsrr_server_get_stats(self.h, C.byref(s))
+        if st != RSRR_OK:
+            raise RSRRError(st, rsrr_last_error(None).decode())
+        return {f: getattr(s, f) for f, _ in rsrr_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            rsrr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Solver:
     """Owns one rsrr_t handle built from a problem description: either
     n, row_ptr, col_idx, values (list of m arrays), fns (kind, param, scale)
@@ -159,38 +336,8 @@ class Solver:
         self.N = int(N if N is not None else prob.N)
         self.L = int(L if L is not None else prob.L)
         self.n = int(prob.n)
-        nep = rsrr_nep()
-        nep.n = self.n
-        self.dense = getattr(prob, "points", None) is not None and not hasattr(prob, "row_ptr")
-        if self.dense:
-            self._points = np.ascontiguousarray(np.asarray(prob.points, dtype=np.float64))
-            nep.kind = RSRR_NEP_HELMHOLTZ
-            nep.points = self._points.ctypes.data_as(C.POINTER(C.c_double))
-            nep.diag = float(prob.diag)
-        else:
-            self._row_ptr = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
-            self._col_idx = np.ascontiguousarray(prob.col_idx, dtype=np.int32)
-            self._values = np.ascontiguousarray(np.concatenate(
-                [np.asarray(v, dtype=np.float64) for v in prob.values]))
-            nep.kind = RSRR_NEP_SPARSE
-            nep.m = len(prob.values)
-            nep.row_ptr = self._row_ptr.ctypes.data_as(C.POINTER(C.c_int64))
-            nep.col_idx = self._col_idx.ctypes.data_as(C.POINTER(C.c_int32))
-            nep.values = self._values.ctypes.data_as(C.POINTER(C.c_double))
-            for i, fn in enumerate(prob.fns):
-                sc = complex(fn.scale)
-                nep.fn[i] = rsrr_fn(int(fn.kind), 0, float(fn.param), rsrr_c128(sc.real, sc.imag))
-        reg = rsrr_region()
-        r = prob.region
-        reg.center = rsrr_c128(complex(r.center).real, complex(r.center).imag)
-        reg.a, reg.b = float(r.a), float(r.b)
-        self._pts = None
-        if getattr(r, "kind", "ellipse") == "points":
-            reg.kind = RSRR_REGION_POINTS
-            self._pts = np.ascontiguousarray(np.asarray(r.points, dtype=np.complex128))
-            reg.points = self._pts.ctypes.data_as(C.POINTER(rsrr_c128))
-        else:
-            reg.kind = RSRR_REGION_ELLIPSE
+        nep, reg, self._keep = describe(prob)
+        self.dense = nep.kind == RSRR_NEP_HELMHOLTZ
         self.opts = opts if opts is not None else default_opts()
         h = _h()
         st = rsrr_create(C.byref(nep), C.byref(reg), self.N, self.L, C.byref(self.opts),

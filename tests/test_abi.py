@@ -104,3 +104,47 @@ def test_ctypes_structs_match_the_c_compiler(tmp_path):
         assert int(val) == want, (name, field, int(val), want)
         seen += 1
     assert seen == sum(len(s._fields_) + 1 for s in structs)
+
+
+def test_ctypes_structs_match_the_c_layouts(lib, tmp_path):
+    """sizeof and field offsets of every struct the binding mirrors, as the C
+    compiler lays them out from include/rsrr.h."""
+    from paper_1605_07951_gb300 import rsrr
+    structs = ["rsrr_c128", "rsrr_fn", "rsrr_nep", "rsrr_region", "rsrr_opts", "rsrr_stats",
+               "rsrr_result", "rsrr_server_opts", "rsrr_reply", "rsrr_server_stats"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rsrr.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in getattr(rsrr, s)._fields_:
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        s, f, v = line.split()
+        cls = getattr(rsrr, s)
+        got = ctypes.sizeof(cls) if f == "size" else getattr(cls, f).offset
+        assert got == int(v), (s, f, got, v)
+
+
+def test_estimate_bytes_needs_no_gpu_and_counts_the_resident_buffers(lib):
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    p = W.config("c1")
+    b = rsrr.estimate_bytes(p)
+    kl = ku = 200
+    band = (2 * kl + ku + 32) * p.n * p.N * 8        # complex64 factors of all points
+    samples = 16 * p.n * p.N * p.L                   # S in complex128
+    assert band + 3 * samples <= b <= 3 * (band + 3 * samples)
+    assert rsrr.estimate_bytes(p, N=32) < b
+    fp64 = rsrr.estimate_bytes(p, rsrr.default_opts(precision=rsrr.RSRR_PREC_FP64))
+    assert fp64 > b  # complex128 factors
+    bad = W.config("c1")
+    bad.row_ptr = bad.row_ptr.copy()
+    bad.row_ptr[0] = 1
+    with pytest.raises(rsrr.RSRRError) as e:
+        rsrr.estimate_bytes(bad)
+    assert e.value.status == rsrr.RSRR_EINVAL

@@ -389,3 +389,36 @@ def helmholtz_sphere(n: int = 4096, N: int = 32, L: int = 64, center: complex = 
     h = mean_nn_distance(P)
     return DenseProblem(name, n, P, 1.0 / (2.0 * h), Region(complex(center), radius, radius), N, L,
                         probe(n, L, seed_u), meta=dict(h=h, seed=seed, seed_u=seed_u))
+
+
+# ----------------------------------------------------------------------------
+# request stream for the serving measurement: requests from the three
+# benchmark families with randomised regions and sizes
+# ----------------------------------------------------------------------------
+
+def serving_stream(count: int = 48, seed: int = 5000):
+    """`count` requests, family uniform over {quadratic tridiagonal (c0
+    shape), rational grid (c1 shape), dense sphere kernel (c2 shape)}, sizes
+    and regions drawn from `seed`.  Returns a list of (family, problem).
+    Sizes are scaled down from the full configs so that a stream of tens of
+    requests runs in seconds: grid side 40..100, dense n 128..512."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        fam = ("quadratic", "grid", "dense")[int(rng.integers(0, 3))]
+        s_u = seed + 1 + i
+        if fam == "quadratic":
+            p = quadratic_tridiag(n=1000, N=32, L=8,
+                                  center=complex(-25.0, float(rng.uniform(40.0, 60.0))),
+                                  radius=40.0, seed_u=s_u, name="c0_req")
+        elif fam == "grid":
+            g = int(rng.integers(40, 101))
+            p = rational_grid(g=g, N=int(rng.choice([32, 64])), L=int(rng.choice([8, 16, 32])),
+                              center=float(rng.uniform(70.0, 130.0)), seed_u=s_u, name="c1_req")
+        else:
+            n = int(rng.integers(128, 513))
+            p = helmholtz_sphere(n=n, N=32, L=int(rng.choice([8, 16])),
+                                 center=complex(float(rng.uniform(2.9, 3.1)), 0.0),
+                                 seed_u=s_u, name="c2_req")
+        out.append((fam, p))
+    return out
