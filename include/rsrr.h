@@ -162,7 +162,11 @@ enum { RSRR_GEMM_AUTO = 0, RSRR_GEMM_FP64 = 1, RSRR_GEMM_OZAKI = 2 };
  * solve (factor panels read straight from global memory) instead of the
  * streaming solve; same arithmetic, kept for comparison and as the fallback
  * for bands too wide for the streaming solve's shared-memory window. */
-enum { RSRR_FLAG_PLAIN_SOLVE = 1 };
+/* RSRR_FLAG_ONE_CTA_LU: band LU of rsrr_sample by one CTA per sampling point
+ * instead of a cluster of two CTAs per point (the second CTA updates most of
+ * the trailing window while the first factors the next panel); the factors
+ * are bitwise the same, the flag exists for comparison. */
+enum { RSRR_FLAG_PLAIN_SOLVE = 1, RSRR_FLAG_ONE_CTA_LU = 2 };
 
 typedef struct {
     int32_t precision;   /* RSRR_PREC_MIXED by default */

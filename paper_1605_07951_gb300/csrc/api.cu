@@ -563,6 +563,7 @@ cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, cudaStr
 
 // Step 2 of RSRR on the GPU, asynchronously on stream s.
 rsrr_status Handle::sample(cudaStream_t s) {
+    const bool cluster_lu = !(opts.flags & RSRR_FLAG_ONE_CTA_LU);
     Handle *h = this;
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L;
@@ -573,7 +574,7 @@ rsrr_status Handle::sample(cudaStream_t s) {
     if (opts.precision == RSRR_PREC_MIXED) {
         CK(launch_assemble<float2>(d_ab32, geom, dp, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c64(d_ab32, d_piv, d_info, d_dinv32, geom, N, nn, s), "band LU");
+        CK(launch_band_lu_c64(d_ab32, d_piv, d_info, d_dinv32, geom, N, nn, s, cluster_lu), "band LU");
         if (solve2) {
             CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "block permutations");
             launches += 1;
@@ -597,7 +598,7 @@ rsrr_status Handle::sample(cudaStream_t s) {
     } else {
         CK(launch_assemble<double2>(d_ab64, geom, dp, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c128(d_ab64, d_piv, d_info, d_dinv64, geom, N, nn, s), "band LU");
+        CK(launch_band_lu_c128(d_ab64, d_piv, d_info, d_dinv64, geom, N, nn, s, cluster_lu), "band LU");
         if (solve2) {
             CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "block permutations");
             launches += 1;

@@ -473,8 +473,10 @@ static cudaError_t solve_dispatch(const C *ab, const int32_t *piv, const C *dinv
                                   const BandGeom &g, int N, int n, int L, const int32_t *skip,
                                   cudaStream_t s) {
     const size_t smem = solve_smem<C, NB, LC>(g);
+    const int limit = smem_optin_limit();
+    if (smem > (size_t)limit) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<C, NB, LC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     if (e != cudaSuccess) return e;
     dim3 grid((L + LC - 1) / LC, N);
     band_solve_kernel<C, NB, LC><<<grid, SV_THREADS, smem, s>>>(ab, piv, dinv, B, n, g.kl, g.ku,

@@ -1,8 +1,22 @@
 // Batched banded LU with partial pivoting for RSRR step 2 (Section 3.3):
-// the factorisation of every T(z_j), one CTA per sampling point.  The band
-// storage is described in band.cu.
+// the factorisation of every T(z_j).  The band storage is described in
+// band.cu.  Two launch shapes share the same device routines and perform the
+// same arithmetic on every element, in the same order:
+//   band_lu_kernel          one CTA per sampling point;
+//   band_lu_cluster_kernel  a cluster of two CTAs per point with a one-panel
+//                           lookahead: CTA 0 updates the first chunk of the
+//                           trailing window (which holds the next panel) and
+//                           factors the next panel while CTA 1 updates the
+//                           rest of the window; one cluster barrier a panel.
+// Global reads of the factor, pivots and block inverses bypass L1 (__ldcg):
+// the two CTAs of a cluster sit on different SMs and read what the other
+// wrote, and L1 is not coherent between SMs.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "rsrr_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace rsrr {
 
@@ -10,7 +24,7 @@ constexpr int LU_THREADS = 512;
 constexpr int LU_WARPS = LU_THREADS / 32;
 
 // --------------------------------------------------------------------------
-// Banded LU with partial pivoting, blocked by NB columns, one CTA per point.
+// Blocked by NB columns.
 //
 // Panel (columns j0..j0+jb-1, rows j0..j0+pr-1, pr <= jb + kl): thread r owns
 // panel row r in registers.  Per column: block-wide argmax of |re|+|im| over
@@ -26,13 +40,292 @@ constexpr int LU_WARPS = LU_THREADS / 32;
 // row permutation of the panel) happen before any write of that chunk.
 // --------------------------------------------------------------------------
 template <typename C, int NB, int RA, int CB>
+struct LuSm {
+    using R = typename real_of<C>::type;
+    static constexpr int CW = LU_WARPS * CB;
+    static constexpr int PRA = NB + 32 * RA;  // allocated panel rows (>= NB + kl)
+    C *P;      // [NB][PRA], column major
+    C *Linv;   // [NB][NB+1], column major, padded
+    C *Uinv;   // [NB][NB+1]
+    C *Ut;     // [NB][CW]  (row t, col) at t*CW+col
+    C *U2;     // [NB][CW]
+    C *prow;   // [2][NB]
+    C *drow;   // [2][NB]
+    R *wval;   // [2][LU_WARPS]
+    int *widx; // [2][LU_WARPS]
+    int *perm; // [PRA]
+    int *sw;   // [NB]
+
+    RSRR_DEV explicit LuSm(unsigned char *raw) {
+        P = reinterpret_cast<C *>(raw);
+        Linv = P + NB * PRA;
+        Uinv = Linv + NB * (NB + 1);
+        Ut = Uinv + NB * (NB + 1);
+        U2 = Ut + NB * CW;
+        prow = U2 + NB * CW;
+        drow = prow + 2 * NB;
+        wval = reinterpret_cast<R *>(drow + 2 * NB);
+        widx = reinterpret_cast<int *>(wval + 2 * LU_WARPS);
+        perm = widx + 2 * LU_WARPS;
+        sw = perm + PRA;
+    }
+    static size_t bytes() {
+        size_t b = sizeof(C) * ((size_t)NB * PRA + 2 * NB * (NB + 1) + 2 * NB * CW + 4 * NB);
+        b += sizeof(R) * 2 * LU_WARPS + sizeof(int) * (2 * LU_WARPS + PRA + NB);
+        return b;
+    }
+};
+
+// Factors the panel at column j0: the factored columns go to global memory
+// and to sm.P, the pivots to piv, the composed row permutation to sm.perm,
+// L11^{-1} and U11^{-1} to sm.Linv / sm.Uinv and to the block's dinv slot.
+template <typename C, int NB, int RA, int CB>
+RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restrict__ dinv, int n,
+                       int kl, int KV, int ldab, int j0, const LuSm<C, NB, RA, CB> &sm, int &info) {
+    using R = typename real_of<C>::type;
+    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int jb = min(NB, n - j0);
+    const int pr = min(n - j0, jb + kl);
+
+    C row[NB];
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) {
+        row[cc] = czero<C>();
+        if (tid < pr && cc < jb) {
+            const int d = tid - cc;  // (j0 + tid) - (j0 + cc)
+            if (d >= -KV && d < kl + NB) row[cc] = __ldcg(&ab[(size_t)(j0 + cc) * ldab + KV + d]);
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) {
+        if (cc < jb) {
+            const int buf = cc & 1;
+            const int rend = min(pr, cc + kl + 1);
+            R v = (R)-1;
+            int ix = 0x7fffffff;
+            if (tid >= cc && tid < rend) { v = cabs1(row[cc]); ix = tid; }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const R ov = shfl_down(v, off);
+                const int oi = shfl_down(ix, off);
+                if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
+            }
+            if (lane == 0) { sm.wval[buf * LU_WARPS + warp] = v; sm.widx[buf * LU_WARPS + warp] = ix; }
+            __syncthreads();
+            R bv = sm.wval[buf * LU_WARPS];
+            int p = sm.widx[buf * LU_WARPS];
+#pragma unroll
+            for (int w = 1; w < LU_WARPS; ++w) {
+                const R ov = sm.wval[buf * LU_WARPS + w];
+                const int oi = sm.widx[buf * LU_WARPS + w];
+                if (ov > bv || (ov == bv && oi < p)) { bv = ov; p = oi; }
+            }
+            if (tid == p) {
+#pragma unroll
+                for (int c2 = 0; c2 < NB; ++c2) sm.prow[buf * NB + c2] = row[c2];
+            }
+            if (tid == cc) {
+#pragma unroll
+                for (int c2 = 0; c2 < NB; ++c2) sm.drow[buf * NB + c2] = row[c2];
+            }
+            __syncthreads();
+            if (tid == cc) {
+#pragma unroll
+                for (int c2 = 0; c2 < NB; ++c2) row[c2] = sm.prow[buf * NB + c2];
+            } else if (tid == p) {
+#pragma unroll
+                for (int c2 = 0; c2 < NB; ++c2) row[c2] = sm.drow[buf * NB + c2];
+            }
+            const C pv = sm.prow[buf * NB + cc];
+            const bool nz = cnonzero(pv);
+            if (tid > cc && tid < rend && nz) {
+                const C l = cmul(row[cc], crecip(pv));
+                row[cc] = l;
+#pragma unroll
+                for (int c2 = cc + 1; c2 < NB; ++c2) row[c2] = cfms(row[c2], l, sm.prow[buf * NB + c2]);
+            }
+            if (tid == 0) {
+                sm.sw[cc] = p;
+                piv[j0 + cc] = j0 + p;
+                if (!nz && info == 0) info = j0 + cc + 1;
+            }
+        }
+    }
+    // panel -> shared (column major) and global
+    if (tid < pr) {
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) {
+            if (cc < jb) {
+                sm.P[cc * PRA + tid] = row[cc];
+                const int d = tid - cc;
+                if (d >= -KV && d < kl + NB) ab[(size_t)(j0 + cc) * ldab + KV + d] = row[cc];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int r = 0; r < pr; ++r) sm.perm[r] = r;
+        for (int cc = 0; cc < jb; ++cc) {
+            const int p = sm.sw[cc];
+            const int t = sm.perm[cc]; sm.perm[cc] = sm.perm[p]; sm.perm[p] = t;
+        }
+    }
+    if (warp == 1) {
+        // column j = lane of L11^{-1}: x_i = [i == j] - sum_{t<i} L(i,t) x_t,
+        // kept in shared memory (row stride NB + 1 avoids bank conflicts)
+        const int j = lane;
+        if (j < NB) {
+            for (int i = 0; i < NB; ++i) {
+                C s = (i == j) ? cone<C>() : czero<C>();
+                for (int t = j; t < i; ++t) s = cfms(s, sm.P[t * PRA + i], sm.Linv[j * (NB + 1) + t]);
+                sm.Linv[j * (NB + 1) + i] = (i < j || i >= jb || j >= jb) ? czero<C>() : s;
+            }
+        }
+    } else if (warp == 2) {
+        // column j = lane of U11^{-1}: x_j = 1/u_jj,
+        // x_i = -(sum_{i<t<=j} u_it x_t) / u_ii for i = j-1 .. 0
+        const int j = lane;
+        if (j < NB) {
+            for (int i = 0; i < NB; ++i) sm.Uinv[j * (NB + 1) + i] = czero<C>();
+            if (j < jb) {
+                sm.Uinv[j * (NB + 1) + j] = crecip(sm.P[j * PRA + j]);
+                for (int i = j - 1; i >= 0; --i) {
+                    C s = czero<C>();
+                    for (int t = i + 1; t <= j; ++t) s = cfma(s, sm.P[t * PRA + i], sm.Uinv[j * (NB + 1) + t]);
+                    sm.Uinv[j * (NB + 1) + i] = cmul(csub(czero<C>(), s), crecip(sm.P[i * PRA + i]));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    C *dst = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
+    for (int q = tid; q < 2 * NB * NB; q += LU_THREADS) {
+        const int w = q / (NB * NB), e = q % (NB * NB), j = e / NB, i = e % NB;
+        dst[q] = (w == 0 ? sm.Linv : sm.Uinv)[j * (NB + 1) + i];
+    }
+}
+
+// What the trailing update of the panel at j0 needs, read back from global
+// memory (written there by the CTA that factored it): the multipliers L21
+// into sm.P, L11^{-1} into sm.Linv, and the composed permutation from piv.
+template <typename C, int NB, int RA, int CB>
+RSRR_DEV void lu_load_panel(const C *__restrict__ ab, const int32_t *__restrict__ piv,
+                            const C *__restrict__ dinv, int n, int kl, int KV, int ldab, int j0,
+                            const LuSm<C, NB, RA, CB> &sm) {
+    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+    const int tid = threadIdx.x;
+    const int jb = min(NB, n - j0);
+    const int pr = min(n - j0, jb + kl);
+    for (int q = tid; q < NB * PRA; q += LU_THREADS) {
+        const int cc = q / PRA, r = q % PRA;
+        C v = czero<C>();
+        if (cc < jb && r >= jb && r < pr) v = __ldcg(&ab[(size_t)(j0 + cc) * ldab + KV + (r - cc)]);
+        sm.P[q] = v;
+    }
+    const C *src = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
+    for (int q = tid; q < NB * NB; q += LU_THREADS) {
+        const int j = q / NB, i = q % NB;
+        sm.Linv[j * (NB + 1) + i] = __ldcg(&src[q]);
+    }
+    if (tid == 0) {
+        for (int r = 0; r < pr; ++r) sm.perm[r] = r;
+        for (int cc = 0; cc < jb; ++cc) {
+            const int p = __ldcg(&piv[j0 + cc]) - j0;
+            const int t = sm.perm[cc]; sm.perm[cc] = sm.perm[p]; sm.perm[p] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// Trailing update of the panel at j0 over columns [c_lo, c_hi).
+template <typename C, int NB, int RA, int CB>
+RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int j0, int c_lo,
+                        int c_hi, const LuSm<C, NB, RA, CB> &sm) {
+    constexpr int CW = LuSm<C, NB, RA, CB>::CW;
+    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int jb = min(NB, n - j0);
+    const int pr = min(n - j0, jb + kl);
+    for (int c0 = c_lo; c0 < c_hi; c0 += CW) {
+        const int cw = min(CW, c_hi - c0);
+        // (1) all reads of the chunk: U rows into Ut, A22 into registers
+        for (int o = tid; o < NB * CW; o += LU_THREADS) {
+            const int t = o % NB, col = o / NB;
+            C v = czero<C>();
+            if (t < jb && col < cw) {
+                const int c = c0 + col;
+                const int d = j0 + sm.perm[t] - c;
+                if (d >= -KV) v = __ldcg(&ab[(size_t)c * ldab + KV + d]);
+            }
+            sm.Ut[t * CW + col] = v;
+        }
+        C acc[RA][CB];
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+            const int r = jb + lane + 32 * a;
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int col = warp + LU_WARPS * b;
+                acc[a][b] = czero<C>();
+                if (r < pr && col < cw) {
+                    const int c = c0 + col;
+                    const int d = j0 + sm.perm[r] - c;
+                    if (d >= -KV) acc[a][b] = __ldcg(&ab[(size_t)c * ldab + KV + d]);
+                }
+            }
+        }
+        __syncthreads();
+        // (2) U12 = L11^{-1} Ut  -> U2 and global rows j0..j0+jb-1
+        for (int o = tid; o < NB * CW; o += LU_THREADS) {
+            const int t = o % NB, col = o / NB;
+            C s = czero<C>();
+#pragma unroll
+            for (int q = 0; q < NB; ++q) s = cfma(s, sm.Linv[q * (NB + 1) + t], sm.Ut[q * CW + col]);
+            sm.U2[t * CW + col] = s;
+            if (t < jb && col < cw) {
+                const int c = c0 + col;
+                const int d = j0 + t - c;
+                if (d >= -KV) ab[(size_t)c * ldab + KV + d] = s;
+            }
+        }
+        __syncthreads();
+        // (3) A22 -= L21 U12, rows j0+jb.., written at their (permuted) positions
+#pragma unroll 4
+        for (int q = 0; q < NB; ++q) {
+            C uq[CB];
+#pragma unroll
+            for (int b = 0; b < CB; ++b) uq[b] = sm.U2[q * CW + warp + LU_WARPS * b];
+#pragma unroll
+            for (int a = 0; a < RA; ++a) {
+                const C l = sm.P[q * PRA + jb + lane + 32 * a];
+#pragma unroll
+                for (int b = 0; b < CB; ++b) acc[a][b] = cfms(acc[a][b], l, uq[b]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+            const int r = jb + lane + 32 * a;
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int col = warp + LU_WARPS * b;
+                if (r < pr && col < cw) {
+                    const int c = c0 + col;
+                    ab[(size_t)c * ldab + KV + (j0 + r - c)] = acc[a][b];
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One CTA per point: panel, then the whole trailing window, panel by panel.
+template <typename C, int NB, int RA, int CB>
 __global__ void __launch_bounds__(LU_THREADS, 1)
 band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
                int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl, int ku,
                int ldab) {
-    using R = typename real_of<C>::type;
-    constexpr int CW = LU_WARPS * CB;
-    constexpr int PRA = NB + 32 * RA;  // allocated panel rows (>= NB + kl)
+    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
     const int pt = blockIdx.x;
     C *ab = ab_all + (size_t)pt * ldab * n;
     int32_t *piv = piv_all + (size_t)pt * n;
@@ -40,267 +333,109 @@ band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     // per block: L11^{-1} then U11^{-1}, both NB x NB column major
     C *dinv = dinv_all + (size_t)pt * nblk * 2 * NB * NB;
     const int KV = kl + ku;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *P = reinterpret_cast<C *>(smem_raw);  // [NB][PRA], column major
-    C *Linv = P + NB * PRA;                  // [NB][NB+1], column major, padded
-    C *Uinv = Linv + NB * (NB + 1);          // [NB][NB+1], column major, padded
-    C *Ut = Uinv + NB * (NB + 1);            // [NB][CW]  (row t, col) at t*CW+col
-    C *U2 = Ut + NB * CW;                    // [NB][CW]
-    C *prow = U2 + NB * CW;                  // [2][NB]
-    C *drow = prow + 2 * NB;                 // [2][NB]
-    R *wval = reinterpret_cast<R *>(drow + 2 * NB);  // [2][LU_WARPS]
-    int *widx = reinterpret_cast<int *>(wval + 2 * LU_WARPS);  // [2][LU_WARPS]
-    int *perm = widx + 2 * LU_WARPS;         // [PRA]
-    int *sw = perm + PRA;                    // [NB]
-
-    for (int q = tid; q < NB * PRA; q += LU_THREADS) P[q] = czero<C>();
+    const LuSm<C, NB, RA, CB> sm(smem_raw);
+    for (int q = threadIdx.x; q < NB * PRA; q += LU_THREADS) sm.P[q] = czero<C>();
     int info = 0;
     __syncthreads();
-
     for (int j0 = 0; j0 < n; j0 += NB) {
         const int jb = min(NB, n - j0);
-        const int pr = min(n - j0, jb + kl);
-
-        // ---------------- panel factorisation (rows in registers)
-        C row[NB];
-#pragma unroll
-        for (int cc = 0; cc < NB; ++cc) {
-            row[cc] = czero<C>();
-            if (tid < pr && cc < jb) {
-                const int d = tid - cc;  // (j0 + tid) - (j0 + cc)
-                if (d >= -KV && d < kl + NB) row[cc] = ab[(size_t)(j0 + cc) * ldab + KV + d];
-            }
-        }
-#pragma unroll
-        for (int cc = 0; cc < NB; ++cc) {
-            if (cc < jb) {
-                const int buf = cc & 1;
-                const int rend = min(pr, cc + kl + 1);
-                R v = (R)-1;
-                int ix = 0x7fffffff;
-                if (tid >= cc && tid < rend) { v = cabs1(row[cc]); ix = tid; }
-#pragma unroll
-                for (int off = 16; off; off >>= 1) {
-                    const R ov = shfl_down(v, off);
-                    const int oi = shfl_down(ix, off);
-                    if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
-                }
-                if (lane == 0) { wval[buf * LU_WARPS + warp] = v; widx[buf * LU_WARPS + warp] = ix; }
-                __syncthreads();
-                R bv = wval[buf * LU_WARPS];
-                int p = widx[buf * LU_WARPS];
-#pragma unroll
-                for (int w = 1; w < LU_WARPS; ++w) {
-                    const R ov = wval[buf * LU_WARPS + w];
-                    const int oi = widx[buf * LU_WARPS + w];
-                    if (ov > bv || (ov == bv && oi < p)) { bv = ov; p = oi; }
-                }
-                if (tid == p) {
-#pragma unroll
-                    for (int c2 = 0; c2 < NB; ++c2) prow[buf * NB + c2] = row[c2];
-                }
-                if (tid == cc) {
-#pragma unroll
-                    for (int c2 = 0; c2 < NB; ++c2) drow[buf * NB + c2] = row[c2];
-                }
-                __syncthreads();
-                if (tid == cc) {
-#pragma unroll
-                    for (int c2 = 0; c2 < NB; ++c2) row[c2] = prow[buf * NB + c2];
-                } else if (tid == p) {
-#pragma unroll
-                    for (int c2 = 0; c2 < NB; ++c2) row[c2] = drow[buf * NB + c2];
-                }
-                const C pv = prow[buf * NB + cc];
-                const bool nz = cnonzero(pv);
-                if (tid > cc && tid < rend && nz) {
-                    const C l = cmul(row[cc], crecip(pv));
-                    row[cc] = l;
-#pragma unroll
-                    for (int c2 = cc + 1; c2 < NB; ++c2) row[c2] = cfms(row[c2], l, prow[buf * NB + c2]);
-                }
-                if (tid == 0) {
-                    sw[cc] = p;
-                    piv[j0 + cc] = j0 + p;
-                    if (!nz && info == 0) info = j0 + cc + 1;
-                }
-            }
-        }
-        // panel -> shared (column major) and global
-        if (tid < pr) {
-#pragma unroll
-            for (int cc = 0; cc < NB; ++cc) {
-                if (cc < jb) {
-                    P[cc * PRA + tid] = row[cc];
-                    const int d = tid - cc;
-                    if (d >= -KV && d < kl + NB) ab[(size_t)(j0 + cc) * ldab + KV + d] = row[cc];
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int r = 0; r < pr; ++r) perm[r] = r;
-            for (int cc = 0; cc < jb; ++cc) {
-                const int p = sw[cc];
-                const int t = perm[cc]; perm[cc] = perm[p]; perm[p] = t;
-            }
-        }
-        if (warp == 1) {
-            // column j = lane of L11^{-1}: x_i = [i == j] - sum_{t<i} L(i,t) x_t,
-            // kept in shared memory (row stride NB + 1 avoids bank conflicts)
-            const int j = lane;
-            if (j < NB) {
-                for (int i = 0; i < NB; ++i) {
-                    C s = (i == j) ? cone<C>() : czero<C>();
-                    for (int t = j; t < i; ++t) s = cfms(s, P[t * PRA + i], Linv[j * (NB + 1) + t]);
-                    Linv[j * (NB + 1) + i] = (i < j || i >= jb || j >= jb) ? czero<C>() : s;
-                }
-            }
-        } else if (warp == 2) {
-            // column j = lane of U11^{-1}: x_j = 1/u_jj,
-            // x_i = -(sum_{i<t<=j} u_it x_t) / u_ii for i = j-1 .. 0
-            const int j = lane;
-            if (j < NB) {
-                for (int i = 0; i < NB; ++i) Uinv[j * (NB + 1) + i] = czero<C>();
-                if (j < jb) {
-                    Uinv[j * (NB + 1) + j] = crecip(P[j * PRA + j]);
-                    for (int i = j - 1; i >= 0; --i) {
-                        C s = czero<C>();
-                        for (int t = i + 1; t <= j; ++t) s = cfma(s, P[t * PRA + i], Uinv[j * (NB + 1) + t]);
-                        Uinv[j * (NB + 1) + i] = cmul(csub(czero<C>(), s), crecip(P[i * PRA + i]));
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        {
-            C *dst = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
-            for (int q = tid; q < 2 * NB * NB; q += LU_THREADS) {
-                const int w = q / (NB * NB), e = q % (NB * NB), j = e / NB, i = e % NB;
-                dst[q] = (w == 0 ? Linv : Uinv)[j * (NB + 1) + i];
-            }
-        }
-
-        // ---------------- trailing update
-        const int c_beg = j0 + jb;
-        const int c_end = min(n, j0 + jb + KV);
-        for (int c0 = c_beg; c0 < c_end; c0 += CW) {
-            const int cw = min(CW, c_end - c0);
-            // (1) all reads of the chunk: U rows into Ut, A22 into registers
-            for (int o = tid; o < NB * CW; o += LU_THREADS) {
-                const int t = o % NB, col = o / NB;
-                C v = czero<C>();
-                if (t < jb && col < cw) {
-                    const int c = c0 + col;
-                    const int d = j0 + perm[t] - c;
-                    if (d >= -KV) v = ab[(size_t)c * ldab + KV + d];
-                }
-                Ut[t * CW + col] = v;
-            }
-            C acc[RA][CB];
-#pragma unroll
-            for (int a = 0; a < RA; ++a) {
-                const int r = jb + lane + 32 * a;
-#pragma unroll
-                for (int b = 0; b < CB; ++b) {
-                    const int col = warp + LU_WARPS * b;
-                    acc[a][b] = czero<C>();
-                    if (r < pr && col < cw) {
-                        const int c = c0 + col;
-                        const int d = j0 + perm[r] - c;
-                        if (d >= -KV) acc[a][b] = ab[(size_t)c * ldab + KV + d];
-                    }
-                }
-            }
-            __syncthreads();
-            // (2) U12 = L11^{-1} Ut  -> U2 and global rows j0..j0+jb-1
-            for (int o = tid; o < NB * CW; o += LU_THREADS) {
-                const int t = o % NB, col = o / NB;
-                C s = czero<C>();
-#pragma unroll
-                for (int q = 0; q < NB; ++q) s = cfma(s, Linv[q * (NB + 1) + t], Ut[q * CW + col]);
-                U2[t * CW + col] = s;
-                if (t < jb && col < cw) {
-                    const int c = c0 + col;
-                    const int d = j0 + t - c;
-                    if (d >= -KV) ab[(size_t)c * ldab + KV + d] = s;
-                }
-            }
-            __syncthreads();
-            // (3) A22 -= L21 U12, rows j0+jb.., written at their (permuted) positions
-#pragma unroll 4
-            for (int q = 0; q < NB; ++q) {
-                C uq[CB];
-#pragma unroll
-                for (int b = 0; b < CB; ++b) uq[b] = U2[q * CW + warp + LU_WARPS * b];
-#pragma unroll
-                for (int a = 0; a < RA; ++a) {
-                    const C l = P[q * PRA + jb + lane + 32 * a];
-#pragma unroll
-                    for (int b = 0; b < CB; ++b) acc[a][b] = cfms(acc[a][b], l, uq[b]);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < RA; ++a) {
-                const int r = jb + lane + 32 * a;
-#pragma unroll
-                for (int b = 0; b < CB; ++b) {
-                    const int col = warp + LU_WARPS * b;
-                    if (r < pr && col < cw) {
-                        const int c = c0 + col;
-                        ab[(size_t)c * ldab + KV + (j0 + r - c)] = acc[a][b];
-                    }
-                }
-            }
-        }
-        __syncthreads();
+        lu_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, j0, sm, info);
+        lu_update<C, NB, RA, CB>(ab, n, kl, KV, ldab, j0, j0 + jb, min(n, j0 + jb + KV), sm);
     }
-    if (tid == 0) info_all[pt] = info;
+    if (threadIdx.x == 0) info_all[pt] = info;
 }
 
+// A cluster of two CTAs per point.  Iteration of panel j0 (factored and
+// published in global memory before the iteration starts):
+//   CTA 0: update columns [j0+jb, j0+jb+CW) -- they hold the next panel --
+//          then factor the next panel;
+//   CTA 1: load the panel's multipliers, L11^{-1} and permutation from global
+//          memory, update columns [j0+jb+CW, j0+jb+KV);
+//   cluster barrier (release/acquire; every thread of both CTAs).
+// The barrier orders CTA 1's writes of a panel before CTA 0 reads them as
+// the next panel's columns, and CTA 0's factored panel before CTA 1 loads
+// it.  Both CTAs run the same number of barriers: one before the loop, one
+// per panel, with no exit in between.
 template <typename C, int NB, int RA, int CB>
-static size_t lu_smem_bytes() {
-    constexpr int CW = LU_WARPS * CB;
-    constexpr int PRA = NB + 32 * RA;
-    size_t b = sizeof(C) * ((size_t)NB * PRA + 2 * NB * (NB + 1) + 2 * NB * CW + 4 * NB);
-    b += sizeof(typename real_of<C>::type) * 2 * LU_WARPS + sizeof(int) * (2 * LU_WARPS + PRA + NB);
-    return b;
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LU_THREADS, 1)
+band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
+                       int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl,
+                       int ku, int ldab) {
+    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+    constexpr int CW = LuSm<C, NB, RA, CB>::CW;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    const int pt = blockIdx.x / 2;
+    C *ab = ab_all + (size_t)pt * ldab * n;
+    int32_t *piv = piv_all + (size_t)pt * n;
+    const int nblk = (n + NB - 1) / NB;
+    C *dinv = dinv_all + (size_t)pt * nblk * 2 * NB * NB;
+    const int KV = kl + ku;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LuSm<C, NB, RA, CB> sm(smem_raw);
+    for (int q = threadIdx.x; q < NB * PRA; q += LU_THREADS) sm.P[q] = czero<C>();
+    int info = 0;
+    __syncthreads();
+    if (rank == 0) lu_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, 0, sm, info);
+    __threadfence();
+    cluster.sync();
+    for (int j0 = 0; j0 < n; j0 += NB) {
+        const int jb = min(NB, n - j0);
+        const int c_beg = j0 + jb, c_end = min(n, j0 + jb + KV);
+        const int c_split = min(c_end, c_beg + CW);
+        if (rank == 0) {
+            lu_update<C, NB, RA, CB>(ab, n, kl, KV, ldab, j0, c_beg, c_split, sm);
+            if (c_beg < n) lu_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, c_beg, sm, info);
+        } else {
+            lu_load_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, j0, sm);
+            lu_update<C, NB, RA, CB>(ab, n, kl, KV, ldab, j0, c_split, c_end, sm);
+        }
+        __threadfence();
+        cluster.sync();
+    }
+    if (rank == 0 && threadIdx.x == 0) info_all[pt] = info;
 }
 
 template <typename C, int NB, int RA, int CB>
 static cudaError_t lu_dispatch(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g,
-                               int N, int n, cudaStream_t s) {
-    const size_t smem = lu_smem_bytes<C, NB, RA, CB>();
+                               int N, int n, bool cluster, cudaStream_t s) {
+    const size_t smem = LuSm<C, NB, RA, CB>::bytes();
+    if (cluster) {
+        cudaError_t e = cudaFuncSetAttribute(band_lu_cluster_kernel<C, NB, RA, CB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        band_lu_cluster_kernel<C, NB, RA, CB><<<2 * N, LU_THREADS, smem, s>>>(ab, piv, info, dinv, n, g.kl,
+                                                                              g.ku, g.ldab);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<C, NB, RA, CB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    band_lu_kernel<C, NB, RA, CB><<<N, LU_THREADS, smem, s>>>(ab, piv, info, dinv, n, g.kl, g.ku,
-                                                               g.ldab);
+    band_lu_kernel<C, NB, RA, CB><<<N, LU_THREADS, smem, s>>>(ab, piv, info, dinv, n, g.kl, g.ku, g.ldab);
     return cudaGetLastError();
 }
 
 template <typename C, int NB, int CB>
 static cudaError_t lu_by_kl(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g, int N,
-                            int n, cudaStream_t s) {
+                            int n, bool cluster, cudaStream_t s) {
     const int kl = g.kl;
-    if (kl <= 32) return lu_dispatch<C, NB, 1, CB>(ab, piv, info, dinv, g, N, n, s);
-    if (kl <= 128) return lu_dispatch<C, NB, 4, CB>(ab, piv, info, dinv, g, N, n, s);
-    if (kl <= 224) return lu_dispatch<C, NB, 7, CB>(ab, piv, info, dinv, g, N, n, s);
-    return lu_dispatch<C, NB, 15, CB>(ab, piv, info, dinv, g, N, n, s);
+    if (kl <= 32) return lu_dispatch<C, NB, 1, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
+    if (kl <= 128) return lu_dispatch<C, NB, 4, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
+    if (kl <= 224) return lu_dispatch<C, NB, 7, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
+    return lu_dispatch<C, NB, 15, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
 
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 64
 cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *dinv,
-                               const BandGeom &g, int N, int n, cudaStream_t s) {
-    return lu_by_kl<float2, NB_C64, 4>(ab, piv, info, dinv, g, N, n, s);
+                               const BandGeom &g, int N, int n, cudaStream_t s, bool cluster) {
+    return lu_by_kl<float2, NB_C64, 4>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
 #endif
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 128
 cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, double2 *dinv,
-                                const BandGeom &g, int N, int n, cudaStream_t s) {
-    return lu_by_kl<double2, NB_C128, 1>(ab, piv, info, dinv, g, N, n, s);
+                                const BandGeom &g, int N, int n, cudaStream_t s, bool cluster) {
+    return lu_by_kl<double2, NB_C128, 1>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
 #endif
 

@@ -333,9 +333,10 @@ static cudaError_t s2_dispatch(const C *ab, const int32_t *bperm, const C *dinv,
                                const BandGeom &g, int N, int n, int L, const int32_t *skip,
                                cudaStream_t s) {
     const size_t smem = s2_smem<C, NB, LC>(g);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const int limit = smem_optin_limit();
+    if (smem > 227 * 1024 || smem > (size_t)limit) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(band_solve2_kernel<C, NB, LC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     if (e != cudaSuccess) return e;
     dim3 grid((L + LC - 1) / LC, N);
     band_solve2_kernel<C, NB, LC><<<grid, S2_THREADS, smem, s>>>(ab, bperm, dinv, B, n, g.kl, g.ku,

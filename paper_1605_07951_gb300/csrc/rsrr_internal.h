@@ -16,6 +16,18 @@ constexpr int NB_C128 = 16;
 // Largest lower half-bandwidth the band kernels accept (panel rows <= 512).
 constexpr int KL_MAX = 480;
 
+// Largest opt-in dynamic shared memory per block of the current device.
+// Kernels whose shared memory depends on the problem raise their limit to
+// this value instead of to each launch's size: the limit belongs to the
+// function, and host threads launching it with different sizes at the same
+// time would otherwise overwrite each other's limit between set and launch.
+inline int smem_optin_limit() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
 struct BandGeom {
     int kl, ku, nb, ldab;  // ldab = kl + ku + kl + nb
 };
@@ -39,10 +51,12 @@ template <typename C>
 cudaError_t launch_assemble(C *ab, const BandGeom &g, const DevProblem &p, cudaStream_t s);
 cudaError_t launch_tnorm(double *tnorm, const DevProblem &p, cudaStream_t s);
 // dinv: per point and NB block, L11^{-1} then U11^{-1} (NB x NB each)
+// cluster: two CTAs per point with one-panel lookahead (band_lu.cu); the
+// factors are bitwise those of the one-CTA kernel
 cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *dinv,
-                               const BandGeom &g, int N, int n, cudaStream_t s);
+                               const BandGeom &g, int N, int n, cudaStream_t s, bool cluster = false);
 cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, double2 *dinv,
-                                const BandGeom &g, int N, int n, cudaStream_t s);
+                                const BandGeom &g, int N, int n, cudaStream_t s, bool cluster = false);
 cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const float2 *dinv,
                                   float2 *B, const BandGeom &g, int N, int n, int L,
                                   const int32_t *skip, cudaStream_t s);

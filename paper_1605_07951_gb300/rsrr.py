@@ -29,7 +29,7 @@ RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = 
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI = 0, 1, 2
-RSRR_FLAG_PLAIN_SOLVE = 1
+RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU = 1, 2
 RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ = 0, 1
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",

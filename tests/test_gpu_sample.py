@@ -169,3 +169,22 @@ def test_streaming_solve_matches_the_one_kernel_solve(rs, name, make, precision)
     if precision == 1:
         out = run(rs, p, precision)
         compare(p, out, rel_tol=1e-6, eta_tol=ETA_TOL)
+
+
+# the band LU as a cluster of two CTAs per point (the default) against one CTA
+# per point: same arithmetic on every element in the same order, so the
+# factors, and the samples of one solve, agree bit for bit
+LU_CASES = SOLVE_CASES + [("grid_g40", lambda: W.rational_grid(g=40, N=4, L=4)),
+                          ("band_above_224", lambda: W.random_banded(n=900, kl=240, ku=30, N=2, L=3, seed=13))]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,make", LU_CASES, ids=[c[0] for c in LU_CASES])
+def test_cluster_lu_matches_the_one_cta_lu_bitwise(rs, name, make, precision):
+    p = make()
+    a = run(rs, p, precision, max_refine=0)
+    b = run(rs, p, precision, max_refine=0, flags=rs.RSRR_FLAG_ONE_CTA_LU)
+    assert a["status"] == b["status"]
+    assert np.array_equal(a["S"], b["S"])
+    if precision == 1:
+        compare(p, run(rs, p, precision), rel_tol=1e-6, eta_tol=ETA_TOL)

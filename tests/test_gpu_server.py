@@ -97,7 +97,7 @@ def test_each_result_in_the_mix_equals_the_result_alone(rs, lone_results):
 
 
 def test_admission_respects_the_memory_budget(rs, lone_results):
-    probs = [(name, make(), NQ) for name, make, NQ in MIX[:4]]
+    probs = [(name, make(), NQ) for name, make, NQ in MIX[:3]]  # requests of similar size
     est = [rs.estimate_bytes(p, rs.default_opts(NQ=NQ)) for _, p, NQ in probs]
     budget = int(max(est) * 1.2)  # room for one request at a time
     assert min(est) * 2 > budget
