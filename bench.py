@@ -350,7 +350,7 @@ def run_ours(a, rank, world, local):
     lu_avg = statistics.mean(lu_ms)
     achieved = lu_flops / (lu_avg / 1e3) / 1e12
     ldab = 2 * kl + ku + 32
-    roof_lu = {"bound": "alu", "kernel": "band_lu_kernel<float2> (complex64, one CTA per point)",
+    roof_lu = {"bound": "alu", "kernel": "band_lu_cluster_kernel<float2> (complex64, two-CTA cluster per point)",
                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": achieved / FP32_PEAK_TFLOPS,
                "traffic": LU_TRAFFIC_PER_ENTRY * ldab * n * p.N,

@@ -429,12 +429,20 @@ RSRR_DEV Rot rot_of(const double2 *__restrict__ H, int k, int p, int q) {
 }
 
 // One round of the round-robin ordering, grid-stride over the 2x2 blocks and
-// the rows of Y (same arithmetic as jacobi_round_kernel).
+// the rows of Y.  Every CTA first computes the round's np rotations (one per
+// pair, from the old matrix) into shared memory `srot`, so that the FP64
+// square roots and divisions run once per pair rather than once per block.
 RSRR_DEV void jacobi_round(const double2 *__restrict__ Hold, double2 *__restrict__ Hnew,
-                           double2 *__restrict__ Y, int k, int kp, int r) {
+                           double2 *__restrict__ Y, int k, int kp, int r, Rot *__restrict__ srot) {
     const int np = kp / 2;
     const int64_t nblk = (int64_t)np * np;
     const int64_t nY = (int64_t)k * np;
+    for (int a = threadIdx.x; a < np; a += blockDim.x) {
+        int p, q;
+        pair_of(r, a, kp, p, q);
+        srot[a] = rot_of(Hold, k, p, q);
+    }
+    __syncthreads();
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nblk + nY;
          q += (int64_t)gridDim.x * blockDim.x) {
         if (q < nblk) {
@@ -442,7 +450,7 @@ RSRR_DEV void jacobi_round(const double2 *__restrict__ Hold, double2 *__restrict
             int pa, qa, pb, qb;
             pair_of(r, a, kp, pa, qa);
             pair_of(r, b, kp, pb, qb);
-            const Rot Ra = rot_of(Hold, k, pa, qa), Rb = rot_of(Hold, k, pb, qb);
+            const Rot Ra = srot[a], Rb = srot[b];
             const bool va = qa < k, vb = qb < k;
             double2 h00 = (pa < k && pb < k) ? Hold[(int64_t)pb * k + pa] : make_double2(0, 0);
             double2 h01 = (pa < k && vb) ? Hold[(int64_t)qb * k + pa] : make_double2(0, 0);
@@ -478,7 +486,7 @@ RSRR_DEV void jacobi_round(const double2 *__restrict__ Hold, double2 *__restrict
             int pb, qb;
             pair_of(r, b, kp, pb, qb);
             if (qb >= k) continue;
-            const Rot Rb = rot_of(Hold, k, pb, qb);
+            const Rot Rb = srot[b];
             const double2 yp = Y[(int64_t)pb * k + i], yq = Y[(int64_t)qb * k + i];
             const double2 sbc = make_double2(-Rb.se.x, Rb.se.y);
             Y[(int64_t)pb * k + i] = cadd(make_double2(yp.x * Rb.c, yp.y * Rb.c), cmul(yq, sbc));
@@ -499,6 +507,7 @@ jacobi_persistent_kernel(double2 *__restrict__ H0, double2 *__restrict__ H1,
                          unsigned int *__restrict__ bar) {
     const int kp = k + (k & 1);
     const int64_t kk = (int64_t)k * k;
+    extern __shared__ Rot srot[];  // kp / 2 rotations of the current round
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < kk;
          q += (int64_t)gridDim.x * blockDim.x)
         Y[q] = make_double2((q % k) == (q / k) ? 1.0 : 0.0, 0.0);
@@ -508,7 +517,7 @@ jacobi_persistent_kernel(double2 *__restrict__ H0, double2 *__restrict__ H1,
     if (k > 1) {
         for (int sw = 0; sw < max_sweeps; ++sw) {
             for (int r = 0; r < kp - 1; ++r) {
-                jacobi_round(a, b, Y, k, kp, r);
+                jacobi_round(a, b, Y, k, kp, r, srot);
                 if (!grid_sync(bar, gridDim.x)) return;
                 double2 *t = a; a = b; b = t;
             }
@@ -644,17 +653,27 @@ template <typename T> static T *carve(char *&p, size_t count) {
         if (_e != cudaSuccess) return fail(RSRR_ECUDA, what, _e);        \
     } while (0)
 
-// Cooperative launch helper: as many CTAs as can be co-resident (<= cap).
+// Cooperative launch helper: as many CTAs as can be co-resident (<= cap),
+// `smem` bytes of dynamic shared memory each.
 template <typename K, typename... Args>
-static cudaError_t launch_coop(K kern, int cap, cudaStream_t s, Args... args) {
+static cudaError_t launch_coop_smem(K kern, int cap, size_t smem, cudaStream_t s, Args... args) {
     int dev = 0, nsm = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+    if (e == cudaSuccess && smem > 48 * 1024) {
+        const int limit = smem_optin_limit();
+        if (smem > (size_t)limit) return cudaErrorInvalidConfiguration;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    }
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
     if (e != cudaSuccess) return e;
     int grid = std::max(1, std::min(cap, nsm * std::max(per, 1)));
     void *argv[] = {(void *)&args...};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), argv, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), argv, smem, s);
+}
+template <typename K, typename... Args>
+static cudaError_t launch_coop(K kern, int cap, cudaStream_t s, Args... args) {
+    return launch_coop_smem(kern, cap, 0, s, args...);
 }
 
 // Jacobi on the k x k Hermitian matrix in ws.H (overwritten with its
@@ -668,8 +687,9 @@ static cudaError_t jacobi_eig(ProjWs &ws, int k, cudaStream_t s, int64_t *counte
     if (e != cudaSuccess) return e;
     const double tol2 = 1e-30;  // off(H) <= 1e-15 ||diag(H)||
     const int64_t work = (int64_t)(k + 1) / 2 * ((k + 1) / 2) + (int64_t)k * ((k + 1) / 2);
-    e = launch_coop(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, 4096), s,
-                    ws.H, ws.H2, ws.Y, k, max_sweeps, tol2, ws.jacc, ws.state + 1, ws.bar);
+    const size_t smem = sizeof(Rot) * (size_t)((k + 1) / 2);
+    e = launch_coop_smem(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, 4096), smem,
+                         s, ws.H, ws.H2, ws.Y, k, max_sweeps, tol2, ws.jacc, ws.state + 1, ws.bar);
     if (e != cudaSuccess) return e;
     sort_desc_kernel<<<1, 256, 0, s>>>(ws.H, k, ws.order, ws.evals);
     gather_cols_kernel<<<grid1d((int64_t)k * k), 256, 0, s>>>(ws.Ysort, ws.Y, k, k, ws.order);
