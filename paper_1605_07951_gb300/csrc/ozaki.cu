@@ -229,6 +229,22 @@ RSRR_DEV void mma_bf16(float c[4], const unsigned a[4], unsigned b0, unsigned b1
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// round(f 2^32) for a group sum f of groups t <= 4, in integer instructions.
+// Such an f is an integer multiple of 2^-32 below 2^24 in magnitude (step 3
+// above), so f = m 2^(e-150) with a 24-bit m and e >= 95, and f 2^32 =
+// m 2^(e-118) is an integer below 2^56: the shift loses only zero bits and
+// the result is exactly the float-to-int64 conversion of f 2^32, without the
+// conversion unit (it shares the GPU's slow double-precision pipe).
+RSRR_DEV long long scaled_group_to_ll(float f) {
+    const int bits = __float_as_int(f);
+    const int e = (bits >> 23) & 0xFF;
+    if (e == 0) return 0;  // +-0 (subnormals cannot occur: |f| >= 2^-32)
+    long long m = (long long)((bits & 0x7FFFFF) | 0x800000);
+    const int sh = e - 118;
+    m = sh >= 0 ? (m << sh) : (m >> -sh);
+    return bits < 0 ? -m : m;
+}
+
 // One CTA: a 64 x 64 tile of C~ over K' range [sp kchunk, (sp+1) kchunk).
 // W != null: FP64 partial tile into W[sp][i][j'] (Mp x Np, row major).
 // W == null: C = alpha C~ + beta C written directly (one split).
@@ -338,7 +354,7 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
                     for (int q = 0; q < 4; ++q) {
 #pragma unroll
                         for (int t = 0; t < 5; ++t) {
-                            acc[a][b][q] += __float2ll_rn(gs[t][a][b][q] * 0x1p32f);
+                            acc[a][b][q] += scaled_group_to_ll(gs[t][a][b][q]);
                             gs[t][a][b][q] = 0.f;
                         }
                         low[a][b][q] += gs[5][a][b][q];
