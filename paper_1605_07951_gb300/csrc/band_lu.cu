@@ -4,10 +4,11 @@
 // same arithmetic on every element, in the same order:
 //   band_lu_kernel          one CTA per sampling point;
 //   band_lu_cluster_kernel  a cluster of two CTAs per point with a one-panel
-//                           lookahead: CTA 0 updates the first chunk of the
-//                           trailing window (which holds the next panel) and
-//                           factors the next panel while CTA 1 updates the
-//                           rest of the window; one cluster barrier a panel.
+//                           lookahead: CTA 0 updates the first chunk(s) of
+//                           the trailing window (the first holds the next
+//                           panel) and factors the next panel while CTA 1
+//                           updates the rest of the window; one cluster
+//                           barrier a panel.
 // Global reads of the factor, pivots and block inverses bypass L1 (__ldcg):
 // the two CTAs of a cluster sit on different SMs and read what the other
 // wrote, and L1 is not coherent between SMs.
@@ -20,29 +21,27 @@ namespace cg = cooperative_groups;
 
 namespace rsrr {
 
-constexpr int LU_THREADS = 512;
-constexpr int LU_WARPS = LU_THREADS / 32;
 
 // --------------------------------------------------------------------------
 // Blocked by NB columns.
 //
-// Panel (columns j0..j0+jb-1, rows j0..j0+pr-1, pr <= jb + kl): thread r owns
-// panel row r in registers.  Per column: block-wide argmax of |re|+|im| over
+// Panel (columns j0..j0+jb-1, rows j0..j0+pr-1, pr <= jb + kl <= TH): thread r
+// owns panel row r in registers.  Per column: block-wide argmax of |re|+|im| over
 // the candidate rows (first index on ties), the pivot row and the displaced
 // row exchange through shared memory, then every row below scales its
 // multiplier and updates its remaining panel entries.  Two barriers a column.
 //
 // Trailing columns c in [j0+jb, min(n, j0+jb+KV)) are updated in chunks of
-// CW = 16*CB columns: U12 = L11^{-1} * (P A12) with an explicit inverse of
+// CW = (TH/32)*CB columns: U12 = L11^{-1} * (P A12) with an explicit inverse of
 // the unit lower triangle L11 (computed once per panel), then
 // A22 -= L21 * U12, accumulated in registers over row groups of 32 (RA of
 // them cover the kl rows below the panel).  All reads of a chunk (through the
 // row permutation of the panel) happen before any write of that chunk.
 // --------------------------------------------------------------------------
-template <typename C, int NB, int RA, int CB>
+template <typename C, int NB, int RA, int CB, int TH>
 struct LuSm {
     using R = typename real_of<C>::type;
-    static constexpr int CW = LU_WARPS * CB;
+    static constexpr int CW = (TH / 32) * CB;
     static constexpr int PRA = NB + 32 * RA;  // allocated panel rows (>= NB + kl)
     C *P;      // [NB][PRA], column major
     C *Linv;   // [NB][NB+1], column major, padded
@@ -51,8 +50,8 @@ struct LuSm {
     C *U2;     // [NB][CW]
     C *prow;   // [2][NB]
     C *drow;   // [2][NB]
-    R *wval;   // [2][LU_WARPS]
-    int *widx; // [2][LU_WARPS]
+    R *wval;   // [2][(TH / 32)]
+    int *widx; // [2][(TH / 32)]
     int *perm; // [PRA]
     int *sw;   // [NB]
 
@@ -65,13 +64,13 @@ struct LuSm {
         prow = U2 + NB * CW;
         drow = prow + 2 * NB;
         wval = reinterpret_cast<R *>(drow + 2 * NB);
-        widx = reinterpret_cast<int *>(wval + 2 * LU_WARPS);
-        perm = widx + 2 * LU_WARPS;
+        widx = reinterpret_cast<int *>(wval + 2 * (TH / 32));
+        perm = widx + 2 * (TH / 32);
         sw = perm + PRA;
     }
     static size_t bytes() {
         size_t b = sizeof(C) * ((size_t)NB * PRA + 2 * NB * (NB + 1) + 2 * NB * CW + 4 * NB);
-        b += sizeof(R) * 2 * LU_WARPS + sizeof(int) * (2 * LU_WARPS + PRA + NB);
+        b += sizeof(R) * 2 * (TH / 32) + sizeof(int) * (2 * (TH / 32) + PRA + NB);
         return b;
     }
 };
@@ -79,11 +78,11 @@ struct LuSm {
 // Factors the panel at column j0: the factored columns go to global memory
 // and to sm.P, the pivots to piv, the composed row permutation to sm.perm,
 // L11^{-1} and U11^{-1} to sm.Linv / sm.Uinv and to the block's dinv slot.
-template <typename C, int NB, int RA, int CB>
+template <typename C, int NB, int RA, int CB, int TH>
 RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restrict__ dinv, int n,
-                       int kl, int KV, int ldab, int j0, const LuSm<C, NB, RA, CB> &sm, int &info) {
+                       int kl, int KV, int ldab, int j0, const LuSm<C, NB, RA, CB, TH> &sm, int &info) {
     using R = typename real_of<C>::type;
-    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
@@ -111,14 +110,14 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
                 const int oi = shfl_down(ix, off);
                 if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
             }
-            if (lane == 0) { sm.wval[buf * LU_WARPS + warp] = v; sm.widx[buf * LU_WARPS + warp] = ix; }
+            if (lane == 0) { sm.wval[buf * (TH / 32) + warp] = v; sm.widx[buf * (TH / 32) + warp] = ix; }
             __syncthreads();
-            R bv = sm.wval[buf * LU_WARPS];
-            int p = sm.widx[buf * LU_WARPS];
+            R bv = sm.wval[buf * (TH / 32)];
+            int p = sm.widx[buf * (TH / 32)];
 #pragma unroll
-            for (int w = 1; w < LU_WARPS; ++w) {
-                const R ov = sm.wval[buf * LU_WARPS + w];
-                const int oi = sm.widx[buf * LU_WARPS + w];
+            for (int w = 1; w < (TH / 32); ++w) {
+                const R ov = sm.wval[buf * (TH / 32) + w];
+                const int oi = sm.widx[buf * (TH / 32) + w];
                 if (ov > bv || (ov == bv && oi < p)) { bv = ov; p = oi; }
             }
             if (tid == p) {
@@ -200,7 +199,7 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
     }
     __syncthreads();
     C *dst = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
-    for (int q = tid; q < 2 * NB * NB; q += LU_THREADS) {
+    for (int q = tid; q < 2 * NB * NB; q += TH) {
         const int w = q / (NB * NB), e = q % (NB * NB), j = e / NB, i = e % NB;
         dst[q] = (w == 0 ? sm.Linv : sm.Uinv)[j * (NB + 1) + i];
     }
@@ -209,22 +208,22 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
 // What the trailing update of the panel at j0 needs, read back from global
 // memory (written there by the CTA that factored it): the multipliers L21
 // into sm.P, L11^{-1} into sm.Linv, and the composed permutation from piv.
-template <typename C, int NB, int RA, int CB>
+template <typename C, int NB, int RA, int CB, int TH>
 RSRR_DEV void lu_load_panel(const C *__restrict__ ab, const int32_t *__restrict__ piv,
                             const C *__restrict__ dinv, int n, int kl, int KV, int ldab, int j0,
-                            const LuSm<C, NB, RA, CB> &sm) {
-    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+                            const LuSm<C, NB, RA, CB, TH> &sm) {
+    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     const int tid = threadIdx.x;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
-    for (int q = tid; q < NB * PRA; q += LU_THREADS) {
+    for (int q = tid; q < NB * PRA; q += TH) {
         const int cc = q / PRA, r = q % PRA;
         C v = czero<C>();
         if (cc < jb && r >= jb && r < pr) v = __ldcg(&ab[(size_t)(j0 + cc) * ldab + KV + (r - cc)]);
         sm.P[q] = v;
     }
     const C *src = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
-    for (int q = tid; q < NB * NB; q += LU_THREADS) {
+    for (int q = tid; q < NB * NB; q += TH) {
         const int j = q / NB, i = q % NB;
         sm.Linv[j * (NB + 1) + i] = __ldcg(&src[q]);
     }
@@ -239,18 +238,18 @@ RSRR_DEV void lu_load_panel(const C *__restrict__ ab, const int32_t *__restrict_
 }
 
 // Trailing update of the panel at j0 over columns [c_lo, c_hi).
-template <typename C, int NB, int RA, int CB>
+template <typename C, int NB, int RA, int CB, int TH>
 RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int j0, int c_lo,
-                        int c_hi, const LuSm<C, NB, RA, CB> &sm) {
-    constexpr int CW = LuSm<C, NB, RA, CB>::CW;
-    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+                        int c_hi, const LuSm<C, NB, RA, CB, TH> &sm) {
+    constexpr int CW = LuSm<C, NB, RA, CB, TH>::CW;
+    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
     for (int c0 = c_lo; c0 < c_hi; c0 += CW) {
         const int cw = min(CW, c_hi - c0);
         // (1) all reads of the chunk: U rows into Ut, A22 into registers
-        for (int o = tid; o < NB * CW; o += LU_THREADS) {
+        for (int o = tid; o < NB * CW; o += TH) {
             const int t = o % NB, col = o / NB;
             C v = czero<C>();
             if (t < jb && col < cw) {
@@ -266,7 +265,7 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
             const int r = jb + lane + 32 * a;
 #pragma unroll
             for (int b = 0; b < CB; ++b) {
-                const int col = warp + LU_WARPS * b;
+                const int col = warp + (TH / 32) * b;
                 acc[a][b] = czero<C>();
                 if (r < pr && col < cw) {
                     const int c = c0 + col;
@@ -277,7 +276,7 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
         }
         __syncthreads();
         // (2) U12 = L11^{-1} Ut  -> U2 and global rows j0..j0+jb-1
-        for (int o = tid; o < NB * CW; o += LU_THREADS) {
+        for (int o = tid; o < NB * CW; o += TH) {
             const int t = o % NB, col = o / NB;
             C s = czero<C>();
 #pragma unroll
@@ -295,7 +294,7 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
         for (int q = 0; q < NB; ++q) {
             C uq[CB];
 #pragma unroll
-            for (int b = 0; b < CB; ++b) uq[b] = sm.U2[q * CW + warp + LU_WARPS * b];
+            for (int b = 0; b < CB; ++b) uq[b] = sm.U2[q * CW + warp + (TH / 32) * b];
 #pragma unroll
             for (int a = 0; a < RA; ++a) {
                 const C l = sm.P[q * PRA + jb + lane + 32 * a];
@@ -308,7 +307,7 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
             const int r = jb + lane + 32 * a;
 #pragma unroll
             for (int b = 0; b < CB; ++b) {
-                const int col = warp + LU_WARPS * b;
+                const int col = warp + (TH / 32) * b;
                 if (r < pr && col < cw) {
                     const int c = c0 + col;
                     ab[(size_t)c * ldab + KV + (j0 + r - c)] = acc[a][b];
@@ -320,12 +319,12 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
 }
 
 // One CTA per point: panel, then the whole trailing window, panel by panel.
-template <typename C, int NB, int RA, int CB>
-__global__ void __launch_bounds__(LU_THREADS, 1)
+template <typename C, int NB, int RA, int CB, int TH>
+__global__ void __launch_bounds__(TH, 1)
 band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
                int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl, int ku,
                int ldab) {
-    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
+    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     const int pt = blockIdx.x;
     C *ab = ab_all + (size_t)pt * ldab * n;
     int32_t *piv = piv_all + (size_t)pt * n;
@@ -334,36 +333,36 @@ band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     C *dinv = dinv_all + (size_t)pt * nblk * 2 * NB * NB;
     const int KV = kl + ku;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const LuSm<C, NB, RA, CB> sm(smem_raw);
-    for (int q = threadIdx.x; q < NB * PRA; q += LU_THREADS) sm.P[q] = czero<C>();
+    const LuSm<C, NB, RA, CB, TH> sm(smem_raw);
+    for (int q = threadIdx.x; q < NB * PRA; q += TH) sm.P[q] = czero<C>();
     int info = 0;
     __syncthreads();
     for (int j0 = 0; j0 < n; j0 += NB) {
         const int jb = min(NB, n - j0);
-        lu_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, j0, sm, info);
-        lu_update<C, NB, RA, CB>(ab, n, kl, KV, ldab, j0, j0 + jb, min(n, j0 + jb + KV), sm);
+        lu_panel<C, NB, RA, CB, TH>(ab, piv, dinv, n, kl, KV, ldab, j0, sm, info);
+        lu_update<C, NB, RA, CB, TH>(ab, n, kl, KV, ldab, j0, j0 + jb, min(n, j0 + jb + KV), sm);
     }
     if (threadIdx.x == 0) info_all[pt] = info;
 }
 
 // A cluster of two CTAs per point.  Iteration of panel j0 (factored and
 // published in global memory before the iteration starts):
-//   CTA 0: update columns [j0+jb, j0+jb+CW) -- they hold the next panel --
-//          then factor the next panel;
+//   CTA 0: update the first chunk(s) of columns [j0+jb, j0+jb+KV) -- the
+//          first holds the next panel -- then factor the next panel;
 //   CTA 1: load the panel's multipliers, L11^{-1} and permutation from global
-//          memory, update columns [j0+jb+CW, j0+jb+KV);
+//          memory, update the remaining chunks;
 //   cluster barrier (release/acquire; every thread of both CTAs).
 // The barrier orders CTA 1's writes of a panel before CTA 0 reads them as
 // the next panel's columns, and CTA 0's factored panel before CTA 1 loads
 // it.  Both CTAs run the same number of barriers: one before the loop, one
 // per panel, with no exit in between.
-template <typename C, int NB, int RA, int CB>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LU_THREADS, 1)
+template <typename C, int NB, int RA, int CB, int TH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TH, 1)
 band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
                        int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl,
                        int ku, int ldab) {
-    constexpr int PRA = LuSm<C, NB, RA, CB>::PRA;
-    constexpr int CW = LuSm<C, NB, RA, CB>::CW;
+    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
+    constexpr int CW = LuSm<C, NB, RA, CB, TH>::CW;
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
     const int pt = blockIdx.x / 2;
@@ -373,23 +372,27 @@ band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     C *dinv = dinv_all + (size_t)pt * nblk * 2 * NB * NB;
     const int KV = kl + ku;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const LuSm<C, NB, RA, CB> sm(smem_raw);
-    for (int q = threadIdx.x; q < NB * PRA; q += LU_THREADS) sm.P[q] = czero<C>();
+    const LuSm<C, NB, RA, CB, TH> sm(smem_raw);
+    for (int q = threadIdx.x; q < NB * PRA; q += TH) sm.P[q] = czero<C>();
     int info = 0;
     __syncthreads();
-    if (rank == 0) lu_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, 0, sm, info);
+    if (rank == 0) lu_panel<C, NB, RA, CB, TH>(ab, piv, dinv, n, kl, KV, ldab, 0, sm, info);
     __threadfence();
     cluster.sync();
     for (int j0 = 0; j0 < n; j0 += NB) {
         const int jb = min(NB, n - j0);
         const int c_beg = j0 + jb, c_end = min(n, j0 + jb + KV);
-        const int c_split = min(c_end, c_beg + CW);
+        // CTA 0 takes the first `s` chunks (the first holds the next panel):
+        // its panel costs about two chunks of update, so s = (chunks - 2) / 2
+        // balances the two CTAs
+        const int nch = (c_end - c_beg + CW - 1) / CW;
+        const int c_split = min(c_end, c_beg + max(1, (nch - 2) / 2) * CW);
         if (rank == 0) {
-            lu_update<C, NB, RA, CB>(ab, n, kl, KV, ldab, j0, c_beg, c_split, sm);
-            if (c_beg < n) lu_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, c_beg, sm, info);
+            lu_update<C, NB, RA, CB, TH>(ab, n, kl, KV, ldab, j0, c_beg, c_split, sm);
+            if (c_beg < n) lu_panel<C, NB, RA, CB, TH>(ab, piv, dinv, n, kl, KV, ldab, c_beg, sm, info);
         } else {
-            lu_load_panel<C, NB, RA, CB>(ab, piv, dinv, n, kl, KV, ldab, j0, sm);
-            lu_update<C, NB, RA, CB>(ab, n, kl, KV, ldab, j0, c_split, c_end, sm);
+            lu_load_panel<C, NB, RA, CB, TH>(ab, piv, dinv, n, kl, KV, ldab, j0, sm);
+            lu_update<C, NB, RA, CB, TH>(ab, n, kl, KV, ldab, j0, c_split, c_end, sm);
         }
         __threadfence();
         cluster.sync();
@@ -397,33 +400,38 @@ band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     if (rank == 0 && threadIdx.x == 0) info_all[pt] = info;
 }
 
-template <typename C, int NB, int RA, int CB>
+template <typename C, int NB, int RA, int CB, int TH>
 static cudaError_t lu_dispatch(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g,
                                int N, int n, bool cluster, cudaStream_t s) {
-    const size_t smem = LuSm<C, NB, RA, CB>::bytes();
+    const size_t smem = LuSm<C, NB, RA, CB, TH>::bytes();
     if (cluster) {
-        cudaError_t e = cudaFuncSetAttribute(band_lu_cluster_kernel<C, NB, RA, CB>,
+        cudaError_t e = cudaFuncSetAttribute(band_lu_cluster_kernel<C, NB, RA, CB, TH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        band_lu_cluster_kernel<C, NB, RA, CB><<<2 * N, LU_THREADS, smem, s>>>(ab, piv, info, dinv, n, g.kl,
+        band_lu_cluster_kernel<C, NB, RA, CB, TH><<<2 * N, TH, smem, s>>>(ab, piv, info, dinv, n, g.kl,
                                                                               g.ku, g.ldab);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<C, NB, RA, CB>,
+    cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<C, NB, RA, CB, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    band_lu_kernel<C, NB, RA, CB><<<N, LU_THREADS, smem, s>>>(ab, piv, info, dinv, n, g.kl, g.ku, g.ldab);
+    band_lu_kernel<C, NB, RA, CB, TH><<<N, TH, smem, s>>>(ab, piv, info, dinv, n, g.kl, g.ku, g.ldab);
     return cudaGetLastError();
 }
 
-template <typename C, int NB, int CB>
+// Panel rows need one thread each: 256 threads cover kl <= 224 (more
+// registers per thread for the trailing update), 512 threads the wider bands.
+// The chunk width CW = (threads / 32) * CB is the same in both, so every
+// element is computed the same way.
+template <typename C, int NB, int CB512>
 static cudaError_t lu_by_kl(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g, int N,
                             int n, bool cluster, cudaStream_t s) {
     const int kl = g.kl;
-    if (kl <= 32) return lu_dispatch<C, NB, 1, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
-    if (kl <= 128) return lu_dispatch<C, NB, 4, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
-    if (kl <= 224) return lu_dispatch<C, NB, 7, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
-    return lu_dispatch<C, NB, 15, CB>(ab, piv, info, dinv, g, N, n, cluster, s);
+    constexpr int CB256 = 2 * CB512;
+    if (kl <= 32) return lu_dispatch<C, NB, 1, CB256, 256>(ab, piv, info, dinv, g, N, n, cluster, s);
+    if (kl <= 128) return lu_dispatch<C, NB, 4, CB256, 256>(ab, piv, info, dinv, g, N, n, cluster, s);
+    if (kl <= 224) return lu_dispatch<C, NB, 7, CB256, 256>(ab, piv, info, dinv, g, N, n, cluster, s);
+    return lu_dispatch<C, NB, 15, CB512, 512>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
 
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 64
