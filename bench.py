@@ -46,13 +46,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2"],
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3"],
                     help="c1: banded grid (the benchmark line); c2: dense kernel, sampling only")
     ap.add_argument("--sample-points", type=int, default=2,
                     help="sampling points of the oracle's bounded sample")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency leg")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--batch-full", action="store_true", help="c3 at its full sizes")
     return ap.parse_args()
 
 
@@ -466,11 +467,37 @@ def run_dense(a):
                       "dense_lu_tflops": lu_flops / (st["stage_ms"][1] / 1e3) / 1e12}))
 
 
+def run_batch(a):
+    """Batched uneven workload through the request server: every problem
+    submitted at t = 0, slots and memory budget admit them as room frees up.
+    Scaled sizes by default (--batch-full for the full ranges)."""
+    import torch
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    torch.cuda.set_device(0)
+    if a.batch_full:
+        probs = W.batch_uneven(256)
+        desc = "256 problems: dense n 256..2048, grids g 100..316, N 16..64, L 8..32 (seed 4000)"
+    else:
+        probs = W.batch_uneven(32, dense_n=(256, 1024), grid_g=(40, 100))
+        desc = "32 problems: dense n 256..1024, grids g 40..100, N 16..64, L 8..32 (seed 4000)"
+    serve_stream(rsrr, probs[:2], None, rsrr.RSRR_PREC_MIXED, a.serve_slots, 1)  # warm-up
+    r = serve_stream(rsrr, probs, None, rsrr.RSRR_PREC_MIXED, a.serve_slots, 4001)
+    print(json.dumps({"workload": "batched uneven NEPs", "problems": desc, "metric": UNIT,
+                      "value": r["columns_per_s"], "makespan_s": r["makespan_s"], "ok": r["ok"],
+                      "requests": r["requests"], "slots": a.serve_slots, "peak_active": r["peak_active"],
+                      "peak_bytes": r["peak_bytes"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"]}))
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
     if a.workload == "c2":
         run_dense(a)
+        return
+    if a.workload == "c3":
+        if rank == 0:
+            run_batch(a)
         return
     if a.impl == "reference":
         run_reference(a, rank, world)

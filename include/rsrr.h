@@ -155,8 +155,12 @@ enum { RSRR_PREC_FP64 = 0, RSRR_PREC_MIXED = 1 };
  *                    8-bit slices; slice products are summed exactly in FP32
  *                    groups and combined in 64-bit integers (Ozaki scheme).
  *                    Error per entry below 2^-52 max|a_i.| max|b_.j| K.
+ *                    The slice products run on the 5th-generation tensor
+ *                    cores (tcgen05.mma, accumulators in tensor memory).
+ *   RSRR_GEMM_OZAKI_MMA  the same slices with the warp-level mma.sync
+ *                    instructions instead (kept for comparison).
  *   RSRR_GEMM_AUTO   OZAKI for products of at least 2^30 flops, else FP64. */
-enum { RSRR_GEMM_AUTO = 0, RSRR_GEMM_FP64 = 1, RSRR_GEMM_OZAKI = 2 };
+enum { RSRR_GEMM_AUTO = 0, RSRR_GEMM_FP64 = 1, RSRR_GEMM_OZAKI = 2, RSRR_GEMM_OZAKI_MMA = 3 };
 
 /* RSRR_FLAG_PLAIN_SOLVE: banded solves of rsrr_sample by the one-kernel
  * solve (factor panels read straight from global memory) instead of the
@@ -342,7 +346,8 @@ rsrr_status rsrr_solve_band_noalloc(int64_t n, int32_t kl, int32_t ku, const rsr
  *              (the product then runs in chunks of K)
  *   stream     work is queued on it; the call waits for it before returning
  * Work space is allocated and freed inside the call.  Returns OK, EINVAL,
- * ENOMEM (work space) or ECUDA; the message is in rsrr_last_error(NULL). */
+ * ENOMEM (work space), ETIMEOUT (a bounded wait of the tensor-core kernel ran
+ * out) or ECUDA; the message is in rsrr_last_error(NULL). */
 rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsrr_c128 *A,
                        int64_t lda, const rsrr_c128 *B, int64_t ldb, rsrr_c128 *C, int64_t ldc,
                        double alpha, double beta, int32_t method, int32_t hermitian,

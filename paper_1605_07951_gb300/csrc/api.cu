@@ -251,7 +251,7 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
     const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
     if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
         return create_fail("rsrr_create: unknown precision");
-    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI))
+    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI_MMA))
         return create_fail("rsrr_create: unknown gemm method");
 
     Handle *h = new (std::nothrow) Handle();
@@ -681,7 +681,7 @@ rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_
     const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
     if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
         return create_fail("rsrr_create: unknown precision");
-    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI))
+    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI_MMA))
         return create_fail("rsrr_create: unknown gemm method");
     Handle *h = new (std::nothrow) Handle();
     if (!h) { thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }

@@ -386,15 +386,245 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
             }
 }
 
+// ----------------------------------------------------------- tcgen05 path
+// The same products on the 5th-generation tensor cores: a CTA of 256 threads
+// owns a 128 x 64 tile of C~.  Per 16-deep stage of K' the 7 A slices (128
+// rows) and the 7 B slices (64 rows each, stacked to 448 rows) are copied by
+// cp.async into shared memory in the K-major core-matrix layout (8 rows x 16
+// bytes per core matrix, no swizzle), four stages deep, and one thread issues
+// 19 tcgen05.mma per stage (M = 128, N = 64..256, bf16 -> FP32 in tensor
+// memory): the slice pairs of one A slice whose groups t = p + q <= 4 are
+// one MMA over the consecutive B slices (their accumulators are consecutive
+// 64-column regions of tensor memory); the pairs with t >= 5 go to a sixth
+// region, which is inexact by design (relative weight <= 2^-40) and simply
+// keeps accumulating.  Groups t <= 4 hold at most (t+1) 2^14 per K' element,
+// so every 192 of K' (and at the end) all threads wait for the MMAs
+// (tcgen05.commit -> mbarrier), read their part of regions 0..4 (tcgen05.ld;
+// warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows, columns 32 (w / 4)
+// .. +31), and fold them into 64-bit integers; the next MMAs restart those
+// regions.  Every mbarrier wait is bounded; a wait that runs out counts in
+// g_ozt_timeouts and the kernel finishes without hanging.
+constexpr int OZT_BM = 128;
+constexpr int OZT_BN = 64;
+constexpr int OZT_KC = 16;
+constexpr int OZT_THREADS = 256;
+constexpr int OZT_A_SLICE = OZT_BM * OZT_KC * 2;           // bytes of one A slice per stage
+constexpr int OZT_B_SLICE = OZT_BN * OZT_KC * 2;           // bytes of one B slice per stage
+constexpr int OZT_STAGE = OZ_S * (OZT_A_SLICE + OZT_B_SLICE);
+constexpr int OZT_NST = 4;
+constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;  // + mbarriers, TMEM address
+constexpr uint32_t OZT_LBO = 128;                 // next core matrix along K
+constexpr uint32_t OZT_SBO = (OZT_KC / 8) * 128;  // next 8-row group
+constexpr int OZT_FOLD = 12;                      // stages per exact fold (K' = 192)
+constexpr long long OZT_WAIT_LIMIT = 1LL << 26;
+static_assert((4 + 1) * OZT_FOLD * OZT_KC * 16384 < (1 << 24), "group sums must stay exact in FP32");
+
+__device__ unsigned int g_ozt_timeouts;
+
+// shared-memory matrix descriptor: K-major, no swizzle, start / LBO / SBO in
+// 16-byte units, descriptor version 1
+RSRR_DEV uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((OZT_LBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((OZT_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = n
+RSRR_DEV uint32_t umma_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZT_BM >> 4) << 24);
+}
+RSRR_DEV void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+RSRR_DEV void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 ::"r"(mbar) : "memory");
+}
+RSRR_DEV bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < OZT_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+RSRR_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(OZT_THREADS, 1)
+oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs,
+                  const int *__restrict__ Ea, const int *__restrict__ Eb, double *__restrict__ W,
+                  double2 *__restrict__ C, int64_t ldc, int M, int N, int Mp, int Np, int Kp, int kchunk,
+                  int halfN_tiles, int upper_only, double alpha, double beta) {
+    const int bm = blockIdx.x, bn = blockIdx.y, sp = blockIdx.z;
+    if (upper_only && OZT_BM * bm > OZT_BN * (bn % halfN_tiles) + OZT_BN - 1) return;
+    extern __shared__ __align__(1024) unsigned char ozt_smem[];
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(ozt_smem);
+    const uint32_t mb_stage = sbase + OZT_NST * OZT_STAGE;  // OZT_NST mbarriers
+    const uint32_t mb_fold = mb_stage + 8 * OZT_NST;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + 8 * OZT_NST + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = bm * OZT_BM, n0 = bn * OZT_BN;
+    const int kbeg = sp * kchunk;
+    const int kend = min(Kp, kbeg + kchunk);
+    const int nk = kend > kbeg ? (kend - kbeg) / OZT_KC : 0;
+    const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
+
+    if (tid == 0) {
+        for (int q = 0; q <= OZT_NST; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_stage + 8 * q));
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    // rows of one stage: 7 x 128 A rows, then 7 x 64 B rows; 2 copies of 16 B each
+    auto load_stage = [&](int slot, int k0) {
+        const uint32_t dst0 = sbase + (uint32_t)(slot * OZT_STAGE);
+        for (int q = tid; q < OZ_S * (OZT_BM + OZT_BN) * 2; q += OZT_THREADS) {
+            const int c = q & 1, row = q >> 1;
+            const __nv_bfloat16 *src;
+            uint32_t dst;
+            if (row < OZ_S * OZT_BM) {
+                const int p = row / OZT_BM, r = row % OZT_BM;
+                src = As + p * sA + (size_t)(m0 + r) * Kp + k0 + c * 8;
+                dst = dst0 + p * OZT_A_SLICE + (r >> 3) * OZT_SBO + c * OZT_LBO + (r & 7) * 16;
+            } else {
+                const int rb = row - OZ_S * OZT_BM, qs = rb / OZT_BN, r = rb % OZT_BN;
+                src = Bs + qs * sB + (size_t)(n0 + r) * Kp + k0 + c * 8;
+                dst = dst0 + OZ_S * OZT_A_SLICE + qs * OZT_B_SLICE + (r >> 3) * OZT_SBO + c * OZT_LBO +
+                      (r & 7) * 16;
+            }
+            cp_async16(dst, src);
+        }
+    };
+#pragma unroll
+    for (int st = 0; st < OZT_NST - 1; ++st) {
+        if (st < nk) load_stage(st, kbeg + st * OZT_KC);
+        cp_async_commit();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // this thread's part of the tile: row 32 (w % 4) + lane, columns 32 (w / 4) ..
+    const int lrow = 32 * (warp & 3) + lane, lcol = 32 * (warp >> 2);
+    const uint32_t tpart = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)lcol;
+
+    long long acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    bool ok = true;
+    int folds = 0;
+    for (int it = 0; it < nk; ++it) {
+        const int slot = it % OZT_NST;
+        const int nx = it + OZT_NST - 1;
+        if (nx < nk) {
+            // slot nx % NST was last read by the MMAs of stage nx - NST = it - 1
+            if (nx >= OZT_NST)
+                ok = mbar_wait(mb_stage + 8 * (nx % OZT_NST), ((nx / OZT_NST) - 1) & 1) && ok;
+            load_stage(nx % OZT_NST, kbeg + nx * OZT_KC);
+        }
+        cp_async_commit();
+        cp_async_wait<OZT_NST - 1>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        const bool fold = ((it + 1) % OZT_FOLD) == 0 || it == nk - 1;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
+            const uint32_t b0 = a0 + OZ_S * OZT_A_SLICE;
+            const uint32_t keep = (it % OZT_FOLD) == 0 ? 0u : 1u;  // regions 0..4 restart after a fold
+            const uint32_t keep5 = it == 0 ? 0u : 1u;                // region 5 starts once
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p) {
+                const uint64_t ad = umma_desc(a0 + p * OZT_A_SLICE);
+                // groups p .. 4: one MMA over B slices 0 .. 4 - p (at most 4 at a time)
+                for (int q0 = 0; q0 <= 4 - p; q0 += 4) {
+                    const int nq = min(4, 5 - p - q0);
+                    umma_bf16(tmem + (uint32_t)((p + q0) * OZT_BN), ad, umma_desc(b0 + q0 * OZT_B_SLICE),
+                              umma_idesc(nq * OZT_BN), p == 0 ? keep : 1u);
+                }
+                // groups 5 and 6 share the sixth region
+                for (int q = max(0, 5 - p); q <= OZ_S - 1 - p; ++q)
+                    umma_bf16(tmem + 5 * OZT_BN, ad, umma_desc(b0 + q * OZT_B_SLICE), umma_idesc(OZT_BN),
+                              (p == 0 && q == 5) ? keep5 : 1u);
+            }
+            umma_commit(mb_stage + 8 * slot);
+            if (fold) umma_commit(mb_fold);
+        }
+        if (fold) {
+            ok = mbar_wait(mb_fold, folds & 1) && ok;
+            ++folds;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tpart + (uint32_t)(t * OZT_BN + c0), r);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c0 + j] += scaled_group_to_ll(__uint_as_float(r[j]));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+        }
+    }
+    cp_async_wait<0>();
+    float low[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) low[c] = 0.f;
+    if (nk > 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tpart + (uint32_t)(5 * OZT_BN + c0), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) low[c0 + j] = __uint_as_float(r[j]);
+        }
+    }
+    if (!ok && lane == 0) atomicAdd(&g_ozt_timeouts, 1u);
+
+    const int i = m0 + lrow;
+    const int ea = Ea[i];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int jj = n0 + lcol + c;
+        const double v = ldexp((double)acc[c] + (double)low[c] * 0x1p32, ea + Eb[jj] - 2090);
+        if (W) {
+            W[(size_t)sp * Mp * Np + (size_t)i * Np + jj] = v;
+        } else if (i < M && jj < 2 * N) {
+            const int part = jj >= N, j = jj - part * N;
+            double *cp = reinterpret_cast<double *>(C + (int64_t)j * ldc + i) + part;
+            double r = alpha * v;
+            if (beta != 0.0) r = fma(beta, *cp, r);
+            *cp = r;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+}
+
 // C = alpha sum_s W[s] + beta C (fixed order over the splits)
 __global__ void oz_combine_kernel(double2 *__restrict__ C, int64_t ldc, const double *__restrict__ W,
                                   int M, int N, int Mp, int Np, int splits, double alpha, double beta,
-                                  int upper_only) {
+                                  int upper_only, int bm) {
     const int64_t total = (int64_t)M * N;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(q % M), j = (int)(q / M);
-        if (upper_only && (i / OZ_BM) > (j / OZ_BN)) continue;
+        if (upper_only && bm * (i / bm) > OZ_BN * (j / OZ_BN) + OZ_BN - 1) continue;
         double re = 0.0, im = 0.0;
         for (int s = 0; s < splits; ++s) {
             const double *Wp = W + (size_t)s * Mp * Np + (size_t)i * Np;
@@ -474,11 +704,21 @@ int choose_splits(int64_t tiles, int64_t Kp) {
     return best;
 }
 
-OzPlan make_plan(int M, int N, int K, bool hermitian, size_t ws_bytes) {
+// computed tiles of a bm x 64 tiling (upper block triangle only for Hermitian results)
+int64_t tile_count(int64_t Mp, int64_t Np, int bm, bool upper, int64_t halfN) {
+    if (!upper) return (Mp / bm) * (Np / OZ_BN);
+    int64_t t = 0;
+    for (int64_t a = 0; a < Mp / bm; ++a)
+        for (int64_t b = 0; b < Np / OZ_BN; ++b)
+            if (bm * a <= OZ_BN * (b % halfN) + OZ_BN - 1) ++t;
+    return t;
+}
+
+OzPlan make_plan(int M, int N, int K, bool hermitian, size_t ws_bytes, int bm) {
     OzPlan p{};
-    p.Mp = rup(M, OZ_BM);
+    p.Mp = rup(M, bm);
     p.Np = rup(2 * (int64_t)N, OZ_BN);
-    const int64_t tiles = (p.Mp / OZ_BM) * (p.Np / OZ_BN) / (hermitian ? 2 : 1);
+    const int64_t tiles = (p.Mp / bm) * (p.Np / OZ_BN) / (hermitian ? 2 : 1);
     const int64_t Kall = std::max(K, 1);
     auto fit = [&](int64_t kc) {
         p.Kc = kc;
@@ -500,22 +740,24 @@ OzPlan make_plan(int M, int N, int K, bool hermitian, size_t ws_bytes) {
 }  // namespace
 
 size_t ozaki_workspace_bytes(int M, int N, int K, bool hermitian) {
-    return make_plan(M, N, K, hermitian, SIZE_MAX).bytes;
+    return std::max(make_plan(M, N, K, hermitian, SIZE_MAX, OZ_BM).bytes,
+                    make_plan(M, N, K, hermitian, SIZE_MAX, OZT_BM).bytes);
 }
 
-double ozaki_tc_flops(int M, int N, int K, bool hermitian) {
+double ozaki_tc_flops(int M, int N, int K, bool hermitian, bool legacy) {
     if (M <= 0 || N <= 0 || K <= 0) return 0.0;
-    const OzPlan p = make_plan(M, N, K, hermitian, SIZE_MAX);
+    const int bm = legacy ? OZ_BM : OZT_BM;
+    const OzPlan p = make_plan(M, N, K, hermitian, SIZE_MAX, bm);
     const double pairs = OZ_S * (OZ_S + 1) / 2;
-    const double tm = (double)(p.Mp / OZ_BM), tn = (double)(p.Np / OZ_BN);
-    const double tiles = hermitian && M == N && (N % OZ_BN) == 0 ? tm * (tm + 1) : tm * tn;
-    return 2.0 * pairs * tiles * OZ_BM * OZ_BN * (double)p.Kp;
+    const bool upper = hermitian && M == N && (N % OZ_BN) == 0;
+    const double tiles = (double)tile_count(p.Mp, p.Np, bm, upper, upper ? N / OZ_BN : p.Np / OZ_BN);
+    return 2.0 * pairs * tiles * bm * OZ_BN * (double)p.Kp;
 }
 
 cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                         const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
                         double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
-                        int64_t *launches, EventPool *timer, double *tc_flops) {
+                        int64_t *launches, EventPool *timer, double *tc_flops, bool legacy) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     cudaError_t e;
     if (K <= 0 || alpha == 0.0) {
@@ -524,9 +766,13 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
         return cudaGetLastError();
     }
     if (hermitian && (M != N || !conjA || A != B || lda != ldb)) hermitian = false;
-    const OzPlan p = make_plan(M, N, K, hermitian, ws_bytes);
+    const int bm = legacy ? OZ_BM : OZT_BM;
+    const OzPlan p = make_plan(M, N, K, hermitian, ws_bytes, bm);
     if (p.bytes > ws_bytes) return cudaErrorMemoryAllocation;
-    e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    if (legacy)
+        e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    else
+        e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZT_SMEM);
     if (e != cudaSuccess) return e;
     char *w = static_cast<char *>(ws);
     __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(w);
@@ -562,7 +808,7 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
         oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Np, 65535)), 256, 0, s>>>(
             Bs, Eb, Bk, ldb, 1, 2 * N, N, Kc, (int)p.Np, (int)p.Kp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const dim3 grid((unsigned)(p.Mp / OZ_BM), (unsigned)(p.Np / OZ_BN), (unsigned)p.splits);
+        const dim3 grid((unsigned)(p.Mp / bm), (unsigned)(p.Np / OZ_BN), (unsigned)p.splits);
         cudaEvent_t ev1 = nullptr;
         if (timer) {
             cudaEvent_t ev0;
@@ -570,16 +816,22 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
             if ((e = timer->next(&ev1)) != cudaSuccess) return e;
             if ((e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
         }
-        oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N, (int)p.Mp,
-                                                        (int)p.Np, (int)p.Kp, (int)p.kchunk,
-                                                        halfN_tiles, upper ? 1 : 0, alpha, b);
+        if (legacy)
+            oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N, (int)p.Mp,
+                                                            (int)p.Np, (int)p.Kp, (int)p.kchunk,
+                                                            halfN_tiles, upper ? 1 : 0, alpha, b);
+        else
+            oz_gemm_tc_kernel<<<grid, OZT_THREADS, OZT_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N,
+                                                                 (int)p.Mp, (int)p.Np, (int)p.Kp,
+                                                                 (int)p.kchunk, halfN_tiles,
+                                                                 upper ? 1 : 0, alpha, b);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (timer && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
-        if (tc_flops) *tc_flops += ozaki_tc_flops(M, N, Kc, upper);
+        if (tc_flops) *tc_flops += ozaki_tc_flops(M, N, Kc, upper, legacy);
         if (Wp) {
             oz_combine_kernel<<<grid_for((int64_t)M * N), 256, 0, s>>>(C, ldc, Wp, M, N, (int)p.Mp,
                                                                        (int)p.Np, p.splits, alpha, b,
-                                                                       upper ? 1 : 0);
+                                                                       upper ? 1 : 0, bm);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (launches) *launches += 5 + (Wp ? 1 : 0);
@@ -614,7 +866,7 @@ extern "C" rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA
     const int64_t rowsA = conjA ? K : M;
     if (ldc < std::max(1, M) || ldb < std::max(1, K) || lda < std::max<int64_t>(1, rowsA))
         return fail(RSRR_EINVAL, "leading dimension too small");
-    if (method < RSRR_GEMM_AUTO || method > RSRR_GEMM_OZAKI) return fail(RSRR_EINVAL, "unknown method");
+    if (method < RSRR_GEMM_AUTO || method > RSRR_GEMM_OZAKI_MMA) return fail(RSRR_EINVAL, "unknown method");
     if (hermitian && (!conjA || A != B || lda != ldb || M != N || beta != 0.0))
         return fail(RSRR_EINVAL, "hermitian needs conjA, A == B, lda == ldb, M == N, beta == 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -622,7 +874,9 @@ extern "C" rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA
     const double2 *b = reinterpret_cast<const double2 *>(B);
     double2 *c = reinterpret_cast<double2 *>(C);
     const double flops = 8.0 * M * (double)N * K;
-    const bool sliced = method == RSRR_GEMM_OZAKI || (method == RSRR_GEMM_AUTO && flops >= 1073741824.0);
+    const bool legacy = method == RSRR_GEMM_OZAKI_MMA;
+    const bool sliced = method == RSRR_GEMM_OZAKI || legacy ||
+                        (method == RSRR_GEMM_AUTO && flops >= 1073741824.0);
     cudaError_t e;
     if (!sliced) {
         if ((e = fp64_gemm(M, N, K, conjA != 0, a, lda, b, ldb, c, ldc, alpha, beta, s)) != cudaSuccess)
@@ -632,8 +886,19 @@ extern "C" rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA
         if (max_ws_bytes > 0) need = std::min(need, max_ws_bytes);
         void *ws = nullptr;
         if ((e = cudaMalloc(&ws, need)) != cudaSuccess) return fail(RSRR_ENOMEM, "work space", e);
+        unsigned int t0 = 0, t1 = 0;
+        if ((e = cudaMemcpyFromSymbol(&t0, g_ozt_timeouts, sizeof t0)) != cudaSuccess) {
+            cudaFree(ws);
+            return fail(RSRR_ECUDA, "timeout counter", e);
+        }
         e = ozaki_zgemm(M, N, K, conjA != 0, a, lda, b, ldb, c, ldc, alpha, beta, hermitian != 0, ws,
-                        need, s, nullptr);
+                        need, s, nullptr, nullptr, nullptr, legacy);
+        if (e == cudaSuccess && (e = cudaStreamSynchronize(s)) == cudaSuccess)
+            e = cudaMemcpyFromSymbol(&t1, g_ozt_timeouts, sizeof t1);
+        if (e == cudaSuccess && t1 != t0) {
+            cudaFree(ws);
+            return fail(RSRR_ETIMEOUT, "a bounded tensor-core wait ran out");
+        }
         cudaError_t e2 = cudaStreamSynchronize(s);
         cudaFree(ws);
         if (e == cudaErrorMemoryAllocation) return fail(RSRR_ENOMEM, "work space below one chunk");

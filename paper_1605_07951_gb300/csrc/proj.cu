@@ -153,8 +153,10 @@ struct Gemm {
                     bool hermitian = false, double alpha = 1.0, double beta = 0.0) {
         if (M <= 0 || N <= 0) return cudaSuccess;
         const double flops = hermitian ? 8.0 * (double)M * (M + 1) / 2 * K : 8.0 * M * N * (double)K;
+        const bool legacy = method == RSRR_GEMM_OZAKI_MMA;
         const bool sliced = ows && K > 0 &&
-                            (method == RSRR_GEMM_OZAKI || (method == RSRR_GEMM_AUTO && flops >= 1073741824.0));
+                            (method == RSRR_GEMM_OZAKI || legacy ||
+                             (method == RSRR_GEMM_AUTO && flops >= 1073741824.0));
         if (sliced) {
             cudaError_t e;
             cudaEvent_t ev1 = nullptr;
@@ -167,7 +169,7 @@ struct Gemm {
             }
             e = ozaki_zgemm(M, N, K, conjA, A, lda, B, ldb, C, ldc, alpha, beta, hermitian, ows,
                             ows_bytes, s, counter, timer ? &timer->tc_pool : nullptr,
-                            timer ? &timer->tc_flops : nullptr);
+                            timer ? &timer->tc_flops : nullptr, legacy);
             if (e == cudaSuccess && timer) e = cudaEventRecord(ev1, s);
             return e;
         }

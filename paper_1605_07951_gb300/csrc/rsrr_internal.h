@@ -138,14 +138,17 @@ cudaError_t fp64_gemm(int M, int N, int K, bool conjA, const double2 *A, int64_t
 // ozaki_workspace_bytes.  cudaErrorMemoryAllocation if ws cannot hold one
 // chunk of 16.
 // With timer set, a pair of events brackets every launch of the main kernel
-// and *tc_flops grows by the tensor-core flops it issues.
+// and *tc_flops grows by the tensor-core flops it issues.  The main kernel is
+// the tcgen05 one; legacy selects the mma.sync kernel (kept for comparison).
 struct EventPool;
 cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                         const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
                         double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
-                        int64_t *launches, EventPool *timer = nullptr, double *tc_flops = nullptr);
+                        int64_t *launches, EventPool *timer = nullptr, double *tc_flops = nullptr,
+                        bool legacy = false);
 size_t ozaki_workspace_bytes(int M, int N, int K, bool hermitian);
-// bf16 tensor-core flops the product issues (2 per multiply-add of slices)
-double ozaki_tc_flops(int M, int N, int K, bool hermitian);
+// bf16 tensor-core flops the product issues (2 per multiply-add of slices);
+// legacy: the mma.sync kernel (64-row tiles) instead of the tcgen05 kernel
+double ozaki_tc_flops(int M, int N, int K, bool hermitian, bool legacy = false);
 
 }  // namespace rsrr

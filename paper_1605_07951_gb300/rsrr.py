@@ -28,7 +28,7 @@ RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7
 RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = range(6)
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
-RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI = 0, 1, 2
+RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI, RSRR_GEMM_OZAKI_MMA = 0, 1, 2, 3
 RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU = 1, 2
 RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ = 0, 1
 RSRR_MAX_TERMS = 8

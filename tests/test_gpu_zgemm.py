@@ -62,7 +62,7 @@ def exact_product(A, B, conjA):
     return ar @ br - ai @ bi, ar @ bi + ai @ br
 
 
-METHODS = [(1, "fp64"), (2, "ozaki")]
+METHODS = [(1, "fp64"), (2, "ozaki_tcgen05"), (3, "ozaki_mma")]
 SHAPES = [(1, 1, 1), (37, 53, 29), (130, 70, 301), (64, 128, 1000), (200, 9, 777)]
 
 
@@ -106,13 +106,14 @@ def test_scaled_random_products_within_the_bound(env, method, conjA, shape):
     assert np.all(err_r <= bound) and np.all(err_i <= bound)
 
 
-@pytest.mark.parametrize("shape", [(64, 5000), (100, 3001), (192, 20000)])
-def test_hermitian_gram_is_exactly_hermitian(env, shape):
+@pytest.mark.parametrize("method", [2, 3], ids=["ozaki_tcgen05", "ozaki_mma"])
+@pytest.mark.parametrize("shape", [(64, 5000), (100, 3001), (192, 20000), (320, 1024)])
+def test_hermitian_gram_is_exactly_hermitian(env, shape, method):
     N, K = shape
     rng = np.random.default_rng(N + K)
     S = rand(rng, K, N)
     S /= np.linalg.norm(S, axis=0)
-    G = zgemm(env, S, S, True, 2, hermitian=True)
+    G = zgemm(env, S, S, True, method, hermitian=True)
     assert np.array_equal(G, G.conj().T)
     rr, ri = exact_product(S, S, True)
     ref = (rr + 1j * ri).astype(np.complex128)
@@ -121,15 +122,16 @@ def test_hermitian_gram_is_exactly_hermitian(env, shape):
     assert np.all(np.abs(G - ref) <= bound + 1e-300)
 
 
-def test_chunked_and_split_K_agree_with_the_whole_product(env):
+@pytest.mark.parametrize("method", [2, 3], ids=["ozaki_tcgen05", "ozaki_mma"])
+def test_chunked_and_split_K_agree_with_the_whole_product(env, method):
     torch, rsrr = env
     rng = np.random.default_rng(5)
     M, N, K = 40, 24, 20000   # few tiles, long K: split across CTAs
     A = rand(rng, K, M)
     B = rand(rng, K, N)
-    whole = zgemm(env, A, B, True, 2)
-    # a work space for about 1/5 of K forces chunks of K
-    chunked = zgemm(env, A, B, True, 2, ws=14 * (64 + 64) * 2 * 4096 + 4096)
+    whole = zgemm(env, A, B, True, method)
+    # a work space for a fraction of K forces chunks of K
+    chunked = zgemm(env, A, B, True, method, ws=14 * (128 + 64) * 2 * 4096 + 4096)
     scale = np.abs(A).max() * np.abs(B).max() * K
     assert np.abs(whole - chunked).max() <= 8 * K * 2.0 ** -53 * np.abs(A).max() * np.abs(B).max()
     rr, ri = exact_product(A, B, True)
@@ -142,7 +144,7 @@ def test_alpha_beta_and_empty_depth(env):
     A = rand(rng, M, K)
     B = rand(rng, K, N)
     C0 = rand(rng, M, N)
-    for method in (1, 2):
+    for method in (1, 2, 3):
         got = zgemm(env, A, B, False, method, C0=C0, alpha=-1.0, beta=1.0)
         ref = C0 - A @ B
         assert np.abs(got - ref).max() <= 1e-12 * (np.abs(A) @ np.abs(B)).max()
@@ -163,3 +165,18 @@ def test_bad_arguments_are_rejected(env):
     assert rsrr.rsrr_zgemm(2, 2, 2, 0, p, 2, p, 2, p, 2, 1.0, 0.0, 7, 0, 0, None) == rsrr.RSRR_EINVAL
     # hermitian needs A^H A
     assert rsrr.rsrr_zgemm(2, 2, 2, 0, p, 2, p, 2, p, 2, 1.0, 0.0, 2, 1, 0, None) == rsrr.RSRR_EINVAL
+
+
+@pytest.mark.parametrize("shape", [(256, 128, 3000), (130, 70, 5001)])
+def test_tcgen05_and_mma_slice_products_agree(env, shape):
+    """The two kernels sum the same exact slice products; only the rounded
+    sixth group (relative weight <= 2^-40) may differ."""
+    M, N, K = shape
+    rng = np.random.default_rng(M * N + K)
+    A = rand(rng, K, M)
+    B = rand(rng, K, N)
+    a = zgemm(env, A, B, True, 2)
+    b = zgemm(env, A, B, True, 3)
+    amax = np.maximum(np.abs(A.real), np.abs(A.imag)).max(axis=0)
+    bmax = np.maximum(np.abs(B.real), np.abs(B.imag)).max(axis=0)
+    assert np.all(np.abs(a - b) <= 2 * K * 2.0 ** -53 * np.outer(amax, bmax))

@@ -422,3 +422,26 @@ def serving_stream(count: int = 48, seed: int = 5000):
                                  seed_u=s_u, name="c2_req")
         out.append((fam, p))
     return out
+
+
+def batch_uneven(count: int = 256, seed: int = 4000, dense_n=(256, 2048), grid_g=(100, 316),
+                 N=(16, 64), L=(8, 32)):
+    """The batched uneven workload: `count` problems, half dense sphere kernels
+    with n uniform in dense_n, half rational grids with side g uniform in
+    grid_g, N uniform in N and L uniform in L, in a seeded shuffled order.
+    Returns a list of (family, problem)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nN = int(rng.integers(N[0], N[1] + 1))
+        nL = int(rng.integers(L[0], L[1] + 1))
+        if i % 2 == 0:
+            n = int(rng.integers(dense_n[0], dense_n[1] + 1))
+            out.append(("dense", helmholtz_sphere(n=n, N=nN, L=nL, seed=seed + 1 + i,
+                                                  seed_u=seed + 10001 + i, name="c3_dense")))
+        else:
+            g = int(rng.integers(grid_g[0], grid_g[1] + 1))
+            out.append(("grid", rational_grid(g=g, N=nN, L=nL, seed_e=seed + 1 + i,
+                                              seed_u=seed + 10001 + i, name="c3_grid")))
+    order = rng.permutation(count)
+    return [out[k] for k in order]
