@@ -334,13 +334,13 @@ def run_ours(a, rank, world, local):
     peaks = measured_peaks()
     tc_avg = statistics.mean(tc_ms)
     tc_ach = statistics.mean(tc_flops) / (tc_avg / 1e3) / 1e12 if tc_avg > 0 else 0.0
-    roof_tc = {"bound": "tensor", "kernel": "oz_gemm_kernel (bf16 slice products, Ozaki GEMMs)",
+    roof_tc = {"bound": "tensor", "kernel": "oz_gemm_tc_kernel (bf16 slice products on tcgen05, Ozaki GEMMs)",
                "achieved": tc_ach, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                "frac": tc_ach / peaks["bf16_sustained"], "traffic": None,
                "tensor_flop_per_step": statistics.mean(tc_flops), "ms_per_step": tc_avg,
                "peak_note": f"bf16 dense, sustained, {peaks['source']}; flops = the 28 slice-pair "
-                            "products per tile the scheme needs (mma.sync m16n8k16); traffic null: "
-                            "many GEMM shapes per step",
+                            "products per 128x64 tile the scheme needs (tcgen05.mma kind::f16); "
+                            "traffic null: many GEMM shapes per step",
                "fp64_equivalent": {"flop_per_step": statistics.mean(gemm_flops),
                                    "gemm_ms_per_step": statistics.mean(gemm_ms),
                                    "tflops": statistics.mean(gemm_flops)

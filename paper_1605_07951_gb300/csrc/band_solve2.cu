@@ -25,9 +25,9 @@
 namespace rsrr {
 
 constexpr int S2_THREADS = 512;
-constexpr int S2_RC = 128;          // panel rows per unit
-constexpr int S2_NSLOT = 3;         // ring slots
-constexpr int S2_DIST = S2_NSLOT - 1;
+// Two unit shapes: RC = 256 panel rows per unit with two ring slots (8
+// right-hand sides of one row per thread: fewer shared-memory loads per FMA),
+// used when it fits in shared memory, else RC = 128 with three slots.
 
 // ---------------------------------------------------------------------------
 // Composed permutation of each block: the LU swaps row j0+cc with piv[j0+cc]
@@ -95,7 +95,7 @@ template <typename C> RSRR_DEV void s2_cp_elem(unsigned saddr, const C *g);
 template <> RSRR_DEV void s2_cp_elem<float2>(unsigned saddr, const float2 *g) { s2_cp8(saddr, g); }
 template <> RSRR_DEV void s2_cp_elem<double2>(unsigned saddr, const double2 *g) { s2_cp16(saddr, g); }
 
-template <typename C, int NB, int LC>
+template <typename C, int NB, int LC, int S2_RC, int S2_NSLOT>
 struct S2Layout {
     static constexpr int E16 = 16 / (int)sizeof(C);          // elements per 16 bytes
     static constexpr int PLD = S2_RC + E16;                   // panel column stride (elements)
@@ -128,16 +128,18 @@ RSRR_DEV S2Blk s2_blk(int j, int n, int NB, int kl) {
 RSRR_DEV int s2_rows(int phase, const S2Blk &b, int KV) {
     return phase == 0 ? b.pr - b.jb : min(KV, b.j0);
 }
+template <int S2_RC>
 RSRR_DEV int s2_units(int phase, const S2Blk &b, int KV) {
     return max(1, (s2_rows(phase, b, KV) + S2_RC - 1) / S2_RC);
 }
 
-template <typename C, int NB, int LC>
+template <typename C, int NB, int LC, int S2_RC, int S2_NSLOT>
 __global__ void __launch_bounds__(S2_THREADS, 1)
 band_solve2_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ bperm_all,
                    const C *__restrict__ dinv_all, C *__restrict__ B_all, int n, int kl, int ku,
                    int ldab, int L, int WR, const int32_t *__restrict__ skip) {
-    using LY = S2Layout<C, NB, LC>;
+    using LY = S2Layout<C, NB, LC, S2_RC, S2_NSLOT>;
+    constexpr int S2_DIST = S2_NSLOT - 1;
     constexpr int E16 = LY::E16, PLD = LY::PLD, MAXCH = LY::MAXCH, PAIRS = LY::PAIRS;
     constexpr int WLD = LY::WLD;
     constexpr int CG = LC * S2_RC / S2_THREADS;  // right-hand sides per thread in an update
@@ -169,7 +171,7 @@ band_solve2_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ bpe
         bool pdone = false;
         auto advance = [&](int &j, int &k) -> bool {  // false at the end of the phase
             const S2Blk b = s2_blk(j, n, NB, kl);
-            if (++k < s2_units(phase, b, KV)) return true;
+            if (++k < s2_units<S2_RC>(phase, b, KV)) return true;
             k = 0;
             j += phase == 0 ? 1 : -1;
             return phase == 0 ? j < nblk : j >= 0;
@@ -318,30 +320,47 @@ cudaError_t launch_block_perm(int32_t *bperm, const int32_t *piv, int n, int kl,
     return cudaGetLastError();
 }
 
-static int s2_window(const BandGeom &g, int nb) { return g.kl + g.ku + (S2_DIST + 1) * nb; }
+static int s2_window(const BandGeom &g, int nb, int nslot) { return g.kl + g.ku + nslot * nb; }
 
-template <typename C, int NB, int LC>
+template <typename C, int NB, int LC, int RC, int NSLOT>
 static size_t s2_smem(const BandGeom &g) {
-    return S2Layout<C, NB, LC>::smem(s2_window(g, NB));
+    return S2Layout<C, NB, LC, RC, NSLOT>::smem(s2_window(g, NB, NSLOT));
 }
 
-size_t band_solve2_smem_c64(const BandGeom &g) { return s2_smem<float2, NB_C64, 16>(g); }
-size_t band_solve2_smem_c128(const BandGeom &g) { return s2_smem<double2, NB_C128, 8>(g); }
+// the wide unit shape when it fits in shared memory
+template <typename C, int NB, int LC>
+static bool s2_wide(const BandGeom &g) {
+    return s2_smem<C, NB, LC, 256, 2>(g) <= 227 * 1024;
+}
+template <typename C, int NB, int LC>
+static size_t s2_smem_used(const BandGeom &g) {
+    return s2_wide<C, NB, LC>(g) ? s2_smem<C, NB, LC, 256, 2>(g) : s2_smem<C, NB, LC, 128, 3>(g);
+}
+
+size_t band_solve2_smem_c64(const BandGeom &g) { return s2_smem_used<float2, NB_C64, 16>(g); }
+size_t band_solve2_smem_c128(const BandGeom &g) { return s2_smem_used<double2, NB_C128, 8>(g); }
+
+template <typename C, int NB, int LC, int RC, int NSLOT>
+static cudaError_t s2_launch(const C *ab, const int32_t *bperm, const C *dinv, C *B, const BandGeom &g,
+                             int N, int n, int L, const int32_t *skip, cudaStream_t s) {
+    const size_t smem = s2_smem<C, NB, LC, RC, NSLOT>(g);
+    const int limit = smem_optin_limit();
+    if (smem > 227 * 1024 || smem > (size_t)limit) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(band_solve2_kernel<C, NB, LC, RC, NSLOT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    if (e != cudaSuccess) return e;
+    dim3 grid((L + LC - 1) / LC, N);
+    band_solve2_kernel<C, NB, LC, RC, NSLOT><<<grid, S2_THREADS, smem, s>>>(
+        ab, bperm, dinv, B, n, g.kl, g.ku, g.ldab, L, s2_window(g, NB, NSLOT), skip);
+    return cudaGetLastError();
+}
 
 template <typename C, int NB, int LC>
 static cudaError_t s2_dispatch(const C *ab, const int32_t *bperm, const C *dinv, C *B,
                                const BandGeom &g, int N, int n, int L, const int32_t *skip,
                                cudaStream_t s) {
-    const size_t smem = s2_smem<C, NB, LC>(g);
-    const int limit = smem_optin_limit();
-    if (smem > 227 * 1024 || smem > (size_t)limit) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(band_solve2_kernel<C, NB, LC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-    if (e != cudaSuccess) return e;
-    dim3 grid((L + LC - 1) / LC, N);
-    band_solve2_kernel<C, NB, LC><<<grid, S2_THREADS, smem, s>>>(ab, bperm, dinv, B, n, g.kl, g.ku,
-                                                                 g.ldab, L, s2_window(g, NB), skip);
-    return cudaGetLastError();
+    if (s2_wide<C, NB, LC>(g)) return s2_launch<C, NB, LC, 256, 2>(ab, bperm, dinv, B, g, N, n, L, skip, s);
+    return s2_launch<C, NB, LC, 128, 3>(ab, bperm, dinv, B, g, N, n, L, skip, s);
 }
 
 cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const float2 *dinv,

@@ -391,7 +391,9 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 // owns a 128 x 64 tile of C~.  Per 16-deep stage of K' the 7 A slices (128
 // rows) and the 7 B slices (64 rows each, stacked to 448 rows) are copied by
 // cp.async into shared memory in the K-major core-matrix layout (8 rows x 16
-// bytes per core matrix, no swizzle), four stages deep, and one thread issues
+// bytes per core matrix, no swizzle), two stages ahead in a ring of four (so
+// that the MMAs of the previous stage still run while a slot is refilled),
+// and one thread issues
 // 19 tcgen05.mma per stage (M = 128, N = 64..256, bf16 -> FP32 in tensor
 // memory): the slice pairs of one A slice whose groups t = p + q <= 4 are
 // one MMA over the consecutive B slices (their accumulators are consecutive
@@ -412,6 +414,7 @@ constexpr int OZT_A_SLICE = OZT_BM * OZT_KC * 2;           // bytes of one A sli
 constexpr int OZT_B_SLICE = OZT_BN * OZT_KC * 2;           // bytes of one B slice per stage
 constexpr int OZT_STAGE = OZ_S * (OZT_A_SLICE + OZT_B_SLICE);
 constexpr int OZT_NST = 4;
+constexpr int OZT_DIST = OZT_NST - 2;  // stages loaded ahead: a refilled slot was read two stages ago
 constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;  // + mbarriers, TMEM address
 constexpr uint32_t OZT_LBO = 128;                 // next core matrix along K
 constexpr uint32_t OZT_SBO = (OZT_KC / 8) * 128;  // next 8-row group
@@ -507,7 +510,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
         }
     };
 #pragma unroll
-    for (int st = 0; st < OZT_NST - 1; ++st) {
+    for (int st = 0; st < OZT_DIST; ++st) {
         if (st < nk) load_stage(st, kbeg + st * OZT_KC);
         cp_async_commit();
     }
@@ -526,15 +529,16 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     int folds = 0;
     for (int it = 0; it < nk; ++it) {
         const int slot = it % OZT_NST;
-        const int nx = it + OZT_NST - 1;
+        const int nx = it + OZT_DIST;
         if (nx < nk) {
-            // slot nx % NST was last read by the MMAs of stage nx - NST = it - 1
+            // slot nx % NST was last read by the MMAs of stage nx - NST = it - 2, which
+            // ran while stage it - 1 was issued: the MMAs of it - 1 stay in flight
             if (nx >= OZT_NST)
                 ok = mbar_wait(mb_stage + 8 * (nx % OZT_NST), ((nx / OZT_NST) - 1) & 1) && ok;
             load_stage(nx % OZT_NST, kbeg + nx * OZT_KC);
         }
         cp_async_commit();
-        cp_async_wait<OZT_NST - 1>();
+        cp_async_wait<OZT_DIST>();
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         const bool fold = ((it + 1) % OZT_FOLD) == 0 || it == nk - 1;
