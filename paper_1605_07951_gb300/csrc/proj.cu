@@ -690,7 +690,11 @@ static cudaError_t jacobi_eig(ProjWs &ws, int k, cudaStream_t s, int64_t *counte
     const double tol2 = 1e-30;  // off(H) <= 1e-15 ||diag(H)||
     const int64_t work = (int64_t)(k + 1) / 2 * ((k + 1) / 2) + (int64_t)k * ((k + 1) / 2);
     const size_t smem = sizeof(Rot) * (size_t)((k + 1) / 2);
-    e = launch_coop_smem(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, 4096), smem,
+    // at most one CTA per SM: the round's work is FP64-bound per SM either way,
+    // and fewer arrivals make the grid barrier after every round cheaper
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = launch_coop_smem(jacobi_persistent_kernel, (int)std::min<int64_t>((work + 255) / 256, nsm), smem,
                          s, ws.H, ws.H2, ws.Y, k, max_sweeps, tol2, ws.jacc, ws.state + 1, ws.bar);
     if (e != cudaSuccess) return e;
     sort_desc_kernel<<<1, 256, 0, s>>>(ws.H, k, ws.order, ws.evals);
