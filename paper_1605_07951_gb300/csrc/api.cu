@@ -752,6 +752,12 @@ rsrr_status Handle::allocate_dense() {
     CK(alloc(&d_done, N), "alloc");
     CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
     CK(alloc(&d_T64, nn2 * N), "alloc dense matrices (complex128)");
+    // the FP64 residuals U - T X (n x n times n x L per point) are FP64-accurate
+    // tensor-core products when the GEMM method allows them
+    if (dense_residual_sliced()) {
+        dws_bytes = ozaki_workspace_bytes((int)n, L, (int)n, false);
+        CK(raw_alloc(&d_dws, dws_bytes), "alloc residual product work space");
+    }
     if (mixed) {
         CK(alloc(&d_A32, nn2 * N), "alloc dense factors (complex64)");
         CK(alloc(&d_D, nL * N), "alloc correction");
@@ -776,6 +782,14 @@ rsrr_status Handle::allocate_dense() {
     return RSRR_OK;
 }
 
+// whether the residual products of the dense path use the sliced tensor-core
+// GEMM: by the GEMM method, AUTO for products of at least 2^30 flops
+bool Handle::dense_residual_sliced() const {
+    const double flops = 8.0 * (double)n * (double)L * (double)n;
+    return opts.gemm == RSRR_GEMM_OZAKI || opts.gemm == RSRR_GEMM_OZAKI_MMA ||
+           (opts.gemm == RSRR_GEMM_AUTO && flops >= 1073741824.0);
+}
+
 // R = U - T X in FP64 (stored complex128 T) and the column maxima of |R|, |X|,
 // for every point, or (skip_done) only for points whose done flag is 0 (the
 // flags are read on the host first).
@@ -790,8 +804,13 @@ rsrr_status Handle::dense_residual(bool skip_done, cudaStream_t s) {
     for (int pt = 0; pt < N; ++pt) {
         if (done[pt]) continue;
         CK(cudaMemcpyAsync(d_R + pt * per, d_U, sizeof(double2) * per, cudaMemcpyDeviceToDevice, s), "R = U");
-        CK(fp64_gemm((int)n, L, (int)n, false, d_T64 + pt * nn2, n, d_X + pt * per, n, d_R + pt * per, n,
-                     -1.0, 1.0, s), "R -= T X");
+        if (dense_residual_sliced())
+            CK(ozaki_zgemm((int)n, L, (int)n, false, d_T64 + pt * nn2, n, d_X + pt * per, n, d_R + pt * per, n,
+                           -1.0, 1.0, false, d_dws, dws_bytes, s, &launches, nullptr, nullptr,
+                           opts.gemm == RSRR_GEMM_OZAKI_MMA), "R -= T X");
+        else
+            CK(fp64_gemm((int)n, L, (int)n, false, d_T64 + pt * nn2, n, d_X + pt * per, n, d_R + pt * per, n,
+                         -1.0, 1.0, s), "R -= T X");
         CK(launch_dense_colmax(d_R + pt * per, d_X + pt * per, (int)n, L, d_rmax + pt * L, d_xmax + pt * L, s),
            "colmax");
         launches += 2;

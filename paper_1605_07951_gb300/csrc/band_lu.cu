@@ -290,7 +290,7 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
         }
         __syncthreads();
         // (3) A22 -= L21 U12, rows j0+jb.., written at their (permuted) positions
-#pragma unroll 4
+#pragma unroll 1
         for (int q = 0; q < NB; ++q) {
             C uq[CB];
 #pragma unroll

@@ -391,20 +391,22 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 // owns a 128 x 64 tile of C~.  Per 16-deep stage of K' the 7 A slices (128
 // rows) and the 7 B slices (64 rows each, stacked to 448 rows) are copied by
 // cp.async into shared memory in the K-major core-matrix layout (8 rows x 16
-// bytes per core matrix, no swizzle), two stages ahead in a ring of four (so
-// that the MMAs of the previous stage still run while a slot is refilled),
-// and one thread issues
-// 19 tcgen05.mma per stage (M = 128, N = 64..256, bf16 -> FP32 in tensor
-// memory): the slice pairs of one A slice whose groups t = p + q <= 4 are
-// one MMA over the consecutive B slices (their accumulators are consecutive
-// 64-column regions of tensor memory); the pairs with t >= 5 go to a sixth
-// region, which is inexact by design (relative weight <= 2^-40) and simply
-// keeps accumulating.  Groups t <= 4 hold at most (t+1) 2^14 per K' element,
-// so every 192 of K' (and at the end) all threads wait for the MMAs
-// (tcgen05.commit -> mbarrier), read their part of regions 0..4 (tcgen05.ld;
-// warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows, columns 32 (w / 4)
-// .. +31), and fold them into 64-bit integers; the next MMAs restart those
-// regions.  Every mbarrier wait is bounded; a wait that runs out counts in
+// bytes per core matrix, no swizzle) by four copy warps, in a ring of four
+// stages: a stage's copies are signalled complete (mbarrier, 128 arrivals)
+// two stages after they were issued, and a slot is refilled once the MMAs
+// that read it have committed.  One thread issues
+// 10 tcgen05.mma per stage (M = 128, N = 64..256, bf16 -> FP32 in tensor
+// memory): every group t = p + q has its own 64-column region of tensor
+// memory (7 regions, 448 of the 512 columns), so the pairs of one A slice
+// (q = 0 .. 6 - p) are MMAs over consecutive B slices into consecutive
+// regions, four slices (N = 256) at a time; the issuing thread never waits
+// at a CTA-wide barrier except for the folds.  Groups t <= 4 hold at most
+// (t+1) 2^14 per K' element, so every 192 of K' (and at the end) all threads
+// wait for the MMAs (tcgen05.commit -> mbarrier), read their part of the
+// regions (tcgen05.ld; warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows,
+// columns 32 (w / 4) .. +31), fold groups 0..4 into 64-bit integers and add
+// groups 5..6 (relative weight <= 2^-40, rounded by design) into an FP32 sum;
+// the next MMAs restart every region.  Every mbarrier wait is bounded; a wait that runs out counts in
 // g_ozt_timeouts and the kernel finishes without hanging.
 constexpr int OZT_BM = 128;
 constexpr int OZT_BN = 64;
@@ -415,12 +417,13 @@ constexpr int OZT_B_SLICE = OZT_BN * OZT_KC * 2;           // bytes of one B sli
 constexpr int OZT_STAGE = OZ_S * (OZT_A_SLICE + OZT_B_SLICE);
 constexpr int OZT_NST = 4;
 constexpr int OZT_DIST = OZT_NST - 2;  // stages loaded ahead: a refilled slot was read two stages ago
-constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;  // + mbarriers, TMEM address
+constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;  // + 2 NST + 1 mbarriers, TMEM address
 constexpr uint32_t OZT_LBO = 128;                 // next core matrix along K
 constexpr uint32_t OZT_SBO = (OZT_KC / 8) * 128;  // next 8-row group
 constexpr int OZT_FOLD = 12;                      // stages per exact fold (K' = 192)
-constexpr long long OZT_WAIT_LIMIT = 1LL << 26;
+constexpr long long OZT_WAIT_LIMIT = 1LL << 22;
 static_assert((4 + 1) * OZT_FOLD * OZT_KC * 16384 < (1 << 24), "group sums must stay exact in FP32");
+static_assert(OZ_S * OZT_BN <= 512, "one tensor-memory region per group");
 
 __device__ unsigned int g_ozt_timeouts;
 
@@ -470,19 +473,27 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     if (upper_only && OZT_BM * bm > OZT_BN * (bn % halfN_tiles) + OZT_BN - 1) return;
     extern __shared__ __align__(1024) unsigned char ozt_smem[];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(ozt_smem);
-    const uint32_t mb_stage = sbase + OZT_NST * OZT_STAGE;  // OZT_NST mbarriers
-    const uint32_t mb_fold = mb_stage + 8 * OZT_NST;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + 8 * OZT_NST + 16);
+    const uint32_t mb_full = sbase + OZT_NST * OZT_STAGE;  // OZT_NST: stage copied (128 arrivals)
+    const uint32_t mb_empty = mb_full + 8 * OZT_NST;       // OZT_NST: stage's MMAs done
+    const uint32_t mb_fold = mb_empty + 8 * OZT_NST;       // all MMAs so far done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = bm * OZT_BM, n0 = bn * OZT_BN;
     const int kbeg = sp * kchunk;
     const int kend = min(Kp, kbeg + kchunk);
     const int nk = kend > kbeg ? (kend - kbeg) / OZT_KC : 0;
     const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
+    // roles: warps 4..7 copy the stages, warp 0 lane 0 issues the MMAs, all
+    // eight warps fold (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..)
+    const bool producer = warp >= 4;
+    const int ptid = tid - 4 * 32;
 
     if (tid == 0) {
-        for (int q = 0; q <= OZT_NST; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_stage + 8 * q));
+        for (int q = 0; q < OZT_NST; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb_full + 8 * q), "r"(OZT_THREADS / 2));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_empty + 8 * q));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_fold));
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n"
@@ -492,7 +503,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     // rows of one stage: 7 x 128 A rows, then 7 x 64 B rows; 2 copies of 16 B each
     auto load_stage = [&](int slot, int k0) {
         const uint32_t dst0 = sbase + (uint32_t)(slot * OZT_STAGE);
-        for (int q = tid; q < OZ_S * (OZT_BM + OZT_BN) * 2; q += OZT_THREADS) {
+        for (int q = ptid; q < OZ_S * (OZT_BM + OZT_BN) * 2; q += OZT_THREADS / 2) {
             const int c = q & 1, row = q >> 1;
             const __nv_bfloat16 *src;
             uint32_t dst;
@@ -509,92 +520,90 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
             cp_async16(dst, src);
         }
     };
-#pragma unroll
-    for (int st = 0; st < OZT_DIST; ++st) {
-        if (st < nk) load_stage(st, kbeg + st * OZT_KC);
-        cp_async_commit();
-    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tslot;
-    // this thread's part of the tile: row 32 (w % 4) + lane, columns 32 (w / 4) ..
     const int lrow = 32 * (warp & 3) + lane, lcol = 32 * (warp >> 2);
     const uint32_t tpart = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)lcol;
 
     long long acc[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0;
-    bool ok = true;
-    int folds = 0;
-    for (int it = 0; it < nk; ++it) {
-        const int slot = it % OZT_NST;
-        const int nx = it + OZT_DIST;
-        if (nx < nk) {
-            // slot nx % NST was last read by the MMAs of stage nx - NST = it - 2, which
-            // ran while stage it - 1 was issued: the MMAs of it - 1 stay in flight
-            if (nx >= OZT_NST)
-                ok = mbar_wait(mb_stage + 8 * (nx % OZT_NST), ((nx / OZT_NST) - 1) & 1) && ok;
-            load_stage(nx % OZT_NST, kbeg + nx * OZT_KC);
-        }
-        cp_async_commit();
-        cp_async_wait<OZT_DIST>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        const bool fold = ((it + 1) % OZT_FOLD) == 0 || it == nk - 1;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
-            const uint32_t b0 = a0 + OZ_S * OZT_A_SLICE;
-            const uint32_t keep = (it % OZT_FOLD) == 0 ? 0u : 1u;  // regions 0..4 restart after a fold
-            const uint32_t keep5 = it == 0 ? 0u : 1u;                // region 5 starts once
-#pragma unroll
-            for (int p = 0; p < OZ_S; ++p) {
-                const uint64_t ad = umma_desc(a0 + p * OZT_A_SLICE);
-                // groups p .. 4: one MMA over B slices 0 .. 4 - p (at most 4 at a time)
-                for (int q0 = 0; q0 <= 4 - p; q0 += 4) {
-                    const int nq = min(4, 5 - p - q0);
-                    umma_bf16(tmem + (uint32_t)((p + q0) * OZT_BN), ad, umma_desc(b0 + q0 * OZT_B_SLICE),
-                              umma_idesc(nq * OZT_BN), p == 0 ? keep : 1u);
-                }
-                // groups 5 and 6 share the sixth region
-                for (int q = max(0, 5 - p); q <= OZ_S - 1 - p; ++q)
-                    umma_bf16(tmem + 5 * OZT_BN, ad, umma_desc(b0 + q * OZT_B_SLICE), umma_idesc(OZT_BN),
-                              (p == 0 && q == 5) ? keep5 : 1u);
-            }
-            umma_commit(mb_stage + 8 * slot);
-            if (fold) umma_commit(mb_fold);
-        }
-        if (fold) {
-            ok = mbar_wait(mb_fold, folds & 1) && ok;
-            ++folds;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-#pragma unroll
-            for (int t = 0; t < 5; ++t) {
-#pragma unroll
-                for (int c0 = 0; c0 < 32; c0 += 16) {
-                    uint32_t r[16];
-                    tmem_ld16(tpart + (uint32_t)(t * OZT_BN + c0), r);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[c0 + j] += scaled_group_to_ll(__uint_as_float(r[j]));
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncthreads();
-        }
-    }
-    cp_async_wait<0>();
     float low[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) low[c] = 0.f;
-    if (nk > 0) {
+    for (int c = 0; c < 32; ++c) {
+        acc[c] = 0;
+        low[c] = 0.f;
+    }
+    bool ok = true;
+    int folds = 0;
+    auto is_fold = [&](int st) { return ((st + 1) % OZT_FOLD) == 0 || st == nk - 1; };
+    // every warp, after the MMAs of a fold stage: regions 0..4 into the integers
+    auto fold_part = [&]() {
+        ok = mbar_wait(mb_fold, folds & 1) && ok;
+        ++folds;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tpart + (uint32_t)(5 * OZT_BN + c0), r);
+        for (int t = 0; t < OZ_S; ++t) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) low[c0 + j] = __uint_as_float(r[j]);
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tpart + (uint32_t)(t * OZT_BN + c0), r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (t < 5) acc[c0 + j] += scaled_group_to_ll(__uint_as_float(r[j]));
+                    else low[c0 + j] += __uint_as_float(r[j]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        asm volatile("bar.sync 1, %0;\n" ::"n"(OZT_THREADS) : "memory");  // regions free again
+    };
+    if (producer) {
+        // copies run OZT_DIST stages ahead of the signal that a stage is complete
+        for (int st = 0; st < nk + OZT_DIST; ++st) {
+            if (st < nk) {
+                // slot st % NST was last read by the MMAs of stage st - NST
+                if (st >= OZT_NST)
+                    ok = mbar_wait(mb_empty + 8 * (st % OZT_NST), ((st / OZT_NST) - 1) & 1) && ok;
+                load_stage(st % OZT_NST, kbeg + st * OZT_KC);
+            }
+            cp_async_commit();
+            const int done = st - OZT_DIST;
+            if (done >= 0) {
+                cp_async_wait<OZT_DIST>();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mb_full + 8 * (done % OZT_NST))
+                             : "memory");
+                if (is_fold(done)) fold_part();
+            }
+        }
+        cp_async_wait<0>();
+    } else {
+        for (int it = 0; it < nk; ++it) {
+            if (tid == 0) {
+                const int slot = it % OZT_NST;
+                ok = mbar_wait(mb_full + 8 * slot, (it / OZT_NST) & 1) && ok;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
+                const uint32_t b0 = a0 + OZ_S * OZT_A_SLICE;
+                const uint32_t keep = (it % OZT_FOLD) == 0 ? 0u : 1u;  // all regions restart after a fold
+#pragma unroll
+                for (int p = 0; p < OZ_S; ++p) {
+                    const uint64_t ad = umma_desc(a0 + p * OZT_A_SLICE);
+                    // groups p .. 6 (q = 0 .. 6 - p): consecutive B slices into
+                    // consecutive regions, at most 4 slices (N = 256) per MMA
+#pragma unroll
+                    for (int q0 = 0; q0 <= OZ_S - 1 - p; q0 += 4) {
+                        const int nq = min(4, OZ_S - p - q0);
+                        umma_bf16(tmem + (uint32_t)((p + q0) * OZT_BN), ad, umma_desc(b0 + q0 * OZT_B_SLICE),
+                                  umma_idesc(nq * OZT_BN), p == 0 ? keep : 1u);
+                    }
+                }
+                umma_commit(mb_empty + 8 * slot);
+                if (is_fold(it)) umma_commit(mb_fold);
+            }
+            __syncwarp();
+            if (is_fold(it)) fold_part();
         }
     }
     if (!ok && lane == 0) atomicAdd(&g_ozt_timeouts, 1u);

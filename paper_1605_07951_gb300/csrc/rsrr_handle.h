@@ -44,6 +44,8 @@ struct Handle {
     double2 *d_z = nullptr;           // N sampling points
     double2 *d_T64 = nullptr;         // N dense complex128 matrices (residuals)
     float2 *d_A32 = nullptr;          // N dense complex64 factors
+    void *d_dws = nullptr;            // slices of the residual products T X (Ozaki)
+    size_t dws_bytes = 0;
     // device buffers (owned)
     std::vector<void *> allocations;
     size_t device_bytes = 0;
@@ -114,6 +116,7 @@ struct Handle {
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, cudaStream_t s);
     rsrr_status sample_dense(cudaStream_t s);
     rsrr_status dense_residual(bool skip_done, cudaStream_t s);
+    bool dense_residual_sliced() const;
     rsrr_status allocate_dense();
     rsrr_status read_outcome();
     rsrr_status mark(int i, cudaStream_t s);

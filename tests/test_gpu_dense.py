@@ -20,11 +20,15 @@ def rs():
     return rsrr
 
 
-@pytest.mark.parametrize("n,N,L,prec", [(256, 6, 8, "mixed"), (300, 4, 5, "mixed"),
-                                        (70, 3, 3, "mixed"), (256, 4, 8, "fp64")])
-def test_dense_samples_match_oracle(rs, n, N, L, prec):
+# gemm 0: the residual products T X in native FP64 at these sizes; gemm 2:
+# forced onto the FP64-accurate tensor-core slices (the large sizes' default)
+@pytest.mark.parametrize("n,N,L,prec,gemm", [(256, 6, 8, "mixed", 0), (300, 4, 5, "mixed", 0),
+                                             (70, 3, 3, "mixed", 0), (256, 4, 8, "fp64", 0),
+                                             (300, 4, 5, "mixed", 2), (200, 3, 7, "fp64", 2)])
+def test_dense_samples_match_oracle(rs, n, N, L, prec, gemm):
     p = W.helmholtz_sphere(n=n, N=N, L=L)
-    o = rs.default_opts(precision=rs.RSRR_PREC_MIXED if prec == "mixed" else rs.RSRR_PREC_FP64)
+    o = rs.default_opts(precision=rs.RSRR_PREC_MIXED if prec == "mixed" else rs.RSRR_PREC_FP64,
+                        gemm=gemm)
     s = rs.Solver(p, o)
     s.sample()
     assert s.check_status() == rs.RSRR_OK
