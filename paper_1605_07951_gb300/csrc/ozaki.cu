@@ -30,7 +30,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <string>
 
 #include "rsrr.h"
@@ -390,10 +392,10 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 // The same products on the 5th-generation tensor cores: a CTA of 256 threads
 // owns a 128 x 64 tile of C~.  Per 16-deep stage of K' the 7 A slices (128
 // rows) and the 7 B slices (64 rows each, stacked to 448 rows) are copied by
-// cp.async into shared memory in the K-major core-matrix layout (8 rows x 16
-// bytes per core matrix, no swizzle) by four copy warps, in a ring of four
-// stages: a stage's copies are signalled complete (mbarrier, 128 arrivals)
-// two stages after they were issued, and a slot is refilled once the MMAs
+// TMA (28 boxes of 16 bytes x rows, issued by one thread, completion counted
+// in bytes on the stage's mbarrier) into shared memory in the K-major
+// core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle), in a
+// ring of four stages; a slot is refilled once the MMAs
 // that read it have committed.  One thread issues
 // 10 tcgen05.mma per stage (M = 128, N = 64..256, bf16 -> FP32 in tensor
 // memory): every group t = p + q has its own 64-column region of tensor
@@ -416,10 +418,14 @@ constexpr int OZT_A_SLICE = OZT_BM * OZT_KC * 2;           // bytes of one A sli
 constexpr int OZT_B_SLICE = OZT_BN * OZT_KC * 2;           // bytes of one B slice per stage
 constexpr int OZT_STAGE = OZ_S * (OZT_A_SLICE + OZT_B_SLICE);
 constexpr int OZT_NST = 4;
-constexpr int OZT_DIST = OZT_NST - 2;  // stages loaded ahead: a refilled slot was read two stages ago
+constexpr int OZT_DIST = OZT_NST - 2;  // stages the copies run ahead of a fold
 constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;  // + 2 NST + 1 mbarriers, TMEM address
-constexpr uint32_t OZT_LBO = 128;                 // next core matrix along K
-constexpr uint32_t OZT_SBO = (OZT_KC / 8) * 128;  // next 8-row group
+// stage layout, K-major core matrices (8 rows x 16 bytes), no swizzle: per
+// K-column of core matrices (8 of K) all rows of an operand are contiguous,
+// 16 bytes a row, so one TMA box of 16 bytes x rows fills one such column
+constexpr uint32_t OZT_SBO = 128;                          // next 8-row group
+constexpr uint32_t OZT_LBO_A = OZT_BM * 16;                // next core column of an A slice
+constexpr uint32_t OZT_LBO_B = OZ_S * OZT_BN * 16;         // next core column of the stacked B
 constexpr int OZT_FOLD = 12;                      // stages per exact fold (K' = 192)
 constexpr long long OZT_WAIT_LIMIT = 1LL << 22;
 static_assert((4 + 1) * OZT_FOLD * OZT_KC * 16384 < (1 << 24), "group sums must stay exact in FP32");
@@ -427,10 +433,10 @@ static_assert(OZ_S * OZT_BN <= 512, "one tensor-memory region per group");
 
 __device__ unsigned int g_ozt_timeouts;
 
-// shared-memory matrix descriptor: K-major, no swizzle, start / LBO / SBO in
-// 16-byte units, descriptor version 1
-RSRR_DEV uint64_t umma_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((OZT_LBO >> 4) & 0x3FFF) << 16) |
+// shared-memory matrix descriptor: K-major, no swizzle, start / LBO (next core
+// matrix along K) / SBO (next 8-row group) in 16-byte units, version 1
+RSRR_DEV uint64_t umma_desc(uint32_t saddr, uint32_t lbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
            ((uint64_t)((OZT_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 // instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = n
@@ -445,6 +451,14 @@ RSRR_DEV void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
 RSRR_DEV void umma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                  ::"r"(mbar) : "memory");
+}
+// 2-D TMA load of one box into shared memory, completion counted in bytes on mbar
+RSRR_DEV void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+RSRR_DEV void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
 }
 RSRR_DEV bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (long long it = 0; it < OZT_WAIT_LIMIT; ++it) {
@@ -468,12 +482,13 @@ __global__ void __launch_bounds__(OZT_THREADS, 1)
 oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs,
                   const int *__restrict__ Ea, const int *__restrict__ Eb, double *__restrict__ W,
                   double2 *__restrict__ C, int64_t ldc, int M, int N, int Mp, int Np, int Kp, int kchunk,
-                  int halfN_tiles, int upper_only, double alpha, double beta) {
+                  int halfN_tiles, int upper_only, double alpha, double beta,
+                  const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     const int bm = blockIdx.x, bn = blockIdx.y, sp = blockIdx.z;
     if (upper_only && OZT_BM * bm > OZT_BN * (bn % halfN_tiles) + OZT_BN - 1) return;
     extern __shared__ __align__(1024) unsigned char ozt_smem[];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(ozt_smem);
-    const uint32_t mb_full = sbase + OZT_NST * OZT_STAGE;  // OZT_NST: stage copied (128 arrivals)
+    const uint32_t mb_full = sbase + OZT_NST * OZT_STAGE;  // OZT_NST: stage's bytes landed (TMA)
     const uint32_t mb_empty = mb_full + 8 * OZT_NST;       // OZT_NST: stage's MMAs done
     const uint32_t mb_fold = mb_empty + 8 * OZT_NST;       // all MMAs so far done
     uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16);
@@ -482,15 +497,13 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     const int kbeg = sp * kchunk;
     const int kend = min(Kp, kbeg + kchunk);
     const int nk = kend > kbeg ? (kend - kbeg) / OZT_KC : 0;
-    const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
-    // roles: warps 4..7 copy the stages, warp 0 lane 0 issues the MMAs, all
+    // roles: warp 4 lane 0 copies the stages, warp 0 lane 0 issues the MMAs, all
     // eight warps fold (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..)
     const bool producer = warp >= 4;
-    const int ptid = tid - 4 * 32;
 
     if (tid == 0) {
         for (int q = 0; q < OZT_NST; ++q) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb_full + 8 * q), "r"(OZT_THREADS / 2));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_full + 8 * q));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_empty + 8 * q));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_fold));
@@ -500,26 +513,6 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
                      ::"r"((uint32_t)__cvta_generic_to_shared(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    // rows of one stage: 7 x 128 A rows, then 7 x 64 B rows; 2 copies of 16 B each
-    auto load_stage = [&](int slot, int k0) {
-        const uint32_t dst0 = sbase + (uint32_t)(slot * OZT_STAGE);
-        for (int q = ptid; q < OZ_S * (OZT_BM + OZT_BN) * 2; q += OZT_THREADS / 2) {
-            const int c = q & 1, row = q >> 1;
-            const __nv_bfloat16 *src;
-            uint32_t dst;
-            if (row < OZ_S * OZT_BM) {
-                const int p = row / OZT_BM, r = row % OZT_BM;
-                src = As + p * sA + (size_t)(m0 + r) * Kp + k0 + c * 8;
-                dst = dst0 + p * OZT_A_SLICE + (r >> 3) * OZT_SBO + c * OZT_LBO + (r & 7) * 16;
-            } else {
-                const int rb = row - OZ_S * OZT_BM, qs = rb / OZT_BN, r = rb % OZT_BN;
-                src = Bs + qs * sB + (size_t)(n0 + r) * Kp + k0 + c * 8;
-                dst = dst0 + OZ_S * OZT_A_SLICE + qs * OZT_B_SLICE + (r >> 3) * OZT_SBO + c * OZT_LBO +
-                      (r & 7) * 16;
-            }
-            cp_async16(dst, src);
-        }
-    };
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -559,25 +552,36 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
         asm volatile("bar.sync 1, %0;\n" ::"n"(OZT_THREADS) : "memory");  // regions free again
     };
     if (producer) {
-        // copies run OZT_DIST stages ahead of the signal that a stage is complete
+        // one thread issues the stage copies (TMA boxes of 8 K-elements x rows,
+        // each box one column of 8 x 16-byte core matrices), OZT_DIST stages
+        // ahead of the fold that follows a stage
         for (int st = 0; st < nk + OZT_DIST; ++st) {
-            if (st < nk) {
+            if (st < nk && tid == 4 * 32) {
+                const int slot = st % OZT_NST;
                 // slot st % NST was last read by the MMAs of stage st - NST
-                if (st >= OZT_NST)
-                    ok = mbar_wait(mb_empty + 8 * (st % OZT_NST), ((st / OZT_NST) - 1) & 1) && ok;
-                load_stage(st % OZT_NST, kbeg + st * OZT_KC);
+                if (st >= OZT_NST) ok = mbar_wait(mb_empty + 8 * slot, ((st / OZT_NST) - 1) & 1) && ok;
+                const uint32_t full = mb_full + 8 * slot;
+                mbar_expect_tx(full, (uint32_t)OZT_STAGE);
+                const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
+                const uint32_t b0 = a0 + OZ_S * OZT_A_SLICE;
+                const int k = kbeg + st * OZT_KC;
+#pragma unroll
+                for (int p = 0; p < OZ_S; ++p)
+#pragma unroll
+                    for (int kc = 0; kc < 2; ++kc) {
+                        tma_load_2d(a0 + p * OZT_A_SLICE + kc * OZT_LBO_A, &tmA, k + 8 * kc, p * Mp + m0, full);
+                        tma_load_2d(b0 + kc * OZT_LBO_B + p * OZT_BN * 16, &tmB, k + 8 * kc, p * Np + n0, full);
+                    }
             }
-            cp_async_commit();
+            __syncwarp();
             const int done = st - OZT_DIST;
-            if (done >= 0) {
-                cp_async_wait<OZT_DIST>();
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mb_full + 8 * (done % OZT_NST))
-                             : "memory");
-                if (is_fold(done)) fold_part();
-            }
+            if (done >= 0 && is_fold(done)) fold_part();
         }
-        cp_async_wait<0>();
+        // every copy has landed before the CTA leaves (waits bounded)
+        if (tid == 4 * 32)
+            for (int st = max(0, nk - OZT_NST); st < nk; ++st)
+                ok = mbar_wait(mb_full + 8 * (st % OZT_NST), (st / OZT_NST) & 1) && ok;
+        __syncwarp();
     } else {
         for (int it = 0; it < nk; ++it) {
             if (tid == 0) {
@@ -589,13 +593,13 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
                 const uint32_t keep = (it % OZT_FOLD) == 0 ? 0u : 1u;  // all regions restart after a fold
 #pragma unroll
                 for (int p = 0; p < OZ_S; ++p) {
-                    const uint64_t ad = umma_desc(a0 + p * OZT_A_SLICE);
+                    const uint64_t ad = umma_desc(a0 + p * OZT_A_SLICE, OZT_LBO_A);
                     // groups p .. 6 (q = 0 .. 6 - p): consecutive B slices into
                     // consecutive regions, at most 4 slices (N = 256) per MMA
 #pragma unroll
                     for (int q0 = 0; q0 <= OZ_S - 1 - p; q0 += 4) {
                         const int nq = min(4, OZ_S - p - q0);
-                        umma_bf16(tmem + (uint32_t)((p + q0) * OZT_BN), ad, umma_desc(b0 + q0 * OZT_B_SLICE),
+                        umma_bf16(tmem + (uint32_t)((p + q0) * OZT_BN), ad, umma_desc(b0 + q0 * OZT_BN * 16, OZT_LBO_B),
                                   umma_idesc(nq * OZT_BN), p == 0 ? keep : 1u);
                     }
                 }
@@ -767,6 +771,31 @@ double ozaki_tc_flops(int M, int N, int K, bool hermitian, bool legacy) {
     return 2.0 * pairs * tiles * bm * OZ_BN * (double)p.Kp;
 }
 
+// TMA descriptor of a stacked slice array (rows x Kp bf16, row-major, rows =
+// 7 x padded rows): boxes of 8 K-elements (16 bytes) x box_rows rows
+static cudaError_t slice_tensor_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t Kp,
+                                    int64_t rows, int box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (Kp % 8) || rows <= 0) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                         const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
                         double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
@@ -798,6 +827,11 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
     double *Wp = p.splits > 1 ? reinterpret_cast<double *>(w) : nullptr;
     const bool upper = hermitian && (N % OZ_BN) == 0;
     const int halfN_tiles = upper ? N / OZ_BN : (int)(p.Np / OZ_BN);
+    CUtensorMap tmA{}, tmB{};
+    if (!legacy) {
+        if ((e = slice_tensor_map(&tmA, As, p.Kp, OZ_S * p.Mp, OZT_BM)) != cudaSuccess) return e;
+        if ((e = slice_tensor_map(&tmB, Bs, p.Kp, OZ_S * p.Np, OZT_BN)) != cudaSuccess) return e;
+    }
 
     for (int64_t kc0 = 0; kc0 < K; kc0 += p.Kc) {
         const int Kc = (int)std::min<int64_t>(p.Kc, K - kc0);
@@ -837,7 +871,7 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
             oz_gemm_tc_kernel<<<grid, OZT_THREADS, OZT_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N,
                                                                  (int)p.Mp, (int)p.Np, (int)p.Kp,
                                                                  (int)p.kchunk, halfN_tiles,
-                                                                 upper ? 1 : 0, alpha, b);
+                                                                 upper ? 1 : 0, alpha, b, tmA, tmB);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (timer && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
         if (tc_flops) *tc_flops += ozaki_tc_flops(M, N, Kc, upper, legacy);
