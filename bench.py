@@ -80,6 +80,23 @@ print(json.dumps({{"seconds": dt, "columns": int(len(z) * p.L)}}))
 """
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """Step time of the whole job: the slowest rank's (all-reduce MAX; the
+    identity on one rank)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(cols_per_rank, world, ms):
+    """Whole-job throughput of `world` replicas, each sampling `cols_per_rank`
+    resolvent columns per step of `ms` milliseconds (the max over ranks)."""
+    return cols_per_rank * world / (ms / 1e3)
+
+
 def oracle_sample(g, npts):
     """Time the oracle's resolvent samples (LAPACK banded solves) on `npts`
     points of the workload in a 1-thread subprocess (BLAS pinned to 1 thread)."""
@@ -168,7 +185,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_e2e(a, s, p, stats, stream, world):
+def run_e2e(a, s, p, stats, stream, world, dist=None):
     """Same metric through the C ABI with host buffers: U copied from pinned
     host memory and the projected matrices copied back, every step."""
     import ctypes as C
@@ -191,12 +208,14 @@ def run_e2e(a, s, p, stats, stream, world):
         assert st == 0 and kk == k
     e2e_step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(a.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / a.steps
-    e2e = {"value": cols * world / e2e_s, "unit": UNIT,
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / a.steps * 1e3, dist, "cuda")
+    e2e = {"value": replica_value(cols, world, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(Uh.numel() * 16),
            "d2h_bytes_per_step": int(p.m * k * k * 16)}
 
@@ -310,21 +329,17 @@ def run_ours(a, rank, world, local):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dist, "cuda")
     stats = s.stats()
     assert stats["converged"] == 1 and stats["max_eta"] <= 1e-10, stats
     launches = (stats["launches"] - launches0)
     cols = p.N * p.L
-    value = cols * world / (ms / 1e3)
+    value = replica_value(cols, world, ms)
 
     # e2e: U from pinned host memory, projected matrices back to the host, per step
     e2e = None
     if not a.no_e2e:
-        e2e = run_e2e(a, s, p, stats, stream, world)
+        e2e = run_e2e(a, s, p, stats, stream, world, dist)
     fp64 = None
     # rooflines of the two kernels that dominate a step, from the library's
     # own CUDA events on the launching stream (opts.timing): the bf16 slice
