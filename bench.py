@@ -306,6 +306,7 @@ def run_ours(a, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     lu_ms, sample_ms, project_ms, gemm_ms, gemm_flops, tc_ms, tc_flops = [], [], [], [], [], [], []
+    asm_ms = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -317,6 +318,7 @@ def run_ours(a, rank, world, local):
         # the library's own events on the same stream give the stage times
         torch.cuda.synchronize()
         sti = s.stats()
+        asm_ms.append(sti["stage_ms"][0])
         lu_ms.append(sti["stage_ms"][1])
         sample_ms.append(sum(sti["stage_ms"][:5]))
         project_ms.append(sti["stage_ms"][5])
@@ -374,6 +376,16 @@ def run_ours(a, rank, world, local):
                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; traffic "
                             "scaled from an ncu capture at n=4096 by stored band entries"}
     roof, roof_other = (roof_lu, roof_tc) if lu_avg >= tc_avg else (roof_tc, roof_lu)
+    # band assembly: the complex64 band storage of every point written once
+    asm_bytes = 8.0 * ldab * n * p.N
+    asm_avg = statistics.mean(asm_ms)
+    asm_gbs = asm_bytes / (asm_avg / 1e3) / 1e9
+    roof_asm = {"bound": "hbm", "kernel": "assemble_band_kernel<float2> (one warp per band column)",
+                "achieved": asm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": asm_gbs / peaks["hbm_gbs"], "traffic": None,
+                "algorithmic_bytes_per_launch": asm_bytes, "avg_stage_ms": asm_avg,
+                "peak_note": f"copy bandwidth, {peaks['source']}; time = the assembly stage "
+                             "(the ||T(z_j)|| kernel + the assembly), so the fraction is a lower bound"}
 
     if not a.no_fp64:
         s64 = rsrr.Solver(p, rsrr.default_opts(precision=rsrr.RSRR_PREC_FP64, timing=1))
@@ -406,7 +418,8 @@ def run_ours(a, rank, world, local):
         "project_ms": statistics.mean(project_ms), "rank_k": stats["k"],
         "pivoted_cholesky_kc": stats["kc"],
         "fp64_plain_path": fp64,
-        "roofline": roof, "roofline_second": roof_other, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roof, "roofline_second": roof_other, "roofline_assembly": roof_asm,
+        "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
     }
     s.close()

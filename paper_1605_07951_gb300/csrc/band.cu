@@ -24,10 +24,13 @@ RSRR_DEV void store_c(float2 *p, double2 v) { *p = to_c64(v); }
 RSRR_DEV void store_c(double2 *p, double2 v) { *p = v; }
 
 // --------------------------------------------------------------------------
-// Assembly: one thread per stored band entry (column c, band row t) of one
-// point.  The value is sum_q coef[pt][q] * vals[q][e] for the pattern entry
-// e = (i, c), found by binary search in column c of a CSC copy of the
-// pattern; every other stored entry (fill rows, zeros) is written as zero.
+// Assembly: one warp per column c of one point.  The warp first writes the
+// whole stored column (ldab entries, fill rows and zeros) as zero with
+// coalesced stores, then, after a warp barrier that orders the two passes,
+// writes each pattern entry e = (i, c) of the column (a CSC copy of the
+// pattern) at band row KV + i - c as sum_q coef[pt][q] * vals[q][e].  The
+// second pass touches lines the first just wrote, so DRAM sees one write
+// stream of the band storage.
 // --------------------------------------------------------------------------
 template <typename C>
 __global__ void assemble_band_kernel(C *__restrict__ ab_all, const double2 *__restrict__ coef,
@@ -37,35 +40,29 @@ __global__ void assemble_band_kernel(C *__restrict__ ab_all, const double2 *__re
                                      const double *__restrict__ vals, int64_t nnz, int m, int n,
                                      int kl, int ku, int ldab) {
     const int pt = blockIdx.y;
-    const int64_t total = (int64_t)ldab * n;
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
     const int KV = kl + ku;
-    C *ab = ab_all + (size_t)pt * total;
+    C *ab = ab_all + (size_t)pt * ldab * n;
     __shared__ double2 s_coef[RSRR_MAX_TERMS_DEV];
     if (threadIdx.x < m) s_coef[threadIdx.x] = coef[pt * m + threadIdx.x];
     __syncthreads();
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(idx / ldab);
-        const int t = (int)(idx - (int64_t)c * ldab);
-        const int i = c + t - KV;
-        double2 v = make_double2(0.0, 0.0);
-        if (i >= 0 && i < n && i - c <= kl && c - i <= ku) {
-            int lo = csc_ptr[c], hi = csc_ptr[c + 1];
-            const int end = hi;
-            while (lo < hi) {  // first entry of column c with row >= i
-                const int mid = (lo + hi) >> 1;
-                if (csc_row[mid] < i) lo = mid + 1; else hi = mid;
+    for (int c = blockIdx.x * warps + (threadIdx.x >> 5); c < n; c += gridDim.x * warps) {
+        C *col = ab + (size_t)c * ldab;
+        for (int t = lane; t < ldab; t += 32) store_c(col + t, make_double2(0.0, 0.0));
+        __syncwarp();
+        for (int k = csc_ptr[c] + lane; k < csc_ptr[c + 1]; k += 32) {
+            const int i = csc_row[k];
+            if (i - c > kl || c - i > ku) continue;
+            const int64_t e = csc_perm[k];
+            double2 v = make_double2(0.0, 0.0);
+            for (int q = 0; q < m; ++q) {
+                const double a = vals[(int64_t)q * nnz + e];
+                v.x = fma(s_coef[q].x, a, v.x);
+                v.y = fma(s_coef[q].y, a, v.y);
             }
-            if (lo < end && csc_row[lo] == i) {
-                const int64_t e = csc_perm[lo];
-                for (int q = 0; q < m; ++q) {
-                    const double a = vals[(int64_t)q * nnz + e];
-                    v.x = fma(s_coef[q].x, a, v.x);
-                    v.y = fma(s_coef[q].y, a, v.y);
-                }
-            }
+            store_c(col + (KV + i - c), v);
         }
-        store_c(ab + idx, v);
     }
 }
 
@@ -445,8 +442,8 @@ static int grid_for(int64_t work, int threads, int cap = 152 * 16) {
 
 template <typename C>
 cudaError_t launch_assemble(C *ab, const BandGeom &g, const DevProblem &p, cudaStream_t s) {
-    const int64_t total = (int64_t)g.ldab * p.n;
-    dim3 grid(grid_for(total, 256, 4096), p.N);
+    // 8 columns per block of 256 threads
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((p.n + 7) / 8, 2048)), p.N);
     assemble_band_kernel<C><<<grid, 256, 0, s>>>(ab, p.coef, p.csc_ptr, p.csc_row, p.csc_perm,
                                                  p.vals, p.nnz, p.m, (int)p.n, g.kl, g.ku, g.ldab);
     return cudaGetLastError();
