@@ -19,6 +19,11 @@ Parity status per function:
                                        companion linearisation, Lambert W, the
                                        loaded-string example of Section 4.2)
   rsrr ............................... pinned (as above)
+  assemble_dense, taylor_coefficients,
+  resolvent_samples_dense, rsrr_dense  pinned (two-point problem with closed-form
+                                       eigenvalues k pi / r + i im and eigenvectors;
+                                       Taylor series against the kernel matrix;
+                                       argument-principle counts)
 """
 from __future__ import annotations
 

@@ -257,3 +257,78 @@ def test_dense_eigenvalue_drifts_towards_pi():
         assert len(lam) == 1
         d.append(abs(lam[0] - np.pi))
     assert d[1] < d[0]
+
+
+# -------------------------------------------- dense kernel: two-point closed form
+def _pair_problem(r=1.0, im=0.5):
+    """Two points at distance r, diagonal d = e^{-im r} / (4 pi r).  Then
+    det T(z) = d^2 - (e^{i z r} / (4 pi r))^2 vanishes exactly where
+    e^{i z r} = +-e^{-im r}, i.e. at z = k pi / r + i im for every integer k,
+    with eigenvectors (1, -+1)."""
+    P = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    reg = W.Region(complex(3.0, im), 3.5, 3.5)
+    U = np.asfortranarray(W.probe(2, 2, 7))
+    p = W.DenseProblem("pair", 2, P, np.exp(-im * r) / (4.0 * np.pi * r), reg, 16, 2, U)
+    ks = np.arange(-8, 9)
+    ref = ks * np.pi / r + 1j * im
+    return p, ref[oracle.inside(reg, ref)]
+
+
+def _pair_ok(p, ref):
+    out = oracle.rsrr_dense(p, NQ=256)
+    if len(out["lam"]) != len(ref) or match_eigs(ref, out["lam"]) > 1e-9:
+        return False, out
+    return True, out
+
+
+def test_dense_two_point_problem_matches_its_closed_form():
+    p, ref = _pair_problem()
+    assert len(ref) == 3  # k = 0, 1, 2 inside |z - (3 + 0.5i)| < 3.5
+    ok, out = _pair_ok(p, ref)
+    assert ok, out["lam"]
+    assert out["res"].max() <= 1e-12
+    for j, lam in enumerate(out["lam"]):
+        v = out["V"][:, j]
+        sign = 1.0 if round(lam.real / np.pi) % 2 == 0 else -1.0  # e^{i z r} = +-d 4 pi r
+        assert abs(v[1] / v[0] + sign) <= 1e-10
+
+
+def _planted_dense(monkeypatch, which):
+    base_asm, base_tay = ORACLE_MOD.assemble_dense, ORACLE_MOD.taylor_coefficients
+    if which == "diagonal_doubled":
+        def tay(prob, R=None, P=None):
+            A = base_tay(prob, R, P)
+            A[0] = A[0] + np.diag(np.full(prob.n, prob.diag))
+            return A
+        monkeypatch.setattr(ORACLE_MOD, "taylor_coefficients", tay)
+    elif which == "exponent_sign":
+        monkeypatch.setattr(ORACLE_MOD, "taylor_coefficients",
+                            lambda prob, R=None, P=None: [
+                                np.where(np.eye(prob.n, dtype=bool), A, A.conj() * (-1) ** q)
+                                for q, A in enumerate(base_tay(prob, R, P))])
+    elif which == "dropped_4pi":
+        def asm(prob, z, R=None):
+            T = base_asm(prob, z, R)
+            off = ~np.eye(prob.n, dtype=bool)
+            T[off] *= 4.0 * np.pi
+            return T
+
+        def tay(prob, R=None, P=None):
+            A = base_tay(prob, R, P)
+            off = ~np.eye(prob.n, dtype=bool)
+            for Aq in A:
+                Aq[off] *= 4.0 * np.pi
+            return A
+        monkeypatch.setattr(ORACLE_MOD, "assemble_dense", asm)
+        monkeypatch.setattr(ORACLE_MOD, "taylor_coefficients", tay)
+
+
+@pytest.mark.parametrize("which", ["diagonal_doubled", "exponent_sign", "dropped_4pi"])
+def test_planted_dense_mistakes_fail_the_two_point_pin(monkeypatch, which):
+    p, ref = _pair_problem()
+    _planted_dense(monkeypatch, which)
+    try:
+        ok, _ = _pair_ok(p, ref)
+    except Exception:
+        ok = False
+    assert not ok, f"planted mistake {which!r} went unnoticed"
