@@ -26,6 +26,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "admission.h"
 #include "rsrr.h"
 #include "rsrr_handle.h"
 
@@ -70,26 +71,24 @@ struct Server {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
 
-    // first queued request that fits, honouring the bypass limit; reserves
-    // its bytes and removes it from the queue (mu held)
+    // the request admit_index picks; the requests it passed over count one
+    // more bypass; reserves its bytes and removes it from the queue (mu held)
     Request *pick_locked() {
-        if (active >= o.slots) return nullptr;
-        for (size_t q = 0; q < queue.size(); ++q) {
-            Request *r = queue[q];
-            if (used + r->bytes <= (size_t)o.mem_budget_bytes) {
-                for (size_t e = 0; e < q; ++e) queue[e]->bypassed++;
-                queue.erase(queue.begin() + q);
-                used += r->bytes;
-                peak_used = std::max(peak_used, used);
-                active++;
-                peak_active = std::max(peak_active, active);
-                r->holds_budget = true;
-                r->t_admit = now();
-                return r;
-            }
-            if (r->bypassed >= kMaxBypass) return nullptr;  // it goes next
-        }
-        return nullptr;
+        const int q = admit_index(
+            (int)queue.size(), [this](int i) { return queue[i]->bytes; },
+            [this](int i) { return queue[i]->bypassed; }, used, (size_t)o.mem_budget_bytes, active, o.slots,
+            kMaxBypass);
+        if (q < 0) return nullptr;
+        Request *r = queue[q];
+        for (int e = 0; e < q; ++e) queue[e]->bypassed++;
+        queue.erase(queue.begin() + q);
+        used += r->bytes;
+        peak_used = std::max(peak_used, used);
+        active++;
+        peak_active = std::max(peak_active, active);
+        r->holds_budget = true;
+        r->t_admit = now();
+        return r;
     }
 
     void run(Request *r, cudaStream_t s) {
