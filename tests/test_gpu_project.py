@@ -47,6 +47,8 @@ FAMILIES = [
     ("diag_delay", lambda: W.diag_delay(), 256, 2),
     ("quadratic_c0b", lambda: W.config("c0b"), 500, 2),
     ("grid_g30", lambda: W.rational_grid(g=30, N=64, L=8), 500, 2),
+    ("diag_sqrt", lambda: W.diag_sqrt(), 256, 2),
+    ("diag_inv", lambda: W.diag_inv(), 256, 2),
 ]
 
 

@@ -37,6 +37,21 @@ def exact_roots(p):
         tau = p.fns[2].param
         r = np.concatenate([a + lambertw(b * tau * np.exp(-a * tau), br) / tau
                             for br in range(-8, 9)])
+    elif p.name == "diag_sqrt":             # k - z m + e sqrt(z^2 - kappa^2)
+        k, m, e = d
+        kap = p.fns[2].param
+        # squaring gives (m^2 - e^2) z^2 - 2 m k z + k^2 + e^2 kappa^2 = 0; of its two
+        # real roots only (m k + e sqrt(k^2 - kappa^2 (m^2 - e^2))) / (m^2 - e^2) has
+        # z m - k > 0, the sign the principal square root requires
+        r = (m * k + e * np.sqrt(k * k - kap * kap * (m * m - e * e))) / (m * m - e * e)
+        r = r.astype(complex)
+    elif p.name == "diag_inv":              # k - z m + e / (sigma - z)
+        k, m, e = d
+        s = p.fns[2].param
+        # (k - z m)(sigma - z) + e = 0:  m z^2 - (k + m sigma) z + k sigma + e = 0
+        B = k + m * s
+        disc = np.sqrt((B * B - 4 * m * (k * s + e)).astype(complex))
+        r = np.concatenate([(B + disc) / (2 * m), (B - disc) / (2 * m)])
     else:
         raise KeyError(p.name)
     return r[oracle.inside(p.region, r)]
@@ -66,7 +81,8 @@ def test_points_lie_on_ellipse_and_weights_integrate_cauchy():
 
 
 # ------------------------------------------------------------ resolvent (step 2)
-@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational", "diag_delay"])
+@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational", "diag_delay", "diag_sqrt",
+                                  "diag_inv"])
 def test_resolvent_matches_decoupled_closed_form(name):
     p = _family(name)
     G1 = W.givens_layers(p.n, p.meta["layers"], p.meta["g_seed"])
@@ -87,7 +103,8 @@ def test_resolvent_backward_error_is_fp64_level():
 
 
 # --------------------------------------------------- eigenvalues (steps 3..5)
-@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational", "diag_delay"])
+@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational", "diag_delay", "diag_sqrt",
+                                  "diag_inv"])
 def test_rsrr_finds_closed_form_eigenvalues(name):
     p = _family(name)
     ref, out, err = check_family(p)

@@ -306,6 +306,34 @@ def diag_delay(n: int = 200, seed: int = 31, N: int = 48, L: int = 4,
                            layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_delay")
 
 
+def diag_sqrt(n: int = 240, seed: int = 51, N: int = 32, L: int = 4, kappa: float = 1.0,
+              layers: int = 3) -> Problem:
+    """Decoupled k_r - z m_r + e_r sqrt(z^2 - kappa^2) (principal branch; the
+    square-root coupling of Section 2.1), k_r ~ U(1.5, 40): one real root per
+    row, near k_r / m_r.  The region (centre 5, semi-axes 1.5 / 0.5) stays away
+    from the branch cuts (real |z| < kappa and the imaginary axis)."""
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(1.5, 40.0, n)
+    m = rng.uniform(0.8, 1.2, n)
+    e = rng.uniform(0.05, 0.5, n)
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1, -1.0), Fn(F_SQRT, kappa)]
+    return hidden_diagonal([k, m, e], fns, Region(5.0 + 0.0j, 1.5, 0.5), N, L,
+                           layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_sqrt")
+
+
+def diag_inv(n: int = 240, seed: int = 61, N: int = 32, L: int = 4, sigma: float = 5.0,
+             layers: int = 3) -> Problem:
+    """Decoupled k_r - z m_r + e_r / (sigma - z) (the 1/(sigma - z) form of
+    Section 2.1), real roots."""
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(0.2, 40.0, n)
+    m = rng.uniform(0.8, 1.2, n)
+    e = rng.uniform(0.05, 0.5, n)
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1, -1.0), Fn(F_INV, sigma)]
+    return hidden_diagonal([k, m, e], fns, Region(2.0 + 0.0j, 1.5, 0.5), N, L,
+                           layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_inv")
+
+
 def random_banded(n: int = 300, kl: int = 7, ku: int = 7, m: int = 3, seed: int = 41,
                   N: int = 8, L: int = 5) -> Problem:
     """Random real band matrices (every band entry present) with quadratic f;
