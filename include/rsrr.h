@@ -266,7 +266,8 @@ rsrr_status rsrr_project(rsrr_t *h, void *stream);
  * T_Q(z) = sum_i f_i(z) P_i in FP64 -- the moments of T_Q^{-1} over the N_Q
  * quadrature nodes on the GPU (batched complex128 LU), the Hankel SVD and
  * the small eigenproblem on the host -- then v = Q g and residuals on the GPU.
- * Returns OK or WGAP (gap test failed; results still filled). */
+ * Returns OK or WGAP (gap test failed; results still filled); ETIMEOUT if a
+ * bounded wait of a tensor-core product kernel ran out since rsrr_sample. */
 rsrr_status rsrr_solve(rsrr_t *h, rsrr_result *out);
 
 /* Copies S = [X_0 ... X_{N-1}] (n x N*L, column major, before normalisation)
@@ -352,6 +353,16 @@ rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsr
                        int64_t lda, const rsrr_c128 *B, int64_t ldb, rsrr_c128 *C, int64_t ldc,
                        double alpha, double beta, int32_t method, int32_t hermitian,
                        size_t max_ws_bytes, void *stream);
+
+/* Failure detection without a GPU fault: one thread waits, with the bounded
+ * mbarrier wait of the tensor-core product kernel, on a barrier that nothing
+ * completes, giving up after `tries` polls (1 .. 2^20).  The wait is counted
+ * in the same device counter that rsrr_zgemm and rsrr_solve read (rsrr_solve
+ * returns ETIMEOUT when a wait of the sample or project products ran out).
+ * Returns ETIMEOUT when the wait ran out and was counted, with the CUDA
+ * context still usable; OK (with a message) if it was not counted; EINVAL or
+ * ECUDA otherwise.  Waits for `stream` before and after. */
+rsrr_status rsrr_check_wait_timeout(int32_t tries, void *stream);
 
 /* Device bytes a handle for this problem holds at its peak (its buffers, the
  * projection work space and rsrr_solve's temporaries), without allocating

@@ -568,6 +568,7 @@ rsrr_status Handle::sample(cudaStream_t s) {
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L;
     rsrr_status ms;
+    CK(ozaki_timeouts(&tmo_mark), "timeout counter");
     if ((ms = mark(0, s)) != RSRR_OK) return ms;
     CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
     CK(launch_tnorm(d_tnorm, dp, s), "tnorm");
@@ -824,6 +825,7 @@ rsrr_status Handle::sample_dense(cudaStream_t s) {
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L, total = (int64_t)n * n * N;
     rsrr_status ms;
+    CK(ozaki_timeouts(&tmo_mark), "timeout counter");
     if ((ms = mark(0, s)) != RSRR_OK) return ms;
     CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
     CK(launch_assemble_dense_c128(d_T64, d_points, d_z, diag, nn, N, s), "assemble");

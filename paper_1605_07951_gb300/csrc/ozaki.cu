@@ -460,8 +460,8 @@ RSRR_DEV void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, ui
 RSRR_DEV void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
 }
-RSRR_DEV bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < OZT_WAIT_LIMIT; ++it) {
+RSRR_DEV bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = OZT_WAIT_LIMIT) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
@@ -631,6 +631,21 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+}
+
+// Failure-detection check of the bounded wait: one thread waits on an
+// mbarrier that nothing arrives on; the wait gives up after `limit` tries and
+// is counted in g_ozt_timeouts, exactly as in the tensor-core kernel.
+__global__ void ozt_wait_check_kernel(long long limit) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(a) : "memory");
+    if (!mbar_wait(a, 0, limit)) atomicAdd(&g_ozt_timeouts, 1u);
+}
+
+cudaError_t ozaki_timeouts(unsigned int *count) {
+    return cudaMemcpyFromSymbol(count, g_ozt_timeouts, sizeof *count);
 }
 
 // C = alpha sum_s W[s] + beta C (fixed order over the splits)
@@ -955,4 +970,24 @@ extern "C" rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(RSRR_ECUDA, "sync", e);
     thread_error().clear();
     return RSRR_OK;
+}
+
+extern "C" rsrr_status rsrr_check_wait_timeout(int32_t tries, void *stream) {
+    using namespace rsrr;
+    auto fail = [](rsrr_status st, const char *msg, cudaError_t e = cudaSuccess) {
+        thread_error() = e == cudaSuccess ? std::string(msg) : std::string(msg) + ": " + cudaGetErrorString(e);
+        return st;
+    };
+    if (tries < 1 || tries > (1 << 20)) return fail(RSRR_EINVAL, "rsrr_check_wait_timeout: tries out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned int t0 = 0, t1 = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = ozaki_timeouts(&t0);
+    if (e != cudaSuccess) return fail(RSRR_ECUDA, "rsrr_check_wait_timeout", e);
+    ozt_wait_check_kernel<<<1, 32, 0, s>>>((long long)tries);
+    if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaStreamSynchronize(s)) == cudaSuccess)
+        e = ozaki_timeouts(&t1);
+    if (e != cudaSuccess) return fail(RSRR_ECUDA, "rsrr_check_wait_timeout", e);
+    if (t1 == t0) return fail(RSRR_OK, "rsrr_check_wait_timeout: the wait did not run out");
+    return fail(RSRR_ETIMEOUT, "a bounded tensor-core wait ran out");
 }

@@ -1076,6 +1076,12 @@ rsrr_status Handle::solve(rsrr_result *out) {
     using cplx = std::complex<double>;
     cudaStream_t s = hs;
     PK(wait(), "solve sync");
+    {  // a bounded wait of a tensor-core product that ran out since rsrr_sample
+        unsigned int tnow = 0;
+        PK(ozaki_timeouts(&tnow), "timeout counter");
+        if (tnow != tmo_mark)
+            return fail(RSRR_ETIMEOUT, "rsrr_solve: a bounded tensor-core wait ran out in sample or project");
+    }
     const auto D2H = cudaMemcpyDeviceToHost;
     const auto H2D = cudaMemcpyHostToDevice;
     std::vector<cplx> lam, G;

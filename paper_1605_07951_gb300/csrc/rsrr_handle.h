@@ -94,6 +94,7 @@ struct Handle {
     int64_t launches = 0;
     cudaEvent_t events[8] = {};
     bool timed_sample = false, timed_project = false;
+    unsigned int tmo_mark = 0;  // tensor-core wait timeouts counted before this sample
     double stage_ms[6] = {};
     // GEMM timing of the last rsrr_project (opts.timing)
     EventPool gemm_pool;                // pairs around every product

@@ -147,6 +147,8 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
                         int64_t *launches, EventPool *timer = nullptr, double *tc_flops = nullptr,
                         bool legacy = false);
 size_t ozaki_workspace_bytes(int M, int N, int K, bool hermitian);
+// bounded tensor-core waits that ran out so far (a device-wide counter)
+cudaError_t ozaki_timeouts(unsigned int *count);
 // bf16 tensor-core flops the product issues (2 per multiply-add of slices);
 // legacy: the mma.sync kernel (64-row tiles) instead of the tcgen05 kernel
 double ozaki_tc_flops(int M, int N, int K, bool hermitian, bool legacy = false);

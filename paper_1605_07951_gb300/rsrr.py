@@ -150,6 +150,7 @@ rsrr_server_destroy = _sig("rsrr_server_destroy", None, [_h])
 rsrr_zgemm = _sig("rsrr_zgemm", C.c_int,
                   [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, C.c_int64, _p, C.c_int64, _p,
                    C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_size_t, _p])
+rsrr_check_wait_timeout = _sig("rsrr_check_wait_timeout", C.c_int, [C.c_int32, _p])
 
 
 class RSRRError(RuntimeError):

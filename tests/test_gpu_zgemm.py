@@ -180,3 +180,20 @@ def test_tcgen05_and_mma_slice_products_agree(env, shape):
     amax = np.maximum(np.abs(A.real), np.abs(A.imag)).max(axis=0)
     bmax = np.maximum(np.abs(B.real), np.abs(B.imag)).max(axis=0)
     assert np.all(np.abs(a - b) <= 2 * K * 2.0 ** -53 * np.outer(amax, bmax))
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(env):
+    """Failure detection without a GPU fault: a bounded wait on a barrier that
+    nothing completes gives up, is counted and reported as ETIMEOUT; products
+    and whole solves afterwards succeed."""
+    torch, rsrr = env
+    assert rsrr.rsrr_check_wait_timeout(256, None) == rsrr.RSRR_ETIMEOUT
+    assert b"ran out" in rsrr.rsrr_last_error(None)
+    assert rsrr.rsrr_check_wait_timeout(0, None) == rsrr.RSRR_EINVAL
+    torch.cuda.synchronize()
+    # the counter is compared around each call: a later product is not blamed
+    rng = np.random.default_rng(5)
+    A = rng.integers(-9, 10, (256, 512)) + 1j * rng.integers(-9, 10, (256, 512))
+    B = rng.integers(-9, 10, (512, 64)) + 1j * rng.integers(-9, 10, (512, 64))
+    C = zgemm(env, A, B, False, 2)
+    assert np.array_equal(C, A @ B)
