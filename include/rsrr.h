@@ -364,6 +364,17 @@ rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsr
  * ECUDA otherwise.  Waits for `stream` before and after. */
 rsrr_status rsrr_check_wait_timeout(int32_t tries, void *stream);
 
+/* Host-only view of what rsrr_create prepares, without touching the GPU:
+ * the N sampling points z_j (step 1; Section 4.1 trapezoid nodes on the
+ * ellipse, or the explicit points), the coefficient table f_i(z_j) (sparse
+ * kind: N x m, point-major, coef[j * m + i]; not written for the Helmholtz
+ * kind) and the half-bandwidths kl, ku detected from the pattern (0 for the
+ * Helmholtz kind).  Outputs are host memory owned by the caller; any of them
+ * may be NULL.  Same arguments, validation and errors as rsrr_create. */
+rsrr_status rsrr_describe(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                          const rsrr_opts *opts, rsrr_c128 *z, rsrr_c128 *coef, int32_t *kl,
+                          int32_t *ku);
+
 /* Device bytes a handle for this problem holds at its peak (its buffers, the
  * projection work space and rsrr_solve's temporaries), without allocating
  * anything or touching the GPU.  Same arguments and validation as

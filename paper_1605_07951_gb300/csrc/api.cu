@@ -203,6 +203,22 @@ rsrr_status rsrr_estimate_bytes(const rsrr_nep *nep, const rsrr_region *region, 
     return RSRR_OK;
 }
 
+rsrr_status rsrr_describe(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                          const rsrr_opts *opts, rsrr_c128 *z, rsrr_c128 *coef, int32_t *kl,
+                          int32_t *ku) {
+    Handle *h = nullptr;
+    rsrr_status st = rsrr::prepare(nep, region, N, L, opts, &h);
+    if (st != RSRR_OK) return st;
+    if (z)
+        for (int j = 0; j < h->N; ++j) z[j] = rsrr_c128{h->z[j].real(), h->z[j].imag()};
+    if (coef && !h->dense)
+        for (size_t e = 0; e < h->h_coef.size(); ++e) coef[e] = rsrr_c128{h->h_coef[e].x, h->h_coef[e].y};
+    if (kl) *kl = h->dense ? 0 : h->kl;
+    if (ku) *ku = h->dense ? 0 : h->ku;
+    delete h;
+    return RSRR_OK;
+}
+
 }  // extern "C"
 
 namespace rsrr {

@@ -151,6 +151,9 @@ rsrr_zgemm = _sig("rsrr_zgemm", C.c_int,
                   [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, C.c_int64, _p, C.c_int64, _p,
                    C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_size_t, _p])
 rsrr_check_wait_timeout = _sig("rsrr_check_wait_timeout", C.c_int, [C.c_int32, _p])
+rsrr_describe = _sig("rsrr_describe", C.c_int,
+                     [C.POINTER(rsrr_nep), C.POINTER(rsrr_region), C.c_int32, C.c_int32,
+                      C.POINTER(rsrr_opts), _p, _p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
 
 
 class RSRRError(RuntimeError):
@@ -234,6 +237,25 @@ def estimate_bytes(prob, opts: rsrr_opts | None = None, N=None, L=None) -> int:
     if st != RSRR_OK:
         raise RSRRError(st, rsrr_last_error(None).decode())
     return int(b.value)
+
+
+def prepared(prob, opts: rsrr_opts | None = None, N=None, L=None):
+    """What rsrr_create prepares on the host for `prob` (no GPU needed):
+    sampling points z (N), coefficient table (N x m; None for the dense
+    kind) and the detected half-bandwidths (kl, ku)."""
+    nep, reg, keep = describe(prob)
+    o = opts if opts is not None else default_opts()
+    N = int(N if N is not None else prob.N)
+    L = int(L if L is not None else prob.L)
+    dense = nep.kind == RSRR_NEP_HELMHOLTZ
+    z = np.zeros(N, dtype=np.complex128)
+    coef = None if dense else np.zeros((N, nep.m), dtype=np.complex128)
+    kl, ku = C.c_int32(-1), C.c_int32(-1)
+    st = rsrr_describe(C.byref(nep), C.byref(reg), N, L, C.byref(o), z.ctypes.data,
+                       None if coef is None else coef.ctypes.data, C.byref(kl), C.byref(ku))
+    if st != RSRR_OK:
+        raise RSRRError(st, rsrr_last_error(None).decode())
+    return z, coef, (kl.value, ku.value)
 
 
 def _complex_array(ptr, count):

@@ -1,0 +1,87 @@
+"""CPU parity of what rsrr_create prepares on the host (rsrr_describe, no GPU):
+the sampling points z_j (step 1, Section 4.1 trapezoid nodes or explicit
+points), the coefficient table f_i(z_j) for every function family of the ABI
+(Section 2.1: polynomial, z/(z - sigma), 1/(sigma - z), sqrt(z^2 - kappa^2) on
+the principal branch, exp(-tau z)) against the oracle, and the half-bandwidths
+detected from the pattern against their definition."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_1605_07951_gb300", "librsrr.so")
+
+
+@pytest.fixture(scope="module")
+def rsrr():
+    if not os.path.exists(LIB):  # a fresh checkout: build the library first
+        from paper_1605_07951_gb300 import build
+        build.build()
+    from paper_1605_07951_gb300 import rsrr as binding
+    return binding
+
+
+FAMILIES = {
+    "diag_quadratic": lambda: W.diag_quadratic(),
+    "diag_rational": lambda: W.diag_rational(),
+    "diag_delay": lambda: W.diag_delay(),
+    "diag_sqrt": lambda: W.diag_sqrt(),
+    "diag_inv": lambda: W.diag_inv(),
+    "grid_g30": lambda: W.rational_grid(g=30, N=64, L=8),
+    "random_banded": lambda: W.random_banded(kl=5, ku=9),
+    "loaded_string_points": lambda: W.loaded_string(),
+}
+
+
+def bandwidths(p):
+    rows = np.repeat(np.arange(p.n), np.diff(p.row_ptr))
+    d = rows - np.asarray(p.col_idx)
+    return int(max(d.max(), 0)), int(max(-d.min(), 0))
+
+
+@pytest.mark.parametrize("name", list(FAMILIES))
+def test_points_coefficients_and_bandwidths_match(rsrr, name):
+    p = FAMILIES[name]()
+    z, coef, (kl, ku) = rsrr.prepared(p)
+    zo = oracle.sample_points(p.region, p.N)
+    assert np.abs(z - zo).max() <= 1e-15 * max(1.0, np.abs(zo).max())
+    for i, fn in enumerate(p.fns):
+        want = oracle.eval_fn(fn, zo)
+        assert np.abs(coef[:, i] - want).max() <= 1e-14 * max(1.0, np.abs(want).max()), (name, i)
+    assert (kl, ku) == bandwidths(p)
+
+
+def test_square_root_takes_the_principal_branch(rsrr):
+    # points on both sides of the cut of sqrt(w) (w = z^2 - kappa^2 <= 0 on
+    # the real segment |z| < kappa and on the imaginary axis)
+    p = W.diag_sqrt(n=16)
+    pts = np.array([0.3 + 1e-3j, 0.3 - 1e-3j, -0.3 + 1e-3j, 2e-3 + 0.7j, -2e-3 + 0.7j, 3.0 + 0.5j])
+    p.region = W.Region(p.region.center, p.region.a, p.region.b, kind="points", points=pts)
+    p.N = len(pts)
+    z, coef, _ = rsrr.prepared(p)
+    kappa = p.fns[2].param
+    got = coef[:, 2] / complex(p.fns[2].scale)
+    assert np.all(got.real >= 0.0)  # principal branch: Re sqrt >= 0
+    assert np.abs(got ** 2 - (pts ** 2 - kappa ** 2)).max() <= 1e-14
+    # across the cut the value jumps sign (the imaginary part flips)
+    assert got[0].imag * got[1].imag < 0 and got[3].imag * got[4].imag < 0
+
+
+def test_describe_validates_like_create(rsrr):
+    p = W.diag_quadratic()
+    p.row_ptr = p.row_ptr.copy()
+    p.row_ptr[0] = 1
+    with pytest.raises(rsrr.RSRRError) as e:
+        rsrr.prepared(p)
+    assert e.value.status == rsrr.RSRR_EINVAL
+
+
+def test_dense_kind_has_points_but_no_table(rsrr):
+    p = W.helmholtz_sphere(n=64, N=8, L=4)
+    z, coef, (kl, ku) = rsrr.prepared(p)
+    assert coef is None and (kl, ku) == (0, 0)
+    assert np.abs(z - oracle.sample_points(p.region, p.N)).max() <= 1e-15 * 4
