@@ -349,3 +349,57 @@ def test_planted_dense_mistakes_fail_the_two_point_pin(monkeypatch, which):
     except Exception:
         ok = False
     assert not ok, f"planted mistake {which!r} went unnoticed"
+
+
+# ------------------------------------------------- unit pins of steps 3 and 4
+def test_truncated_basis_keeps_the_singular_values_above_delta():
+    """S = U diag(sigma) V^H with prescribed sigma: the kept count is the
+    number of sigma_j > delta sigma_1 and Q spans the matching columns of U."""
+    rng = np.random.default_rng(3)
+    n, c = 60, 12
+    U, _ = np.linalg.qr(rng.normal(size=(n, c)) + 1j * rng.normal(size=(n, c)))
+    V, _ = np.linalg.qr(rng.normal(size=(c, c)) + 1j * rng.normal(size=(c, c)))
+    sigma = np.logspace(0, -20, c)  # 1 ... 1e-20
+    S = (U * sigma) @ V.conj().T
+    Q, sig, k = oracle.truncated_basis(S, delta=1e-8)
+    assert k == int(np.sum(sigma > 1e-8)) == 5
+    # span(Q) = span(U[:, :k]): the projector difference is at rounding level
+    Pq, Pu = Q @ Q.conj().T, U[:, :k] @ U[:, :k].conj().T
+    assert np.abs(Pq - Pu).max() <= 1e-7  # sigma_k / sigma_{k+1} = 1e2 bounds the angle
+    assert np.abs(sig[:k] - sigma[:k]).max() <= 1e-14
+
+
+def test_projection_onto_coordinate_vectors_is_a_submatrix():
+    """With Q = [e_a, e_b, ...], P_i = Q^H A_i Q is A_i restricted to rows and
+    columns a, b, ..."""
+    p = W.random_banded(n=50, kl=3, ku=4)
+    idx = np.array([0, 7, 8, 31, 49])
+    Q = np.zeros((p.n, len(idx)), dtype=np.complex128)
+    Q[idx, np.arange(len(idx))] = 1.0
+    P = oracle.project(p, Q)
+    for i, Pi in enumerate(P):
+        dense = np.zeros((p.n, p.n))
+        rows = np.repeat(np.arange(p.n), np.diff(p.row_ptr))
+        dense[rows, p.col_idx] = p.values[i]
+        assert np.array_equal(Pi, dense[np.ix_(idx, idx)])
+
+
+def test_ss_full_on_a_linear_projected_problem():
+    """T_Q(z) = K - z I with K = X diag(mu) X^{-1}: SS-FULL returns the mu
+    inside the ellipse and eigenvectors parallel to X's columns."""
+    rng = np.random.default_rng(4)
+    k = 9
+    reg = W.Region(complex(0.5, 0.2), 1.0, 0.6)
+    mu = np.array([0.3 + 0.1j, 0.9 + 0.3j, 0.2 + 0.5j, 0.6 - 0.2j,
+                   3.0, -2.0 + 1j, 0.5 + 2.0j, 2.5 - 1.5j, -1.2 - 0.9j])
+    X = rng.normal(size=(k, k)) + 1j * rng.normal(size=(k, k)) + 3 * np.eye(k)
+    K = X @ np.diag(mu) @ np.linalg.inv(X)
+    fns = [W.Fn(W.F_ONE), W.Fn(W.F_ZPOW, 1, -1.0)]
+    lam, G, info = oracle.ss_full([K, np.eye(k)], fns, reg, NQ=256, KQ=2)
+    inside = oracle.inside(reg, mu)
+    assert len(lam) == inside.sum() == 4
+    for l, g in zip(lam, G.T):
+        j = int(np.argmin(np.abs(mu - l)))
+        assert inside[j] and abs(mu[j] - l) <= 1e-10
+        x = X[:, j]
+        assert abs(np.vdot(x, g)) / (np.linalg.norm(x) * np.linalg.norm(g)) >= 1 - 1e-10
