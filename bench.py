@@ -77,6 +77,24 @@ print(json.dumps({{"seconds": dt, "columns": int(len(z) * p.L)}}))
 """
 
 
+ORACLE_PAR_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import oracle, workloads as W
+p = W.rational_grid(g={g})
+z = oracle.sample_points(p.region, p.N)[{j}:{j} + 1]
+oracle.resolvent_samples(p, z)  # warm the code paths
+open(os.path.join({tmp!r}, "ready.{j}"), "w").close()
+t_end = time.time() + 600
+while len(os.listdir({tmp!r})) < {procs} and time.time() < t_end:  # every worker set up
+    time.sleep(0.01)
+t0 = time.time()
+X = oracle.resolvent_samples(p, z)
+t1 = time.time()
+print(json.dumps({{"t0": t0, "t1": t1, "columns": int(len(z) * p.L)}}))
+"""
+
+
 def max_over_ranks(ms, dist=None, device="cpu"):
     """Step time of the whole job: the slowest rank's (all-reduce MAX; the
     identity on one rank)."""
@@ -109,11 +127,63 @@ def oracle_sample(g, npts):
     return d["columns"] / d["seconds"], d
 
 
-def cpu_baseline(g, npts):
+def oracle_parallel(g, procs):
+    """The oracle on `procs` host processes at once, one sampling point each
+    (1 BLAS thread each): every process sets up and warms up, they meet at a
+    file barrier, then solve; wall time = last finish - first start."""
+    import tempfile
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    with tempfile.TemporaryDirectory() as tmp:
+        ps = [subprocess.Popen([sys.executable, "-c",
+                                ORACLE_PAR_SNIPPET.format(root=ROOT, g=g, j=j, tmp=tmp, procs=procs)],
+                               stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+              for j in range(procs)]
+        outs = [q.communicate(timeout=1800) for q in ps]
+    for q, (_, err) in zip(ps, outs):
+        if q.returncode != 0:
+            raise RuntimeError(err[-2000:])
+    ds = [json.loads(o.strip().splitlines()[-1]) for o, _ in outs]
+    wall = max(d["t1"] for d in ds) - min(d["t0"] for d in ds)
+    cols = sum(d["columns"] for d in ds)
+    return cols / wall, wall, cols
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu), else the machine type."""
+    import platform
+    import shutil
+    if shutil.which("lscpu"):
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=30).stdout
+            for ln in out.splitlines():
+                if ln.startswith("Model name:"):
+                    return ln.split(":", 1)[1].strip() + f" ({platform.machine()})"
+        except Exception:
+            pass
+    return platform.machine()
+
+
+def cpu_baseline(g, npts, par=True):
     v, d = oracle_sample(g, npts)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{npts} of the 64 sampling points ({d['columns']} resolvent columns, "
-                      f"scipy banded LU, FP64) in {d['seconds']:.1f} s, 1 BLAS thread"}
+    out = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{npts} of the 64 sampling points ({d['columns']} resolvent columns, "
+                     f"scipy banded LU, FP64) in {d['seconds']:.1f} s, 1 BLAS thread",
+           "cpu": cpu_model()}
+    if par:
+        # one process per core this process may run on, at most 16 (about
+        # 0.7 GB of host memory each at the benchmark size)
+        try:
+            ncpu = len(os.sched_getaffinity(0))
+        except AttributeError:
+            ncpu = os.cpu_count() or 1
+        procs = max(1, min(16, ncpu))
+        pv, wall, cols = oracle_parallel(g, procs)
+        out["parallel"] = {"value": pv, "unit": UNIT, "cores": procs,
+                            "sample": f"{procs} sampling points, one per process (1 BLAS thread "
+                                      f"each), solved at once: {cols} columns in {wall:.1f} s"}
+    return out
 
 
 def measured_peaks():

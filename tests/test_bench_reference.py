@@ -38,3 +38,13 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_only_rank_zero_prints():
     assert run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_cpu_baseline_reports_one_core_and_all_cores_runs():
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.cpu_baseline(40, 2)
+    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0 and d["cpu"]
+    par = d["parallel"]
+    assert 1 <= par["cores"] <= 16 and par["value"] > 0
+    assert f"{par['cores']} sampling points" in par["sample"]
