@@ -451,6 +451,7 @@ def run_ours(a, rank, world, local):
                 "achieved": asm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": asm_gbs / peaks["hbm_gbs"], "traffic": None,
                 "algorithmic_bytes_per_launch": asm_bytes, "avg_stage_ms": asm_avg,
+                "pattern_only_bytes_per_launch": 8 * len(p.col_idx) * p.N,
                 "peak_note": f"copy bandwidth, {peaks['source']}; time = the assembly stage "
                              "(the ||T(z_j)|| kernel + the assembly), so the fraction is a lower bound"}
 
