@@ -440,6 +440,9 @@ def run_ours(a, rank, world, local):
                "frac": achieved / FP32_PEAK_TFLOPS,
                "traffic": None,
                "algorithmic_flop_per_launch": lu_flops, "avg_launch_ms": lu_avg,
+               # the other roof: the band storage read and written once
+               "algorithmic_bytes_per_launch": 2 * 8.0 * ldab * n * p.N,
+               "hbm_frac": 2 * 8.0 * ldab * n * p.N / (lu_avg / 1e3) / 1e9 / peaks["hbm_gbs"],
                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; traffic "
                             "null: the kernel changed after its last DRAM capture"}
     roof, roof_other = (roof_lu, roof_tc) if lu_avg >= tc_avg else (roof_tc, roof_lu)
