@@ -17,8 +17,15 @@ Parity status per function:
   resolvent_samples .................. pinned (decoupled closed forms, residual)
   truncated_basis, project, ss_full .. pinned (closed-form spectra, inertia counts,
                                        companion linearisation, Lambert W, the
-                                       loaded-string example of Section 4.2)
+                                       loaded-string example of Section 5.2)
   rsrr ............................... pinned (as above)
+  backward_error_inf, residual,
+  backward_error_inf_dense,
+  residual_dense ..................... pinned (hand-computed values on a 3 x 3
+                                       non-symmetric T and the two-point kernel,
+                                       tests/golden/checker_norms.json; the
+                                       Rigal-Gaches minimal perturbation; planted
+                                       mutations of each fail a pin)
   assemble_dense, taylor_coefficients,
   resolvent_samples_dense, rsrr_dense  pinned (two-point problem with closed-form
                                        eigenvalues k pi / r + i im and eigenvectors;
@@ -30,18 +37,18 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
-from workloads import (F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP, Problem,
-                       Region)
+from workloads import (F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP, F_TAYLOR, F_CALLBACK,
+                       Problem, Region)
 
 
 # ---------------------------------------------------------------------------
-# Step 1 of RSRR: sampling points (Section 4.1, ellipse contour and N-point
-# trapezoid rule; the RIA allows explicit points, Section 3.1)
+# Step 1 of RSRR: sampling points (Section 5.1, ellipse contour and N-point
+# trapezoid rule; the RIA allows explicit points, Section 3.3)
 # ---------------------------------------------------------------------------
 
 def sample_points(region: Region, N: int) -> np.ndarray:
     """z_j = phi(alpha_j), alpha_j = 2 pi (j + 1/2)/N on the ellipse
-    phi(alpha) = gamma + a cos(alpha) + i b sin(alpha) (Section 4.1, ellipse
+    phi(alpha) = gamma + a cos(alpha) + i b sin(alpha) (Section 5.1, ellipse
     contour and trapezoid nodes), or the region's explicit points."""
     if region.kind == "points":
         return np.asarray(region.points, dtype=np.complex128).copy()
@@ -51,7 +58,7 @@ def sample_points(region: Region, N: int) -> np.ndarray:
 
 
 def quad_weights(region: Region, NQ: int) -> np.ndarray:
-    """omega_j = (1/N) dphi/dalpha at alpha_j (Section 4.1 trapezoid rule)."""
+    """omega_j = (1/N) dphi/dalpha at alpha_j (Section 5.1 trapezoid rule)."""
     j = np.arange(NQ)
     alpha = 2.0 * np.pi * (j + 0.5) / NQ
     return (-region.a * np.sin(alpha) + 1j * region.b * np.cos(alpha)) / NQ
@@ -86,6 +93,10 @@ def eval_fn(fn, z):
         base = np.sqrt(z * z - fn.param * fn.param)
     elif fn.kind == F_EXP:
         base = np.exp(-fn.param * z)
+    elif fn.kind == F_TAYLOR:
+        base = (z - complex(fn.shift)) ** int(fn.power)
+    elif fn.kind == F_CALLBACK:
+        base = np.asarray(fn.callback(np.atleast_1d(z)), dtype=np.complex128).reshape(z.shape)
     else:
         raise ValueError(f"unknown function kind {fn.kind}")
     return complex(fn.scale) * base
@@ -116,11 +127,11 @@ def _to_band(T, kl: int, ku: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Step 2 of RSRR: the resolvent samples X_j = T(z_j)^{-1} U (Section 3.3)
+# Step 2 of RSRR: the resolvent samples X_j = T(z_j)^{-1} U (Section 4.3)
 # ---------------------------------------------------------------------------
 
 def resolvent_samples(prob: Problem, z: np.ndarray, U: np.ndarray | None = None) -> list:
-    """X_j = T(z_j)^{-1} U for each sampling point (Section 3.3, step 2),
+    """X_j = T(z_j)^{-1} U for each sampling point (Section 4.3, step 2),
     by a banded LU solve with partial pivoting (LAPACK gbsv) per point."""
     if U is None:
         U = prob.U
@@ -146,30 +157,30 @@ def backward_error_inf(prob: Problem, z: complex, X: np.ndarray, U: np.ndarray |
 
 
 # ---------------------------------------------------------------------------
-# Step 3 of RSRR: S, column normalisation, truncated SVD (Eq. hatS, Section 3.2
-# last paragraph, Section 3.3 step 3)
+# Step 3 of RSRR: S, column normalisation, truncated SVD (Eq. 51, Section 4.2
+# last paragraph, Section 4.3 step 3)
 # ---------------------------------------------------------------------------
 
 def sample_matrix(samples: list) -> np.ndarray:
-    """S = [T(z_0)^{-1}U, ..., T(z_{N-1})^{-1}U] (Eq. for S in Section 3.2)."""
+    """S = [T(z_0)^{-1}U, ..., T(z_{N-1})^{-1}U] (Eq. 51 in Section 4.2)."""
     return np.concatenate(samples, axis=1)
 
 
 def normalize_columns(S: np.ndarray) -> np.ndarray:
-    """Scale every column of S to unit 2-norm before the SVD (Section 3.2)."""
+    """Scale every column of S to unit 2-norm before the SVD (Section 4.2)."""
     return S / np.linalg.norm(S, axis=0, keepdims=True)
 
 
 def truncated_basis(S: np.ndarray, delta: float = 1e-14):
     """S ~ Q Sigma V^H keeping the k singular values > delta*sigma_1
-    (Section 3.3 step 3; delta = 1e-14 as in the paper)."""
+    (Section 4.3 step 3; delta = 1e-14 as in the paper)."""
     Qf, sig, _ = np.linalg.svd(S, full_matrices=False)
     k = int(np.sum(sig > delta * sig[0]))
     return Qf[:, :k], sig, k
 
 
 # ---------------------------------------------------------------------------
-# Step 4 of RSRR: projection T_Q(z) = Q^H T(z) Q (Eq. for T_Q, Section 3)
+# Step 4 of RSRR: projection T_Q(z) = Q^H T(z) Q (Eq. 45, Section 4)
 # ---------------------------------------------------------------------------
 
 def project(prob: Problem, Q: np.ndarray) -> list:
@@ -179,16 +190,16 @@ def project(prob: Problem, Q: np.ndarray) -> list:
 
 def ss_full(P: list, fns: list, region: Region, NQ: int = 500, KQ: int = 2,
             tol_gap: float = 1e3):
-    """SS-FULL: the SS-RI algorithm of Section 2.3 with U = I (F = T_Q^{-1}),
-    sampling points on the ellipse by the trapezoid rule of Section 4.1.
+    """SS-FULL: the SS-RI algorithm of Section 3.3 with U = I (F = T_Q^{-1}),
+    sampling points on the ellipse by the trapezoid rule of Section 5.1.
 
     Moments A_alpha = sum_q omega_q ((z_q - gamma)/rho)^alpha F(z_q), alpha <
     2 KQ (the scaled-moment reading: a fixed change of basis of z that keeps
     the pencil's eigenvalues, applied against overflow), block Hankel H, H^<
-    (Eq. HH), truncated SVD of H with the count fixed by the largest gap
+    (Eq. 33), truncated SVD of H with the count fixed by the largest gap
     sigma_j/sigma_{j+1} (gap strategy, tol_gap = 1e3), A = V0^H H^< W0
-    Sigma0^{-1} (Eq. A), eigenpairs of A, and g = M W0 Sigma0^{-1} b
-    (Eq. eigens) with M = [A_0 ... A_{KQ-1}] since U = I.
+    Sigma0^{-1} (Eq. 38), eigenpairs of A, and g = M W0 Sigma0^{-1} b
+    (Eq. 41) with M = [A_0 ... A_{KQ-1}] since U = I.
 
     Returns (lam, G, info): eigenvalues of the projected NEP, the projected
     eigenvectors as columns of G, and {"nbar", "gmax", "sv"}.
@@ -224,12 +235,12 @@ def ss_full(P: list, fns: list, region: Region, NQ: int = 500, KQ: int = 2,
 
 
 # ---------------------------------------------------------------------------
-# Residual measure (Section 4.4, E(v, lambda) with the 1-norms of the A_i)
+# Residual measure (Section 5.4, E(v, lambda) with the 1-norms of the A_i)
 # ---------------------------------------------------------------------------
 
 def residual(prob: Problem, lam: complex, v: np.ndarray) -> float:
     """rho(lam, v) = ||T(lam) v||_2 / ((sum_i |f_i(lam)| ||A_i||_1) ||v||_2),
-    the normalised relative residual of Section 4.4."""
+    the normalised relative residual of Section 5.4."""
     T = assemble(prob, lam)
     scale = 0.0
     for i, fn in enumerate(prob.fns):
@@ -239,12 +250,12 @@ def residual(prob: Problem, lam: complex, v: np.ndarray) -> float:
 
 
 def plain_residual(prob: Problem, lam: complex, v: np.ndarray) -> float:
-    """||T(lam) v||_2 / ||v||_2 (Section 2.3, gap-strategy remark)."""
+    """||T(lam) v||_2 / ||v||_2 (Section 3.3, gap-strategy remark)."""
     return float(np.linalg.norm(assemble(prob, lam) @ v) / np.linalg.norm(v))
 
 
 # ---------------------------------------------------------------------------
-# The whole method (Section 3.3, steps 1-5)
+# The whole method (Section 4.3, steps 1-5)
 # ---------------------------------------------------------------------------
 
 def rsrr(prob: Problem, delta: float = 1e-14, NQ: int = 500, KQ: int = 2,
@@ -255,7 +266,7 @@ def rsrr(prob: Problem, delta: float = 1e-14, NQ: int = 500, KQ: int = 2,
 
     Acceptance (readings): only pairs strictly inside the contour are kept (the
     method asks for the n_C pairs inside), and, following the advice of the
-    gap-strategy paragraph of Section 2.3 to check residuals, a pair is kept
+    gap-strategy paragraph of Section 3.3 to check residuals, a pair is kept
     only if its normalised residual is <= res_tol."""
     z = sample_points(prob.region, prob.N)
     X = resolvent_samples(prob, z, U)
@@ -280,9 +291,84 @@ def rsrr(prob: Problem, delta: float = 1e-14, NQ: int = 500, KQ: int = 2,
 # ---------------------------------------------------------------------------
 
 def negative_inertia(prob: Problem, x: float) -> int:
-    """nu(T(x)): number of negative eigenvalues of the real symmetric T(x)."""
+    """nu(T(x)): number of negative eigenvalues of the real symmetric T(x)
+    (dense symmetric eigenvalues; small problems only)."""
     T = assemble(prob, x).toarray().real
     return int(np.sum(np.linalg.eigvalsh(T) < 0.0))
+
+
+_INERTIA_LIB = None
+
+
+def _inertia_lib():
+    """The plain-C band LDL^T of oracle/band_inertia.c, compiled on first use
+    (gcc, into oracle/_band_inertia.so) and loaded with ctypes."""
+    global _INERTIA_LIB
+    if _INERTIA_LIB is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "band_inertia.c")
+        lib = os.path.join(here, "_band_inertia.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".{os.getpid()}.tmp"
+            subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src], check=True)
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        L.band_ldlt_negcount.restype = ctypes.c_int
+        L.band_ldlt_negcount.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+        _INERTIA_LIB = L
+    return _INERTIA_LIB
+
+
+def negative_inertia_band(prob: Problem, x: float) -> int:
+    """nu(T(x)) by Sylvester's law of inertia: the number of negative pivots of
+    the symmetric band LDL^T of the real symmetric T(x) (oracle/band_inertia.c),
+    usable at full size (n = 40000, half-bandwidth 200).  Raises if a pivot is
+    exactly zero."""
+    T = assemble(prob, x).tocoo()
+    if np.abs(T.data.imag).max(initial=0.0) != 0.0:
+        raise ValueError("T(x) is not real")
+    low = T.row >= T.col
+    bw = int((T.row - T.col).max(initial=0))
+    ab = np.zeros((prob.n, bw + 1), dtype=np.float64)   # row j = column j of the band
+    ab[T.col[low], (T.row - T.col)[low]] = T.data.real[low]
+    ab = np.ascontiguousarray(ab)
+    neg = _inertia_lib().band_ldlt_negcount(prob.n, bw, ab.ctypes.data, bw + 1)
+    if neg < 0:
+        raise ZeroDivisionError(f"zero pivot in the LDL^T of T({x})")
+    return int(neg)
+
+
+def bisect_real_eigenvalues(prob: Problem, lo: float, hi: float, rtol: float = 1e-13,
+                            count_fn=None) -> np.ndarray:
+    """Every eigenvalue of a real symmetric NEP with T'(x) negative definite in
+    (lo, hi), by bisection on the inertia count: #eigenvalues in (a, b) =
+    nu(T(b)) - nu(T(a)).  Intervals are split until each holds one eigenvalue
+    (or one multiple eigenvalue), which is then bisected to rtol."""
+    nu = count_fn or (lambda x: negative_inertia_band(prob, x))
+    out = []
+    stack = [(lo, hi, nu(lo), nu(hi))]
+    while stack:
+        a, b, na, nb = stack.pop()
+        c = nb - na
+        if c <= 0:
+            continue
+        if b - a <= rtol * max(abs(a), abs(b)):
+            out += [0.5 * (a + b)] * c
+            continue
+        mid = 0.5 * (a + b)
+        nm = nu(mid)
+        if c == 1 or nm in (na, nb):
+            # one eigenvalue (or a cluster not split yet) on one side of mid
+            stack.append((a, mid, na, nm) if nm > na else (mid, b, nm, nb))
+            if nm != na and nm != nb:
+                stack.append((mid, b, nm, nb))
+        else:
+            stack.append((a, mid, na, nm))
+            stack.append((mid, b, nm, nb))
+    return np.sort(np.array(out, dtype=np.float64))
 
 
 def argument_principle_count(prob: Problem, region: Region, npts: int = 4096) -> int:
@@ -310,8 +396,8 @@ def companion_eigvals(prob: Problem) -> np.ndarray:
     scaled coefficient matrices) from its first companion linearisation
     [[0, I], [-B0, -B1]] w = z [[I, 0], [0, B2]] w, solved densely (QZ).
     Brute force used to pin the RSRR count and eigenvalues of quadratic
-    problems (Section 2.1 remarks that polynomial problems admit
-    linearisation)."""
+    problems (linearisation of polynomial problems is the standard route the
+    paper's Section 1 reviews)."""
     B = [None, None, None]
     for i, fn in enumerate(prob.fns):
         if fn.kind == F_ONE:
@@ -376,7 +462,7 @@ def taylor_coefficients(prob, R: np.ndarray | None = None, P: int | None = None)
     """A_p with T(z) = sum_{p<P} (z - c)^p A_p: A_p(i,j) = e^{i c r}(i r)^p /
     (p! 4 pi r) off the diagonal, A_0 diagonal = diag, A_p diagonal = 0 (p > 0).
     The Taylor series of exp(i z r) about the region centre c: the
-    interpolation of T that makes T_Q = Q^H T Q computable (Section 5.2 uses
+    interpolation of T that makes T_Q = Q^H T Q computable (Section 6 uses
     a Chebyshev interpolant for the same purpose)."""
     if R is None:
         R = distances(prob)
@@ -416,7 +502,7 @@ def backward_error_inf_dense(prob, z: complex, X: np.ndarray, U: np.ndarray | No
 
 def rsrr_dense(prob, delta: float = 1e-14, NQ: int = 500, KQ: int = 2, tol_gap: float = 1e3,
                U: np.ndarray | None = None, res_tol: float = 1e-6):
-    """RSRR (Section 3.3) for the dense kernel problem: samples by dense
+    """RSRR (Section 4.3) for the dense kernel problem: samples by dense
     solves, the truncated SVD basis of the normalised S, projection of the
     Taylor coefficients P_p = Q^H A_p Q, SS-FULL on T_Q(z) = sum_p (z-c)^p P_p,
     v = Q g, acceptance as in rsrr()."""
@@ -459,19 +545,92 @@ def eval_fn(fn, z):  # noqa: F811  (extends the families with the Taylor powers)
 
 
 def argument_principle_count_dense(prob, npts: int = 2048) -> int:
-    """Zeros of det T inside the region by the winding number of det T(z)."""
+    """Zeros of det T inside the region by the winding number of det T(z):
+    the phase of det T along the contour, sampled at npts points and refined
+    segment by segment (midpoints inserted only where a step of the phase is
+    at least pi/4) until every step is below pi/4; the winding number is the
+    sum of the steps over 2 pi."""
     R = distances(prob)
     reg = prob.region
 
-    def phase(z):
+    def phase(al):
+        z = reg.center + reg.a * np.cos(al) + 1j * reg.b * np.sin(al)
         s, _ = np.linalg.slogdet(assemble_dense(prob, z, R))
         return np.angle(s)
-    alpha = np.linspace(0.0, 2.0 * np.pi, npts + 1)
-    while True:
-        zz = reg.center + reg.a * np.cos(alpha) + 1j * reg.b * np.sin(alpha)
-        ph = np.array([phase(z) for z in zz])
-        d = np.angle(np.exp(1j * np.diff(ph)))
-        if np.all(np.abs(d) < np.pi / 4) or len(alpha) > 1 << 15:
-            break
-        alpha = np.sort(np.concatenate([alpha, 0.5 * (alpha[1:] + alpha[:-1])]))
-    return int(round(d.sum() / (2.0 * np.pi)))
+
+    alpha = list(np.linspace(0.0, 2.0 * np.pi, npts + 1))
+    ph = [phase(a) for a in alpha]
+    total = 0.0
+    stack = [(alpha[i], alpha[i + 1], ph[i], ph[i + 1], 0) for i in range(npts)]
+    while stack:
+        a, b, pa, pb, depth = stack.pop()
+        d = float(np.angle(np.exp(1j * (pb - pa))))
+        if abs(d) < np.pi / 4 or depth >= 20:
+            total += d
+            continue
+        m = 0.5 * (a + b)
+        pm = phase(m)
+        stack.append((m, b, pm, pb, depth + 1))
+        stack.append((a, m, pa, pm, depth + 1))
+    return int(round(total / (2.0 * np.pi)))
+
+
+# ---------------------------------------------------------------------------
+# General dense terms T(z) = sum_i f_i(z) A_i (Eq. 1 with dense A_i; the
+# "black-box" BEM matrices of Section 2.1 with a separated z-dependence)
+# ---------------------------------------------------------------------------
+
+def assemble_terms(prob, z: complex) -> np.ndarray:
+    """T(z) = sum_i f_i(z) A_i, dense."""
+    T = np.zeros((prob.n, prob.n), dtype=np.complex128)
+    for fn, A in zip(prob.fns, prob.As):
+        T += complex(eval_fn(fn, z)) * A
+    return T
+
+
+def resolvent_samples_terms(prob, z: np.ndarray, U: np.ndarray | None = None) -> list:
+    """X_j = T(z_j)^{-1} U by dense LU with partial pivoting (LAPACK gesv)."""
+    if U is None:
+        U = prob.U
+    return [np.linalg.solve(assemble_terms(prob, zj), U) for zj in z]
+
+
+def backward_error_inf_terms(prob, z: complex, X: np.ndarray, U: np.ndarray | None = None):
+    """Per-column eta = ||U - T X||_inf / (||T||_inf ||X||_inf + ||U||_inf)."""
+    if U is None:
+        U = prob.U
+    T = assemble_terms(prob, z)
+    Rr = U - T @ X
+    tn = np.abs(T).sum(axis=1).max()
+    return np.abs(Rr).max(axis=0) / (tn * np.abs(X).max(axis=0) + np.abs(U).max(axis=0))
+
+
+def residual_terms(prob, lam: complex, v: np.ndarray) -> float:
+    """||T(lam) v||_2 / ((sum_i |f_i(lam)| ||A_i||_1) ||v||_2), the normalised
+    residual of Section 5.4 with the 1-norms of the dense A_i."""
+    scale = sum(abs(complex(eval_fn(fn, lam))) * np.abs(A).sum(axis=0).max()
+                for fn, A in zip(prob.fns, prob.As))
+    return float(np.linalg.norm(assemble_terms(prob, lam) @ v) / (scale * np.linalg.norm(v)))
+
+
+def rsrr_terms(prob, delta: float = 1e-14, NQ: int = 500, KQ: int = 2, tol_gap: float = 1e3,
+               U: np.ndarray | None = None, res_tol: float = 1e-6):
+    """RSRR (Section 4.3) for dense terms: samples by dense solves, truncated
+    SVD basis of the normalised S, P_i = Q^H A_i Q, SS-FULL on T_Q, v = Q g,
+    acceptance as in rsrr()."""
+    z = sample_points(prob.region, prob.N)
+    X = resolvent_samples_terms(prob, z, U)
+    S = normalize_columns(sample_matrix(X))
+    Q, sig, k = truncated_basis(S, delta)
+    P = [Q.conj().T @ (A @ Q) for A in prob.As]
+    lam, G, info = ss_full(P, prob.fns, prob.region, NQ, KQ, tol_gap)
+    V = Q @ G
+    V = V / np.linalg.norm(V, axis=0, keepdims=True)
+    keep = inside(prob.region, lam)
+    lam, V = lam[keep], V[:, keep]
+    res = np.array([residual_terms(prob, l, V[:, j]) for j, l in enumerate(lam)])
+    ok = res <= res_tol
+    lam, V, res = lam[ok], V[:, ok], res[ok]
+    order = np.lexsort((np.angle(lam), np.abs(lam)))
+    return dict(lam=lam[order], V=V[:, order], res=res[order], k=k, sigma=sig, info=info,
+                z=z, X=X, P=P, Q=Q)

@@ -403,3 +403,210 @@ def test_ss_full_on_a_linear_projected_problem():
         assert inside[j] and abs(mu[j] - l) <= 1e-10
         x = X[:, j]
         assert abs(np.vdot(x, g)) / (np.linalg.norm(x) * np.linalg.norm(g)) >= 1 - 1e-10
+
+
+# ------------------------------------------- acceptance checks (eta and rho)
+# The oracle's backward error and residual decide every parity test's
+# acceptance; they are pinned to hand-computed values (tests/golden), to the
+# Rigal-Gaches characterisation of the normwise backward error, and planted
+# mutations of their source must each fail one of these pins.
+def _cplx(a):
+    a = np.asarray(a, dtype=np.float64)
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def _checker_gold():
+    with open(os.path.join(GOLD, "checker_norms.json")) as f:
+        return json.load(f)
+
+
+def _gold_sparse_problem(g):
+    A0 = np.array(g["A0"], dtype=np.float64)
+    A1 = np.array(g["A1"], dtype=np.float64)
+    pat = (A0 != 0) | (A1 != 0)
+    rows, cols = np.nonzero(pat)
+    row_ptr = np.concatenate([[0], np.cumsum(pat.sum(axis=1))]).astype(np.int64)
+    fns = [W.Fn(W.F_ONE), W.Fn(W.F_ZPOW, 1)]
+    return W.Problem("gold3", 3, row_ptr, cols.astype(np.int32), [A0[rows, cols], A1[rows, cols]], fns,
+                     W.Region(0j, 1.0, 1.0), 1, 2, np.zeros((3, 2), np.complex128))
+
+
+def _gold_dense_problem(g):
+    return W.DenseProblem("gold2", 2, np.array(g["points"], dtype=np.float64), float(g["diag"]),
+                          W.Region(0j, 1.0, 1.0), 1, 1, np.zeros((2, 1), np.complex128))
+
+
+def _checkers_match_gold():
+    g = _checker_gold()
+    ok = True
+    s = g["sparse"]
+    p = _gold_sparse_problem(s)
+    e = s["eta"]
+    eta = ORACLE_MOD.backward_error_inf(p, complex(*e["z"]), _cplx(e["X"]), _cplx(e["U"]))
+    ok &= np.allclose(eta, [c["value"] for c in e["columns"]], rtol=1e-13, atol=0)
+    for r in s["residual"]:
+        rho = ORACLE_MOD.residual(p, complex(*r["lam"]), _cplx(r["v"]))
+        ok &= abs(rho - r["value"]) <= 1e-13 * r["value"]
+    d = g["dense"]
+    q = _gold_dense_problem(d)
+    eta = ORACLE_MOD.backward_error_inf_dense(q, complex(*d["z"]), _cplx(d["eta"]["X"]), _cplx(d["eta"]["U"]))
+    ok &= abs(eta[0] - d["eta"]["value"]) <= 1e-13 * d["eta"]["value"]
+    r = d["residual"]
+    rho = ORACLE_MOD.residual_dense(q, complex(*r["lam"]), _cplx(r["v"]))
+    ok &= abs(rho - r["value"]) <= 1e-13 * r["value"]
+    return bool(ok)
+
+
+def test_acceptance_checks_match_hand_computed_values():
+    assert _checkers_match_gold()
+
+
+def _rigal_gaches_holds(T, X, U, eta):
+    """eta is the normwise backward error: the rank-one perturbation dT = eta
+    ||T|| r y^H/||r||, du = -eta ||u|| r/||r|| (y the dual vector of x, ||y||_1
+    = 1, y^H x = ||x||_inf) has relative size eta in both T and u and makes x
+    an exact solution of (T + dT) x = u + du; no smaller one can, since
+    ||r|| <= eps (||T|| ||x|| + ||u||) for any perturbation of relative size eps."""
+    Tinf = np.linalg.norm(T, np.inf)
+    for c in range(X.shape[1]):
+        x, u = X[:, c], U[:, c]
+        r = u - T @ x
+        rn = np.abs(r).max()
+        k = int(np.argmax(np.abs(x)))
+        y = np.zeros_like(x)
+        y[k] = x[k] / abs(x[k])
+        dT = eta[c] * Tinf * np.outer(r, y.conj()) / rn
+        du = -eta[c] * np.abs(u).max() * r / rn
+        if not np.isclose(np.linalg.norm(dT, np.inf), eta[c] * Tinf, rtol=1e-12):
+            return False
+        if np.abs((T + dT) @ x - (u + du)).max() > 1e-8 * rn:
+            return False
+    return True
+
+
+def _perturbed_solution(T, U, seed):
+    rng = np.random.default_rng(seed)
+    X = np.linalg.solve(T, U)
+    return X * (1.0 + 1e-4 * (rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)))
+
+
+def test_backward_error_is_the_smallest_relative_perturbation():
+    p = W.random_banded(n=60, kl=4, ku=2, N=1, L=3, seed=17)   # non-symmetric
+    z = 0.4 + 0.1j
+    T = oracle.assemble(p, z).toarray()
+    X = _perturbed_solution(T, p.U, 1)
+    assert _rigal_gaches_holds(T, X, p.U, oracle.backward_error_inf(p, z, X))
+    q = W.helmholtz_sphere(n=40, N=1, L=3, seed=9, seed_u=10)
+    z = 3.1 + 0.05j
+    T = oracle.assemble_dense(q, z)
+    X = _perturbed_solution(T, q.U, 2)
+    assert _rigal_gaches_holds(T, X, q.U, oracle.backward_error_inf_dense(q, z, X))
+
+
+def _mutated(func, old, new):
+    """A copy of an oracle function with one plausible mistake planted in its
+    source (compiled in the oracle module's namespace)."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(func))
+    assert old in src, (func.__name__, old)
+    ns = {}
+    exec(compile(src.replace(old, new, 1), "<mutant>", "exec"), ORACLE_MOD.__dict__.copy(), ns)
+    return ns[func.__name__]
+
+
+CHECKER_MUTANTS = [
+    # row sums -> column sums for ||T||_inf
+    ("backward_error_inf", "np.abs(T).sum(axis=1).max()", "np.abs(T).sum(axis=0).max()"),
+    # the ||u||_inf term dropped from the denominator
+    ("backward_error_inf", "+ np.abs(U).max(axis=0)", ""),
+    # ||x||_1 in place of ||x||_inf
+    ("backward_error_inf", "np.abs(X).max(axis=0) +", "np.abs(X).sum(axis=0) +"),
+    # ||A_i||_inf in place of ||A_i||_1
+    ("residual", "coeff_matrix(prob, i)).sum(axis=0).max()", "coeff_matrix(prob, i)).sum(axis=1).max()"),
+    # |f_i(lam)| dropped from the scale
+    ("residual", "scale += abs(eval_fn(fn, lam)) * a1", "scale += a1"),
+    # ||v||_2 dropped
+    ("residual", "(scale * np.linalg.norm(v))", "scale"),
+    # the ||u||_inf term dropped (dense)
+    ("backward_error_inf_dense", "+ np.abs(U).max(axis=0)", ""),
+    # residual in the 1-norm (dense)
+    ("residual_dense", "np.linalg.norm(T @ v)", "np.linalg.norm(T @ v, 1)"),
+    # largest entry in place of ||T||_1 (dense)
+    ("residual_dense", "np.abs(T).sum(axis=0).max()", "np.abs(T).max()"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", CHECKER_MUTANTS)
+def test_planted_checker_mistakes_fail_a_pin(monkeypatch, name, old, new):
+    monkeypatch.setattr(ORACLE_MOD, name, _mutated(getattr(ORACLE_MOD, name), old, new))
+    try:
+        gold = _checkers_match_gold()
+    except Exception:
+        gold = False
+    assert not gold, f"planted mistake in {name} ({old!r} -> {new!r}) went unnoticed"
+
+
+# ---------------------------------------------- Sylvester inertia (band LDL^T)
+def _grid_closed_form(g):
+    """Eigenvalues of K = (g+1)^2 (5-point Laplacian) on a g x g grid:
+    (g+1)^2 (4 sin^2(j pi / 2(g+1)) + 4 sin^2(k pi / 2(g+1))), 1 <= j, k <= g."""
+    j = np.arange(1, g + 1)
+    lam1 = 4.0 * np.sin(j * np.pi / (2.0 * (g + 1))) ** 2
+    return np.sort(((g + 1) ** 2 * (lam1[:, None] + lam1[None, :])).ravel())
+
+
+def _band_counts_agree(count_fn):
+    p = W.rational_grid(g=30, N=8, L=2)
+    for x in (20.0, 55.5, 100.0, 180.0, 250.0):
+        if count_fn(p, x) != oracle.negative_inertia(p, x):
+            return False
+    q = W.rational_grid(g=40, N=8, L=2, frac_e=0.0)   # E = 0: T(x) = K - x I
+    ev = _grid_closed_form(40)
+    for x in (10.0, 60.0, 123.4, 250.0):
+        if count_fn(q, x) != int(np.sum(ev < x)):
+            return False
+    s = W.loaded_string()
+    for x in (3.0, 500.0, 1e4):
+        if count_fn(s, x) != oracle.negative_inertia(s, x):
+            return False
+    return True
+
+
+def test_band_inertia_matches_dense_count_and_closed_form():
+    assert _band_counts_agree(oracle.negative_inertia_band)
+
+
+def test_bisection_recovers_the_closed_form_grid_eigenvalues():
+    q = W.rational_grid(g=30, N=8, L=2, frac_e=0.0)
+    ev = _grid_closed_form(30)
+    ev = ev[(ev > 20.0) & (ev < 180.0)]
+    bis = oracle.bisect_real_eigenvalues(q, 20.0, 180.0)
+    assert len(bis) == len(ev) > 5          # includes double eigenvalues (j, k), (k, j)
+    assert np.max(np.abs(bis - ev) / ev) < 1e-12
+
+
+@pytest.mark.parametrize("old,new", [
+    ("cj[i - j] -= lj * col[i];", "cj[i - j] -= lj * col[j];"),   # transposed operand
+    ("const double lj = col[j] / d;", "const double lj = col[j];"),  # dropped pivot division
+])
+def test_planted_inertia_mistakes_fail_a_pin(tmp_path, old, new):
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(ORACLE_MOD.__file__), "band_inertia.c")).read()
+    assert old in src
+    (tmp_path / "m.c").write_text(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-o", str(tmp_path / "m.so"), str(tmp_path / "m.c")],
+                   check=True)
+    lib = ctypes.CDLL(str(tmp_path / "m.so"))
+    lib.band_ldlt_negcount.restype = ctypes.c_int
+    lib.band_ldlt_negcount.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    saved = ORACLE_MOD._INERTIA_LIB
+    ORACLE_MOD._INERTIA_LIB = lib
+    try:
+        agree = _band_counts_agree(oracle.negative_inertia_band)
+    except ZeroDivisionError:
+        agree = False
+    finally:
+        ORACLE_MOD._INERTIA_LIB = saved
+    assert not agree, f"planted mistake {old!r} -> {new!r} went unnoticed"

@@ -7,7 +7,7 @@ the region, N, L and the seeded probe matrix U.  It contains none of the
 resolvent-sampling arithmetic (no sampling points, no solves, no projections).
 
 The problem families follow the paper's NEP classes (Section 2.1: quadratic,
-rational, square-root types) and its loaded-string example (Section 4.1), plus
+rational, square-root types) and its loaded-string example (Section 5.1), plus
 synthetic stand-ins for its FEM workloads with the shapes of the benchmark
 configurations (quadratic tridiagonal n=1000; rational 5-point grid n=g^2).
 """
@@ -24,7 +24,9 @@ import numpy as np
 #   F_INV       base = 1 / (param - z)
 #   F_SQRT      base = sqrt(z**2 - param**2)   (principal branch)
 #   F_EXP       base = exp(-param * z)
-F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP = range(6)
+#   F_TAYLOR    base = (z - shift)**power    (power a non-negative integer)
+#   F_CALLBACK  base = callback(z)           (any function the caller evaluates)
+F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP, F_TAYLOR, F_CALLBACK = range(8)
 
 
 @dataclass
@@ -32,6 +34,9 @@ class Fn:
     kind: int
     param: float = 0.0
     scale: complex = 1.0
+    power: int = 0
+    shift: complex = 0.0
+    callback: object = None   # F_CALLBACK: vectorised z -> base(z)
 
 
 @dataclass
@@ -109,7 +114,8 @@ def _shared_csr(n: int, mats: list):
 
 
 def _csr_from_dense_band(dense_list: list, kl: int, ku: int):
-    """Shared CSR holding every entry inside the (kl, ku) band (zeros kept)."""
+    """Shared CSR holding every entry inside the (kl, ku) band (zeros kept);
+    real or complex values as the matrices are."""
     n = dense_list[0].shape[0]
     rows, cols = [], []
     for i in range(n):
@@ -121,7 +127,8 @@ def _csr_from_dense_band(dense_list: list, kl: int, ku: int):
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.add.at(row_ptr, rows + 1, 1)
     row_ptr = np.cumsum(row_ptr)
-    values = [np.ascontiguousarray(D[rows, cols], dtype=np.float64) for D in dense_list]
+    values = [np.ascontiguousarray(D[rows, cols], dtype=np.complex128 if np.iscomplexobj(D) else np.float64)
+              for D in dense_list]
     return row_ptr, cols.astype(np.int32), values
 
 
@@ -207,11 +214,11 @@ def rational_grid(g: int = 200, N: int = 64, L: int = 32, sigma: float = 300.0,
 
 def loaded_string(n: int = 400, N: int = 100, L: int = 1, kn_last: float = 1.0,
                   seed_u: int = 7001, name: str = "string") -> Problem:
-    """Loaded string of Section 4.1: T(z) = K_s + z/(z-1) e_n e_n^T - z M.
+    """Loaded string of Section 5.1: T(z) = K_s + z/(z-1) e_n e_n^T - z M.
     K_s = n*tridiag(-1,2,-1) with K_s[n-1,n-1] = n*kn_last, M = tridiag(1,4,1)/(6n)
     with M[n-1,n-1] = 2/(6n).  Sampling points: N Chebyshev points of the first
     kind in [3, 1e4]; contour for the projected problem: ellipse centre 5001.5,
-    a = 4998.5, b = 0.1a (Section 4.2)."""
+    a = 4998.5, b = 0.1a (Section 5.2)."""
     K = {k: v * n for k, v in _tridiag(n, -1.0, 2.0, -1.0, last=kn_last).items()}
     M = {k: v / (6.0 * n) for k, v in _tridiag(n, 1.0, 4.0, 1.0, last=2.0).items()}
     E = {(n - 1, n - 1): 1.0}
@@ -258,7 +265,8 @@ def hidden_diagonal(diags: list, fns: list, region: Region, N: int, L: int,
     n = len(diags[0])
     G1 = givens_layers(n, layers, seed)
     G2 = givens_layers(n, layers, seed + 100)
-    dense = [G1.T @ np.diag(np.asarray(d, dtype=np.float64)) @ G2 for d in diags]
+    dt = np.complex128 if any(np.iscomplexobj(d) for d in diags) else np.float64
+    dense = [G1.T @ np.diag(np.asarray(d, dtype=dt)) @ G2 for d in diags]
     w = 2 * layers
     row_ptr, col_idx, values = _csr_from_dense_band(dense, w, w)
     return Problem(name, n, row_ptr, col_idx, values, fns, region, N, L,
@@ -332,6 +340,23 @@ def diag_inv(n: int = 240, seed: int = 61, N: int = 32, L: int = 4, sigma: float
     fns = [Fn(F_ONE), Fn(F_ZPOW, 1, -1.0), Fn(F_INV, sigma)]
     return hidden_diagonal([k, m, e], fns, Region(2.0 + 0.0j, 1.5, 0.5), N, L,
                            layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_inv")
+
+
+def diag_quadratic_complex(n: int = 240, seed: int = 71, N: int = 32, L: int = 4,
+                           layers: int = 3) -> Problem:
+    """Decoupled quadratics k_r + z c_r + z^2 m_r with complex k, c, m (roots
+    placed as in diag_quadratic, then all three coefficients multiplied by a
+    seeded unit phase per row): a banded NEP with complex coefficient values."""
+    rng = np.random.default_rng(seed)
+    re = rng.uniform(-6.0, 6.0, n)
+    im = rng.uniform(0.05, 8.0, n)
+    m = rng.uniform(0.5, 2.0, n)
+    c = -2.0 * re * m
+    k = m * (re ** 2 + im ** 2)
+    ph = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, n))
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1), Fn(F_ZPOW, 2)]
+    return hidden_diagonal([k * ph, c * ph, m * ph], fns, Region(0.6j - 0.2, 1.0, 0.8), N, L,
+                           layers=layers, seed=seed + 1, seed_u=seed + 2, name="diag_quadratic_complex")
 
 
 def random_banded(n: int = 300, kl: int = 7, ku: int = 7, m: int = 3, seed: int = 41,
@@ -473,3 +498,52 @@ def batch_uneven(count: int = 256, seed: int = 4000, dense_n=(256, 2048), grid_g
                                               seed_u=seed + 10001 + i, name="c3_grid")))
     order = rng.permutation(count)
     return [out[k] for k in order]
+
+
+# ----------------------------------------------------------------------------
+# general dense terms: T(z) = sum_i f_i(z) A_i with caller-supplied dense A_i
+# ----------------------------------------------------------------------------
+
+@dataclass
+class DenseTermsProblem:
+    """T(z) = sum_i f_i(z) A_i with dense complex A_i (n x n)."""
+    name: str
+    n: int
+    As: list             # m complex128 [n, n]
+    fns: list            # m Fn
+    region: Region
+    N: int
+    L: int
+    U: np.ndarray        # complex128 [n, L], Fortran order
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return len(self.As)
+
+
+def random_unitary(n: int, seed: int) -> np.ndarray:
+    """Haar-like unitary: QR of a complex Gaussian matrix with the phases of
+    R's diagonal moved into Q."""
+    rng = np.random.default_rng(seed)
+    Z = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    Qm, R = np.linalg.qr(Z)
+    d = np.diag(R)
+    return Qm * (d / np.abs(d))
+
+
+def dense_hidden_quadratic(n: int = 200, seed: int = 81, N: int = 32, L: int = 4) -> DenseTermsProblem:
+    """Decoupled quadratics k_r + z c_r + z^2 m_r (as diag_quadratic) hidden by
+    one seeded unitary W: A_i = W diag(d_i) W^H, dense and complex; the
+    eigenvalues are the scalar roots."""
+    rng = np.random.default_rng(seed)
+    re = rng.uniform(-6.0, 6.0, n)
+    im = rng.uniform(0.05, 8.0, n)
+    m = rng.uniform(0.5, 2.0, n)
+    c = -2.0 * re * m
+    k = m * (re ** 2 + im ** 2)
+    Wm = random_unitary(n, seed + 1)
+    As = [np.asfortranarray((Wm * d[None, :]) @ Wm.conj().T) for d in (k, c, m)]
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 1), Fn(F_ZPOW, 2)]
+    return DenseTermsProblem("dense_hidden_quadratic", n, As, fns, Region(0.6j - 0.2, 1.0, 0.8), N, L,
+                             probe(n, L, seed + 2), meta=dict(diags=[k, c, m], seed=seed))
