@@ -9,7 +9,7 @@
  *
  * where the A_i are real n x n matrices sharing one sparse (banded) pattern
  * and the f_i are scalar functions.  The steps are those of the RSRR
- * algorithm in Section 3.3:
+ * algorithm in Section 4.3:
  *
  *   rsrr_create   step 1: sampling points z_j, coefficient table f_i(z_j),
  *                 device copies of the pattern and values.
@@ -17,11 +17,11 @@
  *                 banded LU with partial pivoting, triangular solves and FP64
  *                 iterative refinement), all on the GPU.
  *   rsrr_project  steps 3-4 (GPU part): S = [X_0 ... X_{N-1}] with unit-norm
- *                 columns (Section 3.2, last paragraph), orthonormal basis Q of
- *                 its dominant singular subspace (Section 3.3 step 3), and the
- *                 projected coefficients P_i = Q^H A_i Q (Section 3, T_Q).
+ *                 columns (Section 4.2, last paragraph), orthonormal basis Q of
+ *                 its dominant singular subspace (Section 4.3 step 3), and the
+ *                 projected coefficients P_i = Q^H A_i Q (Section 4, T_Q).
  *   rsrr_solve    steps 4-5 (host part): the projected NEP by SS-FULL
- *                 (Section 2.3 with U = I), eigenvectors v = Q g and their
+ *                 (Section 3.3 with U = I), eigenvectors v = Q g and their
  *                 residuals.
  *
  * Conventions.
@@ -62,70 +62,103 @@ typedef enum {
     RSRR_ETIMEOUT = -5,  /* a bounded device-side wait ran out */
     RSRR_ECUDA = -6,     /* a CUDA runtime error */
     RSRR_ESTATE = -7,    /* call out of order (e.g. rsrr_project before rsrr_sample) */
-    RSRR_WGAP = 1        /* warning: the gap test g_max >= tol_gap failed (Section 2.3) */
+    RSRR_WGAP = 1        /* warning: the gap test g_max >= tol_gap failed (Section 3.3) */
 } rsrr_status;
 
-/* Scalar coefficient functions f(z) = scale * base(z; param) (families of
- * Section 2.1; EXP covers delay problems):
+/* Scalar coefficient functions f(z) = scale * base(z) (the families of
+ * Section 2.1; EXP covers delay problems, TAYLOR the power basis of an
+ * expanded T, CALLBACK any f the caller can evaluate, Section 4.3 notes that
+ * the method only needs T at the sampling points):
  *   RSRR_F_ONE       base = 1
  *   RSRR_F_ZPOW      base = z^param, param a non-negative integer
  *   RSRR_F_RATIONAL  base = z / (z - param)
  *   RSRR_F_INV       base = 1 / (param - z)
  *   RSRR_F_SQRT      base = sqrt(z^2 - param^2), principal branch
- *   RSRR_F_EXP       base = exp(-param z)                                   */
+ *   RSRR_F_EXP       base = exp(-param z)
+ *   RSRR_F_TAYLOR    base = (z - shift)^power, power a non-negative integer
+ *   RSRR_F_CALLBACK  base = the value rsrr_nep.callback returns for this term
+ *                    (it is asked for whole arrays of points at once)        */
 enum {
     RSRR_F_ONE = 0,
     RSRR_F_ZPOW = 1,
     RSRR_F_RATIONAL = 2,
     RSRR_F_INV = 3,
     RSRR_F_SQRT = 4,
-    RSRR_F_EXP = 5
+    RSRR_F_EXP = 5,
+    RSRR_F_TAYLOR = 6,
+    RSRR_F_CALLBACK = 7
 };
 
 typedef struct {
     int32_t kind;
-    int32_t reserved;
+    int32_t power;     /* RSRR_F_TAYLOR: the exponent (0 .. 64) */
     double param;
     rsrr_c128 scale;
+    rsrr_c128 shift;   /* RSRR_F_TAYLOR: the expansion point */
 } rsrr_fn;
+
+/* Host callback for RSRR_F_CALLBACK terms: writes base_term(z[q]) into out[q]
+ * for q < count.  It is called by rsrr_create / rsrr_describe /
+ * rsrr_estimate_bytes (at the sampling points), rsrr_add_points (at the new
+ * points) and rsrr_solve (at the quadrature nodes and at the eigenvalues),
+ * on the calling thread or, for the request server, on a worker thread.  It
+ * and `user` must stay valid until the handle is destroyed; it must return
+ * finite values at every point it is asked for. */
+typedef void (*rsrr_fn_callback)(int32_t term, const rsrr_c128 *z, int64_t count, rsrr_c128 *out,
+                                 void *user);
 
 #define RSRR_MAX_TERMS 8
 
-/* The NEP.  Two kinds:
+/* The NEP.  Three kinds:
  *
  * RSRR_NEP_SPARSE: T(z) = sum_{i<m} fn[i](z) A_i.  All A_i share one CSR
  * pattern (row_ptr, col_idx; columns need not be sorted; duplicates are not
- * allowed); their real values are stored term-major: A_i's value for pattern
- * entry e is values[i * nnz + e], nnz = row_ptr[n].  The half-bandwidths kl,
- * ku are detected from the pattern (kl <= 480) and the band path is used.
+ * allowed); their values are stored term-major: A_i's value for pattern
+ * entry e is values[i * nnz + e], nnz = row_ptr[n], real doubles, or
+ * rsrr_c128 when values_complex is nonzero (values then points to 2 m nnz
+ * doubles).  The half-bandwidths kl, ku are detected from the pattern
+ * (kl <= 480) and the band path is used.  A term with complex values is held
+ * as two real terms, Re A_i with fn[i] and Im A_i with i fn[i]; the
+ * statistics and rsrr_get_projected count terms that way.
  *
  * RSRR_NEP_HELMHOLTZ: the dense Nystrom single-layer kernel of Section 2.1,
  * T(z)_ij = exp(i z r_ij) / (4 pi r_ij) for i != j and T_ii = diag, with
  * r_ij the distances between the n points (points[3i..3i+2], row major);
  * m, fn and the CSR fields are ignored.  The dense path is used, and the
  * projection expands T in a Taylor series about the region centre
- * (Section 5.2 interpolates T for the same purpose).
+ * (Section 6 interpolates T for the same purpose).
+ *
+ * RSRR_NEP_DENSE: T(z) = sum_{i<m} fn[i](z) A_i with caller-supplied dense
+ * complex A_i (dense[i]: n x n, column major, n <= 32768) -- a general
+ * "black-box" T such as the BEM matrices of Section 2.1 with their
+ * dependence on z separated into known functions.  The dense path is used;
+ * P_i = Q^H A_i Q.
  *
  * All arrays are host memory and are copied by rsrr_create. */
-enum { RSRR_NEP_SPARSE = 0, RSRR_NEP_HELMHOLTZ = 1 };
+enum { RSRR_NEP_SPARSE = 0, RSRR_NEP_HELMHOLTZ = 1, RSRR_NEP_DENSE = 2 };
 
 typedef struct {
     int64_t n;
-    int32_t m;    /* 1 <= m <= RSRR_MAX_TERMS (sparse kind) */
-    int32_t kind; /* RSRR_NEP_SPARSE or RSRR_NEP_HELMHOLTZ */
+    int32_t m;    /* 1 <= m <= RSRR_MAX_TERMS (sparse and dense kinds) */
+    int32_t kind; /* RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ or RSRR_NEP_DENSE */
     const int64_t *row_ptr; /* host, n + 1 */
     const int32_t *col_idx; /* host, nnz */
-    const double *values;   /* host, m * nnz */
+    const double *values;   /* host, m * nnz (real) or 2 * m * nnz (values_complex) */
     rsrr_fn fn[RSRR_MAX_TERMS];
     const double *points;   /* host, 3n (Helmholtz kind) */
     double diag;            /* T_ii (Helmholtz kind) */
+    int32_t values_complex; /* sparse kind: values are rsrr_c128 */
+    int32_t reserved;
+    const rsrr_c128 *const *dense; /* host, m pointers to n x n column-major A_i (dense kind) */
+    rsrr_fn_callback callback;     /* for RSRR_F_CALLBACK terms */
+    void *callback_user;           /* passed to callback */
 } rsrr_nep;
 
 /* Region.  The ellipse phi(t) = center + a cos t + i b sin t is the contour
  * of the projected solve and defines "inside".  Sampling points are the
- * N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Section 4.1) for
+ * N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Section 5.1) for
  * RSRR_REGION_ELLIPSE, or the N given host points for RSRR_REGION_POINTS
- * (the rational interpolation approach lets them lie anywhere, Section 2.2). */
+ * (the rational interpolation approach lets them lie anywhere, Section 3.3). */
 enum { RSRR_REGION_ELLIPSE = 0, RSRR_REGION_POINTS = 1 };
 
 typedef struct {
@@ -147,7 +180,7 @@ typedef struct {
 enum { RSRR_PREC_FP64 = 0, RSRR_PREC_MIXED = 1 };
 
 /* Arithmetic of the projection's dense complex products (Gram matrices of S,
- * Q^H R, R W, Q^H A_i Q; Section 3.3's orthonormalisation and projection).
+ * Q^H R, R W, Q^H A_i Q; Section 4.3's orthonormalisation and projection).
  *   RSRR_GEMM_FP64   native FP64 fused multiply-adds.
  *   RSRR_GEMM_OZAKI  FP64-accurate products on the bf16 tensor cores: both
  *                    operands are scaled per row / column by powers of two,
@@ -170,7 +203,21 @@ enum { RSRR_GEMM_AUTO = 0, RSRR_GEMM_FP64 = 1, RSRR_GEMM_OZAKI = 2, RSRR_GEMM_OZ
  * instead of a cluster of two CTAs per point (the second CTA updates most of
  * the trailing window while the first factors the next panel); the factors
  * are bitwise the same, the flag exists for comparison. */
-enum { RSRR_FLAG_PLAIN_SOLVE = 1, RSRR_FLAG_ONE_CTA_LU = 2 };
+/* RSRR_FLAG_INJECT_TIMEOUT: failure detection without a GPU fault.
+ * rsrr_sample also runs one bounded device wait on a barrier that nothing
+ * completes (a few thousand polls); the wait runs out and is counted in this
+ * handle's own status word, exactly like a timed-out wait of its tensor-core
+ * products, so rsrr_solve returns RSRR_ETIMEOUT.  Nothing else changes.  It
+ * exists to test that a timeout stays with the request that met it. */
+/* RSRR_FLAG_SIMT_DENSE_UPDATE: the trailing updates of the dense complex64 LU
+ * (Helmholtz and dense kinds, mixed precision) on FP32 FMAs instead of the
+ * tensor cores (tcgen05, 3xTF32); kept for comparison. */
+enum {
+    RSRR_FLAG_PLAIN_SOLVE = 1,
+    RSRR_FLAG_ONE_CTA_LU = 2,
+    RSRR_FLAG_INJECT_TIMEOUT = 4,
+    RSRR_FLAG_SIMT_DENSE_UPDATE = 8
+};
 
 typedef struct {
     int32_t precision;   /* RSRR_PREC_MIXED by default */
@@ -178,7 +225,7 @@ typedef struct {
     double eta_tol;      /* default 1e-10 */
     double delta;        /* SVD truncation of S relative to sigma_1, paper's 1e-14 */
     double delta_floor;  /* resolution floor of the Gram-based SVD, default 1e-12 */
-    double tol_gap;      /* gap test of SS-FULL, default 1e3 (Section 2.3) */
+    double tol_gap;      /* gap test of SS-FULL, default 1e3 (Section 3.3) */
     double res_tol;      /* acceptance of an eigenpair by residual, default 1e-6 */
     int32_t NQ;          /* SS-FULL quadrature points, default 500 */
     int32_t KQ;          /* SS-FULL moments, default 2 */
@@ -187,6 +234,10 @@ typedef struct {
                             caller's stream; times appear in rsrr_stats.stage_ms */
     int32_t gemm;        /* RSRR_GEMM_AUTO by default */
     int32_t flags;       /* RSRR_FLAG_* bits, 0 by default */
+    uint64_t seed;       /* seed of the default probe U (complex normal entries from
+                            a splitmix64 stream); rsrr_set_probe replaces U */
+    int64_t mem_budget_bytes; /* > 0: rsrr_create refuses (ENOMEM) a handle whose
+                            rsrr_estimate_bytes exceed it; 0 (default): no limit */
 } rsrr_opts;
 
 typedef struct rsrr_handle rsrr_t;
@@ -240,7 +291,7 @@ void rsrr_opts_default(rsrr_opts *o);
 rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t N,
                         int32_t L, const rsrr_opts *opts, rsrr_t **out);
 
-/* Sets the probe matrix U (n x L, column major, Section 3.3 step 1).  U is
+/* Sets the probe matrix U (n x L, column major, Section 4.3 step 1).  U is
  * host memory if on_device == 0, else device memory; it is copied (async on
  * `stream` for device input, synchronous for host input). */
 rsrr_status rsrr_set_probe(rsrr_t *h, const rsrr_c128 *U, int32_t on_device, void *stream);
@@ -249,6 +300,20 @@ rsrr_status rsrr_set_probe(rsrr_t *h, const rsrr_c128 *U, int32_t on_device, voi
  * The outcome (ESINGULAR, ENOCONV) is known after the stream is synchronised
  * and is returned by rsrr_get_stats / rsrr_check. */
 rsrr_status rsrr_sample(rsrr_t *h, void *stream);
+
+/* Two-stage sampling (Section 5.4): appends `count` sampling points z_new
+ * (host) to the handle -- typically the eigenvalues of a first rsrr_solve,
+ * where the rational interpolation approach lets sampling points sit close to
+ * eigenvalues -- and computes X_j = T(z_j)^{-1} U for the new points only,
+ * with the same probe U and precision, asynchronously on `stream`.  The
+ * samples of the earlier points stay resident and unchanged (bit for bit);
+ * rsrr_project and rsrr_solve then use all N + count points.  The handle's
+ * per-point buffers are reallocated for the larger N (the call waits for the
+ * handle's earlier work first); rsrr_get_points, rsrr_get_samples and the
+ * statistics report all points.  Requires a previous rsrr_sample.  Errors:
+ * EINVAL (count < 1, a point not finite, f not finite there), ESTATE, ENOMEM,
+ * ECUDA; the outcome of the new points' sampling is reported by rsrr_check. */
+rsrr_status rsrr_add_points(rsrr_t *h, const rsrr_c128 *z_new, int32_t count, void *stream);
 
 /* Waits for `stream` and reports the outcome of the last rsrr_sample:
  * OK, ESINGULAR (a zero pivot; stats.singular_point names the point) or
@@ -267,7 +332,12 @@ rsrr_status rsrr_project(rsrr_t *h, void *stream);
  * quadrature nodes on the GPU (batched complex128 LU), the Hankel SVD and
  * the small eigenproblem on the host -- then v = Q g and residuals on the GPU.
  * Returns OK or WGAP (gap test failed; results still filled); ETIMEOUT if a
- * bounded wait of a tensor-core product kernel ran out since rsrr_sample. */
+ * bounded wait of one of this handle's tensor-core product kernels ran out
+ * since rsrr_sample (each handle counts its own in a device status word, so a
+ * timeout in another handle or request never shows here).  After ETIMEOUT
+ * the results of later calls on the same CUDA context are unverified: the
+ * kernel that gave up stopped issuing work, but copies or MMAs it had issued
+ * may not have finished within its bounded drain. */
 rsrr_status rsrr_solve(rsrr_t *h, rsrr_result *out);
 
 /* Copies S = [X_0 ... X_{N-1}] (n x N*L, column major, before normalisation)
@@ -292,6 +362,14 @@ rsrr_status rsrr_get_projected(rsrr_t *h, rsrr_c128 *dst, int32_t dst_on_device,
 /* Copies the N sampling points (host). */
 rsrr_status rsrr_get_points(rsrr_t *h, rsrr_c128 *dst);
 
+/* Copies the result of the last rsrr_solve into caller-owned host buffers:
+ * lam (count), res (count) and V (n x count, column major); any of them may
+ * be NULL.  `capacity` is the number of eigenpairs the buffers hold; EINVAL
+ * if it is below the count (the count is written to *count first, when
+ * count is not NULL).  ESTATE before the first rsrr_solve. */
+rsrr_status rsrr_copy_result(rsrr_t *h, int32_t capacity, int32_t *count, rsrr_c128 *lam,
+                             double *res, rsrr_c128 *V);
+
 /* Fills the statistics of the handle (synchronises the handle's work). */
 rsrr_status rsrr_get_stats(rsrr_t *h, rsrr_stats *out);
 
@@ -312,27 +390,30 @@ void rsrr_destroy(rsrr_t *h);
  * allocator.  Nothing is allocated: the work space comes from a fixed 32 MiB
  * device array inside the library, which every GPU that loads the library
  * holds until the process exits.
- *   n, kl, ku  order and half-bandwidths of T (kl <= 480)
+ *   n, kl, ku  order and half-bandwidths of T (kl <= 480, kl and ku <= n - 1)
  *   band       device, (kl+ku+1) x n, LAPACK general band layout:
  *              T(i,j) at band[(ku + i - j) + j*(kl+ku+1)]
  *   L, U       device, n x L right-hand sides (column major); not modified
  *   X          device, n x L solution (column major); may not alias U
  *   stream     work is queued on it; the call waits for it before returning
  * Limit: 16*n*(2kl+ku+16) + 32*n*16 + 4*n bytes (each rounded up to 256) must
- * fit in 32 MiB, else RSRR_EINVAL with the needed size in the message.
+ * fit in 32 MiB, else RSRR_EINVAL with the needed size in the message; bands
+ * whose solve would not fit in shared memory are refused the same way.  Every
+ * check is made before anything is launched.
  * Returns OK, EINVAL, ESINGULAR (an exactly zero pivot) or ECUDA; the message
  * is in rsrr_last_error(NULL).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and overwrites
- * all of it that it uses (no state carries over), so calls that overlap on
- * the GPU -- from several host threads or on several streams -- race: issue
- * them one after another. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest
+ * of the process; make that first call before any stream capture.  The entry
+ * point does not survive a cudaDeviceReset.  Every call shares the one array
+ * and overwrites all of it that it uses (no state carries over), so calls that
+ * overlap on the GPU -- from several host threads or on several streams --
+ * race: issue them one after another. */
 rsrr_status rsrr_solve_band_noalloc(int64_t n, int32_t kl, int32_t ku, const rsrr_c128 *band,
                                     int32_t L, const rsrr_c128 *U, rsrr_c128 *X, void *stream);
 
 /* One dense complex product C = alpha op(A) B + beta C on the device, by the
- * method the projection uses (Section 3.3's Gram matrices and Q^H A_i Q are
+ * method the projection uses (Section 4.3's Gram matrices and Q^H A_i Q are
  * such products); exposed so that callers and tests can use or check it alone.
  *   M, N, K    op(A) is M x K, B is K x N, C is M x N
  *   conjA      0: op(A) = A (M x K),  1: op(A) = A^H (A is K x M)
@@ -357,15 +438,16 @@ rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA, const rsr
 /* Failure detection without a GPU fault: one thread waits, with the bounded
  * mbarrier wait of the tensor-core product kernel, on a barrier that nothing
  * completes, giving up after `tries` polls (1 .. 2^20).  The wait is counted
- * in the same device counter that rsrr_zgemm and rsrr_solve read (rsrr_solve
- * returns ETIMEOUT when a wait of the sample or project products ran out).
+ * in a status word of this call (allocated and freed inside it), the same way
+ * a wait of a product kernel is counted in its caller's word: rsrr_zgemm's
+ * own, or the handle's for rsrr_sample / rsrr_project (read by rsrr_solve).
  * Returns ETIMEOUT when the wait ran out and was counted, with the CUDA
  * context still usable; OK (with a message) if it was not counted; EINVAL or
  * ECUDA otherwise.  Waits for `stream` before and after. */
 rsrr_status rsrr_check_wait_timeout(int32_t tries, void *stream);
 
 /* Host-only view of what rsrr_create prepares, without touching the GPU:
- * the N sampling points z_j (step 1; Section 4.1 trapezoid nodes on the
+ * the N sampling points z_j (step 1; Section 5.1 trapezoid nodes on the
  * ellipse, or the explicit points), the coefficient table f_i(z_j) (sparse
  * kind: N x m, point-major, coef[j * m + i]; not written for the Helmholtz
  * kind) and the half-bandwidths kl, ku detected from the pattern (0 for the

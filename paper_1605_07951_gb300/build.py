@@ -24,6 +24,7 @@ UNITS = [
     ("ssfull_host.cpp", ["-x", "cu", "-Xcompiler", "-fcx-fortran-rules"], "ssfull_host.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("dense.cu", [], "dense.o"),
+    ("dense_tc.cu", [], "dense_tc.o"),
     ("ozaki.cu", [], "ozaki.o"),
     ("band_solve2.cu", [], "band_solve2.o"),
     ("server.cu", [], "server.o"),

@@ -1,5 +1,5 @@
 // Host side of the C ABI declared in include/rsrr.h: descriptor validation,
-// sampling points and coefficient table (RSRR step 1, Section 3.3), device
+// sampling points and coefficient table (RSRR step 1, Section 4.3), device
 // buffers, and the orchestration of the sampling kernels (step 2).
 #include <algorithm>
 #include <cmath>
@@ -36,15 +36,22 @@ cplx eval_fn_host(const rsrr_fn &f, cplx z) {
         case RSRR_F_INV: base = 1.0 / (f.param - z); break;
         case RSRR_F_SQRT: base = std::sqrt(z * z - f.param * f.param); break;
         case RSRR_F_EXP: base = std::exp(-f.param * z); break;
-        default: base = 0.0;
+        case RSRR_F_TAYLOR: {
+            base = 1.0;
+            const cplx d = z - cplx(f.shift.re, f.shift.im);
+            for (int q = 0; q < f.power; ++q) base *= d;
+            break;
+        }
+        default: base = cplx(NAN, NAN);  // callbacks are evaluated by Handle::eval_terms
     }
     return cplx(f.scale.re, f.scale.im) * base;
 }
 
-// complex normal entries (g1 + i g2)/sqrt(2) from splitmix64 + Box-Muller
-void default_probe(std::vector<double2> &U, size_t count) {
+// complex normal entries (g1 + i g2)/sqrt(2) from splitmix64 + Box-Muller;
+// seed 0 is the library's historical default stream
+void default_probe(std::vector<double2> &U, size_t count, uint64_t seed) {
     U.resize(count);
-    uint64_t st = 0x9E3779B97F4A7C15ull;
+    uint64_t st = 0x9E3779B97F4A7C15ull + seed * 0xD1B54A32D192ED03ull;
     auto next = [&st]() {
         uint64_t z = (st += 0x9E3779B97F4A7C15ull);
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -56,6 +63,39 @@ void default_probe(std::vector<double2> &U, size_t count) {
         const double r = std::sqrt(-2.0 * std::log(next())), t = 2.0 * M_PI * next();
         U[q] = make_double2(r * std::cos(t) / std::sqrt(2.0), r * std::sin(t) / std::sqrt(2.0));
     }
+}
+
+rsrr_status Handle::eval_terms(const cplx *zz, int64_t count, std::vector<cplx> &out) {
+    const int mt = (int)fn.size();
+    out.assign((size_t)count * mt, cplx(0.0, 0.0));
+    std::vector<rsrr_c128> zin, val;
+    for (int t = 0; t < mt; ++t) {
+        const rsrr_fn &f = fn[t];
+        if (f.kind == RSRR_F_CALLBACK) {
+            if (!cb) return fail(RSRR_EINVAL, "callback term without a callback");
+            if (zin.empty()) {
+                zin.resize(count);
+                for (int64_t q = 0; q < count; ++q) zin[q] = rsrr_c128{zz[q].real(), zz[q].imag()};
+            }
+            val.assign(count, rsrr_c128{NAN, NAN});
+            cb(fn_src[t], zin.data(), count, val.data(), cb_user);
+            const cplx sc(f.scale.re, f.scale.im);
+            for (int64_t q = 0; q < count; ++q) out[(size_t)q * mt + t] = sc * cplx(val[q].re, val[q].im);
+        } else {
+            for (int64_t q = 0; q < count; ++q) out[(size_t)q * mt + t] = eval_fn_host(f, zz[q]);
+        }
+    }
+    for (const cplx &v : out)
+        if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+            return fail(RSRR_EINVAL, "f_i is not finite at a point where it is needed");
+    return RSRR_OK;
+}
+
+double Handle::residual_scale(const cplx *f_held) const {
+    double scale = 0.0;
+    for (size_t t = 0; t < fn.size(); ++t)
+        if (!fn_imag[t]) scale += std::abs(f_held[t]) * a1[fn_src[t]];  // |i f_u| = |f_u|: count once
+    return scale;
 }
 
 rsrr_status Handle::fail(rsrr_status st, const char *what, cudaError_t e) {
@@ -181,6 +221,17 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
     Handle *h = nullptr;
     rsrr_status st = rsrr::prepare(nep, region, N, L, opts, &h);
     if (st != RSRR_OK) return st;
+    if (h->opts.mem_budget_bytes > 0) {
+        const size_t need = h->estimate_bytes();
+        if (need > (size_t)h->opts.mem_budget_bytes) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "rsrr_create: the handle needs %zu device bytes, mem_budget_bytes is %lld",
+                     need, (long long)h->opts.mem_budget_bytes);
+            rsrr::thread_error() = buf;
+            delete h;
+            return RSRR_ENOMEM;
+        }
+    }
     st = h->allocate();
     if (st != RSRR_OK) {
         rsrr::thread_error() = h->err;
@@ -211,7 +262,7 @@ rsrr_status rsrr_describe(const rsrr_nep *nep, const rsrr_region *region, int32_
     if (st != RSRR_OK) return st;
     if (z)
         for (int j = 0; j < h->N; ++j) z[j] = rsrr_c128{h->z[j].real(), h->z[j].imag()};
-    if (coef && !h->dense)
+    if (coef && (!h->dense || h->dense_terms))
         for (size_t e = 0; e < h->h_coef.size(); ++e) coef[e] = rsrr_c128{h->h_coef[e].x, h->h_coef[e].y};
     if (kl) *kl = h->dense ? 0 : h->kl;
     if (ku) *ku = h->dense ? 0 : h->ku;
@@ -223,6 +274,85 @@ rsrr_status rsrr_describe(const rsrr_nep *nep, const rsrr_region *region, int32_
 
 namespace rsrr {
 
+static rsrr_status check_fns(const rsrr_nep *nep) {
+    for (int i = 0; i < nep->m; ++i) {
+        const rsrr_fn &f = nep->fn[i];
+        if (f.kind < RSRR_F_ONE || f.kind > RSRR_F_CALLBACK) return create_fail("rsrr_create: bad fn kind");
+        if (f.kind == RSRR_F_ZPOW && (f.param < 0 || f.param != std::floor(f.param) || f.param > 64))
+            return create_fail("rsrr_create: ZPOW needs a small non-negative integer");
+        if (f.kind == RSRR_F_TAYLOR && (f.power < 0 || f.power > 64))
+            return create_fail("rsrr_create: TAYLOR power out of range (0 .. 64)");
+        if (f.kind == RSRR_F_CALLBACK && !nep->callback)
+            return create_fail("rsrr_create: CALLBACK term without nep->callback");
+    }
+    return RSRR_OK;
+}
+
+static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts) {
+    if (!(region->a > 0.0) || !(region->b > 0.0))
+        return create_fail("rsrr_create: ellipse semi-axes must be > 0");
+    if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS)
+        return create_fail("rsrr_create: unknown region kind");
+    if (region->kind == RSRR_REGION_POINTS && !region->points)
+        return create_fail("rsrr_create: points region without points");
+    const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
+    if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
+        return create_fail("rsrr_create: unknown precision");
+    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI_MMA))
+        return create_fail("rsrr_create: unknown gemm method");
+    if (opts && opts->mem_budget_bytes < 0) return create_fail("rsrr_create: negative mem_budget_bytes");
+    return RSRR_OK;
+}
+
+// step 1: the sampling points, trapezoid nodes on the ellipse (Eq. 58,
+// Section 5.1) or the explicit points (any points, Section 3.3)
+static void fill_points(Handle *h, const rsrr_region *region, int N) {
+    h->z.resize(N);
+    for (int j = 0; j < N; ++j) {
+        if (region->kind == RSRR_REGION_POINTS) {
+            h->z[j] = cplx(region->points[j].re, region->points[j].im);
+        } else {
+            const double al = 2.0 * M_PI * (j + 0.5) / N;
+            h->z[j] = cplx(region->center.re + region->a * std::cos(al),
+                           region->center.im + region->b * std::sin(al));
+        }
+    }
+}
+
+// the coefficient table f_i(z_j) of the held terms, N x m point-major
+static rsrr_status fill_coef(Handle *h) {
+    std::vector<cplx> f;
+    rsrr_status st = h->eval_terms(h->z.data(), h->N, f);
+    if (st != RSRR_OK) {
+        thread_error() = "rsrr_create: " + h->err;
+        return st;
+    }
+    h->h_coef.resize(f.size());
+    for (size_t e = 0; e < f.size(); ++e) h->h_coef[e] = make_double2(f[e].real(), f[e].imag());
+    return RSRR_OK;
+}
+
+static Handle *new_handle(const rsrr_nep *nep, const rsrr_region *region, int N, int L,
+                          const rsrr_opts *opts) {
+    Handle *h = new (std::nothrow) Handle();
+    if (!h) return nullptr;
+    if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);
+    h->seed = h->opts.seed;
+    h->n = nep->n;
+    h->N = N;
+    h->L = L;
+    h->region = *region;
+    h->region.points = nullptr;
+    h->cb = nep->callback;
+    h->cb_user = nep->callback_user;
+    return h;
+}
+
+rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                          const rsrr_opts *opts, Handle **out);
+rsrr_status prepare_dense_terms(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                                const rsrr_opts *opts, Handle **out);
+
 rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
                     const rsrr_opts *opts, Handle **out) {
     *out = nullptr;
@@ -230,24 +360,16 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
     if (!nep || !region) return create_fail("rsrr_create: nep or region is NULL");
     if (nep->n < 1 || nep->n > (int64_t)1 << 30) return create_fail("rsrr_create: n out of range");
     if (N < 1 || L < 1) return create_fail("rsrr_create: N and L must be >= 1");
-    if (nep->kind != RSRR_NEP_SPARSE && nep->kind != RSRR_NEP_HELMHOLTZ)
+    if (nep->kind != RSRR_NEP_SPARSE && nep->kind != RSRR_NEP_HELMHOLTZ && nep->kind != RSRR_NEP_DENSE)
         return create_fail("rsrr_create: unknown NEP kind");
+    rsrr_status cst = check_common(region, opts);
+    if (cst != RSRR_OK) return cst;
     if (nep->kind == RSRR_NEP_HELMHOLTZ) return rsrr::prepare_dense(nep, region, N, L, opts, out);
     if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
+    if ((cst = check_fns(nep)) != RSRR_OK) return cst;
+    if (nep->kind == RSRR_NEP_DENSE) return rsrr::prepare_dense_terms(nep, region, N, L, opts, out);
     if (!nep->row_ptr || !nep->col_idx || !nep->values)
         return create_fail("rsrr_create: pattern or values NULL");
-    if (!(region->a > 0.0) || !(region->b > 0.0))
-        return create_fail("rsrr_create: ellipse semi-axes must be > 0");
-    if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS)
-        return create_fail("rsrr_create: unknown region kind");
-    if (region->kind == RSRR_REGION_POINTS && !region->points)
-        return create_fail("rsrr_create: points region without points");
-    for (int i = 0; i < nep->m; ++i) {
-        const rsrr_fn &f = nep->fn[i];
-        if (f.kind < RSRR_F_ONE || f.kind > RSRR_F_EXP) return create_fail("rsrr_create: bad fn kind");
-        if (f.kind == RSRR_F_ZPOW && (f.param < 0 || f.param != std::floor(f.param) || f.param > 64))
-            return create_fail("rsrr_create: ZPOW needs a small non-negative integer");
-    }
     const int64_t n = nep->n;
     const int64_t nnz = nep->row_ptr[n];
     if (nep->row_ptr[0] != 0 || nnz < 1 || nnz > INT32_MAX)
@@ -265,19 +387,11 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
     }
     if (kl > rsrr::KL_MAX) return create_fail("rsrr_create: lower bandwidth above 480");
     const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
-    if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
-        return create_fail("rsrr_create: unknown precision");
-    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI_MMA))
-        return create_fail("rsrr_create: unknown gemm method");
 
-    Handle *h = new (std::nothrow) Handle();
+    Handle *h = new_handle(nep, region, N, L, opts);
     if (!h) { rsrr::thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
-    if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);
-    h->n = n; h->nnz = nnz; h->N = N; h->L = L; h->m = nep->m;
+    h->nnz = nnz;
     h->kl = (int)kl; h->ku = (int)ku;
-    h->region = *region;
-    h->region.points = nullptr;
-    for (int i = 0; i < nep->m; ++i) h->fn[i] = nep->fn[i];
     h->geom.kl = (int)kl;
     h->geom.ku = (int)ku;
     h->geom.nb = prec == RSRR_PREC_MIXED ? rsrr::NB_C64 : rsrr::NB_C128;
@@ -287,7 +401,47 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
     h->h_row_ptr.resize(n + 1);
     for (int64_t i = 0; i <= n; ++i) h->h_row_ptr[i] = (int32_t)nep->row_ptr[i];
     h->h_col_idx.assign(nep->col_idx, nep->col_idx + nnz);
-    h->h_vals.assign(nep->values, nep->values + (size_t)nep->m * nnz);
+    // the terms as held: real values one term each; complex values Re A_u with
+    // f_u and, unless every imaginary part is zero, Im A_u with i f_u
+    // (T = sum_u f_u (Re A_u + i Im A_u) exactly); ||A_u||_1 of every caller term
+    h->a1.assign(nep->m, 0.0);
+    for (int u = 0; u < nep->m; ++u) {
+        std::vector<double> colsum(n, 0.0);
+        if (nep->values_complex) {
+            const double *v = nep->values + (size_t)2 * u * nnz;
+            bool imag = false;
+            for (int64_t e = 0; e < nnz; ++e) {
+                colsum[h->h_col_idx[e]] += std::hypot(v[2 * e], v[2 * e + 1]);
+                imag = imag || v[2 * e + 1] != 0.0;
+            }
+            for (int64_t e = 0; e < nnz; ++e) h->h_vals.push_back(v[2 * e]);
+            h->fn.push_back(nep->fn[u]);
+            h->fn_src.push_back(u);
+            h->fn_imag.push_back(0);
+            if (imag) {
+                for (int64_t e = 0; e < nnz; ++e) h->h_vals.push_back(v[2 * e + 1]);
+                rsrr_fn fi = nep->fn[u];
+                fi.scale = rsrr_c128{-nep->fn[u].scale.im, nep->fn[u].scale.re};  // i * scale
+                h->fn.push_back(fi);
+                h->fn_src.push_back(u);
+                h->fn_imag.push_back(1);
+            }
+        } else {
+            const double *v = nep->values + (size_t)u * nnz;
+            for (int64_t e = 0; e < nnz; ++e) colsum[h->h_col_idx[e]] += std::fabs(v[e]);
+            h->h_vals.insert(h->h_vals.end(), v, v + nnz);
+            h->fn.push_back(nep->fn[u]);
+            h->fn_src.push_back(u);
+            h->fn_imag.push_back(0);
+        }
+        for (double c : colsum) h->a1[u] = std::max(h->a1[u], c);
+    }
+    for (double v : h->h_vals)
+        if (!std::isfinite(v)) {
+            delete h;
+            return create_fail("rsrr_create: values must be finite");
+        }
+    h->m = (int)h->fn.size();
     // duplicates inside a row are rejected (a CSC lookup needs unique entries)
     {
         std::vector<int32_t> cnt(n + 1, 0);
@@ -314,29 +468,12 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
         h->h_csc_row = std::move(crow);
         h->h_csc_perm = std::move(cperm);
     }
-    // step 1: sampling points (trapezoid nodes on the ellipse, Section 4.1, or
-    // the explicit points) and the coefficient table f_i(z_j)
-    h->z.resize(N);
-    for (int j = 0; j < N; ++j) {
-        if (region->kind == RSRR_REGION_POINTS) {
-            h->z[j] = cplx(region->points[j].re, region->points[j].im);
-        } else {
-            const double al = 2.0 * M_PI * (j + 0.5) / N;
-            h->z[j] = cplx(region->center.re + region->a * std::cos(al),
-                           region->center.im + region->b * std::sin(al));
-        }
+    fill_points(h, region, N);
+    rsrr_status st = fill_coef(h);
+    if (st != RSRR_OK) {
+        delete h;
+        return st;
     }
-    std::vector<double2> &coef = h->h_coef;
-    coef.resize((size_t)N * nep->m);
-    for (int j = 0; j < N; ++j)
-        for (int i = 0; i < nep->m; ++i) {
-            const cplx v = rsrr::eval_fn_host(nep->fn[i], h->z[j]);
-            if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) {
-                delete h;
-                return create_fail("rsrr_create: f_i is not finite at a sampling point");
-            }
-            coef[(size_t)j * nep->m + i] = make_double2(v.real(), v.imag());
-        }
     *out = h;
     return RSRR_OK;
 }
@@ -358,6 +495,7 @@ size_t Handle::estimate_bytes() {
     b += projection_ws_bytes(N * L, n, m);
     b += ssfull_dev_bytes(std::min<int64_t>((int64_t)N * L, n), m, opts.NQ, opts.KQ);
     b += sizeof(double2) * ((size_t)n + (size_t)N * L + 8) * 256 + (1u << 20);
+    if (dense_terms) b += 2 * sizeof(double2) * (size_t)n * 256;  // A_i V and T(lambda) V
     return b;
 }
 
@@ -384,8 +522,18 @@ rsrr_status rsrr_set_probe(rsrr_t *hh, const rsrr_c128 *U, int32_t on_device, vo
 rsrr_status rsrr_sample(rsrr_t *hh, void *stream) {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h) return RSRR_EINVAL;
-    rsrr_status st = h->dense ? h->sample_dense((cudaStream_t)stream) : h->sample((cudaStream_t)stream);
+    rsrr_status st = h->sample((cudaStream_t)stream);
     if (st == RSRR_OK) { h->sampled = true; h->projected = false; }
+    return st;
+}
+
+rsrr_status rsrr_add_points(rsrr_t *hh, const rsrr_c128 *z_new, int32_t count, void *stream) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h || !z_new) return RSRR_EINVAL;
+    std::vector<cplx> zz(count > 0 ? count : 0);
+    for (int q = 0; q < count; ++q) zz[q] = cplx(z_new[q].re, z_new[q].im);
+    rsrr_status st = h->add_points(zz.data(), count, (cudaStream_t)stream);
+    if (st == RSRR_OK) h->sampled = true;
     return st;
 }
 
@@ -418,6 +566,20 @@ rsrr_status rsrr_get_eta(rsrr_t *hh, double *dst) {
     if (!h->sampled) return h->fail(RSRR_ESTATE, "rsrr_get_eta: no rsrr_sample yet");
     CK(cudaDeviceSynchronize(), "get_eta sync");
     CK(cudaMemcpy(dst, h->d_eta, sizeof(double) * h->N * h->L, cudaMemcpyDeviceToHost), "get_eta");
+    return RSRR_OK;
+}
+
+rsrr_status rsrr_copy_result(rsrr_t *hh, int32_t capacity, int32_t *count, rsrr_c128 *lam, double *res,
+                             rsrr_c128 *V) {
+    Handle *h = reinterpret_cast<Handle *>(hh);
+    if (!h) return RSRR_EINVAL;
+    if (!h->solved) return h->fail(RSRR_ESTATE, "rsrr_copy_result: no rsrr_solve yet");
+    const int32_t cnt = (int32_t)h->res_lam.size();
+    if (count) *count = cnt;
+    if (capacity < cnt) return h->fail(RSRR_EINVAL, "rsrr_copy_result: capacity below the eigenpair count");
+    if (lam) std::copy(h->res_lam.begin(), h->res_lam.end(), lam);
+    if (res) std::copy(h->res_res.begin(), h->res_res.end(), res);
+    if (V) std::copy(h->res_V.begin(), h->res_V.end(), V);
     return RSRR_OK;
 }
 
@@ -504,6 +666,7 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     CK(alloc(&d_xmax, NL), "alloc");
     CK(alloc(&d_done, N), "alloc");
     CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
+    CK(alloc(&d_tmo, 1), "alloc");
     const size_t band = (size_t)geom.ldab * n * N;
     {
         const size_t smem2 = opts.precision == RSRR_PREC_MIXED ? band_solve2_smem_c64(geom)
@@ -539,7 +702,7 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     // rsrr_set_probe replaces it
     {
         std::vector<double2> U;
-        default_probe(U, nL);
+        default_probe(U, nL, seed);
         CK(cudaMemcpyAsync(d_U, U.data(), sizeof(double2) * nL, H2D, hs), "upload");
     }
     CK(launch_colmax(d_umax, d_U, (int)n, L, hs), "colmax");
@@ -562,79 +725,223 @@ rsrr_status Handle::mark(int i, cudaStream_t s) {
     return RSRR_OK;
 }
 
-// X = (P L U)^{-1} X in place for every point not skipped (factors of the
-// last LU): the streaming solve when it fits, else the one-kernel solve.
-cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, cudaStream_t s) {
+// X = (P L U)^{-1} X in place for points p0 .. p0+np-1 not skipped (factors
+// of the last LU; B and skip point at the first point of the range): the
+// streaming solve when it fits, else the one-kernel solve.
+cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s) {
     const int nn = (int)n;
+    const size_t ab_pt = (size_t)geom.ldab * n;
+    const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
+    const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
     if (mixed)
-        return solve2 ? launch_band_solve2_c64(d_ab32, d_bperm, d_dinv32, static_cast<float2 *>(B), geom,
-                                               N, nn, L, skip, s)
-                      : launch_band_solve_c64(d_ab32, d_piv, d_dinv32, static_cast<float2 *>(B), geom, N,
-                                              nn, L, skip, s);
-    return solve2 ? launch_band_solve2_c128(d_ab64, d_bperm, d_dinv64, static_cast<double2 *>(B), geom, N,
-                                            nn, L, skip, s)
-                  : launch_band_solve_c128(d_ab64, d_piv, d_dinv64, static_cast<double2 *>(B), geom, N,
-                                           nn, L, skip, s);
+        return solve2 ? launch_band_solve2_c64(d_ab32 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv32 + p0 * dv_pt,
+                                               static_cast<float2 *>(B), geom, np, nn, L, skip, s)
+                      : launch_band_solve_c64(d_ab32 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv32 + p0 * dv_pt,
+                                              static_cast<float2 *>(B), geom, np, nn, L, skip, s);
+    return solve2 ? launch_band_solve2_c128(d_ab64 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv64 + p0 * dv_pt,
+                                            static_cast<double2 *>(B), geom, np, nn, L, skip, s)
+                  : launch_band_solve_c128(d_ab64 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv64 + p0 * dv_pt,
+                                           static_cast<double2 *>(B), geom, np, nn, L, skip, s);
 }
 
-// Step 2 of RSRR on the GPU, asynchronously on stream s.
-rsrr_status Handle::sample(cudaStream_t s) {
+rsrr_status Handle::sample(cudaStream_t s) { return dense ? sample_dense(0, N, s) : sample_band(0, N, s); }
+
+// Step 2 of RSRR on the GPU for sampling points p0 .. p0+np-1, asynchronously
+// on stream s (every point for rsrr_sample; the appended points for
+// rsrr_add_points, which leaves the others' samples untouched).
+rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
     const bool cluster_lu = !(opts.flags & RSRR_FLAG_ONE_CTA_LU);
     Handle *h = this;
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L;
+    const size_t ab_pt = (size_t)geom.ldab * n;
+    const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
+    const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
+    // the range's view of the problem: coefficient rows p0 .. p0+np-1
+    DevProblem dq = dp;
+    dq.N = np;
+    dq.coef = dp.coef + (size_t)p0 * m;
+    int32_t *piv = d_piv + (size_t)p0 * n, *info = d_info + p0, *done = d_done + p0;
+    double *tnorm = d_tnorm + p0, *eta = d_eta + (size_t)p0 * L;
+    double *rmax = d_rmax + (size_t)p0 * L, *xmax = d_xmax + (size_t)p0 * L;
+    double2 *X = d_X + p0 * per_pt;
     rsrr_status ms;
-    CK(ozaki_timeouts(&tmo_mark), "timeout counter");
+    CK(cudaMemsetAsync(d_tmo, 0, sizeof(unsigned int), s), "memset");
     if ((ms = mark(0, s)) != RSRR_OK) return ms;
     CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
-    CK(launch_tnorm(d_tnorm, dp, s), "tnorm");
+    if (opts.flags & RSRR_FLAG_INJECT_TIMEOUT) {
+        CK(launch_wait_check(4096, d_tmo, s), "injected wait");
+        launches += 1;
+    }
+    CK(launch_tnorm(tnorm, dq, s), "tnorm");
     if (opts.precision == RSRR_PREC_MIXED) {
-        CK(launch_assemble<float2>(d_ab32, geom, dp, s), "assemble");
+        float2 *ab = d_ab32 + p0 * ab_pt, *D = d_D + p0 * per_pt;
+        double2 *R = d_R + p0 * per_pt;
+        CK(launch_assemble<float2>(ab, geom, dq, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c64(d_ab32, d_piv, d_info, d_dinv32, geom, N, nn, s, cluster_lu), "band LU");
+        CK(launch_band_lu_c64(ab, piv, info, d_dinv32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (solve2) {
-            CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "block permutations");
+            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
-        CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
-        CK(band_solve(true, d_D, nullptr, s), "band solve");
-        CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
-        CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
+        CK(launch_broadcast_probe_c64(D, d_U, per_pt, np, s), "probe");
+        CK(band_solve(true, D, nullptr, p0, np, s), "band solve");
+        CK(launch_widen(X, D, per_pt * np, s), "widen");
+        CK(cudaMemsetAsync(done, 0, sizeof(int32_t) * np, s), "memset");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         launches += 5;  // assemble, LU, probe, solve, widen
         for (int it = 0; it < opts.max_refine; ++it) {
-            CK(launch_residual(d_R, d_X, dp, d_rmax, d_xmax, d_done, s), "residual");
-            CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
-                          d_sweep_flags + it, d_done, s), "eta");
-            CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
-            CK(band_solve(true, d_D, d_done, s), "band solve");
-            CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
+            CK(launch_residual(R, X, dq, rmax, xmax, done, s), "residual");
+            CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),
+               "eta");
+            CK(launch_narrow(D, R, per_pt, np, done, s), "narrow");
+            CK(band_solve(true, D, done, p0, np, s), "band solve");
+            CK(launch_update(X, D, per_pt, np, done, s), "update");
             launches += 5;
         }
     } else {
-        CK(launch_assemble<double2>(d_ab64, geom, dp, s), "assemble");
+        double2 *ab = d_ab64 + p0 * ab_pt;
+        CK(launch_assemble<double2>(ab, geom, dq, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c128(d_ab64, d_piv, d_info, d_dinv64, geom, N, nn, s, cluster_lu), "band LU");
+        CK(launch_band_lu_c128(ab, piv, info, d_dinv64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (solve2) {
-            CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "block permutations");
+            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
-        CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
-        CK(band_solve(false, d_X, nullptr, s), "band solve");
+        CK(launch_broadcast_probe_c128(X, d_U, per_pt, np, s), "probe");
+        CK(band_solve(false, X, nullptr, p0, np, s), "band solve");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         launches += 4;  // assemble, LU, probe, solve
     }
     if ((ms = mark(4, s)) != RSRR_OK) return ms;
-    // final backward errors of every column (statistics and convergence)
-    CK(launch_residual(nullptr, d_X, dp, d_rmax, d_xmax, nullptr, s), "residual");
-    CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
+    // final backward errors of every column of the range (statistics and convergence)
+    CK(launch_residual(nullptr, X, dq, rmax, xmax, nullptr, s), "residual");
+    CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol,
                   d_sweep_flags + opts.max_refine + 1, nullptr, s), "eta");
     if ((ms = mark(5, s)) != RSRR_OK) return ms;
     launches += 3;  // tnorm, final residual, final eta
     timed_sample = opts.timing != 0;
     return RSRR_OK;
+}
+
+// frees one buffer obtained by alloc() and forgets it
+void Handle::release(void *p, size_t bytes) {
+    if (!p) return;
+    for (size_t q = 0; q < allocations.size(); ++q)
+        if (allocations[q] == p) {
+            allocations.erase(allocations.begin() + q);
+            break;
+        }
+    raw_free(p);
+    device_bytes -= std::min(device_bytes, bytes);
+}
+
+// a per-point buffer grown from N0 to N1 points of `per` elements; with keep,
+// the first N0 points' contents are copied (bit for bit)
+template <typename T>
+cudaError_t Handle::regrow(T **p, size_t per, int N0, int N1, bool keep) {
+    T *q = nullptr;
+    cudaError_t e = alloc(&q, per * N1);
+    if (e != cudaSuccess) return e;
+    if (keep && *p && per * N0 > 0) {
+        e = cudaMemcpyAsync(q, *p, sizeof(T) * per * N0, cudaMemcpyDeviceToDevice, hs);
+        if (e == cudaSuccess) e = wait();
+        if (e != cudaSuccess) return e;
+    }
+    release(*p, sizeof(T) * per * N0);
+    *p = q;
+    return cudaSuccess;
+}
+
+// Two-stage sampling (Section 5.4): the points z_new are appended to the
+// handle's sampling points and only they are assembled, factored, solved and
+// refined; the samples X_j of the earlier points stay resident, unchanged.
+rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
+    Handle *h = this;
+    if (!sampled) return fail(RSRR_ESTATE, "rsrr_add_points: no rsrr_sample yet");
+    if (count < 1) return fail(RSRR_EINVAL, "rsrr_add_points: count must be >= 1");
+    for (int q = 0; q < count; ++q)
+        if (!std::isfinite(znew[q].real()) || !std::isfinite(znew[q].imag()))
+            return fail(RSRR_EINVAL, "rsrr_add_points: points must be finite");
+    if ((int64_t)N + count > (int64_t)INT32_MAX / std::max(1, L))
+        return fail(RSRR_EINVAL, "rsrr_add_points: too many points");
+    std::vector<cplx> fnew;
+    if (!dense || dense_terms) {
+        rsrr_status st = eval_terms(znew, count, fnew);
+        if (st != RSRR_OK) return st;
+    }
+    CK(cudaStreamSynchronize(s), "add_points sync");
+    CK(wait(), "add_points sync");
+    const int N0 = N, N1 = N + count;
+    const size_t per_pt = (size_t)n * L;
+    const bool mixed = opts.precision == RSRR_PREC_MIXED;
+    // kept: the samples, their backward errors, the pivot status, the
+    // coefficient rows / points; the rest is work space of the next sampling
+    CK(regrow(&d_X, per_pt, N0, N1, true), "regrow S");
+    CK(regrow(&d_eta, (size_t)L, N0, N1, true), "regrow");
+    CK(regrow(&d_info, 1, N0, N1, true), "regrow");
+    CK(regrow(&d_piv, (size_t)n, N0, N1, false), "regrow");
+    CK(regrow(&d_tnorm, 1, N0, N1, false), "regrow");
+    CK(regrow(&d_rmax, (size_t)L, N0, N1, false), "regrow");
+    CK(regrow(&d_xmax, (size_t)L, N0, N1, false), "regrow");
+    CK(regrow(&d_done, 1, N0, N1, false), "regrow");
+    if (d_R) CK(regrow(&d_R, per_pt, N0, N1, false), "regrow");
+    if (d_D) CK(regrow(&d_D, per_pt, N0, N1, false), "regrow");
+    if (!dense || dense_terms) CK(regrow(&d_coef, (size_t)m, N0, N1, true), "regrow");
+    if (dense) {
+        const size_t nn2 = (size_t)n * n;
+        const int nb = mixed ? NB_C64 : NB_C128;
+        const size_t dv_pt = (((size_t)n + nb - 1) / nb) * 2 * nb * nb;
+        CK(regrow(&d_z, 1, N0, N1, true), "regrow");
+        CK(regrow(&d_T64, nn2, N0, N1, false), "regrow dense matrices");
+        if (mixed) {
+            CK(regrow(&d_A32, nn2, N0, N1, false), "regrow dense factors");
+            CK(regrow(&d_dinv32, dv_pt, N0, N1, false), "regrow");
+        } else {
+            CK(regrow(&d_ab64, nn2, N0, N1, false), "regrow dense factors");
+            CK(regrow(&d_dinv64, dv_pt, N0, N1, false), "regrow");
+        }
+    } else {
+        const size_t ab_pt = (size_t)geom.ldab * n;
+        const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
+        if (mixed) {
+            CK(regrow(&d_ab32, ab_pt, N0, N1, false), "regrow band factors");
+            CK(regrow(&d_dinv32, nblk * 2 * geom.nb * geom.nb, N0, N1, false), "regrow");
+        } else {
+            CK(regrow(&d_ab64, ab_pt, N0, N1, false), "regrow band factors");
+            CK(regrow(&d_dinv64, nblk * 2 * geom.nb * geom.nb, N0, N1, false), "regrow");
+        }
+        if (d_bperm) CK(regrow(&d_bperm, nblk * 2 * geom.nb, N0, N1, false), "regrow");
+    }
+    // the projection's work space is sized by N L: rebuilt by the next rsrr_project
+    if (proj_ws) {
+        release(proj_ws, proj_ws_bytes);
+        proj_ws = nullptr;
+        proj_ws_bytes = 0;
+        d_Q = nullptr;
+        d_P = nullptr;
+    }
+    // the new points and their coefficient rows
+    std::vector<double2> zs(count);
+    for (int q = 0; q < count; ++q) zs[q] = make_double2(znew[q].real(), znew[q].imag());
+    if (dense && !dense_terms)
+        CK(cudaMemcpyAsync(d_z + N0, zs.data(), sizeof(double2) * count, cudaMemcpyHostToDevice, hs), "upload");
+    if (!fnew.empty()) {
+        std::vector<double2> cf(fnew.size());
+        for (size_t e = 0; e < cf.size(); ++e) cf[e] = make_double2(fnew[e].real(), fnew[e].imag());
+        CK(cudaMemcpyAsync(d_coef + (size_t)N0 * m, cf.data(), sizeof(double2) * cf.size(), cudaMemcpyHostToDevice,
+                           hs), "upload");
+    }
+    CK(wait(), "upload sync");
+    z.insert(z.end(), znew, znew + count);
+    N = N1;
+    dp.N = N1;
+    dp.coef = d_coef;
+    projected = false;
+    solved = false;
+    return dense ? sample_dense(N0, count, s) : sample_band(N0, count, s);
 }
 
 rsrr_status Handle::read_outcome() {
@@ -695,19 +1002,11 @@ rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_
     if (!(std::isfinite(nep->diag))) return create_fail("rsrr_create: diag is not finite");
     const int64_t n = nep->n;
     if (n > 65536) return create_fail("rsrr_create: dense order above 65536");
-    const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
-    if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
-        return create_fail("rsrr_create: unknown precision");
-    if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI_MMA))
-        return create_fail("rsrr_create: unknown gemm method");
-    Handle *h = new (std::nothrow) Handle();
+    Handle *h = new_handle(nep, region, N, L, opts);
     if (!h) { thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
-    if (opts) h->opts = *opts; else rsrr_opts_default(&h->opts);
     h->dense = true;
-    h->n = n; h->nnz = 0; h->N = N; h->L = L;
+    h->nnz = 0;
     h->diag = nep->diag;
-    h->region = *region;
-    h->region.points = nullptr;
     h->h_points.assign(nep->points, nep->points + 3 * n);
     double rmax = 0.0;
     for (int64_t i = 0; i < n; ++i) {
@@ -728,21 +1027,76 @@ rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_
             rmax = std::max(rmax, r);
         }
     }
-    // Taylor terms: smallest P with (r_max rho)^P / P! < 1e-17
+    // Taylor terms about the centre: smallest P with (r_max rho)^P / P! < 1e-17;
+    // the held terms are the powers (z - c)^p
     const double x = rmax * std::max(region->a, region->b);
     int P = 0;
     double term = 1.0;
     while (term >= 1e-17 && P < 200) { ++P; term *= x / P; }
     h->m = P;
-    h->z.resize(N);
-    for (int j = 0; j < N; ++j) {
-        if (region->kind == RSRR_REGION_POINTS) {
-            h->z[j] = cplx(region->points[j].re, region->points[j].im);
-        } else {
-            const double al = 2.0 * M_PI * (j + 0.5) / N;
-            h->z[j] = cplx(region->center.re + region->a * std::cos(al),
-                           region->center.im + region->b * std::sin(al));
+    for (int p = 0; p < P; ++p) {
+        rsrr_fn f{};
+        f.kind = RSRR_F_TAYLOR;
+        f.power = p;
+        f.scale = rsrr_c128{1.0, 0.0};
+        f.shift = region->center;
+        h->fn.push_back(f);
+        h->fn_src.push_back(p);
+        h->fn_imag.push_back(0);
+    }
+    fill_points(h, region, N);
+    *out = h;
+    return RSRR_OK;
+}
+
+// T(z) = sum_i f_i(z) A_i with dense caller-supplied A_i
+rsrr_status prepare_dense_terms(const rsrr_nep *nep, const rsrr_region *region, int32_t N, int32_t L,
+                                const rsrr_opts *opts, Handle **out) {
+    const int64_t n = nep->n;
+    if (n > 32768) return create_fail("rsrr_create: dense order above 32768");
+    if (!nep->dense) return create_fail("rsrr_create: dense kind without matrices");
+    for (int i = 0; i < nep->m; ++i)
+        if (!nep->dense[i]) return create_fail("rsrr_create: dense kind with a NULL matrix");
+    Handle *h = new_handle(nep, region, N, L, opts);
+    if (!h) { thread_error() = "rsrr_create: out of host memory"; return RSRR_ENOMEM; }
+    h->dense = true;
+    h->dense_terms = true;
+    h->nnz = 0;
+    h->m = nep->m;
+    const size_t nn2 = (size_t)n * n;
+    try {
+        h->h_Aterms.resize(nn2 * nep->m);
+    } catch (...) {
+        delete h;
+        thread_error() = "rsrr_create: out of host memory";
+        return RSRR_ENOMEM;
+    }
+    h->a1.assign(nep->m, 0.0);
+    for (int i = 0; i < nep->m; ++i) {
+        const rsrr_c128 *A = nep->dense[i];
+        double2 *dst = h->h_Aterms.data() + nn2 * i;
+        for (int64_t c = 0; c < n; ++c) {
+            double cs = 0.0;
+            for (int64_t r = 0; r < n; ++r) {
+                const rsrr_c128 v = A[c * n + r];
+                if (!std::isfinite(v.re) || !std::isfinite(v.im)) {
+                    delete h;
+                    return create_fail("rsrr_create: dense matrix entries must be finite");
+                }
+                dst[c * n + r] = make_double2(v.re, v.im);
+                cs += std::hypot(v.re, v.im);
+            }
+            h->a1[i] = std::max(h->a1[i], cs);
         }
+        h->fn.push_back(nep->fn[i]);
+        h->fn_src.push_back(i);
+        h->fn_imag.push_back(0);
+    }
+    fill_points(h, region, N);
+    rsrr_status st = fill_coef(h);
+    if (st != RSRR_OK) {
+        delete h;
+        return st;
     }
     *out = h;
     return RSRR_OK;
@@ -754,7 +1108,12 @@ rsrr_status Handle::allocate_dense() {
     const bool mixed = opts.precision == RSRR_PREC_MIXED;
     const int nb = mixed ? NB_C64 : NB_C128;
     const size_t nblk = ((size_t)n + nb - 1) / nb;
-    CK(alloc(&d_points, 3 * n), "alloc");
+    if (dense_terms) {
+        CK(alloc(&d_Aterms, (size_t)m * nn2), "alloc dense terms");
+        CK(alloc(&d_coef, (size_t)N * m), "alloc");
+    } else {
+        CK(alloc(&d_points, 3 * n), "alloc");
+    }
     CK(alloc(&d_z, N), "alloc");
     CK(alloc(&d_U, nL), "alloc");
     CK(alloc(&d_umax, L), "alloc");
@@ -768,6 +1127,7 @@ rsrr_status Handle::allocate_dense() {
     CK(alloc(&d_xmax, NL), "alloc");
     CK(alloc(&d_done, N), "alloc");
     CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
+    CK(alloc(&d_tmo, 1), "alloc");
     CK(alloc(&d_T64, nn2 * N), "alloc dense matrices (complex128)");
     // the FP64 residuals U - T X (n x n times n x L per point) are FP64-accurate
     // tensor-core products when the GEMM method allows them
@@ -786,16 +1146,25 @@ rsrr_status Handle::allocate_dense() {
     if (dry) return RSRR_OK;
     std::vector<double2> zs(N);
     for (int j = 0; j < N; ++j) zs[j] = make_double2(z[j].real(), z[j].imag());
-    CK(cudaMemcpyAsync(d_points, h_points.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, hs), "upload");
+    if (dense_terms) {
+        CK(cudaMemcpyAsync(d_Aterms, h_Aterms.data(), sizeof(double2) * h_Aterms.size(), cudaMemcpyHostToDevice, hs),
+           "upload");
+        CK(cudaMemcpyAsync(d_coef, h_coef.data(), sizeof(double2) * h_coef.size(), cudaMemcpyHostToDevice, hs),
+           "upload");
+    } else {
+        CK(cudaMemcpyAsync(d_points, h_points.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, hs),
+           "upload");
+    }
     CK(cudaMemcpyAsync(d_z, zs.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, hs), "upload");
     {
         std::vector<double2> U;
-        default_probe(U, nL);
+        default_probe(U, nL, seed);
         CK(cudaMemcpyAsync(d_U, U.data(), sizeof(double2) * nL, cudaMemcpyHostToDevice, hs), "upload");
     }
     CK(launch_colmax(d_umax, d_U, (int)n, L, hs), "colmax");
     CK(wait(), "create sync");
-    dp.n = n; dp.N = N; dp.L = L; dp.m = m; dp.U = d_U;
+    if (dense_terms) std::vector<double2>().swap(h_Aterms);  // the device copy is the one used
+    dp.n = n; dp.N = N; dp.L = L; dp.m = m; dp.U = d_U; dp.coef = d_coef;
     return RSRR_OK;
 }
 
@@ -808,23 +1177,24 @@ bool Handle::dense_residual_sliced() const {
 }
 
 // R = U - T X in FP64 (stored complex128 T) and the column maxima of |R|, |X|,
-// for every point, or (skip_done) only for points whose done flag is 0 (the
-// flags are read on the host first).
-rsrr_status Handle::dense_residual(bool skip_done, cudaStream_t s) {
+// for points p0 .. p0+np-1, or (skip_done) only for those whose done flag is 0
+// (the flags are read on the host first).
+rsrr_status Handle::dense_residual(bool skip_done, int p0, int np, cudaStream_t s) {
     Handle *h = this;
-    std::vector<int32_t> done(N, 0);
+    std::vector<int32_t> done(np, 0);
     if (skip_done) {
-        CK(cudaMemcpyAsync(done.data(), d_done, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s), "done");
+        CK(cudaMemcpyAsync(done.data(), d_done + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToHost, s), "done");
         CK(cudaStreamSynchronize(s), "done sync");
     }
     const size_t per = (size_t)n * L, nn2 = (size_t)n * n;
-    for (int pt = 0; pt < N; ++pt) {
-        if (done[pt]) continue;
+    for (int q = 0; q < np; ++q) {
+        if (done[q]) continue;
+        const size_t pt = (size_t)p0 + q;
         CK(cudaMemcpyAsync(d_R + pt * per, d_U, sizeof(double2) * per, cudaMemcpyDeviceToDevice, s), "R = U");
         if (dense_residual_sliced())
             CK(ozaki_zgemm((int)n, L, (int)n, false, d_T64 + pt * nn2, n, d_X + pt * per, n, d_R + pt * per, n,
                            -1.0, 1.0, false, d_dws, dws_bytes, s, &launches, nullptr, nullptr,
-                           opts.gemm == RSRR_GEMM_OZAKI_MMA), "R -= T X");
+                           opts.gemm == RSRR_GEMM_OZAKI_MMA, d_tmo), "R -= T X");
         else
             CK(fp64_gemm((int)n, L, (int)n, false, d_T64 + pt * nn2, n, d_X + pt * per, n, d_R + pt * per, n,
                          -1.0, 1.0, s), "R -= T X");
@@ -835,53 +1205,71 @@ rsrr_status Handle::dense_residual(bool skip_done, cudaStream_t s) {
     return RSRR_OK;
 }
 
-// Step 2 of RSRR for the dense kernel problem.
-rsrr_status Handle::sample_dense(cudaStream_t s) {
+// Step 2 of RSRR for the dense problems, points p0 .. p0+np-1.
+rsrr_status Handle::sample_dense(int p0, int np, cudaStream_t s) {
     Handle *h = this;
     const int nn = (int)n;
-    const int64_t per_pt = (int64_t)n * L, total = (int64_t)n * n * N;
+    const bool mixed = opts.precision == RSRR_PREC_MIXED;
+    const int nb = mixed ? NB_C64 : NB_C128;
+    const size_t nn2 = (size_t)n * n;
+    const size_t dv_pt = (((size_t)n + nb - 1) / nb) * 2 * nb * nb;
+    const int64_t per_pt = (int64_t)n * L, total = (int64_t)nn2 * np;
+    int32_t *piv = d_piv + (size_t)p0 * n, *info = d_info + p0, *done = d_done + p0;
+    double *tnorm = d_tnorm + p0, *eta = d_eta + (size_t)p0 * L;
+    double *rmax = d_rmax + (size_t)p0 * L, *xmax = d_xmax + (size_t)p0 * L;
+    double2 *X = d_X + p0 * per_pt, *T64 = d_T64 + p0 * nn2;
     rsrr_status ms;
-    CK(ozaki_timeouts(&tmo_mark), "timeout counter");
+    CK(cudaMemsetAsync(d_tmo, 0, sizeof(unsigned int), s), "memset");
     if ((ms = mark(0, s)) != RSRR_OK) return ms;
     CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
-    CK(launch_assemble_dense_c128(d_T64, d_points, d_z, diag, nn, N, s), "assemble");
-    CK(launch_dense_tnorm(d_tnorm, d_T64, nn, N, s), "tnorm");
+    if (opts.flags & RSRR_FLAG_INJECT_TIMEOUT) {
+        CK(launch_wait_check(4096, d_tmo, s), "injected wait");
+        launches += 1;
+    }
+    if (dense_terms)
+        CK(launch_assemble_dense_terms(T64, d_Aterms, d_coef + (size_t)p0 * m, nn, np, m, s), "assemble");
+    else
+        CK(launch_assemble_dense_c128(T64, d_points, d_z + p0, diag, nn, np, s), "assemble");
+    CK(launch_dense_tnorm(tnorm, T64, nn, np, s), "tnorm");
     launches += 2;
-    if (opts.precision == RSRR_PREC_MIXED) {
-        CK(launch_narrow_all(d_A32, d_T64, total, s), "narrow");
+    if (mixed) {
+        float2 *A32 = d_A32 + p0 * nn2, *D = d_D + p0 * per_pt;
+        CK(launch_narrow_all(A32, T64, total, s), "narrow");
         launches += 1;
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_dense_lu_c64(d_A32, d_piv, d_info, d_dinv32, nn, N, s, &launches), "dense LU");
+        CK(launch_dense_lu_c64(A32, piv, info, d_dinv32 + p0 * dv_pt, nn, np, s, &launches, d_tmo,
+                               !(opts.flags & RSRR_FLAG_SIMT_DENSE_UPDATE)), "dense LU");
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
-        CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "probe");
-        CK(launch_dense_solve_c64(d_A32, d_piv, d_dinv32, d_D, nn, N, L, nullptr, s), "dense solve");
-        CK(launch_widen(d_X, d_D, per_pt * N, s), "widen");
-        CK(cudaMemsetAsync(d_done, 0, sizeof(int32_t) * N, s), "memset");
+        CK(launch_broadcast_probe_c64(D, d_U, per_pt, np, s), "probe");
+        CK(launch_dense_solve_c64(A32, piv, d_dinv32 + p0 * dv_pt, D, nn, np, L, nullptr, s), "dense solve");
+        CK(launch_widen(X, D, per_pt * np, s), "widen");
+        CK(cudaMemsetAsync(done, 0, sizeof(int32_t) * np, s), "memset");
         launches += 3;
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         for (int it = 0; it < opts.max_refine; ++it) {
-            if ((ms = dense_residual(true, s)) != RSRR_OK) return ms;
-            CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
-                          d_sweep_flags + it, d_done, s), "eta");
-            CK(launch_narrow(d_D, d_R, per_pt, N, d_done, s), "narrow");
-            CK(launch_dense_solve_c64(d_A32, d_piv, d_dinv32, d_D, nn, N, L, d_done, s), "dense solve");
-            CK(launch_update(d_X, d_D, per_pt, N, d_done, s), "update");
+            if ((ms = dense_residual(true, p0, np, s)) != RSRR_OK) return ms;
+            CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),
+               "eta");
+            CK(launch_narrow(D, d_R + p0 * per_pt, per_pt, np, done, s), "narrow");
+            CK(launch_dense_solve_c64(A32, piv, d_dinv32 + p0 * dv_pt, D, nn, np, L, done, s), "dense solve");
+            CK(launch_update(X, D, per_pt, np, done, s), "update");
             launches += 4;
         }
     } else {
-        CK(cudaMemcpyAsync(d_ab64, d_T64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s), "copy");
+        double2 *A64 = d_ab64 + p0 * nn2;
+        CK(cudaMemcpyAsync(A64, T64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s), "copy");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_dense_lu_c128(d_ab64, d_piv, d_info, d_dinv64, nn, N, s, &launches), "dense LU");
+        CK(launch_dense_lu_c128(A64, piv, info, d_dinv64 + p0 * dv_pt, nn, np, s, &launches), "dense LU");
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
-        CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "probe");
-        CK(launch_dense_solve_c128(d_ab64, d_piv, d_dinv64, d_X, nn, N, L, nullptr, s), "dense solve");
+        CK(launch_broadcast_probe_c128(X, d_U, per_pt, np, s), "probe");
+        CK(launch_dense_solve_c128(A64, piv, d_dinv64 + p0 * dv_pt, X, nn, np, L, nullptr, s), "dense solve");
         launches += 2;
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
     }
     if ((ms = mark(4, s)) != RSRR_OK) return ms;
-    if ((ms = dense_residual(false, s)) != RSRR_OK) return ms;
-    CK(launch_eta(d_eta, d_done, d_rmax, d_xmax, d_umax, d_tnorm, N, L, opts.eta_tol,
-                  d_sweep_flags + opts.max_refine + 1, nullptr, s), "eta");
+    if ((ms = dense_residual(false, p0, np, s)) != RSRR_OK) return ms;
+    CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + opts.max_refine + 1,
+                  nullptr, s), "eta");
     launches += 1;
     if ((ms = mark(5, s)) != RSRR_OK) return ms;
     timed_sample = opts.timing != 0;

@@ -1,4 +1,4 @@
-// Resolvent sampling on banded T(z_j) (RSRR step 2, Section 3.3):
+// Resolvent sampling on banded T(z_j) (RSRR step 2, Section 4.3):
 //   assembly of T(z_j) = sum_i f_i(z_j) A_i into band LU storage,
 //   batched banded LU with partial pivoting (one CTA per sampling point),
 //   blocked triangular solves for the L probe columns,
@@ -488,6 +488,9 @@ cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const fl
     if (solve_smem<float2, NB_C64, 16>(g) <= 200 * 1024)
         return solve_dispatch<float2, NB_C64, 16>(ab, piv, dinv, B, g, N, n, L, skip, s);
     return solve_dispatch<float2, NB_C64, 8>(ab, piv, dinv, B, g, N, n, L, skip, s);
+}
+bool band_solve_fits_c128(const BandGeom &g) {
+    return solve_smem<double2, NB_C128, 4>(g) <= (size_t)smem_optin_limit();
 }
 cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, const double2 *dinv,
                                    double2 *B, const BandGeom &g, int N, int n, int L,

@@ -1,4 +1,4 @@
-// Batched banded LU with partial pivoting for RSRR step 2 (Section 3.3):
+// Batched banded LU with partial pivoting for RSRR step 2 (Section 4.3):
 // the factorisation of every T(z_j).  The band storage is described in
 // band.cu.  Two launch shapes share the same device routines and perform the
 // same arithmetic on every element, in the same order:

@@ -1,5 +1,5 @@
 // Streaming banded solve with the factors of band_lu_kernel: X = (P L U)^{-1} B
-// for every sampling point (Section 3.3's X_j = T(z_j)^{-1} U), one CTA per
+// for every sampling point (Section 4.3's X_j = T(z_j)^{-1} U), one CTA per
 // (point, chunk of LC right-hand sides).
 //
 // Forward, block by block (NB rows): the block's composed row permutation

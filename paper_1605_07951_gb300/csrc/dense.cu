@@ -1,4 +1,4 @@
-// Resolvent sampling on dense BEM-like T(z_j) (RSRR step 2, Section 3.3, for
+// Resolvent sampling on dense BEM-like T(z_j) (RSRR step 2, Section 4.3, for
 // the Nystrom single-layer kernel of Section 2.1):
 //   T(z)_ij = exp(i z r_ij) / (4 pi r_ij) (i != j), T_ii = diag,
 // assembled per sampling point, factored by a batched blocked LU with partial
@@ -10,6 +10,7 @@
 // never to the columns already factored: the solve applies each block's
 // interchanges just before that block's elimination, as the band solve does.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "rsrr_internal.h"
@@ -71,6 +72,78 @@ __global__ void assemble_dense_c128_kernel(double2 *__restrict__ A_all, const do
             v = make_double2(mag * c, mag * s);
         }
         A[q] = v;
+    }
+}
+
+// T(z_j) = sum_i f_i(z_j) A_i for caller-supplied dense A_i (m x n^2
+// complex128, term-major): every thread loads the m coefficients of one
+// entry once and writes that entry of every point of the chunk, so the A_i
+// are read once per chunk of points and the N matrices written once (the
+// write stream is the bound).  coef is point-major, f_i(z_j) at [j m + i].
+__global__ void assemble_dense_terms_kernel(double2 *__restrict__ T_all, const double2 *__restrict__ A,
+                                            const double2 *__restrict__ coef, int64_t nn2, int j0, int nj,
+                                            int m) {
+    extern __shared__ double2 s_cf[];  // nj x m
+    for (int t = threadIdx.x; t < nj * m; t += blockDim.x) s_cf[t] = coef[(size_t)j0 * m + t];
+    __syncthreads();
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nn2;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        double2 a[RSRR_MAX_TERMS_DEV];
+#pragma unroll
+        for (int i = 0; i < RSRR_MAX_TERMS_DEV; ++i)
+            a[i] = i < m ? A[(int64_t)i * nn2 + q] : make_double2(0.0, 0.0);
+        for (int j = 0; j < nj; ++j) {
+            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int i = 0; i < RSRR_MAX_TERMS_DEV; ++i)
+                if (i < m) acc = cfma(acc, s_cf[j * m + i], a[i]);
+            T_all[(int64_t)(j0 + j) * nn2 + q] = acc;
+        }
+    }
+}
+
+// R(:, c) (+)= cf[c m + i] Y(:, c): one term of T(lambda_c) v_c = sum_i
+// f_i(lambda_c) A_i v_c for the residuals of the dense-terms kind
+__global__ void accum_term_cols_kernel(double2 *__restrict__ R, const double2 *__restrict__ Y,
+                                       const double2 *__restrict__ cf, int m, int i, int n, int cnt,
+                                       int first) {
+    const int64_t total = (int64_t)n * cnt;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(q / n);
+        const double2 v = cmul(cf[(size_t)c * m + i], Y[q]);
+        R[q] = first ? v : cadd(R[q], v);
+    }
+}
+
+// rr[c] = ||R(:, c)||_2^2 and vv[c] = ||V(:, c)||_2^2 (block per column)
+__global__ void col_norms2_kernel(const double2 *__restrict__ R, const double2 *__restrict__ V, int n,
+                                  double *__restrict__ rr, double *__restrict__ vv) {
+    const int c = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 r = R[(int64_t)c * n + i], v = V[(int64_t)c * n + i];
+        a += r.x * r.x + r.y * r.y;
+        b += v.x * v.x + v.y * v.y;
+    }
+    __shared__ double sa[32], sb[32];
+    for (int off = 16; off; off >>= 1) {
+        a += shfl_down(a, off);
+        b += shfl_down(b, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        rr[c] = ta;
+        vv[c] = tb;
     }
 }
 
@@ -509,6 +582,31 @@ cudaError_t launch_assemble_dense_c128(double2 *A, const double *pts, const doub
                                                                                            zs, diag, n);
     return cudaGetLastError();
 }
+cudaError_t launch_assemble_dense_terms(double2 *T, const double2 *A, const double2 *coef, int n, int N,
+                                        int m, cudaStream_t s) {
+    if (m < 1 || m > RSRR_MAX_TERMS_DEV) return cudaErrorInvalidValue;
+    const int64_t nn2 = (int64_t)n * n;
+    const int chunk = std::max(1, 2048 / m);  // coefficients of a chunk: <= 32 KB of shared memory
+    for (int j0 = 0; j0 < N; j0 += chunk) {
+        const int nj = std::min(chunk, N - j0);
+        assemble_dense_terms_kernel<<<grid_for_d(nn2, 256, 152 * 8), 256, sizeof(double2) * nj * m, s>>>(
+            T, A, coef, nn2, j0, nj, m);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+cudaError_t launch_accum_term_cols(double2 *R, const double2 *Y, const double2 *cf, int m, int i, int n,
+                                   int cnt, bool first, cudaStream_t s) {
+    accum_term_cols_kernel<<<grid_for_d((int64_t)n * cnt), 256, 0, s>>>(R, Y, cf, m, i, n, cnt, first ? 1 : 0);
+    return cudaGetLastError();
+}
+cudaError_t launch_col_norms2(const double2 *R, const double2 *V, int n, int cnt, double *rr, double *vv,
+                              cudaStream_t s) {
+    if (cnt < 1) return cudaSuccess;
+    col_norms2_kernel<<<cnt, 256, 0, s>>>(R, V, n, rr, vv);
+    return cudaGetLastError();
+}
 cudaError_t launch_dense_tnorm(double *tnorm, const double2 *A, int n, int N, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(tnorm, 0, sizeof(double) * N, s);
     if (e != cudaSuccess) return e;
@@ -516,9 +614,23 @@ cudaError_t launch_dense_tnorm(double *tnorm, const double2 *A, int n, int N, cu
     return cudaGetLastError();
 }
 
+cudaError_t launch_dense_tc_update(float2 *A, int n, int k0, int jb, int N, unsigned int *status,
+                                   cudaStream_t s);
+
+// the trailing update A22 -= L21 U12 of one panel: FP32 / FP64 FMAs, or, for
+// complex64 with tc, the 3xTF32 tensor-core kernel of dense_tc.cu
+template <typename C, int NB>
+static cudaError_t dense_update(C *A, int n, int k0, int N, unsigned int *status, bool tc, cudaStream_t s) {
+    const int jb = std::min(NB, n - k0), rest = n - k0 - jb;
+    if constexpr (std::is_same<C, float2>::value)
+        if (tc) return launch_dense_tc_update(A, n, k0, jb, N, status, s);
+    dense_gemm_update_kernel<C, NB><<<dim3((rest + 63) / 64, (rest + 63) / 64, N), 256, 0, s>>>(A, n, k0);
+    return cudaGetLastError();
+}
+
 template <typename C, int NB>
 static cudaError_t dense_lu_t(C *A, int32_t *piv, int32_t *info, C *dinv, int n, int N, cudaStream_t s,
-                              int64_t *launches) {
+                              int64_t *launches, unsigned int *status, bool tc) {
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int32_t) * N, s);
     if (e != cudaSuccess) return e;
     for (int k0 = 0; k0 < n; k0 += NB) {
@@ -527,8 +639,8 @@ static cudaError_t dense_lu_t(C *A, int32_t *piv, int32_t *info, C *dinv, int n,
         const int rest = n - k0 - jb;
         if (rest > 0) {
             dense_laswp_trsm_kernel<C, NB><<<dim3((rest + 31) / 32, N), 256, 0, s>>>(A, piv, dinv, n, k0);
-            dense_gemm_update_kernel<C, NB><<<dim3((rest + 63) / 64, (rest + 63) / 64, N), 256, 0, s>>>(A, n,
-                                                                                                  k0);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = dense_update<C, NB>(A, n, k0, N, status, tc, s)) != cudaSuccess) return e;
             *launches += 2;
         }
         *launches += 1;
@@ -538,12 +650,12 @@ static cudaError_t dense_lu_t(C *A, int32_t *piv, int32_t *info, C *dinv, int n,
 }
 
 cudaError_t launch_dense_lu_c64(float2 *A, int32_t *piv, int32_t *info, float2 *dinv, int n, int N,
-                                cudaStream_t s, int64_t *launches) {
-    return dense_lu_t<float2, NB_C64>(A, piv, info, dinv, n, N, s, launches);
+                                cudaStream_t s, int64_t *launches, unsigned int *status, bool tc) {
+    return dense_lu_t<float2, NB_C64>(A, piv, info, dinv, n, N, s, launches, status, tc);
 }
 cudaError_t launch_dense_lu_c128(double2 *A, int32_t *piv, int32_t *info, double2 *dinv, int n, int N,
                                  cudaStream_t s, int64_t *launches) {
-    return dense_lu_t<double2, NB_C128>(A, piv, info, dinv, n, N, s, launches);
+    return dense_lu_t<double2, NB_C128>(A, piv, info, dinv, n, N, s, launches, nullptr, false);
 }
 
 cudaError_t launch_dense_solve_c64(const float2 *A, const int32_t *piv, const float2 *dinv, float2 *B,

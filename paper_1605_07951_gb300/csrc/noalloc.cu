@@ -72,14 +72,21 @@ extern "C" rsrr_status rsrr_solve_band_noalloc(int64_t n, int32_t kl, int32_t ku
     if (n < 1 || n > (int64_t)1 << 30 || kl < 0 || ku < 0 || L < 1 || !band || !U || !X)
         return noalloc_fail(RSRR_EINVAL, "bad argument");
     if (kl > KL_MAX) return noalloc_fail(RSRR_EINVAL, "lower bandwidth above 480");
+    // band rows beyond n - 1 would hold no entry of T; they are refused rather
+    // than carried through the factor storage
+    if ((int64_t)kl > n - 1 || (int64_t)ku > n - 1)
+        return noalloc_fail(RSRR_EINVAL, "half-bandwidths must be at most n - 1");
     const int NB = NB_C128;
-    BandGeom g;
-    g.kl = kl;
-    g.ku = ku;
-    g.nb = NB;
-    g.ldab = 2 * kl + ku + NB;
+    // every size in 64 bits (ku <= n - 1 < 2^30, kl <= 480, so ldab fits in int)
+    const int64_t ldab = 2 * (int64_t)kl + ku + NB;
     const int64_t nblk = (n + NB - 1) / NB;
-    const size_t b_ab = align256(sizeof(double2) * (size_t)g.ldab * n);
+    if (ldab > (int64_t)(kNoallocScratchBytes / sizeof(double2)) / n) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "needs more than %zu bytes of scratch, the fixed maximum is %zu",
+                 kNoallocScratchBytes, kNoallocScratchBytes);
+        return noalloc_fail(RSRR_EINVAL, buf);
+    }
+    const size_t b_ab = align256(sizeof(double2) * (size_t)ldab * (size_t)n);
     const size_t b_dinv = align256(sizeof(double2) * (size_t)nblk * 2 * NB * NB);
     const size_t b_piv = align256(sizeof(int32_t) * (size_t)n);
     const size_t b_info = align256(sizeof(int32_t));
@@ -89,8 +96,18 @@ extern "C" rsrr_status rsrr_solve_band_noalloc(int64_t n, int32_t kl, int32_t ku
                  b_ab + b_dinv + b_piv + b_info, kNoallocScratchBytes);
         return noalloc_fail(RSRR_EINVAL, buf);
     }
-    // device address of the scratch array on the current device (first call
-    // on a device only; it must come before any stream capture)
+    BandGeom g;
+    g.kl = kl;
+    g.ku = ku;
+    g.nb = NB;
+    g.ldab = (int)ldab;
+    // the solve's shared memory is checked before anything is launched
+    if (!band_solve_fits_c128(g))
+        return noalloc_fail(RSRR_EINVAL, "band too wide for the solve's shared memory");
+    // device address of the scratch array on the current device, looked up by
+    // the first call on that device (which should come before any stream
+    // capture) and kept for the life of the process; a cudaDeviceReset
+    // invalidates it, and the entry point is not usable after one
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(RSRR_ECUDA, "cudaGetDevice", e);

@@ -408,8 +408,11 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 // regions (tcgen05.ld; warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows,
 // columns 32 (w / 4) .. +31), fold groups 0..4 into 64-bit integers and add
 // groups 5..6 (relative weight <= 2^-40, rounded by design) into an FP32 sum;
-// the next MMAs restart every region.  Every mbarrier wait is bounded; a wait that runs out counts in
-// g_ozt_timeouts and the kernel finishes without hanging.
+// the next MMAs restart every region.  Every mbarrier wait is bounded; a wait that runs out is
+// counted in the caller's device status word, and from then on the CTA issues no further TMA copy
+// or MMA (the copy and MMA threads share an abort flag in shared memory; skipped stages still
+// commit their mbarriers so that the folds stay balanced), waits (bounded) for the copies it did
+// issue, and finishes without hanging.
 constexpr int OZT_BM = 128;
 constexpr int OZT_BN = 64;
 constexpr int OZT_KC = 16;
@@ -430,8 +433,6 @@ constexpr int OZT_FOLD = 12;                      // stages per exact fold (K' =
 constexpr long long OZT_WAIT_LIMIT = 1LL << 22;
 static_assert((4 + 1) * OZT_FOLD * OZT_KC * 16384 < (1 << 24), "group sums must stay exact in FP32");
 static_assert(OZ_S * OZT_BN <= 512, "one tensor-memory region per group");
-
-__device__ unsigned int g_ozt_timeouts;
 
 // shared-memory matrix descriptor: K-major, no swizzle, start / LBO (next core
 // matrix along K) / SBO (next 8-row group) in 16-byte units, version 1
@@ -469,6 +470,20 @@ RSRR_DEV bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = OZT_WA
     }
     return false;
 }
+// bounded wait that also gives up as soon as another thread of the CTA has
+// raised the abort flag (the copy and MMA threads; folds and the final drain
+// use the plain bounded wait so that operations in flight still land)
+RSRR_DEV bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, volatile int *abort_flag,
+                                 long long limit = OZT_WAIT_LIMIT) {
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (*abort_flag) return false;
+    }
+    return false;
+}
 RSRR_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
@@ -483,6 +498,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
                   const int *__restrict__ Ea, const int *__restrict__ Eb, double *__restrict__ W,
                   double2 *__restrict__ C, int64_t ldc, int M, int N, int Mp, int Np, int Kp, int kchunk,
                   int halfN_tiles, int upper_only, double alpha, double beta,
+                  unsigned int *__restrict__ status,
                   const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     const int bm = blockIdx.x, bn = blockIdx.y, sp = blockIdx.z;
     if (upper_only && OZT_BM * bm > OZT_BN * (bn % halfN_tiles) + OZT_BN - 1) return;
@@ -492,6 +508,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     const uint32_t mb_empty = mb_full + 8 * OZT_NST;       // OZT_NST: stage's MMAs done
     const uint32_t mb_fold = mb_empty + 8 * OZT_NST;       // all MMAs so far done
     uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(ozt_smem + OZT_NST * OZT_STAGE + 96);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = bm * OZT_BM, n0 = bn * OZT_BN;
     const int kbeg = sp * kchunk;
@@ -507,6 +524,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_empty + 8 * q));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_fold));
+        *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n"
@@ -532,7 +550,10 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     auto is_fold = [&](int st) { return ((st + 1) % OZT_FOLD) == 0 || st == nk - 1; };
     // every warp, after the MMAs of a fold stage: regions 0..4 into the integers
     auto fold_part = [&]() {
-        ok = mbar_wait(mb_fold, folds & 1) && ok;
+        if (!mbar_wait(mb_fold, folds & 1)) {
+            ok = false;
+            *abort_flag = 1;
+        }
         ++folds;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
@@ -555,11 +576,19 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
         // one thread issues the stage copies (TMA boxes of 8 K-elements x rows,
         // each box one column of 8 x 16-byte core matrices), OZT_DIST stages
         // ahead of the fold that follows a stage
+        int issued = 0;  // stages whose copies were issued (all of them unless a wait ran out)
         for (int st = 0; st < nk + OZT_DIST; ++st) {
-            if (st < nk && tid == 4 * 32) {
+            if (st < nk && tid == 4 * 32 && !*abort_flag) {
                 const int slot = st % OZT_NST;
                 // slot st % NST was last read by the MMAs of stage st - NST
-                if (st >= OZT_NST) ok = mbar_wait(mb_empty + 8 * slot, ((st / OZT_NST) - 1) & 1) && ok;
+                if (st >= OZT_NST &&
+                    !mbar_wait_or_abort(mb_empty + 8 * slot, ((st / OZT_NST) - 1) & 1, abort_flag)) {
+                    ok = false;
+                    *abort_flag = 1;
+                }
+            }
+            if (st < nk && tid == 4 * 32 && !*abort_flag) {
+                const int slot = st % OZT_NST;
                 const uint32_t full = mb_full + 8 * slot;
                 mbar_expect_tx(full, (uint32_t)OZT_STAGE);
                 const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
@@ -572,27 +601,35 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
                         tma_load_2d(a0 + p * OZT_A_SLICE + kc * OZT_LBO_A, &tmA, k + 8 * kc, p * Mp + m0, full);
                         tma_load_2d(b0 + kc * OZT_LBO_B + p * OZT_BN * 16, &tmB, k + 8 * kc, p * Np + n0, full);
                     }
+                issued = st + 1;
             }
             __syncwarp();
             const int done = st - OZT_DIST;
             if (done >= 0 && is_fold(done)) fold_part();
         }
-        // every copy has landed before the CTA leaves (waits bounded)
+        // every copy that was issued has landed before the CTA leaves (waits
+        // bounded; the last issued stage of each slot is its latest phase)
         if (tid == 4 * 32)
-            for (int st = max(0, nk - OZT_NST); st < nk; ++st)
+            for (int st = max(0, issued - OZT_NST); st < issued; ++st)
                 ok = mbar_wait(mb_full + 8 * (st % OZT_NST), (st / OZT_NST) & 1) && ok;
         __syncwarp();
     } else {
         for (int it = 0; it < nk; ++it) {
             if (tid == 0) {
                 const int slot = it % OZT_NST;
-                ok = mbar_wait(mb_full + 8 * slot, (it / OZT_NST) & 1) && ok;
+                bool go = !*abort_flag;
+                if (go && !mbar_wait_or_abort(mb_full + 8 * slot, (it / OZT_NST) & 1, abort_flag)) {
+                    ok = false;
+                    *abort_flag = 1;
+                    go = false;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
                 const uint32_t b0 = a0 + OZ_S * OZT_A_SLICE;
                 const uint32_t keep = (it % OZT_FOLD) == 0 ? 0u : 1u;  // all regions restart after a fold
 #pragma unroll
                 for (int p = 0; p < OZ_S; ++p) {
+                    if (!go) break;  // no MMA on a stage whose copies did not land
                     const uint64_t ad = umma_desc(a0 + p * OZT_A_SLICE, OZT_LBO_A);
                     // groups p .. 6 (q = 0 .. 6 - p): consecutive B slices into
                     // consecutive regions, at most 4 slices (N = 256) per MMA
@@ -603,6 +640,8 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
                                   umma_idesc(nq * OZT_BN), p == 0 ? keep : 1u);
                     }
                 }
+                // committed whether or not MMAs were issued: the slot and the
+                // fold barrier complete once every earlier MMA has finished
                 umma_commit(mb_empty + 8 * slot);
                 if (is_fold(it)) umma_commit(mb_fold);
             }
@@ -610,7 +649,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
             if (is_fold(it)) fold_part();
         }
     }
-    if (!ok && lane == 0) atomicAdd(&g_ozt_timeouts, 1u);
+    if (!ok && lane == 0) atomicAdd(status, 1u);
 
     const int i = m0 + lrow;
     const int ea = Ea[i];
@@ -635,17 +674,18 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
 
 // Failure-detection check of the bounded wait: one thread waits on an
 // mbarrier that nothing arrives on; the wait gives up after `limit` tries and
-// is counted in g_ozt_timeouts, exactly as in the tensor-core kernel.
-__global__ void ozt_wait_check_kernel(long long limit) {
+// is counted in the status word, exactly as in the tensor-core kernel.
+__global__ void ozt_wait_check_kernel(long long limit, unsigned int *status) {
     __shared__ __align__(8) unsigned long long bar;
     if (threadIdx.x != 0) return;
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(a) : "memory");
-    if (!mbar_wait(a, 0, limit)) atomicAdd(&g_ozt_timeouts, 1u);
+    if (!mbar_wait(a, 0, limit)) atomicAdd(status, 1u);
 }
 
-cudaError_t ozaki_timeouts(unsigned int *count) {
-    return cudaMemcpyFromSymbol(count, g_ozt_timeouts, sizeof *count);
+cudaError_t launch_wait_check(long long limit, unsigned int *status, cudaStream_t s) {
+    ozt_wait_check_kernel<<<1, 32, 0, s>>>(limit, status);
+    return cudaGetLastError();
 }
 
 // C = alpha sum_s W[s] + beta C (fixed order over the splits)
@@ -814,8 +854,10 @@ static cudaError_t slice_tensor_map(CUtensorMap *map, const __nv_bfloat16 *base,
 cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                         const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
                         double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
-                        int64_t *launches, EventPool *timer, double *tc_flops, bool legacy) {
+                        int64_t *launches, EventPool *timer, double *tc_flops, bool legacy,
+                        unsigned int *status) {
     if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!legacy && !status) return cudaErrorInvalidValue;
     cudaError_t e;
     if (K <= 0 || alpha == 0.0) {
         oz_scale_kernel<<<grid_for((int64_t)M * N), 256, 0, s>>>(C, ldc, M, N, beta);
@@ -886,7 +928,8 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
             oz_gemm_tc_kernel<<<grid, OZT_THREADS, OZT_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N,
                                                                  (int)p.Mp, (int)p.Np, (int)p.Kp,
                                                                  (int)p.kchunk, halfN_tiles,
-                                                                 upper ? 1 : 0, alpha, b, tmA, tmB);
+                                                                 upper ? 1 : 0, alpha, b, status,
+                                                                 tmA, tmB);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (timer && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
         if (tc_flops) *tc_flops += ozaki_tc_flops(M, N, Kc, upper, legacy);
@@ -946,18 +989,20 @@ extern "C" rsrr_status rsrr_zgemm(int32_t M, int32_t N, int32_t K, int32_t conjA
     } else {
         size_t need = ozaki_workspace_bytes(M, N, K, hermitian != 0);
         if (max_ws_bytes > 0) need = std::min(need, max_ws_bytes);
+        // the call's own status word (bounded waits that ran out) follows the
+        // slices in the same allocation
+        const size_t ws_bytes = need / 256 * 256;
         void *ws = nullptr;
-        if ((e = cudaMalloc(&ws, need)) != cudaSuccess) return fail(RSRR_ENOMEM, "work space", e);
-        unsigned int t0 = 0, t1 = 0;
-        if ((e = cudaMemcpyFromSymbol(&t0, g_ozt_timeouts, sizeof t0)) != cudaSuccess) {
-            cudaFree(ws);
-            return fail(RSRR_ECUDA, "timeout counter", e);
-        }
-        e = ozaki_zgemm(M, N, K, conjA != 0, a, lda, b, ldb, c, ldc, alpha, beta, hermitian != 0, ws,
-                        need, s, nullptr, nullptr, nullptr, legacy);
-        if (e == cudaSuccess && (e = cudaStreamSynchronize(s)) == cudaSuccess)
-            e = cudaMemcpyFromSymbol(&t1, g_ozt_timeouts, sizeof t1);
-        if (e == cudaSuccess && t1 != t0) {
+        if ((e = cudaMalloc(&ws, ws_bytes + 256)) != cudaSuccess) return fail(RSRR_ENOMEM, "work space", e);
+        unsigned int *status = reinterpret_cast<unsigned int *>(static_cast<char *>(ws) + ws_bytes);
+        unsigned int tmo = 0;
+        e = cudaMemsetAsync(status, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess)
+            e = ozaki_zgemm(M, N, K, conjA != 0, a, lda, b, ldb, c, ldc, alpha, beta, hermitian != 0, ws,
+                            ws_bytes, s, nullptr, nullptr, nullptr, legacy, status);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&tmo, status, sizeof tmo, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && tmo != 0) {
             cudaFree(ws);
             return fail(RSRR_ETIMEOUT, "a bounded tensor-core wait ran out");
         }
@@ -980,14 +1025,19 @@ extern "C" rsrr_status rsrr_check_wait_timeout(int32_t tries, void *stream) {
     };
     if (tries < 1 || tries > (1 << 20)) return fail(RSRR_EINVAL, "rsrr_check_wait_timeout: tries out of range");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned int t0 = 0, t1 = 0;
+    unsigned int *status = nullptr, tmo = 0;
     cudaError_t e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = ozaki_timeouts(&t0);
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(unsigned int));
     if (e != cudaSuccess) return fail(RSRR_ECUDA, "rsrr_check_wait_timeout", e);
-    ozt_wait_check_kernel<<<1, 32, 0, s>>>((long long)tries);
-    if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaStreamSynchronize(s)) == cudaSuccess)
-        e = ozaki_timeouts(&t1);
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        ozt_wait_check_kernel<<<1, 32, 0, s>>>((long long)tries, status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tmo, status, sizeof tmo, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(status);
     if (e != cudaSuccess) return fail(RSRR_ECUDA, "rsrr_check_wait_timeout", e);
-    if (t1 == t0) return fail(RSRR_OK, "rsrr_check_wait_timeout: the wait did not run out");
+    if (tmo == 0) return fail(RSRR_OK, "rsrr_check_wait_timeout: the wait did not run out");
     return fail(RSRR_ETIMEOUT, "a bounded tensor-core wait ran out");
 }

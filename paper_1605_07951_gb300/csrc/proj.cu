@@ -1,4 +1,4 @@
-// RSRR steps 3-4 on the GPU (Section 3.2 last paragraph, Section 3.3 steps
+// RSRR steps 3-4 on the GPU (Section 4.2 last paragraph, Section 4.3 steps
 // 3-4): unit-norm columns of S, an orthonormal basis Q of the dominant
 // singular subspace of S, and the projected coefficients P_i = Q^H A_i Q.
 //
@@ -148,6 +148,7 @@ struct Gemm {
     int method = RSRR_GEMM_FP64;
     void *ows = nullptr;      // work space of the sliced tensor-core products
     size_t ows_bytes = 0;
+    unsigned int *tmo = nullptr;  // the handle's status word of bounded waits that ran out
     cudaError_t run(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                     const double2 *B, int64_t ldb, double2 *C, int64_t ldc, cudaStream_t s,
                     bool hermitian = false, double alpha = 1.0, double beta = 0.0) {
@@ -169,7 +170,7 @@ struct Gemm {
             }
             e = ozaki_zgemm(M, N, K, conjA, A, lda, B, ldb, C, ldc, alpha, beta, hermitian, ows,
                             ows_bytes, s, counter, timer ? &timer->tc_pool : nullptr,
-                            timer ? &timer->tc_flops : nullptr, legacy);
+                            timer ? &timer->tc_flops : nullptr, legacy, tmo);
             if (e == cudaSuccess && timer) e = cudaEventRecord(ev1, s);
             return e;
         }
@@ -837,6 +838,7 @@ rsrr_status Handle::project(cudaStream_t s) {
     gm.method = opts.gemm;
     gm.ows = ws.ows;
     gm.ows_bytes = ws.ows_bytes;
+    gm.tmo = d_tmo;
     if (opts.timing) {
         gm.timer = this;
         gemm_pool.used = 0;
@@ -959,7 +961,13 @@ rsrr_status Handle::project(cudaStream_t s) {
     // (A10) P_q = Q^H (A_q Q); for the dense kernel the A_p are the Taylor
     // coefficients about the region centre, generated in place one after the
     // other in the (now free) complex128 matrix storage of the first point
-    if (dense) {
+    if (dense_terms) {  // caller-supplied dense A_q, resident on the device
+        for (int q = 0; q < m; ++q) {
+            const double2 *Aq = d_Aterms + (size_t)q * nn * nn;
+            PK(gm.run((int)nn, k, (int)nn, false, Aq, nn, d_Q, nn, ws.Ytmp, nn, s), "A_q Q");
+            PK(gm.run(k, k, (int)nn, true, d_Q, nn, ws.Ytmp, nn, d_P + (size_t)q * k * k, k, s), "Q^H A_q Q");
+        }
+    } else if (dense) {
         const double2 c = make_double2(region.center.re, region.center.im);
         for (int q = 0; q < m; ++q) {
             PK(launch_taylor_step(d_T64, d_points, c, diag, (int)nn, q, s), "Taylor coefficient");
@@ -1076,10 +1084,12 @@ rsrr_status Handle::solve(rsrr_result *out) {
     using cplx = std::complex<double>;
     cudaStream_t s = hs;
     PK(wait(), "solve sync");
-    {  // a bounded wait of a tensor-core product that ran out since rsrr_sample
-        unsigned int tnow = 0;
-        PK(ozaki_timeouts(&tnow), "timeout counter");
-        if (tnow != tmo_mark)
+    {  // a bounded wait of one of this handle's tensor-core products that ran
+       // out since rsrr_sample (the handle's own status word, read on its stream)
+        unsigned int tmo = 0;
+        PK(cudaMemcpyAsync(&tmo, d_tmo, sizeof tmo, cudaMemcpyDeviceToHost, s), "status word");
+        PK(cudaStreamSynchronize(s), "status word");
+        if (tmo != 0)
             return fail(RSRR_ETIMEOUT, "rsrr_solve: a bounded tensor-core wait ran out in sample or project");
     }
     const auto D2H = cudaMemcpyDeviceToHost;
@@ -1087,23 +1097,16 @@ rsrr_status Handle::solve(rsrr_result *out) {
     std::vector<cplx> lam, G;
     int nbar = 0;
     double gmax = 0.0;
-    const cplx cen(region.center.re, region.center.im);
-    auto f = [this, cen](int i, cplx z) {
-        if (dense) {  // Taylor powers (z - c)^i
-            cplx r = 1.0;
-            for (int q = 0; q < i; ++q) r *= (z - cen);
-            return r;
-        }
-        return eval_fn_host(fn[i], z);
-    };
     const cplx gamma(region.center.re, region.center.im);
-    // moments of T_Q^{-1} on the GPU, the rest of SS-FULL on the host
-    std::vector<cplx> fq((size_t)opts.NQ * m);
+    // moments of T_Q^{-1} on the GPU, the rest of SS-FULL on the host; f of
+    // every held term at the N_Q trapezoid nodes (Eq. 58)
+    std::vector<cplx> zq(opts.NQ), fq;
     for (int q = 0; q < opts.NQ; ++q) {
         const double t = 2.0 * M_PI * (q + 0.5) / opts.NQ;
-        const cplx z = gamma + cplx(region.a * std::cos(t), region.b * std::sin(t));
-        for (int i = 0; i < m; ++i) fq[(size_t)q * m + i] = f(i, z);
+        zq[q] = gamma + cplx(region.a * std::cos(t), region.b * std::sin(t));
     }
+    rsrr_status est = eval_terms(zq.data(), opts.NQ, fq);
+    if (est != RSRR_OK) return est;
     std::vector<std::vector<cplx>> Am;
     const rsrr_status mst = ssfull_moments(fq, opts.NQ, opts.KQ, Am);
     if (mst != RSRR_OK) return mst;
@@ -1124,7 +1127,9 @@ rsrr_status Handle::solve(rsrr_result *out) {
     const size_t vbytes = sizeof(double2) * (size_t)n * nbar;
     const size_t cbytes = sizeof(double2) * (size_t)nbar * std::max(m, 2);
     void *buf = nullptr;
-    const size_t tbytes = gbytes + vbytes + cbytes + sizeof(double) * 2 * nbar;
+    // dense terms: A_i V and the accumulated T(lambda) V as well
+    const size_t ybytes = dense_terms ? 2 * vbytes : 0;
+    const size_t tbytes = gbytes + vbytes + cbytes + sizeof(double) * 2 * nbar + ybytes;
     PK(pool ? cudaMallocFromPoolAsync(&buf, tbytes, pool, s) : cudaMalloc(&buf, tbytes), "solve buffers");
     struct Free {
         Handle *h;
@@ -1139,7 +1144,27 @@ rsrr_status Handle::solve(rsrr_result *out) {
     PK(cudaMemcpyAsync(d_G, G.data(), gbytes, H2D, s), "G");
     PK(gm.run((int)n, nbar, k, false, d_Q, n, d_G, k, d_V, n, s), "Q G");
     std::vector<double> t1(nbar, 0.0);
-    if (dense) {
+    // f of every held term at the eigenvalues (residual scale, sparse and dense-terms kinds)
+    std::vector<cplx> flam;
+    if (!dense || dense_terms) {
+        rsrr_status fst = eval_terms(lam.data(), nbar, flam);
+        if (fst != RSRR_OK) return fst;
+    }
+    if (dense_terms) {
+        std::vector<double2> cf((size_t)nbar * m);
+        for (size_t e = 0; e < cf.size(); ++e) cf[e] = make_double2(flam[e].real(), flam[e].imag());
+        PK(cudaMemcpyAsync(d_cf, cf.data(), sizeof(double2) * cf.size(), H2D, s), "coef");
+        double2 *d_Y = reinterpret_cast<double2 *>(reinterpret_cast<char *>(d_rr) + sizeof(double) * 2 * nbar);
+        double2 *d_TV = d_Y + (size_t)n * nbar;
+        // T(lambda_c) v_c = sum_i f_i(lambda_c) (A_i V)(:, c)
+        for (int i = 0; i < m; ++i) {
+            PK(gm.run((int)n, nbar, (int)n, false, d_Aterms + (size_t)i * n * n, n, d_V, n, d_Y, n, s), "A_i V");
+            PK(launch_accum_term_cols(d_TV, d_Y, d_cf, m, i, (int)n, nbar, i == 0, s), "T V");
+            launches += 1;
+        }
+        PK(launch_col_norms2(d_TV, d_V, (int)n, nbar, d_rr, d_vv, s), "residual norms");
+        launches += 1;
+    } else if (dense) {
         std::vector<double2> lz(nbar);
         for (int c = 0; c < nbar; ++c) lz[c] = make_double2(lam[c].real(), lam[c].imag());
         PK(cudaMemcpyAsync(d_cf, lz.data(), sizeof(double2) * nbar, H2D, s), "lam");
@@ -1152,11 +1177,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
         launches += 1;
     } else {
         std::vector<double2> cf((size_t)nbar * m);
-        for (int c = 0; c < nbar; ++c)
-            for (int q = 0; q < m; ++q) {
-                const cplx v = eval_fn_host(fn[q], lam[c]);
-                cf[(size_t)c * m + q] = make_double2(v.real(), v.imag());
-            }
+        for (size_t e = 0; e < cf.size(); ++e) cf[e] = make_double2(flam[e].real(), flam[e].imag());
         PK(cudaMemcpyAsync(d_cf, cf.data(), sizeof(double2) * cf.size(), H2D, s), "coef");
         PK(cudaMemsetAsync(d_rr, 0, sizeof(double) * 2 * nbar, s), "memset");
         eig_residual_kernel<<<dim3((unsigned)((n + 255) / 256), nbar), 256, 0, s>>>(
@@ -1170,13 +1191,6 @@ rsrr_status Handle::solve(rsrr_result *out) {
     PK(cudaMemcpyAsync(vv.data(), d_vv, sizeof(double) * nbar, D2H, s), "vv");
     PK(cudaMemcpyAsync(V.data(), d_V, sizeof(double2) * V.size(), D2H, s), "V");
     PK(cudaStreamSynchronize(s), "solve results");
-    // ||A_i||_1 (max column sum) on the host
-    std::vector<double> a1(m, 0.0);
-    for (int q = 0; q < m && !dense; ++q) {
-        std::vector<double> colsum(n, 0.0);
-        for (int64_t e = 0; e < nnz; ++e) colsum[h_col_idx[e]] += std::fabs(h_vals[(size_t)q * nnz + e]);
-        for (double v : colsum) a1[q] = std::max(a1[q], v);
-    }
     struct Pair { cplx lam; double res; int c; };
     std::vector<Pair> keep;
     for (int c = 0; c < nbar; ++c) {
@@ -1184,9 +1198,8 @@ rsrr_status Handle::solve(rsrr_result *out) {
         const double y = (lam[c].imag() - region.center.im) / region.b;
         if (!(x * x + y * y < 1.0)) continue;
         double scale = 0.0;
-        if (dense) scale = t1[c];  // ||T(lam)||_1 computed directly
-        else
-            for (int q = 0; q < m; ++q) scale += std::abs(eval_fn_host(fn[q], lam[c])) * a1[q];
+        if (dense && !dense_terms) scale = t1[c];  // ||T(lam)||_1 of the kernel computed directly
+        else scale = residual_scale(flam.data() + (size_t)c * m);  // sum_u |f_u(lam)| ||A_u||_1
         const double res = std::sqrt(rr[c]) / (scale * std::sqrt(vv[c]));
         if (!(res <= opts.res_tol)) continue;
         keep.push_back({lam[c], res, c});
@@ -1222,5 +1235,7 @@ extern "C" rsrr_status rsrr_solve(rsrr_t *hh, rsrr_result *out) {
     rsrr::Handle *h = reinterpret_cast<rsrr::Handle *>(hh);
     if (!h || !out) return RSRR_EINVAL;
     if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_solve: no rsrr_project yet");
-    return h->solve(out);
+    const rsrr_status st = h->solve(out);
+    h->solved = st >= 0;
+    return st;
 }

@@ -28,7 +28,15 @@ struct Handle {
     // problem
     int64_t n = 0, nnz = 0;
     int N = 0, L = 0, m = 0, kl = 0, ku = 0;
-    rsrr_fn fn[RSRR_MAX_TERMS] = {};
+    // the terms as held: a caller term with complex sparse values becomes two,
+    // Re A_u with f_u and Im A_u with i f_u (fn_imag marks the second)
+    std::vector<rsrr_fn> fn;
+    std::vector<int> fn_src;          // caller term of each held term
+    std::vector<char> fn_imag;        // held term is the imaginary part of its caller term
+    std::vector<double> a1;           // ||A_u||_1 of the caller's terms (residual scale)
+    rsrr_fn_callback cb = nullptr;    // RSRR_F_CALLBACK terms
+    void *cb_user = nullptr;
+    uint64_t seed = 0;                // default probe
     rsrr_region region = {};
     rsrr_opts opts = {};
     BandGeom geom = {};
@@ -36,8 +44,11 @@ struct Handle {
     std::vector<std::complex<double>> z;
     std::vector<int32_t> h_row_ptr, h_col_idx, h_csc_ptr, h_csc_row, h_csc_perm;
     std::vector<double> h_vals;
-    // dense (Helmholtz kernel) problems
+    // dense problems: the Helmholtz kernel, or caller-supplied dense terms
     bool dense = false;
+    bool dense_terms = false;         // T = sum_i f_i A_i with dense A_i (RSRR_NEP_DENSE)
+    std::vector<double2> h_Aterms;    // m x n^2 host copy, dropped after the upload
+    double2 *d_Aterms = nullptr;      // m x n^2 on the device
     double diag = 0.0;
     std::vector<double> h_points;
     double *d_points = nullptr;       // 3n
@@ -87,14 +98,16 @@ struct Handle {
     std::vector<double> res_res;
 
     // state
-    bool sampled = false, projected = false;
+    bool sampled = false, projected = false, solved = false;
     int stat_sweeps = 0, stat_converged = 0, stat_singular = -1;
     double stat_max_eta = 0.0;
     std::string err;
     int64_t launches = 0;
     cudaEvent_t events[8] = {};
     bool timed_sample = false, timed_project = false;
-    unsigned int tmo_mark = 0;  // tensor-core wait timeouts counted before this sample
+    // device word counting the bounded tensor-core waits that ran out in this
+    // handle's products since its last rsrr_sample (zeroed there, read by rsrr_solve)
+    unsigned int *d_tmo = nullptr;
     double stage_ms[6] = {};
     // GEMM timing of the last rsrr_project (opts.timing)
     EventPool gemm_pool;                // pairs around every product
@@ -109,20 +122,32 @@ struct Handle {
     template <typename T> cudaError_t alloc(T **p, size_t count);
     cudaError_t raw_alloc(void **p, size_t bytes);
     cudaError_t raw_free(void *p);
+    void release(void *p, size_t bytes);
+    template <typename T> cudaError_t regrow(T **p, size_t per, int N0, int N1, bool keep);
     cudaError_t wait();
     rsrr_status allocate();
     size_t estimate_bytes();
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);
-    rsrr_status sample(cudaStream_t s);
-    cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, cudaStream_t s);
-    rsrr_status sample_dense(cudaStream_t s);
-    rsrr_status dense_residual(bool skip_done, cudaStream_t s);
+    rsrr_status sample(cudaStream_t s);  // every point, band or dense
+    rsrr_status sample_band(int p0, int np, cudaStream_t s);
+    cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);
+    rsrr_status sample_dense(int p0, int np, cudaStream_t s);
+    rsrr_status dense_residual(bool skip_done, int p0, int np, cudaStream_t s);
+    // appends sampling points (buffers regrown, the old samples kept) and
+    // samples only the new ones
+    rsrr_status add_points(const std::complex<double> *znew, int count, cudaStream_t s);
     bool dense_residual_sliced() const;
     rsrr_status allocate_dense();
     rsrr_status read_outcome();
     rsrr_status mark(int i, cudaStream_t s);
     rsrr_status project(cudaStream_t s);
     rsrr_status solve(rsrr_result *out);
+    // f of every held term at count points (point-major, count x fn.size());
+    // EINVAL if a value is not finite
+    rsrr_status eval_terms(const std::complex<double> *z, int64_t count,
+                           std::vector<std::complex<double>> &out);
+    // sum over the caller's terms of |f_u(lam)| ||A_u||_1, from held-term values
+    double residual_scale(const std::complex<double> *f_held) const;
     rsrr_status ssfull_moments(const std::vector<std::complex<double>> &fq, int NQ, int KQ,
                                std::vector<std::vector<std::complex<double>>> &Am);
 };

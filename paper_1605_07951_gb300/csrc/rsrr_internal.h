@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#define RSRR_MAX_TERMS_DEV 8
+#define RSRR_MAX_TERMS_DEV 16
 
 namespace rsrr {
 
@@ -63,6 +63,9 @@ cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const fl
 cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, const double2 *dinv,
                                    double2 *B, const BandGeom &g, int N, int n, int L,
                                    const int32_t *skip, cudaStream_t s);
+// whether the one-kernel complex128 solve's shared memory (its smallest
+// right-hand-side chunk) fits the device's opt-in limit for this geometry
+bool band_solve_fits_c128(const BandGeom &g);
 cudaError_t launch_residual(double2 *R, const double2 *X, const DevProblem &p, double *rmax,
                             double *xmax, const int32_t *skip, cudaStream_t s);
 cudaError_t launch_eta(double *eta, int32_t *done, const double *rmax, const double *xmax,
@@ -85,8 +88,19 @@ cudaError_t launch_assemble_dense_c64(float2 *A, const double *pts, const double
 cudaError_t launch_assemble_dense_c128(double2 *A, const double *pts, const double2 *zs, double diag,
                                        int n, int N, cudaStream_t s);
 cudaError_t launch_dense_tnorm(double *tnorm, const double2 *A, int n, int N, cudaStream_t s);
+// dense-terms kind: T(z_j) = sum_i coef[j m + i] A_i (A: m x n^2, term-major)
+cudaError_t launch_assemble_dense_terms(double2 *T, const double2 *A, const double2 *coef, int n, int N,
+                                        int m, cudaStream_t s);
+// R(:, c) (+)= cf[c m + i] Y(:, c), c < cnt (first: R = ...)
+cudaError_t launch_accum_term_cols(double2 *R, const double2 *Y, const double2 *cf, int m, int i, int n,
+                                   int cnt, bool first, cudaStream_t s);
+// squared 2-norms of the columns of R and V
+cudaError_t launch_col_norms2(const double2 *R, const double2 *V, int n, int cnt, double *rr, double *vv,
+                              cudaStream_t s);
+// complex64 LU; tc: trailing updates on the tensor cores (3xTF32, dense_tc.cu),
+// bounded waits counted in *status
 cudaError_t launch_dense_lu_c64(float2 *A, int32_t *piv, int32_t *info, float2 *dinv, int n, int N,
-                                cudaStream_t s, int64_t *launches);
+                                cudaStream_t s, int64_t *launches, unsigned int *status, bool tc);
 cudaError_t launch_dense_lu_c128(double2 *A, int32_t *piv, int32_t *info, double2 *dinv, int n, int N,
                                  cudaStream_t s, int64_t *launches);
 cudaError_t launch_dense_solve_c64(const float2 *A, const int32_t *piv, const float2 *dinv, float2 *B,
@@ -140,15 +154,21 @@ cudaError_t fp64_gemm(int M, int N, int K, bool conjA, const double2 *A, int64_t
 // With timer set, a pair of events brackets every launch of the main kernel
 // and *tc_flops grows by the tensor-core flops it issues.  The main kernel is
 // the tcgen05 one; legacy selects the mma.sync kernel (kept for comparison).
+// status: a device word of the caller (a handle, a request, one rsrr_zgemm
+// call) into which every bounded wait of the tcgen05 kernel that ran out is
+// counted; required unless legacy.  Callers zero it and read it back on their
+// own stream, so a timeout in one caller's product never reaches another's.
 struct EventPool;
 cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                         const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
                         double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
                         int64_t *launches, EventPool *timer = nullptr, double *tc_flops = nullptr,
-                        bool legacy = false);
+                        bool legacy = false, unsigned int *status = nullptr);
 size_t ozaki_workspace_bytes(int M, int N, int K, bool hermitian);
-// bounded tensor-core waits that ran out so far (a device-wide counter)
-cudaError_t ozaki_timeouts(unsigned int *count);
+// one thread waits, with the tcgen05 kernel's bounded mbarrier wait, on a
+// barrier that nothing completes; after `limit` polls the wait is counted in
+// *status (failure detection without a GPU fault)
+cudaError_t launch_wait_check(long long limit, unsigned int *status, cudaStream_t s);
 // bf16 tensor-core flops the product issues (2 per multiply-add of slices);
 // legacy: the mma.sync kernel (64-row tiles) instead of the tcgen05 kernel
 double ozaki_tc_flops(int M, int N, int K, bool hermitian, bool legacy = false);

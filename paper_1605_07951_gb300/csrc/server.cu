@@ -1,5 +1,5 @@
 // Request server: continuous batching of whole RSRR solves (steps 1-5 of
-// Section 3.3) on one GPU.
+// Section 4.3) on one GPU.
 //
 // A request is prepared on the submitting thread (descriptors validated and
 // copied, sampling points and f_i(z_j) computed, device bytes estimated) and
@@ -102,7 +102,7 @@ struct Server {
             if (e == cudaSuccess) e = launch_colmax(h->d_umax, h->d_U, (int)h->n, h->L, s);
             if (e != cudaSuccess) st = h->fail(RSRR_ECUDA, "probe upload", e);
         }
-        if (st == RSRR_OK) st = h->dense ? h->sample_dense(s) : h->sample(s);
+        if (st == RSRR_OK) st = h->sample(s);
         if (st == RSRR_OK) {
             h->sampled = true;
             cudaError_t e = cudaStreamSynchronize(s);

@@ -1,11 +1,11 @@
-// Moments of SS-FULL (Section 2.3 with U = I) for the projected NEP on the
+// Moments of SS-FULL (Section 3.3 with U = I) for the projected NEP on the
 // GPU, in FP64:
 //
 //     A_alpha = sum_q w_q s_q^alpha T_Q(z_q)^{-1},   alpha < 2 K_Q,
 //
 // with the N_Q trapezoid nodes z_q = gamma + a cos t_q + i b sin t_q,
 // t_q = 2 pi (q + 1/2) / N_Q, weights w_q = (-a sin t_q + i b cos t_q) / N_Q
-// (Section 4.1) and scaled powers s_q = (z_q - gamma) / rho, rho = max(a, b).
+// (Section 5.1) and scaled powers s_q = (z_q - gamma) / rho, rho = max(a, b).
 // Nodes are processed in chunks: T_Q(z_q) = sum_i f_i(z_q) P_i is assembled
 // for every node of the chunk, factored by the batched complex128 dense LU
 // (partial pivoting), T_Q^{-1} obtained by the batched solve with the identity

@@ -1,7 +1,7 @@
 // SS-FULL on the projected NEP T_Q(z) = sum_i f_i(z) P_i (k x k), in FP64 on
 // the host, from the moments A_alpha = sum_q w_q ((z_q - gamma)/rho)^alpha
 // T_Q(z_q)^{-1} (computed on the GPU, ssfull_dev.cu): the SS-RI algorithm of
-// Section 2.3 with U = I, block Hankel matrices H and H^<, truncated SVD of H
+// Section 3.3 with U = I, block Hankel matrices H and H^<, truncated SVD of H
 // with the count given by the largest singular-value gap (tol_gap test),
 // A = V0^H H^< W0 Sigma0^{-1}, and the eigenpairs of A lifted by
 // g = M W0 Sigma0^{-1} b with M = [A_0 .. A_{K-1}].

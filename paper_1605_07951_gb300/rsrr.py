@@ -25,12 +25,13 @@ _lib = C.CDLL(LIB_PATH)
 # ---------------------------------------------------------------- constants
 RSRR_OK, RSRR_EINVAL, RSRR_ENOMEM, RSRR_ESINGULAR = 0, -1, -2, -3
 RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7, 1
-RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP = range(6)
+(RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP, RSRR_F_TAYLOR,
+ RSRR_F_CALLBACK) = range(8)
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI, RSRR_GEMM_OZAKI_MMA = 0, 1, 2, 3
-RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU = 1, 2
-RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ = 0, 1
+RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU, RSRR_FLAG_INJECT_TIMEOUT, RSRR_FLAG_SIMT_DENSE_UPDATE = 1, 2, 4, 8
+RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ, RSRR_NEP_DENSE = 0, 1, 2
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",
                 -5: "ETIMEOUT", -6: "ECUDA", -7: "ESTATE", 1: "WGAP"}
@@ -42,15 +43,23 @@ class rsrr_c128(C.Structure):
 
 
 class rsrr_fn(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("param", C.c_double),
-                ("scale", rsrr_c128)]
+    _fields_ = [("kind", C.c_int32), ("power", C.c_int32), ("param", C.c_double),
+                ("scale", rsrr_c128), ("shift", rsrr_c128)]
+
+
+# void (*)(int32_t term, const rsrr_c128 *z, int64_t count, rsrr_c128 *out, void *user)
+rsrr_fn_callback = C.CFUNCTYPE(None, C.c_int32, C.POINTER(rsrr_c128), C.c_int64,
+                               C.POINTER(rsrr_c128), C.c_void_p)
 
 
 class rsrr_nep(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("kind", C.c_int32),
                 ("row_ptr", C.POINTER(C.c_int64)), ("col_idx", C.POINTER(C.c_int32)),
                 ("values", C.POINTER(C.c_double)), ("fn", rsrr_fn * RSRR_MAX_TERMS),
-                ("points", C.POINTER(C.c_double)), ("diag", C.c_double)]
+                ("points", C.POINTER(C.c_double)), ("diag", C.c_double),
+                ("values_complex", C.c_int32), ("reserved", C.c_int32),
+                ("dense", C.POINTER(C.POINTER(rsrr_c128))), ("callback", rsrr_fn_callback),
+                ("callback_user", C.c_void_p)]
 
 
 class rsrr_region(C.Structure):
@@ -63,7 +72,7 @@ class rsrr_opts(C.Structure):
                 ("delta", C.c_double), ("delta_floor", C.c_double), ("tol_gap", C.c_double),
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
                 ("host_threads", C.c_int32), ("timing", C.c_int32), ("gemm", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("seed", C.c_uint64), ("mem_budget_bytes", C.c_int64)]
 
 
 class rsrr_stats(C.Structure):
@@ -122,6 +131,7 @@ rsrr_create = _sig("rsrr_create", C.c_int, [C.POINTER(rsrr_nep), C.POINTER(rsrr_
 rsrr_set_probe = _sig("rsrr_set_probe", C.c_int, [_h, _p, C.c_int32, _p])
 rsrr_sample = _sig("rsrr_sample", C.c_int, [_h, _p])
 rsrr_check = _sig("rsrr_check", C.c_int, [_h, _p])
+rsrr_add_points = _sig("rsrr_add_points", C.c_int, [_h, _p, C.c_int32, _p])
 rsrr_project = _sig("rsrr_project", C.c_int, [_h, _p])
 rsrr_solve = _sig("rsrr_solve", C.c_int, [_h, C.POINTER(rsrr_result)])
 rsrr_get_samples = _sig("rsrr_get_samples", C.c_int, [_h, _p, C.c_int32, _p])
@@ -129,6 +139,8 @@ rsrr_get_eta = _sig("rsrr_get_eta", C.c_int, [_h, _p])
 rsrr_get_Q = _sig("rsrr_get_Q", C.c_int, [_h, _p, C.c_int32, _p])
 rsrr_get_projected = _sig("rsrr_get_projected", C.c_int, [_h, _p, C.c_int32, _p])
 rsrr_get_points = _sig("rsrr_get_points", C.c_int, [_h, _p])
+rsrr_copy_result = _sig("rsrr_copy_result", C.c_int,
+                        [_h, C.c_int32, C.POINTER(C.c_int32), _p, _p, _p])
 rsrr_get_stats = _sig("rsrr_get_stats", C.c_int, [_h, C.POINTER(rsrr_stats)])
 rsrr_last_error = _sig("rsrr_last_error", C.c_char_p, [_h])
 rsrr_destroy = _sig("rsrr_destroy", None, [_h])
@@ -185,34 +197,65 @@ def default_opts(**kw) -> rsrr_opts:
     return o
 
 
+def _fn_struct(fn):
+    sc = complex(fn.scale)
+    sh = complex(getattr(fn, "shift", 0.0))
+    return rsrr_fn(int(fn.kind), int(getattr(fn, "power", 0)), float(fn.param),
+                   rsrr_c128(sc.real, sc.imag), rsrr_c128(sh.real, sh.imag))
+
+
+def _make_callback(fns, keep):
+    """One C callback for the problem's RSRR_F_CALLBACK terms: term i is
+    evaluated by fns[i].callback(z) (a numpy vector of points)."""
+    def cb(term, zp, count, outp, user):
+        z = np.ctypeslib.as_array(C.cast(zp, C.POINTER(C.c_double)), shape=(count * 2,)).view(np.complex128)
+        out = np.ctypeslib.as_array(C.cast(outp, C.POINTER(C.c_double)), shape=(count * 2,)).view(np.complex128)
+        out[:] = np.asarray(fns[term].callback(z.copy()), dtype=np.complex128)
+    f = rsrr_fn_callback(cb)
+    keep.append(f)
+    return f
+
+
 def describe(prob):
     """rsrr_nep and rsrr_region structures for a problem description (see
-    Solver), plus the arrays they point into (keep them alive while the
-    structures are in use)."""
+    Solver), plus the objects they point into (keep them alive while the
+    structures, or a handle built from them, are in use)."""
     keep = []
     nep = rsrr_nep()
     nep.n = int(prob.n)
-    dense = getattr(prob, "points", None) is not None and not hasattr(prob, "row_ptr")
-    if dense:
+    fns = getattr(prob, "fns", [])
+    if getattr(prob, "As", None) is not None:
+        nep.kind = RSRR_NEP_DENSE
+        nep.m = len(prob.As)
+        mats = [np.asfortranarray(np.asarray(A, dtype=np.complex128)) for A in prob.As]
+        keep += mats
+        ptrs = (C.POINTER(rsrr_c128) * len(mats))(*[m.ctypes.data_as(C.POINTER(rsrr_c128)) for m in mats])
+        keep.append(ptrs)
+        nep.dense = C.cast(ptrs, C.POINTER(C.POINTER(rsrr_c128)))
+    elif getattr(prob, "points", None) is not None and not hasattr(prob, "row_ptr"):
         pts = np.ascontiguousarray(np.asarray(prob.points, dtype=np.float64))
         keep.append(pts)
         nep.kind = RSRR_NEP_HELMHOLTZ
         nep.points = pts.ctypes.data_as(C.POINTER(C.c_double))
         nep.diag = float(prob.diag)
+        fns = []
     else:
         row_ptr = np.ascontiguousarray(prob.row_ptr, dtype=np.int64)
         col_idx = np.ascontiguousarray(prob.col_idx, dtype=np.int32)
-        values = np.ascontiguousarray(np.concatenate(
-            [np.asarray(v, dtype=np.float64) for v in prob.values]))
+        cplx = any(np.iscomplexobj(v) for v in prob.values)
+        dt = np.complex128 if cplx else np.float64
+        values = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=dt) for v in prob.values]))
         keep += [row_ptr, col_idx, values]
         nep.kind = RSRR_NEP_SPARSE
         nep.m = len(prob.values)
+        nep.values_complex = 1 if cplx else 0
         nep.row_ptr = row_ptr.ctypes.data_as(C.POINTER(C.c_int64))
         nep.col_idx = col_idx.ctypes.data_as(C.POINTER(C.c_int32))
         nep.values = values.ctypes.data_as(C.POINTER(C.c_double))
-        for i, fn in enumerate(prob.fns):
-            sc = complex(fn.scale)
-            nep.fn[i] = rsrr_fn(int(fn.kind), 0, float(fn.param), rsrr_c128(sc.real, sc.imag))
+    for i, fn in enumerate(fns):
+        nep.fn[i] = _fn_struct(fn)
+    if any(int(fn.kind) == RSRR_F_CALLBACK for fn in fns):
+        nep.callback = _make_callback(fns, keep)
     reg = rsrr_region()
     r = prob.region
     reg.center = rsrr_c128(complex(r.center).real, complex(r.center).imag)
@@ -249,12 +292,24 @@ def prepared(prob, opts: rsrr_opts | None = None, N=None, L=None):
     L = int(L if L is not None else prob.L)
     dense = nep.kind == RSRR_NEP_HELMHOLTZ
     z = np.zeros(N, dtype=np.complex128)
-    coef = None if dense else np.zeros((N, nep.m), dtype=np.complex128)
+    # held terms: a term with complex sparse values may be held as two
+    mh = 2 * nep.m if nep.values_complex else nep.m
+    coef = None if dense else np.zeros((N, mh), dtype=np.complex128)
     kl, ku = C.c_int32(-1), C.c_int32(-1)
     st = rsrr_describe(C.byref(nep), C.byref(reg), N, L, C.byref(o), z.ctypes.data,
                        None if coef is None else coef.ctypes.data, C.byref(kl), C.byref(ku))
     if st != RSRR_OK:
         raise RSRRError(st, rsrr_last_error(None).decode())
+    if coef is not None and nep.values_complex:
+        # keep the held terms' columns (terms whose imaginary parts are all
+        # zero are held once)
+        held = []
+        for v in prob.values:
+            held.append(True)
+            held.append(bool(np.any(np.asarray(v).imag != 0)))
+        cols = [c for c, h in enumerate(held) if h]
+        flat = coef.reshape(-1)[:N * len(cols)].reshape(N, len(cols))
+        coef = flat
     return z, coef, (kl.value, ku.value)
 
 
@@ -360,7 +415,7 @@ class Solver:
         self.L = int(L if L is not None else prob.L)
         self.n = int(prob.n)
         nep, reg, self._keep = describe(prob)
-        self.dense = nep.kind == RSRR_NEP_HELMHOLTZ
+        self.dense = nep.kind in (RSRR_NEP_HELMHOLTZ, RSRR_NEP_DENSE)
         self.opts = opts if opts is not None else default_opts()
         h = _h()
         st = rsrr_create(C.byref(nep), C.byref(reg), self.N, self.L, C.byref(self.opts),
@@ -398,6 +453,13 @@ class Solver:
 
     def sample(self, stream=None):
         return self._check(rsrr_sample(self.h, _stream_handle(stream)))
+
+    def add_points(self, z_new, stream=None):
+        """Appends sampling points and samples only them (rsrr_add_points)."""
+        z = np.ascontiguousarray(np.asarray(z_new, dtype=np.complex128).ravel())
+        st = self._check(rsrr_add_points(self.h, z.ctypes.data_as(C.c_void_p), len(z), _stream_handle(stream)))
+        self.N += len(z)
+        return st
 
     def check(self, stream=None):
         return self._check(rsrr_check(self.h, _stream_handle(stream)))
@@ -454,6 +516,20 @@ class Solver:
         self._check(rsrr_get_projected(self.h, P.ctypes.data_as(C.c_void_p), 0,
                                        _stream_handle(stream)))
         return [P[i].T.copy() for i in range(m)]
+
+    def copy_result(self):
+        """The last rsrr_solve's eigenpairs through rsrr_copy_result (caller buffers)."""
+        cnt = C.c_int32(0)
+        st = rsrr_copy_result(self.h, 0, C.byref(cnt), None, None, None)
+        if st not in (RSRR_OK, RSRR_EINVAL):
+            self._check(st)
+        k = cnt.value
+        lam = np.zeros(k, dtype=np.complex128)
+        res = np.zeros(k, dtype=np.float64)
+        V = np.zeros((k, self.n), dtype=np.complex128)
+        self._check(rsrr_copy_result(self.h, k, C.byref(cnt), lam.ctypes.data_as(C.c_void_p),
+                                     res.ctypes.data_as(C.c_void_p), V.ctypes.data_as(C.c_void_p)))
+        return dict(lam=lam, res=res, V=V.T)
 
     def solve(self) -> dict:
         r = rsrr_result()

@@ -52,7 +52,7 @@ def test_binding_uses_the_same_names(lib):
 def test_struct_layouts_match_the_header(lib):
     from paper_1605_07951_gb300 import rsrr
     assert ctypes.sizeof(rsrr.rsrr_c128) == 16
-    assert ctypes.sizeof(rsrr.rsrr_fn) == 32
+    assert ctypes.sizeof(rsrr.rsrr_fn) == 48
     assert ctypes.sizeof(rsrr.rsrr_region) == 48
     # defaults come from the library itself
     o = rsrr.default_opts()
@@ -148,3 +148,16 @@ def test_estimate_bytes_needs_no_gpu_and_counts_the_resident_buffers(lib):
     with pytest.raises(rsrr.RSRRError) as e:
         rsrr.estimate_bytes(bad)
     assert e.value.status == rsrr.RSRR_EINVAL
+
+
+def test_create_refuses_a_handle_above_its_memory_budget(lib):
+    """mem_budget_bytes is checked against rsrr_estimate_bytes before any
+    device memory is touched."""
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    p = W.config("c1")
+    need = rsrr.estimate_bytes(p)
+    with pytest.raises(rsrr.RSRRError) as e:
+        rsrr.Solver(p, rsrr.default_opts(mem_budget_bytes=need - 1))
+    assert e.value.status == rsrr.RSRR_ENOMEM
+    assert "mem_budget_bytes" in str(e.value)

@@ -70,3 +70,31 @@ def test_dense_eigenpairs_match_oracle(rs, n):
     for q in (0, 1, 5, len(A) - 1):
         Pr = Q.conj().T @ A[q] @ Q
         assert np.abs(P[q] - Pr).max() <= 1e-12 * max(np.abs(A[q]).sum(axis=0).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,N,L", [(300, 4, 5), (160, 3, 8), (129, 2, 3)])
+def test_tensor_core_dense_update_matches_the_fma_update(rs, n, N, L):
+    """The complex64 LU's trailing updates on the tensor cores (3xTF32) and on
+    FP32 FMAs: one solve from each factor agrees to complex64 rounding, and
+    both refine to the oracle."""
+    p = W.helmholtz_sphere(n=n, N=N, L=L)
+    out = {}
+    for name, flags in (("tc", 0), ("simt", rs.RSRR_FLAG_SIMT_DENSE_UPDATE)):
+        s = rs.Solver(p, rs.default_opts(max_refine=0, flags=flags))
+        s.sample()
+        S0 = s.samples()
+        s.close()
+        s = rs.Solver(p, rs.default_opts(flags=flags))
+        s.sample()
+        assert s.check_status() == rs.RSRR_OK
+        out[name] = (S0, s.samples(), s.eta())
+        s.close()
+    a0, b0 = out["tc"][0], out["simt"][0]
+    assert np.abs(a0 - b0).max() <= 1e-4 * np.abs(b0).max()
+    zo = oracle.sample_points(p.region, p.N)
+    ref = oracle.resolvent_samples_dense(p, zo)
+    for name in out:
+        S, eta = out[name][1], out[name][2]
+        assert eta.max() <= 1e-10
+        for j, Xr in enumerate(ref):
+            assert np.abs(S[:, j * L:(j + 1) * L] - Xr).max() <= 1e-6 * np.abs(Xr).max()

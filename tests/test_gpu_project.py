@@ -113,7 +113,7 @@ def test_loaded_string_example_of_the_paper(rs, mode, gemm):
     refinement target is tightened from 1e-10 to 1e-14."""
     gold = json.load(open(os.path.join(GOLD, "loaded_string.json")))
     p = W.loaded_string(n=gold["n"], N=gold["N"], L=gold["L"])
-    # the paper's truncation delta = 1e-14 (Section 3.3) as the resolution floor
+    # the paper's truncation delta = 1e-14 (Section 4.3) as the resolution floor
     if mode == "fp64":
         out = gpu_rsrr(rs, p, NQ=gold["NQ"], KQ=gold["KQ"], precision=rs.RSRR_PREC_FP64,
                        delta_floor=1e-14, gemm=gemm)
@@ -125,7 +125,7 @@ def test_loaded_string_example_of_the_paper(rs, mode, gemm):
     assert len(lam) == gold["count"]
     assert np.all((lam.real > lo) & (lam.real < hi))
     plain = [oracle.plain_residual(p, l, v) for l, v in zip(lam, out["V"].T)]
-    # the paper's level: ~1e-11 typical (Section 4.2), floor around 1e-10 (Section 4.3)
+    # the paper's level: ~1e-11 typical (Section 5.2), floor around 1e-10 (Section 5.3)
     assert np.median(plain) <= 10 * gold["plain_residual_level"]
     assert max(plain) <= 2 * gold["residual_floor"]
     ref = oracle.rsrr(p, NQ=gold["NQ"], KQ=gold["KQ"])

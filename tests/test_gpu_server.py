@@ -160,3 +160,24 @@ def test_failed_request_does_not_disturb_the_others(rs, lone_results):
     st = sv.stats()
     sv.close()
     assert st["failed"] == 1 and st["completed"] == 3 and st["used_bytes"] == 0
+
+
+def test_timeout_in_one_request_stays_with_that_request(rs, lone_results):
+    """A bounded device wait that runs out in one request (injected on the
+    host side: a wait on a barrier nothing completes, counted in that
+    request's own status word) makes that request return ETIMEOUT; the
+    requests running beside it return OK with their lone results."""
+    sv = rs.Server(slots=4)
+    good = [(name, sv.submit(make(), rs.default_opts(NQ=NQ))) for name, make, NQ in MIX[:3]]
+    bad = sv.submit(W.diag_quadratic(),
+                    rs.default_opts(NQ=256, flags=rs.RSRR_FLAG_INJECT_TIMEOUT))
+    more = [(name, sv.submit(make(), rs.default_opts(NQ=NQ))) for name, make, NQ in MIX[3:5]]
+    rb = sv.wait(bad, timeout=600.0)
+    assert rb["status"] == rs.RSRR_ETIMEOUT, rb["error"]
+    for name, rid in good + more:
+        rep = sv.wait(rid, timeout=600.0)
+        assert rep["status"] == rs.RSRR_OK, rep["error"]
+        check_same(lone_results[name], rep)
+    st = sv.stats()
+    sv.close()
+    assert st["failed"] == 1 and st["completed"] == 5 and st["used_bytes"] == 0

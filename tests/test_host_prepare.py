@@ -1,5 +1,5 @@
 """CPU parity of what rsrr_create prepares on the host (rsrr_describe, no GPU):
-the sampling points z_j (step 1, Section 4.1 trapezoid nodes or explicit
+the sampling points z_j (step 1, Section 5.1 trapezoid nodes or explicit
 points), the coefficient table f_i(z_j) for every function family of the ABI
 (Section 2.1: polynomial, z/(z - sigma), 1/(sigma - z), sqrt(z^2 - kappa^2) on
 the principal branch, exp(-tau z)) against the oracle, and the half-bandwidths
@@ -85,3 +85,70 @@ def test_dense_kind_has_points_but_no_table(rsrr):
     z, coef, (kl, ku) = rsrr.prepared(p)
     assert coef is None and (kl, ku) == (0, 0)
     assert np.abs(z - oracle.sample_points(p.region, p.N)).max() <= 1e-15 * 4
+
+
+# ------------------------------------------------ the wider boundary (no GPU)
+def taylor_quadratic(c0=0.3 + 0.2j, n=240, seed=11):
+    """diag_quadratic rewritten in powers of (z - c0): k' = k + c c0 + m c0^2,
+    c' = c + 2 m c0, m' = m with TAYLOR functions (same eigenvalues)."""
+    p = W.diag_quadratic(n=n, seed=seed)
+    k, c, m = p.meta["diags"]
+    fns = [W.Fn(W.F_TAYLOR, power=q, shift=c0) for q in range(3)]
+    return W.hidden_diagonal([k + c * c0 + m * c0 * c0, c + 2 * m * c0, m.astype(complex)], fns,
+                             p.region, p.N, p.L, layers=p.meta["layers"], seed=seed + 1, seed_u=seed + 2,
+                             name="taylor_quadratic")
+
+
+def callback_rational():
+    """diag_rational with its z/(z - sigma) term given as a host callback."""
+    p = W.diag_rational()
+    s = p.fns[2].param
+    p.fns[2] = W.Fn(W.F_CALLBACK, scale=p.fns[2].scale, callback=lambda z: z / (z - s))
+    return p
+
+
+def test_complex_values_are_held_as_real_and_imaginary_terms(rsrr):
+    p = W.diag_quadratic_complex()
+    z, coef, _ = rsrr.prepared(p)
+    zo = oracle.sample_points(p.region, p.N)
+    # held terms: f_u for Re A_u, i f_u for Im A_u, in caller order
+    want = []
+    for fn in p.fns:
+        f = oracle.eval_fn(fn, zo)
+        want += [f, 1j * f]
+    want = np.stack(want, axis=1)
+    assert coef.shape == want.shape
+    assert np.abs(coef - want).max() <= 1e-14 * np.abs(want).max()
+
+
+def test_callback_and_taylor_terms_are_evaluated_as_defined(rsrr):
+    p = callback_rational()
+    z, coef, _ = rsrr.prepared(p)
+    zo = oracle.sample_points(p.region, p.N)
+    ref = W.diag_rational()
+    for i, fn in enumerate(ref.fns):
+        assert np.abs(coef[:, i] - oracle.eval_fn(fn, zo)).max() <= 1e-14 * np.abs(coef[:, i]).max()
+    q = taylor_quadratic()
+    z, coef, _ = rsrr.prepared(q)
+    zo = oracle.sample_points(q.region, q.N)
+    for i in range(3):
+        want = (zo - (0.3 + 0.2j)) ** i
+        assert np.abs(coef[:, 2 * i] - want).max() <= 1e-14 * max(1.0, np.abs(want).max())
+
+
+def test_dense_terms_kind_prepares_points_and_coefficients(rsrr):
+    q = W.dense_hidden_quadratic(n=64)
+    z, coef, (kl, ku) = rsrr.prepared(q)
+    zo = oracle.sample_points(q.region, q.N)
+    assert np.abs(z - zo).max() <= 1e-15
+    for i, fn in enumerate(q.fns):
+        assert np.abs(coef[:, i] - oracle.eval_fn(fn, zo)).max() <= 1e-14 * max(1.0, np.abs(coef[:, i]).max())
+    assert (kl, ku) == (0, 0)
+
+
+def test_callback_returning_a_non_finite_value_is_refused(rsrr):
+    p = W.diag_rational()
+    p.fns[2] = W.Fn(W.F_CALLBACK, callback=lambda z: np.full(z.shape, np.nan))
+    with pytest.raises(rsrr.RSRRError) as e:
+        rsrr.prepared(p)
+    assert e.value.status == rsrr.RSRR_EINVAL

@@ -1,7 +1,7 @@
 """CPU tests of the library's host SS-FULL finish (csrc/ssfull_host.cpp: block
 Hankel matrices of the moments, truncated SVD by column-pivoted QR + Jacobi,
 singular-value gap, the small eigenproblem and the lifted eigenvectors;
-Section 2.3 with U = I).  The source is compiled here with g++ behind a
+Section 3.3 with U = I).  The source is compiled here with g++ behind a
 one-function C harness and fed moments with a closed form: for
 T(z) = V diag(z - mu_i) V^{-1}, the contour moments of T^{-1} are
 c * V diag(s_i^alpha [mu_i inside]) V^{-1}, s_i = (mu_i - gamma) / rho, for any
