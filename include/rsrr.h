@@ -156,10 +156,13 @@ typedef struct {
 
 /* Region.  The ellipse phi(t) = center + a cos t + i b sin t is the contour
  * of the projected solve and defines "inside".  Sampling points are the
- * N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Section 5.1) for
- * RSRR_REGION_ELLIPSE, or the N given host points for RSRR_REGION_POINTS
- * (the rational interpolation approach lets them lie anywhere, Section 3.3). */
-enum { RSRR_REGION_ELLIPSE = 0, RSRR_REGION_POINTS = 1 };
+ * N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Eq. 58, Section 5.1)
+ * for RSRR_REGION_ELLIPSE, the N given host points for RSRR_REGION_POINTS
+ * (the rational interpolation approach lets them lie anywhere, Section 3.3),
+ * or, for RSRR_REGION_INTERVAL, the N Chebyshev points of the first kind
+ * z_i = center + a cos((2i + 1) pi / 2N) (Eq. 42) on the ellipse's major axis
+ * (an interval of interest of a real NEP, Sections 3.3 and 5.1). */
+enum { RSRR_REGION_ELLIPSE = 0, RSRR_REGION_POINTS = 1, RSRR_REGION_INTERVAL = 2 };
 
 typedef struct {
     int32_t kind;
@@ -238,7 +241,28 @@ typedef struct {
                             a splitmix64 stream); rsrr_set_probe replaces U */
     int64_t mem_budget_bytes; /* > 0: rsrr_create refuses (ENOMEM) a handle whose
                             rsrr_estimate_bytes exceed it; 0 (default): no limit */
+    int32_t method;      /* RSRR_METHOD_*, default RSRR_METHOD_RSRR */
+    int32_t K;           /* moments of SSRR-M and SS-RI (1 <= K <= N), default 2 */
 } rsrr_opts;
+
+/* Method of rsrr_project / rsrr_solve on the same samples X_j:
+ *   RSRR_METHOD_RSRR    the resolvent sampling scheme (Section 4.3): basis of
+ *                       S = [X_0 ... X_{N-1}].
+ *   RSRR_METHOD_SSRR_M  the resolvent moment scheme (Section 4.1): basis of
+ *                       M = [M_0 ... M_{K-1}], M_a = sum_i w_i s_i^a X_i (Eq. 40,
+ *                       Eq. 48), then the same projection and SS-FULL.
+ *   RSRR_METHOD_SS_RI   SS-RI (Section 3.3): moments A_a = sum_i w_i s_i^a U^H X_i
+ *                       (Eq. 18), the Hankel pencil H^< - lambda H (Eq. 33) by
+ *                       truncated SVD and the gap test (Eq. 44), eigenvectors
+ *                       v = M W0 Sigma0^{-1} b (Eq. 41); rsrr_project does
+ *                       nothing for it and rsrr_solve follows rsrr_sample.
+ * s_i = (z_i - center) / max(a, b) (a fixed change of polynomial basis that
+ * keeps the pencil's eigenvalues and span(M)); the weights w_i are the
+ * trapezoid weights (1/N) phi'(alpha_i) of Eq. 58 on the ellipse, the
+ * Chebyshev weights (-1)^i sin((2i + 1) pi / 2N) of Eq. 43 on an interval,
+ * and the scaled barycentric weights of Eq. 19 for explicit points.  Both
+ * moment methods are kept for comparison (Sections 5.1, 5.2). */
+enum { RSRR_METHOD_RSRR = 0, RSRR_METHOD_SSRR_M = 1, RSRR_METHOD_SS_RI = 2 };
 
 typedef struct rsrr_handle rsrr_t;
 

@@ -13,4 +13,5 @@ from .rsrr import (sample_points, quad_weights, inside, eval_fn, assemble,
                    distances, assemble_dense, resolvent_samples_dense, taylor_terms,
                    taylor_coefficients, residual_dense, backward_error_inf_dense, rsrr_dense,
                    argument_principle_count_dense, ShiftPow, assemble_terms,
-                   resolvent_samples_terms, backward_error_inf_terms, residual_terms, rsrr_terms)
+                   resolvent_samples_terms, backward_error_inf_terms, residual_terms, rsrr_terms,
+                   interpolation_weights, moment_matrix, ss_ri, ssrr_m)

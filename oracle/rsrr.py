@@ -49,9 +49,15 @@ from workloads import (F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP, F_TAYLOR
 def sample_points(region: Region, N: int) -> np.ndarray:
     """z_j = phi(alpha_j), alpha_j = 2 pi (j + 1/2)/N on the ellipse
     phi(alpha) = gamma + a cos(alpha) + i b sin(alpha) (Section 5.1, ellipse
-    contour and trapezoid nodes), or the region's explicit points."""
+    contour and trapezoid nodes), the region's explicit points, or the
+    Chebyshev points of the first kind x_i = cos((2i + 1) pi / 2N) (Eq. 42)
+    mapped to the interval [gamma - a, gamma + a] (Section 3.3, real points
+    for an interval of interest)."""
     if region.kind == "points":
         return np.asarray(region.points, dtype=np.complex128).copy()
+    if region.kind == "interval":
+        i = np.arange(N)
+        return region.center + region.a * np.cos((2 * i + 1) * np.pi / (2 * N)) + 0j
     j = np.arange(N)
     alpha = 2.0 * np.pi * (j + 0.5) / N
     return region.center + region.a * np.cos(alpha) + 1j * region.b * np.sin(alpha)
@@ -634,3 +640,107 @@ def rsrr_terms(prob, delta: float = 1e-14, NQ: int = 500, KQ: int = 2, tol_gap: 
     order = np.lexsort((np.angle(lam), np.abs(lam)))
     return dict(lam=lam[order], V=V[:, order], res=res[order], k=k, sigma=sig, info=info,
                 z=z, X=X, P=P, Q=Q)
+
+
+# ---------------------------------------------------------------------------
+# The comparison methods of Sections 3 and 4.1: SS-RI (moments of
+# F(z) = U^H T(z)^{-1} U, Hankel pencil) and SSRR-M (Rayleigh-Ritz on the
+# moment matrix M instead of S).  Both use the sampled X_j = T(z_j)^{-1} U.
+# ---------------------------------------------------------------------------
+
+def interpolation_weights(region: Region, z: np.ndarray) -> np.ndarray:
+    """Weights omega_i of the moments (up to a common factor, which changes
+    neither the pencil's eigenvalues nor span(M), Section 3.3 item 3):
+    trapezoid nodes on the ellipse -> the quadrature weights (1/N) phi'(alpha_i)
+    of Eq. 58 (the contour-integral special case); Chebyshev points of an
+    interval -> (-1)^i sin((2i + 1) pi / 2N) (Eq. 43); explicit points -> the
+    barycentric weights 1 / prod_{j != i} (z_i - z_j) of Eq. 19, every factor
+    scaled by the reciprocal capacity (here 2 / rho of the region's scale rho)
+    and formed through logarithms against under- and overflow."""
+    N = len(z)
+    if region.kind == "ellipse":
+        return quad_weights(region, N)
+    if region.kind == "interval":
+        i = np.arange(N)
+        return (-1.0) ** i * np.sin((2 * i + 1) * np.pi / (2 * N)) + 0j
+    rho = max(region.a, region.b)
+    s = (np.asarray(z) - region.center) * (2.0 / rho)
+    logw = np.zeros(N, dtype=np.complex128)
+    for i in range(N):
+        d = s[i] - np.delete(s, i)
+        logw[i] = -np.sum(np.log(d))
+    logw -= logw.real.max()
+    return np.exp(logw)
+
+
+def moment_matrix(X: list, z: np.ndarray, w: np.ndarray, region: Region, K: int) -> np.ndarray:
+    """M = [M_0 ... M_{K-1}], M_alpha = sum_i omega_i s_i^alpha X_i (Eq. 40 and
+    Eq. 48) with the scaled powers s_i = (z_i - gamma)/rho (a fixed change of
+    basis of the polynomials of degree < K: span(M) is unchanged)."""
+    rho = max(region.a, region.b)
+    s = (np.asarray(z) - region.center) / rho
+    return np.concatenate([sum(w[i] * s[i] ** al * X[i] for i in range(len(X))) for al in range(K)],
+                          axis=1)
+
+
+def ss_ri(prob: Problem, K: int, U: np.ndarray | None = None, tol_gap: float = 1e3,
+          res_tol: float = 1e-6):
+    """SS-RI (Section 3.3, steps 1-6): F(z_i) = U^H X_i (Eq. 14), moments
+    A_alpha = sum_i omega_i s_i^alpha F(z_i) (Eq. 18, scaled powers), Hankel H
+    and H^< (Eq. 33), truncated SVD of H with the count from the largest gap
+    (Eq. 37, Eq. 44), A = V0^H H^< W0 Sigma0^{-1} (Eq. 38), its eigenpairs,
+    lambda = gamma + rho lambda' and v = M W0 Sigma0^{-1} b (Eq. 41) with
+    M = [M_0 ... M_{K-1}] (Eq. 39-40); acceptance as in rsrr()."""
+    if U is None:
+        U = prob.U
+    region = prob.region
+    z = sample_points(region, prob.N)
+    X = resolvent_samples(prob, z, U)
+    w = interpolation_weights(region, z)
+    rho = max(region.a, region.b)
+    s = (z - region.center) / rho
+    F = [U.conj().T @ Xi for Xi in X]
+    A = [sum(w[i] * s[i] ** al * F[i] for i in range(len(F))) for al in range(2 * K)]
+    H = np.block([[A[i + j] for j in range(K)] for i in range(K)])
+    Hs = np.block([[A[i + j + 1] for j in range(K)] for i in range(K)])
+    V, sv, Wh = np.linalg.svd(H)
+    ratios = sv[:-1] / np.maximum(sv[1:], np.finfo(float).tiny)
+    nbar = int(np.argmax(ratios)) + 1
+    V0, W0 = V[:, :nbar], Wh.conj().T[:, :nbar]
+    S0inv = np.diag(1.0 / sv[:nbar])
+    Am = V0.conj().T @ Hs @ W0 @ S0inv
+    lam_s, B = np.linalg.eig(Am)
+    lam = region.center + rho * lam_s
+    M = moment_matrix(X, z, w, region, K)
+    Vv = M @ (W0 @ S0inv @ B)
+    Vv = Vv / np.linalg.norm(Vv, axis=0, keepdims=True)
+    keep = inside(region, lam)
+    lam, Vv = lam[keep], Vv[:, keep]
+    res = np.array([residual(prob, l, Vv[:, c]) for c, l in enumerate(lam)])
+    ok = res <= res_tol
+    lam, Vv, res = lam[ok], Vv[:, ok], res[ok]
+    order = np.lexsort((np.angle(lam), np.abs(lam)))
+    return dict(lam=lam[order], V=Vv[:, order], res=res[order], nbar=nbar, sv=sv)
+
+
+def ssrr_m(prob: Problem, K: int, delta: float = 1e-14, NQ: int = 500, KQ: int = 2,
+           tol_gap: float = 1e3, U: np.ndarray | None = None, res_tol: float = 1e-6):
+    """SSRR-M (Section 4.1 and the last paragraphs of Section 4.3): RSRR with
+    the moment matrix M (Eq. 48) in place of the sampling matrix S: truncated
+    SVD basis of M (normalised columns), projection, SS-FULL, v = Q g."""
+    z = sample_points(prob.region, prob.N)
+    X = resolvent_samples(prob, z, U)
+    w = interpolation_weights(prob.region, z)
+    M = normalize_columns(moment_matrix(X, z, w, prob.region, K))
+    Q, sig, k = truncated_basis(M, delta)
+    P = project(prob, Q)
+    lam, G, info = ss_full(P, prob.fns, prob.region, NQ, KQ, tol_gap)
+    V = Q @ G
+    V = V / np.linalg.norm(V, axis=0, keepdims=True)
+    keep = inside(prob.region, lam)
+    lam, V = lam[keep], V[:, keep]
+    res = np.array([residual(prob, l, V[:, c]) for c, l in enumerate(lam)])
+    ok = res <= res_tol
+    lam, V, res = lam[ok], V[:, ok], res[ok]
+    order = np.lexsort((np.angle(lam), np.abs(lam)))
+    return dict(lam=lam[order], V=V[:, order], res=res[order], k=k, sigma=sig, info=info)

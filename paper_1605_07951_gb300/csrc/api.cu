@@ -91,6 +91,41 @@ rsrr_status Handle::eval_terms(const cplx *zz, int64_t count, std::vector<cplx> 
     return RSRR_OK;
 }
 
+// weights w_i of the moment methods (up to a common factor): trapezoid
+// weights (1/N) phi'(alpha_i) on the ellipse (Eq. 58), Chebyshev weights
+// (-1)^i sin((2i + 1) pi / 2N) on an interval (Eq. 43), otherwise the
+// barycentric weights 1 / prod_{j != i} (z_i - z_j) (Eq. 19) with every factor
+// scaled by 2 / rho and formed through logarithms
+void Handle::moment_weights(std::vector<cplx> &w) const {
+    const int n_ = (int)z.size();
+    w.assign(n_, cplx(0.0, 0.0));
+    const double rho = std::max(region.a, region.b);
+    const cplx gamma(region.center.re, region.center.im);
+    if (region.kind == RSRR_REGION_ELLIPSE && !points_added) {
+        for (int j = 0; j < n_; ++j) {
+            const double al = 2.0 * M_PI * (j + 0.5) / n_;
+            w[j] = cplx(-region.a * std::sin(al), region.b * std::cos(al)) / (double)n_;
+        }
+        return;
+    }
+    if (region.kind == RSRR_REGION_INTERVAL && !points_added) {
+        for (int j = 0; j < n_; ++j)
+            w[j] = cplx(((j & 1) ? -1.0 : 1.0) * std::sin((2.0 * j + 1.0) * M_PI / (2.0 * n_)), 0.0);
+        return;
+    }
+    std::vector<cplx> lw(n_);
+    double top = -1e300;
+    for (int i = 0; i < n_; ++i) {
+        cplx acc = 0.0;
+        for (int j = 0; j < n_; ++j)
+            if (j != i) acc -= std::log((z[i] - z[j]) * (2.0 / rho));
+        lw[i] = acc;
+        top = std::max(top, acc.real());
+    }
+    for (int i = 0; i < n_; ++i) w[i] = std::exp(lw[i] - top);
+    (void)gamma;
+}
+
 double Handle::residual_scale(const cplx *f_held) const {
     double scale = 0.0;
     for (size_t t = 0; t < fn.size(); ++t)
@@ -202,6 +237,8 @@ void rsrr_opts_default(rsrr_opts *o) {
     o->KQ = 2;
     o->host_threads = 0;
     o->gemm = RSRR_GEMM_AUTO;
+    o->method = RSRR_METHOD_RSRR;
+    o->K = 2;
 }
 
 static rsrr_status create_fail(const char *msg) {
@@ -288,10 +325,11 @@ static rsrr_status check_fns(const rsrr_nep *nep) {
     return RSRR_OK;
 }
 
-static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts) {
+static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts, int N) {
     if (!(region->a > 0.0) || !(region->b > 0.0))
         return create_fail("rsrr_create: ellipse semi-axes must be > 0");
-    if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS)
+    if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS &&
+        region->kind != RSRR_REGION_INTERVAL)
         return create_fail("rsrr_create: unknown region kind");
     if (region->kind == RSRR_REGION_POINTS && !region->points)
         return create_fail("rsrr_create: points region without points");
@@ -301,16 +339,24 @@ static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts
     if (opts && (opts->gemm < RSRR_GEMM_AUTO || opts->gemm > RSRR_GEMM_OZAKI_MMA))
         return create_fail("rsrr_create: unknown gemm method");
     if (opts && opts->mem_budget_bytes < 0) return create_fail("rsrr_create: negative mem_budget_bytes");
+    if (opts && (opts->method < RSRR_METHOD_RSRR || opts->method > RSRR_METHOD_SS_RI))
+        return create_fail("rsrr_create: unknown method");
+    if (opts && opts->method != RSRR_METHOD_RSRR && (opts->K < 1 || opts->K > N))
+        return create_fail("rsrr_create: the moment methods need 1 <= K <= N");
     return RSRR_OK;
 }
 
 // step 1: the sampling points, trapezoid nodes on the ellipse (Eq. 58,
-// Section 5.1) or the explicit points (any points, Section 3.3)
+// Section 5.1), the explicit points (any points, Section 3.3) or the
+// Chebyshev points of the first kind on the major axis (Eq. 42)
 static void fill_points(Handle *h, const rsrr_region *region, int N) {
     h->z.resize(N);
     for (int j = 0; j < N; ++j) {
         if (region->kind == RSRR_REGION_POINTS) {
             h->z[j] = cplx(region->points[j].re, region->points[j].im);
+        } else if (region->kind == RSRR_REGION_INTERVAL) {
+            h->z[j] = cplx(region->center.re + region->a * std::cos((2.0 * j + 1.0) * M_PI / (2.0 * N)),
+                           region->center.im);
         } else {
             const double al = 2.0 * M_PI * (j + 0.5) / N;
             h->z[j] = cplx(region->center.re + region->a * std::cos(al),
@@ -362,7 +408,7 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
     if (N < 1 || L < 1) return create_fail("rsrr_create: N and L must be >= 1");
     if (nep->kind != RSRR_NEP_SPARSE && nep->kind != RSRR_NEP_HELMHOLTZ && nep->kind != RSRR_NEP_DENSE)
         return create_fail("rsrr_create: unknown NEP kind");
-    rsrr_status cst = check_common(region, opts);
+    rsrr_status cst = check_common(region, opts, N);
     if (cst != RSRR_OK) return cst;
     if (nep->kind == RSRR_NEP_HELMHOLTZ) return rsrr::prepare_dense(nep, region, N, L, opts, out);
     if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
@@ -936,6 +982,7 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
     }
     CK(wait(), "upload sync");
     z.insert(z.end(), znew, znew + count);
+    points_added = true;
     N = N1;
     dp.N = N1;
     dp.coef = d_coef;

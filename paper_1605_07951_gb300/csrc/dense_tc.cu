@@ -120,6 +120,7 @@ dense_tc_update_kernel(float2 *__restrict__ A_all, int n, int k0, int jb, unsign
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     // A' = [Ar | Ai]: row r, depth t (real part) and 32 + t (imaginary part)
+#pragma unroll 4
     for (int e = tid; e < BM * 32; e += THREADS) {
         const int t = e / BM, r = e % BM;
         float2 v = make_float2(0.f, 0.f);
@@ -134,6 +135,7 @@ dense_tc_update_kernel(float2 *__restrict__ A_all, int n, int k0, int jb, unsign
     }
     // B' rows j (real output columns) and BN + j (imaginary): depth t carries
     // (Br, Bi), depth 32 + t carries (-Bi, Br)
+#pragma unroll 4
     for (int e = tid; e < BN * 32; e += THREADS) {
         const int t = e % 32, j = e / 32;
         float2 v = make_float2(0.f, 0.f);
@@ -171,15 +173,26 @@ dense_tc_update_kernel(float2 *__restrict__ A_all, int n, int k0, int jb, unsign
         commit(mb);
     }
     __syncwarp();
-    const bool ok = wait_parity(mb, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its 32 rows) for the
     // complex columns 64 (w / 4) .. +63: real parts in TMEM columns j, imaginary
-    // parts in columns BN + j
+    // parts in columns BN + j.  A22 is read 16 columns at a time into registers
+    // (all 16 loads in flight together; the first group is issued before the
+    // MMAs are waited for), then the product is subtracted and stored.
     const int rl = 32 * (warp & 3) + lane;
     const int cbase = 64 * (warp >> 2);
     const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const int row = r0 + rl;
+    float2 cv[16];
+    auto load_group = [&](int q) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int c = c0 + cbase + q + j;
+            cv[j] = (row < n && c < n) ? A[(size_t)c * n + row] : make_float2(0.f, 0.f);
+        }
+    };
+    load_group(0);
+    const bool ok = wait_parity(mb, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
     for (int q = 0; q < 64; q += 16) {
         float re[16], im[16];
@@ -189,15 +202,10 @@ dense_tc_update_kernel(float2 *__restrict__ A_all, int n, int k0, int jb, unsign
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int c = c0 + cbase + q + j;
-                if (c < n) {
-                    float2 *p = A + (size_t)c * n + row;
-                    float2 v = *p;
-                    v.x -= re[j];
-                    v.y -= im[j];
-                    *p = v;
-                }
+                if (c < n) A[(size_t)c * n + row] = make_float2(cv[j].x - re[j], cv[j].y - im[j]);
             }
         }
+        if (q + 16 < 64) load_group(q + 16);
     }
     if (!ok && lane == 0) atomicAdd(status, 1u);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

@@ -817,8 +817,12 @@ size_t projection_ws_bytes(int NL, int64_t n, int terms) { return ws_bytes(NL, n
 // Each level sees only directions far above its own rounding level, so the
 // levels together resolve singular values down to ~lev_tol^L of sigma_1.
 rsrr_status Handle::project(cudaStream_t s) {
+    using cplx = std::complex<double>;
     const int NL = N * L;
     const int64_t nn = n;
+    if (opts.method == RSRR_METHOD_SS_RI) return RSRR_OK;  // SS-RI works on the samples directly
+    // columns of the matrix whose basis is taken: S (N L) or the moments M (K L)
+    const int nc = opts.method == RSRR_METHOD_SSRR_M ? opts.K * L : NL;
     if (!proj_ws) {
         const size_t bytes = ws_bytes(NL, nn, m);
         void *p = nullptr;
@@ -850,9 +854,36 @@ rsrr_status Handle::project(cudaStream_t s) {
     rsrr_status mst = mark(6, s);
     if (mst != RSRR_OK) return mst;
 
-    // (A8) unit-norm columns: R_0 = X D^{-1}
-    colnorm_kernel<<<NL, 256, 0, s>>>(ws.norms, d_X, nn);
-    scale_cols_kernel<<<grid1d(nn * NL), 256, 0, s>>>(ws.Q1, d_X, ws.norms, nn, NL);
+    const double2 *src = d_X;
+    if (opts.method == RSRR_METHOD_SSRR_M) {
+        // M = [M_0 ... M_{K-1}], M_a = sum_i w_i s_i^a X_i (Eq. 40, Eq. 48): for
+        // every probe column l, M(:, a L + l) = sum_i X(:, i L + l) C(i, a), one
+        // product of the strided columns of S by C (N x K) in ws.W
+        std::vector<cplx> w;
+        moment_weights(w);
+        const double rho = std::max(region.a, region.b);
+        const cplx gamma(region.center.re, region.center.im);
+        const int K = opts.K;
+        std::vector<double2> Cm((size_t)N * K);
+        for (int i = 0; i < N; ++i) {
+            const cplx si = (z[i] - gamma) / rho;
+            cplx pw = 1.0;
+            for (int a = 0; a < K; ++a) {
+                const cplx c = w[i] * pw;
+                Cm[(size_t)a * N + i] = make_double2(c.real(), c.imag());
+                pw *= si;
+            }
+        }
+        PK(cudaMemcpyAsync(ws.W, Cm.data(), sizeof(double2) * Cm.size(), cudaMemcpyHostToDevice, s), "moment coefs");
+        for (int l = 0; l < L; ++l)
+            PK(gm.run((int)nn, K, N, false, d_X + (size_t)l * nn, (int64_t)L * nn, ws.W, N, ws.Ytmp + (size_t)l * nn,
+                      (int64_t)L * nn, s), "M = S Z");
+        PK(cudaStreamSynchronize(s), "moment coefs");  // the host copy of the coefficients stays valid until here
+        src = ws.Ytmp;
+    }
+    // (A8) unit-norm columns: R_0 = X D^{-1} (or M D^{-1})
+    colnorm_kernel<<<nc, 256, 0, s>>>(ws.norms, src, nn);
+    scale_cols_kernel<<<grid1d(nn * nc), 256, 0, s>>>(ws.Q1, src, ws.norms, nn, nc);
     PK(cudaGetLastError(), "normalise");
     launches += 2;
     double2 *R = ws.Q1;
@@ -862,19 +893,19 @@ rsrr_status Handle::project(cudaStream_t s) {
     double s1sq = 0.0;     // sigma_1^2 of Sn (from level 0)
     double smallest = 0.0; // smallest kept eigenvalue (for sigma_k)
     kc = 0;
-    for (int lev = 0; lev < 6 && kt < NL; ++lev) {
+    for (int lev = 0; lev < 6 && kt < nc; ++lev) {
         // (A9) Gram of the remainder and its largest diagonal
         double maxd = 1.0;
-        PK(gm.run(NL, NL, (int)nn, true, R, nn, R, nn, ws.G, NL, s, true), "Gram");
-        max_diag_kernel<<<1, 256, 0, s>>>(ws.acc, ws.G, NL);
+        PK(gm.run(nc, nc, (int)nn, true, R, nn, R, nn, ws.G, nc, s, true), "Gram");
+        max_diag_kernel<<<1, 256, 0, s>>>(ws.acc, ws.G, nc);
         PK(cudaMemcpyAsync(&maxd, ws.acc, sizeof(double), cudaMemcpyDeviceToHost, s), "maxdiag");
         PK(cudaStreamSynchronize(s), "maxdiag sync");
         launches += 1;
         const double tau = std::max(lev_tol * lev_tol * maxd, floor_ * floor_ * s1sq);
         PK(cudaMemsetAsync(ws.state, 0, sizeof(int32_t) * 4, s), "memset");
         PK(cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int) * 4, s), "memset");
-        diag_real_kernel<<<(NL + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, NL);
-        PK(launch_coop(pchol_persistent_kernel, (NL + 255) / 256, s, (const double2 *)ws.G, NL,
+        diag_real_kernel<<<(nc + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, nc);
+        PK(launch_coop(pchol_persistent_kernel, (nc + 255) / 256, s, (const double2 *)ws.G, nc,
                        ws.Lm, ws.dbuf, tau, ws.state, ws.bar), "pivoted Cholesky");
         launches += 2;
         int32_t st2[2];
@@ -883,11 +914,11 @@ rsrr_status Handle::project(cudaStream_t s) {
         PK(cudaMemcpyAsync(&bar_err, ws.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s), "kc");
         PK(cudaStreamSynchronize(s), "kc sync");
         if (bar_err) return fail(RSRR_ETIMEOUT, "rsrr_project: grid barrier timeout (pivoted Cholesky)");
-        const int kcl = st2[0] ? st2[1] : NL;
+        const int kcl = st2[0] ? st2[1] : nc;
         if (kcl < 1) break;
         kc += kcl;
         // small Hermitian eigenproblem B^H B
-        PK(gm.run(kcl, kcl, NL, true, ws.Lm, NL, ws.Lm, NL, ws.H, kcl, s, true), "B^H B");
+        PK(gm.run(kcl, kcl, nc, true, ws.Lm, nc, ws.Lm, nc, ws.H, kcl, s, true), "B^H B");
         PK(jacobi_eig(ws, kcl, s, &launches), "Jacobi (B^H B)");
         std::vector<double> ev(kcl);
         PK(cudaMemcpyAsync(ev.data(), ws.evals, sizeof(double) * kcl, cudaMemcpyDeviceToHost, s), "evals");
@@ -901,13 +932,13 @@ rsrr_status Handle::project(cudaStream_t s) {
             if (ev[j] > keep_tol) kb = j + 1;
         if (kb < 1) break;
         smallest = ev[kb - 1];
-        if (kt + kb > NL) kb = NL - kt;
+        if (kt + kb > nc) kb = nc - kt;
         // new directions Qb = R B Y_kb Lambda_kb^{-1} (n x kb) into Ytmp
-        PK(gm.run(NL, kb, kcl, false, ws.Lm, NL, ws.Ysort, kcl, ws.W, NL, s), "B Y");
-        scale_rc_kernel<<<grid1d((int64_t)NL * kb), 256, 0, s>>>(ws.W, NL, NL, kb, nullptr,
+        PK(gm.run(nc, kb, kcl, false, ws.Lm, nc, ws.Ysort, kcl, ws.W, nc, s), "B Y");
+        scale_rc_kernel<<<grid1d((int64_t)nc * kb), 256, 0, s>>>(ws.W, nc, nc, kb, nullptr,
                                                                  ws.evals, false, false);
         launches += 1;
-        PK(gm.run((int)nn, kb, NL, false, R, nn, ws.W, NL, ws.Ytmp, nn, s), "R W");
+        PK(gm.run((int)nn, kb, nc, false, R, nn, ws.W, nc, ws.Ytmp, nn, s), "R W");
         // orthogonalise against the basis so far, twice
         for (int pass = 0; pass < 2 && kt > 0; ++pass) {
             PK(gm.run(kt, kb, (int)nn, true, ws.Qall, nn, ws.Ytmp, nn, ws.C, kt, s), "Q^H Qb");
@@ -938,18 +969,18 @@ rsrr_status Handle::project(cudaStream_t s) {
         // Before pass 1's update, the column norms the deflation would leave,
         // diag(G) - |Qnew^H R|^2, tell whether another level is needed; if
         // not, R is not needed any more and the updates are skipped.
-        PK(gm.run(kb2, NL, (int)nn, true, Qnew, nn, R, nn, ws.C, kb2, s), "Qnew^H R");
-        remainder_norm_kernel<<<(NL + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, ws.C, kb2, NL);
-        max_vec_kernel<<<1, 256, 0, s>>>(ws.acc, ws.dbuf, NL);
+        PK(gm.run(kb2, nc, (int)nn, true, Qnew, nn, R, nn, ws.C, kb2, s), "Qnew^H R");
+        remainder_norm_kernel<<<(nc + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, ws.C, kb2, nc);
+        max_vec_kernel<<<1, 256, 0, s>>>(ws.acc, ws.dbuf, nc);
         launches += 2;
         double rem = 0.0;
         PK(cudaMemcpyAsync(&rem, ws.acc, sizeof(double), cudaMemcpyDeviceToHost, s), "remainder");
         PK(cudaStreamSynchronize(s), "remainder sync");
-        if (!(rem > floor_ * floor_ * s1sq) || kt >= NL) break;
-        PK(gm.run((int)nn, NL, kb2, false, Qnew, nn, ws.C, kb2, R, nn, s, false, -1.0, 1.0),
+        if (!(rem > floor_ * floor_ * s1sq) || kt >= nc) break;
+        PK(gm.run((int)nn, nc, kb2, false, Qnew, nn, ws.C, kb2, R, nn, s, false, -1.0, 1.0),
            "R -= Qnew C");
-        PK(gm.run(kt, NL, (int)nn, true, ws.Qall, nn, R, nn, ws.C, kt, s), "Q^H R");
-        PK(gm.run((int)nn, NL, kt, false, ws.Qall, nn, ws.C, kt, R, nn, s, false, -1.0, 1.0),
+        PK(gm.run(kt, nc, (int)nn, true, ws.Qall, nn, R, nn, ws.C, kt, s), "Q^H R");
+        PK(gm.run((int)nn, nc, kt, false, ws.Qall, nn, ws.C, kt, R, nn, s, false, -1.0, 1.0),
            "R -= Q C");
         (void)kprev;
     }
@@ -1008,7 +1039,7 @@ rsrr_status rsrr_project(rsrr_t *hh, void *stream) {
 rsrr_status rsrr_get_Q(rsrr_t *hh, rsrr_c128 *dst, int32_t dst_on_device, void *stream) {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h || !dst) return RSRR_EINVAL;
-    if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_get_Q: no rsrr_project yet");
+    if (!h->projected || !h->d_Q) return h->fail(RSRR_ESTATE, "rsrr_get_Q: no basis (rsrr_project, RSRR or SSRR-M)");
     const size_t bytes = sizeof(double2) * (size_t)h->n * h->k;
     cudaError_t e;
     if (dst_on_device) {
@@ -1024,7 +1055,7 @@ rsrr_status rsrr_get_Q(rsrr_t *hh, rsrr_c128 *dst, int32_t dst_on_device, void *
 rsrr_status rsrr_get_projected(rsrr_t *hh, rsrr_c128 *dst, int32_t dst_on_device, void *stream) {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h || !dst) return RSRR_EINVAL;
-    if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_get_projected: no rsrr_project yet");
+    if (!h->projected || !h->d_P) return h->fail(RSRR_ESTATE, "rsrr_get_projected: no rsrr_project yet");
     const size_t bytes = sizeof(double2) * (size_t)h->m * h->k * h->k;
     cudaError_t e;
     if (dst_on_device) {
@@ -1080,6 +1111,76 @@ __global__ void eig_residual_kernel(const double2 *__restrict__ V, const double2
     }
 }
 
+// SS-RI (Section 3.3) on the resident samples: F(z_i) = U^H X_i (Eq. 14) by
+// one product on the GPU, the moments A_a = sum_i w_i s_i^a F(z_i), a < 2K
+// (Eq. 18, scaled powers s_i = (z_i - gamma)/rho) on the host, the Hankel
+// pencil, truncated SVD and gap test, eigenpairs of A (Eq. 33-38) by the
+// SS-FULL finish, and the eigenvector coefficients in the sample space:
+// v = M W0 Sigma0^{-1} b = S ZWB with ZWB((i, l), c) = sum_a w_i s_i^a
+// (W0 Sigma0^{-1} B)((a, l), c) (Eq. 39-41).
+rsrr_status Handle::ss_ri(cudaStream_t s, std::vector<std::complex<double>> &lam,
+                          std::vector<std::complex<double>> &ZWB, int &nbar, double &gmax) {
+    using cplx = std::complex<double>;
+    const int NL = N * L, K = opts.K;
+    if (!proj_ws) {
+        const size_t bytes = ws_bytes(NL, n, m);
+        void *p = nullptr;
+        cudaError_t e = raw_alloc(&p, bytes);
+        if (e != cudaSuccess) return fail(RSRR_ENOMEM, "SS-RI work space", e);
+        proj_ws = p;
+        proj_ws_bytes = bytes;
+    }
+    ProjWs ws;
+    carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, n, m);
+    Gemm gm;
+    gm.ws = ws.gws;
+    gm.ws_elems = ws.gws_elems;
+    gm.counter = &launches;
+    gm.method = opts.gemm;
+    gm.ows = ws.ows;
+    gm.ows_bytes = ws.ows_bytes;
+    gm.tmo = d_tmo;
+    PK(gm.run(L, NL, (int)n, true, d_U, n, d_X, n, ws.W, L, s), "U^H S");
+    std::vector<double2> Y((size_t)L * NL);
+    PK(cudaMemcpyAsync(Y.data(), ws.W, sizeof(double2) * Y.size(), cudaMemcpyDeviceToHost, s), "U^H S");
+    PK(cudaStreamSynchronize(s), "U^H S");
+    std::vector<cplx> w;
+    moment_weights(w);
+    const double rho = std::max(region.a, region.b);
+    const cplx gamma(region.center.re, region.center.im);
+    std::vector<std::vector<cplx>> Am(2 * K, std::vector<cplx>((size_t)L * L, 0.0));
+    std::vector<cplx> sp((size_t)N * 2 * K);  // w_i s_i^a
+    for (int i = 0; i < N; ++i) {
+        const cplx si = (z[i] - gamma) / rho;
+        cplx pw = 1.0;
+        for (int a = 0; a < 2 * K; ++a) {
+            sp[(size_t)i * 2 * K + a] = w[i] * pw;
+            pw *= si;
+        }
+    }
+    for (int a = 0; a < 2 * K; ++a)
+        for (int i = 0; i < N; ++i) {
+            const cplx c = sp[(size_t)i * 2 * K + a];
+            for (int cc = 0; cc < L; ++cc)
+                for (int r = 0; r < L; ++r) {
+                    const double2 y = Y[((size_t)i * L + cc) * L + r];
+                    Am[a][(size_t)cc * L + r] += c * cplx(y.x, y.y);
+                }
+        }
+    std::vector<cplx> Gdummy, WB;
+    if (ss_full_finish(Am, L, K, gamma, rho, opts.host_threads, lam, Gdummy, nbar, gmax, &WB) != 0)
+        return fail(RSRR_ESINGULAR, "rsrr_solve: the SS-RI moments vanish");
+    ZWB.assign((size_t)NL * nbar, 0.0);
+    for (int c = 0; c < nbar; ++c)
+        for (int i = 0; i < N; ++i)
+            for (int l = 0; l < L; ++l) {
+                cplx acc = 0.0;
+                for (int a = 0; a < K; ++a) acc += sp[(size_t)i * 2 * K + a] * WB[(size_t)c * K * L + a * L + l];
+                ZWB[(size_t)c * NL + (size_t)i * L + l] = acc;
+            }
+    return RSRR_OK;
+}
+
 rsrr_status Handle::solve(rsrr_result *out) {
     using cplx = std::complex<double>;
     cudaStream_t s = hs;
@@ -1098,24 +1199,35 @@ rsrr_status Handle::solve(rsrr_result *out) {
     int nbar = 0;
     double gmax = 0.0;
     const cplx gamma(region.center.re, region.center.im);
-    // moments of T_Q^{-1} on the GPU, the rest of SS-FULL on the host; f of
-    // every held term at the N_Q trapezoid nodes (Eq. 58)
-    std::vector<cplx> zq(opts.NQ), fq;
-    for (int q = 0; q < opts.NQ; ++q) {
-        const double t = 2.0 * M_PI * (q + 0.5) / opts.NQ;
-        zq[q] = gamma + cplx(region.a * std::cos(t), region.b * std::sin(t));
-    }
-    rsrr_status est = eval_terms(zq.data(), opts.NQ, fq);
-    if (est != RSRR_OK) return est;
-    std::vector<std::vector<cplx>> Am;
-    const rsrr_status mst = ssfull_moments(fq, opts.NQ, opts.KQ, Am);
-    if (mst != RSRR_OK) return mst;
-    if (ss_full_finish(Am, k, opts.KQ, gamma, std::max(region.a, region.b), opts.host_threads, lam, G,
-                       nbar, gmax) != 0)
-        return fail(RSRR_ESINGULAR, "rsrr_solve: the SS-FULL moments vanish");
-    // v = Q g on the GPU
-    ProjWs ws;
     const int NL = N * L;
+    // the eigenvectors are v = B g: B = Q (k columns) for the projected
+    // methods, B = S (N L columns) for SS-RI
+    const double2 *Bsrc = d_Q;
+    int kb = k;
+    if (opts.method == RSRR_METHOD_SS_RI) {
+        const rsrr_status rst = ss_ri(s, lam, G, nbar, gmax);
+        if (rst != RSRR_OK) return rst;
+        Bsrc = d_X;
+        kb = NL;
+    } else {
+        // moments of T_Q^{-1} on the GPU, the rest of SS-FULL on the host; f of
+        // every held term at the N_Q trapezoid nodes (Eq. 58)
+        std::vector<cplx> zq(opts.NQ), fq;
+        for (int q = 0; q < opts.NQ; ++q) {
+            const double t = 2.0 * M_PI * (q + 0.5) / opts.NQ;
+            zq[q] = gamma + cplx(region.a * std::cos(t), region.b * std::sin(t));
+        }
+        rsrr_status est = eval_terms(zq.data(), opts.NQ, fq);
+        if (est != RSRR_OK) return est;
+        std::vector<std::vector<cplx>> Am;
+        const rsrr_status mst = ssfull_moments(fq, opts.NQ, opts.KQ, Am);
+        if (mst != RSRR_OK) return mst;
+        if (ss_full_finish(Am, k, opts.KQ, gamma, std::max(region.a, region.b), opts.host_threads, lam, G,
+                           nbar, gmax) != 0)
+            return fail(RSRR_ESINGULAR, "rsrr_solve: the SS-FULL moments vanish");
+    }
+    // v = B g on the GPU
+    ProjWs ws;
     carve_ws(reinterpret_cast<char *>(proj_ws), ws, NL, n, m);
     Gemm gm;
     gm.ws = ws.gws;
@@ -1123,7 +1235,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
     gm.counter = &launches;
     // G (k x nbar), V = Q G (n x nbar), f_i(lam_c) and the residual sums in a
     // buffer of their own (nbar may exceed the sample count)
-    const size_t gbytes = sizeof(double2) * (size_t)k * nbar;
+    const size_t gbytes = sizeof(double2) * (size_t)kb * nbar;
     const size_t vbytes = sizeof(double2) * (size_t)n * nbar;
     const size_t cbytes = sizeof(double2) * (size_t)nbar * std::max(m, 2);
     void *buf = nullptr;
@@ -1142,7 +1254,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
     double *d_rr = reinterpret_cast<double *>(reinterpret_cast<char *>(buf) + gbytes + vbytes + cbytes);
     double *d_vv = d_rr + nbar;
     PK(cudaMemcpyAsync(d_G, G.data(), gbytes, H2D, s), "G");
-    PK(gm.run((int)n, nbar, k, false, d_Q, n, d_G, k, d_V, n, s), "Q G");
+    PK(gm.run((int)n, nbar, kb, false, Bsrc, n, d_G, kb, d_V, n, s), "B G");
     std::vector<double> t1(nbar, 0.0);
     // f of every held term at the eigenvalues (residual scale, sparse and dense-terms kinds)
     std::vector<cplx> flam;
@@ -1234,7 +1346,8 @@ rsrr_status Handle::solve(rsrr_result *out) {
 extern "C" rsrr_status rsrr_solve(rsrr_t *hh, rsrr_result *out) {
     rsrr::Handle *h = reinterpret_cast<rsrr::Handle *>(hh);
     if (!h || !out) return RSRR_EINVAL;
-    if (!h->projected) return h->fail(RSRR_ESTATE, "rsrr_solve: no rsrr_project yet");
+    if (h->opts.method == RSRR_METHOD_SS_RI ? !h->sampled : !h->projected)
+        return h->fail(RSRR_ESTATE, "rsrr_solve: no rsrr_project (rsrr_sample for SS-RI) yet");
     const rsrr_status st = h->solve(out);
     h->solved = st >= 0;
     return st;

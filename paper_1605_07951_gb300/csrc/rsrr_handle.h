@@ -37,6 +37,7 @@ struct Handle {
     rsrr_fn_callback cb = nullptr;    // RSRR_F_CALLBACK terms
     void *cb_user = nullptr;
     uint64_t seed = 0;                // default probe
+    bool points_added = false;        // rsrr_add_points ran: the points are explicit
     rsrr_region region = {};
     rsrr_opts opts = {};
     BandGeom geom = {};
@@ -148,6 +149,12 @@ struct Handle {
                            std::vector<std::complex<double>> &out);
     // sum over the caller's terms of |f_u(lam)| ||A_u||_1, from held-term values
     double residual_scale(const std::complex<double> *f_held) const;
+    // weights of the moment methods at the sampling points
+    void moment_weights(std::vector<std::complex<double>> &w) const;
+    // SS-RI on the samples (rsrr_solve with RSRR_METHOD_SS_RI): eigenvalues
+    // and the sample-space coefficients ZWB (N L x nbar) of v = S ZWB
+    rsrr_status ss_ri(cudaStream_t s, std::vector<std::complex<double>> &lam,
+                      std::vector<std::complex<double>> &ZWB, int &nbar, double &gmax);
     rsrr_status ssfull_moments(const std::vector<std::complex<double>> &fq, int NQ, int KQ,
                                std::vector<std::vector<std::complex<double>>> &Am);
 };

@@ -348,7 +348,8 @@ void eig_general(const Mat &A0, std::vector<cplx> &lam, Mat &V) {
 }  // namespace
 
 int ss_full_finish(const std::vector<std::vector<cplx>> &Amom, int k, int KQ, cplx gamma, double rho,
-                   int threads, std::vector<cplx> &lam, std::vector<cplx> &G, int &nbar, double &gmax) {
+                   int threads, std::vector<cplx> &lam, std::vector<cplx> &G, int &nbar, double &gmax,
+                   std::vector<cplx> *WBout) {
     if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
     std::vector<Mat> Am(2 * KQ, Mat(k, k));
     for (int al2 = 0; al2 < 2 * KQ; ++al2) Am[al2].a = Amom[al2];
@@ -404,6 +405,11 @@ int ss_full_finish(const std::vector<std::vector<cplx>> &Amom, int k, int KQ, cp
             const cplx bl = B(l, j) / sv[l];
             for (int i = 0; i < dim; ++i) WB(i, j) += Ws(i, l) * bl;
         }
+    if (WBout) {
+        WBout->assign((size_t)dim * nbar, 0.0);
+        for (int j = 0; j < nbar; ++j)
+            for (int i = 0; i < dim; ++i) (*WBout)[(size_t)j * dim + i] = WB(i, j);
+    }
     G.assign((size_t)k * nbar, 0.0);
     for (int j = 0; j < nbar; ++j)
         for (int bi = 0; bi < KQ; ++bi)

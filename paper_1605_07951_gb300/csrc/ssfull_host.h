@@ -11,9 +11,11 @@ namespace rsrr {
 // eigenvalues of the projected NEP), G (k x nbar, column major; projected
 // eigenvectors), nbar and the gap gmax.  Returns 0, or -1 if the moments
 // vanish.
+// With WB set, it also receives W0 Sigma0^{-1} B (KQ k x nbar, column major),
+// the coefficients of the eigenvectors in the block moments (SS-RI, Eq. 41).
 int ss_full_finish(const std::vector<std::vector<std::complex<double>>> &Amom, int k, int KQ,
                    std::complex<double> gamma, double rho, int threads,
                    std::vector<std::complex<double>> &lam, std::vector<std::complex<double>> &G,
-                   int &nbar, double &gmax);
+                   int &nbar, double &gmax, std::vector<std::complex<double>> *WB = nullptr);
 
 }  // namespace rsrr

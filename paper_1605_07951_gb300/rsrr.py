@@ -27,7 +27,8 @@ RSRR_OK, RSRR_EINVAL, RSRR_ENOMEM, RSRR_ESINGULAR = 0, -1, -2, -3
 RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7, 1
 (RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP, RSRR_F_TAYLOR,
  RSRR_F_CALLBACK) = range(8)
-RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS = 0, 1
+RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS, RSRR_REGION_INTERVAL = 0, 1, 2
+RSRR_METHOD_RSRR, RSRR_METHOD_SSRR_M, RSRR_METHOD_SS_RI = 0, 1, 2
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI, RSRR_GEMM_OZAKI_MMA = 0, 1, 2, 3
 RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU, RSRR_FLAG_INJECT_TIMEOUT, RSRR_FLAG_SIMT_DENSE_UPDATE = 1, 2, 4, 8
@@ -72,7 +73,8 @@ class rsrr_opts(C.Structure):
                 ("delta", C.c_double), ("delta_floor", C.c_double), ("tol_gap", C.c_double),
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
                 ("host_threads", C.c_int32), ("timing", C.c_int32), ("gemm", C.c_int32),
-                ("flags", C.c_int32), ("seed", C.c_uint64), ("mem_budget_bytes", C.c_int64)]
+                ("flags", C.c_int32), ("seed", C.c_uint64), ("mem_budget_bytes", C.c_int64),
+                ("method", C.c_int32), ("K", C.c_int32)]
 
 
 class rsrr_stats(C.Structure):
@@ -265,6 +267,8 @@ def describe(prob):
         pz = np.ascontiguousarray(np.asarray(r.points, dtype=np.complex128))
         keep.append(pz)
         reg.points = pz.ctypes.data_as(C.POINTER(rsrr_c128))
+    elif getattr(r, "kind", "ellipse") == "interval":
+        reg.kind = RSRR_REGION_INTERVAL
     else:
         reg.kind = RSRR_REGION_ELLIPSE
     return nep, reg, keep

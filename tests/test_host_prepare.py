@@ -34,7 +34,14 @@ FAMILIES = {
     "grid_g30": lambda: W.rational_grid(g=30, N=64, L=8),
     "random_banded": lambda: W.random_banded(kl=5, ku=9),
     "loaded_string_points": lambda: W.loaded_string(),
+    "loaded_string_interval": lambda: _interval_string(),
 }
+
+
+def _interval_string():
+    s = W.loaded_string(N=37)
+    s.region = W.Region(5001.5, 4998.5, 0.1 * 4998.5, kind="interval")
+    return s
 
 
 def bandwidths(p):

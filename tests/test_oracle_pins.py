@@ -610,3 +610,99 @@ def test_planted_inertia_mistakes_fail_a_pin(tmp_path, old, new):
     finally:
         ORACLE_MOD._INERTIA_LIB = saved
     assert not agree, f"planted mistake {old!r} -> {new!r} went unnoticed"
+
+
+# ------------------------------ SS-RI and SSRR-M (Sections 3.3, 4.1, 5.1, 5.2)
+def _string(N, L):
+    """The loaded string of Example 1 with N Chebyshev points of the first kind
+    on [3, 1e4] (Section 5.1) and L probe columns."""
+    s = W.loaded_string(N=N, L=L)
+    s.region = W.Region(5001.5, 4998.5, 0.1 * 4998.5, kind="interval")
+    return s
+
+
+def test_chebyshev_points_and_weights():
+    reg = W.Region(2.0, 3.0, 0.5, kind="interval")
+    z = oracle.sample_points(reg, 7)
+    x = np.cos((2 * np.arange(7) + 1) * np.pi / 14)
+    assert np.allclose(z, 2.0 + 3.0 * x, rtol=0, atol=1e-15)
+    # the Chebyshev weights are the barycentric weights up to a common factor
+    w = oracle.interpolation_weights(reg, z)
+    wb = oracle.interpolation_weights(W.Region(2.0, 3.0, 0.5, kind="points", points=z), z)
+    r = wb / w
+    assert np.allclose(r, r[0], rtol=1e-12)
+    # barycentric weights: sum_i w_i p(z_i) = leading coefficient of the
+    # interpolant, 0 for polynomials of degree < N - 1
+    zz = np.array([0.3, -1.1 + 0.4j, 2.0, 0.7 - 0.9j, 1.5j])
+    wb = oracle.interpolation_weights(W.Region(0j, 1.0, 1.0, kind="points", points=zz), zz)
+    for d in range(4):
+        assert abs(np.sum(wb * zz ** d)) <= 1e-13 * np.abs(wb).sum()
+    assert abs(np.sum(wb * zz ** 4)) > 1e-3 * np.abs(wb).sum()
+
+
+def test_ss_ri_on_the_loaded_string_follows_section_5_1():
+    """Section 5.1: with L = K = 10 (N = 200) SS-RI reaches about 1e-10 on the
+    32 eigenvalues; L = 3, K = 40 loses accuracy; L = 2, K = 60 fails."""
+    exact = oracle.bisect_real_eigenvalues(_string(200, 10), 3.0, 1e4).astype(complex)
+    assert len(exact) == 32
+    good = oracle.ss_ri(_string(200, 10), K=10)
+    assert len(good["lam"]) == 32 and match_eigs(exact, good["lam"]) <= 1e-9
+    worse = oracle.ss_ri(_string(200, 3), K=40)
+    assert len(worse["lam"]) != 32 or match_eigs(exact, worse["lam"]) > 10 * match_eigs(exact, good["lam"])
+    bad = oracle.ss_ri(_string(200, 2), K=60)
+    assert len(bad["lam"]) < 32
+
+
+def test_sampling_beats_moments_on_the_loaded_string_section_5_2():
+    """Section 5.2: with L = 1 and N = 100 Chebyshev points RSRR finds the 32
+    eigenvalues; SSRR-M with K = N does not (its moment matrix loses rank)."""
+    exact = oracle.bisect_real_eigenvalues(_string(100, 1), 3.0, 1e4).astype(complex)
+    s = oracle.rsrr(_string(100, 1), NQ=500, KQ=8)
+    assert len(s["lam"]) == 32 and match_eigs(exact, s["lam"]) <= 1e-9
+    m = oracle.ssrr_m(_string(100, 1), K=100, NQ=500, KQ=8)
+    assert len(m["lam"]) < 32 or match_eigs(exact, m["lam"]) > 1e-6
+
+
+@pytest.mark.parametrize("name", ["diag_quadratic", "diag_rational"])
+def test_ssrr_m_finds_closed_form_eigenvalues(name):
+    p = getattr(W, name)(N=48, L=8)
+    ref = exact_roots(p)
+    out = oracle.ssrr_m(p, K=6, NQ=256)
+    assert len(out["lam"]) == len(ref) and match_eigs(ref, out["lam"]) <= 1e-9
+
+
+@pytest.mark.parametrize("which", ["weights_sign", "hankel_unshifted"])
+def test_planted_moment_mistakes_fail_a_pin(monkeypatch, which):
+    ss_ri = ORACLE_MOD.ss_ri
+    if which == "weights_sign":   # (-1)^i dropped from the Chebyshev weights
+        orig = ORACLE_MOD.interpolation_weights
+        monkeypatch.setattr(ORACLE_MOD, "interpolation_weights", lambda r, z: np.abs(orig(r, z)))
+    else:   # H^< built from A_{i+j} instead of A_{i+j+1}
+        ss_ri = _mutated(ss_ri, "Hs = np.block([[A[i + j + 1]", "Hs = np.block([[A[i + j]")
+    exact = oracle.bisect_real_eigenvalues(_string(200, 10), 3.0, 1e4).astype(complex)
+    out = ss_ri(_string(200, 10), K=10)
+    assert len(out["lam"]) != 32 or match_eigs(exact, out["lam"]) > 1e-9
+
+
+# ------------------------------------------- stored full-size golden values
+def test_full_size_grid_golden_is_consistent():
+    """tests/golden/c1_eigs.json: the full-size count recomputed by the band
+    inertia, and the oracle's RSRR eigenvalues against the bisected ones."""
+    with open(os.path.join(GOLD, "c1_eigs.json")) as f:
+        g = json.load(f)
+    p = W.config("c1")
+    assert oracle.negative_inertia_band(p, 180.0) - oracle.negative_inertia_band(p, 20.0) == g["count_in_region"]
+    bis = np.array(g["bisection_eigenvalues"])
+    lam = np.array([complex(*z) for z in g["oracle_rsrr_eigenvalues"]])
+    assert len(bis) == len(lam) == g["count_in_region"] == 10
+    assert match_eigs(bis.astype(complex), lam) <= 1e-11
+    assert max(g["oracle_rsrr_residuals"]) <= 1e-14
+
+
+def test_dense_n1024_golden_is_consistent():
+    with open(os.path.join(GOLD, "dense_n1024.json")) as f:
+        g = json.load(f)
+    assert g["count_in_region"] == len(g["oracle_rsrr_eigenvalues"]) >= 1
+    lam = np.array([complex(*z) for z in g["oracle_rsrr_eigenvalues"]])
+    assert np.all(np.abs(lam - 3.0) < 1.0)
+    assert max(g["oracle_rsrr_residuals"]) <= 1e-12

@@ -41,11 +41,13 @@ class Fn:
 
 @dataclass
 class Region:
-    """Ellipse phi(a) = center + a*cos(t) + i*b*sin(t), or explicit sample points.
+    """Ellipse phi(a) = center + a*cos(t) + i*b*sin(t), explicit sample points,
+    or the real interval [center - a, center + a] of the ellipse's major axis.
 
-    For kind == "points" the explicit points are the sampling points and the
-    ellipse (center, a, b) is still the contour used for the projected solve
-    and for the inside test.
+    For kind == "points" the explicit points are the sampling points, and for
+    kind == "interval" the N Chebyshev points of the first kind on the
+    interval are; in both cases the ellipse (center, a, b) is still the
+    contour used for the projected solve and for the inside test.
     """
     center: complex
     a: float
