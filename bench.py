@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--batch-full", action="store_true", help="c3 at its full sizes")
+    ap.add_argument("--dense-n", type=int, default=4096, help="points of the dense kernel workload (c2)")
+    ap.add_argument("--dense-flags", type=int, default=0, help="RSRR_FLAG_* bits of the dense run (c2)")
     return ap.parse_args()
 
 
@@ -541,8 +543,8 @@ def run_dense(a):
     import workloads as W
     from paper_1605_07951_gb300 import rsrr
     torch.cuda.set_device(0)
-    p = W.helmholtz_sphere(n=4096, N=32, L=64)
-    s = rsrr.Solver(p, rsrr.default_opts(timing=1))
+    p = W.helmholtz_sphere(n=a.dense_n, N=32, L=64)
+    s = rsrr.Solver(p, rsrr.default_opts(timing=1, flags=a.dense_flags))
     stream = torch.cuda.current_stream()
     for _ in range(a.warmup):
         s.sample(stream)
@@ -559,7 +561,8 @@ def run_dense(a):
     s.close()
     n = p.n
     lu_flops = 8.0 / 3.0 * n ** 3 * p.N
-    print(json.dumps({"workload": "helmholtz_sphere_n4096_N32_L64", "metric": UNIT,
+    print(json.dumps({"workload": f"helmholtz_sphere_n{n}_N32_L64", "metric": UNIT,
+                      "dense_update": "fma" if a.dense_flags & rsrr.RSRR_FLAG_SIMT_DENSE_UPDATE else "tcgen05",
                       "sample_value": p.N * p.L / (ms / 1e3), "ms_per_sample": ms,
                       "stage_ms": st["stage_ms"][:5], "refine_sweeps": st["refine_sweeps"],
                       "max_eta": st["max_eta"],
