@@ -219,8 +219,32 @@ enum {
     RSRR_FLAG_PLAIN_SOLVE = 1,
     RSRR_FLAG_ONE_CTA_LU = 2,
     RSRR_FLAG_INJECT_TIMEOUT = 4,
-    RSRR_FLAG_SIMT_DENSE_UPDATE = 8
+    RSRR_FLAG_SIMT_DENSE_UPDATE = 8,
+    RSRR_FLAG_GRAPH = 16,
+    RSRR_FLAG_AUTOTUNE = 32,
+    RSRR_FLAG_WIDE_SOLVE_ONLY = 64
 };
+/* RSRR_FLAG_WIDE_SOLVE_ONLY: the refinement sweeps' streaming solves always
+ * take 16 right-hand sides per CTA.  By default a sweep in which few points
+ * are still above eta_tol (the points next to an eigenvalue converge last)
+ * runs a narrow shape instead, 4 right-hand sides per CTA and so four times
+ * as many CTAs per point, which shortens the per-point chain of block
+ * solves; the shape is chosen on the device from the points' done flags, so
+ * the sweeps stay asynchronous.  Both shapes do the same operations on every
+ * column (bit for bit the same samples); the flag exists for comparison. */
+/* RSRR_FLAG_GRAPH: rsrr_sample of the band path replays a CUDA graph: the
+ * first call runs eagerly, the second captures the call's launches on the
+ * caller's stream (it must not be the legacy default stream) and launches the
+ * graph, later calls launch it again (one launch in place of about 5 per
+ * refinement sweep).  If capture is not possible the call runs eagerly.
+ * rsrr_add_points drops the graph (buffers move).
+ * RSRR_FLAG_AUTOTUNE: the first rsrr_sample of the band path times the band
+ * LU as a cluster of two CTAs per point and as one CTA per point, and the
+ * streaming and the one-kernel solve, on the handle's own data, keeps the
+ * faster of each (results agree: the LU variants bitwise, the solves to
+ * rounding before refinement) and caches the choice per shape (n, kl, ku, N,
+ * L, precision) for the rest of the process; that first call waits for its
+ * timings. */
 
 typedef struct {
     int32_t precision;   /* RSRR_PREC_MIXED by default */

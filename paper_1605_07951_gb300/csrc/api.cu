@@ -3,6 +3,9 @@
 // buffers, and the orchestration of the sampling kernels (step 2).
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <complex>
 #include <cstdio>
 #include <cstring>
@@ -172,6 +175,7 @@ cudaError_t Handle::raw_free(void *p) { return pool ? cudaFreeAsync(p, hs) : cud
 cudaError_t Handle::wait() { return hs ? cudaStreamSynchronize(hs) : cudaDeviceSynchronize(); }
 
 Handle::~Handle() {
+    drop_graph();
     for (void *p : allocations) {
         if (pool) cudaFreeAsync(p, hs);
         else cudaFree(p);
@@ -719,9 +723,13 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
                                                                : band_solve2_smem_c128(geom);
         solve2 = !(opts.flags & RSRR_FLAG_PLAIN_SOLVE) && smem2 <= 227 * 1024 &&
                  geom.kl + geom.nb <= KL_MAX + 32;
-        if (solve2)
+        use_solve2 = solve2;
+        cluster_lu = !(opts.flags & RSRR_FLAG_ONE_CTA_LU);
+        if (solve2) {
             CK(alloc(&d_bperm, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb),
                "alloc block permutations");
+            CK(alloc(&d_gate, 1), "alloc");
+        }
     }
     if (opts.precision == RSRR_PREC_MIXED) {
         CK(alloc(&d_ab32, band), "alloc band factors (complex64)");
@@ -780,23 +788,180 @@ cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, int p0,
     const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
     const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
     if (mixed)
-        return solve2 ? launch_band_solve2_c64(d_ab32 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv32 + p0 * dv_pt,
+        return use_solve2 ? launch_band_solve2_c64(d_ab32 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv32 + p0 * dv_pt,
                                                static_cast<float2 *>(B), geom, np, nn, L, skip, s)
                       : launch_band_solve_c64(d_ab32 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv32 + p0 * dv_pt,
                                               static_cast<float2 *>(B), geom, np, nn, L, skip, s);
-    return solve2 ? launch_band_solve2_c128(d_ab64 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv64 + p0 * dv_pt,
+    return use_solve2 ? launch_band_solve2_c128(d_ab64 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv64 + p0 * dv_pt,
                                             static_cast<double2 *>(B), geom, np, nn, L, skip, s)
                   : launch_band_solve_c128(d_ab64 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv64 + p0 * dv_pt,
                                            static_cast<double2 *>(B), geom, np, nn, L, skip, s);
 }
 
-rsrr_status Handle::sample(cudaStream_t s) { return dense ? sample_dense(0, N, s) : sample_band(0, N, s); }
+cudaError_t Handle::sweep_solve(float2 *B, const int32_t *skip, int p0, int np, cudaStream_t s) {
+    if (!use_solve2 || !d_gate || (opts.flags & RSRR_FLAG_WIDE_SOLVE_ONLY)) return band_solve(true, B, skip, p0, np, s);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_point = (L + 3) / 4;  // CTAs of a point in the narrow shape
+    const int thr = std::max(1, sms / per_point);
+    const size_t ab_pt = (size_t)geom.ldab * n;
+    const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
+    const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
+    const float2 *ab = d_ab32 + p0 * ab_pt, *dv = d_dinv32 + p0 * dv_pt;
+    const int32_t *bp = d_bperm + p0 * bp_pt;
+    cudaError_t e = launch_solve_gate(skip, np, thr, d_gate, s);
+    if (e == cudaSuccess) e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, false, d_gate, 0);
+    if (e == cudaSuccess) e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, true, d_gate, 1);
+    launches += 2;
+    return e;
+}
+
+rsrr_status Handle::sample(cudaStream_t s) {
+    if (dense) return sample_dense(0, N, s);
+    if ((opts.flags & RSRR_FLAG_AUTOTUNE) && !tuned) {
+        rsrr_status st = autotune(s);
+        if (st != RSRR_OK) return st;
+    }
+    if (opts.flags & RSRR_FLAG_GRAPH) return sample_graph(s);
+    return sample_band(0, N, s);
+}
+
+namespace {
+// the autotuner's choices per problem shape, for the whole process
+struct TuneKey {
+    int64_t n;
+    int kl, ku, N, L, prec;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(n, kl, ku, N, L, prec) < std::tie(o.n, o.kl, o.ku, o.N, o.L, o.prec);
+    }
+};
+struct TuneVal {
+    bool cluster, solve2;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+}  // namespace
+
+// Times the band LU variants (cluster of two CTAs, one CTA per point; same
+// factors bit for bit) and the solve variants (streaming, one-kernel) on the
+// handle's own problem, keeps the faster of each, and caches the choice.
+rsrr_status Handle::autotune(cudaStream_t s) {
+    Handle *h = this;
+    tuned = true;
+    const TuneKey key{n, kl, ku, N, L, opts.precision};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            cluster_lu = it->second.cluster;
+            use_solve2 = solve2 && it->second.solve2;
+            return RSRR_OK;
+        }
+    }
+    const bool mixed = opts.precision == RSRR_PREC_MIXED;
+    const int nn = (int)n;
+    const int64_t per_pt = (int64_t)n * L;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "tune event");
+    CK(cudaEventCreate(&e1), "tune event");
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } guard{e0, e1};
+    auto elapsed = [&](float *ms) {
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        return e;
+    };
+    float t_lu[2] = {0.f, 0.f}, t_sv[2] = {1e30f, 1e30f};
+    for (int c = 0; c < 2; ++c) {  // c = 1: cluster
+        if (mixed) CK(launch_assemble<float2>(d_ab32, geom, dp, s), "tune assemble");
+        else CK(launch_assemble<double2>(d_ab64, geom, dp, s), "tune assemble");
+        CK(cudaEventRecord(e0, s), "tune event");
+        if (mixed) CK(launch_band_lu_c64(d_ab32, d_piv, d_info, d_dinv32, geom, N, nn, s, c == 1), "tune LU");
+        else CK(launch_band_lu_c128(d_ab64, d_piv, d_info, d_dinv64, geom, N, nn, s, c == 1), "tune LU");
+        CK(cudaEventRecord(e1, s), "tune event");
+        CK(elapsed(&t_lu[c]), "tune timing");
+        launches += 2;
+    }
+    if (solve2) {
+        CK(launch_block_perm(d_bperm, d_piv, nn, geom.kl, geom.nb, N, s), "tune block permutations");
+        launches += 1;
+    }
+    const bool save = use_solve2;
+    for (int v = 0; v < (solve2 ? 2 : 1); ++v) {  // v = 1: streaming
+        use_solve2 = v == 1;
+        void *B = mixed ? (void *)d_D : (void *)d_X;
+        if (mixed) CK(launch_broadcast_probe_c64(d_D, d_U, per_pt, N, s), "tune probe");
+        else CK(launch_broadcast_probe_c128(d_X, d_U, per_pt, N, s), "tune probe");
+        CK(cudaEventRecord(e0, s), "tune event");
+        CK(band_solve(mixed, B, nullptr, 0, N, s), "tune solve");
+        CK(cudaEventRecord(e1, s), "tune event");
+        CK(elapsed(&t_sv[v]), "tune timing");
+        launches += 2;
+    }
+    use_solve2 = save;
+    const TuneVal val{t_lu[1] <= t_lu[0], solve2 && t_sv[1] <= t_sv[0]};
+    cluster_lu = val.cluster;
+    use_solve2 = val.solve2;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = val;
+    return RSRR_OK;
+}
+
+void Handle::drop_graph() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    graph_exec = nullptr;
+    graph = nullptr;
+    graph_calls = 0;
+}
+
+// rsrr_sample as a CUDA graph: eager first call, capture on the second, replays after
+rsrr_status Handle::sample_graph(cudaStream_t s) {
+    Handle *h = this;
+    if (graph_exec) {
+        CK(cudaGraphLaunch(graph_exec, s), "graph launch");
+        launches += graph_launches;
+        timed_sample = opts.timing != 0;
+        return RSRR_OK;
+    }
+    if (graph_failed || s == nullptr || graph_calls++ == 0) return sample_band(0, N, s);
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        graph_failed = true;
+        return sample_band(0, N, s);
+    }
+    const int64_t l0 = launches;
+    const rsrr_status st = sample_band(0, N, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (st != RSRR_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        graph_failed = true;
+        launches = l0;
+        return sample_band(0, N, s);
+    }
+    graph = g;
+    graph_launches = launches - l0;
+    launches = l0;
+    if (cudaGraphInstantiate(&graph_exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph();
+        graph_failed = true;
+        return sample_band(0, N, s);
+    }
+    CK(cudaGraphLaunch(graph_exec, s), "graph launch");
+    launches += graph_launches;
+    return RSRR_OK;
+}
 
 // Step 2 of RSRR on the GPU for sampling points p0 .. p0+np-1, asynchronously
 // on stream s (every point for rsrr_sample; the appended points for
 // rsrr_add_points, which leaves the others' samples untouched).
 rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
-    const bool cluster_lu = !(opts.flags & RSRR_FLAG_ONE_CTA_LU);
     Handle *h = this;
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L;
@@ -826,7 +991,7 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
         CK(launch_assemble<float2>(ab, geom, dq, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
         CK(launch_band_lu_c64(ab, piv, info, d_dinv32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
-        if (solve2) {
+        if (use_solve2) {
             CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
@@ -842,7 +1007,7 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
             CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),
                "eta");
             CK(launch_narrow(D, R, per_pt, np, done, s), "narrow");
-            CK(band_solve(true, D, done, p0, np, s), "band solve");
+            CK(sweep_solve(D, done, p0, np, s), "band solve");
             CK(launch_update(X, D, per_pt, np, done, s), "update");
             launches += 5;
         }
@@ -851,7 +1016,7 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
         CK(launch_assemble<double2>(ab, geom, dq, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
         CK(launch_band_lu_c128(ab, piv, info, d_dinv64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
-        if (solve2) {
+        if (use_solve2) {
             CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
@@ -961,6 +1126,7 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
         }
         if (d_bperm) CK(regrow(&d_bperm, nblk * 2 * geom.nb, N0, N1, false), "regrow");
     }
+    drop_graph();  // the captured launches name the old buffers
     // the projection's work space is sized by N L: rebuilt by the next rsrr_project
     if (proj_ws) {
         release(proj_ws, proj_ws_bytes);

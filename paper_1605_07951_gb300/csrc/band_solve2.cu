@@ -137,8 +137,12 @@ template <typename C, int NB, int LC, int S2_RC, int S2_NSLOT>
 __global__ void __launch_bounds__(S2_THREADS, 1)
 band_solve2_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ bperm_all,
                    const C *__restrict__ dinv_all, C *__restrict__ B_all, int n, int kl, int ku,
-                   int ldab, int L, int WR, const int32_t *__restrict__ skip) {
+                   int ldab, int L, int WR, const int32_t *__restrict__ skip,
+                   const int32_t *__restrict__ gate, int gate_want) {
     using LY = S2Layout<C, NB, LC, S2_RC, S2_NSLOT>;
+    // a gated launch runs only if the gate word holds gate_want (one of the
+    // two shapes of a refinement sweep, chosen on the device)
+    if (gate && __ldg(gate) != gate_want) return;
     constexpr int S2_DIST = S2_NSLOT - 1;
     constexpr int E16 = LY::E16, PLD = LY::PLD, MAXCH = LY::MAXCH, PAIRS = LY::PAIRS;
     constexpr int WLD = LY::WLD;
@@ -340,9 +344,28 @@ static size_t s2_smem_used(const BandGeom &g) {
 size_t band_solve2_smem_c64(const BandGeom &g) { return s2_smem_used<float2, NB_C64, 16>(g); }
 size_t band_solve2_smem_c128(const BandGeom &g) { return s2_smem_used<double2, NB_C128, 8>(g); }
 
+// gate = 1 if at most thr points have done == 0 (few points left: the
+// narrow shape, more CTAs per point), else 0
+__global__ void solve_gate_kernel(const int32_t *__restrict__ done, int N, int thr, int32_t *__restrict__ gate) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) c += done[i] == 0 ? 1 : 0;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *gate = cnt <= thr ? 1 : 0;
+}
+
+cudaError_t launch_solve_gate(const int32_t *done, int N, int thr, int32_t *gate, cudaStream_t s) {
+    solve_gate_kernel<<<1, 256, 0, s>>>(done, N, thr, gate);
+    return cudaGetLastError();
+}
+
 template <typename C, int NB, int LC, int RC, int NSLOT>
 static cudaError_t s2_launch(const C *ab, const int32_t *bperm, const C *dinv, C *B, const BandGeom &g,
-                             int N, int n, int L, const int32_t *skip, cudaStream_t s) {
+                             int N, int n, int L, const int32_t *skip, const int32_t *gate, int want,
+                             cudaStream_t s) {
     const size_t smem = s2_smem<C, NB, LC, RC, NSLOT>(g);
     const int limit = smem_optin_limit();
     if (smem > 227 * 1024 || smem > (size_t)limit) return cudaErrorInvalidConfiguration;
@@ -351,27 +374,30 @@ static cudaError_t s2_launch(const C *ab, const int32_t *bperm, const C *dinv, C
     if (e != cudaSuccess) return e;
     dim3 grid((L + LC - 1) / LC, N);
     band_solve2_kernel<C, NB, LC, RC, NSLOT><<<grid, S2_THREADS, smem, s>>>(
-        ab, bperm, dinv, B, n, g.kl, g.ku, g.ldab, L, s2_window(g, NB, NSLOT), skip);
+        ab, bperm, dinv, B, n, g.kl, g.ku, g.ldab, L, s2_window(g, NB, NSLOT), skip, gate, want);
     return cudaGetLastError();
 }
 
 template <typename C, int NB, int LC>
 static cudaError_t s2_dispatch(const C *ab, const int32_t *bperm, const C *dinv, C *B,
                                const BandGeom &g, int N, int n, int L, const int32_t *skip,
-                               cudaStream_t s) {
-    if (s2_wide<C, NB, LC>(g)) return s2_launch<C, NB, LC, 256, 2>(ab, bperm, dinv, B, g, N, n, L, skip, s);
-    return s2_launch<C, NB, LC, 128, 3>(ab, bperm, dinv, B, g, N, n, L, skip, s);
+                               const int32_t *gate, int want, cudaStream_t s) {
+    if (s2_wide<C, NB, LC>(g))
+        return s2_launch<C, NB, LC, 256, 2>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    return s2_launch<C, NB, LC, 128, 3>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
 }
 
 cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const float2 *dinv,
                                    float2 *B, const BandGeom &g, int N, int n, int L,
-                                   const int32_t *skip, cudaStream_t s) {
-    return s2_dispatch<float2, NB_C64, 16>(ab, bperm, dinv, B, g, N, n, L, skip, s);
+                                   const int32_t *skip, cudaStream_t s, bool narrow,
+                                   const int32_t *gate, int want) {
+    if (narrow) return s2_dispatch<float2, NB_C64, 4>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    return s2_dispatch<float2, NB_C64, 16>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
 }
 cudaError_t launch_band_solve2_c128(const double2 *ab, const int32_t *bperm, const double2 *dinv,
                                     double2 *B, const BandGeom &g, int N, int n, int L,
                                     const int32_t *skip, cudaStream_t s) {
-    return s2_dispatch<double2, NB_C128, 8>(ab, bperm, dinv, B, g, N, n, L, skip, s);
+    return s2_dispatch<double2, NB_C128, 8>(ab, bperm, dinv, B, g, N, n, L, skip, nullptr, 0, s);
 }
 
 }  // namespace rsrr

@@ -40,6 +40,7 @@ constexpr int BM = 128;              // complex rows of a tile
 constexpr int BN = 128;              // complex columns of a tile
 constexpr int KR = 64;               // real depth (2 x 32)
 constexpr int THREADS = 256;
+static_assert(BM == BN && (BM * 32) % THREADS == 0, "packing: equal A and B element counts per thread");
 constexpr int A_BYTES = BM * KR * 4;           // one TF32 part of A' (32 KB)
 constexpr int B_BYTES = 2 * BN * KR * 4;       // one TF32 part of B' (64 KB)
 constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 64;
@@ -119,12 +120,24 @@ dense_tc_update_kernel(float2 *__restrict__ A_all, int n, int k0, int jb, unsign
                      ::"r"((uint32_t)__cvta_generic_to_shared(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    // A' = [Ar | Ai]: row r, depth t (real part) and 32 + t (imaginary part)
-#pragma unroll 4
-    for (int e = tid; e < BM * 32; e += THREADS) {
+    // A' = [Ar | Ai]: row r, depth t (real part) and 32 + t (imaginary part).
+    // Every thread first loads all its elements of A and B (32 loads in
+    // flight), then splits and stores them.
+    constexpr int PER = BM * 32 / THREADS;  // elements of A (and of B) per thread
+    float2 va[PER], vb[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * THREADS;
         const int t = e / BM, r = e % BM;
-        float2 v = make_float2(0.f, 0.f);
-        if (t < jb && r0 + r < n) v = A[(size_t)(k0 + t) * n + r0 + r];
+        va[q] = (t < jb && r0 + r < n) ? A[(size_t)(k0 + t) * n + r0 + r] : make_float2(0.f, 0.f);
+        const int tb = e % 32, j = e / 32;
+        vb[q] = (tb < jb && c0 + j < n) ? A[(size_t)(c0 + j) * n + k0 + tb] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * THREADS;
+        const int t = e / BM, r = e % BM;
+        const float2 v = va[q];
         float h, l;
         split_tf32(v.x, h, l);
         *reinterpret_cast<float *>(a_hi + kmajor_off(r, t, BM)) = h;
@@ -135,11 +148,11 @@ dense_tc_update_kernel(float2 *__restrict__ A_all, int n, int k0, int jb, unsign
     }
     // B' rows j (real output columns) and BN + j (imaginary): depth t carries
     // (Br, Bi), depth 32 + t carries (-Bi, Br)
-#pragma unroll 4
-    for (int e = tid; e < BN * 32; e += THREADS) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * THREADS;
         const int t = e % 32, j = e / 32;
-        float2 v = make_float2(0.f, 0.f);
-        if (t < jb && c0 + j < n) v = A[(size_t)(c0 + j) * n + k0 + t];
+        const float2 v = vb[q];
         float rh, rl, ih, il, nh, nl;
         split_tf32(v.x, rh, rl);
         split_tf32(v.y, ih, il);

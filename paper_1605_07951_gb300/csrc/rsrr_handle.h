@@ -83,7 +83,17 @@ struct Handle {
     double2 *d_dinv64 = nullptr;      // per block L11^{-1}, U11^{-1} (complex128)
     int32_t *d_piv = nullptr, *d_info = nullptr, *d_done = nullptr, *d_sweep_flags = nullptr;
     int32_t *d_bperm = nullptr;       // composed row permutation of every block (streaming solve)
-    bool solve2 = false;              // streaming band solve in use
+    int32_t *d_gate = nullptr;        // shape of a refinement sweep's solve (few points left: narrow)
+    bool solve2 = false;              // streaming band solve possible (block permutations allocated)
+    bool use_solve2 = false;          // streaming band solve in use (autotuned or solve2)
+    bool cluster_lu = true;           // band LU by a cluster of two CTAs per point
+    bool tuned = false;               // the autotuner's choice is applied
+    // CUDA graph of rsrr_sample (RSRR_FLAG_GRAPH, band path)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
+    int graph_calls = 0;
+    bool graph_failed = false;
     double *d_tnorm = nullptr, *d_eta = nullptr, *d_rmax = nullptr, *d_xmax = nullptr;
 
     // projection stage (proj.cu)
@@ -130,8 +140,15 @@ struct Handle {
     size_t estimate_bytes();
     rsrr_status allocate_and_upload(const std::vector<double2> &coef);
     rsrr_status sample(cudaStream_t s);  // every point, band or dense
+    rsrr_status sample_graph(cudaStream_t s);
+    rsrr_status autotune(cudaStream_t s);
+    void drop_graph();
     rsrr_status sample_band(int p0, int np, cudaStream_t s);
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);
+    // a refinement sweep's complex64 solve: streaming solve in the wide shape
+    // while many points are left, in the narrow one when few are (chosen on
+    // the device from the done flags)
+    cudaError_t sweep_solve(float2 *B, const int32_t *skip, int p0, int np, cudaStream_t s);
     rsrr_status sample_dense(int p0, int np, cudaStream_t s);
     rsrr_status dense_residual(bool skip_done, int p0, int np, cudaStream_t s);
     // appends sampling points (buffers regrown, the old samples kept) and

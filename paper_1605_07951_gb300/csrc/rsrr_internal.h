@@ -125,9 +125,15 @@ cudaError_t launch_block_perm(int32_t *bperm, const int32_t *piv, int n, int kl,
                               cudaStream_t s);
 size_t band_solve2_smem_c64(const BandGeom &g);
 size_t band_solve2_smem_c128(const BandGeom &g);
+// narrow: 4 right-hand sides per CTA instead of 16 (more CTAs per point, the
+// same operations on every column); with gate set, the launch runs only if
+// *gate == want (launch_solve_gate writes it on the device)
 cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const float2 *dinv,
                                    float2 *B, const BandGeom &g, int N, int n, int L,
-                                   const int32_t *skip, cudaStream_t s);
+                                   const int32_t *skip, cudaStream_t s, bool narrow = false,
+                                   const int32_t *gate = nullptr, int want = 0);
+// *gate = 1 if at most thr of the N done flags are 0, else 0
+cudaError_t launch_solve_gate(const int32_t *done, int N, int thr, int32_t *gate, cudaStream_t s);
 cudaError_t launch_band_solve2_c128(const double2 *ab, const int32_t *bperm, const double2 *dinv,
                                     double2 *B, const BandGeom &g, int N, int n, int L,
                                     const int32_t *skip, cudaStream_t s);

@@ -188,3 +188,42 @@ def test_cluster_lu_matches_the_one_cta_lu_bitwise(rs, name, make, precision):
     assert np.array_equal(a["S"], b["S"])
     if precision == 1:
         compare(p, run(rs, p, precision), rel_tol=1e-6, eta_tol=ETA_TOL)
+
+
+def test_graph_replay_gives_the_eager_samples(rs):
+    """RSRR_FLAG_GRAPH: the eager first call, the captured second call and a
+    replay give bit for bit the samples of a handle without the flag."""
+    import torch
+    p = W.rational_grid(g=40, N=8, L=4)
+    stream = torch.cuda.Stream()
+    ref = run(rs, p, rs.RSRR_PREC_MIXED)["S"]
+    s = rs.Solver(p, rs.default_opts(flags=rs.RSRR_FLAG_GRAPH))
+    for _ in range(3):
+        s.sample(stream)
+        stream.synchronize()
+        assert s.check_status(stream) == rs.RSRR_OK
+        assert np.array_equal(s.samples(), ref)
+    s.close()
+
+
+def test_autotuned_sampling_reaches_the_oracle(rs):
+    """RSRR_FLAG_AUTOTUNE: whichever LU and solve variants the first call
+    keeps, the refined samples reach the oracle (and the cached choice serves
+    a second handle of the same shape)."""
+    p = W.rational_grid(g=40, N=8, L=4)
+    for _ in range(2):
+        out = run(rs, p, rs.RSRR_PREC_MIXED, flags=rs.RSRR_FLAG_AUTOTUNE)
+        compare(p, out, rel_tol=1e-6, eta_tol=ETA_TOL)
+
+
+def test_narrow_late_sweeps_give_the_wide_samples_bitwise(rs):
+    """The refinement sweeps switch to the narrow solve shape (4 right-hand
+    sides per CTA) once few points are left; every column sees the same
+    operations, so the samples equal those of the wide shape bit for bit."""
+    p = W.rational_grid(g=48, N=64, L=16)
+    a = run(rs, p, rs.RSRR_PREC_MIXED)
+    b = run(rs, p, rs.RSRR_PREC_MIXED, flags=rs.RSRR_FLAG_WIDE_SOLVE_ONLY)
+    assert a["status"] == b["status"] == rs.RSRR_OK
+    assert a["stats"]["refine_sweeps"] == b["stats"]["refine_sweeps"] >= 2
+    assert np.array_equal(a["S"], b["S"])
+    compare(p, a, rel_tol=1e-6, eta_tol=ETA_TOL)
