@@ -317,10 +317,19 @@ def serve_stream(rsrr, reqs, rate, precision, slots, seed):
     lat = np.array([(r["t_done"] - r["t_submit"]) + lg for r, lg in zip(reps, lag)])
     cols = sum(p.N * p.L for _, p in reqs)
     ok = sum(1 for r in reps if r["status"] >= 0)
+    # where a request's time goes, per family (medians over the stream):
+    # queueing, the three stages on the request's own stream, sweeps and rank
+    stages = {}
+    for fam in sorted({f for f, _ in reqs}):
+        rr = [r for (f, _), r in zip(reqs, reps) if f == fam]
+        med = lambda key, sc=1e3: float(np.median([r[key] for r in rr]) * sc)  # noqa: E731
+        stages[fam] = {"count": len(rr), "queue_ms": float(np.median([r["t_admit"] - r["t_submit"] for r in rr]) * 1e3),
+                       "sample_ms": med("t_sample"), "project_ms": med("t_project"), "solve_ms": med("t_solve"),
+                       "refine_sweeps": med("refine_sweeps", 1), "k": med("k", 1)}
     return {"requests": len(reqs), "ok": ok, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
             "makespan_s": t_end, "req_per_s": len(reqs) / t_end, "columns_per_s": cols / t_end,
-            "peak_active": st["peak_active"], "peak_bytes": int(st["peak_bytes"])}
+            "peak_active": st["peak_active"], "peak_bytes": int(st["peak_bytes"]), "stages": stages}
 
 
 def run_serving(a):

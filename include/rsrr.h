@@ -267,7 +267,24 @@ typedef struct {
                             rsrr_estimate_bytes exceed it; 0 (default): no limit */
     int32_t method;      /* RSRR_METHOD_*, default RSRR_METHOD_RSRR */
     int32_t K;           /* moments of SSRR-M and SS-RI (1 <= K <= N), default 2 */
+    int32_t refine;      /* RSRR_REFINE_*, default RSRR_REFINE_IR (band path, mixed precision) */
+    int32_t gmres_m;     /* Krylov steps per GMRES cycle (1 .. 16), default 4 */
 } rsrr_opts;
+
+/* Refinement of the mixed-precision samples (band path):
+ *   RSRR_REFINE_IR     r = U - T X in FP64, d = LU \ r in complex64, X += d,
+ *                      sweeps queued asynchronously (the default).
+ *   RSRR_REFINE_GMRES  each of the max_refine cycles computes r = U - T X in
+ *                      FP64 and runs gmres_m steps of GMRES on T d = r per
+ *                      column, right-preconditioned by the complex64 LU
+ *                      (Arnoldi vectors and products in FP64, modified
+ *                      Gram-Schmidt on the GPU, the small least-squares
+ *                      problems on the host), then X += d; robust where
+ *                      T(z_j) is too ill-conditioned for plain refinement
+ *                      (points close to eigenvalues).  It waits for the
+ *                      stream once a cycle and holds (2 gmres_m + 1) n N L
+ *                      complex128 of Krylov vectors, allocated on first use. */
+enum { RSRR_REFINE_IR = 0, RSRR_REFINE_GMRES = 1 };
 
 /* Method of rsrr_project / rsrr_solve on the same samples X_j:
  *   RSRR_METHOD_RSRR    the resolvent sampling scheme (Section 4.3): basis of
@@ -550,6 +567,9 @@ typedef struct {
     double t_submit;       /* seconds since rsrr_server_create: submission (arrival), */
     double t_admit;        /* admission (slot and memory granted) and */
     double t_done;         /* results on the host */
+    double t_sample;       /* wall seconds of the request's rsrr_sample (to its outcome), */
+    double t_project;      /* rsrr_project (to its last product) and */
+    double t_solve;        /* rsrr_solve (SS-FULL, eigenvectors, residuals) */
     size_t device_bytes;   /* bytes admitted against the budget */
     int64_t n;
     const rsrr_c128 *lam;  /* count eigenvalues, as rsrr_result */

@@ -25,6 +25,7 @@ UNITS = [
     ("noalloc.cu", [], "noalloc.o"),
     ("dense.cu", [], "dense.o"),
     ("dense_tc.cu", [], "dense_tc.o"),
+    ("refine.cu", [], "refine.o"),
     ("ozaki.cu", [], "ozaki.o"),
     ("band_solve2.cu", [], "band_solve2.o"),
     ("server.cu", [], "server.o"),

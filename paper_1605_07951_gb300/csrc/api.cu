@@ -243,6 +243,8 @@ void rsrr_opts_default(rsrr_opts *o) {
     o->gemm = RSRR_GEMM_AUTO;
     o->method = RSRR_METHOD_RSRR;
     o->K = 2;
+    o->refine = RSRR_REFINE_IR;
+    o->gmres_m = 4;
 }
 
 static rsrr_status create_fail(const char *msg) {
@@ -347,6 +349,10 @@ static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts
         return create_fail("rsrr_create: unknown method");
     if (opts && opts->method != RSRR_METHOD_RSRR && (opts->K < 1 || opts->K > N))
         return create_fail("rsrr_create: the moment methods need 1 <= K <= N");
+    if (opts && (opts->refine < RSRR_REFINE_IR || opts->refine > RSRR_REFINE_GMRES))
+        return create_fail("rsrr_create: unknown refinement");
+    if (opts && opts->refine == RSRR_REFINE_GMRES && (opts->gmres_m < 1 || opts->gmres_m > 16))
+        return create_fail("rsrr_create: gmres_m out of range (1 .. 16)");
     return RSRR_OK;
 }
 
@@ -816,6 +822,121 @@ cudaError_t Handle::sweep_solve(float2 *B, const int32_t *skip, int p0, int np, 
     return e;
 }
 
+// GMRES refinement (Section 4.3's X_j = T(z_j)^{-1} U to FP64 backward
+// error): per cycle r = U - T X and eta (done flags), then gmres_m Arnoldi
+// steps per active column: z_j = LU^{-1} v_j (complex64 solve), w = T z_j
+// (FP64), modified Gram-Schmidt against v_0..v_j, v_{j+1} = w / ||w||; the
+// (m+1) x m Hessenberg least-squares problem min ||beta e_1 - H y|| of every
+// column is solved on the host by Givens rotations, and X += Z y.
+rsrr_status Handle::refine_gmres(int p0, int np, const DevProblem &dq, cudaStream_t s) {
+    Handle *h = this;
+    const int m_ = opts.gmres_m, NL = N * L;
+    const int64_t per_pt = (int64_t)n * L;
+    const int nc = np * L;  // columns of the range
+    const size_t vec = (size_t)n * NL;
+    if (!d_gV) {
+        CK(alloc(&d_gV, vec * (m_ + 1)), "alloc GMRES vectors");
+        CK(alloc(&d_gZ, vec * m_), "alloc GMRES directions");
+        CK(alloc(&d_zeroU, (size_t)per_pt), "alloc");
+        CK(alloc(&d_gH, (size_t)NL * (m_ + 1) * m_), "alloc");
+        CK(alloc(&d_gy, (size_t)NL * m_), "alloc");
+        CK(alloc(&d_gnorm, (size_t)NL * (m_ + 1)), "alloc");
+        CK(cudaMemsetAsync(d_zeroU, 0, sizeof(double2) * per_pt, s), "memset");
+    }
+    DevProblem d0 = dq;  // T z with a zero probe: residual kernel gives -T z
+    d0.U = d_zeroU;
+    int32_t *done = d_done + p0;
+    double *tnorm = d_tnorm + p0, *eta = d_eta + (size_t)p0 * L;
+    double *rmax = d_rmax + (size_t)p0 * L, *xmax = d_xmax + (size_t)p0 * L;
+    double2 *X = d_X + p0 * per_pt, *R = d_R + p0 * per_pt;
+    float2 *D = d_D + p0 * per_pt;
+    auto Vj = [&](int j) { return d_gV + (size_t)j * vec + p0 * per_pt; };
+    auto Zj = [&](int j) { return d_gZ + (size_t)j * vec + p0 * per_pt; };
+    double2 *H = d_gH;        // (i, j) block of nc entries at (i m + j) NL
+    double *nrm = d_gnorm;    // beta at 0, ||w_j|| at (j + 1) NL
+    std::vector<int32_t> hdone(np);
+    std::vector<double2> hH((size_t)NL * (m_ + 1) * m_), hy((size_t)NL * m_);
+    std::vector<double> hn((size_t)NL * (m_ + 1));
+    for (int it = 0; it < opts.max_refine; ++it) {
+        CK(launch_residual(R, X, dq, rmax, xmax, done, s), "residual");
+        CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),
+           "eta");
+        CK(cudaMemcpyAsync(hdone.data(), done, sizeof(int32_t) * np, cudaMemcpyDeviceToHost, s), "done");
+        CK(cudaStreamSynchronize(s), "done sync");
+        bool any = false;
+        for (int q = 0; q < np; ++q) any = any || !hdone[q];
+        launches += 2;
+        if (!any) break;
+        CK(rf_norm(R, n, nc, L, done, nrm, s), "beta");
+        CK(rf_scale(Vj(0), R, nrm, n, nc, L, done, s), "v0");
+        launches += 2;
+        for (int j = 0; j < m_; ++j) {
+            CK(launch_narrow(D, Vj(j), per_pt, np, done, s), "narrow");
+            CK(sweep_solve(D, done, p0, np, s), "preconditioner");
+            CK(launch_widen(Zj(j), D, per_pt * np, s), "widen");
+            CK(launch_residual(R, Zj(j), d0, rmax, xmax, done, s), "T z");
+            CK(rf_axpy(R, nullptr, nullptr, -1.0, n, nc, L, done, s), "w = T z");
+            launches += 5;
+            for (int i = 0; i <= j; ++i) {
+                double2 *hij = H + (size_t)(i * m_ + j) * NL;
+                CK(rf_dot(Vj(i), R, n, nc, L, done, hij, s), "h_ij");
+                CK(rf_axpy(R, Vj(i), hij, 1.0, n, nc, L, done, s), "w -= h v");
+                launches += 2;
+            }
+            CK(rf_norm(R, n, nc, L, done, nrm + (size_t)(j + 1) * NL, s), "h_j+1,j");
+            CK(rf_scale(Vj(j + 1), R, nrm + (size_t)(j + 1) * NL, n, nc, L, done, s), "v_j+1");
+            launches += 2;
+        }
+        CK(cudaMemcpyAsync(hH.data(), H, sizeof(double2) * hH.size(), cudaMemcpyDeviceToHost, s), "H");
+        CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost, s), "H");
+        CK(cudaStreamSynchronize(s), "H sync");
+        // per column: Givens QR of the (m+1) x m Hessenberg, y = R^{-1} g
+        for (int c = 0; c < nc; ++c) {
+            if (hdone[c / L]) continue;
+            std::vector<cplx> Hc((size_t)(m_ + 1) * m_, 0.0), g(m_ + 1, 0.0);
+            for (int j = 0; j < m_; ++j) {
+                for (int i = 0; i <= j; ++i) {
+                    const double2 v = hH[(size_t)(i * m_ + j) * NL + c];
+                    Hc[(size_t)j * (m_ + 1) + i] = cplx(v.x, v.y);
+                }
+                Hc[(size_t)j * (m_ + 1) + j + 1] = hn[(size_t)(j + 1) * NL + c];
+            }
+            g[0] = hn[c];
+            int kk = m_;  // columns used: up to the first (lucky) breakdown
+            for (int j = 0; j < m_; ++j) {
+                cplx &a = Hc[(size_t)j * (m_ + 1) + j], &b = Hc[(size_t)j * (m_ + 1) + j + 1];
+                // (the rotations of steps < j were applied to this column at their step)
+                const double r = std::sqrt(std::norm(a) + std::norm(b));
+                if (r == 0.0) { kk = j; break; }
+                const cplx cs = a / r, sn = b / r;
+                // rotation G = [[conj(cs), conj(sn)], [-sn, cs]] on rows j, j+1 of columns j.. and of g
+                for (int jj = j; jj < m_; ++jj) {
+                    cplx &x = Hc[(size_t)jj * (m_ + 1) + j], &y2 = Hc[(size_t)jj * (m_ + 1) + j + 1];
+                    const cplx t1 = std::conj(cs) * x + std::conj(sn) * y2, t2 = -sn * x + cs * y2;
+                    x = t1;
+                    y2 = t2;
+                }
+                const cplx g1 = std::conj(cs) * g[j] + std::conj(sn) * g[j + 1], g2 = -sn * g[j] + cs * g[j + 1];
+                g[j] = g1;
+                g[j + 1] = g2;
+                if (hn[(size_t)(j + 1) * NL + c] == 0.0) { kk = j + 1; break; }
+            }
+            std::vector<cplx> y(m_, 0.0);
+            for (int j = kk - 1; j >= 0; --j) {
+                cplx acc = g[j];
+                for (int jj = j + 1; jj < kk; ++jj) acc -= Hc[(size_t)jj * (m_ + 1) + j] * y[jj];
+                y[j] = acc / Hc[(size_t)j * (m_ + 1) + j];
+            }
+            for (int j = 0; j < m_; ++j) hy[(size_t)c * m_ + j] = make_double2(y[j].real(), y[j].imag());
+        }
+        CK(cudaMemcpyAsync(d_gy, hy.data(), sizeof(double2) * (size_t)nc * m_, cudaMemcpyHostToDevice, s), "y");
+        CK(rf_update(X, Zj(0), (int64_t)vec, d_gy, m_, n, nc, L, done, s), "X += Z y");
+        CK(cudaStreamSynchronize(s), "y sync");  // the host copy of y is reused next cycle
+        launches += 1;
+    }
+    return RSRR_OK;
+}
+
 rsrr_status Handle::sample(cudaStream_t s) {
     if (dense) return sample_dense(0, N, s);
     if ((opts.flags & RSRR_FLAG_AUTOTUNE) && !tuned) {
@@ -1002,6 +1123,9 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
         CK(cudaMemsetAsync(done, 0, sizeof(int32_t) * np, s), "memset");
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         launches += 5;  // assemble, LU, probe, solve, widen
+        if (opts.refine == RSRR_REFINE_GMRES) {
+            if ((ms = refine_gmres(p0, np, dq, s)) != RSRR_OK) return ms;
+        } else
         for (int it = 0; it < opts.max_refine; ++it) {
             CK(launch_residual(R, X, dq, rmax, xmax, done, s), "residual");
             CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),

@@ -84,6 +84,12 @@ struct Handle {
     int32_t *d_piv = nullptr, *d_info = nullptr, *d_done = nullptr, *d_sweep_flags = nullptr;
     int32_t *d_bperm = nullptr;       // composed row permutation of every block (streaming solve)
     int32_t *d_gate = nullptr;        // shape of a refinement sweep's solve (few points left: narrow)
+    // GMRES refinement (allocated on first use): Krylov vectors V_0..V_m and
+    // preconditioned directions Z_0..Z_{m-1} (n x N L each), zero probe, the
+    // per-column Hessenberg entries, norms and coefficients
+    double2 *d_gV = nullptr, *d_gZ = nullptr, *d_zeroU = nullptr, *d_gH = nullptr, *d_gy = nullptr;
+    double *d_gnorm = nullptr;
+    size_t gmres_bytes = 0;
     bool solve2 = false;              // streaming band solve possible (block permutations allocated)
     bool use_solve2 = false;          // streaming band solve in use (autotuned or solve2)
     bool cluster_lu = true;           // band LU by a cluster of two CTAs per point
@@ -144,6 +150,8 @@ struct Handle {
     rsrr_status autotune(cudaStream_t s);
     void drop_graph();
     rsrr_status sample_band(int p0, int np, cudaStream_t s);
+    // GMRES refinement cycles of points p0 .. p0+np-1 (mixed band path)
+    rsrr_status refine_gmres(int p0, int np, const DevProblem &dq, cudaStream_t s);
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);
     // a refinement sweep's complex64 solve: streaming solve in the wide shape
     // while many points are left, in the narrow one when few are (chosen on

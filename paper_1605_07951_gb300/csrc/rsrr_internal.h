@@ -138,6 +138,19 @@ cudaError_t launch_band_solve2_c128(const double2 *ab, const int32_t *bperm, con
                                     double2 *B, const BandGeom &g, int N, int n, int L,
                                     const int32_t *skip, cudaStream_t s);
 
+// ---- column kernels of the GMRES refinement (refine.cu); column c belongs to
+// point c / L, columns of points with done set are skipped
+cudaError_t rf_norm(const double2 *W, int64_t n, int ncols, int L, const int32_t *done, double *out,
+                    cudaStream_t s);
+cudaError_t rf_dot(const double2 *V, const double2 *W, int64_t n, int ncols, int L, const int32_t *done,
+                   double2 *h, cudaStream_t s);
+cudaError_t rf_axpy(double2 *W, const double2 *V, const double2 *h, double sgn, int64_t n, int ncols, int L,
+                    const int32_t *done, cudaStream_t s);
+cudaError_t rf_scale(double2 *V, const double2 *W, const double *den, int64_t n, int ncols, int L,
+                     const int32_t *done, cudaStream_t s);
+cudaError_t rf_update(double2 *X, const double2 *Z, int64_t zstride, const double2 *y, int m, int64_t n,
+                      int ncols, int L, const int32_t *done, cudaStream_t s);
+
 // ---- CUDA events recorded in pairs around launches (grown on demand; api.cu)
 struct EventPool {
     std::vector<cudaEvent_t> ev;

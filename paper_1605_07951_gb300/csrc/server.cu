@@ -46,6 +46,7 @@ struct Request {
     std::string error;
     int32_t count = 0, nbar = 0, k = 0, sweeps = 0;
     double gmax = 0.0, max_eta = 0.0;
+    double t_sample = 0.0, t_project = 0.0, t_solve = 0.0;  // wall seconds of the stages
     std::vector<rsrr_c128> lam, V;
     std::vector<double> res;
     bool holds_budget = false;
@@ -102,19 +103,29 @@ struct Server {
             if (e == cudaSuccess) e = launch_colmax(h->d_umax, h->d_U, (int)h->n, h->L, s);
             if (e != cudaSuccess) st = h->fail(RSRR_ECUDA, "probe upload", e);
         }
+        const double ta = now();
         if (st == RSRR_OK) st = h->sample(s);
         if (st == RSRR_OK) {
             h->sampled = true;
             cudaError_t e = cudaStreamSynchronize(s);
             st = e == cudaSuccess ? h->read_outcome() : h->fail(RSRR_ECUDA, "sample", e);
         }
+        const double tb = now();
         if (st == RSRR_OK) {
             st = h->project(s);
             h->projected = st == RSRR_OK;
+            if (st == RSRR_OK) {
+                cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) st = h->fail(RSRR_ECUDA, "project", e);
+            }
         }
+        const double tc = now();
+        r->t_sample = tb - ta;
+        r->t_project = tc - tb;
         if (st == RSRR_OK) {
             rsrr_result res = {};
             st = h->solve(&res);
+            r->t_solve = now() - tc;
             if (st >= 0) {
                 r->count = res.count;
                 r->nbar = res.nbar;
@@ -320,6 +331,9 @@ rsrr_status rsrr_server_wait(rsrr_server_t *server, int64_t id, double timeout_s
     out->t_submit = r->t_submit;
     out->t_admit = r->t_admit;
     out->t_done = r->t_done;
+    out->t_sample = r->t_sample;
+    out->t_project = r->t_project;
+    out->t_solve = r->t_solve;
     out->device_bytes = r->bytes;
     out->n = r->n;
     out->lam = r->lam.data();

@@ -29,6 +29,7 @@ RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7
  RSRR_F_CALLBACK) = range(8)
 RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS, RSRR_REGION_INTERVAL = 0, 1, 2
 RSRR_METHOD_RSRR, RSRR_METHOD_SSRR_M, RSRR_METHOD_SS_RI = 0, 1, 2
+RSRR_REFINE_IR, RSRR_REFINE_GMRES = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI, RSRR_GEMM_OZAKI_MMA = 0, 1, 2, 3
 (RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU, RSRR_FLAG_INJECT_TIMEOUT, RSRR_FLAG_SIMT_DENSE_UPDATE,
@@ -75,7 +76,7 @@ class rsrr_opts(C.Structure):
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
                 ("host_threads", C.c_int32), ("timing", C.c_int32), ("gemm", C.c_int32),
                 ("flags", C.c_int32), ("seed", C.c_uint64), ("mem_budget_bytes", C.c_int64),
-                ("method", C.c_int32), ("K", C.c_int32)]
+                ("method", C.c_int32), ("K", C.c_int32), ("refine", C.c_int32), ("gmres_m", C.c_int32)]
 
 
 class rsrr_stats(C.Structure):
@@ -104,7 +105,8 @@ class rsrr_reply(C.Structure):
     _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("count", C.c_int32),
                 ("nbar", C.c_int32), ("k", C.c_int32), ("refine_sweeps", C.c_int32),
                 ("gmax", C.c_double), ("max_eta", C.c_double), ("t_submit", C.c_double),
-                ("t_admit", C.c_double), ("t_done", C.c_double), ("device_bytes", C.c_size_t),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("t_sample", C.c_double),
+                ("t_project", C.c_double), ("t_solve", C.c_double), ("device_bytes", C.c_size_t),
                 ("n", C.c_int64), ("lam", C.POINTER(rsrr_c128)), ("res", C.POINTER(C.c_double)),
                 ("V", C.POINTER(rsrr_c128)), ("error", C.c_char_p)]
 
@@ -377,6 +379,7 @@ class Server:
         return dict(id=r.id, status=r.status, count=cnt, nbar=r.nbar, k=r.k,
                     refine_sweeps=r.refine_sweeps, gmax=r.gmax, max_eta=r.max_eta,
                     t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done,
+                    t_sample=r.t_sample, t_project=r.t_project, t_solve=r.t_solve,
                     device_bytes=r.device_bytes, lam=lam, res=res, V=V,
                     error=(r.error or b"").decode())
 

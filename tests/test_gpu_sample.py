@@ -227,3 +227,36 @@ def test_narrow_late_sweeps_give_the_wide_samples_bitwise(rs):
     assert a["stats"]["refine_sweeps"] == b["stats"]["refine_sweeps"] >= 2
     assert np.array_equal(a["S"], b["S"])
     compare(p, a, rel_tol=1e-6, eta_tol=ETA_TOL)
+
+
+@pytest.mark.parametrize("name,make", [("grid_g48", lambda: W.rational_grid(g=48, N=64, L=16)),
+                                       ("random_banded", lambda: W.random_banded(n=700, kl=9, ku=6, N=8, L=5))])
+def test_gmres_refinement_reaches_the_oracle(rs, name, make):
+    """RSRR_REFINE_GMRES: right-preconditioned GMRES cycles on the complex64
+    LU reach the same backward error as plain refinement, in fewer cycles
+    than plain refinement needs sweeps, and the samples agree with the oracle."""
+    p = make()
+    ir = run(rs, p, rs.RSRR_PREC_MIXED)
+    gm = run(rs, p, rs.RSRR_PREC_MIXED, refine=rs.RSRR_REFINE_GMRES, gmres_m=3)
+    assert gm["status"] == rs.RSRR_OK
+    assert gm["stats"]["refine_sweeps"] <= ir["stats"]["refine_sweeps"]
+    compare(p, gm, rel_tol=1e-6, eta_tol=ETA_TOL)
+
+
+def test_gmres_refinement_reaches_a_tight_target_near_eigenvalues(rs):
+    """Points close to eigenvalues (the second stage of two-stage sampling):
+    GMRES refinement reaches eta <= 1e-13."""
+    p = W.diag_rational(N=10)
+    s = rs.Solver(p, rs.default_opts(NQ=256, res_tol=1e-2))
+    s.sample()
+    s.check()
+    s.project()
+    lam1 = s.solve()["lam"]
+    s.close()
+    q = W.diag_rational(N=len(lam1))
+    q.region = W.Region(p.region.center, p.region.a, p.region.b, kind="points", points=lam1)
+    out = run(rs, q, rs.RSRR_PREC_MIXED, refine=rs.RSRR_REFINE_GMRES, gmres_m=4, eta_tol=1e-13,
+              max_refine=6)
+    assert out["status"] == rs.RSRR_OK
+    assert out["eta"].max() <= 1e-13
+    compare(q, out, rel_tol=1e-3, eta_tol=1e-13)
