@@ -380,6 +380,19 @@ rsrr_status rsrr_sample(rsrr_t *h, void *stream);
  * ECUDA; the outcome of the new points' sampling is reported by rsrr_check. */
 rsrr_status rsrr_add_points(rsrr_t *h, const rsrr_c128 *z_new, int32_t count, void *stream);
 
+/* rsrr_sample for `count` band-path handles (sparse kind) of uneven sizes at
+ * once, asynchronously on `stream`: each handle's assembly, then ONE
+ * persistent grouped band LU over every sampling point of every handle (its
+ * CTAs take (handle, point) tasks from a device queue, longest first; one
+ * launch for the complex64 handles and one for the complex128 ones), then
+ * each handle's solves and refinement.  The factors are bitwise those of the
+ * one-CTA-per-point LU (RSRR_FLAG_ONE_CTA_LU), so each handle's samples are
+ * those of its own rsrr_sample with that flag.  Check each handle's outcome
+ * with rsrr_check.  The task table is allocated (cudaMallocAsync) and freed
+ * on `stream`.  Errors: EINVAL (no handles, a dense handle, a handle twice),
+ * ENOMEM, ECUDA (message in rsrr_last_error(NULL)) or a handle's own error. */
+rsrr_status rsrr_sample_batch(rsrr_t *const *handles, int32_t count, void *stream);
+
 /* Waits for `stream` and reports the outcome of the last rsrr_sample:
  * OK, ESINGULAR (a zero pivot; stats.singular_point names the point) or
  * ENOCONV (some column above eta_tol after max_refine sweeps). */

@@ -583,6 +583,90 @@ rsrr_status rsrr_sample(rsrr_t *hh, void *stream) {
     return st;
 }
 
+// Batched sampling of several band-path handles: each handle's assembly,
+// then one persistent grouped band LU over every point of every handle
+// (complex64 handles in one launch, complex128 ones in another; tasks
+// ordered longest first), then each handle's solves and refinement.
+rsrr_status rsrr_sample_batch(rsrr_t *const *handles, int32_t count, void *stream) {
+    if (!handles || count < 1) {
+        rsrr::thread_error() = "rsrr_sample_batch: no handles";
+        return RSRR_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Handle *> hs_(count);
+    for (int i = 0; i < count; ++i) {
+        hs_[i] = reinterpret_cast<Handle *>(handles[i]);
+        if (!hs_[i] || hs_[i]->dense) {
+            rsrr::thread_error() = "rsrr_sample_batch: every handle must be a band-path (sparse kind) handle";
+            return RSRR_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (hs_[j] == hs_[i]) {
+                rsrr::thread_error() = "rsrr_sample_batch: a handle appears twice";
+                return RSRR_EINVAL;
+            }
+    }
+    for (Handle *h : hs_) {
+        rsrr_status st = h->sample_band(0, h->N, s, 1);
+        if (st != RSRR_OK) return st;
+    }
+    // the tasks: one per point, longest first (about n kl (kl + ku) each)
+    std::vector<rsrr::LuTask> t64, t128;
+    int kl64 = 0, kl128 = 0;
+    for (Handle *h : hs_) {
+        const bool mixed = h->opts.precision == RSRR_PREC_MIXED;
+        const size_t ab_pt = (size_t)h->geom.ldab * h->n;
+        const size_t dv_pt = (((size_t)h->n + h->geom.nb - 1) / h->geom.nb) * 2 * h->geom.nb * h->geom.nb;
+        for (int pt = 0; pt < h->N; ++pt) {
+            rsrr::LuTask t;
+            t.ab = mixed ? (void *)(h->d_ab32 + pt * ab_pt) : (void *)(h->d_ab64 + pt * ab_pt);
+            t.dinv = mixed ? (void *)(h->d_dinv32 + pt * dv_pt) : (void *)(h->d_dinv64 + pt * dv_pt);
+            t.piv = h->d_piv + (size_t)pt * h->n;
+            t.info = h->d_info + pt;
+            t.n = (int)h->n;
+            t.kl = h->kl;
+            t.ku = h->ku;
+            t.ldab = h->geom.ldab;
+            (mixed ? t64 : t128).push_back(t);
+            (mixed ? kl64 : kl128) = std::max(mixed ? kl64 : kl128, h->kl);
+        }
+    }
+    auto work = [](const rsrr::LuTask &t) { return (double)t.n * t.kl * (double)(t.kl + t.ku + 1); };
+    auto by_work = [&](const rsrr::LuTask &a, const rsrr::LuTask &b) { return work(a) > work(b); };
+    std::stable_sort(t64.begin(), t64.end(), by_work);
+    std::stable_sort(t128.begin(), t128.end(), by_work);
+    const size_t tb = sizeof(rsrr::LuTask) * (t64.size() + t128.size());
+    void *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, tb + 256, s);
+    if (e != cudaSuccess) {
+        rsrr::thread_error() = std::string("rsrr_sample_batch: task table: ") + cudaGetErrorString(e);
+        return RSRR_ENOMEM;
+    }
+    rsrr::LuTask *dt = static_cast<rsrr::LuTask *>(buf);
+    int *next = reinterpret_cast<int *>(static_cast<char *>(buf) + tb);
+    std::vector<rsrr::LuTask> all(t64);
+    all.insert(all.end(), t128.begin(), t128.end());
+    e = cudaMemcpyAsync(dt, all.data(), tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess && !t64.empty()) e = rsrr::launch_band_lu_grouped_c64(dt, (int)t64.size(), kl64, next, s);
+    if (e == cudaSuccess && !t128.empty())
+        e = rsrr::launch_band_lu_grouped_c128(dt + t64.size(), (int)t128.size(), kl128, next + 1, s);
+    cudaError_t e2 = cudaFreeAsync(buf, s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        rsrr::thread_error() = std::string("rsrr_sample_batch: grouped band LU: ") + cudaGetErrorString(e);
+        return RSRR_ECUDA;
+    }
+    hs_[0]->launches += (t64.empty() ? 0 : 1) + (t128.empty() ? 0 : 1);
+    for (Handle *h : hs_) {
+        rsrr_status st = h->sample_band(0, h->N, s, 2);
+        if (st != RSRR_OK) return st;
+        h->sampled = true;
+        h->projected = false;
+    }
+    return RSRR_OK;
+}
+
 rsrr_status rsrr_add_points(rsrr_t *hh, const rsrr_c128 *z_new, int32_t count, void *stream) {
     Handle *h = reinterpret_cast<Handle *>(hh);
     if (!h || !z_new) return RSRR_EINVAL;
@@ -1082,7 +1166,7 @@ rsrr_status Handle::sample_graph(cudaStream_t s) {
 // Step 2 of RSRR on the GPU for sampling points p0 .. p0+np-1, asynchronously
 // on stream s (every point for rsrr_sample; the appended points for
 // rsrr_add_points, which leaves the others' samples untouched).
-rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
+rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
     Handle *h = this;
     const int nn = (int)n;
     const int64_t per_pt = (int64_t)n * L;
@@ -1098,20 +1182,25 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
     double *rmax = d_rmax + (size_t)p0 * L, *xmax = d_xmax + (size_t)p0 * L;
     double2 *X = d_X + p0 * per_pt;
     rsrr_status ms;
-    CK(cudaMemsetAsync(d_tmo, 0, sizeof(unsigned int), s), "memset");
-    if ((ms = mark(0, s)) != RSRR_OK) return ms;
-    CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
-    if (opts.flags & RSRR_FLAG_INJECT_TIMEOUT) {
-        CK(launch_wait_check(4096, d_tmo, s), "injected wait");
-        launches += 1;
+    if (phase != 2) {
+        CK(cudaMemsetAsync(d_tmo, 0, sizeof(unsigned int), s), "memset");
+        if ((ms = mark(0, s)) != RSRR_OK) return ms;
+        CK(cudaMemsetAsync(d_sweep_flags, 0, sizeof(int32_t) * (opts.max_refine + 2), s), "memset");
+        if (opts.flags & RSRR_FLAG_INJECT_TIMEOUT) {
+            CK(launch_wait_check(4096, d_tmo, s), "injected wait");
+            launches += 1;
+        }
+        CK(launch_tnorm(tnorm, dq, s), "tnorm");
+        if (opts.precision == RSRR_PREC_MIXED) CK(launch_assemble<float2>(d_ab32 + p0 * ab_pt, geom, dq, s), "assemble");
+        else CK(launch_assemble<double2>(d_ab64 + p0 * ab_pt, geom, dq, s), "assemble");
+        if ((ms = mark(1, s)) != RSRR_OK) return ms;
+        if (phase == 1) return RSRR_OK;  // the caller factors (grouped LU of rsrr_sample_batch)
     }
-    CK(launch_tnorm(tnorm, dq, s), "tnorm");
     if (opts.precision == RSRR_PREC_MIXED) {
         float2 *ab = d_ab32 + p0 * ab_pt, *D = d_D + p0 * per_pt;
         double2 *R = d_R + p0 * per_pt;
-        CK(launch_assemble<float2>(ab, geom, dq, s), "assemble");
-        if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c64(ab, piv, info, d_dinv32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+        if (phase == 0)
+            CK(launch_band_lu_c64(ab, piv, info, d_dinv32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (use_solve2) {
             CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
@@ -1137,9 +1226,8 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s) {
         }
     } else {
         double2 *ab = d_ab64 + p0 * ab_pt;
-        CK(launch_assemble<double2>(ab, geom, dq, s), "assemble");
-        if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_band_lu_c128(ab, piv, info, d_dinv64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+        if (phase == 0)
+            CK(launch_band_lu_c128(ab, piv, info, d_dinv64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (use_solve2) {
             CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;

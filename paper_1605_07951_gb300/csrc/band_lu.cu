@@ -12,6 +12,7 @@
 // Global reads of the factor, pivots and block inverses bypass L1 (__ldcg):
 // the two CTAs of a cluster sit on different SMs and read what the other
 // wrote, and L1 is not coherent between SMs.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -400,6 +401,63 @@ band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     if (rank == 0 && threadIdx.x == 0) info_all[pt] = info;
 }
 
+// Many problems of uneven size in one persistent launch: every CTA takes
+// the next (problem, point) task from a device counter (the host orders the
+// tasks longest first) and factors it exactly as band_lu_kernel would, so the
+// factors are bitwise those of the one-CTA kernel.  The instance covers the
+// widest lower bandwidth of the batch (kl <= 32 RA).
+template <typename C, int NB, int RA, int CB, int TH>
+__global__ void __launch_bounds__(TH, 1)
+band_lu_grouped_kernel(const LuTask *__restrict__ tasks, int ntasks, int *__restrict__ next) {
+    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LuSm<C, NB, RA, CB, TH> sm(smem_raw);
+    __shared__ int s_task;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(next, 1);
+        __syncthreads();
+        const int t = s_task;
+        __syncthreads();
+        if (t >= ntasks) break;
+        const LuTask tk = tasks[t];
+        C *ab = static_cast<C *>(tk.ab);
+        C *dinv = static_cast<C *>(tk.dinv);
+        const int n = tk.n, kl = tk.kl, KV = tk.kl + tk.ku, ldab = tk.ldab;
+        for (int q = threadIdx.x; q < NB * PRA; q += TH) sm.P[q] = czero<C>();
+        int info = 0;
+        __syncthreads();
+        for (int j0 = 0; j0 < n; j0 += NB) {
+            const int jb = min(NB, n - j0);
+            lu_panel<C, NB, RA, CB, TH>(ab, tk.piv, dinv, n, kl, KV, ldab, j0, sm, info);
+            lu_update<C, NB, RA, CB, TH>(ab, n, kl, KV, ldab, j0, j0 + jb, min(n, j0 + jb + KV), sm);
+        }
+        if (threadIdx.x == 0) *tk.info = info;
+        __syncthreads();
+    }
+}
+
+template <typename C, int NB, int RA, int CB, int TH>
+static cudaError_t lu_grouped(const LuTask *tasks, int ntasks, int *next, cudaStream_t s) {
+    const size_t smem = LuSm<C, NB, RA, CB, TH>::bytes();
+    cudaError_t e = cudaFuncSetAttribute(band_lu_grouped_kernel<C, NB, RA, CB, TH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    band_lu_grouped_kernel<C, NB, RA, CB, TH><<<std::max(1, std::min(ntasks, sms)), TH, smem, s>>>(tasks, ntasks,
+                                                                                                   next);
+    return cudaGetLastError();
+}
+
+template <typename C, int NB, int CB512>
+static cudaError_t grouped_by_kl(const LuTask *tasks, int ntasks, int kl_max, int *next, cudaStream_t s) {
+    constexpr int CB256 = 2 * CB512;
+    if (kl_max <= 32) return lu_grouped<C, NB, 1, CB256, 256>(tasks, ntasks, next, s);
+    if (kl_max <= 128) return lu_grouped<C, NB, 4, CB256, 256>(tasks, ntasks, next, s);
+    if (kl_max <= 224) return lu_grouped<C, NB, 7, CB256, 256>(tasks, ntasks, next, s);
+    return lu_grouped<C, NB, 15, CB512, 512>(tasks, ntasks, next, s);
+}
+
 template <typename C, int NB, int RA, int CB, int TH>
 static cudaError_t lu_dispatch(C *ab, int32_t *piv, int32_t *info, C *dinv, const BandGeom &g,
                                int N, int n, bool cluster, cudaStream_t s) {
@@ -435,12 +493,20 @@ static cudaError_t lu_by_kl(C *ab, int32_t *piv, int32_t *info, C *dinv, const B
 }
 
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 64
+cudaError_t launch_band_lu_grouped_c64(const LuTask *tasks, int ntasks, int kl_max, int *next, cudaStream_t s) {
+    if (kl_max > KL_MAX) return cudaErrorInvalidValue;
+    return grouped_by_kl<float2, NB_C64, 4>(tasks, ntasks, kl_max, next, s);
+}
 cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *dinv,
                                const BandGeom &g, int N, int n, cudaStream_t s, bool cluster) {
     return lu_by_kl<float2, NB_C64, 4>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
 #endif
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 128
+cudaError_t launch_band_lu_grouped_c128(const LuTask *tasks, int ntasks, int kl_max, int *next, cudaStream_t s) {
+    if (kl_max > KL_MAX) return cudaErrorInvalidValue;
+    return grouped_by_kl<double2, NB_C128, 1>(tasks, ntasks, kl_max, next, s);
+}
 cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, double2 *dinv,
                                 const BandGeom &g, int N, int n, cudaStream_t s, bool cluster) {
     return lu_by_kl<double2, NB_C128, 1>(ab, piv, info, dinv, g, N, n, cluster, s);

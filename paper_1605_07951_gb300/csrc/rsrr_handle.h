@@ -149,7 +149,9 @@ struct Handle {
     rsrr_status sample_graph(cudaStream_t s);
     rsrr_status autotune(cudaStream_t s);
     void drop_graph();
-    rsrr_status sample_band(int p0, int np, cudaStream_t s);
+    // phase 0: everything; 1: up to the assembly (the caller factors); 2: from
+    // after the LU (the caller factored)
+    rsrr_status sample_band(int p0, int np, cudaStream_t s, int phase = 0);
     // GMRES refinement cycles of points p0 .. p0+np-1 (mixed band path)
     rsrr_status refine_gmres(int p0, int np, const DevProblem &dq, cudaStream_t s);
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);

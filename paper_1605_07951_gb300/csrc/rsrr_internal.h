@@ -57,6 +57,18 @@ cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *
                                const BandGeom &g, int N, int n, cudaStream_t s, bool cluster = false);
 cudaError_t launch_band_lu_c128(double2 *ab, int32_t *piv, int32_t *info, double2 *dinv,
                                 const BandGeom &g, int N, int n, cudaStream_t s, bool cluster = false);
+// one point of one problem for the grouped band LU (ab, dinv: complex64 or
+// complex128 storage of that point)
+struct LuTask {
+    void *ab;
+    int32_t *piv, *info;
+    void *dinv;
+    int n, kl, ku, ldab;
+};
+// persistent band LU over a task list (ordered by the caller, longest first);
+// *next is a zeroed device counter; kl_max the widest lower bandwidth
+cudaError_t launch_band_lu_grouped_c64(const LuTask *tasks, int ntasks, int kl_max, int *next, cudaStream_t s);
+cudaError_t launch_band_lu_grouped_c128(const LuTask *tasks, int ntasks, int kl_max, int *next, cudaStream_t s);
 cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const float2 *dinv,
                                   float2 *B, const BandGeom &g, int N, int n, int L,
                                   const int32_t *skip, cudaStream_t s);

@@ -137,6 +137,16 @@ rsrr_set_probe = _sig("rsrr_set_probe", C.c_int, [_h, _p, C.c_int32, _p])
 rsrr_sample = _sig("rsrr_sample", C.c_int, [_h, _p])
 rsrr_check = _sig("rsrr_check", C.c_int, [_h, _p])
 rsrr_add_points = _sig("rsrr_add_points", C.c_int, [_h, _p, C.c_int32, _p])
+rsrr_sample_batch = _sig("rsrr_sample_batch", C.c_int, [C.POINTER(_h), C.c_int32, _p])
+
+
+def sample_batch(solvers, stream=None):
+    """rsrr_sample_batch over several Solver objects (band path)."""
+    arr = (_h * len(solvers))(*[sv.h for sv in solvers])
+    st = rsrr_sample_batch(arr, len(solvers), _stream_handle(stream))
+    if st != RSRR_OK:
+        raise RSRRError(st, rsrr_last_error(None).decode())
+    return st
 rsrr_project = _sig("rsrr_project", C.c_int, [_h, _p])
 rsrr_solve = _sig("rsrr_solve", C.c_int, [_h, C.POINTER(rsrr_result)])
 rsrr_get_samples = _sig("rsrr_get_samples", C.c_int, [_h, _p, C.c_int32, _p])
