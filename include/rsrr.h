@@ -251,7 +251,9 @@ typedef struct {
     int32_t max_refine;  /* refinement sweeps, default 8 */
     double eta_tol;      /* default 1e-10 */
     double delta;        /* SVD truncation of S relative to sigma_1, paper's 1e-14 */
-    double delta_floor;  /* resolution floor of the Gram-based SVD, default 1e-12 */
+    double delta_floor;  /* resolution floor of the Gram-based SVD relative to sigma_1;
+                            <= 0 (default): the samples' accuracy -- 0.1 eta_tol
+                            for the mixed path (1e-11), 1e-12 for the FP64 path */
     double tol_gap;      /* gap test of SS-FULL, default 1e3 (Section 3.3) */
     double res_tol;      /* acceptance of an eigenpair by residual, default 1e-6 */
     int32_t NQ;          /* SS-FULL quadrature points, default 500 */

@@ -234,7 +234,7 @@ void rsrr_opts_default(rsrr_opts *o) {
     o->max_refine = 8;
     o->eta_tol = 1e-10;
     o->delta = 1e-14;
-    o->delta_floor = 1e-12;
+    o->delta_floor = 0.0;  // automatic: 0.1 eta_tol (mixed), 1e-12 (FP64)
     o->tol_gap = 1e3;
     o->res_tol = 1e-6;
     o->NQ = 500;
