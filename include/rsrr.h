@@ -222,8 +222,22 @@ enum {
     RSRR_FLAG_SIMT_DENSE_UPDATE = 8,
     RSRR_FLAG_GRAPH = 16,
     RSRR_FLAG_AUTOTUNE = 32,
-    RSRR_FLAG_WIDE_SOLVE_ONLY = 64
+    RSRR_FLAG_WIDE_SOLVE_ONLY = 64,
+    RSRR_FLAG_REAL = 128
 };
+/* RSRR_FLAG_REAL: real arithmetic for a real NEP at real sampling points
+ * (Sections 3.3 and 5.1: real points, e.g. the Chebyshev points of an
+ * RSRR_REGION_INTERVAL, keep T(z_j) real and halve the time and memory of
+ * the solves).  Requires the sparse kind with real values, real sampling
+ * points and real f_i there (rsrr_create checks all three, EINVAL
+ * otherwise).  The band factors, block inverses and corrections are real
+ * (float for the mixed path, double for the FP64 path); the probe U is real
+ * (imaginary parts of a given U are dropped); the samples S are stored as
+ * complex numbers with zero imaginary parts, so the FP64 residuals, the
+ * projection and rsrr_get_samples are those of the complex path.
+ * RSRR_REFINE_GMRES with it is refused by rsrr_create (EINVAL), as are
+ * rsrr_add_points and rsrr_sample_batch on such a handle; RSRR_FLAG_AUTOTUNE
+ * is ignored. */
 /* RSRR_FLAG_WIDE_SOLVE_ONLY: the refinement sweeps' streaming solves always
  * take 16 right-hand sides per CTA.  By default a sweep in which few points
  * are still above eta_tol (the points next to an eigenvalue converge last)
@@ -252,8 +266,10 @@ typedef struct {
     double eta_tol;      /* default 1e-10 */
     double delta;        /* SVD truncation of S relative to sigma_1, paper's 1e-14 */
     double delta_floor;  /* resolution floor of the Gram-based SVD relative to sigma_1;
-                            <= 0 (default): the samples' accuracy -- 0.1 eta_tol
-                            for the mixed path (1e-11), 1e-12 for the FP64 path */
+                            <= 0 (default): for RSRR the samples' accuracy --
+                            0.1 eta_tol for the mixed path (1e-11), 1e-12 for
+                            the FP64 path; 1e-12 for SSRR-M, whose high moments
+                            carry eigen-directions far below sigma_1 of M */
     double tol_gap;      /* gap test of SS-FULL, default 1e3 (Section 3.3) */
     double res_tol;      /* acceptance of an eigenpair by residual, default 1e-6 */
     int32_t NQ;          /* SS-FULL quadrature points, default 500 */

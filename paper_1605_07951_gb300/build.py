@@ -20,6 +20,8 @@ UNITS = [
     ("band.cu", [], "band.o"),
     ("band_lu.cu", ["-DRSRR_LU_ONLY=64"], "band_lu64.o"),
     ("band_lu.cu", ["-DRSRR_LU_ONLY=128"], "band_lu128.o"),
+    ("band_lu.cu", ["-DRSRR_LU_ONLY=32"], "band_lu_r32.o"),
+    ("band_lu.cu", ["-DRSRR_LU_ONLY=65"], "band_lu_r64.o"),
     ("proj.cu", [], "proj.o"),
     ("ssfull_host.cpp", ["-x", "cu", "-Xcompiler", "-fcx-fortran-rules"], "ssfull_host.o"),
     ("noalloc.cu", [], "noalloc.o"),

@@ -420,6 +420,8 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
         return create_fail("rsrr_create: unknown NEP kind");
     rsrr_status cst = check_common(region, opts, N);
     if (cst != RSRR_OK) return cst;
+    if (opts && (opts->flags & RSRR_FLAG_REAL) && nep->kind != RSRR_NEP_SPARSE)
+        return create_fail("rsrr_create: RSRR_FLAG_REAL needs the sparse kind");
     if (nep->kind == RSRR_NEP_HELMHOLTZ) return rsrr::prepare_dense(nep, region, N, L, opts, out);
     if (nep->m < 1 || nep->m > RSRR_MAX_TERMS) return create_fail("rsrr_create: m out of range");
     if ((cst = check_fns(nep)) != RSRR_OK) return cst;
@@ -530,6 +532,23 @@ rsrr_status prepare(const rsrr_nep *nep, const rsrr_region *region, int32_t N, i
         delete h;
         return st;
     }
+    if (h->opts.flags & RSRR_FLAG_REAL) {
+        // real arithmetic: T(z_j) = sum_i f_i(z_j) A_i real at every point
+        bool ok = true;
+        for (int imag : h->fn_imag) ok = ok && !imag;
+        for (const cplx &zj : h->z) ok = ok && zj.imag() == 0.0;
+        for (const double2 &c : h->h_coef) ok = ok && c.y == 0.0;
+        if (!ok) {
+            delete h;
+            return create_fail("rsrr_create: RSRR_FLAG_REAL needs real values, real sampling points "
+                               "and real f_i there");
+        }
+        if (h->opts.refine == RSRR_REFINE_GMRES) {
+            delete h;
+            return create_fail("rsrr_create: RSRR_FLAG_REAL does not combine with RSRR_REFINE_GMRES");
+        }
+        h->real = true;
+    }
     *out = h;
     return RSRR_OK;
 }
@@ -569,6 +588,7 @@ rsrr_status rsrr_set_probe(rsrr_t *hh, const rsrr_c128 *U, int32_t on_device, vo
     } else {
         CK(cudaMemcpy(h->d_U, U, bytes, cudaMemcpyHostToDevice), "set_probe copy");
     }
+    if (h->real) CK(rsrr::launch_real_part(h->d_U, (int64_t)h->n * h->L, s), "set_probe real part");
     CK(rsrr::launch_colmax(h->d_umax, h->d_U, (int)h->n, h->L, s), "set_probe colmax");
     h->sampled = false;
     h->projected = false;
@@ -596,8 +616,8 @@ rsrr_status rsrr_sample_batch(rsrr_t *const *handles, int32_t count, void *strea
     std::vector<Handle *> hs_(count);
     for (int i = 0; i < count; ++i) {
         hs_[i] = reinterpret_cast<Handle *>(handles[i]);
-        if (!hs_[i] || hs_[i]->dense) {
-            rsrr::thread_error() = "rsrr_sample_batch: every handle must be a band-path (sparse kind) handle";
+        if (!hs_[i] || hs_[i]->dense || hs_[i]->real) {
+            rsrr::thread_error() = "rsrr_sample_batch: every handle must be a complex band-path (sparse kind) handle";
             return RSRR_EINVAL;
         }
         for (int j = 0; j < i; ++j)
@@ -809,8 +829,9 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     CK(alloc(&d_tmo, 1), "alloc");
     const size_t band = (size_t)geom.ldab * n * N;
     {
-        const size_t smem2 = opts.precision == RSRR_PREC_MIXED ? band_solve2_smem_c64(geom)
-                                                               : band_solve2_smem_c128(geom);
+        const bool mx = opts.precision == RSRR_PREC_MIXED;
+        const size_t smem2 = real ? (mx ? band_solve2_smem_r32(geom) : band_solve2_smem_r64(geom))
+                                  : (mx ? band_solve2_smem_c64(geom) : band_solve2_smem_c128(geom));
         solve2 = !(opts.flags & RSRR_FLAG_PLAIN_SOLVE) && smem2 <= 227 * 1024 &&
                  geom.kl + geom.nb <= KL_MAX + 32;
         use_solve2 = solve2;
@@ -821,7 +842,17 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
             CK(alloc(&d_gate, 1), "alloc");
         }
     }
-    if (opts.precision == RSRR_PREC_MIXED) {
+    const size_t dinv_n = (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb;
+    if (real && opts.precision == RSRR_PREC_MIXED) {
+        CK(alloc(&d_abr32, band), "alloc band factors (float)");
+        CK(alloc(&d_dinvr32, dinv_n), "alloc block inverses");
+        CK(alloc(&d_R, nL * N), "alloc residual");
+        CK(alloc(&d_Dr32, nL * N), "alloc correction");
+    } else if (real) {
+        CK(alloc(&d_abr64, band), "alloc band factors (double)");
+        CK(alloc(&d_dinvr64, dinv_n), "alloc block inverses");
+        CK(alloc(&d_Dr64, nL * N), "alloc real solve buffer");
+    } else if (opts.precision == RSRR_PREC_MIXED) {
         CK(alloc(&d_ab32, band), "alloc band factors (complex64)");
         CK(alloc(&d_dinv32, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
            "alloc block inverses");
@@ -849,6 +880,7 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
         default_probe(U, nL, seed);
         CK(cudaMemcpyAsync(d_U, U.data(), sizeof(double2) * nL, H2D, hs), "upload");
     }
+    if (real) CK(launch_real_part(d_U, (int64_t)nL, hs), "probe real part");
     CK(launch_colmax(d_umax, d_U, (int)n, L, hs), "colmax");
     CK(wait(), "create sync");
     dp.n = n; dp.nnz = nnz; dp.N = N; dp.L = L; dp.m = m;
@@ -886,6 +918,24 @@ cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, int p0,
                                             static_cast<double2 *>(B), geom, np, nn, L, skip, s)
                   : launch_band_solve_c128(d_ab64 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv64 + p0 * dv_pt,
                                            static_cast<double2 *>(B), geom, np, nn, L, skip, s);
+}
+
+// the real path's X = (P L U)^{-1} X (float B for the mixed path, double for
+// the FP64 path), same choice of kernels as band_solve
+cudaError_t Handle::real_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s) {
+    const int nn = (int)n;
+    const size_t ab_pt = (size_t)geom.ldab * n;
+    const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
+    const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
+    if (mixed)
+        return use_solve2 ? launch_band_solve2_r32(d_abr32 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinvr32 + p0 * dv_pt,
+                                                   static_cast<float *>(B), geom, np, nn, L, skip, s)
+                          : launch_band_solve_r32(d_abr32 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinvr32 + p0 * dv_pt,
+                                                  static_cast<float *>(B), geom, np, nn, L, skip, s);
+    return use_solve2 ? launch_band_solve2_r64(d_abr64 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinvr64 + p0 * dv_pt,
+                                               static_cast<double *>(B), geom, np, nn, L, skip, s)
+                      : launch_band_solve_r64(d_abr64 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinvr64 + p0 * dv_pt,
+                                              static_cast<double *>(B), geom, np, nn, L, skip, s);
 }
 
 cudaError_t Handle::sweep_solve(float2 *B, const int32_t *skip, int p0, int np, cudaStream_t s) {
@@ -1023,7 +1073,7 @@ rsrr_status Handle::refine_gmres(int p0, int np, const DevProblem &dq, cudaStrea
 
 rsrr_status Handle::sample(cudaStream_t s) {
     if (dense) return sample_dense(0, N, s);
-    if ((opts.flags & RSRR_FLAG_AUTOTUNE) && !tuned) {
+    if ((opts.flags & RSRR_FLAG_AUTOTUNE) && !tuned && !real) {
         rsrr_status st = autotune(s);
         if (st != RSRR_OK) return st;
     }
@@ -1191,12 +1241,54 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
             launches += 1;
         }
         CK(launch_tnorm(tnorm, dq, s), "tnorm");
-        if (opts.precision == RSRR_PREC_MIXED) CK(launch_assemble<float2>(d_ab32 + p0 * ab_pt, geom, dq, s), "assemble");
+        if (real && opts.precision == RSRR_PREC_MIXED)
+            CK(launch_assemble<float>(d_abr32 + p0 * ab_pt, geom, dq, s), "assemble");
+        else if (real) CK(launch_assemble<double>(d_abr64 + p0 * ab_pt, geom, dq, s), "assemble");
+        else if (opts.precision == RSRR_PREC_MIXED)
+            CK(launch_assemble<float2>(d_ab32 + p0 * ab_pt, geom, dq, s), "assemble");
         else CK(launch_assemble<double2>(d_ab64 + p0 * ab_pt, geom, dq, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
         if (phase == 1) return RSRR_OK;  // the caller factors (grouped LU of rsrr_sample_batch)
     }
-    if (opts.precision == RSRR_PREC_MIXED) {
+    if (real && opts.precision == RSRR_PREC_MIXED) {
+        // real float factors, FP64 complex residuals (zero imaginary parts)
+        float *ab = d_abr32 + p0 * ab_pt, *D = d_Dr32 + p0 * per_pt;
+        double2 *R = d_R + p0 * per_pt;
+        CK(launch_band_lu_r32(ab, piv, info, d_dinvr32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+        if (use_solve2) {
+            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
+            launches += 1;
+        }
+        if ((ms = mark(2, s)) != RSRR_OK) return ms;
+        CK(launch_broadcast_probe_r32(D, d_U, per_pt, np, s), "probe");
+        CK(real_solve(true, D, nullptr, p0, np, s), "band solve");
+        CK(launch_widen_r32(X, D, per_pt * np, s), "widen");
+        CK(cudaMemsetAsync(done, 0, sizeof(int32_t) * np, s), "memset");
+        if ((ms = mark(3, s)) != RSRR_OK) return ms;
+        launches += 5;  // assemble, LU, probe, solve, widen
+        for (int it = 0; it < opts.max_refine; ++it) {
+            CK(launch_residual(R, X, dq, rmax, xmax, done, s), "residual");
+            CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),
+               "eta");
+            CK(launch_narrow_r32(D, R, per_pt, np, done, s), "narrow");
+            CK(real_solve(true, D, done, p0, np, s), "band solve");
+            CK(launch_update_r32(X, D, per_pt, np, done, s), "update");
+            launches += 5;
+        }
+    } else if (real) {
+        double *ab = d_abr64 + p0 * ab_pt, *D = d_Dr64 + p0 * per_pt;
+        CK(launch_band_lu_r64(ab, piv, info, d_dinvr64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+        if (use_solve2) {
+            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
+            launches += 1;
+        }
+        if ((ms = mark(2, s)) != RSRR_OK) return ms;
+        CK(launch_broadcast_probe_r64(D, d_U, per_pt, np, s), "probe");
+        CK(real_solve(false, D, nullptr, p0, np, s), "band solve");
+        CK(launch_widen_r64(X, D, per_pt * np, s), "widen");
+        if ((ms = mark(3, s)) != RSRR_OK) return ms;
+        launches += 5;  // assemble, LU, probe, solve, widen
+    } else if (opts.precision == RSRR_PREC_MIXED) {
         float2 *ab = d_ab32 + p0 * ab_pt, *D = d_D + p0 * per_pt;
         double2 *R = d_R + p0 * per_pt;
         if (phase == 0)
@@ -1284,6 +1376,7 @@ cudaError_t Handle::regrow(T **p, size_t per, int N0, int N1, bool keep) {
 rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
     Handle *h = this;
     if (!sampled) return fail(RSRR_ESTATE, "rsrr_add_points: no rsrr_sample yet");
+    if (real) return fail(RSRR_EINVAL, "rsrr_add_points: not on a RSRR_FLAG_REAL handle");
     if (count < 1) return fail(RSRR_EINVAL, "rsrr_add_points: count must be >= 1");
     for (int q = 0; q < count; ++q)
         if (!std::isfinite(znew[q].real()) || !std::isfinite(znew[q].imag()))

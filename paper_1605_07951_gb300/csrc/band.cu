@@ -22,6 +22,9 @@ namespace rsrr {
 
 RSRR_DEV void store_c(float2 *p, double2 v) { *p = to_c64(v); }
 RSRR_DEV void store_c(double2 *p, double2 v) { *p = v; }
+// real storage (real NEP at real points: the imaginary parts are zero)
+RSRR_DEV void store_c(float *p, double2 v) { *p = (float)v.x; }
+RSRR_DEV void store_c(double *p, double2 v) { *p = v.x; }
 
 // --------------------------------------------------------------------------
 // Assembly: one warp per column c of one point.  The warp first writes the
@@ -430,6 +433,45 @@ __global__ void update_kernel(double2 *__restrict__ X, const float2 *__restrict_
     }
 }
 
+// ---- real path (real NEP at real points): real factor storage, complex S
+// with zero imaginary parts (so the FP64 residual and the projection are
+// shared with the complex path)
+
+// X = (real part D, 0)
+template <typename R>
+__global__ void widen_real_kernel(double2 *__restrict__ X, const R *__restrict__ D, int64_t total) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        X[q] = make_double2((double)D[q], 0.0);
+}
+
+// D = Re R for points still refining
+__global__ void narrow_real_kernel(float *__restrict__ D, const double2 *__restrict__ R, int64_t per_pt,
+                                   const int32_t *__restrict__ skip) {
+    const int pt = blockIdx.y;
+    if (skip[pt]) return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < per_pt;
+         q += (int64_t)gridDim.x * blockDim.x)
+        D[pt * per_pt + q] = (float)R[pt * per_pt + q].x;
+}
+
+// Re X += D for points still refining
+__global__ void update_real_kernel(double2 *__restrict__ X, const float *__restrict__ D, int64_t per_pt,
+                                   const int32_t *__restrict__ skip) {
+    const int pt = blockIdx.y;
+    if (skip[pt]) return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < per_pt;
+         q += (int64_t)gridDim.x * blockDim.x)
+        X[pt * per_pt + q].x += (double)D[pt * per_pt + q];
+}
+
+// U = Re U (the real path's probe is real)
+__global__ void real_part_kernel(double2 *__restrict__ U, int64_t total) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        U[q].y = 0.0;
+}
+
 // ==========================================================================
 // launchers
 // ==========================================================================
@@ -554,6 +596,51 @@ cudaError_t launch_update(double2 *X, const float2 *D, int64_t per_pt, int N, co
     return cudaGetLastError();
 }
 
+cudaError_t launch_broadcast_probe_r32(float *D, const double2 *U, int64_t nL, int N, cudaStream_t s) {
+    broadcast_probe_kernel<float><<<grid_for(nL * N, 256), 256, 0, s>>>(D, U, nL, N);
+    return cudaGetLastError();
+}
+cudaError_t launch_broadcast_probe_r64(double *D, const double2 *U, int64_t nL, int N, cudaStream_t s) {
+    broadcast_probe_kernel<double><<<grid_for(nL * N, 256), 256, 0, s>>>(D, U, nL, N);
+    return cudaGetLastError();
+}
+cudaError_t launch_widen_r32(double2 *X, const float *D, int64_t total, cudaStream_t s) {
+    widen_real_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(X, D, total);
+    return cudaGetLastError();
+}
+cudaError_t launch_widen_r64(double2 *X, const double *D, int64_t total, cudaStream_t s) {
+    widen_real_kernel<double><<<grid_for(total, 256), 256, 0, s>>>(X, D, total);
+    return cudaGetLastError();
+}
+cudaError_t launch_narrow_r32(float *D, const double2 *R, int64_t per_pt, int N, const int32_t *skip,
+                              cudaStream_t s) {
+    narrow_real_kernel<<<dim3(grid_for(per_pt, 256, 64), N), 256, 0, s>>>(D, R, per_pt, skip);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_r32(double2 *X, const float *D, int64_t per_pt, int N, const int32_t *skip,
+                              cudaStream_t s) {
+    update_real_kernel<<<dim3(grid_for(per_pt, 256, 64), N), 256, 0, s>>>(X, D, per_pt, skip);
+    return cudaGetLastError();
+}
+cudaError_t launch_real_part(double2 *U, int64_t total, cudaStream_t s) {
+    real_part_kernel<<<grid_for(total, 256), 256, 0, s>>>(U, total);
+    return cudaGetLastError();
+}
+cudaError_t launch_band_solve_r32(const float *ab, const int32_t *piv, const float *dinv, float *B,
+                                  const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s) {
+    if (solve_smem<float, NB_C64, 16>(g) <= 200 * 1024)
+        return solve_dispatch<float, NB_C64, 16>(ab, piv, dinv, B, g, N, n, L, skip, s);
+    return solve_dispatch<float, NB_C64, 8>(ab, piv, dinv, B, g, N, n, L, skip, s);
+}
+cudaError_t launch_band_solve_r64(const double *ab, const int32_t *piv, const double *dinv, double *B,
+                                  const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s) {
+    if (solve_smem<double, NB_C128, 8>(g) <= 200 * 1024)
+        return solve_dispatch<double, NB_C128, 8>(ab, piv, dinv, B, g, N, n, L, skip, s);
+    return solve_dispatch<double, NB_C128, 4>(ab, piv, dinv, B, g, N, n, L, skip, s);
+}
+
+template cudaError_t launch_assemble<float>(float *, const BandGeom &, const DevProblem &, cudaStream_t);
+template cudaError_t launch_assemble<double>(double *, const BandGeom &, const DevProblem &, cudaStream_t);
 template cudaError_t launch_assemble<float2>(float2 *, const BandGeom &, const DevProblem &,
                                              cudaStream_t);
 template cudaError_t launch_assemble<double2>(double2 *, const BandGeom &, const DevProblem &,

@@ -502,6 +502,19 @@ cudaError_t launch_band_lu_c64(float2 *ab, int32_t *piv, int32_t *info, float2 *
     return lu_by_kl<float2, NB_C64, 4>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
 #endif
+// real factors (real NEP at real points): RSRR_LU_ONLY = 32 (float), 65 (double)
+#if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 32
+cudaError_t launch_band_lu_r32(float *ab, int32_t *piv, int32_t *info, float *dinv, const BandGeom &g, int N,
+                               int n, cudaStream_t s, bool cluster) {
+    return lu_by_kl<float, NB_C64, 4>(ab, piv, info, dinv, g, N, n, cluster, s);
+}
+#endif
+#if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 65
+cudaError_t launch_band_lu_r64(double *ab, int32_t *piv, int32_t *info, double *dinv, const BandGeom &g, int N,
+                               int n, cudaStream_t s, bool cluster) {
+    return lu_by_kl<double, NB_C128, 1>(ab, piv, info, dinv, g, N, n, cluster, s);
+}
+#endif
 #if !defined(RSRR_LU_ONLY) || RSRR_LU_ONLY == 128
 cudaError_t launch_band_lu_grouped_c128(const LuTask *tasks, int ntasks, int kl_max, int *next, cudaStream_t s) {
     if (kl_max > KL_MAX) return cudaErrorInvalidValue;

@@ -94,6 +94,11 @@ RSRR_DEV void s2_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 template <typename C> RSRR_DEV void s2_cp_elem(unsigned saddr, const C *g);
 template <> RSRR_DEV void s2_cp_elem<float2>(unsigned saddr, const float2 *g) { s2_cp8(saddr, g); }
 template <> RSRR_DEV void s2_cp_elem<double2>(unsigned saddr, const double2 *g) { s2_cp16(saddr, g); }
+RSRR_DEV void s2_cp4(unsigned saddr, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g));
+}
+template <> RSRR_DEV void s2_cp_elem<float>(unsigned saddr, const float *g) { s2_cp4(saddr, g); }
+template <> RSRR_DEV void s2_cp_elem<double>(unsigned saddr, const double *g) { s2_cp8(saddr, g); }
 
 template <typename C, int NB, int LC, int S2_RC, int S2_NSLOT>
 struct S2Layout {
@@ -343,6 +348,8 @@ static size_t s2_smem_used(const BandGeom &g) {
 
 size_t band_solve2_smem_c64(const BandGeom &g) { return s2_smem_used<float2, NB_C64, 16>(g); }
 size_t band_solve2_smem_c128(const BandGeom &g) { return s2_smem_used<double2, NB_C128, 8>(g); }
+size_t band_solve2_smem_r32(const BandGeom &g) { return s2_smem_used<float, NB_C64, 16>(g); }
+size_t band_solve2_smem_r64(const BandGeom &g) { return s2_smem_used<double, NB_C128, 8>(g); }
 
 // gate = 1 if at most thr points have done == 0 (few points left: the
 // narrow shape, more CTAs per point), else 0
@@ -393,6 +400,14 @@ cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const
                                    const int32_t *gate, int want) {
     if (narrow) return s2_dispatch<float2, NB_C64, 4>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
     return s2_dispatch<float2, NB_C64, 16>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+}
+cudaError_t launch_band_solve2_r32(const float *ab, const int32_t *bperm, const float *dinv, float *B,
+                                   const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s) {
+    return s2_dispatch<float, NB_C64, 16>(ab, bperm, dinv, B, g, N, n, L, skip, nullptr, 0, s);
+}
+cudaError_t launch_band_solve2_r64(const double *ab, const int32_t *bperm, const double *dinv, double *B,
+                                   const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s) {
+    return s2_dispatch<double, NB_C128, 8>(ab, bperm, dinv, B, g, N, n, L, skip, nullptr, 0, s);
 }
 cudaError_t launch_band_solve2_c128(const double2 *ab, const int32_t *bperm, const double2 *dinv,
                                     double2 *B, const BandGeom &g, int N, int n, int L,

@@ -109,6 +109,36 @@ RSRR_DEV double2 crecip(double2 b) {
 RSRR_DEV float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
 RSRR_DEV double2 to_c128(float2 a) { return make_double2((double)a.x, (double)a.y); }
 
+// Real overloads of the same helpers: the band LU and solves instantiated for
+// float / double factor real NEPs at real sampling points (real arithmetic
+// at a quarter of the multiplies and half the storage of the complex path).
+template <> struct real_of<float> { using type = float; };
+template <> struct real_of<double> { using type = double; };
+template <> RSRR_DEV float czero<float>() { return 0.f; }
+template <> RSRR_DEV double czero<double>() { return 0.0; }
+template <> RSRR_DEV float cone<float>() { return 1.f; }
+template <> RSRR_DEV double cone<double>() { return 1.0; }
+RSRR_DEV float cadd(float a, float b) { return a + b; }
+RSRR_DEV double cadd(double a, double b) { return a + b; }
+RSRR_DEV float csub(float a, float b) { return a - b; }
+RSRR_DEV double csub(double a, double b) { return a - b; }
+RSRR_DEV float cmul(float a, float b) { return a * b; }
+RSRR_DEV double cmul(double a, double b) { return a * b; }
+RSRR_DEV float cmulc(float a, float b) { return a * b; }
+RSRR_DEV double cmulc(double a, double b) { return a * b; }
+RSRR_DEV float cfms(float acc, float a, float b) { return fmaf(-a, b, acc); }
+RSRR_DEV double cfms(double acc, double a, double b) { return fma(-a, b, acc); }
+RSRR_DEV float cfma(float acc, float a, float b) { return fmaf(a, b, acc); }
+RSRR_DEV double cfma(double acc, double a, double b) { return fma(a, b, acc); }
+RSRR_DEV float cabs1(float a) { return fabsf(a); }
+RSRR_DEV double cabs1(double a) { return fabs(a); }
+RSRR_DEV float cabsv(float a) { return fabsf(a); }
+RSRR_DEV double cabsv(double a) { return fabs(a); }
+RSRR_DEV bool cnonzero(float a) { return a != 0.f; }
+RSRR_DEV bool cnonzero(double a) { return a != 0.0; }
+RSRR_DEV float crecip(float b) { return 1.f / b; }
+RSRR_DEV double crecip(double b) { return 1.0 / b; }
+
 template <typename T> RSRR_DEV T shfl_down(T v, int off) { return __shfl_down_sync(0xffffffffu, v, off); }
 
 // max of non-negative doubles through their ordered bit patterns

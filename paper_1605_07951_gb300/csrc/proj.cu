@@ -891,8 +891,12 @@ rsrr_status Handle::project(cudaStream_t s) {
     // resolution floor of the basis: the caller's, or automatic -- the samples'
     // own accuracy (a tenth of eta_tol for the refined mixed-precision samples,
     // 1e-12 for the FP64 path): singular values of S below it are noise of the
-    // samples, and keeping them only grows k (and the k^3 SS-FULL behind it)
-    const double floor_auto = opts.precision == RSRR_PREC_MIXED ? 0.1 * opts.eta_tol : 1e-12;
+    // samples, and keeping them only grows k (and the k^3 SS-FULL behind it).
+    // The moment matrix of SSRR-M is not S: its higher moments carry the
+    // eigen-directions scaled by ((lambda - gamma) / rho)^a, far below its
+    // sigma_1, so it keeps the fixed 1e-12.
+    const double floor_auto =
+        opts.precision == RSRR_PREC_MIXED && opts.method == RSRR_METHOD_RSRR ? 0.1 * opts.eta_tol : 1e-12;
     const double floor_ = std::max(opts.delta, opts.delta_floor > 0.0 ? opts.delta_floor : floor_auto);
     int kt = 0;            // columns of Qall so far
     double s1sq = 0.0;     // sigma_1^2 of Sn (from level 0)

@@ -77,6 +77,11 @@ struct Handle {
     double2 *d_X = nullptr;           // S = [X_0 ... X_{N-1}], n x NL
     double2 *d_R = nullptr;           // FP64 residuals (mixed path)
     float2 *d_D = nullptr;            // complex64 corrections (mixed path)
+    // real path (RSRR_FLAG_REAL: real NEP at real points): real factors, block
+    // inverses and corrections; S stays complex with zero imaginary parts
+    bool real = false;
+    float *d_abr32 = nullptr, *d_dinvr32 = nullptr, *d_Dr32 = nullptr;
+    double *d_abr64 = nullptr, *d_dinvr64 = nullptr, *d_Dr64 = nullptr;
     float2 *d_ab32 = nullptr;         // complex64 band factors
     double2 *d_ab64 = nullptr;        // complex128 band factors
     float2 *d_dinv32 = nullptr;       // per block L11^{-1}, U11^{-1} (complex64)
@@ -155,6 +160,8 @@ struct Handle {
     // GMRES refinement cycles of points p0 .. p0+np-1 (mixed band path)
     rsrr_status refine_gmres(int p0, int np, const DevProblem &dq, cudaStream_t s);
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);
+    // the real path's solve of points p0 .. p0+np-1 (float or double B)
+    cudaError_t real_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);
     // a refinement sweep's complex64 solve: streaming solve in the wide shape
     // while many points are left, in the narrow one when few are (chosen on
     // the device from the done flags)

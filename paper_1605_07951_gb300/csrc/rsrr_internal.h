@@ -75,6 +75,33 @@ cudaError_t launch_band_solve_c64(const float2 *ab, const int32_t *piv, const fl
 cudaError_t launch_band_solve_c128(const double2 *ab, const int32_t *piv, const double2 *dinv,
                                    double2 *B, const BandGeom &g, int N, int n, int L,
                                    const int32_t *skip, cudaStream_t s);
+// ---- real path: real NEP at real points, real factor storage (float for
+// the mixed path, double for the FP64 path), S complex with zero imaginary
+// parts; the launchers mirror their complex counterparts
+cudaError_t launch_band_lu_r32(float *ab, int32_t *piv, int32_t *info, float *dinv, const BandGeom &g, int N,
+                               int n, cudaStream_t s, bool cluster);
+cudaError_t launch_band_lu_r64(double *ab, int32_t *piv, int32_t *info, double *dinv, const BandGeom &g, int N,
+                               int n, cudaStream_t s, bool cluster);
+cudaError_t launch_band_solve_r32(const float *ab, const int32_t *piv, const float *dinv, float *B,
+                                  const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_band_solve_r64(const double *ab, const int32_t *piv, const double *dinv, double *B,
+                                  const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s);
+size_t band_solve2_smem_r32(const BandGeom &g);
+size_t band_solve2_smem_r64(const BandGeom &g);
+cudaError_t launch_band_solve2_r32(const float *ab, const int32_t *bperm, const float *dinv, float *B,
+                                   const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_band_solve2_r64(const double *ab, const int32_t *bperm, const double *dinv, double *B,
+                                   const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s);
+cudaError_t launch_broadcast_probe_r32(float *D, const double2 *U, int64_t nL, int N, cudaStream_t s);
+cudaError_t launch_broadcast_probe_r64(double *D, const double2 *U, int64_t nL, int N, cudaStream_t s);
+cudaError_t launch_widen_r32(double2 *X, const float *D, int64_t total, cudaStream_t s);
+cudaError_t launch_widen_r64(double2 *X, const double *D, int64_t total, cudaStream_t s);
+cudaError_t launch_narrow_r32(float *D, const double2 *R, int64_t per_pt, int N, const int32_t *skip,
+                              cudaStream_t s);
+cudaError_t launch_update_r32(double2 *X, const float *D, int64_t per_pt, int N, const int32_t *skip,
+                              cudaStream_t s);
+cudaError_t launch_real_part(double2 *U, int64_t total, cudaStream_t s);
+
 // whether the one-kernel complex128 solve's shared memory (its smallest
 // right-hand-side chunk) fits the device's opt-in limit for this geometry
 bool band_solve_fits_c128(const BandGeom &g);

@@ -33,7 +33,7 @@ RSRR_REFINE_IR, RSRR_REFINE_GMRES = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI, RSRR_GEMM_OZAKI_MMA = 0, 1, 2, 3
 (RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU, RSRR_FLAG_INJECT_TIMEOUT, RSRR_FLAG_SIMT_DENSE_UPDATE,
- RSRR_FLAG_GRAPH, RSRR_FLAG_AUTOTUNE, RSRR_FLAG_WIDE_SOLVE_ONLY) = 1, 2, 4, 8, 16, 32, 64
+ RSRR_FLAG_GRAPH, RSRR_FLAG_AUTOTUNE, RSRR_FLAG_WIDE_SOLVE_ONLY, RSRR_FLAG_REAL) = 1, 2, 4, 8, 16, 32, 64, 128
 RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ, RSRR_NEP_DENSE = 0, 1, 2
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",

@@ -159,3 +159,34 @@ def test_callback_returning_a_non_finite_value_is_refused(rsrr):
     with pytest.raises(rsrr.RSRRError) as e:
         rsrr.prepared(p)
     assert e.value.status == rsrr.RSRR_EINVAL
+
+
+def test_real_flag_needs_a_real_problem_at_real_points(rsrr):
+    """RSRR_FLAG_REAL (real arithmetic for T(z_j) real, Sections 3.3 and 5.1)
+    is accepted only where every T(z_j) is real: real values, real points,
+    real f_i there; otherwise rsrr_create refuses it with EINVAL."""
+    real = rsrr.default_opts(flags=rsrr.RSRR_FLAG_REAL)
+    z, coef, _ = rsrr.prepared(_interval_string(), real)  # Chebyshev points on [3, 1e4]
+    assert np.all(z.imag == 0) and np.all(coef.imag == 0)
+    refused = [
+        (W.loaded_string(N=37), real),                      # explicit real points: accepted below
+        (W.rational_grid(g=20, N=16, L=4), real),           # points on an ellipse
+        (W.diag_quadratic_complex(), real),                 # complex values
+        (W.helmholtz_sphere(n=64, N=8, L=4), real),         # dense kind
+        (_interval_string(), rsrr.default_opts(flags=rsrr.RSRR_FLAG_REAL, refine=rsrr.RSRR_REFINE_GMRES)),
+    ]
+    rsrr.prepared(*refused[0])
+    for p, o in refused[1:]:
+        with pytest.raises(rsrr.RSRRError) as e:
+            rsrr.prepared(p, o)
+        assert e.value.status == rsrr.RSRR_EINVAL
+        assert "RSRR_FLAG_REAL" in str(e.value)
+
+
+def test_real_flag_halves_the_factor_storage(rsrr):
+    p = _interval_string()
+    p.N, p.L = 64, 8
+    for prec in (rsrr.RSRR_PREC_MIXED, rsrr.RSRR_PREC_FP64):
+        c = rsrr.estimate_bytes(p, rsrr.default_opts(precision=prec))
+        r = rsrr.estimate_bytes(p, rsrr.default_opts(precision=prec, flags=rsrr.RSRR_FLAG_REAL))
+        assert r < c
