@@ -14,4 +14,6 @@ from .rsrr import (sample_points, quad_weights, inside, eval_fn, assemble,
                    taylor_coefficients, residual_dense, backward_error_inf_dense, rsrr_dense,
                    argument_principle_count_dense, ShiftPow, assemble_terms,
                    resolvent_samples_terms, backward_error_inf_terms, residual_terms, rsrr_terms,
-                   interpolation_weights, moment_matrix, ss_ri, ssrr_m)
+                   interpolation_weights, moment_matrix, ss_ri, ssrr_m, gauss_legendre,
+                   rect_sides, rect_counts, rect_rule, contour_quadrature, contour_path,
+                   phase_det_band, RECT_PANEL)

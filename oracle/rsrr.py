@@ -49,18 +49,86 @@ from workloads import (F_ONE, F_ZPOW, F_RATIONAL, F_INV, F_SQRT, F_EXP, F_TAYLOR
 def sample_points(region: Region, N: int) -> np.ndarray:
     """z_j = phi(alpha_j), alpha_j = 2 pi (j + 1/2)/N on the ellipse
     phi(alpha) = gamma + a cos(alpha) + i b sin(alpha) (Section 5.1, ellipse
-    contour and trapezoid nodes), the region's explicit points, or the
+    contour and trapezoid nodes), the region's explicit points, the
     Chebyshev points of the first kind x_i = cos((2i + 1) pi / 2N) (Eq. 42)
     mapped to the interval [gamma - a, gamma + a] (Section 3.3, real points
-    for an interval of interest)."""
-    if region.kind == "points":
+    for an interval of interest), or Gauss-Legendre nodes on the sides of a
+    rectangle (Section 5.4; explicit points with a rectangular contour for
+    the second stage of two-stage sampling)."""
+    if region.kind == "points" or (region.kind == "rect" and region.points is not None):
         return np.asarray(region.points, dtype=np.complex128).copy()
     if region.kind == "interval":
         i = np.arange(N)
         return region.center + region.a * np.cos((2 * i + 1) * np.pi / (2 * N)) + 0j
+    if region.kind == "rect":
+        return rect_rule(region, rect_counts(region, N))[0]
     j = np.arange(N)
     alpha = 2.0 * np.pi * (j + 0.5) / N
     return region.center + region.a * np.cos(alpha) + 1j * region.b * np.sin(alpha)
+
+
+# ---------------------------------------------------------------------------
+# Rectangular contour (Section 5.4: Gauss-Legendre nodes on the four sides,
+# composite Gauss quadrature for the contour integrals of SS-FULL)
+# ---------------------------------------------------------------------------
+
+def gauss_legendre(n: int):
+    """Nodes x_k and weights w_k of the n-point Gauss-Legendre rule on
+    [-1, 1] (numpy's leggauss as the library primitive)."""
+    return np.polynomial.legendre.leggauss(n)
+
+
+def rect_sides(region: Region) -> list:
+    """The four sides (start, end) counterclockwise from the lower-left
+    vertex center - a - i b."""
+    c, a, b = complex(region.center), region.a, region.b
+    v = [c - a - 1j * b, c + a - 1j * b, c + a + 1j * b, c - a + 1j * b]
+    return [(v[s], v[(s + 1) % 4]) for s in range(4)]
+
+
+def rect_counts(region: Region, N: int) -> list:
+    """Sampling points per side: nx on the two sides parallel to the real
+    axis, N/2 - nx on the other two (27 and 13 for N = 80 in Section 5.4)."""
+    ny = N // 2 - region.nx
+    return [region.nx, ny, region.nx, ny]
+
+
+def rect_rule(region: Region, counts: list):
+    """Gauss-Legendre nodes on each side (counts[s] of them on side s,
+    increasing along the side's direction) and the contour weights
+    omega = dz / (2 pi): for a side from p to q, z = (p + q)/2 + (q - p) x/2,
+    dz = (q - p) w / 2 -- the same normalisation as the trapezoid weights
+    (1/N) phi'(alpha) of the ellipse (a change of 1/i, common to all)."""
+    zs, ws = [], []
+    for (p, q), c in zip(rect_sides(region), counts):
+        x, w = gauss_legendre(int(c))
+        zs.append(0.5 * (p + q) + 0.5 * (q - p) * x)
+        ws.append(0.5 * (q - p) * w / (2.0 * np.pi))
+    return np.concatenate(zs), np.concatenate(ws)
+
+
+RECT_PANEL = 10  # nodes of one Gauss-Legendre panel of the composite rule
+
+
+def contour_quadrature(region: Region, NQ: int):
+    """Nodes and weights omega_q of the contour integrals of SS-FULL: the
+    NQ-point trapezoid rule on the ellipse (Eq. 58), or on the rectangle
+    composite Gauss quadrature (Section 5.4): side s of length len_s is cut
+    into P_s = max(1, round(NQ len_s / (10 perimeter))) equal panels, each
+    with the 10-point Gauss-Legendre rule."""
+    if region.kind != "rect":
+        zq = sample_points(Region(region.center, region.a, region.b), NQ)
+        return zq, quad_weights(region, NQ)
+    per = 4.0 * (region.a + region.b)
+    x, w = gauss_legendre(RECT_PANEL)
+    zs, ws = [], []
+    for p, q in rect_sides(region):
+        P = max(1, int(round(NQ * abs(q - p) / (RECT_PANEL * per))))
+        for t in range(P):
+            a0, a1 = p + (q - p) * t / P, p + (q - p) * (t + 1) / P
+            zs.append(0.5 * (a0 + a1) + 0.5 * (a1 - a0) * x)
+            ws.append(0.5 * (a1 - a0) * w / (2.0 * np.pi))
+    return np.concatenate(zs), np.concatenate(ws)
 
 
 def quad_weights(region: Region, NQ: int) -> np.ndarray:
@@ -71,10 +139,13 @@ def quad_weights(region: Region, NQ: int) -> np.ndarray:
 
 
 def inside(region: Region, z) -> np.ndarray:
-    """Strict interior of the ellipse ((x-gr)/a)^2 + ((y-gi)/b)^2 < 1."""
+    """Strict interior of the ellipse ((x-gr)/a)^2 + ((y-gi)/b)^2 < 1, or of
+    the rectangle |x - gr| < a, |y - gi| < b."""
     z = np.asarray(z)
-    x = (z.real - region.center.real) / region.a
-    y = (z.imag - region.center.imag) / region.b
+    x = (z.real - complex(region.center).real) / region.a
+    y = (z.imag - complex(region.center).imag) / region.b
+    if region.kind == "rect":
+        return (np.abs(x) < 1.0) & (np.abs(y) < 1.0)
     return x * x + y * y < 1.0
 
 
@@ -197,7 +268,8 @@ def project(prob: Problem, Q: np.ndarray) -> list:
 def ss_full(P: list, fns: list, region: Region, NQ: int = 500, KQ: int = 2,
             tol_gap: float = 1e3):
     """SS-FULL: the SS-RI algorithm of Section 3.3 with U = I (F = T_Q^{-1}),
-    sampling points on the ellipse by the trapezoid rule of Section 5.1.
+    quadrature nodes on the contour: the trapezoid rule on the ellipse
+    (Section 5.1) or composite Gauss on the rectangle (Section 5.4).
 
     Moments A_alpha = sum_q omega_q ((z_q - gamma)/rho)^alpha F(z_q), alpha <
     2 KQ (the scaled-moment reading: a fixed change of basis of z that keeps
@@ -211,8 +283,7 @@ def ss_full(P: list, fns: list, region: Region, NQ: int = 500, KQ: int = 2,
     eigenvectors as columns of G, and {"nbar", "gmax", "sv"}.
     """
     k = P[0].shape[0]
-    zq = sample_points(Region(region.center, region.a, region.b), NQ)
-    wq = quad_weights(region, NQ)
+    zq, wq = contour_quadrature(region, NQ)
     gamma = region.center
     rho = max(region.a, region.b)
     Amom = [np.zeros((k, k), dtype=np.complex128) for _ in range(2 * KQ)]
@@ -377,18 +448,54 @@ def bisect_real_eigenvalues(prob: Problem, lo: float, hi: float, rtol: float = 1
     return np.sort(np.array(out, dtype=np.float64))
 
 
-def argument_principle_count(prob: Problem, region: Region, npts: int = 4096) -> int:
-    """Number of zeros of det T inside the ellipse: the winding number of
-    det T(phi(alpha)) for alpha in [0, 2 pi), with the phase unwrapped and the
-    contour refined until every step changes the argument by < pi/4."""
+def contour_path(region: Region, t: np.ndarray) -> np.ndarray:
+    """The closed contour at parameters t in [0, 1], counterclockwise: the
+    ellipse phi(2 pi t), or the rectangle's perimeter at arc length
+    t * perimeter from the lower-left vertex."""
+    t = np.asarray(t, dtype=np.float64)
+    if region.kind != "rect":
+        al = 2.0 * np.pi * t
+        return region.center + region.a * np.cos(al) + 1j * region.b * np.sin(al)
+    sides = rect_sides(region)
+    lens = np.array([abs(q - p) for p, q in sides])
+    cum = np.concatenate([[0.0], np.cumsum(lens)]) / lens.sum()
+    out = np.empty(t.shape, dtype=np.complex128)
+    for s, (p, q) in enumerate(sides):
+        sel = (t >= cum[s]) & ((t < cum[s + 1]) if s < 3 else (t <= cum[4]))
+        out[sel] = p + (q - p) * (t[sel] - cum[s]) / (cum[s + 1] - cum[s])
+    return out
+
+
+def phase_det_band(prob: Problem, z: complex) -> float:
+    """arg det T(z) from the banded LU with partial pivoting (LAPACK zgbtrf as
+    the library primitive): det = (-1)^(row swaps) prod u_ii."""
+    from scipy.linalg.lapack import zgbtrf
+    kl, ku = prob.bandwidths()
+    T = assemble(prob, z).tocoo()
+    ab = np.zeros((2 * kl + ku + 1, prob.n), dtype=np.complex128)
+    ab[kl + ku + T.row - T.col, T.col] = T.data
+    lu, piv, info = zgbtrf(ab, kl, ku)
+    d = lu[kl + ku, :]
+    swaps = int(np.count_nonzero(piv != np.arange(prob.n)))
+    return float(np.angle(np.prod(d / np.abs(d))) + np.pi * (swaps % 2))
+
+
+def argument_principle_count(prob: Problem, region: Region, npts: int = 4096,
+                             band: bool = False) -> int:
+    """Number of zeros of det T inside the contour: the winding number of
+    det T along the closed contour (contour_path), with the phase unwrapped and
+    the contour refined until every step changes the argument by < pi/4.
+    band=True takes the phase from the banded LU (large n)."""
     def logdet(z):
+        if band:
+            return phase_det_band(prob, z)
         T = assemble(prob, z).toarray()
         sgn, _ = np.linalg.slogdet(T)
         return np.angle(sgn)
 
-    alpha = np.linspace(0.0, 2.0 * np.pi, npts + 1)
+    alpha = np.linspace(0.0, 1.0, npts + 1)
     while True:
-        zz = region.center + region.a * np.cos(alpha) + 1j * region.b * np.sin(alpha)
+        zz = contour_path(region, alpha)
         ph = np.array([logdet(z) for z in zz])
         d = np.angle(np.exp(1j * np.diff(ph)))
         if np.all(np.abs(d) < np.pi / 4) or len(alpha) > 1 << 16:
@@ -660,6 +767,8 @@ def interpolation_weights(region: Region, z: np.ndarray) -> np.ndarray:
     N = len(z)
     if region.kind == "ellipse":
         return quad_weights(region, N)
+    if region.kind == "rect" and region.points is None:  # Gauss-Legendre nodes: dz / (2 pi)
+        return rect_rule(region, rect_counts(region, N))[1]
     if region.kind == "interval":
         i = np.arange(N)
         return (-1.0) ** i * np.sin((2 * i + 1) * np.pi / (2 * N)) + 0j

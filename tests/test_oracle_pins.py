@@ -706,3 +706,145 @@ def test_dense_n1024_golden_is_consistent():
     lam = np.array([complex(*z) for z in g["oracle_rsrr_eigenvalues"]])
     assert np.all(np.abs(lam - 3.0) < 1.0)
     assert max(g["oracle_rsrr_residuals"]) <= 1e-12
+
+
+# ------------------------------------------------ rectangle contour (Section 5.4)
+def _rect(nx=27):
+    return W.Region(272.5 + 15.0j, 57.5, 25.0, kind="rect", nx=nx)
+
+
+def test_gauss_legendre_is_exact_to_degree_2n_minus_1():
+    """The n-point Gauss-Legendre rule integrates x^k over [-1, 1] exactly
+    (2/(k+1) for even k, 0 for odd k) for k <= 2n - 1; for x^(2n) it falls
+    short by the rule's error constant 2^(2n+1) (n!)^4 / ((2n+1) ((2n)!)^2)."""
+    from math import factorial
+    for n in (5, 13, 27):
+        x, w = oracle.gauss_legendre(n)
+        for k in range(2 * n):
+            exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+            assert abs(np.sum(w * x ** k) - exact) <= 1e-14
+        if n < 27:
+            err = 2.0 / (2 * n + 1) - np.sum(w * x ** (2 * n))
+            want = 2 ** (2 * n + 1) * factorial(n) ** 4 / ((2 * n + 1) * factorial(2 * n) ** 2)
+            assert abs(err - want) <= 1e-6 * want
+
+
+def test_rectangle_points_and_weights_integrate_cauchy():
+    """(Through the module, so that planted mistakes are seen.)  Sampling
+    points: nx Gauss-Legendre nodes on each horizontal side, N/2 -
+    nx on each vertical side, counterclockwise; the weights dz/(2 pi) give
+    (1/2 pi) of the contour integral: i for 1/(z - c) with c inside, 0 outside
+    and 0 for polynomials (Cauchy)."""
+    reg = _rect()
+    z = ORACLE_MOD.sample_points(reg, 80)
+    c, a, b = 272.5 + 15.0j, 57.5, 25.0
+    bottom, right, top, left = z[:27], z[27:40], z[40:67], z[67:]
+    assert np.allclose(bottom.imag, c.imag - b) and np.all(np.diff(bottom.real) > 0)
+    assert np.allclose(right.real, c.real + a) and np.all(np.diff(right.imag) > 0)
+    assert np.allclose(top.imag, c.imag + b) and np.all(np.diff(top.real) < 0)
+    assert np.allclose(left.real, c.real - a) and np.all(np.diff(left.imag) < 0)
+    x27, _ = ORACLE_MOD.gauss_legendre(27)
+    assert np.allclose(bottom.real, c.real + a * x27, rtol=0, atol=1e-12)
+    # the 80 sampling points (one Gauss rule per side) and the composite rule
+    # of SS-FULL (10-point panels), each to its own accuracy
+    for (zq, wq), tol, poles in (
+            ((z, ORACLE_MOD.interpolation_weights(reg, z)), 1e-6, (c, 250 + 20j, 400 + 0j, 272 + 80j)),
+            (ORACLE_MOD.contour_quadrature(reg, 500), 1e-10, (c, 300 - 5j, 220 - 5j, 400 + 0j, 272 + 60j))):
+        for pole in poles:
+            expect = 1j if ORACLE_MOD.inside(reg, np.array([pole]))[0] else 0.0
+            assert abs(np.sum(wq / (zq - pole)) - expect) < tol
+        assert abs(np.sum(wq * ((zq - c) / a) ** 5)) < 1e-12
+    zq, wq = ORACLE_MOD.contour_quadrature(reg, 500)
+    assert 480 <= len(zq) <= 520 and len(zq) % ORACLE_MOD.RECT_PANEL == 0
+    assert ORACLE_MOD.inside(reg, np.array([c, c + 57.4, c - 24.9j, c + 58, c + 25.1j])).tolist() == \
+        [True, True, True, False, False]
+    p = ORACLE_MOD.contour_path(reg, np.array([0.0, 115 / 330, 165 / 330, 280 / 330, 1.0]))
+    assert np.allclose(p, [c - a - 1j * b, c + a - 1j * b, c + a + 1j * b, c - a + 1j * b, c - a - 1j * b])
+
+
+# rectangles with every closed-form eigenvalue at least 0.1 from the contour;
+# the quadratic's holds two eigenvalues outside its inscribed ellipse
+RECT_REGION = {"diag_quadratic": (0.2 + 0.3j, 0.6, 0.9), "diag_sqrt": (5.0 + 0.0j, 1.35, 0.45)}
+
+
+def rect_family(name, nx=16, **kw):
+    p = getattr(W, name)(**kw)
+    c, a, b = RECT_REGION[name]
+    p.region = W.Region(c, a, b, kind="rect", nx=nx)
+    return p
+
+
+@pytest.mark.parametrize("name", ["diag_quadratic", "diag_sqrt"])
+def test_rsrr_on_a_rectangle_finds_closed_form_eigenvalues(name):
+    """RSRR with Gauss-Legendre sampling points on a rectangle and SS-FULL by
+    composite Gauss quadrature, on closed-form families; the count inside
+    also by the argument principle along the rectangle."""
+    p = rect_family(name, N=48, L=6)
+    ref = exact_roots(p)
+    assert len(ref) >= 4
+    out = oracle.rsrr(p, NQ=500)
+    assert len(out["lam"]) == len(ref) and match_eigs(ref, out["lam"]) <= 1e-9
+    assert out["res"].max() <= 1e-10
+    q = rect_family(name, nx=2, n=40, N=8, L=2)
+    cnt = len(exact_roots(q))
+    assert oracle.argument_principle_count(q, q.region, npts=512) == cnt
+    assert oracle.argument_principle_count(q, q.region, npts=512, band=True) == cnt
+
+
+def test_moment_methods_on_a_rectangle_find_closed_form_eigenvalues():
+    """SS-RI's moments are contour integrals of U^H T^{-1} U, accurate only as
+    far as the Gauss rule on the sides resolves the poles near the contour:
+    128 points reach 1e-13 here (48 give 4e-6); SSRR-M only needs span(M)."""
+    p = rect_family("diag_quadratic", nx=44, N=128, L=8)
+    ref = exact_roots(p)
+    out = oracle.ss_ri(p, K=8)
+    assert len(out["lam"]) == len(ref) and match_eigs(ref, out["lam"]) <= 1e-9
+    p = rect_family("diag_quadratic", N=48, L=8)
+    out = oracle.ssrr_m(p, K=6, NQ=500)
+    assert len(out["lam"]) == len(ref) and match_eigs(ref, out["lam"]) <= 1e-9
+
+
+@pytest.mark.parametrize("which", ["clockwise", "half_weights", "ellipse_contour"])
+def test_planted_rectangle_mistakes_fail_a_pin(monkeypatch, which):
+    if which == "clockwise":
+        orig = ORACLE_MOD.rect_sides
+        monkeypatch.setattr(ORACLE_MOD, "rect_sides", lambda reg: [(q, p) for p, q in orig(reg)])
+    elif which == "half_weights":
+        orig = ORACLE_MOD.gauss_legendre
+        monkeypatch.setattr(ORACLE_MOD, "gauss_legendre", lambda n: (orig(n)[0], 0.5 * orig(n)[1]))
+    else:   # the ellipse's trapezoid rule for a rectangular region
+        orig = ORACLE_MOD.contour_quadrature
+        monkeypatch.setattr(ORACLE_MOD, "contour_quadrature",
+                            lambda reg, NQ: orig(W.Region(reg.center, reg.a, reg.b), NQ))
+    failed = False
+    try:
+        test_rsrr_on_a_rectangle_finds_closed_form_eigenvalues("diag_quadratic")
+        test_rectangle_points_and_weights_integrate_cauchy()
+    except (AssertionError, Exception):
+        failed = True
+    assert failed, f"planted mistake {which!r} went unnoticed"
+
+
+def test_gun_like_golden_is_consistent():
+    """tests/golden/gun_like.json: the argument-principle count equals the
+    number of eigenpairs of each run, every stored eigenvalue has a tiny
+    normalised residual when recomputed here with an eigenvector from the
+    banded null-space iteration, and the three runs agree."""
+    with open(os.path.join(GOLD, "gun_like.json")) as f:
+        g = json.load(f)
+    runs = [np.array([complex(*z) for z in g[k]["eigenvalues"]])
+            for k in ("contour_N80_L2", "stage1_N30_L2", "stage2_L2")]
+    assert all(len(r) == g["count_in_region"] == 15 for r in runs)
+    assert match_eigs(runs[0], runs[2]) <= 1e-11 and match_eigs(runs[0], runs[1]) <= 1e-9
+    assert max(g["stage2_L2"]["residuals"]) <= max(g["contour_N80_L2"]["residuals"])
+    # inverse iteration at each stored eigenvalue: T(lam) is (numerically)
+    # singular, so two solves with a random right-hand side give a vector
+    # with a residual at rounding level
+    import scipy.sparse.linalg as spla
+    p = W.gun_like()
+    rng = np.random.default_rng(0)
+    for lam in runs[0][:5]:
+        lu = spla.splu(ORACLE_MOD.assemble(p, lam).tocsc())
+        v = lu.solve(rng.standard_normal(p.n) + 0j)
+        v = lu.solve(v / np.linalg.norm(v))
+        assert oracle.residual(p, lam, v) <= 1e-13

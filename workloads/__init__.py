@@ -42,18 +42,23 @@ class Fn:
 @dataclass
 class Region:
     """Ellipse phi(a) = center + a*cos(t) + i*b*sin(t), explicit sample points,
-    or the real interval [center - a, center + a] of the ellipse's major axis.
+    the real interval [center - a, center + a] of the ellipse's major axis, or
+    the rectangle with vertices center +- a +- i b.
 
     For kind == "points" the explicit points are the sampling points, and for
     kind == "interval" the N Chebyshev points of the first kind on the
     interval are; in both cases the ellipse (center, a, b) is still the
-    contour used for the projected solve and for the inside test.
+    contour used for the projected solve and for the inside test.  For
+    kind == "rect" the rectangle is the contour and the region; the sampling
+    points are Gauss-Legendre nodes on its sides, nx on each side parallel
+    to the real axis and N/2 - nx on each of the other two.
     """
     center: complex
     a: float
     b: float
     kind: str = "ellipse"
     points: np.ndarray | None = None
+    nx: int = 0
 
 
 @dataclass
@@ -549,3 +554,49 @@ def dense_hidden_quadratic(n: int = 200, seed: int = 81, N: int = 32, L: int = 4
     fns = [Fn(F_ONE), Fn(F_ZPOW, 1), Fn(F_ZPOW, 2)]
     return DenseTermsProblem("dense_hidden_quadratic", n, As, fns, Region(0.6j - 0.2, 1.0, 0.8), N, L,
                              probe(n, L, seed + 2), meta=dict(diags=[k, c, m], seed=seed))
+
+
+# ----------------------------------------------------------------------------
+# gun-type NEP: square-root couplings on a 2-D grid, rectangular region
+# ----------------------------------------------------------------------------
+
+def gun_like(gx: int = 100, gy: int = 100, N: int = 80, L: int = 2, nx: int = 27,
+             alpha: float = 2405.0, beta: float = 3295.0, w1: float = 1.0e4,
+             w2: float = 1.0e4, kappa2: float = 108.8774, seed_u: int = 9001,
+             name: str = "gun_like") -> Problem:
+    """T(z) = K - z^2 M + i sqrt(z^2 - kappa_1^2) W_1 + i sqrt(z^2 - kappa_2^2) W_2
+    (the radio-frequency gun form of Section 5.4, kappa_1 = 0, kappa_2 =
+    108.8774), synthetic: K is the anisotropic 5-point stiffness of a gx x gy
+    grid with Dirichlet sides (natural row-major ordering, half-bandwidth gx),
+    sx (2 - shifts along x) + sy (2 - shifts along y) with sx = alpha (gx+1)^2
+    / pi^2, sy = beta (gy+1)^2 / pi^2, so that the undamped z^2 are about
+    alpha i^2 + beta j^2; M = I; W_1 = w1 on the grid line x = 0, W_2 = w2 on
+    the line x = gx - 1 (the two ports, diagonal).  The damped eigenvalues lie
+    just above the real axis (imaginary parts up to about 3), so the
+    rectangle is [215, 330] x [-10, 40], its vertical sides in gaps of the
+    spectrum (fifteen eigenvalues inside, none within 6 of the contour), with
+    Gauss-Legendre sampling points, nx on each horizontal side (27 and 13 for
+    N = 80, the paper's rule)."""
+    n = gx * gy
+    idx = np.arange(n)
+    gi, gj = idx // gx, idx % gx          # row (y) and column (x) of the grid node
+    sx = alpha * (gx + 1) ** 2 / np.pi ** 2
+    sy = beta * (gy + 1) ** 2 / np.pi ** 2
+    K, M, W1, W2 = {}, {}, {}, {}
+    for r in range(n):
+        K[(r, r)] = 2.0 * sx + 2.0 * sy
+        M[(r, r)] = 1.0
+    for r in range(n):
+        if gj[r] + 1 < gx:
+            K[(r, r + 1)] = K[(r + 1, r)] = -sx
+        if gi[r] + 1 < gy:
+            K[(r, r + gx)] = K[(r + gx, r)] = -sy
+    for r in idx[gj == 0]:
+        W1[(int(r), int(r))] = w1
+    for r in idx[gj == gx - 1]:
+        W2[(int(r), int(r))] = w2
+    row_ptr, col_idx, values = _shared_csr(n, [K, M, W1, W2])
+    fns = [Fn(F_ONE), Fn(F_ZPOW, 2, -1.0), Fn(F_SQRT, 0.0, 1j), Fn(F_SQRT, kappa2, 1j)]
+    reg = Region(272.5 + 15.0j, 57.5, 25.0, kind="rect", nx=nx)
+    return Problem(name, n, row_ptr, col_idx, values, fns, reg, N, L, probe(n, L, seed_u),
+                   meta=dict(gx=gx, gy=gy, alpha=alpha, beta=beta, w1=w1, w2=w2, kappa2=kappa2))
