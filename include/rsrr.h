@@ -154,22 +154,38 @@ typedef struct {
     void *callback_user;           /* passed to callback */
 } rsrr_nep;
 
-/* Region.  The ellipse phi(t) = center + a cos t + i b sin t is the contour
- * of the projected solve and defines "inside".  Sampling points are the
- * N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Eq. 58, Section 5.1)
- * for RSRR_REGION_ELLIPSE, the N given host points for RSRR_REGION_POINTS
- * (the rational interpolation approach lets them lie anywhere, Section 3.3),
- * or, for RSRR_REGION_INTERVAL, the N Chebyshev points of the first kind
- * z_i = center + a cos((2i + 1) pi / 2N) (Eq. 42) on the ellipse's major axis
- * (an interval of interest of a real NEP, Sections 3.3 and 5.1). */
-enum { RSRR_REGION_ELLIPSE = 0, RSRR_REGION_POINTS = 1, RSRR_REGION_INTERVAL = 2 };
+/* Region.  For every kind but RSRR_REGION_RECT the ellipse
+ * phi(t) = center + a cos t + i b sin t is the contour of the projected
+ * solve (N_Q-point trapezoid rule, Eq. 58) and defines "inside".  Sampling
+ * points are the N-point trapezoid nodes z_j = phi(2 pi (j + 1/2)/N) (Eq. 58,
+ * Section 5.1) for RSRR_REGION_ELLIPSE, the N given host points for
+ * RSRR_REGION_POINTS (the rational interpolation approach lets them lie
+ * anywhere, Section 3.3), or, for RSRR_REGION_INTERVAL, the N Chebyshev
+ * points of the first kind z_i = center + a cos((2i + 1) pi / 2N) (Eq. 42) on
+ * the ellipse's major axis (an interval of interest of a real NEP, Sections
+ * 3.3 and 5.1).
+ *
+ * RSRR_REGION_RECT (Section 5.4): the rectangle with vertices
+ * center +- a +- i b is the contour and the region (strict interior).
+ * Sampling points: Gauss-Legendre nodes on its sides, counterclockwise from
+ * the lower-left vertex -- nx on each side parallel to the real axis and
+ * ny = N/2 - nx on each of the other two (N even, 1 <= nx <= N/2 - 1; the
+ * paper's 27 and 13 for N = 80) -- or, when points is not NULL, the N given
+ * points.  The contour integrals of SS-FULL use composite Gauss quadrature:
+ * side s of length len_s is cut into max(1, round(N_Q len_s / (10 perimeter)))
+ * equal panels with the 10-point Gauss-Legendre rule each (about N_Q nodes).
+ * The moment weights of SS-RI and SSRR-M at the Gauss-Legendre sampling
+ * points are the contour weights dz/(2 pi). */
+enum { RSRR_REGION_ELLIPSE = 0, RSRR_REGION_POINTS = 1, RSRR_REGION_INTERVAL = 2, RSRR_REGION_RECT = 3 };
 
 typedef struct {
     int32_t kind;
-    int32_t reserved;
+    int32_t nx;               /* RSRR_REGION_RECT: points per horizontal side */
     rsrr_c128 center;
-    double a, b;              /* semi-axes along the real and imaginary axis, > 0 */
-    const rsrr_c128 *points;  /* host, N, only for RSRR_REGION_POINTS */
+    double a, b;              /* semi-axes (half-widths for the rectangle) along the
+                                 real and imaginary axis, > 0 */
+    const rsrr_c128 *points;  /* host, N: RSRR_REGION_POINTS, or RSRR_REGION_RECT's
+                                 explicit points (NULL: Gauss-Legendre nodes) */
 } rsrr_region;
 
 /* Precision of the factorisation.

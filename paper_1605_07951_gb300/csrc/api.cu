@@ -94,9 +94,115 @@ rsrr_status Handle::eval_terms(const cplx *zz, int64_t count, std::vector<cplx> 
     return RSRR_OK;
 }
 
+// Gauss-Legendre nodes (ascending) and weights of the n-point rule on [-1, 1]:
+// Newton's method on the Legendre polynomial P_n from the three-term
+// recurrence (k + 1) P_{k+1} = (2k + 1) x P_k - k P_{k-1}, started at the
+// asymptotic root estimates cos(pi (i + 3/4) / (n + 1/2)); with
+// P_n' = n (x P_n - P_{n-1}) / (x^2 - 1), the weights are
+// 2 / ((1 - x^2) P_n'(x)^2).
+static void legendre_at(int n, double t, double &pn, double &dpn) {
+    double p0 = 1.0, p1 = t;
+    for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = p1;
+    dpn = n * (t * p1 - p0) / (t * t - 1.0);
+}
+
+static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double t = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pn = 0.0, dpn = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            legendre_at(n, t, pn, dpn);
+            const double dt = pn / dpn;
+            t -= dt;
+            if (std::fabs(dt) <= 1e-15 * std::fabs(t) + 1e-300) break;
+        }
+        legendre_at(n, t, pn, dpn);
+        const double wt = 2.0 / ((1.0 - t * t) * dpn * dpn);
+        x[n - 1 - i] = t;
+        x[i] = -t;
+        w[i] = w[n - 1 - i] = wt;
+    }
+    if (n & 1) x[n / 2] = 0.0;
+}
+
+// the rectangle's vertices counterclockwise from center - a - i b (v[4] = v[0])
+static void rect_vertices(const rsrr_region &r, cplx v[5]) {
+    const cplx c(r.center.re, r.center.im);
+    v[0] = c + cplx(-r.a, -r.b);
+    v[1] = c + cplx(r.a, -r.b);
+    v[2] = c + cplx(r.a, r.b);
+    v[3] = c + cplx(-r.a, r.b);
+    v[4] = v[0];
+}
+
+// Gauss-Legendre nodes on the rectangle's sides (count[s] on side s, along
+// its direction) and the contour weights dz/(2 pi) = (q - p) w / (4 pi)
+static void rect_rule(const rsrr_region &r, const int count[4], std::vector<cplx> &z, std::vector<cplx> *wz) {
+    cplx v[5];
+    rect_vertices(r, v);
+    z.clear();
+    if (wz) wz->clear();
+    std::vector<double> x, w;
+    for (int sd = 0; sd < 4; ++sd) {
+        gauss_legendre(count[sd], x, w);
+        const cplx p = v[sd], q = v[sd + 1];
+        for (int k = 0; k < count[sd]; ++k) {
+            z.push_back(0.5 * (p + q) + 0.5 * (q - p) * x[k]);
+            if (wz) wz->push_back(0.5 * (q - p) * w[k] / (2.0 * M_PI));
+        }
+    }
+}
+
+void Handle::contour_quadrature(int NQ, std::vector<cplx> &zq, std::vector<cplx> &wq) const {
+    zq.clear();
+    wq.clear();
+    const cplx gamma(region.center.re, region.center.im);
+    if (region.kind != RSRR_REGION_RECT) {
+        for (int q = 0; q < NQ; ++q) {
+            const double t = 2.0 * M_PI * (q + 0.5) / NQ;
+            zq.push_back(gamma + cplx(region.a * std::cos(t), region.b * std::sin(t)));
+            wq.push_back(cplx(-region.a * std::sin(t), region.b * std::cos(t)) / (double)NQ);
+        }
+        return;
+    }
+    // composite Gauss: side s in max(1, round(NQ len_s / (10 perimeter))) equal
+    // panels with the 10-point rule each
+    constexpr int PANEL = 10;
+    std::vector<double> x, w;
+    gauss_legendre(PANEL, x, w);
+    cplx v[5];
+    rect_vertices(region, v);
+    const double per = 4.0 * (region.a + region.b);
+    for (int sd = 0; sd < 4; ++sd) {
+        const cplx p = v[sd], q = v[sd + 1];
+        const int P = std::max(1, (int)std::lround(NQ * std::abs(q - p) / (PANEL * per)));
+        for (int t = 0; t < P; ++t) {
+            const cplx a0 = p + (q - p) * ((double)t / P), a1 = p + (q - p) * ((double)(t + 1) / P);
+            for (int k = 0; k < PANEL; ++k) {
+                zq.push_back(0.5 * (a0 + a1) + 0.5 * (a1 - a0) * x[k]);
+                wq.push_back(0.5 * (a1 - a0) * w[k] / (2.0 * M_PI));
+            }
+        }
+    }
+}
+
+bool Handle::inside(cplx lam) const {
+    const double x = (lam.real() - region.center.re) / region.a;
+    const double y = (lam.imag() - region.center.im) / region.b;
+    if (region.kind == RSRR_REGION_RECT) return std::fabs(x) < 1.0 && std::fabs(y) < 1.0;
+    return x * x + y * y < 1.0;
+}
+
 // weights w_i of the moment methods (up to a common factor): trapezoid
 // weights (1/N) phi'(alpha_i) on the ellipse (Eq. 58), Chebyshev weights
-// (-1)^i sin((2i + 1) pi / 2N) on an interval (Eq. 43), otherwise the
+// (-1)^i sin((2i + 1) pi / 2N) on an interval (Eq. 43), the contour weights
+// dz/(2 pi) at Gauss-Legendre nodes on a rectangle (Section 5.4), otherwise the
 // barycentric weights 1 / prod_{j != i} (z_i - z_j) (Eq. 19) with every factor
 // scaled by 2 / rho and formed through logarithms
 void Handle::moment_weights(std::vector<cplx> &w) const {
@@ -114,6 +220,13 @@ void Handle::moment_weights(std::vector<cplx> &w) const {
     if (region.kind == RSRR_REGION_INTERVAL && !points_added) {
         for (int j = 0; j < n_; ++j)
             w[j] = cplx(((j & 1) ? -1.0 : 1.0) * std::sin((2.0 * j + 1.0) * M_PI / (2.0 * n_)), 0.0);
+        return;
+    }
+    if (rect_gl && !points_added) {  // Gauss-Legendre nodes: the contour weights dz / (2 pi)
+        const int ny = n_ / 2 - region.nx;
+        const int cnt[4] = {region.nx, ny, region.nx, ny};
+        std::vector<cplx> zz;
+        rect_rule(region, cnt, zz, &w);
         return;
     }
     std::vector<cplx> lw(n_);
@@ -335,10 +448,13 @@ static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts
     if (!(region->a > 0.0) || !(region->b > 0.0))
         return create_fail("rsrr_create: ellipse semi-axes must be > 0");
     if (region->kind != RSRR_REGION_ELLIPSE && region->kind != RSRR_REGION_POINTS &&
-        region->kind != RSRR_REGION_INTERVAL)
+        region->kind != RSRR_REGION_INTERVAL && region->kind != RSRR_REGION_RECT)
         return create_fail("rsrr_create: unknown region kind");
     if (region->kind == RSRR_REGION_POINTS && !region->points)
         return create_fail("rsrr_create: points region without points");
+    if (region->kind == RSRR_REGION_RECT && !region->points &&
+        (N < 4 || (N & 1) || region->nx < 1 || region->nx > N / 2 - 1))
+        return create_fail("rsrr_create: a rectangle needs N even and 1 <= nx <= N/2 - 1");
     const int prec = opts ? opts->precision : RSRR_PREC_MIXED;
     if (prec != RSRR_PREC_FP64 && prec != RSRR_PREC_MIXED)
         return create_fail("rsrr_create: unknown precision");
@@ -357,12 +473,20 @@ static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts
 }
 
 // step 1: the sampling points, trapezoid nodes on the ellipse (Eq. 58,
-// Section 5.1), the explicit points (any points, Section 3.3) or the
-// Chebyshev points of the first kind on the major axis (Eq. 42)
+// Section 5.1), the explicit points (any points, Section 3.3), the
+// Chebyshev points of the first kind on the major axis (Eq. 42) or
+// Gauss-Legendre nodes on the sides of a rectangle (Section 5.4)
 static void fill_points(Handle *h, const rsrr_region *region, int N) {
+    if (region->kind == RSRR_REGION_RECT && !region->points) {
+        const int ny = N / 2 - region->nx;
+        const int cnt[4] = {region->nx, ny, region->nx, ny};
+        rect_rule(*region, cnt, h->z, nullptr);
+        h->rect_gl = true;
+        return;
+    }
     h->z.resize(N);
     for (int j = 0; j < N; ++j) {
-        if (region->kind == RSRR_REGION_POINTS) {
+        if (region->kind == RSRR_REGION_POINTS || region->kind == RSRR_REGION_RECT) {
             h->z[j] = cplx(region->points[j].re, region->points[j].im);
         } else if (region->kind == RSRR_REGION_INTERVAL) {
             h->z[j] = cplx(region->center.re + region->a * std::cos((2.0 * j + 1.0) * M_PI / (2.0 * N)),
@@ -568,7 +692,10 @@ size_t Handle::estimate_bytes() {
     size_t b = device_bytes;
     device_bytes = 0;
     b += projection_ws_bytes(N * L, n, m);
-    b += ssfull_dev_bytes(std::min<int64_t>((int64_t)N * L, n), m, opts.NQ, opts.KQ);
+    // (composite Gauss on a rectangle rounds each side to whole panels: up to
+    // two more panels of 10 nodes than N_Q)
+    const int nq = region.kind == RSRR_REGION_RECT ? std::max(opts.NQ + 20, 40) : opts.NQ;
+    b += ssfull_dev_bytes(std::min<int64_t>((int64_t)N * L, n), m, nq, opts.KQ);
     b += sizeof(double2) * ((size_t)n + (size_t)N * L + 8) * 256 + (1u << 20);
     if (dense_terms) b += 2 * sizeof(double2) * (size_t)n * 256;  // A_i V and T(lambda) V
     return b;
@@ -1547,7 +1674,9 @@ rsrr_status prepare_dense(const rsrr_nep *nep, const rsrr_region *region, int32_
     }
     // Taylor terms about the centre: smallest P with (r_max rho)^P / P! < 1e-17;
     // the held terms are the powers (z - c)^p
-    const double x = rmax * std::max(region->a, region->b);
+    // (the region's radius about the centre: the half-diagonal of a rectangle)
+    const double x = rmax * (region->kind == RSRR_REGION_RECT ? std::hypot(region->a, region->b)
+                                                              : std::max(region->a, region->b));
     int P = 0;
     double term = 1.0;
     while (term >= 1e-17 && P < 200) { ++P; term *= x / P; }

@@ -1220,16 +1220,14 @@ rsrr_status Handle::solve(rsrr_result *out) {
         kb = NL;
     } else {
         // moments of T_Q^{-1} on the GPU, the rest of SS-FULL on the host; f of
-        // every held term at the N_Q trapezoid nodes (Eq. 58)
-        std::vector<cplx> zq(opts.NQ), fq;
-        for (int q = 0; q < opts.NQ; ++q) {
-            const double t = 2.0 * M_PI * (q + 0.5) / opts.NQ;
-            zq[q] = gamma + cplx(region.a * std::cos(t), region.b * std::sin(t));
-        }
-        rsrr_status est = eval_terms(zq.data(), opts.NQ, fq);
+        // every held term at the contour nodes (the N_Q trapezoid nodes of
+        // Eq. 58, or composite Gauss on a rectangle)
+        std::vector<cplx> zq, wq, fq;
+        contour_quadrature(opts.NQ, zq, wq);
+        rsrr_status est = eval_terms(zq.data(), (int64_t)zq.size(), fq);
         if (est != RSRR_OK) return est;
         std::vector<std::vector<cplx>> Am;
-        const rsrr_status mst = ssfull_moments(fq, opts.NQ, opts.KQ, Am);
+        const rsrr_status mst = ssfull_moments(fq, zq, wq, opts.KQ, Am);
         if (mst != RSRR_OK) return mst;
         if (ss_full_finish(Am, k, opts.KQ, gamma, std::max(region.a, region.b), opts.host_threads, lam, G,
                            nbar, gmax) != 0)
@@ -1315,9 +1313,7 @@ rsrr_status Handle::solve(rsrr_result *out) {
     struct Pair { cplx lam; double res; int c; };
     std::vector<Pair> keep;
     for (int c = 0; c < nbar; ++c) {
-        const double x = (lam[c].real() - region.center.re) / region.a;
-        const double y = (lam[c].imag() - region.center.im) / region.b;
-        if (!(x * x + y * y < 1.0)) continue;
+        if (!inside(lam[c])) continue;
         double scale = 0.0;
         if (dense && !dense_terms) scale = t1[c];  // ||T(lam)||_1 of the kernel computed directly
         else scale = residual_scale(flam.data() + (size_t)c * m);  // sum_u |f_u(lam)| ||A_u||_1

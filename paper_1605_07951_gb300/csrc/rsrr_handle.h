@@ -38,6 +38,7 @@ struct Handle {
     void *cb_user = nullptr;
     uint64_t seed = 0;                // default probe
     bool points_added = false;        // rsrr_add_points ran: the points are explicit
+    bool rect_gl = false;             // rectangle with Gauss-Legendre sampling points
     rsrr_region region = {};
     rsrr_opts opts = {};
     BandGeom geom = {};
@@ -185,11 +186,18 @@ struct Handle {
     double residual_scale(const std::complex<double> *f_held) const;
     // weights of the moment methods at the sampling points
     void moment_weights(std::vector<std::complex<double>> &w) const;
+    // nodes and weights dz/(2 pi) of the contour integrals of SS-FULL: the
+    // trapezoid rule on the ellipse or composite Gauss on the rectangle
+    void contour_quadrature(int NQ, std::vector<std::complex<double>> &zq,
+                            std::vector<std::complex<double>> &wq) const;
+    bool inside(std::complex<double> z) const;  // strict interior of the contour
     // SS-RI on the samples (rsrr_solve with RSRR_METHOD_SS_RI): eigenvalues
     // and the sample-space coefficients ZWB (N L x nbar) of v = S ZWB
     rsrr_status ss_ri(cudaStream_t s, std::vector<std::complex<double>> &lam,
                       std::vector<std::complex<double>> &ZWB, int &nbar, double &gmax);
-    rsrr_status ssfull_moments(const std::vector<std::complex<double>> &fq, int NQ, int KQ,
+    rsrr_status ssfull_moments(const std::vector<std::complex<double>> &fq,
+                               const std::vector<std::complex<double>> &zq,
+                               const std::vector<std::complex<double>> &wq, int KQ,
                                std::vector<std::vector<std::complex<double>>> &Am);
 };
 

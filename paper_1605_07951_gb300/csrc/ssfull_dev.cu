@@ -76,10 +76,13 @@ size_t ssfull_dev_bytes(int64_t k, int m, int NQ, int KQ) {
            sizeof(int32_t) * (B * k + B) + 8 * 256;
 }
 
-rsrr_status Handle::ssfull_moments(const std::vector<std::complex<double>> &fq, int NQ, int KQ,
+rsrr_status Handle::ssfull_moments(const std::vector<std::complex<double>> &fq,
+                                   const std::vector<std::complex<double>> &zq,
+                                   const std::vector<std::complex<double>> &wq, int KQ,
                                    std::vector<std::vector<std::complex<double>>> &Am) {
     using cplx = std::complex<double>;
     cudaStream_t s = hs;
+    const int NQ = (int)zq.size();
     const int nmom = 2 * KQ;
     const int64_t kk = (int64_t)k * k;
     const int B = ssfull_chunk(k, NQ, kSsfullChunkBytes);
@@ -109,7 +112,7 @@ rsrr_status Handle::ssfull_moments(const std::vector<std::complex<double>> &fq, 
     int32_t *dinfo = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * B));
     if ((size_t)(p - static_cast<char *>(buf)) > bytes) return fail(RSRR_ESTATE, "SS-FULL buffer layout");
 
-    const double a = region.a, b = region.b, rho = std::max(a, b);
+    const double rho = std::max(region.a, region.b);
     const cplx gamma(region.center.re, region.center.im);
     std::vector<double2> hf((size_t)B * m), hc((size_t)B * nmom);
     std::vector<int32_t> info(B);
@@ -119,9 +122,7 @@ rsrr_status Handle::ssfull_moments(const std::vector<std::complex<double>> &fq, 
         const int nb = std::min(B, NQ - q0);
         for (int bq = 0; bq < nb; ++bq) {
             const int q = q0 + bq;
-            const double t = 2.0 * M_PI * (q + 0.5) / NQ;
-            const cplx z = gamma + cplx(a * std::cos(t), b * std::sin(t));
-            const cplx w = cplx(-a * std::sin(t), b * std::cos(t)) / (double)NQ;
+            const cplx z = zq[q], w = wq[q];
             for (int i = 0; i < m; ++i) {
                 const cplx v = fq[(size_t)q * m + i];
                 hf[(size_t)bq * m + i] = make_double2(v.real(), v.imag());

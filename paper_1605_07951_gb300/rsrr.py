@@ -27,7 +27,7 @@ RSRR_OK, RSRR_EINVAL, RSRR_ENOMEM, RSRR_ESINGULAR = 0, -1, -2, -3
 RSRR_ENOCONV, RSRR_ETIMEOUT, RSRR_ECUDA, RSRR_ESTATE, RSRR_WGAP = -4, -5, -6, -7, 1
 (RSRR_F_ONE, RSRR_F_ZPOW, RSRR_F_RATIONAL, RSRR_F_INV, RSRR_F_SQRT, RSRR_F_EXP, RSRR_F_TAYLOR,
  RSRR_F_CALLBACK) = range(8)
-RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS, RSRR_REGION_INTERVAL = 0, 1, 2
+RSRR_REGION_ELLIPSE, RSRR_REGION_POINTS, RSRR_REGION_INTERVAL, RSRR_REGION_RECT = 0, 1, 2, 3
 RSRR_METHOD_RSRR, RSRR_METHOD_SSRR_M, RSRR_METHOD_SS_RI = 0, 1, 2
 RSRR_REFINE_IR, RSRR_REFINE_GMRES = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
@@ -66,7 +66,7 @@ class rsrr_nep(C.Structure):
 
 
 class rsrr_region(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("center", rsrr_c128),
+    _fields_ = [("kind", C.c_int32), ("nx", C.c_int32), ("center", rsrr_c128),
                 ("a", C.c_double), ("b", C.c_double), ("points", C.POINTER(rsrr_c128))]
 
 
@@ -282,6 +282,13 @@ def describe(prob):
         reg.points = pz.ctypes.data_as(C.POINTER(rsrr_c128))
     elif getattr(r, "kind", "ellipse") == "interval":
         reg.kind = RSRR_REGION_INTERVAL
+    elif getattr(r, "kind", "ellipse") == "rect":
+        reg.kind = RSRR_REGION_RECT
+        reg.nx = int(r.nx)
+        if getattr(r, "points", None) is not None:
+            pz = np.ascontiguousarray(np.asarray(r.points, dtype=np.complex128))
+            keep.append(pz)
+            reg.points = pz.ctypes.data_as(C.POINTER(rsrr_c128))
     else:
         reg.kind = RSRR_REGION_ELLIPSE
     return nep, reg, keep

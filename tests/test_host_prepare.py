@@ -35,7 +35,17 @@ FAMILIES = {
     "random_banded": lambda: W.random_banded(kl=5, ku=9),
     "loaded_string_points": lambda: W.loaded_string(),
     "loaded_string_interval": lambda: _interval_string(),
+    "gun_like_rect": lambda: W.gun_like(gx=24, gy=20),
+    "gun_like_rect_points": lambda: _rect_points(),
 }
+
+
+def _rect_points():
+    p = W.gun_like(gx=24, gy=20, N=8, nx=2)
+    r = p.region
+    p.region = W.Region(r.center, r.a, r.b, kind="rect", nx=2,
+                        points=np.array([250 + 1j, 260 - 2j, 300 + 5j, 320 + 0.5j, 230 + 3j, 228 + 1j, 290, 310 - 1j]))
+    return p
 
 
 def _interval_string():
@@ -190,3 +200,14 @@ def test_real_flag_halves_the_factor_storage(rsrr):
         c = rsrr.estimate_bytes(p, rsrr.default_opts(precision=prec))
         r = rsrr.estimate_bytes(p, rsrr.default_opts(precision=prec, flags=rsrr.RSRR_FLAG_REAL))
         assert r < c
+
+
+def test_rectangle_region_is_validated(rsrr):
+    """Gauss-Legendre points on a rectangle need N even and 1 <= nx <= N/2 - 1."""
+    for N, nx in ((81, 27), (80, 0), (80, 40), (2, 1)):
+        p = W.gun_like(gx=12, gy=10, N=N, nx=nx)
+        with pytest.raises(rsrr.RSRRError) as e:
+            rsrr.prepared(p)
+        assert e.value.status == rsrr.RSRR_EINVAL
+    z, _, _ = rsrr.prepared(W.gun_like(gx=12, gy=10, N=80, nx=39))
+    assert len(z) == 80
