@@ -239,8 +239,18 @@ enum {
     RSRR_FLAG_GRAPH = 16,
     RSRR_FLAG_AUTOTUNE = 32,
     RSRR_FLAG_WIDE_SOLVE_ONLY = 64,
-    RSRR_FLAG_REAL = 128
+    RSRR_FLAG_REAL = 128,
+    RSRR_FLAG_CHUNK_POINTS = 256
 };
+/* RSRR_FLAG_CHUNK_POINTS (band path, with mem_budget_bytes > 0): when the
+ * handle would exceed the budget, rsrr_create sizes the band factor storage
+ * (factors, block inverses and permutations, residual and correction
+ * buffers) for as many sampling points as fit, and rsrr_sample factors,
+ * solves and refines the points chunk by chunk through that storage; S, the
+ * backward errors and everything after sampling are those of the whole
+ * handle (the factors of a point are not kept after its chunk).  ENOMEM only
+ * if not even one point fits.  Such a handle is refused by
+ * rsrr_sample_batch; RSRR_FLAG_AUTOTUNE is ignored. */
 /* RSRR_FLAG_REAL: real arithmetic for a real NEP at real sampling points
  * (Sections 3.3 and 5.1: real points, e.g. the Chebyshev points of an
  * RSRR_REGION_INTERVAL, keep T(z_j) real and halve the time and memory of
@@ -298,11 +308,18 @@ typedef struct {
     uint64_t seed;       /* seed of the default probe U (complex normal entries from
                             a splitmix64 stream); rsrr_set_probe replaces U */
     int64_t mem_budget_bytes; /* > 0: rsrr_create refuses (ENOMEM) a handle whose
-                            rsrr_estimate_bytes exceed it; 0 (default): no limit */
+                            rsrr_estimate_bytes exceed it, or with
+                            RSRR_FLAG_CHUNK_POINTS samples the points in chunks
+                            that fit; 0 (default): no limit */
     int32_t method;      /* RSRR_METHOD_*, default RSRR_METHOD_RSRR */
     int32_t K;           /* moments of SSRR-M and SS-RI (1 <= K <= N), default 2 */
     int32_t refine;      /* RSRR_REFINE_*, default RSRR_REFINE_IR (band path, mixed precision) */
     int32_t gmres_m;     /* Krylov steps per GMRES cycle (1 .. 16), default 4 */
+    int32_t chunk_points;/* band path: > 0 holds the band factor storage of at most
+                            this many points and samples the points in chunks of
+                            that many (as RSRR_FLAG_CHUNK_POINTS does to fit a
+                            budget); 0 (default): all N points at once */
+    int32_t reserved;
 } rsrr_opts;
 
 /* Refinement of the mixed-precision samples (band path):

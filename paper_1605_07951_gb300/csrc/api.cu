@@ -358,6 +358,8 @@ void rsrr_opts_default(rsrr_opts *o) {
     o->K = 2;
     o->refine = RSRR_REFINE_IR;
     o->gmres_m = 4;
+    o->chunk_points = 0;
+    o->reserved = 0;
 }
 
 static rsrr_status create_fail(const char *msg) {
@@ -378,8 +380,21 @@ rsrr_status rsrr_create(const rsrr_nep *nep, const rsrr_region *region, int32_t 
     rsrr_status st = rsrr::prepare(nep, region, N, L, opts, &h);
     if (st != RSRR_OK) return st;
     if (h->opts.mem_budget_bytes > 0) {
-        const size_t need = h->estimate_bytes();
-        if (need > (size_t)h->opts.mem_budget_bytes) {
+        size_t need = h->estimate_bytes();
+        const size_t budget = (size_t)h->opts.mem_budget_bytes;
+        if (need > budget && (h->opts.flags & RSRR_FLAG_CHUNK_POINTS) && !h->dense && h->N > 1) {
+            // the band storage of as many points as fit: need(f) is affine in f
+            h->fcap = 1;
+            const size_t need1 = h->estimate_bytes();
+            h->fcap = 2;
+            const size_t per = h->estimate_bytes() - need1;
+            h->fcap = 1;
+            if (need1 <= budget && per > 0)
+                h->fcap = (int)std::min<size_t>((size_t)h->N, 1 + (budget - need1) / per);
+            while (h->fcap > 1 && h->estimate_bytes() > budget) --h->fcap;
+            need = h->estimate_bytes();
+        }
+        if (need > budget) {
             char buf[160];
             snprintf(buf, sizeof buf, "rsrr_create: the handle needs %zu device bytes, mem_budget_bytes is %lld",
                      need, (long long)h->opts.mem_budget_bytes);
@@ -469,6 +484,7 @@ static rsrr_status check_common(const rsrr_region *region, const rsrr_opts *opts
         return create_fail("rsrr_create: unknown refinement");
     if (opts && opts->refine == RSRR_REFINE_GMRES && (opts->gmres_m < 1 || opts->gmres_m > 16))
         return create_fail("rsrr_create: gmres_m out of range (1 .. 16)");
+    if (opts && opts->chunk_points < 0) return create_fail("rsrr_create: negative chunk_points");
     return RSRR_OK;
 }
 
@@ -520,6 +536,8 @@ static Handle *new_handle(const rsrr_nep *nep, const rsrr_region *region, int N,
     h->seed = h->opts.seed;
     h->n = nep->n;
     h->N = N;
+    h->fcap = N;
+    if (nep->kind == RSRR_NEP_SPARSE && h->opts.chunk_points > 0) h->fcap = std::min(N, h->opts.chunk_points);
     h->L = L;
     h->region = *region;
     h->region.points = nullptr;
@@ -743,8 +761,10 @@ rsrr_status rsrr_sample_batch(rsrr_t *const *handles, int32_t count, void *strea
     std::vector<Handle *> hs_(count);
     for (int i = 0; i < count; ++i) {
         hs_[i] = reinterpret_cast<Handle *>(handles[i]);
-        if (!hs_[i] || hs_[i]->dense || hs_[i]->real) {
-            rsrr::thread_error() = "rsrr_sample_batch: every handle must be a complex band-path (sparse kind) handle";
+        if (!hs_[i] || hs_[i]->dense || hs_[i]->real || hs_[i]->chunked()) {
+            rsrr::thread_error() =
+                "rsrr_sample_batch: every handle must be a complex band-path (sparse kind) handle "
+                "holding the factors of all its points";
             return RSRR_EINVAL;
         }
         for (int j = 0; j < i; ++j)
@@ -954,7 +974,7 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
     CK(alloc(&d_done, N), "alloc");
     CK(alloc(&d_sweep_flags, opts.max_refine + 2), "alloc");
     CK(alloc(&d_tmo, 1), "alloc");
-    const size_t band = (size_t)geom.ldab * n * N;
+    const size_t band = (size_t)geom.ldab * n * fcap;
     {
         const bool mx = opts.precision == RSRR_PREC_MIXED;
         const size_t smem2 = real ? (mx ? band_solve2_smem_r32(geom) : band_solve2_smem_r64(geom))
@@ -964,30 +984,30 @@ rsrr_status Handle::allocate_and_upload(const std::vector<double2> &coef) {
         use_solve2 = solve2;
         cluster_lu = !(opts.flags & RSRR_FLAG_ONE_CTA_LU);
         if (solve2) {
-            CK(alloc(&d_bperm, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb),
+            CK(alloc(&d_bperm, (size_t)fcap * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb),
                "alloc block permutations");
             CK(alloc(&d_gate, 1), "alloc");
         }
     }
-    const size_t dinv_n = (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb;
+    const size_t dinv_n = (size_t)fcap * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb;
     if (real && opts.precision == RSRR_PREC_MIXED) {
         CK(alloc(&d_abr32, band), "alloc band factors (float)");
         CK(alloc(&d_dinvr32, dinv_n), "alloc block inverses");
-        CK(alloc(&d_R, nL * N), "alloc residual");
-        CK(alloc(&d_Dr32, nL * N), "alloc correction");
+        CK(alloc(&d_R, nL * fcap), "alloc residual");
+        CK(alloc(&d_Dr32, nL * fcap), "alloc correction");
     } else if (real) {
         CK(alloc(&d_abr64, band), "alloc band factors (double)");
         CK(alloc(&d_dinvr64, dinv_n), "alloc block inverses");
-        CK(alloc(&d_Dr64, nL * N), "alloc real solve buffer");
+        CK(alloc(&d_Dr64, nL * fcap), "alloc real solve buffer");
     } else if (opts.precision == RSRR_PREC_MIXED) {
         CK(alloc(&d_ab32, band), "alloc band factors (complex64)");
-        CK(alloc(&d_dinv32, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
+        CK(alloc(&d_dinv32, dinv_n),
            "alloc block inverses");
-        CK(alloc(&d_R, nL * N), "alloc residual");
-        CK(alloc(&d_D, nL * N), "alloc correction");
+        CK(alloc(&d_R, nL * fcap), "alloc residual");
+        CK(alloc(&d_D, nL * fcap), "alloc correction");
     } else {
         CK(alloc(&d_ab64, band), "alloc band factors (complex128)");
-        CK(alloc(&d_dinv64, (size_t)N * ((n + geom.nb - 1) / geom.nb) * 2 * geom.nb * geom.nb),
+        CK(alloc(&d_dinv64, dinv_n),
            "alloc block inverses");
     }
     if (dry) return RSRR_OK;
@@ -1037,13 +1057,13 @@ cudaError_t Handle::band_solve(bool mixed, void *B, const int32_t *skip, int p0,
     const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
     const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
     if (mixed)
-        return use_solve2 ? launch_band_solve2_c64(d_ab32 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv32 + p0 * dv_pt,
+        return use_solve2 ? launch_band_solve2_c64(d_ab32 + fo(p0) * ab_pt, d_bperm + fo(p0) * bp_pt, d_dinv32 + fo(p0) * dv_pt,
                                                static_cast<float2 *>(B), geom, np, nn, L, skip, s)
-                      : launch_band_solve_c64(d_ab32 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv32 + p0 * dv_pt,
+                      : launch_band_solve_c64(d_ab32 + fo(p0) * ab_pt, d_piv + (size_t)p0 * n, d_dinv32 + fo(p0) * dv_pt,
                                               static_cast<float2 *>(B), geom, np, nn, L, skip, s);
-    return use_solve2 ? launch_band_solve2_c128(d_ab64 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinv64 + p0 * dv_pt,
+    return use_solve2 ? launch_band_solve2_c128(d_ab64 + fo(p0) * ab_pt, d_bperm + fo(p0) * bp_pt, d_dinv64 + fo(p0) * dv_pt,
                                             static_cast<double2 *>(B), geom, np, nn, L, skip, s)
-                  : launch_band_solve_c128(d_ab64 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinv64 + p0 * dv_pt,
+                  : launch_band_solve_c128(d_ab64 + fo(p0) * ab_pt, d_piv + (size_t)p0 * n, d_dinv64 + fo(p0) * dv_pt,
                                            static_cast<double2 *>(B), geom, np, nn, L, skip, s);
 }
 
@@ -1055,13 +1075,13 @@ cudaError_t Handle::real_solve(bool mixed, void *B, const int32_t *skip, int p0,
     const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
     const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
     if (mixed)
-        return use_solve2 ? launch_band_solve2_r32(d_abr32 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinvr32 + p0 * dv_pt,
+        return use_solve2 ? launch_band_solve2_r32(d_abr32 + fo(p0) * ab_pt, d_bperm + fo(p0) * bp_pt, d_dinvr32 + fo(p0) * dv_pt,
                                                    static_cast<float *>(B), geom, np, nn, L, skip, s)
-                          : launch_band_solve_r32(d_abr32 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinvr32 + p0 * dv_pt,
+                          : launch_band_solve_r32(d_abr32 + fo(p0) * ab_pt, d_piv + (size_t)p0 * n, d_dinvr32 + fo(p0) * dv_pt,
                                                   static_cast<float *>(B), geom, np, nn, L, skip, s);
-    return use_solve2 ? launch_band_solve2_r64(d_abr64 + p0 * ab_pt, d_bperm + p0 * bp_pt, d_dinvr64 + p0 * dv_pt,
+    return use_solve2 ? launch_band_solve2_r64(d_abr64 + fo(p0) * ab_pt, d_bperm + fo(p0) * bp_pt, d_dinvr64 + fo(p0) * dv_pt,
                                                static_cast<double *>(B), geom, np, nn, L, skip, s)
-                      : launch_band_solve_r64(d_abr64 + p0 * ab_pt, d_piv + (size_t)p0 * n, d_dinvr64 + p0 * dv_pt,
+                      : launch_band_solve_r64(d_abr64 + fo(p0) * ab_pt, d_piv + (size_t)p0 * n, d_dinvr64 + fo(p0) * dv_pt,
                                               static_cast<double *>(B), geom, np, nn, L, skip, s);
 }
 
@@ -1074,8 +1094,8 @@ cudaError_t Handle::sweep_solve(float2 *B, const int32_t *skip, int p0, int np, 
     const size_t ab_pt = (size_t)geom.ldab * n;
     const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
     const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
-    const float2 *ab = d_ab32 + p0 * ab_pt, *dv = d_dinv32 + p0 * dv_pt;
-    const int32_t *bp = d_bperm + p0 * bp_pt;
+    const float2 *ab = d_ab32 + fo(p0) * ab_pt, *dv = d_dinv32 + fo(p0) * dv_pt;
+    const int32_t *bp = d_bperm + fo(p0) * bp_pt;
     cudaError_t e = launch_solve_gate(skip, np, thr, d_gate, s);
     if (e == cudaSuccess) e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, false, d_gate, 0);
     if (e == cudaSuccess) e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, true, d_gate, 1);
@@ -1109,8 +1129,8 @@ rsrr_status Handle::refine_gmres(int p0, int np, const DevProblem &dq, cudaStrea
     int32_t *done = d_done + p0;
     double *tnorm = d_tnorm + p0, *eta = d_eta + (size_t)p0 * L;
     double *rmax = d_rmax + (size_t)p0 * L, *xmax = d_xmax + (size_t)p0 * L;
-    double2 *X = d_X + p0 * per_pt, *R = d_R + p0 * per_pt;
-    float2 *D = d_D + p0 * per_pt;
+    double2 *X = d_X + p0 * per_pt, *R = d_R + fo(p0) * per_pt;
+    float2 *D = d_D + fo(p0) * per_pt;
     auto Vj = [&](int j) { return d_gV + (size_t)j * vec + p0 * per_pt; };
     auto Zj = [&](int j) { return d_gZ + (size_t)j * vec + p0 * per_pt; };
     double2 *H = d_gH;        // (i, j) block of nc entries at (i m + j) NL
@@ -1200,12 +1220,25 @@ rsrr_status Handle::refine_gmres(int p0, int np, const DevProblem &dq, cudaStrea
 
 rsrr_status Handle::sample(cudaStream_t s) {
     if (dense) return sample_dense(0, N, s);
-    if ((opts.flags & RSRR_FLAG_AUTOTUNE) && !tuned && !real) {
+    if ((opts.flags & RSRR_FLAG_AUTOTUNE) && !tuned && !real && !chunked()) {
         rsrr_status st = autotune(s);
         if (st != RSRR_OK) return st;
     }
     if (opts.flags & RSRR_FLAG_GRAPH) return sample_graph(s);
-    return sample_band(0, N, s);
+    return sample_range(0, N, s);
+}
+
+rsrr_status Handle::sample_range(int p0, int np, cudaStream_t s) {
+    if (!chunked()) return sample_band(p0, np, s);
+    // chunks of fcap points through the same band storage; the stream orders
+    // each chunk's factorisation after the previous chunk's last solve
+    rsrr_status st = RSRR_OK;
+    for (int q = p0; q < p0 + np && st == RSRR_OK; q += fcap) {
+        fbase = q;
+        st = sample_band(q, std::min(fcap, p0 + np - q), s);
+    }
+    fbase = 0;
+    return st;
 }
 
 namespace {
@@ -1308,15 +1341,15 @@ rsrr_status Handle::sample_graph(cudaStream_t s) {
         timed_sample = opts.timing != 0;
         return RSRR_OK;
     }
-    if (graph_failed || s == nullptr || graph_calls++ == 0) return sample_band(0, N, s);
+    if (graph_failed || s == nullptr || graph_calls++ == 0) return sample_range(0, N, s);
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         cudaGetLastError();
         graph_failed = true;
-        return sample_band(0, N, s);
+        return sample_range(0, N, s);
     }
     const int64_t l0 = launches;
-    const rsrr_status st = sample_band(0, N, s);
+    const rsrr_status st = sample_range(0, N, s);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     if (st != RSRR_OK || e != cudaSuccess || !g) {
@@ -1324,7 +1357,7 @@ rsrr_status Handle::sample_graph(cudaStream_t s) {
         cudaGetLastError();
         graph_failed = true;
         launches = l0;
-        return sample_band(0, N, s);
+        return sample_range(0, N, s);
     }
     graph = g;
     graph_launches = launches - l0;
@@ -1333,7 +1366,7 @@ rsrr_status Handle::sample_graph(cudaStream_t s) {
         cudaGetLastError();
         drop_graph();
         graph_failed = true;
-        return sample_band(0, N, s);
+        return sample_range(0, N, s);
     }
     CK(cudaGraphLaunch(graph_exec, s), "graph launch");
     launches += graph_launches;
@@ -1369,21 +1402,21 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
         }
         CK(launch_tnorm(tnorm, dq, s), "tnorm");
         if (real && opts.precision == RSRR_PREC_MIXED)
-            CK(launch_assemble<float>(d_abr32 + p0 * ab_pt, geom, dq, s), "assemble");
-        else if (real) CK(launch_assemble<double>(d_abr64 + p0 * ab_pt, geom, dq, s), "assemble");
+            CK(launch_assemble<float>(d_abr32 + fo(p0) * ab_pt, geom, dq, s), "assemble");
+        else if (real) CK(launch_assemble<double>(d_abr64 + fo(p0) * ab_pt, geom, dq, s), "assemble");
         else if (opts.precision == RSRR_PREC_MIXED)
-            CK(launch_assemble<float2>(d_ab32 + p0 * ab_pt, geom, dq, s), "assemble");
-        else CK(launch_assemble<double2>(d_ab64 + p0 * ab_pt, geom, dq, s), "assemble");
+            CK(launch_assemble<float2>(d_ab32 + fo(p0) * ab_pt, geom, dq, s), "assemble");
+        else CK(launch_assemble<double2>(d_ab64 + fo(p0) * ab_pt, geom, dq, s), "assemble");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
         if (phase == 1) return RSRR_OK;  // the caller factors (grouped LU of rsrr_sample_batch)
     }
     if (real && opts.precision == RSRR_PREC_MIXED) {
         // real float factors, FP64 complex residuals (zero imaginary parts)
-        float *ab = d_abr32 + p0 * ab_pt, *D = d_Dr32 + p0 * per_pt;
-        double2 *R = d_R + p0 * per_pt;
-        CK(launch_band_lu_r32(ab, piv, info, d_dinvr32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+        float *ab = d_abr32 + fo(p0) * ab_pt, *D = d_Dr32 + fo(p0) * per_pt;
+        double2 *R = d_R + fo(p0) * per_pt;
+        CK(launch_band_lu_r32(ab, piv, info, d_dinvr32 + fo(p0) * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (use_solve2) {
-            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
+            CK(launch_block_perm(d_bperm + fo(p0) * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
@@ -1403,10 +1436,10 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
             launches += 5;
         }
     } else if (real) {
-        double *ab = d_abr64 + p0 * ab_pt, *D = d_Dr64 + p0 * per_pt;
-        CK(launch_band_lu_r64(ab, piv, info, d_dinvr64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+        double *ab = d_abr64 + fo(p0) * ab_pt, *D = d_Dr64 + fo(p0) * per_pt;
+        CK(launch_band_lu_r64(ab, piv, info, d_dinvr64 + fo(p0) * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (use_solve2) {
-            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
+            CK(launch_block_perm(d_bperm + fo(p0) * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
@@ -1416,12 +1449,12 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
         launches += 5;  // assemble, LU, probe, solve, widen
     } else if (opts.precision == RSRR_PREC_MIXED) {
-        float2 *ab = d_ab32 + p0 * ab_pt, *D = d_D + p0 * per_pt;
-        double2 *R = d_R + p0 * per_pt;
+        float2 *ab = d_ab32 + fo(p0) * ab_pt, *D = d_D + fo(p0) * per_pt;
+        double2 *R = d_R + fo(p0) * per_pt;
         if (phase == 0)
-            CK(launch_band_lu_c64(ab, piv, info, d_dinv32 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+            CK(launch_band_lu_c64(ab, piv, info, d_dinv32 + fo(p0) * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (use_solve2) {
-            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
+            CK(launch_block_perm(d_bperm + fo(p0) * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
@@ -1444,11 +1477,11 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
             launches += 5;
         }
     } else {
-        double2 *ab = d_ab64 + p0 * ab_pt;
+        double2 *ab = d_ab64 + fo(p0) * ab_pt;
         if (phase == 0)
-            CK(launch_band_lu_c128(ab, piv, info, d_dinv64 + p0 * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
+            CK(launch_band_lu_c128(ab, piv, info, d_dinv64 + fo(p0) * dv_pt, geom, np, nn, s, cluster_lu), "band LU");
         if (use_solve2) {
-            CK(launch_block_perm(d_bperm + p0 * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
+            CK(launch_block_perm(d_bperm + fo(p0) * bp_pt, piv, nn, geom.kl, geom.nb, np, s), "block permutations");
             launches += 1;
         }
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
@@ -1530,8 +1563,9 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
     CK(regrow(&d_rmax, (size_t)L, N0, N1, false), "regrow");
     CK(regrow(&d_xmax, (size_t)L, N0, N1, false), "regrow");
     CK(regrow(&d_done, 1, N0, N1, false), "regrow");
-    if (d_R) CK(regrow(&d_R, per_pt, N0, N1, false), "regrow");
-    if (d_D) CK(regrow(&d_D, per_pt, N0, N1, false), "regrow");
+    const bool grow_factors = !chunked();  // chunked: the new points reuse the chunk storage
+    if (d_R && grow_factors) CK(regrow(&d_R, per_pt, N0, N1, false), "regrow");
+    if (d_D && grow_factors) CK(regrow(&d_D, per_pt, N0, N1, false), "regrow");
     if (!dense || dense_terms) CK(regrow(&d_coef, (size_t)m, N0, N1, true), "regrow");
     if (dense) {
         const size_t nn2 = (size_t)n * n;
@@ -1546,7 +1580,7 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
             CK(regrow(&d_ab64, nn2, N0, N1, false), "regrow dense factors");
             CK(regrow(&d_dinv64, dv_pt, N0, N1, false), "regrow");
         }
-    } else {
+    } else if (grow_factors) {
         const size_t ab_pt = (size_t)geom.ldab * n;
         const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
         if (mixed) {
@@ -1558,6 +1592,7 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
         }
         if (d_bperm) CK(regrow(&d_bperm, nblk * 2 * geom.nb, N0, N1, false), "regrow");
     }
+    if (grow_factors) fcap = N1;
     drop_graph();  // the captured launches name the old buffers
     // the projection's work space is sized by N L: rebuilt by the next rsrr_project
     if (proj_ws) {
@@ -1586,7 +1621,7 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
     dp.coef = d_coef;
     projected = false;
     solved = false;
-    return dense ? sample_dense(N0, count, s) : sample_band(N0, count, s);
+    return dense ? sample_dense(N0, count, s) : sample_range(N0, count, s);
 }
 
 rsrr_status Handle::read_outcome() {
@@ -1765,7 +1800,7 @@ rsrr_status Handle::allocate_dense() {
     CK(alloc(&d_U, nL), "alloc");
     CK(alloc(&d_umax, L), "alloc");
     CK(alloc(&d_X, nL * N), "alloc S");
-    CK(alloc(&d_R, nL * N), "alloc residual");
+    CK(alloc(&d_R, nL * fcap), "alloc residual");
     CK(alloc(&d_piv, (size_t)n * N), "alloc pivots");
     CK(alloc(&d_info, N), "alloc");
     CK(alloc(&d_tnorm, N), "alloc");
@@ -1784,7 +1819,7 @@ rsrr_status Handle::allocate_dense() {
     }
     if (mixed) {
         CK(alloc(&d_A32, nn2 * N), "alloc dense factors (complex64)");
-        CK(alloc(&d_D, nL * N), "alloc correction");
+        CK(alloc(&d_D, nL * fcap), "alloc correction");
         CK(alloc(&d_dinv32, (size_t)N * nblk * 2 * nb * nb), "alloc block inverses");
     } else {
         CK(alloc(&d_ab64, nn2 * N), "alloc dense factors (complex128)");
@@ -1880,15 +1915,15 @@ rsrr_status Handle::sample_dense(int p0, int np, cudaStream_t s) {
     CK(launch_dense_tnorm(tnorm, T64, nn, np, s), "tnorm");
     launches += 2;
     if (mixed) {
-        float2 *A32 = d_A32 + p0 * nn2, *D = d_D + p0 * per_pt;
+        float2 *A32 = d_A32 + p0 * nn2, *D = d_D + fo(p0) * per_pt;
         CK(launch_narrow_all(A32, T64, total, s), "narrow");
         launches += 1;
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_dense_lu_c64(A32, piv, info, d_dinv32 + p0 * dv_pt, nn, np, s, &launches, d_tmo,
+        CK(launch_dense_lu_c64(A32, piv, info, d_dinv32 + fo(p0) * dv_pt, nn, np, s, &launches, d_tmo,
                                !(opts.flags & RSRR_FLAG_SIMT_DENSE_UPDATE)), "dense LU");
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c64(D, d_U, per_pt, np, s), "probe");
-        CK(launch_dense_solve_c64(A32, piv, d_dinv32 + p0 * dv_pt, D, nn, np, L, nullptr, s), "dense solve");
+        CK(launch_dense_solve_c64(A32, piv, d_dinv32 + fo(p0) * dv_pt, D, nn, np, L, nullptr, s), "dense solve");
         CK(launch_widen(X, D, per_pt * np, s), "widen");
         CK(cudaMemsetAsync(done, 0, sizeof(int32_t) * np, s), "memset");
         launches += 3;
@@ -1897,8 +1932,8 @@ rsrr_status Handle::sample_dense(int p0, int np, cudaStream_t s) {
             if ((ms = dense_residual(true, p0, np, s)) != RSRR_OK) return ms;
             CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol, d_sweep_flags + it, done, s),
                "eta");
-            CK(launch_narrow(D, d_R + p0 * per_pt, per_pt, np, done, s), "narrow");
-            CK(launch_dense_solve_c64(A32, piv, d_dinv32 + p0 * dv_pt, D, nn, np, L, done, s), "dense solve");
+            CK(launch_narrow(D, d_R + fo(p0) * per_pt, per_pt, np, done, s), "narrow");
+            CK(launch_dense_solve_c64(A32, piv, d_dinv32 + fo(p0) * dv_pt, D, nn, np, L, done, s), "dense solve");
             CK(launch_update(X, D, per_pt, np, done, s), "update");
             launches += 4;
         }
@@ -1906,10 +1941,10 @@ rsrr_status Handle::sample_dense(int p0, int np, cudaStream_t s) {
         double2 *A64 = d_ab64 + p0 * nn2;
         CK(cudaMemcpyAsync(A64, T64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s), "copy");
         if ((ms = mark(1, s)) != RSRR_OK) return ms;
-        CK(launch_dense_lu_c128(A64, piv, info, d_dinv64 + p0 * dv_pt, nn, np, s, &launches), "dense LU");
+        CK(launch_dense_lu_c128(A64, piv, info, d_dinv64 + fo(p0) * dv_pt, nn, np, s, &launches), "dense LU");
         if ((ms = mark(2, s)) != RSRR_OK) return ms;
         CK(launch_broadcast_probe_c128(X, d_U, per_pt, np, s), "probe");
-        CK(launch_dense_solve_c128(A64, piv, d_dinv64 + p0 * dv_pt, X, nn, np, L, nullptr, s), "dense solve");
+        CK(launch_dense_solve_c128(A64, piv, d_dinv64 + fo(p0) * dv_pt, X, nn, np, L, nullptr, s), "dense solve");
         launches += 2;
         if ((ms = mark(3, s)) != RSRR_OK) return ms;
     }

@@ -39,6 +39,13 @@ struct Handle {
     uint64_t seed = 0;                // default probe
     bool points_added = false;        // rsrr_add_points ran: the points are explicit
     bool rect_gl = false;             // rectangle with Gauss-Legendre sampling points
+    // band factor storage (factors, block inverses and permutations, residual
+    // and correction buffers) holds fcap points; with fcap < N
+    // (RSRR_FLAG_CHUNK_POINTS) the points are sampled in chunks of fcap and
+    // the storage starts at point fbase of the chunk being sampled
+    int fcap = 0, fbase = 0;
+    bool chunked() const { return fcap < N; }
+    int64_t fo(int p0) const { return (int64_t)p0 - fbase; }
     rsrr_region region = {};
     rsrr_opts opts = {};
     BandGeom geom = {};
@@ -158,6 +165,8 @@ struct Handle {
     // phase 0: everything; 1: up to the assembly (the caller factors); 2: from
     // after the LU (the caller factored)
     rsrr_status sample_band(int p0, int np, cudaStream_t s, int phase = 0);
+    // points p0 .. p0+np-1 through sample_band, chunk by chunk when chunked()
+    rsrr_status sample_range(int p0, int np, cudaStream_t s);
     // GMRES refinement cycles of points p0 .. p0+np-1 (mixed band path)
     rsrr_status refine_gmres(int p0, int np, const DevProblem &dq, cudaStream_t s);
     cudaError_t band_solve(bool mixed, void *B, const int32_t *skip, int p0, int np, cudaStream_t s);

@@ -33,7 +33,8 @@ RSRR_REFINE_IR, RSRR_REFINE_GMRES = 0, 1
 RSRR_PREC_FP64, RSRR_PREC_MIXED = 0, 1
 RSRR_GEMM_AUTO, RSRR_GEMM_FP64, RSRR_GEMM_OZAKI, RSRR_GEMM_OZAKI_MMA = 0, 1, 2, 3
 (RSRR_FLAG_PLAIN_SOLVE, RSRR_FLAG_ONE_CTA_LU, RSRR_FLAG_INJECT_TIMEOUT, RSRR_FLAG_SIMT_DENSE_UPDATE,
- RSRR_FLAG_GRAPH, RSRR_FLAG_AUTOTUNE, RSRR_FLAG_WIDE_SOLVE_ONLY, RSRR_FLAG_REAL) = 1, 2, 4, 8, 16, 32, 64, 128
+ RSRR_FLAG_GRAPH, RSRR_FLAG_AUTOTUNE, RSRR_FLAG_WIDE_SOLVE_ONLY, RSRR_FLAG_REAL,
+ RSRR_FLAG_CHUNK_POINTS) = 1, 2, 4, 8, 16, 32, 64, 128, 256
 RSRR_NEP_SPARSE, RSRR_NEP_HELMHOLTZ, RSRR_NEP_DENSE = 0, 1, 2
 RSRR_MAX_TERMS = 8
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV",
@@ -76,7 +77,8 @@ class rsrr_opts(C.Structure):
                 ("res_tol", C.c_double), ("NQ", C.c_int32), ("KQ", C.c_int32),
                 ("host_threads", C.c_int32), ("timing", C.c_int32), ("gemm", C.c_int32),
                 ("flags", C.c_int32), ("seed", C.c_uint64), ("mem_budget_bytes", C.c_int64),
-                ("method", C.c_int32), ("K", C.c_int32), ("refine", C.c_int32), ("gmres_m", C.c_int32)]
+                ("method", C.c_int32), ("K", C.c_int32), ("refine", C.c_int32), ("gmres_m", C.c_int32),
+                ("chunk_points", C.c_int32), ("reserved", C.c_int32)]
 
 
 class rsrr_stats(C.Structure):

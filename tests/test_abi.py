@@ -161,3 +161,14 @@ def test_create_refuses_a_handle_above_its_memory_budget(lib):
         rsrr.Solver(p, rsrr.default_opts(mem_budget_bytes=need - 1))
     assert e.value.status == rsrr.RSRR_ENOMEM
     assert "mem_budget_bytes" in str(e.value)
+
+
+def test_chunked_band_storage_is_smaller(lib):
+    """opts.chunk_points holds the band factor storage of a chunk of points
+    (rsrr_estimate_bytes counts it without a GPU)."""
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    p = W.rational_grid(g=40, N=16, L=4)
+    full = rsrr.estimate_bytes(p)
+    ch = [rsrr.estimate_bytes(p, rsrr.default_opts(chunk_points=c)) for c in (1, 4, 16, 64)]
+    assert ch[0] < ch[1] < ch[2] == ch[3] == full
