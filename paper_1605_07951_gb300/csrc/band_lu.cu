@@ -44,11 +44,16 @@ struct LuSm {
     using R = typename real_of<C>::type;
     static constexpr int CW = (TH / 32) * CB;
     static constexpr int PRA = NB + 32 * RA;  // allocated panel rows (>= NB + kl)
-    C *P;      // [NB][PRA], column major
+    // padded strides: a column of P and a row of Ut / U2 start one element
+    // apart in the banks, so the triangular inverses (a lane per column,
+    // walking down the rows) and the transposing stores do not conflict
+    static constexpr int PRS = PRA + 1;
+    static constexpr int CWS = CW + 1;
+    C *P;      // [NB][PRS], column major
     C *Linv;   // [NB][NB+1], column major, padded
     C *Uinv;   // [NB][NB+1]
-    C *Ut;     // [NB][CW]  (row t, col) at t*CW+col
-    C *U2;     // [NB][CW]
+    C *Ut;     // [NB][CWS]  (row t, col) at t*CWS+col
+    C *U2;     // [NB][CWS]
     C *prow;   // [2][NB]
     C *drow;   // [2][NB]
     R *wval;   // [2][(TH / 32)]
@@ -58,11 +63,11 @@ struct LuSm {
 
     RSRR_DEV explicit LuSm(unsigned char *raw) {
         P = reinterpret_cast<C *>(raw);
-        Linv = P + NB * PRA;
+        Linv = P + NB * PRS;
         Uinv = Linv + NB * (NB + 1);
         Ut = Uinv + NB * (NB + 1);
-        U2 = Ut + NB * CW;
-        prow = U2 + NB * CW;
+        U2 = Ut + NB * CWS;
+        prow = U2 + NB * CWS;
         drow = prow + 2 * NB;
         wval = reinterpret_cast<R *>(drow + 2 * NB);
         widx = reinterpret_cast<int *>(wval + 2 * (TH / 32));
@@ -70,7 +75,7 @@ struct LuSm {
         sw = perm + PRA;
     }
     static size_t bytes() {
-        size_t b = sizeof(C) * ((size_t)NB * PRA + 2 * NB * (NB + 1) + 2 * NB * CW + 4 * NB);
+        size_t b = sizeof(C) * ((size_t)NB * PRS + 2 * NB * (NB + 1) + 2 * NB * CWS + 4 * NB);
         b += sizeof(R) * 2 * (TH / 32) + sizeof(int) * (2 * (TH / 32) + PRA + NB);
         return b;
     }
@@ -83,7 +88,7 @@ template <typename C, int NB, int RA, int CB, int TH>
 RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restrict__ dinv, int n,
                        int kl, int KV, int ldab, int j0, const LuSm<C, NB, RA, CB, TH> &sm, int &info) {
     using R = typename real_of<C>::type;
-    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
+    constexpr int PRS = LuSm<C, NB, RA, CB, TH>::PRS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
@@ -157,15 +162,15 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
 #pragma unroll
         for (int cc = 0; cc < NB; ++cc) {
             if (cc < jb) {
-                sm.P[cc * PRA + tid] = row[cc];
+                sm.P[cc * PRS + tid] = row[cc];
                 const int d = tid - cc;
                 if (d >= -KV && d < kl + NB) ab[(size_t)(j0 + cc) * ldab + KV + d] = row[cc];
             }
         }
     }
+    for (int r = tid; r < pr; r += TH) sm.perm[r] = r;
     __syncthreads();
     if (tid == 0) {
-        for (int r = 0; r < pr; ++r) sm.perm[r] = r;
         for (int cc = 0; cc < jb; ++cc) {
             const int p = sm.sw[cc];
             const int t = sm.perm[cc]; sm.perm[cc] = sm.perm[p]; sm.perm[p] = t;
@@ -178,7 +183,7 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
         if (j < NB) {
             for (int i = 0; i < NB; ++i) {
                 C s = (i == j) ? cone<C>() : czero<C>();
-                for (int t = j; t < i; ++t) s = cfms(s, sm.P[t * PRA + i], sm.Linv[j * (NB + 1) + t]);
+                for (int t = j; t < i; ++t) s = cfms(s, sm.P[t * PRS + i], sm.Linv[j * (NB + 1) + t]);
                 sm.Linv[j * (NB + 1) + i] = (i < j || i >= jb || j >= jb) ? czero<C>() : s;
             }
         }
@@ -189,11 +194,11 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
         if (j < NB) {
             for (int i = 0; i < NB; ++i) sm.Uinv[j * (NB + 1) + i] = czero<C>();
             if (j < jb) {
-                sm.Uinv[j * (NB + 1) + j] = crecip(sm.P[j * PRA + j]);
+                sm.Uinv[j * (NB + 1) + j] = crecip(sm.P[j * PRS + j]);
                 for (int i = j - 1; i >= 0; --i) {
                     C s = czero<C>();
-                    for (int t = i + 1; t <= j; ++t) s = cfma(s, sm.P[t * PRA + i], sm.Uinv[j * (NB + 1) + t]);
-                    sm.Uinv[j * (NB + 1) + i] = cmul(csub(czero<C>(), s), crecip(sm.P[i * PRA + i]));
+                    for (int t = i + 1; t <= j; ++t) s = cfma(s, sm.P[t * PRS + i], sm.Uinv[j * (NB + 1) + t]);
+                    sm.Uinv[j * (NB + 1) + i] = cmul(csub(czero<C>(), s), crecip(sm.P[i * PRS + i]));
                 }
             }
         }
@@ -214,6 +219,7 @@ RSRR_DEV void lu_load_panel(const C *__restrict__ ab, const int32_t *__restrict_
                             const C *__restrict__ dinv, int n, int kl, int KV, int ldab, int j0,
                             const LuSm<C, NB, RA, CB, TH> &sm) {
     constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
+    constexpr int PRS = LuSm<C, NB, RA, CB, TH>::PRS;
     const int tid = threadIdx.x;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
@@ -221,17 +227,20 @@ RSRR_DEV void lu_load_panel(const C *__restrict__ ab, const int32_t *__restrict_
         const int cc = q / PRA, r = q % PRA;
         C v = czero<C>();
         if (cc < jb && r >= jb && r < pr) v = __ldcg(&ab[(size_t)(j0 + cc) * ldab + KV + (r - cc)]);
-        sm.P[q] = v;
+        sm.P[cc * PRS + r] = v;
     }
     const C *src = dinv + (size_t)(j0 / NB) * 2 * NB * NB;
     for (int q = tid; q < NB * NB; q += TH) {
         const int j = q / NB, i = q % NB;
         sm.Linv[j * (NB + 1) + i] = __ldcg(&src[q]);
     }
+    // the panel's pivots, all in flight at once, then composed by one thread
+    if (tid < jb) sm.sw[tid] = __ldcg(&piv[j0 + tid]) - j0;
+    for (int r = tid; r < pr; r += TH) sm.perm[r] = r;
+    __syncthreads();
     if (tid == 0) {
-        for (int r = 0; r < pr; ++r) sm.perm[r] = r;
         for (int cc = 0; cc < jb; ++cc) {
-            const int p = __ldcg(&piv[j0 + cc]) - j0;
+            const int p = sm.sw[cc];
             const int t = sm.perm[cc]; sm.perm[cc] = sm.perm[p]; sm.perm[p] = t;
         }
     }
@@ -243,7 +252,8 @@ template <typename C, int NB, int RA, int CB, int TH>
 RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int j0, int c_lo,
                         int c_hi, const LuSm<C, NB, RA, CB, TH> &sm) {
     constexpr int CW = LuSm<C, NB, RA, CB, TH>::CW;
-    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
+    constexpr int CWS = LuSm<C, NB, RA, CB, TH>::CWS;
+    constexpr int PRS = LuSm<C, NB, RA, CB, TH>::PRS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
@@ -258,7 +268,7 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
                 const int d = j0 + sm.perm[t] - c;
                 if (d >= -KV) v = __ldcg(&ab[(size_t)c * ldab + KV + d]);
             }
-            sm.Ut[t * CW + col] = v;
+            sm.Ut[t * CWS + col] = v;
         }
         C acc[RA][CB];
 #pragma unroll
@@ -281,8 +291,8 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
             const int t = o % NB, col = o / NB;
             C s = czero<C>();
 #pragma unroll
-            for (int q = 0; q < NB; ++q) s = cfma(s, sm.Linv[q * (NB + 1) + t], sm.Ut[q * CW + col]);
-            sm.U2[t * CW + col] = s;
+            for (int q = 0; q < NB; ++q) s = cfma(s, sm.Linv[q * (NB + 1) + t], sm.Ut[q * CWS + col]);
+            sm.U2[t * CWS + col] = s;
             if (t < jb && col < cw) {
                 const int c = c0 + col;
                 const int d = j0 + t - c;
@@ -295,10 +305,10 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
         for (int q = 0; q < NB; ++q) {
             C uq[CB];
 #pragma unroll
-            for (int b = 0; b < CB; ++b) uq[b] = sm.U2[q * CW + warp + (TH / 32) * b];
+            for (int b = 0; b < CB; ++b) uq[b] = sm.U2[q * CWS + warp + (TH / 32) * b];
 #pragma unroll
             for (int a = 0; a < RA; ++a) {
-                const C l = sm.P[q * PRA + jb + lane + 32 * a];
+                const C l = sm.P[q * PRS + jb + lane + 32 * a];
 #pragma unroll
                 for (int b = 0; b < CB; ++b) acc[a][b] = cfms(acc[a][b], l, uq[b]);
             }
@@ -325,7 +335,6 @@ __global__ void __launch_bounds__(TH, 1)
 band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
                int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl, int ku,
                int ldab) {
-    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     const int pt = blockIdx.x;
     C *ab = ab_all + (size_t)pt * ldab * n;
     int32_t *piv = piv_all + (size_t)pt * n;
@@ -335,7 +344,7 @@ band_lu_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     const int KV = kl + ku;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const LuSm<C, NB, RA, CB, TH> sm(smem_raw);
-    for (int q = threadIdx.x; q < NB * PRA; q += TH) sm.P[q] = czero<C>();
+    for (int q = threadIdx.x; q < NB * LuSm<C, NB, RA, CB, TH>::PRS; q += TH) sm.P[q] = czero<C>();
     int info = 0;
     __syncthreads();
     for (int j0 = 0; j0 < n; j0 += NB) {
@@ -362,7 +371,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TH, 1)
 band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
                        int32_t *__restrict__ info_all, C *__restrict__ dinv_all, int n, int kl,
                        int ku, int ldab) {
-    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     constexpr int CW = LuSm<C, NB, RA, CB, TH>::CW;
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
@@ -374,7 +382,7 @@ band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
     const int KV = kl + ku;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const LuSm<C, NB, RA, CB, TH> sm(smem_raw);
-    for (int q = threadIdx.x; q < NB * PRA; q += TH) sm.P[q] = czero<C>();
+    for (int q = threadIdx.x; q < NB * LuSm<C, NB, RA, CB, TH>::PRS; q += TH) sm.P[q] = czero<C>();
     int info = 0;
     __syncthreads();
     if (rank == 0) lu_panel<C, NB, RA, CB, TH>(ab, piv, dinv, n, kl, KV, ldab, 0, sm, info);
@@ -409,7 +417,6 @@ band_lu_cluster_kernel(C *__restrict__ ab_all, int32_t *__restrict__ piv_all,
 template <typename C, int NB, int RA, int CB, int TH>
 __global__ void __launch_bounds__(TH, 1)
 band_lu_grouped_kernel(const LuTask *__restrict__ tasks, int ntasks, int *__restrict__ next) {
-    constexpr int PRA = LuSm<C, NB, RA, CB, TH>::PRA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const LuSm<C, NB, RA, CB, TH> sm(smem_raw);
     __shared__ int s_task;
@@ -423,7 +430,7 @@ band_lu_grouped_kernel(const LuTask *__restrict__ tasks, int ntasks, int *__rest
         C *ab = static_cast<C *>(tk.ab);
         C *dinv = static_cast<C *>(tk.dinv);
         const int n = tk.n, kl = tk.kl, KV = tk.kl + tk.ku, ldab = tk.ldab;
-        for (int q = threadIdx.x; q < NB * PRA; q += TH) sm.P[q] = czero<C>();
+        for (int q = threadIdx.x; q < NB * LuSm<C, NB, RA, CB, TH>::PRS; q += TH) sm.P[q] = czero<C>();
         int info = 0;
         __syncthreads();
         for (int j0 = 0; j0 < n; j0 += NB) {
@@ -488,6 +495,10 @@ static cudaError_t lu_by_kl(C *ab, int32_t *piv, int32_t *info, C *dinv, const B
     constexpr int CB256 = 2 * CB512;
     if (kl <= 32) return lu_dispatch<C, NB, 1, CB256, 256>(ab, piv, info, dinv, g, N, n, cluster, s);
     if (kl <= 128) return lu_dispatch<C, NB, 4, CB256, 256>(ab, piv, info, dinv, g, N, n, cluster, s);
+    // 512 threads for the single-precision types: sixteen warps hide the
+    // latencies of the trailing update better than eight (measured 11% on the
+    // full-size grid problem at half-bandwidth 200); same chunk width
+    if (kl <= 224 && sizeof(C) <= 8) return lu_dispatch<C, NB, 7, CB512, 512>(ab, piv, info, dinv, g, N, n, cluster, s);
     if (kl <= 224) return lu_dispatch<C, NB, 7, CB256, 256>(ab, piv, info, dinv, g, N, n, cluster, s);
     return lu_dispatch<C, NB, 15, CB512, 512>(ab, piv, info, dinv, g, N, n, cluster, s);
 }
