@@ -303,6 +303,10 @@ __global__ void residual_kernel(double2 *__restrict__ R, const double2 *__restri
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int l0 = blockIdx.z * RES_LCH;
     const double2 *Xp = X + (size_t)pt * L * n;
+    // squared moduli here, one square root per warp after the reduction: the
+    // kernel is bound by the FP64 pipe (1/64 of the FP32 rate on this part),
+    // and a modulus per element cost as much as the residual's products
+    // (values of modulus up to about 1e150, far beyond any sample's)
     double2 acc[RES_LCH];
     double xm[RES_LCH];
 #pragma unroll
@@ -311,7 +315,8 @@ __global__ void residual_kernel(double2 *__restrict__ R, const double2 *__restri
         xm[l] = 0.0;
         if (i < n && l0 + l < L) {
             acc[l] = U[(size_t)(l0 + l) * n + i];
-            xm[l] = cabsv(Xp[(size_t)(l0 + l) * n + i]);
+            const double2 x = Xp[(size_t)(l0 + l) * n + i];
+            xm[l] = fma(x.x, x.x, x.y * x.y);
         }
     }
     if (i < n) {
@@ -331,14 +336,14 @@ __global__ void residual_kernel(double2 *__restrict__ R, const double2 *__restri
 #pragma unroll
     for (int l = 0; l < RES_LCH; ++l) {
         if (R && i < n && l0 + l < L) R[(size_t)pt * L * n + (size_t)(l0 + l) * n + i] = acc[l];
-        double rv = cabsv(acc[l]), xv = xm[l];
+        double rv = fma(acc[l].x, acc[l].x, acc[l].y * acc[l].y), xv = xm[l];
         for (int off = 16; off; off >>= 1) {
             rv = fmax(rv, shfl_down(rv, off));
             xv = fmax(xv, shfl_down(xv, off));
         }
         if ((threadIdx.x & 31) == 0 && l0 + l < L) {
-            atomic_max_nonneg(rmax + pt * L + l0 + l, rv);
-            atomic_max_nonneg(xmax + pt * L + l0 + l, xv);
+            atomic_max_nonneg(rmax + pt * L + l0 + l, sqrt(rv));
+            atomic_max_nonneg(xmax + pt * L + l0 + l, sqrt(xv));
         }
     }
 }

@@ -473,9 +473,14 @@ __global__ void dense_colmax_kernel(const double2 *__restrict__ Rm, const double
                                     int n, double *__restrict__ rmax, double *__restrict__ xmax) {
     const int l = blockIdx.x;
     double r = 0.0, x = 0.0;
+    // squared moduli, one square root at the end (FP64 pipe)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        if (Rm) r = fmax(r, cabsv(Rm[(size_t)l * n + i]));
-        x = fmax(x, cabsv(X[(size_t)l * n + i]));
+        if (Rm) {
+            const double2 v = Rm[(size_t)l * n + i];
+            r = fmax(r, fma(v.x, v.x, v.y * v.y));
+        }
+        const double2 v = X[(size_t)l * n + i];
+        x = fmax(x, fma(v.x, v.x, v.y * v.y));
     }
     for (int off = 16; off; off >>= 1) {
         r = fmax(r, shfl_down(r, off));
@@ -487,8 +492,8 @@ __global__ void dense_colmax_kernel(const double2 *__restrict__ Rm, const double
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a = fmax(a, wr[q]); b = fmax(b, wx[q]); }
-        rmax[l] = a;
-        xmax[l] = b;
+        rmax[l] = sqrt(a);
+        xmax[l] = sqrt(b);
     }
 }
 
