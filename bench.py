@@ -384,7 +384,7 @@ def run_ours(a, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     lu_ms, sample_ms, project_ms, gemm_ms, gemm_flops, tc_ms, tc_flops = [], [], [], [], [], [], []
-    asm_ms = []
+    asm_ms, solve_ms = [], []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -397,6 +397,7 @@ def run_ours(a, rank, world, local):
         torch.cuda.synchronize()
         sti = s.stats()
         asm_ms.append(sti["stage_ms"][0])
+        solve_ms.append(sti["stage_ms"][2])
         lu_ms.append(sti["stage_ms"][1])
         sample_ms.append(sum(sti["stage_ms"][:5]))
         project_ms.append(sti["stage_ms"][5])
@@ -427,15 +428,24 @@ def run_ours(a, rank, world, local):
     # the complex64 band LU of rsrr_sample (FP32 FMA pipe); "roofline" is the
     # one with more device time per step
     peaks = measured_peaks()
+    # DRAM bytes of each roofline's kernel, dram__bytes_read.sum +
+    # dram__bytes_write.sum from one ncu capture of this command at this size
+    # (the DRAM traffic summary under profiles/); valid for the kernel
+    # revisions captured there, and only at the default size
+    full = a.g == 200
+    traffic_tc = 154.4e9 if full else None      # all 37 slice GEMMs of one step
+    traffic_lu = 42.67e9 if full else None      # one band LU launch
+    traffic_asm = 13.32e9 if full else None     # one assembly launch
+    traffic_solve = 16.78e9 if full else None   # the first solve (all 64 points)
     tc_avg = statistics.mean(tc_ms)
     tc_ach = statistics.mean(tc_flops) / (tc_avg / 1e3) / 1e12 if tc_avg > 0 else 0.0
     roof_tc = {"bound": "tensor", "kernel": "oz_gemm_tc_kernel (bf16 slice products on tcgen05, Ozaki GEMMs)",
                "achieved": tc_ach, "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
-               "frac": tc_ach / peaks["bf16_sustained"], "traffic": None,
+               "frac": tc_ach / peaks["bf16_sustained"], "traffic": traffic_tc,
                "tensor_flop_per_step": statistics.mean(tc_flops), "ms_per_step": tc_avg,
                "peak_note": f"bf16 dense, sustained, {peaks['source']}; flops = the 28 slice-pair "
                             "products per 128x64 tile the scheme needs (tcgen05.mma kind::f16); "
-                            "traffic null: many GEMM shapes per step",
+                            "achieved and traffic per step (all 37 slice-GEMM launches of a step)",
                "fp64_equivalent": {"flop_per_step": statistics.mean(gemm_flops),
                                    "gemm_ms_per_step": statistics.mean(gemm_ms),
                                    "tflops": statistics.mean(gemm_flops)
@@ -449,13 +459,13 @@ def run_ours(a, rank, world, local):
     roof_lu = {"bound": "alu", "kernel": "band_lu_cluster_kernel<float2> (complex64, two-CTA cluster per point)",
                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": achieved / FP32_PEAK_TFLOPS,
-               "traffic": None,
+               "traffic": traffic_lu,
                "algorithmic_flop_per_launch": lu_flops, "avg_launch_ms": lu_avg,
                # the other roof: the band storage read and written once
                "algorithmic_bytes_per_launch": 2 * 8.0 * ldab * n * p.N,
                "hbm_frac": 2 * 8.0 * ldab * n * p.N / (lu_avg / 1e3) / 1e9 / peaks["hbm_gbs"],
-               "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; traffic "
-                            "null: the kernel changed after its last DRAM capture"}
+               "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; traffic 1.65x the "
+                            "algorithmic bytes: the trailing window written back every panel"}
     roof, roof_other = (roof_lu, roof_tc) if lu_avg >= tc_avg else (roof_tc, roof_lu)
     # band assembly: the complex64 band storage of every point written once
     asm_bytes = 8.0 * ldab * n * p.N
@@ -463,11 +473,23 @@ def run_ours(a, rank, world, local):
     asm_gbs = asm_bytes / (asm_avg / 1e3) / 1e9
     roof_asm = {"bound": "hbm", "kernel": "assemble_band_kernel<float2> (one warp per band column)",
                 "achieved": asm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": asm_gbs / peaks["hbm_gbs"], "traffic": None,
+                "frac": asm_gbs / peaks["hbm_gbs"], "traffic": traffic_asm,
                 "algorithmic_bytes_per_launch": asm_bytes, "avg_stage_ms": asm_avg,
                 "pattern_only_bytes_per_launch": 8 * len(p.col_idx) * p.N,
                 "peak_note": f"copy bandwidth, {peaks['source']}; time = the assembly stage "
                              "(the ||T(z_j)|| kernel + the assembly), so the fraction is a lower bound"}
+
+    # first solve of all points: the complex64 factors streamed once per 16
+    # right-hand sides (two CTAs per point), against the copy bandwidth
+    solve_avg = statistics.mean(solve_ms)
+    solve_bytes = 8.0 * ldab * n * p.N
+    roof_solve = {"bound": "hbm", "kernel": "band_solve2_kernel<float2> (streaming banded solve, first solve)",
+                  "achieved": solve_bytes / (solve_avg / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": solve_bytes / (solve_avg / 1e3) / 1e9 / peaks["hbm_gbs"], "hbm_frac":
+                  solve_bytes / (solve_avg / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": traffic_solve,
+                  "algorithmic_bytes_per_launch": solve_bytes, "avg_stage_ms": solve_avg,
+                  "peak_note": f"copy bandwidth, {peaks['source']}; the solve is a chain of 2n/32 dependent "
+                               "block steps per point and is bound by its per-step latency, not by DRAM"}
 
     if not a.no_fp64:
         s64 = rsrr.Solver(p, rsrr.default_opts(precision=rsrr.RSRR_PREC_FP64, timing=1))
@@ -501,6 +523,7 @@ def run_ours(a, rank, world, local):
         "pivoted_cholesky_kc": stats["kc"],
         "fp64_plain_path": fp64,
         "roofline": roof, "roofline_second": roof_other, "roofline_assembly": roof_asm,
+        "roofline_solve": roof_solve,
         "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
     }
