@@ -41,7 +41,6 @@ namespace rsrr {
 // --------------------------------------------------------------------------
 template <typename C, int NB, int RA, int CB, int TH>
 struct LuSm {
-    using R = typename real_of<C>::type;
     static constexpr int CW = (TH / 32) * CB;
     static constexpr int PRA = NB + 32 * RA;  // allocated panel rows (>= NB + kl)
     // padded strides: a column of P and a row of Ut / U2 start one element
@@ -54,12 +53,9 @@ struct LuSm {
     C *Uinv;   // [NB][NB+1]
     C *Ut;     // [NB][CWS]  (row t, col) at t*CWS+col
     C *U2;     // [NB][CWS]
-    C *prow;   // [2][NB]
-    C *drow;   // [2][NB]
-    R *wval;   // [2][(TH / 32)]
-    int *widx; // [2][(TH / 32)]
-    int *perm; // [PRA]
-    int *sw;   // [NB]
+    int *perm; // [PRA] position -> panel row
+    int *pos;  // [PRA] panel row -> position (panel factorisation)
+    int *sw;   // [NB]  pivots, as panel rows (factorisation) or positions (from piv)
 
     RSRR_DEV explicit LuSm(unsigned char *raw) {
         P = reinterpret_cast<C *>(raw);
@@ -67,23 +63,30 @@ struct LuSm {
         Uinv = Linv + NB * (NB + 1);
         Ut = Uinv + NB * (NB + 1);
         U2 = Ut + NB * CWS;
-        prow = U2 + NB * CWS;
-        drow = prow + 2 * NB;
-        wval = reinterpret_cast<R *>(drow + 2 * NB);
-        widx = reinterpret_cast<int *>(wval + 2 * (TH / 32));
-        perm = widx + 2 * (TH / 32);
-        sw = perm + PRA;
+        perm = reinterpret_cast<int *>(U2 + NB * CWS);
+        pos = perm + PRA;
+        sw = pos + PRA;
     }
     static size_t bytes() {
-        size_t b = sizeof(C) * ((size_t)NB * PRS + 2 * NB * (NB + 1) + 2 * NB * CWS + 4 * NB);
-        b += sizeof(R) * 2 * (TH / 32) + sizeof(int) * (2 * (TH / 32) + PRA + NB);
-        return b;
+        return sizeof(C) * ((size_t)NB * PRS + 2 * NB * (NB + 1) + 2 * NB * CWS) + sizeof(int) * (2 * PRA + NB);
     }
 };
 
 // Factors the panel at column j0: the factored columns go to global memory
 // and to sm.P, the pivots to piv, the composed row permutation to sm.perm,
 // L11^{-1} and U11^{-1} to sm.Linv / sm.Uinv and to the block's dinv slot.
+//
+// The panel is factored in shared memory with its rows in their original
+// order and the interchanges kept virtual: per column every warp that holds
+// panel rows finds the pivot itself (argmax of |re|+|im| over the rows not
+// yet pivots among the first cc + kl + 1, smallest row on ties; each lane
+// keeps a bit mask of its rows that were pivots), so no barrier is needed
+// to publish it; every other active row then forms its multiplier and
+// updates its remaining panel entries against the pivot row.  One barrier a
+// column.  A row's multiplier is stored after the barrier (a slower warp may
+// still be reading the column for its pivot search).  At the end the
+// interchanges are replayed in order, as positions (LAPACK's sequential
+// swaps), for piv and sm.perm, and the rows are moved to their positions.
 template <typename C, int NB, int RA, int CB, int TH>
 RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restrict__ dinv, int n,
                        int kl, int KV, int ldab, int j0, const LuSm<C, NB, RA, CB, TH> &sm, int &info) {
@@ -92,89 +95,102 @@ RSRR_DEV void lu_panel(C *__restrict__ ab, int32_t *__restrict__ piv, C *__restr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int jb = min(NB, n - j0);
     const int pr = min(n - j0, jb + kl);
-
-    C row[NB];
-#pragma unroll
-    for (int cc = 0; cc < NB; ++cc) {
-        row[cc] = czero<C>();
-        if (tid < pr && cc < jb) {
-            const int d = tid - cc;  // (j0 + tid) - (j0 + cc)
-            if (d >= -KV && d < kl + NB) row[cc] = __ldcg(&ab[(size_t)(j0 + cc) * ldab + KV + d]);
-        }
+    // (1) rows j0 .. j0+pr-1, columns j0 .. j0+NB-1 into shared memory (zero
+    // outside the band storage and beyond the last column)
+    for (int q = tid; q < NB * pr; q += TH) {
+        const int cc = q / pr, r = q % pr;
+        const int d = r - cc;
+        C v = czero<C>();
+        if (cc < jb && d >= -KV && d < kl + NB) v = __ldcg(&ab[(size_t)(j0 + cc) * ldab + KV + d]);
+        sm.P[cc * PRS + r] = v;
     }
-#pragma unroll
-    for (int cc = 0; cc < NB; ++cc) {
-        if (cc < jb) {
-            const int buf = cc & 1;
+    __syncthreads();
+    // (2) the columns
+    const bool scan = warp * 32 < pr;  // warps that hold panel rows
+    unsigned dmask = 0;                // bit i: row lane + 32 i is a pivot already
+    bool rdone = false;                // this thread's row is a pivot already
+    C lprev = czero<C>();
+    int cprev = -1;
+    for (int cc = 0; cc < jb; ++cc) {
+        if (cprev >= 0) {
+            sm.P[cprev * PRS + tid] = lprev;
+            cprev = -1;
+        }
+        if (scan) {
             const int rend = min(pr, cc + kl + 1);
             R v = (R)-1;
             int ix = 0x7fffffff;
-            if (tid >= cc && tid < rend) { v = cabs1(row[cc]); ix = tid; }
+            int i = 0;
+            for (int r = lane; r < rend; r += 32, ++i) {
+                if (!((dmask >> i) & 1u)) {
+                    R a = cabs1(sm.P[cc * PRS + r]);
+                    if (!(a >= (R)0)) a = (R)0;  // a NaN never wins, but a row is always chosen
+                    if (a > v) { v = a; ix = r; }
+                }
+            }
 #pragma unroll
             for (int off = 16; off; off >>= 1) {
                 const R ov = shfl_down(v, off);
                 const int oi = shfl_down(ix, off);
                 if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
             }
-            if (lane == 0) { sm.wval[buf * (TH / 32) + warp] = v; sm.widx[buf * (TH / 32) + warp] = ix; }
-            __syncthreads();
-            R bv = sm.wval[buf * (TH / 32)];
-            int p = sm.widx[buf * (TH / 32)];
-#pragma unroll
-            for (int w = 1; w < (TH / 32); ++w) {
-                const R ov = sm.wval[buf * (TH / 32) + w];
-                const int oi = sm.widx[buf * (TH / 32) + w];
-                if (ov > bv || (ov == bv && oi < p)) { bv = ov; p = oi; }
-            }
-            if (tid == p) {
-#pragma unroll
-                for (int c2 = 0; c2 < NB; ++c2) sm.prow[buf * NB + c2] = row[c2];
-            }
-            if (tid == cc) {
-#pragma unroll
-                for (int c2 = 0; c2 < NB; ++c2) sm.drow[buf * NB + c2] = row[c2];
-            }
-            __syncthreads();
-            if (tid == cc) {
-#pragma unroll
-                for (int c2 = 0; c2 < NB; ++c2) row[c2] = sm.prow[buf * NB + c2];
-            } else if (tid == p) {
-#pragma unroll
-                for (int c2 = 0; c2 < NB; ++c2) row[c2] = sm.drow[buf * NB + c2];
-            }
-            const C pv = sm.prow[buf * NB + cc];
+            const int p = __shfl_sync(0xffffffffu, ix, 0);
+            if ((p & 31) == lane) dmask |= 1u << (p >> 5);
+            if (tid == p) rdone = true;
+            const C pv = sm.P[cc * PRS + p];
             const bool nz = cnonzero(pv);
-            if (tid > cc && tid < rend && nz) {
-                const C l = cmul(row[cc], crecip(pv));
-                row[cc] = l;
-#pragma unroll
-                for (int c2 = cc + 1; c2 < NB; ++c2) row[c2] = cfms(row[c2], l, sm.prow[buf * NB + c2]);
+            if (tid < rend && !rdone && nz) {
+                const C l = cmul(sm.P[cc * PRS + tid], crecip(pv));
+                lprev = l;
+                cprev = cc;
+#pragma unroll 4
+                for (int c2 = cc + 1; c2 < jb; ++c2)
+                    sm.P[c2 * PRS + tid] = cfms(sm.P[c2 * PRS + tid], l, sm.P[c2 * PRS + p]);
             }
             if (tid == 0) {
                 sm.sw[cc] = p;
-                piv[j0 + cc] = j0 + p;
                 if (!nz && info == 0) info = j0 + cc + 1;
             }
         }
+        __syncthreads();
     }
-    // panel -> shared (column major) and global
-    if (tid < pr) {
-#pragma unroll
-        for (int cc = 0; cc < NB; ++cc) {
-            if (cc < jb) {
-                sm.P[cc * PRS + tid] = row[cc];
-                const int d = tid - cc;
-                if (d >= -KV && d < kl + NB) ab[(size_t)(j0 + cc) * ldab + KV + d] = row[cc];
-            }
-        }
+    if (cprev >= 0) sm.P[cprev * PRS + tid] = lprev;
+    // (3) the interchanges as positions: piv and sm.perm (position -> row)
+    for (int r = tid; r < pr; r += TH) {
+        sm.perm[r] = r;
+        sm.pos[r] = r;
     }
-    for (int r = tid; r < pr; r += TH) sm.perm[r] = r;
     __syncthreads();
     if (tid == 0) {
         for (int cc = 0; cc < jb; ++cc) {
-            const int p = sm.sw[cc];
-            const int t = sm.perm[cc]; sm.perm[cc] = sm.perm[p]; sm.perm[p] = t;
+            const int p = sm.sw[cc], pp = sm.pos[p], rc = sm.perm[cc];
+            piv[j0 + cc] = j0 + pp;
+            sm.perm[cc] = p;
+            sm.perm[pp] = rc;
+            sm.pos[p] = cc;
+            sm.pos[rc] = pp;
         }
+    }
+    __syncthreads();
+    // (4) rows to their positions, in shared memory and in the band storage
+    constexpr int HALF = NB / 2;
+    const int dpos = tid < pr ? sm.pos[tid] : 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        C v[HALF];
+#pragma unroll
+        for (int c = 0; c < HALF; ++c) v[c] = tid < pr ? sm.P[(h * HALF + c) * PRS + tid] : czero<C>();
+        __syncthreads();
+        if (tid < pr) {
+#pragma unroll
+            for (int c = 0; c < HALF; ++c) {
+                const int cc = h * HALF + c;
+                sm.P[cc * PRS + dpos] = v[c];
+                const int d = dpos - cc;
+                if (cc < jb && d >= -KV && d < kl + NB) ab[(size_t)(j0 + cc) * ldab + KV + d] = v[c];
+            }
+        }
+        __syncthreads();
     }
     if (warp == 1) {
         // column j = lane of L11^{-1}: x_i = [i == j] - sum_{t<i} L(i,t) x_t,
