@@ -1089,17 +1089,17 @@ cudaError_t Handle::sweep_solve(float2 *B, const int32_t *skip, int p0, int np, 
     if (!use_solve2 || !d_gate || (opts.flags & RSRR_FLAG_WIDE_SOLVE_ONLY)) return band_solve(true, B, skip, p0, np, s);
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_point = (L + 3) / 4;  // CTAs of a point in the narrow shape
-    const int thr = std::max(1, sms / per_point);
     const size_t ab_pt = (size_t)geom.ldab * n;
     const size_t nblk = ((size_t)n + geom.nb - 1) / geom.nb;
     const size_t bp_pt = nblk * 2 * geom.nb, dv_pt = nblk * 2 * geom.nb * geom.nb;
     const float2 *ab = d_ab32 + fo(p0) * ab_pt, *dv = d_dinv32 + fo(p0) * dv_pt;
     const int32_t *bp = d_bperm + fo(p0) * bp_pt;
-    cudaError_t e = launch_solve_gate(skip, np, thr, d_gate, s);
-    if (e == cudaSuccess) e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, false, d_gate, 0);
-    if (e == cudaSuccess) e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, true, d_gate, 1);
-    launches += 2;
+    // the device picks the shape (16, 8, 4 or 2 right-hand sides per CTA)
+    // from the points still active; the other three launches return at once
+    cudaError_t e = launch_solve_gate(skip, np, L, sms, d_gate, s);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = launch_band_solve2_c64(ab, bp, dv, B, geom, np, (int)n, L, skip, s, 16 >> k, d_gate, k);
+    launches += 4;
     return e;
 }
 

@@ -353,7 +353,12 @@ size_t band_solve2_smem_r64(const BandGeom &g) { return s2_smem_used<double, NB_
 
 // gate = 1 if at most thr points have done == 0 (few points left: the
 // narrow shape, more CTAs per point), else 0
-__global__ void solve_gate_kernel(const int32_t *__restrict__ done, int N, int thr, int32_t *__restrict__ gate) {
+// the shape of a refinement sweep's solve, from the number of points still
+// active: the narrowest of 16, 8, 4, 2 right-hand sides per CTA whose CTAs
+// for the active points fit in one wave over the SMs (a narrower shape
+// shortens every block step of the chain), else the widest; gate = 0, 1, 2, 3
+__global__ void solve_gate_kernel(const int32_t *__restrict__ done, int N, int L, int sms,
+                                  int32_t *__restrict__ gate) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -361,11 +366,18 @@ __global__ void solve_gate_kernel(const int32_t *__restrict__ done, int N, int t
     for (int i = threadIdx.x; i < N; i += blockDim.x) c += done[i] == 0 ? 1 : 0;
     atomicAdd(&cnt, c);
     __syncthreads();
-    if (threadIdx.x == 0) *gate = cnt <= thr ? 1 : 0;
+    if (threadIdx.x == 0) {
+        int g = 0;
+        for (int k = 3; k >= 1; --k) {
+            const int lc = 16 >> k;
+            if ((long long)cnt * ((L + lc - 1) / lc) <= sms) { g = k; break; }
+        }
+        *gate = g;
+    }
 }
 
-cudaError_t launch_solve_gate(const int32_t *done, int N, int thr, int32_t *gate, cudaStream_t s) {
-    solve_gate_kernel<<<1, 256, 0, s>>>(done, N, thr, gate);
+cudaError_t launch_solve_gate(const int32_t *done, int N, int L, int sms, int32_t *gate, cudaStream_t s) {
+    solve_gate_kernel<<<1, 256, 0, s>>>(done, N, L, sms, gate);
     return cudaGetLastError();
 }
 
@@ -391,15 +403,24 @@ static cudaError_t s2_dispatch(const C *ab, const int32_t *bperm, const C *dinv,
                                const int32_t *gate, int want, cudaStream_t s) {
     if (s2_wide<C, NB, LC>(g))
         return s2_launch<C, NB, LC, 256, 2>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
-    return s2_launch<C, NB, LC, 128, 3>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    if constexpr (LC * 128 < S2_THREADS) {
+        // two right-hand sides do not fill the 128-row units: four per CTA
+        return s2_launch<C, NB, 4, 128, 3>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    } else {
+        return s2_launch<C, NB, LC, 128, 3>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    }
 }
 
 cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const float2 *dinv,
                                    float2 *B, const BandGeom &g, int N, int n, int L,
-                                   const int32_t *skip, cudaStream_t s, bool narrow,
+                                   const int32_t *skip, cudaStream_t s, int lc,
                                    const int32_t *gate, int want) {
-    if (narrow) return s2_dispatch<float2, NB_C64, 4>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
-    return s2_dispatch<float2, NB_C64, 16>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    switch (lc) {
+    case 2: return s2_dispatch<float2, NB_C64, 2>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    case 4: return s2_dispatch<float2, NB_C64, 4>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    case 8: return s2_dispatch<float2, NB_C64, 8>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    default: return s2_dispatch<float2, NB_C64, 16>(ab, bperm, dinv, B, g, N, n, L, skip, gate, want, s);
+    }
 }
 cudaError_t launch_band_solve2_r32(const float *ab, const int32_t *bperm, const float *dinv, float *B,
                                    const BandGeom &g, int N, int n, int L, const int32_t *skip, cudaStream_t s) {

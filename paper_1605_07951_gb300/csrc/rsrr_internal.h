@@ -164,15 +164,16 @@ cudaError_t launch_block_perm(int32_t *bperm, const int32_t *piv, int n, int kl,
                               cudaStream_t s);
 size_t band_solve2_smem_c64(const BandGeom &g);
 size_t band_solve2_smem_c128(const BandGeom &g);
-// narrow: 4 right-hand sides per CTA instead of 16 (more CTAs per point, the
-// same operations on every column); with gate set, the launch runs only if
-// *gate == want (launch_solve_gate writes it on the device)
+// lc: right-hand sides per CTA, 16 (default), 8, 4 or 2 (more CTAs per point
+// for fewer, the same operations on every column); with gate set, the launch
+// runs only if *gate == want (launch_solve_gate writes it on the device)
 cudaError_t launch_band_solve2_c64(const float2 *ab, const int32_t *bperm, const float2 *dinv,
                                    float2 *B, const BandGeom &g, int N, int n, int L,
-                                   const int32_t *skip, cudaStream_t s, bool narrow = false,
+                                   const int32_t *skip, cudaStream_t s, int lc = 16,
                                    const int32_t *gate = nullptr, int want = 0);
-// *gate = 1 if at most thr of the N done flags are 0, else 0
-cudaError_t launch_solve_gate(const int32_t *done, int N, int thr, int32_t *gate, cudaStream_t s);
+// *gate = k for the narrowest lc = 16 >> k (k = 0..3) whose CTAs for the points
+// with a zero done flag fit in one wave over sms SMs, else 0
+cudaError_t launch_solve_gate(const int32_t *done, int N, int L, int sms, int32_t *gate, cudaStream_t s);
 cudaError_t launch_band_solve2_c128(const double2 *ab, const int32_t *bperm, const double2 *dinv,
                                     double2 *B, const BandGeom &g, int N, int n, int L,
                                     const int32_t *skip, cudaStream_t s);
