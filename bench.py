@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--sample-points", type=int, default=2,
                     help="sampling points of the oracle's bounded sample")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the dense-kernel and grouped-batch sub-measurements")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--batch-full", action="store_true", help="c3 at its full sizes")
@@ -528,6 +530,9 @@ def run_ours(a, rank, world, local):
         "clocks": clk,
     }
     s.close()
+    if not a.no_extra and rank == 0:
+        line["dense"] = dense_leg(a)
+        line["batch_grouped"] = batch_leg(a)
     if not a.no_serving and rank == 0:
         line["serving"] = run_serving(a)
     if rank == 0 and not a.no_cpu_baseline:
@@ -599,6 +604,91 @@ def run_dense(a):
                       "stage_ms": st["stage_ms"][:5], "refine_sweeps": st["refine_sweeps"],
                       "max_eta": st["max_eta"],
                       "dense_lu_tflops": lu_flops / (st["stage_ms"][1] / 1e3) / 1e12}))
+
+
+def dense_leg(a):
+    """The dense kernel workload (n = 4096 points on the unit sphere, N = 32,
+    L = 64) as a sub-measurement of the default line: rsrr_sample device time,
+    the dense LU's roofline against the TF32 rate (the measured bf16 rate x the
+    nominal TF32 / bf16 ratio 1.1 / 2.25; the update runs as 3xTF32 on
+    tcgen05), and the oracle's dense LAPACK solve of one point on one core."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    p = W.helmholtz_sphere(n=a.dense_n, N=32, L=64)
+    s = rsrr.Solver(p, rsrr.default_opts(timing=1))
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        s.sample(stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.sample(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = s.stats()
+    ok = s.check_status() == rsrr.RSRR_OK
+    s.close()
+    n = p.n
+    lu_flops = 8.0 / 3.0 * n ** 3 * p.N
+    lu_tflops = lu_flops / (st["stage_ms"][1] / 1e3) / 1e12
+    peaks = measured_peaks()
+    tf32 = peaks["bf16_sustained"] * 1.1 / 2.25
+    out = {"workload": f"helmholtz_sphere_n{n}_N32_L64", "value": p.N * p.L / (ms / 1e3), "unit": UNIT,
+           "ms": ms, "converged": ok, "stage_ms": st["stage_ms"][:5], "max_eta": st["max_eta"],
+           "roofline": {"bound": "tensor", "kernel": "dense LU (tcgen05 3xTF32 trailing update, panel kernels)",
+                        "achieved": lu_tflops, "peak": tf32, "unit": "TFLOP/s", "frac": lu_tflops / tf32,
+                        "traffic": None,
+                        "peak_note": f"TF32 dense = bf16 sustained {peaks['source']} x 1.1/2.25 (nominal); "
+                                     "achieved = 8/3 n^3 complex-LU flops per point; traffic null: the LU "
+                                     "is many launches (a panel and an update per 32 columns)"}}
+    if not a.no_cpu_baseline:
+        import oracle
+        zo = oracle.sample_points(p.region, p.N)
+        t0 = time.perf_counter()
+        oracle.resolvent_samples_dense(p, zo[:1])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": p.L / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"1 of the 32 sampling points (64 columns, dense LAPACK solve, "
+                                         f"FP64) in {dt:.1f} s"}
+    return out
+
+
+def batch_leg(a):
+    """Grouped sampling of uneven band problems (the grid half of the batched
+    workload at scaled sizes, g 40..100): rsrr_sample_batch (one persistent
+    grouped band LU over all points of all handles) against the same handles
+    sampled one after the other."""
+    import torch
+    import workloads as W
+    from paper_1605_07951_gb300 import rsrr
+    probs = [q for fam, q in W.batch_uneven(32, dense_n=(256, 1024), grid_g=(40, 100)) if fam == "grid"]
+    solvers = [rsrr.Solver(q, rsrr.default_opts()) for q in probs]
+    stream = torch.cuda.current_stream()
+    cols = sum(sv.N * sv.L for sv in solvers)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    t_grouped = timed(lambda: rsrr.sample_batch(solvers, stream))
+    t_single = timed(lambda: [sv.sample(stream) for sv in solvers])
+    ok = all(sv.check_status() == rsrr.RSRR_OK for sv in solvers)
+    for sv in solvers:
+        sv.close()
+    return {"workload": f"{len(probs)} uneven grid NEPs (g 40..100, N 16..64, L 8..32, seed 4000)",
+            "value": cols / (t_grouped / 1e3), "unit": UNIT, "ms": t_grouped, "converged": ok,
+            "one_by_one": {"value": cols / (t_single / 1e3), "ms": t_single}}
 
 
 def run_batch(a):
