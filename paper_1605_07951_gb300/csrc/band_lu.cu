@@ -303,16 +303,30 @@ RSRR_DEV void lu_update(C *__restrict__ ab, int n, int kl, int KV, int ldab, int
         }
         __syncthreads();
         // (2) U12 = L11^{-1} Ut  -> U2 and global rows j0..j0+jb-1
-        for (int o = tid; o < NB * CW; o += TH) {
-            const int t = o % NB, col = o / NB;
-            C s = czero<C>();
+        // each thread two rows t and two columns of U12: half the shared
+        // loads of one output per thread, the same sum order per element
+        for (int o = tid; o < NB * CW / 4; o += TH) {
+            const int t2 = 2 * (o % (NB / 2)), col2 = 2 * (o / (NB / 2));
+            C s00 = czero<C>(), s10 = czero<C>(), s01 = czero<C>(), s11 = czero<C>();
 #pragma unroll
-            for (int q = 0; q < NB; ++q) s = cfma(s, sm.Linv[q * (NB + 1) + t], sm.Ut[q * CWS + col]);
-            sm.U2[t * CWS + col] = s;
-            if (t < jb && col < cw) {
-                const int c = c0 + col;
-                const int d = j0 + t - c;
-                if (d >= -KV) ab[(size_t)c * ldab + KV + d] = s;
+            for (int q = 0; q < NB; ++q) {
+                const C l0 = sm.Linv[q * (NB + 1) + t2], l1 = sm.Linv[q * (NB + 1) + t2 + 1];
+                const C u0 = sm.Ut[q * CWS + col2], u1 = sm.Ut[q * CWS + col2 + 1];
+                s00 = cfma(s00, l0, u0);
+                s10 = cfma(s10, l1, u0);
+                s01 = cfma(s01, l0, u1);
+                s11 = cfma(s11, l1, u1);
+            }
+            const C sv[4] = {s00, s10, s01, s11};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int t = t2 + (e & 1), col = col2 + (e >> 1);
+                sm.U2[t * CWS + col] = sv[e];
+                if (t < jb && col < cw) {
+                    const int c = c0 + col;
+                    const int d = j0 + t - c;
+                    if (d >= -KV) ab[(size_t)c * ldab + KV + d] = sv[e];
+                }
             }
         }
         __syncthreads();
