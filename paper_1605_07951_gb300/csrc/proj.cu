@@ -348,11 +348,12 @@ RSRR_DEV void block_argmax(const double *__restrict__ d, int n, double &bv, int 
 }
 
 // Pivoted Cholesky G ~ L L^H in one cooperative launch (left-looking; one
-// grid barrier per column).  state[0] = stopped, state[1] = kc.
+// grid barrier per column).  state[0] = stopped, state[1] = kc; pivots
+// (optional): the row of G chosen in each column.
 __global__ void __launch_bounds__(256)
 pchol_persistent_kernel(const double2 *__restrict__ G, int n, double2 *__restrict__ Lm,
                         double *__restrict__ dbuf, double tau, int32_t *__restrict__ state,
-                        unsigned int *__restrict__ bar) {
+                        unsigned int *__restrict__ bar, int32_t *__restrict__ pivots) {
     for (int j = 0; j < n; ++j) {
         const double *dprev = dbuf + (j & 1) * n;
         double *dnext = dbuf + ((j + 1) & 1) * n;
@@ -363,6 +364,7 @@ pchol_persistent_kernel(const double2 *__restrict__ G, int n, double2 *__restric
             if (blockIdx.x == 0 && threadIdx.x == 0) { state[1] = j; state[0] = 1; }
             return;
         }
+        if (pivots && blockIdx.x == 0 && threadIdx.x == 0) pivots[j] = p;
         const double sq = sqrt(dp);
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
             double2 l = make_double2(0.0, 0.0);
@@ -757,6 +759,62 @@ __global__ void max_vec_kernel(double *__restrict__ out, const double *__restric
     }
 }
 
+// Orthonormalisation of a block Qb (k columns) from its Gram G2 = Qb^H Qb by
+// Cholesky QR with column pivoting: G2 = P L L^H P^T (pivoted Cholesky,
+// stopped when the largest remaining diagonal falls below the threshold);
+// with T = the leading kc x kc block of L in pivot order (lower triangular,
+// real positive diagonal), Qb's pivot columns times T^{-H} have the Gram
+// T^{-1} (T T^H) T^{-H} = I.  X (k x kc) = S T^{-H}, S the pivot selection.
+
+// T(i, j) = L(piv[i], j) for j <= i, else 0 (kc x kc, column major)
+__global__ void tri_from_pchol_kernel(double2 *__restrict__ T, const double2 *__restrict__ L,
+                                      const int32_t *__restrict__ piv, int k, int kc) {
+    const int64_t total = (int64_t)kc * kc;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % kc), j = (int)(q / kc);
+        T[q] = j <= i ? L[(int64_t)j * k + piv[i]] : make_double2(0.0, 0.0);
+    }
+}
+
+// W = T^{-1} for lower triangular T with a real positive diagonal: one warp
+// per column j, forward substitution w_i = ([i == j] - sum_{j<=t<i} T(i,t) w_t)
+// / T(i,i), the sum split over the lanes (fixed order: lane partials, then a
+// shuffle tree)
+__global__ void tri_inverse_lower_kernel(double2 *__restrict__ W, const double2 *__restrict__ T, int kc) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= kc) return;
+    double2 *w = W + (int64_t)j * kc;
+    for (int i = lane; i < j; i += 32) w[i] = make_double2(0.0, 0.0);
+    for (int i = j; i < kc; ++i) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int t = j + lane; t < i; t += 32) acc = cfma(acc, T[(int64_t)t * kc + i], w[t]);
+        for (int off = 16; off; off >>= 1) {
+            acc.x += shfl_down(acc.x, off);
+            acc.y += shfl_down(acc.y, off);
+        }
+        if (lane == 0) {
+            const double d = T[(int64_t)i * kc + i].x;
+            const double rx = (i == j ? 1.0 : 0.0) - acc.x, ry = -acc.y;
+            w[i] = make_double2(rx / d, ry / d);
+        }
+        __syncwarp();
+    }
+}
+
+// X (k x kc, column major, zeroed before) = S W^H: X(piv[i], j) = conj(W(j, i))
+__global__ void scatter_inverse_fill_kernel(double2 *__restrict__ X, const double2 *__restrict__ W,
+                                            const int32_t *__restrict__ piv, int k, int kc) {
+    const int64_t total = (int64_t)kc * kc;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % kc), j = (int)(q / kc);  // X(piv[i], j) = conj(W(j, i))
+        const double2 v = W[(int64_t)i * kc + j];
+        X[(int64_t)j * k + piv[i]] = make_double2(v.x, -v.y);
+    }
+}
+
 // Work space of the sliced products: the Gram matrix of the n x NL block in
 // one piece (the other products of the sparse kind need less), capped at
 // 8 GiB; a product that needs more runs in chunks of K.
@@ -915,7 +973,7 @@ rsrr_status Handle::project(cudaStream_t s) {
         PK(cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int) * 4, s), "memset");
         diag_real_kernel<<<(nc + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.G, nc);
         PK(launch_coop(pchol_persistent_kernel, (nc + 255) / 256, s, (const double2 *)ws.G, nc,
-                       ws.Lm, ws.dbuf, tau, ws.state, ws.bar), "pivoted Cholesky");
+                       ws.Lm, ws.dbuf, tau, ws.state, ws.bar, (int32_t *)nullptr), "pivoted Cholesky");
         launches += 2;
         int32_t st2[2];
         unsigned int bar_err = 0;
@@ -954,23 +1012,41 @@ rsrr_status Handle::project(cudaStream_t s) {
             PK(gm.run((int)nn, kb, kt, false, ws.Qall, nn, ws.C, kt, ws.Ytmp, nn, s, false, -1.0, 1.0),
                "Qb -= Q C");
         }
-        // within the block: Qb^H Qb = Z M Z^H, Qall(:, kt:kt+kb2) = Qb Z M^{-1/2}
+        // within the block: Cholesky QR with column pivoting, Qb^H Qb =
+        // P T T^H P^T, stopped at 1e-10 of the largest diagonal; Qall(:, kt:
+        // kt+kb2) = Qb S T^{-H} (a cyclic Jacobi on this nearly-identity Gram,
+        // with its clustered eigenvalues, took 18 sweeps where the one on
+        // B^H B takes 7)
         PK(gm.run(kb, kb, (int)nn, true, ws.Ytmp, nn, ws.Ytmp, nn, ws.H, kb, s, true), "Qb^H Qb");
-        PK(jacobi_eig(ws, kb, s, &launches), "Jacobi (Qb^H Qb)");
-        std::vector<double> mu(kb);
-        PK(cudaMemcpyAsync(mu.data(), ws.evals, sizeof(double) * kb, cudaMemcpyDeviceToHost, s), "mu");
-        PK(cudaMemcpyAsync(&bar_err, ws.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s), "mu");
-        PK(cudaStreamSynchronize(s), "mu sync");
-        if (bar_err) return fail(RSRR_ETIMEOUT, "rsrr_project: grid barrier timeout (Jacobi)");
+        double maxd2 = 0.0;
         int kb2 = 0;
-        for (int j = 0; j < kb; ++j)
-            if (mu[j] > 1e-10 * mu[0]) kb2 = j + 1;
-        if (kb2 < 1) break;
-        scale_rc_kernel<<<grid1d((int64_t)kb * kb2), 256, 0, s>>>(ws.Ysort, kb, kb, kb2, nullptr,
-                                                                  ws.evals, false, true);
+        max_diag_kernel<<<1, 256, 0, s>>>(ws.acc, ws.H, kb);
+        diag_real_kernel<<<(kb + 255) / 256, 256, 0, s>>>(ws.dbuf, ws.H, kb);
+        launches += 2;
+        PK(cudaMemcpyAsync(&maxd2, ws.acc, sizeof(double), cudaMemcpyDeviceToHost, s), "block Gram diagonal");
+        PK(cudaStreamSynchronize(s), "block Gram diagonal");
+        PK(cudaMemsetAsync(ws.state, 0, sizeof(int32_t) * 4, s), "memset");
+        PK(cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int) * 4, s), "memset");
+        PK(launch_coop(pchol_persistent_kernel, (kb + 255) / 256, s, (const double2 *)ws.H, kb, ws.Lm, ws.dbuf,
+                       1e-10 * maxd2, ws.state, ws.bar, ws.order), "pivoted Cholesky (Qb^H Qb)");
         launches += 1;
+        {
+            int32_t st3[2];
+            PK(cudaMemcpyAsync(st3, ws.state, sizeof st3, cudaMemcpyDeviceToHost, s), "block rank");
+            PK(cudaMemcpyAsync(&bar_err, ws.bar + 2, sizeof bar_err, cudaMemcpyDeviceToHost, s), "block rank");
+            PK(cudaStreamSynchronize(s), "block rank sync");
+            if (bar_err) return fail(RSRR_ETIMEOUT, "rsrr_project: grid barrier timeout (pivoted Cholesky)");
+            kb2 = st3[0] ? st3[1] : kb;
+        }
+        if (kb2 < 1) break;
+        tri_from_pchol_kernel<<<grid1d((int64_t)kb2 * kb2), 256, 0, s>>>(ws.H2, ws.Lm, ws.order, kb, kb2);
+        tri_inverse_lower_kernel<<<(kb2 + 7) / 8, 256, 0, s>>>(ws.Y, ws.H2, kb2);
+        PK(cudaMemsetAsync(ws.Ysort, 0, sizeof(double2) * (size_t)kb * kb2, s), "memset");
+        scatter_inverse_fill_kernel<<<grid1d((int64_t)kb2 * kb2), 256, 0, s>>>(ws.Ysort, ws.Y, ws.order, kb, kb2);
+        PK(cudaGetLastError(), "block Cholesky QR");
+        launches += 3;
         double2 *Qnew = ws.Qall + (size_t)kt * nn;
-        PK(gm.run((int)nn, kb2, kb, false, ws.Ytmp, nn, ws.Ysort, kb, Qnew, nn, s), "Qb Z");
+        PK(gm.run((int)nn, kb2, kb, false, ws.Ytmp, nn, ws.Ysort, kb, Qnew, nn, s), "Qb S T^-H");
         const int kprev = kt;
         kt += kb2;
         // deflate the remainder: pass 1 against the new block (R is already
