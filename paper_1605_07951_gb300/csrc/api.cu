@@ -1491,10 +1491,15 @@ rsrr_status Handle::sample_band(int p0, int np, cudaStream_t s, int phase) {
         launches += 4;  // assemble, LU, probe, solve
     }
     if ((ms = mark(4, s)) != RSRR_OK) return ms;
-    // final backward errors of every column of the range (statistics and convergence)
-    CK(launch_residual(nullptr, X, dq, rmax, xmax, nullptr, s), "residual");
+    // final backward errors of every column of the range (statistics and
+    // convergence).  After iterative refinement a point flagged done was not
+    // corrected after the residual that flagged it, so its backward errors
+    // are final: only the points corrected in the last sweep are recomputed
+    const bool ir = opts.precision == RSRR_PREC_MIXED && opts.refine == RSRR_REFINE_IR && opts.max_refine > 0;
+    const int32_t *fskip = ir ? done : nullptr;
+    CK(launch_residual(nullptr, X, dq, rmax, xmax, fskip, s), "residual");
     CK(launch_eta(eta, done, rmax, xmax, d_umax, tnorm, np, L, opts.eta_tol,
-                  d_sweep_flags + opts.max_refine + 1, nullptr, s), "eta");
+                  d_sweep_flags + opts.max_refine + 1, fskip, s), "eta");
     if ((ms = mark(5, s)) != RSRR_OK) return ms;
     launches += 3;  // tnorm, final residual, final eta
     timed_sample = opts.timing != 0;
