@@ -506,7 +506,7 @@ def run_ours(a, rank, world, local):
         st64 = s64.stats()
         fms = f0.elapsed_time(f1)
         fp64 = {"sample_value": cols / (fms / 1e3), "sample_ms": fms,
-                "max_eta": st64["max_eta"], "lu_ms": st64["stage_ms"][1]}
+                "max_eta": float(np.max(s64.eta())), "lu_ms": st64["stage_ms"][1]}
         s64.close()
 
     line = {

@@ -366,7 +366,8 @@ typedef struct {
     int32_t singular_point;/* first point with an exactly zero pivot, or -1 */
     int32_t k;             /* rank kept by the last rsrr_project */
     int32_t kc;            /* columns kept by its pivoted Cholesky stage */
-    double max_eta;        /* largest per-column backward error after rsrr_sample */
+    double max_eta;        /* largest per-column backward error after rsrr_sample
+                              (NaN if one is not finite or could not be read back) */
     double sigma1, sigmak; /* largest and smallest kept singular value of S */
     size_t device_bytes;   /* device memory held by the handle */
     int64_t launches;      /* CUDA kernels launched by the handle since rsrr_create */

@@ -2,6 +2,7 @@
 // sampling points and coefficient table (RSRR step 1, Section 4.3), device
 // buffers, and the orchestration of the sampling kernels (step 2).
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -1631,15 +1632,9 @@ rsrr_status Handle::add_points(const cplx *znew, int count, cudaStream_t s) {
 
 rsrr_status Handle::read_outcome() {
     Handle *h = this;
-    if (timed_sample) {
-        float t;
-        const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
-        for (int i = 0; i < 5; ++i) {
-            CK(cudaEventElapsedTime(&t, events[pairs[i][0]], events[pairs[i][1]]), "event time");
-            stage_ms[i] = t;
-        }
-        timed_sample = false;
-    }
+    // unknown until read back: a failed copy below leaves NaN, not a stale value
+    stat_max_eta = std::numeric_limits<double>::quiet_NaN();
+    stat_converged = 0;
     std::vector<int32_t> info(N), flags(opts.max_refine + 2);
     std::vector<double> eta((size_t)N * L);
     const auto D2H = cudaMemcpyDeviceToHost;
@@ -1660,6 +1655,21 @@ rsrr_status Handle::read_outcome() {
         stat_max_eta = std::max(stat_max_eta, e);
     }
     stat_converged = (finite && stat_max_eta <= opts.eta_tol) ? 1 : 0;
+    if (!finite) stat_max_eta = std::numeric_limits<double>::quiet_NaN();
+    // the stage times after the outcome, so that a failed timing query never
+    // leaves the statistics of an earlier sampling in place (-1: not timed)
+    if (timed_sample) {
+        const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
+        for (int i = 0; i < 5; ++i) {
+            float t = -1.f;
+            if (cudaEventElapsedTime(&t, events[pairs[i][0]], events[pairs[i][1]]) != cudaSuccess) {
+                cudaGetLastError();
+                t = -1.f;
+            }
+            stage_ms[i] = t;
+        }
+        timed_sample = false;
+    }
     if (stat_singular >= 0) {
         char buf[128];
         snprintf(buf, sizeof buf, "zero pivot at sampling point %d (column %d)", stat_singular,
