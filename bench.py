@@ -175,14 +175,15 @@ def cpu_baseline(g, npts, par=True):
            "sample": f"{npts} of the 64 sampling points ({d['columns']} resolvent columns, "
                      f"scipy banded LU, FP64) in {d['seconds']:.1f} s, 1 BLAS thread",
            "cpu": cpu_model()}
+    try:
+        ncpu = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncpu = os.cpu_count() or 1
+    out["host_cores"] = {"usable": ncpu, "total": os.cpu_count()}
     if par:
-        # one process per core this process may run on, at most 16 (about
-        # 0.7 GB of host memory each at the benchmark size)
-        try:
-            ncpu = len(os.sched_getaffinity(0))
-        except AttributeError:
-            ncpu = os.cpu_count() or 1
-        procs = max(1, min(16, ncpu))
+        # one process per core this process may run on, at most one per
+        # sampling point (64; about 0.7 GB of host memory each)
+        procs = max(1, min(64, ncpu))
         pv, wall, cols = oracle_parallel(g, procs)
         out["parallel"] = {"value": pv, "unit": UNIT, "cores": procs,
                             "sample": f"{procs} sampling points, one per process (1 BLAS thread "
@@ -273,7 +274,9 @@ def run_e2e(a, s, p, stats, stream, world, dist=None):
         assert st == 0
         s.sample(stream)
         s.project(stream)
-        kk = s.stats()["k"]
+        sti = s.stats()
+        assert sti["converged"] == 1 and sti["max_eta"] <= 1e-10, sti
+        kk = sti["k"]
         st = rsrr.rsrr_get_projected(s.h, C.c_void_p(Pout.data_ptr()), 0,
                                      C.c_void_p(stream.cuda_stream))
         assert st == 0 and kk == k
@@ -392,21 +395,10 @@ def run_ours(a, rank, world, local):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # the K timed steps back to back on the device (no host reads in between)
     e0.record(stream)
     for _ in range(a.steps):
         step()
-        # the library's own events on the same stream give the stage times
-        torch.cuda.synchronize()
-        sti = s.stats()
-        asm_ms.append(sti["stage_ms"][0])
-        solve_ms.append(sti["stage_ms"][2])
-        lu_ms.append(sti["stage_ms"][1])
-        sample_ms.append(sum(sti["stage_ms"][:5]))
-        project_ms.append(sti["stage_ms"][5])
-        gemm_ms.append(sti["gemm_ms"])
-        gemm_flops.append(sti["gemm_flops"])
-        tc_ms.append(sti["tc_ms"])
-        tc_flops.append(sti["tc_flops"])
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -416,6 +408,22 @@ def run_ours(a, rank, world, local):
     stats = s.stats()
     assert stats["converged"] == 1 and stats["max_eta"] <= 1e-10, stats
     launches = (stats["launches"] - launches0)
+    # then K more steps, one at a time, for the stage times of the library's
+    # own events (the rooflines) and the convergence of every step
+    for _ in range(a.steps):
+        step()
+        torch.cuda.synchronize()
+        sti = s.stats()
+        assert sti["converged"] == 1 and sti["max_eta"] <= 1e-10, sti
+        asm_ms.append(sti["stage_ms"][0])
+        solve_ms.append(sti["stage_ms"][2])
+        lu_ms.append(sti["stage_ms"][1])
+        sample_ms.append(sum(sti["stage_ms"][:5]))
+        project_ms.append(sti["stage_ms"][5])
+        gemm_ms.append(sti["gemm_ms"])
+        gemm_flops.append(sti["gemm_flops"])
+        tc_ms.append(sti["tc_ms"])
+        tc_flops.append(sti["tc_flops"])
     cols = p.N * p.L
     value = replica_value(cols, world, ms)
 
