@@ -443,7 +443,7 @@ def run_ours(a, rank, world, local):
     # (the DRAM traffic summary under profiles/); valid for the kernel
     # revisions captured there, and only at the default size
     full = a.g == 200
-    traffic_tc = 150.4e9 if full else None      # all 37 slice GEMMs of one step
+    traffic_tc = None                           # all 37 slice GEMMs of one step (not yet captured for this revision)
     traffic_lu = 39.47e9 if full else None      # one band LU launch
     traffic_asm = 13.32e9 if full else None     # one assembly launch
     traffic_solve = 16.78e9 if full else None   # the first solve (all 64 points)

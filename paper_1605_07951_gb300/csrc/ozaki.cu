@@ -32,7 +32,6 @@
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_bf16.h>
-#include <cudaTypedefs.h>
 #include <string>
 
 #include "rsrr.h"
@@ -206,6 +205,54 @@ __global__ void oz_slice_rows_kernel(__nv_bfloat16 *__restrict__ P, const int *_
         }
         const double2 v = t[tx][r];
         store_slices(P, stride, off, v.x, v.y, E[i]);
+    }
+}
+
+// Stage images for the tensor-core kernel: the slices of one operand tile
+// (TR rows, 16 of K') stored in exactly the order that kernel keeps them in
+// shared memory, so that one bulk copy moves one operand of a stage.
+//   chunk (rb, ks): rows TR rb .. +TR-1, K' 16 ks .. +15; OZ_S TR 16 elements
+//   element (s, row, k') of a chunk at  s ss + kc kcs + 8 (row % TR) + k' % 8,
+//   kc = (k' % 16) / 8 the core-matrix column (8 rows x 16 bytes a core matrix)
+//   per-slice operand (A):          ss = 16 TR,  kcs = 8 TR
+//   slices stacked per core column (B, read as one N = 64 q operand):
+//                                   ss = 8 TR,   kcs = 8 OZ_S TR
+// Rows as in oz_slice_cols_kernel (mode 0, 1) or rows of the column-major X
+// itself (mode 2, as oz_slice_rows_kernel); rows >= R and k >= K are zeros.
+// One warp per 8 rows x 4 complex K (a core matrix of every slice): lane =
+// 4 (row % 8) + k % 4, so every slice store of a warp is 128 contiguous bytes.
+__global__ void oz_slice_tiled_kernel(__nv_bfloat16 *__restrict__ P, const int *__restrict__ E,
+                                      const double2 *__restrict__ X, int64_t ld, int mode, int R,
+                                      int Nc, int K, int Rp, int Kp, int TR, int stacked) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nrg = Rp / 8, nkg = Kp / 8, total = nrg * nkg;
+    const int64_t nks = Kp / 16;
+    const size_t ss = stacked ? 8 * (size_t)TR : 16 * (size_t)TR;
+    const size_t kcs = stacked ? 8 * (size_t)OZ_S * TR : 8 * (size_t)TR;
+    const size_t chunk = (size_t)OZ_S * TR * 16;
+    const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += wstep) {
+        // consecutive warps along the contiguous direction of X
+        const int64_t rg = mode == 2 ? w % nrg : w / nkg;
+        const int64_t kg = mode == 2 ? w / nrg : w % nkg;
+        const int r = (int)(8 * rg) + (lane >> 2);
+        const int k = (int)(4 * kg) + (lane & 3);  // complex index, k' = 2k
+        const size_t off = ((size_t)(r / TR) * nks + (size_t)(kg >> 1)) * chunk + (size_t)(kg & 1) * kcs +
+                           8 * (size_t)(r % TR) + 2 * (lane & 3);
+        if (r >= R || k >= K) {
+            store_zero(P, ss, off);
+            continue;
+        }
+        if (mode == 2) {
+            const double2 v = X[(int64_t)k * ld + r];
+            store_slices(P, ss, off, v.x, v.y, E[r]);
+        } else {
+            const int c = (mode == 1 && r >= Nc) ? r - Nc : r;
+            const double2 v = X[(int64_t)c * ld + k];
+            double re = v.x, im = -v.y;
+            if (mode == 1 && r >= Nc) { re = v.y; im = v.x; }
+            store_slices(P, ss, off, re, im, E[c]);
+        }
     }
 }
 
@@ -391,12 +438,12 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 // ----------------------------------------------------------- tcgen05 path
 // The same products on the 5th-generation tensor cores: a CTA of 256 threads
 // owns a 128 x 64 tile of C~.  Per 16-deep stage of K' the 7 A slices (128
-// rows) and the 7 B slices (64 rows each, stacked to 448 rows) are copied by
-// TMA (28 boxes of 16 bytes x rows, issued by one thread, completion counted
-// in bytes on the stage's mbarrier) into shared memory in the K-major
-// core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle), in a
-// ring of four stages; a slot is refilled once the MMAs
-// that read it have committed.  One thread issues
+// rows) and the 7 B slices (64 rows each, stacked to 448 rows) arrive by two
+// bulk copies of the TMA engine (the stage images of oz_slice_tiled_kernel,
+// 28 and 14 KB, contiguous in global memory; issued by one thread, completion
+// counted in bytes on the stage's mbarrier) in the K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix, no swizzle), in a ring of OZT_NST
+// stages; a slot is refilled once the MMAs that read it have committed.  One thread issues
 // 10 tcgen05.mma per stage (M = 128, N = 64..256, bf16 -> FP32 in tensor
 // memory): every group t = p + q has its own 64-column region of tensor
 // memory (7 regions, 448 of the 512 columns), so the pairs of one A slice
@@ -405,8 +452,8 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 // at a CTA-wide barrier except for the folds.  Groups t <= 4 hold at most
 // (t+1) 2^14 per K' element, so every 192 of K' (and at the end) all threads
 // wait for the MMAs (tcgen05.commit -> mbarrier), read their part of the
-// regions (tcgen05.ld; warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows,
-// columns 32 (w / 4) .. +31), fold groups 0..4 into 64-bit integers and add
+// regions (tcgen05.ld; warp w of 16 reads TMEM lanes 32 (w % 4) .. +31 = tile
+// rows, columns 16 (w / 4) .. +15), fold groups 0..4 into 64-bit integers and add
 // groups 5..6 (relative weight <= 2^-40, rounded by design) into an FP32 sum;
 // the next MMAs restart every region.  Every mbarrier wait is bounded; a wait that runs out is
 // counted in the caller's device status word, and from then on the CTA issues no further TMA copy
@@ -416,13 +463,20 @@ oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__rest
 constexpr int OZT_BM = 128;
 constexpr int OZT_BN = 64;
 constexpr int OZT_KC = 16;
-constexpr int OZT_THREADS = 256;
+constexpr int OZT_THREADS = 512;                 // 16 warps: 4 lane quarters x 4 column groups
+constexpr int OZT_CPT = OZT_BN / (OZT_THREADS / 128);  // tile columns a thread folds (16)
+constexpr int OZT_PRODUCER = OZT_THREADS / 2;    // the copy thread (first lane of the upper half)
 constexpr int OZT_A_SLICE = OZT_BM * OZT_KC * 2;           // bytes of one A slice per stage
 constexpr int OZT_B_SLICE = OZT_BN * OZT_KC * 2;           // bytes of one B slice per stage
 constexpr int OZT_STAGE = OZ_S * (OZT_A_SLICE + OZT_B_SLICE);
-constexpr int OZT_NST = 4;
+constexpr int OZT_NST = 5;
 constexpr int OZT_DIST = OZT_NST - 2;  // stages the copies run ahead of a fold
-constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;  // + 2 NST + 1 mbarriers, TMEM address
+// after the stages: 2 NST + 1 mbarriers, the TMEM address, the abort flag
+constexpr int OZT_TSLOT = 16 * OZT_NST + 16;
+constexpr int OZT_ABORT = OZT_TSLOT + 16;
+constexpr size_t OZT_SMEM = (size_t)OZT_NST * OZT_STAGE + 128;
+static_assert(OZT_ABORT + 4 <= 128, "barrier area");
+static_assert(OZT_SMEM <= 232448, "shared memory per CTA");
 // stage layout, K-major core matrices (8 rows x 16 bytes), no swizzle: per
 // K-column of core matrices (8 of K) all rows of an operand are contiguous,
 // 16 bytes a row, so one TMA box of 16 bytes x rows fills one such column
@@ -453,10 +507,12 @@ RSRR_DEV void umma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                  ::"r"(mbar) : "memory");
 }
-// 2-D TMA load of one box into shared memory, completion counted in bytes on mbar
-RSRR_DEV void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar) : "memory");
+// bulk copy (TMA engine) of `bytes` contiguous bytes into shared memory,
+// completion counted in bytes on mbar; both addresses 16-byte aligned, bytes
+// a multiple of 16
+RSRR_DEV void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 RSRR_DEV void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
@@ -493,13 +549,28 @@ RSRR_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+// The integer n of a group sum g = n 2^(-8t) with |n| < 2^24 (t <= 4; the
+// fold cadence bounds n), exactly, in FP32 and integer ALU operations (the
+// conversion instructions are slow on this GPU).  s = 2^(8t), s12 = 2^(8t-12):
+//   r  = fma(g, s12, 1.5 2^23) = 1.5 2^23 + h with h = rint(n 2^-12), |h| <= 2^12:
+//        the sum lies in [2^23, 2^24), where floats are the integers
+//   lo = n - 2^12 h (|lo| <= 2^11), an exact FMA;  r2 = 1.5 2^23 + lo, exact
+//   bits(r) = 0x4B400000 + h and bits(r2) = 0x4B400000 + lo, so
+//   n = 2^12 bits(r) + bits(r2) - 4097 0x4B400000  (mod 2^32; |n| < 2^31)
+RSRR_DEV int group_int(float g, float s12, float s) {
+    const float M = 12582912.f;  // 1.5 2^23
+    const float r = fmaf(g, s12, M);
+    const float lo = fmaf(r - M, -4096.f, g * s);
+    const float r2 = lo + M;
+    return (int)(((uint32_t)__float_as_int(r) << 12) + (uint32_t)__float_as_int(r2) - 4097u * 0x4B400000u);
+}
+
 __global__ void __launch_bounds__(OZT_THREADS, 1)
 oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Bs,
                   const int *__restrict__ Ea, const int *__restrict__ Eb, double *__restrict__ W,
                   double2 *__restrict__ C, int64_t ldc, int M, int N, int Mp, int Np, int Kp, int kchunk,
                   int halfN_tiles, int upper_only, double alpha, double beta,
-                  unsigned int *__restrict__ status,
-                  const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+                  unsigned int *__restrict__ status) {
     const int bm = blockIdx.x, bn = blockIdx.y, sp = blockIdx.z;
     if (upper_only && OZT_BM * bm > OZT_BN * (bn % halfN_tiles) + OZT_BN - 1) return;
     extern __shared__ __align__(1024) unsigned char ozt_smem[];
@@ -507,16 +578,17 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     const uint32_t mb_full = sbase + OZT_NST * OZT_STAGE;  // OZT_NST: stage's bytes landed (TMA)
     const uint32_t mb_empty = mb_full + 8 * OZT_NST;       // OZT_NST: stage's MMAs done
     const uint32_t mb_fold = mb_empty + 8 * OZT_NST;       // all MMAs so far done
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(ozt_smem + OZT_NST * OZT_STAGE + 96);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(ozt_smem + OZT_NST * OZT_STAGE + OZT_TSLOT);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(ozt_smem + OZT_NST * OZT_STAGE + OZT_ABORT);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = bm * OZT_BM, n0 = bn * OZT_BN;
     const int kbeg = sp * kchunk;
     const int kend = min(Kp, kbeg + kchunk);
     const int nk = kend > kbeg ? (kend - kbeg) / OZT_KC : 0;
-    // roles: warp 4 lane 0 copies the stages, warp 0 lane 0 issues the MMAs, all
-    // eight warps fold (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..)
-    const bool producer = warp >= 4;
+    // roles: thread OZT_PRODUCER copies the stages, thread 0 issues the MMAs,
+    // all sixteen warps fold (warp w: TMEM lanes 32 (w % 4) .., columns
+    // 16 (w / 4) ..)
+    const bool producer = tid >= OZT_PRODUCER;
 
     if (tid == 0) {
         for (int q = 0; q < OZT_NST; ++q) {
@@ -535,13 +607,13 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tslot;
-    const int lrow = 32 * (warp & 3) + lane, lcol = 32 * (warp >> 2);
+    const int lrow = 32 * (warp & 3) + lane, lcol = OZT_CPT * (warp >> 2);
     const uint32_t tpart = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)lcol;
 
-    long long acc[32];
-    float low[32];
+    long long acc[OZT_CPT];
+    float low[OZT_CPT];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
+    for (int c = 0; c < OZT_CPT; ++c) {
         acc[c] = 0;
         low[c] = 0.f;
     }
@@ -556,29 +628,33 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
         }
         ++folds;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        static_assert(OZT_CPT == 16, "one 16-column TMEM load per region");
 #pragma unroll
         for (int t = 0; t < OZ_S; ++t) {
+            uint32_t r[16];
+            tmem_ld16(tpart + (uint32_t)(t * OZT_BN), r);
 #pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tpart + (uint32_t)(t * OZT_BN + c0), r);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (t < 5) acc[c0 + j] += scaled_group_to_ll(__uint_as_float(r[j]));
-                    else low[c0 + j] += __uint_as_float(r[j]);
-                }
+            for (int j = 0; j < 16; ++j) {
+                if (t < 5)
+                    acc[j] += (long long)group_int(__uint_as_float(r[j]), 0x1p-12f * (float)(1ull << (8 * t)),
+                                                   (float)(1ull << (8 * t)))
+                              << (32 - 8 * t);
+                else
+                    low[j] += __uint_as_float(r[j]);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         asm volatile("bar.sync 1, %0;\n" ::"n"(OZT_THREADS) : "memory");  // regions free again
     };
     if (producer) {
-        // one thread issues the stage copies (TMA boxes of 8 K-elements x rows,
-        // each box one column of 8 x 16-byte core matrices), OZT_DIST stages
-        // ahead of the fold that follows a stage
+        // one thread issues the stage copies (one stage image of each operand),
+        // OZT_DIST stages ahead of the fold that follows a stage
+        const size_t nks = (size_t)(Kp / OZT_KC);
+        const __nv_bfloat16 *srcA = As + (size_t)bm * nks * (OZ_S * OZT_BM * OZT_KC);
+        const __nv_bfloat16 *srcB = Bs + (size_t)bn * nks * (OZ_S * OZT_BN * OZT_KC);
         int issued = 0;  // stages whose copies were issued (all of them unless a wait ran out)
         for (int st = 0; st < nk + OZT_DIST; ++st) {
-            if (st < nk && tid == 4 * 32 && !*abort_flag) {
+            if (st < nk && tid == OZT_PRODUCER && !*abort_flag) {
                 const int slot = st % OZT_NST;
                 // slot st % NST was last read by the MMAs of stage st - NST
                 if (st >= OZT_NST &&
@@ -587,20 +663,15 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
                     *abort_flag = 1;
                 }
             }
-            if (st < nk && tid == 4 * 32 && !*abort_flag) {
+            if (st < nk && tid == OZT_PRODUCER && !*abort_flag) {
                 const int slot = st % OZT_NST;
                 const uint32_t full = mb_full + 8 * slot;
                 mbar_expect_tx(full, (uint32_t)OZT_STAGE);
                 const uint32_t a0 = sbase + (uint32_t)(slot * OZT_STAGE);
                 const uint32_t b0 = a0 + OZ_S * OZT_A_SLICE;
-                const int k = kbeg + st * OZT_KC;
-#pragma unroll
-                for (int p = 0; p < OZ_S; ++p)
-#pragma unroll
-                    for (int kc = 0; kc < 2; ++kc) {
-                        tma_load_2d(a0 + p * OZT_A_SLICE + kc * OZT_LBO_A, &tmA, k + 8 * kc, p * Mp + m0, full);
-                        tma_load_2d(b0 + kc * OZT_LBO_B + p * OZT_BN * 16, &tmB, k + 8 * kc, p * Np + n0, full);
-                    }
+                const size_t ks = (size_t)(kbeg / OZT_KC + st);
+                bulk_load(a0, srcA + ks * (OZ_S * OZT_BM * OZT_KC), (uint32_t)(OZ_S * OZT_A_SLICE), full);
+                bulk_load(b0, srcB + ks * (OZ_S * OZT_BN * OZT_KC), (uint32_t)(OZ_S * OZT_B_SLICE), full);
                 issued = st + 1;
             }
             __syncwarp();
@@ -609,7 +680,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
         }
         // every copy that was issued has landed before the CTA leaves (waits
         // bounded; the last issued stage of each slot is its latest phase)
-        if (tid == 4 * 32)
+        if (tid == OZT_PRODUCER)
             for (int st = max(0, issued - OZT_NST); st < issued; ++st)
                 ok = mbar_wait(mb_full + 8 * (st % OZT_NST), (st / OZT_NST) & 1) && ok;
         __syncwarp();
@@ -654,7 +725,7 @@ oz_gemm_tc_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__r
     const int i = m0 + lrow;
     const int ea = Ea[i];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
+    for (int c = 0; c < OZT_CPT; ++c) {
         const int jj = n0 + lcol + c;
         const double v = ldexp((double)acc[c] + (double)low[c] * 0x1p32, ea + Eb[jj] - 2090);
         if (W) {
@@ -826,31 +897,6 @@ double ozaki_tc_flops(int M, int N, int K, bool hermitian, bool legacy) {
     return 2.0 * pairs * tiles * bm * OZ_BN * (double)p.Kp;
 }
 
-// TMA descriptor of a stacked slice array (rows x Kp bf16, row-major, rows =
-// 7 x padded rows): boxes of 8 K-elements (16 bytes) x box_rows rows
-static cudaError_t slice_tensor_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t Kp,
-                                    int64_t rows, int box_rows) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            fn = nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }();
-    if (!encode) return cudaErrorNotSupported;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || (Kp % 8) || rows <= 0) return cudaErrorInvalidValue;
-    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(__nv_bfloat16)};
-    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims,
-                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64_t lda,
                         const double2 *B, int64_t ldb, double2 *C, int64_t ldc, double alpha,
                         double beta, bool hermitian, void *ws, size_t ws_bytes, cudaStream_t s,
@@ -884,11 +930,6 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
     double *Wp = p.splits > 1 ? reinterpret_cast<double *>(w) : nullptr;
     const bool upper = hermitian && (N % OZ_BN) == 0;
     const int halfN_tiles = upper ? N / OZ_BN : (int)(p.Np / OZ_BN);
-    CUtensorMap tmA{}, tmB{};
-    if (!legacy) {
-        if ((e = slice_tensor_map(&tmA, As, p.Kp, OZ_S * p.Mp, OZT_BM)) != cudaSuccess) return e;
-        if ((e = slice_tensor_map(&tmB, Bs, p.Kp, OZ_S * p.Np, OZT_BN)) != cudaSuccess) return e;
-    }
 
     for (int64_t kc0 = 0; kc0 < K; kc0 += p.Kc) {
         const int Kc = (int)std::min<int64_t>(p.Kc, K - kc0);
@@ -902,15 +943,26 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
             oz_rowexp_kernel<<<dim3((unsigned)((M + 31) / 32), (unsigned)((Kc + 255) / 256)), 256, 0, s>>>(
                 Ea, Ak, lda, M, Kc);
         oz_colexp_kernel<<<std::min(N, 65535), 256, 0, s>>>(Eb, Bk, ldb, Kc, N, N);
-        const int kx = (int)std::min<int64_t>((p.Kp / 2 + 255) / 256, 64);
-        if (conjA)
-            oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Mp, 65535)), 256, 0, s>>>(
-                As, Ea, Ak, lda, 0, M, M, Kc, (int)p.Mp, (int)p.Kp);
-        else
-            oz_slice_rows_kernel<<<dim3((unsigned)(p.Mp / 32), (unsigned)((p.Kp / 2 + 31) / 32)), 256, 0, s>>>(
-                As, Ea, Ak, lda, M, Kc, (int)p.Mp, (int)p.Kp);
-        oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Np, 65535)), 256, 0, s>>>(
-            Bs, Eb, Bk, ldb, 1, 2 * N, N, Kc, (int)p.Np, (int)p.Kp);
+        if (legacy) {
+            const int kx = (int)std::min<int64_t>((p.Kp / 2 + 255) / 256, 64);
+            if (conjA)
+                oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Mp, 65535)), 256, 0, s>>>(
+                    As, Ea, Ak, lda, 0, M, M, Kc, (int)p.Mp, (int)p.Kp);
+            else
+                oz_slice_rows_kernel<<<dim3((unsigned)(p.Mp / 32), (unsigned)((p.Kp / 2 + 31) / 32)), 256, 0,
+                                       s>>>(As, Ea, Ak, lda, M, Kc, (int)p.Mp, (int)p.Kp);
+            oz_slice_cols_kernel<<<dim3(kx, (unsigned)std::min<int64_t>(p.Np, 65535)), 256, 0, s>>>(
+                Bs, Eb, Bk, ldb, 1, 2 * N, N, Kc, (int)p.Np, (int)p.Kp);
+        } else {
+            // stage images: one warp per 8 rows x 8 of K'
+            auto blocks = [](int64_t rows, int64_t kp) {
+                return (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows / 8 * (kp / 8) / 8, 152 * 16));
+            };
+            oz_slice_tiled_kernel<<<blocks(p.Mp, p.Kp), 256, 0, s>>>(As, Ea, Ak, lda, conjA ? 0 : 2, M, M, Kc,
+                                                                     (int)p.Mp, (int)p.Kp, OZT_BM, 0);
+            oz_slice_tiled_kernel<<<blocks(p.Np, p.Kp), 256, 0, s>>>(Bs, Eb, Bk, ldb, 1, 2 * N, N, Kc,
+                                                                     (int)p.Np, (int)p.Kp, OZT_BN, 1);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const dim3 grid((unsigned)(p.Mp / bm), (unsigned)(p.Np / OZ_BN), (unsigned)p.splits);
         cudaEvent_t ev1 = nullptr;
@@ -928,8 +980,7 @@ cudaError_t ozaki_zgemm(int M, int N, int K, bool conjA, const double2 *A, int64
             oz_gemm_tc_kernel<<<grid, OZT_THREADS, OZT_SMEM, s>>>(As, Bs, Ea, Eb, Wp, C, ldc, M, N,
                                                                  (int)p.Mp, (int)p.Np, (int)p.Kp,
                                                                  (int)p.kchunk, halfN_tiles,
-                                                                 upper ? 1 : 0, alpha, b, status,
-                                                                 tmA, tmB);
+                                                                 upper ? 1 : 0, alpha, b, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (timer && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
         if (tc_flops) *tc_flops += ozaki_tc_flops(M, N, Kc, upper, legacy);
