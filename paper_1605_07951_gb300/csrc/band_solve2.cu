@@ -207,15 +207,21 @@ band_solve2_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ bpe
                     r0 = max(0, b.j0 - KV);
                     r1 = pj == nblk - 1 ? n : max(0, b.j0 + NB - KV);
                 }
+                // rows r0 .. r1-1 (fewer than WR) in 32-row by 16-column passes
                 const int nr = max(0, r1 - r0);
-                for (int o = tid; o < nr * LC; o += S2_THREADS) {
-                    const int i = r0 + o % nr, col = o / nr;
-                    C *dst = W + (size_t)(i % WR) * WLD + col;
-                    if (col < ncol)
-                        s2_cp_elem<C>((unsigned)__cvta_generic_to_shared(dst), B + (size_t)col * n + i);
-                    else
-                        *dst = czero<C>();
-                }
+                const int w0 = r0 % WR;
+                for (int rb = 0; rb < nr; rb += 32)
+                    for (int cb = 0; cb < LC; cb += S2_THREADS / 32) {
+                        const int rr = rb + (tid & 31), col = cb + (tid >> 5);
+                        if (rr >= nr || col >= LC) continue;
+                        int wrow = w0 + rr;
+                        if (wrow >= WR) wrow -= WR;
+                        C *dst = W + (size_t)wrow * WLD + col;
+                        if (col < ncol)
+                            s2_cp_elem<C>((unsigned)__cvta_generic_to_shared(dst), B + (size_t)col * n + r0 + rr);
+                        else
+                            *dst = czero<C>();
+                    }
             }
             const int rows = s2_rows(phase, b, KV);
             const int ra = pk * S2_RC;
@@ -250,19 +256,24 @@ band_solve2_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ bpe
             const C *D = reinterpret_cast<const C *>(slot);
             const int32_t *pairs = reinterpret_cast<const int32_t *>(slot + LY::D_BYTES);
             const C *P = reinterpret_cast<const C *>(slot + LY::D_BYTES + LY::P_BYTES);
+            // window row of the block's first row: a multiple of NB at most
+            // WR - NB, so the block's rows jb0 .. jb0+NB-1 do not wrap; rows
+            // below it (offsets < kl + NB <= WR) wrap at most once
+            const int jb0 = b.j0 % WR;
+            auto wrow = [&](int off) { const int r = jb0 + off; return r >= WR ? r - WR : r; };
             if (ck == 0) {
                 if (phase == 0) {
                     // composed permutation of the block's window
                     for (int o = tid; o < PAIRS * LC; o += S2_THREADS) {
                         const int e = o % PAIRS, col = o / PAIRS;
                         const int pr = pairs[e];
-                        if (pr >= 0) Gp[col * PAIRS + e] = W[(size_t)((b.j0 + (pr & 0xFFFF)) % WR) * WLD + col];
+                        if (pr >= 0) Gp[col * PAIRS + e] = W[(size_t)wrow(pr & 0xFFFF) * WLD + col];
                     }
                     __syncthreads();
                     for (int o = tid; o < PAIRS * LC; o += S2_THREADS) {
                         const int e = o % PAIRS, col = o / PAIRS;
                         const int pr = pairs[e];
-                        if (pr >= 0) W[(size_t)((b.j0 + (pr >> 16)) % WR) * WLD + col] = Gp[col * PAIRS + e];
+                        if (pr >= 0) W[(size_t)wrow(pr >> 16) * WLD + col] = Gp[col * PAIRS + e];
                     }
                     __syncthreads();
                 }
@@ -271,9 +282,10 @@ band_solve2_kernel(const C *__restrict__ ab_all, const int32_t *__restrict__ bpe
                     const int col = o % LC, r = o / LC;
                     C v = czero<C>();
                     if (r < b.jb) {
+                        const C *Wb = W + (size_t)jb0 * WLD + col;
 #pragma unroll 8
                         for (int t = 0; t < b.jb; ++t)
-                            v = cfma(v, D[t * NB + r], W[(size_t)((b.j0 + t) % WR) * WLD + col]);
+                            v = cfma(v, D[t * NB + r], Wb[(size_t)t * WLD]);
                         if (col < ncol) B[(size_t)col * n + b.j0 + r] = v;
                     }
                     Yb[r * LC + col] = v;
@@ -329,7 +341,11 @@ cudaError_t launch_block_perm(int32_t *bperm, const int32_t *piv, int n, int kl,
     return cudaGetLastError();
 }
 
-static int s2_window(const BandGeom &g, int nb, int nslot) { return g.kl + g.ku + nslot * nb; }
+// window rows: every row live at once, rounded up to a multiple of the block
+// size so that the NB rows of a block (j0 a multiple of NB) never wrap around
+static int s2_window(const BandGeom &g, int nb, int nslot) {
+    return (g.kl + g.ku + nslot * nb + nb - 1) / nb * nb;
+}
 
 template <typename C, int NB, int LC, int RC, int NSLOT>
 static size_t s2_smem(const BandGeom &g) {
