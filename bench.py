@@ -444,7 +444,7 @@ def run_ours(a, rank, world, local):
     # revisions captured there, and only at the default size
     full = a.g == 200
     traffic_tc = 101.9e9 if full else None      # all 37 slice GEMMs of one step
-    traffic_lu = 39.59e9 if full else None      # one band LU launch
+    traffic_lu = 39.66e9 if full else None      # one band LU launch
     traffic_asm = 13.32e9 if full else None     # one assembly launch
     traffic_solve = 16.78e9 if full else None   # the first solve (all 64 points)
     tc_avg = statistics.mean(tc_ms)
